@@ -1,0 +1,527 @@
+/* FP64 CPU oracle of the grouped spectral fit -- test infrastructure only.
+ *
+ * Plain loops in double precision, written for a reader to check against
+ * arXiv 2512.24840 section 2.2 by eye.  No blocking, fusion or reordering
+ * beyond what the equations state.  Loaded only by the tests, the smoke check
+ * and the benchmark's CPU-baseline leg; it shares nothing with the CUDA path.
+ *
+ * Readings of the paper used here (each also listed in the design notes):
+ *  - loss: per spectrum l_i = sqrt(sum_j W_ij eps_ij^2 / p) (Eq. 9 with N = 1);
+ *    the group objective is sum_i l_i, so Adam (elementwise) runs per spectrum.
+ *  - W = A ivar / mean(ivar over used pixels); uniform ivar gives Eq. 9 exactly.
+ *  - kernel (Eq. 5): F''_j = sum_{s=-h..h} g_s F'_{j+H-s}, g_s the sampled
+ *    Gaussian exp(-(s-mu)^2 / 2 sigma^2) normalised to unit sum,
+ *    h = ceil(|mu| + 5 sigma); mu = RV / (c dln), sigma = sigma_v / (c dln).
+ *  - the model grid extends the observed one by H = pad pixels each side.
+ *  - Legendre nodes x_j = -1 + 2 j / p, j = 0..p-1 (Eq. 6 as printed).
+ *  - WLS weights of the continuum fit are the loss weights W.
+ *  - stop rules (stage 8): after evaluating l_t: |l_t - l_{t-50}| < tol, or 50
+ *    consecutive rises, or t = max_steps; the parameters returned are x_t.
+ */
+#include "lasp_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define C_KMS 299792.458
+
+int orc_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void orc_phys_from_x(const orc_model* M, const double* x, double* th) {
+    for (int k = 0; k < 5; ++k) th[k] = M->plo[k] + 0.5 * (x[k] + 1.0) * (M->phi[k] - M->plo[k]);
+}
+
+void orc_x_from_phys(const orc_model* M, const double* th, double* x) {
+    for (int k = 0; k < 5; ++k) x[k] = 2.0 * (th[k] - M->plo[k]) / (M->phi[k] - M->plo[k]) - 1.0;
+}
+
+static double ipow(double u, int a) {
+    double r = 1.0;
+    for (int i = 0; i < a; ++i) r *= u;
+    return r;
+}
+
+/* Eq. 1 with one polynomial regime: phi_k = u_T^a u_g^b u_f^c, the u's the
+ * basis variables (log10 Teff, log g, [Fe/H]) mapped linearly onto [-1, 1]. */
+void orc_basis(const orc_model* M, const double* th, double* phi, double* dphi) {
+    double v[3] = {log10(th[0]), th[1], th[2]};
+    double u[3], du[3];
+    for (int i = 0; i < 3; ++i) {
+        u[i] = 2.0 * (v[i] - M->blo[i]) / (M->bhi[i] - M->blo[i]) - 1.0;
+        du[i] = 2.0 / (M->bhi[i] - M->blo[i]);
+    }
+    du[0] /= th[0] * log(10.0);           /* d log10(Teff) / d Teff */
+    for (int k = 0; k < M->K; ++k) {
+        int a = M->exps[3 * k], b = M->exps[3 * k + 1], c = M->exps[3 * k + 2];
+        phi[k] = ipow(u[0], a) * ipow(u[1], b) * ipow(u[2], c);
+        if (dphi) {
+            dphi[3 * k + 0] = a ? a * ipow(u[0], a - 1) * ipow(u[1], b) * ipow(u[2], c) * du[0] : 0.0;
+            dphi[3 * k + 1] = b ? b * ipow(u[0], a) * ipow(u[1], b - 1) * ipow(u[2], c) * du[1] : 0.0;
+            dphi[3 * k + 2] = c ? c * ipow(u[0], a) * ipow(u[1], b) * ipow(u[2], c - 1) * du[2] : 0.0;
+        }
+    }
+}
+
+/* Eq. 5 kernel G(mu, sigma) of length 2 ceil(|mu| + 5 sigma) + 1. */
+int orc_kernel(double mu, double sig, int H, double* g, double* dg_dmu, double* dg_dsig) {
+    int h = (int)ceil(fabs(mu) + 5.0 * sig);
+    if (h > H) h = H;
+    if (h < 0) h = 0;
+    int n = 2 * H + 1;
+    double Z = 0.0, md = 0.0, mq = 0.0;
+    for (int i = 0; i < n; ++i) {
+        int s = i - H;
+        g[i] = 0.0;
+        if (s < -h || s > h) continue;
+        g[i] = exp(-(s - mu) * (s - mu) / (2.0 * sig * sig));
+        Z += g[i];
+    }
+    for (int i = 0; i < n; ++i) g[i] /= Z;
+    for (int i = 0; i < n; ++i) {
+        int s = i - H;
+        md += g[i] * (s - mu) / (sig * sig);
+        mq += g[i] * (s - mu) * (s - mu) / (sig * sig * sig);
+    }
+    for (int i = 0; i < n; ++i) {
+        int s = i - H;
+        if (dg_dmu) dg_dmu[i] = g[i] * ((s - mu) / (sig * sig) - md);
+        if (dg_dsig) dg_dsig[i] = g[i] * ((s - mu) * (s - mu) / (sig * sig * sig) - mq);
+    }
+    return h;
+}
+
+/* Legendre polynomials by Bonnet's recursion at x_j = -1 + 2 j / p. */
+void orc_legendre(int p, int D, double* out) {
+    for (int j = 0; j < p; ++j) {
+        double x = -1.0 + 2.0 * j / p;
+        double* P = out + (size_t)j * (D + 1);
+        P[0] = 1.0;
+        if (D >= 1) P[1] = x;
+        for (int n = 1; n < D; ++n) P[n + 1] = ((2 * n + 1) * x * P[n] - n * P[n - 1]) / (n + 1);
+    }
+}
+
+static void interp_and_broaden(const orc_model* M, const double* th, double* Fp, double* Fpp,
+                               double* g, double* dgm, double* dgs, double* phi, double* dphi) {
+    int H = M->pad, p = M->n_pix, nm = p + 2 * H;
+    orc_basis(M, th, phi, dphi);
+    for (int m = 0; m < nm; ++m) {                     /* Eq. 1: F' = phi C */
+        double acc = 0.0;
+        for (int k = 0; k < M->K; ++k) acc += phi[k] * M->C[(size_t)k * nm + m];
+        Fp[m] = acc;
+    }
+    double mu = th[3] / (C_KMS * M->dln), sig = th[4] / (C_KMS * M->dln);
+    orc_kernel(mu, sig, H, g, dgm, dgs);
+    for (int j = 0; j < p; ++j) {                      /* Eq. 5: F'' = F' (x) G */
+        double acc = 0.0;
+        for (int s = -H; s <= H; ++s) acc += g[s + H] * Fp[j + H - s];
+        Fpp[j] = acc;
+    }
+}
+
+void orc_model_flux(const orc_model* M, const double* th, const double* b, double* Fp,
+                    double* Fpp, double* cont, double* model) {
+    int H = M->pad, p = M->n_pix, D = M->deg;
+    double* g = malloc(sizeof(double) * (2 * H + 1));
+    double* phi = malloc(sizeof(double) * M->K);
+    double* P = malloc(sizeof(double) * (size_t)p * (D + 1));
+    interp_and_broaden(M, th, Fp, Fpp, g, NULL, NULL, phi, NULL);
+    orc_legendre(p, D, P);
+    for (int j = 0; j < p; ++j) {                      /* Eq. 6: (P b) * F'' */
+        double c = 0.0;
+        for (int d = 0; d <= D; ++d) c += b[d] * P[(size_t)j * (D + 1) + d];
+        if (cont) cont[j] = c;
+        if (model) model[j] = c * Fpp[j];
+    }
+    free(g); free(phi); free(P);
+}
+
+/* Backward through the broadening and the interpolator, given dL/dF''.
+ * Adds to gth[0..4] (physical parameters). */
+static void backprop_fpp(const orc_model* M, const double* Fp,
+                         const double* gFpp, const double* dgm, const double* dgs,
+                         const double* g, const double* dphi, double* gth) {
+    int H = M->pad, p = M->n_pix, nm = p + 2 * H;
+    double gmu = 0.0, gsig = 0.0;
+    for (int j = 0; j < p; ++j) {
+        for (int s = -H; s <= H; ++s) {
+            gmu += gFpp[j] * dgm[s + H] * Fp[j + H - s];
+            gsig += gFpp[j] * dgs[s + H] * Fp[j + H - s];
+        }
+    }
+    double* gFp = calloc(nm, sizeof(double));
+    for (int j = 0; j < p; ++j)
+        for (int s = -H; s <= H; ++s) gFp[j + H - s] += gFpp[j] * g[s + H];
+    for (int k = 0; k < M->K; ++k) {
+        double gphi = 0.0;
+        for (int m = 0; m < nm; ++m) gphi += gFp[m] * M->C[(size_t)k * nm + m];
+        for (int i = 0; i < 3; ++i) gth[i] += gphi * dphi[3 * k + i];
+    }
+    gth[3] += gmu / (C_KMS * M->dln);
+    gth[4] += gsig / (C_KMS * M->dln);
+    free(gFp);
+}
+
+void orc_model_vjp(const orc_model* M, const double* th, const double* b, const double* gm,
+                   double* gth, double* gb) {
+    int H = M->pad, p = M->n_pix, nm = p + 2 * H, D = M->deg;
+    double* Fp = malloc(sizeof(double) * nm);
+    double* Fpp = malloc(sizeof(double) * p);
+    double* g = malloc(sizeof(double) * (2 * H + 1));
+    double* dgm = malloc(sizeof(double) * (2 * H + 1));
+    double* dgs = malloc(sizeof(double) * (2 * H + 1));
+    double* phi = malloc(sizeof(double) * M->K);
+    double* dphi = malloc(sizeof(double) * 3 * M->K);
+    double* P = malloc(sizeof(double) * (size_t)p * (D + 1));
+    double* gFpp = malloc(sizeof(double) * p);
+    interp_and_broaden(M, th, Fp, Fpp, g, dgm, dgs, phi, dphi);
+    orc_legendre(p, D, P);
+    for (int d = 0; d <= D; ++d) gb[d] = 0.0;
+    for (int j = 0; j < p; ++j) {
+        double c = 0.0;
+        for (int d = 0; d <= D; ++d) c += b[d] * P[(size_t)j * (D + 1) + d];
+        for (int d = 0; d <= D; ++d) gb[d] += gm[j] * Fpp[j] * P[(size_t)j * (D + 1) + d];
+        gFpp[j] = gm[j] * c;
+    }
+    for (int k = 0; k < 5; ++k) gth[k] = 0.0;
+    backprop_fpp(M, Fp, gFpp, dgm, dgs, g, dphi, gth);
+    free(Fp); free(Fpp); free(g); free(dgm); free(dgs); free(phi); free(dphi); free(P); free(gFpp);
+}
+
+static int cmp_double(const void* a, const void* b) {
+    double x = *(const double*)a, y = *(const double*)b;
+    return (x > y) - (x < y);
+}
+
+int orc_prep(int n_pix, const float* flux, const float* ivar, const unsigned char* good,
+             double quantile, int edge_px, double* y, double* W, double* w_out) {
+    double* v = malloc(sizeof(double) * n_pix);
+    int n = 0;
+    double isum = 0.0;
+    for (int j = 0; j < n_pix; ++j) {
+        int use = good[j] && ivar[j] > 0.0f && isfinite(flux[j]) && isfinite(ivar[j]);
+        if (use) { v[n++] = flux[j]; isum += ivar[j]; }
+    }
+    double w = NAN;
+    if (n > 0) {
+        qsort(v, n, sizeof(double), cmp_double);
+        double pos = quantile * (n - 1);
+        int lo = (int)floor(pos);
+        if (lo >= n - 1) w = v[n - 1];
+        else w = v[lo] + (pos - lo) * (v[lo + 1] - v[lo]);
+    }
+    double imean = n > 0 ? isum / n : 0.0;
+    int n_obj = 0;
+    for (int j = 0; j < n_pix; ++j) {
+        int use = good[j] && ivar[j] > 0.0f && isfinite(flux[j]) && isfinite(ivar[j]);
+        int edge = j < edge_px || j >= n_pix - edge_px;
+        if (use && !edge && w > 0.0) {
+            y[j] = flux[j] / w;
+            W[j] = ivar[j] / imean;
+            ++n_obj;
+        } else {
+            y[j] = 0.0;
+            W[j] = 0.0;
+        }
+    }
+    *w_out = w;
+    free(v);
+    return n_obj;
+}
+
+/* Cholesky solve of the (n x n) SPD system A z = r.  Returns 0 if A is not
+ * numerically positive definite. */
+static int chol_solve(int n, const double* A, const double* r, double* z) {
+    double L[64], t[8];
+    for (int i = 0; i < n; ++i) {
+        for (int j = 0; j <= i; ++j) {
+            double s = A[i * n + j];
+            for (int k = 0; k < j; ++k) s -= L[i * n + k] * L[j * n + k];
+            if (i == j) {
+                if (!(s > 0.0)) return 0;
+                L[i * n + i] = sqrt(s);
+            } else {
+                L[i * n + j] = s / L[j * n + j];
+            }
+        }
+    }
+    for (int i = 0; i < n; ++i) {
+        double s = r[i];
+        for (int k = 0; k < i; ++k) s -= L[i * n + k] * t[k];
+        t[i] = s / L[i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double s = t[i];
+        for (int k = i + 1; k < n; ++k) s -= L[k * n + i] * z[k];
+        z[i] = s / L[i * n + i];
+    }
+    return 1;
+}
+
+/* Eq. 6 by weighted least squares: minimise sum_j W_j (y_j - (P b)_j F''_j)^2. */
+static int solve_continuum(int p, int D, const double* P, const double* Fpp, const double* y,
+                           const double* W, double* b) {
+    int n = D + 1;
+    double G[64], r[8];
+    for (int a = 0; a < n; ++a) {
+        r[a] = 0.0;
+        for (int c = 0; c < n; ++c) G[a * n + c] = 0.0;
+    }
+    for (int j = 0; j < p; ++j) {
+        const double* Pj = P + (size_t)j * n;
+        for (int a = 0; a < n; ++a) {
+            r[a] += W[j] * Fpp[j] * y[j] * Pj[a];
+            for (int c = 0; c < n; ++c) G[a * n + c] += W[j] * Fpp[j] * Fpp[j] * Pj[a] * Pj[c];
+        }
+    }
+    return chol_solve(n, G, r, b);
+}
+
+unsigned orc_eval(const orc_model* M, const double* y, const double* W, const double* x,
+                  double* loss, double* grad_x, double* b_out, double* eps_out, double* cont_out) {
+    int H = M->pad, p = M->n_pix, nm = p + 2 * H, D = M->deg;
+    unsigned st = 0;
+    double th[5], b[8];
+    for (int d = 0; d < 8; ++d) b[d] = NAN;
+    double* Fp = malloc(sizeof(double) * nm);
+    double* Fpp = malloc(sizeof(double) * p);
+    double* g = malloc(sizeof(double) * (2 * H + 1));
+    double* dgm = malloc(sizeof(double) * (2 * H + 1));
+    double* dgs = malloc(sizeof(double) * (2 * H + 1));
+    double* phi = malloc(sizeof(double) * M->K);
+    double* dphi = malloc(sizeof(double) * 3 * M->K);
+    double* P = malloc(sizeof(double) * (size_t)p * (D + 1));
+    double* gFpp = malloc(sizeof(double) * p);
+    orc_phys_from_x(M, x, th);
+    interp_and_broaden(M, th, Fp, Fpp, g, dgm, dgs, phi, dphi);
+    orc_legendre(p, D, P);
+    if (!solve_continuum(p, D, P, Fpp, y, W, b)) {
+        st |= ORC_ST_SINGULAR;
+        *loss = NAN;
+        for (int k = 0; k < 5; ++k) grad_x[k] = 0.0;
+        goto done;
+    }
+    double S = 0.0;
+    for (int j = 0; j < p; ++j) {                      /* Eq. 7 residual */
+        double c = 0.0;
+        for (int d = 0; d <= D; ++d) c += b[d] * P[(size_t)j * (D + 1) + d];
+        double e = y[j] - c * Fpp[j];
+        S += W[j] * e * e;
+        if (W[j] > 0.0 && c <= 0.0) st |= ORC_ST_NONPOS;
+        if (eps_out) eps_out[j] = e;
+        if (cont_out) cont_out[j] = c;
+        gFpp[j] = -W[j] * e * c;                       /* d(S/2)/dF''_j, b held at b* */
+    }
+    double l = sqrt(S / p);                            /* Eq. 9, one spectrum */
+    *loss = l;
+    double scale = l > 0.0 ? 1.0 / (p * l) : 0.0;      /* dl/dS = 1 / (2 p l) */
+    for (int j = 0; j < p; ++j) gFpp[j] *= scale;
+    double gth[5] = {0, 0, 0, 0, 0};
+    backprop_fpp(M, Fp, gFpp, dgm, dgs, g, dphi, gth);
+    for (int k = 0; k < 5; ++k) grad_x[k] = gth[k] * 0.5 * (M->phi[k] - M->plo[k]);
+    if (!isfinite(l)) st |= ORC_ST_NONFINITE;
+    for (int k = 0; k < 5; ++k) if (!isfinite(grad_x[k])) st |= ORC_ST_NONFINITE;
+done:
+    if (b_out) for (int d = 0; d <= D; ++d) b_out[d] = b[d];
+    free(Fp); free(Fpp); free(g); free(dgm); free(dgs); free(phi); free(dphi); free(P); free(gFpp);
+    return st;
+}
+
+/* torch.optim.Adam update with default options except lr, then projection
+ * onto the box [-1, 1] (the parameters are normalised to that range). */
+void orc_adam_update(int n, double* x, double* m, double* v, const double* g, int t, double lr,
+                     double b1, double b2, double eps, int clamp) {
+    double bc1 = 1.0 - pow(b1, t), bc2 = 1.0 - pow(b2, t);
+    for (int i = 0; i < n; ++i) {
+        m[i] = b1 * m[i] + (1.0 - b1) * g[i];
+        v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
+        double denom = sqrt(v[i]) / sqrt(bc2) + eps;
+        x[i] -= (lr / bc1) * m[i] / denom;
+        if (clamp) {
+            if (x[i] < -1.0) x[i] = -1.0;
+            if (x[i] > 1.0) x[i] = 1.0;
+        }
+    }
+}
+
+unsigned orc_stop_rule(const double* hist, int t, int window, double tol, int max_steps) {
+    if (t >= window) {
+        if (fabs(hist[t] - hist[t - window]) < tol) return ORC_ST_CONV_TOL;
+        int rising = 1;
+        for (int i = t - window + 1; i <= t; ++i)
+            if (!(hist[i] > hist[i - 1])) { rising = 0; break; }
+        if (rising) return ORC_ST_CONV_RISE;
+    }
+    if (t >= max_steps) return ORC_ST_MAXSTEPS;
+    return 0;
+}
+
+static void fit_one(const orc_model* M, const orc_opts* O, const float* flux, const float* ivar,
+                    const unsigned char* good, const double* theta0, double* theta, double* loss,
+                    int* steps, unsigned* status, double* b_out) {
+    int p = M->n_pix, D = M->deg;
+    double* y = malloc(sizeof(double) * p);
+    double* W = malloc(sizeof(double) * p);
+    double* hist = malloc(sizeof(double) * (O->max_steps + 1));
+    double w, x[5], m[5] = {0}, v[5] = {0}, g[5], b[8];
+    int n_obj = orc_prep(p, flux, ivar, good, O->quantile, O->edge_px, y, W, &w);
+    for (int k = 0; k < 5; ++k) theta[k] = theta0[k];
+    *loss = NAN;
+    *steps = 0;
+    if (n_obj < D + 1 + 5 || !(w > 0.0) || !isfinite(w)) {
+        *status = ORC_ST_NODATA;
+        goto out;
+    }
+    orc_x_from_phys(M, theta0, x);
+    for (int k = 0; k < 5; ++k) x[k] = x[k] < -1.0 ? -1.0 : (x[k] > 1.0 ? 1.0 : x[k]);
+    for (int t = 0;; ++t) {
+        double l;
+        unsigned st = orc_eval(M, y, W, x, &l, g, b, NULL, NULL);
+        if (st & (ORC_ST_SINGULAR | ORC_ST_NONFINITE)) {
+            *status = st;
+            *loss = l;
+            *steps = t;
+            orc_phys_from_x(M, x, theta);
+            break;
+        }
+        hist[t] = l;
+        unsigned stop = orc_stop_rule(hist, t, O->window, O->tol, O->max_steps);
+        if (stop) {
+            *status = stop | (st & ORC_ST_NONPOS);
+            *loss = l;
+            *steps = t;
+            orc_phys_from_x(M, x, theta);
+            if (b_out) for (int d = 0; d <= D; ++d) b_out[d] = b[d];
+            break;
+        }
+        orc_adam_update(5, x, m, v, g, t + 1, O->lr, O->beta1, O->beta2, O->eps, 1);
+    }
+out:
+    free(y); free(W); free(hist);
+}
+
+void orc_fit(const orc_model* M, const orc_opts* O, int n, const float* flux, const float* ivar,
+             const unsigned char* good, const double* theta0, double* theta, double* loss,
+             int* steps, unsigned* status, double* b, int threads) {
+    int p = M->n_pix, nb = M->deg + 1;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(threads > 0 ? threads : 1)
+    for (int i = 0; i < n; ++i) {
+        fit_one(M, O, flux + (size_t)i * p, ivar + (size_t)i * p, good + (size_t)i * p,
+                theta0 + 5 * i, theta + 5 * i, loss + i, steps + i, status + i,
+                b ? b + (size_t)i * nb : NULL);
+    }
+}
+
+void orc_fit_trajectory(const orc_model* M, const orc_opts* O, const float* flux,
+                        const float* ivar, const unsigned char* good, const double* theta0,
+                        int nsteps, double* x_traj, double* loss_traj) {
+    int p = M->n_pix;
+    double* y = malloc(sizeof(double) * p);
+    double* W = malloc(sizeof(double) * p);
+    double w, x[5], m[5] = {0}, v[5] = {0}, g[5];
+    orc_prep(p, flux, ivar, good, O->quantile, O->edge_px, y, W, &w);
+    orc_x_from_phys(M, theta0, x);
+    for (int k = 0; k < 5; ++k) x[k] = x[k] < -1.0 ? -1.0 : (x[k] > 1.0 ? 1.0 : x[k]);
+    for (int t = 0; t <= nsteps; ++t) {
+        double l;
+        orc_eval(M, y, W, x, &l, g, NULL, NULL, NULL);
+        for (int k = 0; k < 5; ++k) x_traj[5 * t + k] = x[k];
+        loss_traj[t] = l;
+        if (t < nsteps) orc_adam_update(5, x, m, v, g, t + 1, O->lr, O->beta1, O->beta2, O->eps, 1);
+    }
+    free(y); free(W);
+}
+
+/* Weighted residual r = sqrt(W) eps at physical theta with b re-solved. */
+static int weighted_resid(const orc_model* M, const double* y, const double* W,
+                          const double* th, double* r) {
+    double x[5], l, g[5], b[8];
+    int p = M->n_pix;
+    double* eps = malloc(sizeof(double) * p);
+    orc_x_from_phys(M, th, x);
+    unsigned st = orc_eval(M, y, W, x, &l, g, b, eps, NULL);
+    for (int j = 0; j < p; ++j) r[j] = sqrt(W[j]) * eps[j];
+    free(eps);
+    return !(st & ORC_ST_SINGULAR);
+}
+
+/* Gauss-Jordan inverse with partial pivoting of a 5 x 5 matrix. */
+static int inv5(const double* A, double* Ai) {
+    double a[5][10];
+    for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 10; ++j) a[i][j] = j < 5 ? A[i * 5 + j] : (j - 5 == i ? 1.0 : 0.0);
+    for (int c = 0; c < 5; ++c) {
+        int piv = c;
+        for (int i = c + 1; i < 5; ++i) if (fabs(a[i][c]) > fabs(a[piv][c])) piv = i;
+        if (!(fabs(a[piv][c]) > 0.0)) return 0;
+        if (piv != c)
+            for (int j = 0; j < 10; ++j) { double t = a[c][j]; a[c][j] = a[piv][j]; a[piv][j] = t; }
+        double d = a[c][c];
+        for (int j = 0; j < 10; ++j) a[c][j] /= d;
+        for (int i = 0; i < 5; ++i) {
+            if (i == c) continue;
+            double f = a[i][c];
+            for (int j = 0; j < 10; ++j) a[i][j] -= f * a[c][j];
+        }
+    }
+    for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 5; ++j) Ai[i * 5 + j] = a[i][j + 5];
+    return 1;
+}
+
+unsigned orc_errors(const orc_model* M, const orc_opts* O, const float* flux, const float* ivar,
+                    const unsigned char* good, const double* theta, double* sigma, double* cov,
+                    double* jac_out) {
+    int p = M->n_pix;
+    unsigned st = 0;
+    double* y = malloc(sizeof(double) * p);
+    double* W = malloc(sizeof(double) * p);
+    double* r0 = malloc(sizeof(double) * p);
+    double* rp = malloc(sizeof(double) * p);
+    double* rm = malloc(sizeof(double) * p);
+    double* J = malloc(sizeof(double) * (size_t)p * 5);
+    double w;
+    int n_obj = orc_prep(p, flux, ivar, good, O->quantile, O->edge_px, y, W, &w);
+    for (int k = 0; k < 5; ++k) sigma[k] = NAN;
+    for (int k = 0; k < 25; ++k) cov[k] = NAN;
+    if (n_obj <= 5 || !(w > 0.0)) { st |= ORC_ST_NODATA; goto out; }
+    if (!weighted_resid(M, y, W, theta, r0)) { st |= ORC_ST_SINGULAR; goto out; }
+    for (int k = 0; k < 5; ++k) {
+        double h = 1e-4 * 0.5 * (M->phi[k] - M->plo[k]);
+        double tp[5], tm[5];
+        for (int i = 0; i < 5; ++i) tp[i] = tm[i] = theta[i];
+        tp[k] += h;
+        tm[k] -= h;
+        if (!weighted_resid(M, y, W, tp, rp) || !weighted_resid(M, y, W, tm, rm)) {
+            st |= ORC_ST_SINGULAR;
+            goto out;
+        }
+        for (int j = 0; j < p; ++j) J[(size_t)j * 5 + k] = (rp[j] - rm[j]) / (2.0 * h);
+    }
+    double rr = 0.0, JtJ[25], inv[25];
+    for (int j = 0; j < p; ++j) rr += r0[j] * r0[j];
+    for (int a = 0; a < 5; ++a)
+        for (int c = 0; c < 5; ++c) {
+            double s = 0.0;
+            for (int j = 0; j < p; ++j) s += J[(size_t)j * 5 + a] * J[(size_t)j * 5 + c];
+            JtJ[a * 5 + c] = s;
+        }
+    if (!inv5(JtJ, inv)) { st |= ORC_ST_SINGULAR; goto out; }
+    double s2 = rr / (n_obj - 5);
+    for (int k = 0; k < 25; ++k) cov[k] = s2 * inv[k];
+    for (int k = 0; k < 5; ++k) sigma[k] = sqrt(cov[k * 5 + k]);
+    if (jac_out) memcpy(jac_out, J, sizeof(double) * (size_t)p * 5);
+out:
+    free(y); free(W); free(r0); free(rp); free(rm); free(J);
+    return st;
+}

@@ -1,0 +1,376 @@
+"""Pins of the FP64 oracle to facts fixed outside it (CPU only).
+
+Each test checks one part of the oracle against a closed form, an invariant,
+a library routine the oracle does not use, or brute force, chosen so that a
+dropped term, a wrong sign or index or a transposed operand fails a test.
+The paper prints no worked example, so no value here is quoted from it.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import lasp_synth as S
+from oracle import oracle as O
+from tests.helpers import DEG, observed, oracle_model
+
+G = S.SMALL
+
+
+def _model(C=None):
+    return oracle_model(G, C)
+
+
+# ---------------------------------------------------------------- basis (Eq. 1)
+
+def test_basis_box_corners_closed_form():
+    M = _model()
+    lo = np.array([3500.0, 0.5, -2.5, 0.0, 100.0])
+    hi = np.array([7500.0, 5.5, 1.0, 0.0, 100.0])
+    phi_lo, _ = O.basis(M, lo)
+    phi_hi, _ = O.basis(M, hi)
+    deg = S.EXPS.sum(axis=1)
+    np.testing.assert_allclose(phi_lo, (-1.0) ** deg, atol=1e-13)
+    np.testing.assert_allclose(phi_hi, np.ones(S.K_TERMS), atol=1e-13)
+    mid = np.array([10 ** ((math.log10(3500) + math.log10(7500)) / 2), 3.0, -0.75, 0, 100])
+    phi_mid, _ = O.basis(M, mid)
+    expect = np.where(deg == 0, 1.0, 0.0)            # every u = 0 at the box centre
+    np.testing.assert_allclose(phi_mid, expect, atol=1e-13)
+
+
+def test_single_term_table_reproduces_basis():
+    """A table whose only non-zero row k is all ones gives F' = phi_k."""
+    rng = np.random.default_rng(1)
+    th = np.array([5321.0, 2.7, -0.9, 0.0, 100.0])
+    for k in rng.choice(S.K_TERMS, 6, replace=False):
+        C = np.zeros((S.K_TERMS, G.n_model))
+        C[k] = 1.0
+        out = O.model_flux(_model(C), th, np.r_[1.0, np.zeros(DEG)])
+        phi, _ = O.basis(_model(C), th)
+        np.testing.assert_allclose(out["Fp"], phi[k], rtol=0, atol=1e-14)
+
+
+def test_basis_derivative_fd():
+    M = _model()
+    th = np.array([4810.0, 3.9, -1.3, 0.0, 100.0])
+    phi, dphi = O.basis(M, th)
+    for i, h in enumerate([1e-3, 1e-6, 1e-6]):
+        tp, tm = th.copy(), th.copy()
+        tp[i] += h
+        tm[i] -= h
+        fd = (O.basis(M, tp)[0] - O.basis(M, tm)[0]) / (2 * h)
+        np.testing.assert_allclose(dphi[:, i], fd, rtol=1e-6, atol=1e-9)
+
+
+# ------------------------------------------------------------ kernel (Eq. 5)
+
+@pytest.mark.parametrize("mu,sig", [(0.0, 0.8), (1.37, 1.1), (-2.9, 2.2), (4.4, 2.93), (0.3, 0.5)])
+def test_kernel_unit_sum_support_and_mirror(mu, sig):
+    H = 20
+    g, dm, ds, h = O.kernel(mu, sig, H)
+    assert h == math.ceil(abs(mu) + 5 * sig)
+    assert abs(g.sum() - 1.0) < 1e-15
+    s = np.arange(-H, H + 1)
+    assert np.all(g[np.abs(s) > h] == 0.0)
+    assert np.all(g[np.abs(s) <= h] > 0.0)
+    gm, _, _, _ = O.kernel(-mu, sig, H)
+    np.testing.assert_allclose(g, gm[::-1], atol=1e-16)
+    # derivatives of a unit-sum kernel sum to zero
+    assert abs(dm.sum()) < 1e-13 and abs(ds.sum()) < 1e-13
+
+
+def test_kernel_derivative_fd():
+    H = 20
+    for mu, sig in [(1.3, 1.7), (-0.6, 0.9)]:
+        g, dm, ds, _ = O.kernel(mu, sig, H)
+        e = 1e-6
+        fdm = (O.kernel(mu + e, sig, H)[0] - O.kernel(mu - e, sig, H)[0]) / (2 * e)
+        fds = (O.kernel(mu, sig + e, H)[0] - O.kernel(mu, sig - e, H)[0]) / (2 * e)
+        np.testing.assert_allclose(dm, fdm, atol=1e-9)
+        np.testing.assert_allclose(ds, fds, atol=1e-9)
+
+
+def _kms(px):
+    return px * G.kms_per_px
+
+
+def test_broadening_equals_numpy_convolution():
+    """Eq. 5 as a convolution: F'' = np.convolve(F', G, 'valid')."""
+    M = _model()
+    th = np.array([5100.0, 2.2, -0.4, 47.0, 91.0])
+    out = O.model_flux(M, th, np.r_[1.0, np.zeros(DEG)])
+    g, _, _, _ = O.kernel(th[3] / G.kms_per_px, th[4] / G.kms_per_px, G.pad)
+    np.testing.assert_allclose(out["Fpp"], np.convolve(out["Fp"], g, mode="valid"), atol=1e-13)
+
+
+def test_broadening_identity_and_integer_shift():
+    M = _model()
+    b = np.r_[1.0, np.zeros(DEG)]
+    base = np.array([5600.0, 4.1, -0.2, 0.0, 0.0])
+    for shift in (0, 3, -5):
+        th = base.copy()
+        th[3] = _kms(shift)
+        th[4] = _kms(1e-4)                            # sigma -> 0: a unit spike at s = shift
+        out = O.model_flux(M, th, b)
+        H = G.pad
+        np.testing.assert_allclose(out["Fpp"], out["Fp"][H - shift:H - shift + G.n_pix],
+                                   rtol=0, atol=1e-12)
+
+
+def test_broadening_constant_in_constant_out():
+    C = np.zeros((S.K_TERMS, G.n_model))
+    C[0] = 2.5
+    out = O.model_flux(_model(C), np.array([6000.0, 3, 0, 120.0, 140.0]), np.r_[1.0, np.zeros(DEG)])
+    np.testing.assert_allclose(out["Fpp"], 2.5, atol=1e-14)
+
+
+def test_broadening_moments_add():
+    """Mean and variance of an isolated line add under convolution; a positive
+    RV moves the line to higher pixel index by the kernel mean (~ mu)."""
+    C = np.zeros((S.K_TERMS, G.n_model))
+    m = np.arange(G.n_model)
+    C[0] = np.exp(-0.5 * ((m - 500.3) / 1.7) ** 2)
+    M = _model(C)
+    th = np.array([6000.0, 3, 0, _kms(2.6), _kms(1.3)])
+    out = O.model_flux(M, th, np.r_[1.0, np.zeros(DEG)])
+    g, _, _, _ = O.kernel(th[3] / G.kms_per_px, th[4] / G.kms_per_px, G.pad)
+    s = np.arange(-G.pad, G.pad + 1)
+    j = np.arange(G.n_pix)
+    Fp, Fpp = out["Fp"], out["Fpp"]
+    mean_in = (m * Fp).sum() / Fp.sum() - G.pad          # in observed-pixel units
+    var_in = ((m - G.pad - mean_in) ** 2 * Fp).sum() / Fp.sum()
+    mean_out = (j * Fpp).sum() / Fpp.sum()
+    var_out = ((j - mean_out) ** 2 * Fpp).sum() / Fpp.sum()
+    gmean = (s * g).sum()
+    gvar = ((s - gmean) ** 2 * g).sum()
+    assert abs(mean_out - (mean_in + gmean)) < 1e-9
+    assert abs(var_out - (var_in + gvar)) < 1e-8
+    assert abs(gmean - 2.6) < 1e-6 and mean_out > mean_in
+
+
+# --------------------------------------------------------- continuum (Eq. 6)
+
+def test_legendre_matches_numpy():
+    p, D = 1024, DEG
+    x = -1.0 + 2.0 * np.arange(p) / p
+    np.testing.assert_allclose(O.legendre(p, D), np.polynomial.legendre.legvander(x, D),
+                               atol=1e-13)
+
+
+def test_wls_matches_lstsq_and_envelope():
+    M, d = observed(G, 3, 11, noise=True, snr=(20, 20), mask_frac=0.05)
+    for i in range(3):
+        y, W, w, _ = O.prep(d["flux"][i], d["ivar"][i], d["good"][i])
+        x = O.x_from_phys(M, d["theta0"][i])
+        r = O.evaluate(M, y, W, x)
+        th = O.phys_from_x(M, x)
+        Fpp = O.model_flux(M, th, np.r_[1.0, np.zeros(DEG)])["Fpp"]
+        X = np.polynomial.legendre.legvander(-1.0 + 2.0 * np.arange(G.n_pix) / G.n_pix, DEG)
+        X = X * Fpp[:, None]
+        sw = np.sqrt(W)
+        b_ls = np.linalg.lstsq(X * sw[:, None], y * sw, rcond=None)[0]
+        np.testing.assert_allclose(r["b"], b_ls, rtol=1e-9, atol=1e-12)
+        # dS/db = 0 at b*: S(b) = sum W (y - (P b) F'')^2
+        def S_of(b):
+            return float((W * (y - O.model_flux(M, th, b)["model"]) ** 2).sum())
+        S0 = S_of(r["b"])
+        for k in range(DEG + 1):
+            e = np.zeros(DEG + 1)
+            e[k] = 1e-4 * max(1.0, abs(r["b"][0]))
+            dS = (S_of(r["b"] + e) - S_of(r["b"] - e)) / (2 * e[k])
+            assert abs(dS) < 1e-6 * max(S0, 1e-12) / e[k] + 1e-9
+
+
+def test_loss_is_rms_of_weighted_residual():
+    M, d = observed(G, 1, 12, noise=True, snr=(30, 30), mask_frac=0.05)
+    y, W, w, n_obj = O.prep(d["flux"][0], d["ivar"][0], d["good"][0])
+    r = O.evaluate(M, y, W, O.x_from_phys(M, d["theta0"][0]))
+    assert abs(r["loss"] - math.sqrt((W * r["eps"] ** 2).sum() / G.n_pix)) < 1e-14
+    # masked pixels carry weight 0 and their spike values never reach the loss
+    assert np.all(W[d["good"][0] == 0] == 0)
+
+
+# ------------------------------------------------------------ prep (sec. 3.3)
+
+def test_prep_quantile_and_weights():
+    M, d = observed(G, 1, 13, noise=True, snr=(15, 15), mask_frac=0.1)
+    f, iv, gd = d["flux"][0], d["ivar"][0], d["good"][0]
+    used = (gd == 1) & (iv > 0)
+    for q in (0.5, 0.75):
+        y, W, w, n_obj = O.prep(f, iv, gd, quantile=q)
+        assert abs(w - np.quantile(f[used].astype(np.float64), q)) < 1e-12 * abs(w)
+        assert n_obj == used.sum()
+        assert abs(W[used].mean() - 1.0) < 1e-12
+        np.testing.assert_allclose(y[used], f[used].astype(np.float64) / w, rtol=1e-15)
+    y, W, w, n_obj = O.prep(f, iv, gd, edge_px=7)
+    assert np.all(W[:7] == 0) and np.all(W[-7:] == 0) and n_obj == used[7:-7].sum()
+
+
+# --------------------------------------------------------- loss and gradient
+
+def test_zero_loss_at_truth_noise_free():
+    M, d = observed(G, 4, 14, noise=False, mask_frac=0.0)
+    for i in range(4):
+        y, W, w, _ = O.prep(d["flux"][i], d["ivar"][i], d["good"][i])
+        r = O.evaluate(M, y, W, O.x_from_phys(M, d["truth"][i]))
+        assert r["loss"] < 2e-7          # float32 storage of the flux is the floor
+        # the continuum recovers the true one up to the scale fixed by w
+        np.testing.assert_allclose(r["b"] * w, d["b_true"][i], rtol=2e-6, atol=2e-6 * w)
+
+
+def test_flux_scale_invariance():
+    M, d = observed(G, 1, 15, noise=True, snr=(25, 25), mask_frac=0.05)
+    y1, W1, _, _ = O.prep(d["flux"][0], d["ivar"][0], d["good"][0])
+    y2, W2, _, _ = O.prep(d["flux"][0] * np.float32(8.0), d["ivar"][0] / np.float32(64.0),
+                          d["good"][0])
+    x = O.x_from_phys(M, d["theta0"][0])
+    r1, r2 = O.evaluate(M, y1, W1, x), O.evaluate(M, y2, W2, x)
+    assert abs(r1["loss"] - r2["loss"]) < 1e-13
+    np.testing.assert_allclose(r1["grad"], r2["grad"], rtol=1e-10, atol=1e-14)
+
+
+def _richardson(fun, x, k, h):
+    def cd(hh):
+        xp, xm = x.copy(), x.copy()
+        xp[k] += hh
+        xm[k] -= hh
+        return (fun(xp) - fun(xm)) / (2 * hh)
+    return (4 * cd(h / 2) - cd(h)) / 3
+
+
+def test_gradient_matches_finite_differences():
+    M, d = observed(G, 3, 16, noise=True, snr=(40, 40), mask_frac=0.05)
+    for i in range(3):
+        y, W, _, _ = O.prep(d["flux"][i], d["ivar"][i], d["good"][i])
+        x = O.x_from_phys(M, d["theta0"][i])
+        r = O.evaluate(M, y, W, x)
+        fd = np.array([_richardson(lambda z: O.evaluate(M, y, W, z)["loss"], x, k, 1e-4)
+                       for k in range(5)])
+        np.testing.assert_allclose(r["grad"], fd, rtol=1e-7, atol=1e-10 * np.abs(fd).max())
+
+
+def test_model_vjp_matches_finite_differences():
+    """Adjoint of model = (P b) * (G (x) phi C) w.r.t. theta and b."""
+    M = _model()
+    rng = np.random.default_rng(3)
+    th = np.array([5480.0, 3.3, -0.7, 63.0, 88.0])
+    b = np.r_[1.3, rng.normal(0, 0.05, DEG)]
+    gm = rng.normal(0, 1, G.n_pix)
+    gth, gb = O.model_vjp(M, th, b, gm)
+    f = lambda t, bb: float(gm @ O.model_flux(M, t, bb)["model"])
+    steps = [0.5, 1e-4, 1e-4, 0.01, 0.01]
+    fd_th = np.array([_richardson(lambda t: f(t, b), th, k, steps[k]) for k in range(5)])
+    fd_b = np.array([_richardson(lambda bb: f(th, bb), b, k, 1e-3) for k in range(DEG + 1)])
+    np.testing.assert_allclose(gth, fd_th, rtol=1e-7)
+    np.testing.assert_allclose(gb, fd_b, rtol=1e-9)
+
+
+# ------------------------------------------------------------- Adam (stage 8)
+
+def test_adam_matches_torch():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(4)
+    x0 = rng.uniform(-0.5, 0.5, 5)
+    grads = rng.normal(0, 1, (30, 5)) * np.array([1e-3, 1, 10, 1e-2, 5])
+    p = torch.nn.Parameter(torch.tensor(x0, dtype=torch.float64))
+    opt = torch.optim.Adam([p], lr=0.1)
+    x, m, v = x0.copy(), np.zeros(5), np.zeros(5)
+    for t, g in enumerate(grads, start=1):
+        p.grad = torch.tensor(g, dtype=torch.float64)
+        opt.step()
+        x, m, v = O.adam_update(x, m, v, g, t, clamp=False)
+        np.testing.assert_allclose(x, p.detach().numpy(), rtol=0, atol=1e-12)
+
+
+def test_adam_box_projection():
+    x, m, v = O.adam_update(np.array([0.99, -0.99, 0, 0, 0]), np.zeros(5), np.zeros(5),
+                            np.array([-1.0, 1.0, 0, 0, 0]), 1)
+    assert x[0] == 1.0 and x[1] == -1.0
+
+
+def test_stop_rules():
+    W = 50
+    flat = np.r_[np.linspace(1.0, 0.5, 10), np.full(200, 0.5)]
+    # first t >= 50 with |l_t - l_{t-50}| < tol: l_{t-50} on the flat part, t - 50 >= 9
+    stops = [t for t in range(len(flat)) if O.stop_rule(flat, t, W, 1e-5, 5000)]
+    assert stops[0] == 59 and O.stop_rule(flat, 59, W, 1e-5, 5000) == O.ST_CONV_TOL
+    rising = 1.0 + 1e-3 * np.arange(120)
+    assert O.stop_rule(rising, 49, W, 1e-5, 5000) == 0
+    assert O.stop_rule(rising, 50, W, 1e-5, 5000) == O.ST_CONV_RISE
+    one_flat = rising.copy()
+    one_flat[30] = one_flat[29]               # a tie breaks the run of rises
+    assert O.stop_rule(one_flat, 79, W, 1e-5, 5000) == 0
+    assert O.stop_rule(one_flat, 80, W, 1e-5, 5000) == O.ST_CONV_RISE
+    falling = 1.0 - 1e-4 * np.arange(300)     # changes by 5e-3 per window: never tol
+    assert all(O.stop_rule(falling, t, W, 1e-5, 250) == 0 for t in range(250))
+    assert O.stop_rule(falling, 250, W, 1e-5, 250) == O.ST_MAXSTEPS
+    tie = np.r_[np.zeros(50), 1e-5]           # |delta| == tol does not stop (strict <)
+    assert O.stop_rule(tie, 50, W, 1e-5, 5000) == 0
+
+
+# -------------------------------------------------------------- end to end
+
+def test_noise_free_recovery_of_truth():
+    M, d = observed(G, 8, 17, noise=False, mask_frac=0.0)
+    res = O.fit(M, d["flux"], d["ivar"], d["good"], d["theta0"], lr=1e-3, tol=1e-10,
+                max_steps=20000)
+    err = np.abs(res["theta"] - d["truth"])
+    assert np.all(err[:, :4] <= np.array([1.0, 0.005, 0.005, 0.1])), err
+    assert np.all(res["loss"] < 1e-4)
+
+
+def test_fit_step_accounting_and_status():
+    M, d = observed(G, 4, 18, noise=True, snr=(20, 60), mask_frac=0.05)
+    res = O.fit(M, d["flux"], d["ivar"], d["good"], d["theta0"], max_steps=40)
+    assert np.all(res["steps"] == 40) and np.all(res["status"] & O.ST_MAXSTEPS)
+    xs, ls = O.trajectory(M, d["flux"][0], d["ivar"][0], d["good"][0], d["theta0"][0], 40)
+    np.testing.assert_allclose(O.x_from_phys(M, res["theta"][0]), xs[40], atol=1e-12)
+    assert abs(res["loss"][0] - ls[40]) < 1e-15
+    bad = d["good"].copy()
+    bad[1] = 0
+    res2 = O.fit(M, d["flux"], d["ivar"], bad, d["theta0"], max_steps=40)
+    assert res2["status"][1] == O.ST_NODATA and res2["steps"][1] == 0
+
+
+# ----------------------------------------------------------- errors (stage 9)
+
+def test_errors_jacobian_consistent_with_gradient():
+    """J^T r / (p l) equals the analytic gradient of l (envelope theorem)."""
+    M, d = observed(G, 2, 19, noise=True, snr=(30, 30), mask_frac=0.05)
+    for i in range(2):
+        th = d["theta0"][i]
+        e = O.errors(M, d["flux"][i], d["ivar"][i], d["good"][i], th, with_jac=True)
+        y, W, _, n_obj = O.prep(d["flux"][i], d["ivar"][i], d["good"][i])
+        r = O.evaluate(M, y, W, O.x_from_phys(M, th))
+        resid = np.sqrt(W) * r["eps"]
+        gphys = r["grad"] / (0.5 * (S.BOX_HI - S.BOX_LO))
+        np.testing.assert_allclose(e["jac"].T @ resid / (G.n_pix * r["loss"]), gphys,
+                                   rtol=2e-5, atol=1e-6 * np.abs(gphys).max())
+        s2 = (resid ** 2).sum() / (n_obj - 5)
+        np.testing.assert_allclose(e["cov"], s2 * np.linalg.inv(e["jac"].T @ e["jac"]),
+                                   rtol=1e-9)
+        np.testing.assert_allclose(e["sigma"], np.sqrt(np.diag(e["cov"])), rtol=1e-12)
+
+
+def test_errors_vanish_without_noise():
+    M, d = observed(G, 1, 20, noise=False, mask_frac=0.0)
+    e = O.errors(M, d["flux"][0], d["ivar"][0], d["good"][0], d["truth"][0])
+    assert np.all(e["sigma"] < np.array([0.05, 1e-4, 1e-4, 5e-3, 5e-3]))
+
+
+def test_errors_match_monte_carlo_scatter():
+    """Sample scatter of the fitted parameters over noise realisations agrees
+    with the median reported sigma (linear error propagation, stage 9)."""
+    n = 96
+    M = oracle_model(G)
+    d = S.draw_batch(G, n, 21, noise=True, snr=(40, 40), mask_frac=0.0)
+    for k in ("truth", "b_true", "theta0", "snr"):
+        d[k] = np.repeat(d[k][:1], n, axis=0)
+    d["good"] = np.repeat(d["good"][:1], n, axis=0)
+    model = O.model_batch(M, d["truth"][:1], d["b_true"][:1])
+    flux, ivar = S.finish_obs(np.repeat(model, n, axis=0), d)
+    res = O.fit(M, flux, ivar, d["good"], d["truth"], lr=3e-3, tol=1e-10, max_steps=3000)
+    sig = np.array([O.errors(M, flux[i], ivar[i], d["good"][i], res["theta"][i])["sigma"]
+                    for i in range(0, n, 8)])
+    ratio = res["theta"].std(axis=0, ddof=1) / np.median(sig, axis=0)
+    assert np.all((ratio > 0.7) & (ratio < 1.3)), ratio
