@@ -1,0 +1,363 @@
+"""Benchmark: converged spectra/s of the grouped fit on one GB300 per rank.
+
+One step = one pass of the whole hot path over one batch: lasp_fit_batch
+(basis contraction, broadening, continuum WLS, loss, adjoint, grouped Adam
+with per-spectrum stop rules) followed by lasp_errors (stage-9 covariance)
+for 4096 LAMOST-like spectra x 3909 pixels, K = 26, Legendre degree 6,
+SNR 5-100, 5% masked pixels, at most 500 Adam steps (paper defaults lr 0.1,
+tol 1e-5, window 50).  value = spectra that stopped by rule 2 or 3 per
+second.  Inputs (144 MB) exceed L2 and L2 is also flushed between steps.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Multi-GPU: replicas (each rank fits its own batch; no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import lasp_synth as S  # noqa: E402
+
+WORKLOAD = "lamost4096x3909_k26_d6_snr5-100_mask5pct_max500"
+METRIC = "converged spectra/s at fixed param tolerance, plain vs mixed; p50/p99 latency"
+UNIT = "spectra/s"
+N_SPEC, MAX_STEPS, DEG = 4096, 500, 6
+FP32_LANES_PER_SM, N_SM = 128, 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=192)
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.rows, self.proc = index, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace('.', '').isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace('.', '').isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) >= 9:
+                for n, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_flops(theta, steps, grid, K=26, D=DEG):
+    """FLOPs of the fused step per spectrum, summed over the evaluations each
+    spectrum ran (steps + 1), with its kernel width h = ceil(|mu| + 5 sigma)
+    at the result.  Per spectrum-step: 2 K n_model (Eq. 1) + 2 T p (Eq. 5)
+    + 4 T p (kernel-parameter adjoint) + 2 T n_model (transposed
+    correlation) + 2 K n_model (basis adjoint) + p (2 (D+1)(D+2)/2 + 2 (D+1)
+    + 4 D + 2 (D+1) + 8) (Legendre, normal equations, continuum, residual)."""
+    p, nm = grid.n_pix, grid.n_model
+    mu = np.abs(theta[:, 3]) / grid.kms_per_px
+    sg = theta[:, 4] / grid.kms_per_px
+    T = 2 * np.ceil(mu + 5 * sg) + 1
+    nb = D + 1
+    per_px = 2 * nb * (nb + 1) // 2 + 2 * nb + 4 * D + 2 * nb + 8
+    per = 4 * K * nm + 6 * T * p + 2 * T * nm + per_px * p
+    return float((per * (steps + 1)).sum())
+
+
+def make_inputs(rank, torch, lasp, grid, C):
+    """Batch of N_SPEC spectra; the noise-free model comes from the library's
+    forward model, noise and masks from the generator."""
+    d = S.draw_batch(grid, N_SPEC, S.SPECTRA_SEED + 1 + 1000 * rank, snr=(5, 100), mask_frac=0.05)
+    ip = lasp.Interp.from_grid(grid, C, S.EXPS, S.BASIS_LO, S.BASIS_HI, S.BOX_LO, S.BOX_HI)
+    dev = torch.device("cuda")
+    model = ip.forward(torch.tensor(d["truth"], dtype=torch.float32, device=dev),
+                       torch.tensor(d["b_true"], dtype=torch.float32, device=dev))
+    flux, ivar = S.finish_obs(model.double().cpu().numpy(), d)
+    return ip, d, flux, ivar
+
+
+def run_ours(args):
+    import torch
+    from paper_2512_24840_gb300 import lasp
+
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    lasp.load()
+    grid = S.LAMOST
+    C = S.make_table(grid)
+    ip, d, flux, ivar = make_inputs(rank, torch, lasp, grid, C)
+    dev = torch.device("cuda")
+    g_flux = torch.tensor(flux, device=dev)
+    g_ivar = torch.tensor(ivar, device=dev)
+    g_good = torch.tensor(d["good"], device=dev)
+    g_th0 = torch.tensor(d["theta0"], dtype=torch.float32, device=dev)
+    opts = dict(max_steps=MAX_STEPS, legendre_deg=DEG)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    out = None
+
+    def step():
+        nonlocal out
+        out = ip.fit(g_flux, g_ivar, g_good, g_th0, out=out, **opts)
+        e = ip.errors(g_flux, g_ivar, g_good, out["theta"], with_cov=False, **opts)
+        return out, e
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize()
+    # per-kernel timing of the fit kernel on the launching stream
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    flush_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush_ev[k][0].record(stream)
+            flush.fill_(float(k))
+            flush_ev[k][1].record(stream)
+            ev[k][0].record(stream)
+            out = ip.fit(g_flux, g_ivar, g_good, g_th0, out=out, **opts)
+            ev[k][1].record(stream)
+            ip.errors(g_flux, g_ivar, g_good, out["theta"], with_cov=False, **opts)
+            ev[k][2].record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    fit_ms = [a.elapsed_time(b) for a, b, c in ev]
+    err_ms = [b.elapsed_time(c) for a, b, c in ev]
+    step_ms = [a.elapsed_time(c) for a, b, c in ev]
+    ms = sum(step_ms) / len(step_ms)
+    status = out["status"].cpu().numpy()
+    steps_np = out["steps"].cpu().numpy()
+    theta_np = out["theta"].double().cpu().numpy()
+    conv = int(((status & 3) != 0).sum())
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        c = torch.tensor([conv], device=dev, dtype=torch.int64)
+        dist.all_reduce(c)
+        conv_all = int(c.item())
+    else:
+        conv_all = conv
+    value = conv_all / (ms / 1e3)
+
+    # ---- end to end through the public API from pinned host buffers
+    h_flux = torch.tensor(flux).pin_memory()
+    h_ivar = torch.tensor(ivar).pin_memory()
+    h_good = torch.tensor(d["good"]).pin_memory()
+    h_th0 = torch.tensor(d["theta0"], dtype=torch.float32).pin_memory()
+    h_theta = torch.empty((N_SPEC, 5)).pin_memory()
+    h_sig = torch.empty((N_SPEC, 5)).pin_memory()
+    h_status = torch.empty(N_SPEC, dtype=torch.int32).pin_memory()
+    bi = sum(t.numel() * t.element_size() for t in (h_flux, h_ivar, h_good, h_th0))
+    bo = sum(t.numel() * t.element_size() for t in (h_theta, h_sig, h_status))
+    e2e = []
+    for k in range(args.warmup + args.steps):
+        flush.fill_(0.5)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g_flux.copy_(h_flux, non_blocking=True)
+        g_ivar.copy_(h_ivar, non_blocking=True)
+        g_good.copy_(h_good, non_blocking=True)
+        g_th0.copy_(h_th0, non_blocking=True)
+        o2, e2 = step()
+        h_theta.copy_(o2["theta"], non_blocking=True)
+        h_sig.copy_(e2["sigma"], non_blocking=True)
+        h_status.copy_(o2["status"], non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            e2e.append(a.elapsed_time(b))
+    e2e_ms = sum(e2e) / len(e2e)
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_conv = int(((h_status.numpy() & 3) != 0).sum())
+    if dist:
+        c = torch.tensor([e2e_conv], device=dev, dtype=torch.int64)
+        dist.all_reduce(c)
+        e2e_conv = int(c.item())
+
+    pk, pk_kind = peaks()
+    fit_avg = sum(fit_ms) / len(fit_ms)
+    flops = algorithmic_flops(theta_np, steps_np, grid)
+    clocks = clk.summary()
+    mhz = pk.get("sm_max_mhz", 2070.0)
+    alu_peak = N_SM * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    achieved = flops / (fit_avg / 1e3) / 1e12
+    res = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_spectra_per_gpu": N_SPEC, "n_pix": grid.n_pix,
+                   "K": 26, "legendre_deg": DEG, "max_steps": MAX_STEPS, "lr": 0.1,
+                   "tol": 1e-5, "precision": "fp32", "parallelism": f"replicas{world}",
+                   "l2": "flushed (256 MB write) between steps; inputs 144 MB > L2"},
+        "e2e": {"value": e2e_conv / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
+        "gpu_launches": 2 * args.steps,
+        "detail": {"fit_ms": fit_avg, "errors_ms": sum(err_ms) / len(err_ms),
+                   "converged": conv, "n_spectra": N_SPEC,
+                   "mean_steps": float(steps_np.mean()),
+                   "spectrum_steps_per_s": float((steps_np + 1).sum() / (fit_avg / 1e3))},
+        "roofline": {"kernel": "fit_kernel<256,6>", "bound": "alu", "achieved": achieved,
+                     "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
+                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz "
+                                    f"(sm_max_mhz, {pk_kind})",
+                     "traffic": None},
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(args.cpu_sample, grid, C, ip, torch)
+    if rank == 0:
+        print(json.dumps(res))
+    if dist:
+        dist.destroy_process_group()
+
+
+def _oracle_sample(n, grid, C, seed):
+    from oracle import oracle as O
+    M = O.Model(C, S.EXPS, grid.dln, grid.pad, grid.n_pix, DEG, S.BASIS_LO, S.BASIS_HI,
+                S.BOX_LO, S.BOX_HI)
+    d = S.draw_batch(grid, n, seed, snr=(5, 100), mask_frac=0.05)
+    flux, ivar = S.finish_obs(O.model_batch(M, d["truth"], d["b_true"]), d)
+    return O, M, d, flux, ivar
+
+
+def _oracle_step(O, M, d, flux, ivar, threads):
+    r = O.fit(M, flux, ivar, d["good"], d["theta0"], threads=threads, max_steps=MAX_STEPS)
+    for i in range(len(flux)):
+        O.errors(M, flux[i], ivar[i], d["good"][i], r["theta"][i])
+    return r
+
+
+def cpu_baseline(n, grid, C, ip, torch):
+    """The oracle (FP64 C, OpenMP over spectra) timed on this host's cores on
+    a bounded sample of the same workload; the GPU fits the same oracle-made
+    sample to report parameter agreement within tolerance."""
+    O, M, d, flux, ivar = _oracle_sample(n, grid, C, S.SPECTRA_SEED + 1)
+    threads = O.lib().orc_max_threads()
+    t0 = time.perf_counter()
+    r = _oracle_step(O, M, d, flux, ivar, threads)
+    dt = time.perf_counter() - t0
+    conv = int(((r["status"] & 3) != 0).sum())
+    dev = torch.device("cuda")
+    g = ip.fit(torch.tensor(flux, device=dev), torch.tensor(ivar, device=dev),
+               torch.tensor(d["good"], device=dev),
+               torch.tensor(d["theta0"], dtype=torch.float32, device=dev), max_steps=MAX_STEPS)
+    th = g["theta"].double().cpu().numpy()
+    within = np.all(np.abs(th - r["theta"])[:, :4] <= np.array([1.0, 0.005, 0.005, 0.1]), axis=1)
+    return {"value": conv / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{n} spectra of the same workload (fit + errors), {dt:.1f} s",
+            "gpu_vs_oracle_within_tol_frac": float(within.mean())}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", 0))
+    if rank != 0:
+        return
+    grid = S.LAMOST
+    C = S.make_table(grid)
+    n = args.cpu_sample
+    O, M, d, flux, ivar = _oracle_sample(n, grid, C, S.SPECTRA_SEED + 1)
+    threads = O.lib().orc_max_threads()
+    for _ in range(args.warmup):
+        _oracle_step(O, M, {k: (v[:4] if isinstance(v, np.ndarray) else v) for k, v in d.items()},
+                     flux[:4], ivar[:4], threads)
+    times, conv = [], 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = _oracle_step(O, M, d, flux, ivar, threads)
+        times.append(time.perf_counter() - t0)
+        conv = int(((r["status"] & 3) != 0).sum())
+    dt = sum(times) / len(times)
+    value = conv / dt
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_spectra": n, "n_pix": grid.n_pix},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{n} of the 4096 spectra per step (fit + errors)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

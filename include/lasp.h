@@ -1,0 +1,176 @@
+/* lasp.h -- C-ABI of the GB300 grouped spectral-fitting library (liblasp.so).
+ *
+ * The library fits many observed spectra at once with the LASP-Adam method of
+ * arXiv 2512.24840 (section 2.2): each spectrum's model is a polynomial
+ * interpolator in (Teff, log g, [Fe/H]) (Eq. 1), broadened and shifted by a
+ * sampled Gaussian kernel on a ln-lambda grid (Eq. 5), multiplied by a
+ * Legendre continuum solved by weighted least squares (Eq. 6); the
+ * inverse-variance-weighted residual (Eq. 7) gives a per-spectrum RMS loss
+ * (Eq. 9) that Adam minimises until each spectrum meets one of the three stop
+ * rules (stage 8).  Parameter errors come from linear error propagation
+ * (stage 9).
+ *
+ * Conventions
+ *  - Every call returns LASP_OK (0) or a negative LASP_E* code; calls never
+ *    abort and never print.  lasp_strerror() names a code.
+ *  - Array arguments documented "device" must be CUDA device pointers on the
+ *    current device; "host" ones are host memory.  The caller owns every
+ *    batch, result and output buffer.  The library owns the interpolator
+ *    handle (its table copies), and any scratch it allocates per call on the
+ *    given stream (stream-ordered, released before the call's work ends).
+ *  - Calls taking `stream` (a cudaStream_t, NULL = legacy default stream)
+ *    enqueue their work on it and return without synchronising, except where
+ *    noted.  Arguments are validated on the host before anything is enqueued.
+ *  - Row-major layouts.  Physical parameters theta are ordered
+ *    (Teff [K], log g [dex], [Fe/H] [dex], RV [km/s], sigma_v [km/s]).
+ *  - Per-spectrum outcomes are reported in status bits, not return codes.
+ */
+#ifndef LASP_H
+#define LASP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---- */
+#define LASP_OK        0
+#define LASP_EINVAL   (-1)   /* bad argument (NULL, size, degree, option)     */
+#define LASP_ENOMEM   (-2)   /* device allocation failed                       */
+#define LASP_ECUDA    (-3)   /* a CUDA runtime call or launch failed           */
+#define LASP_ETIMEOUT (-4)   /* a bounded device wait gave up                  */
+#define LASP_EGRID    (-5)   /* grid/table mismatch: pad too small for the box */
+#define LASP_ENODEV   (-6)   /* no usable sm_103 device                        */
+
+/* ---- per-spectrum status bits (lasp_result.status) ---- */
+#define LASP_ST_CONV_TOL   1u   /* |l_t - l_{t-window}| < tol (stage 8 rule 2)        */
+#define LASP_ST_CONV_RISE  2u   /* loss rose on `window` consecutive steps (rule 3)   */
+#define LASP_ST_MAXSTEPS   4u   /* max_steps updates taken (rule 1)                   */
+#define LASP_ST_NONPOS     8u   /* continuum P b <= 0 on a used pixel at the result   */
+#define LASP_ST_NONFINITE 16u   /* loss or gradient not finite; fit stopped           */
+#define LASP_ST_SINGULAR  32u   /* continuum normal equations not positive definite  */
+#define LASP_ST_NODATA    64u   /* fewer than D+1+5 usable pixels, or weight <= 0    */
+#define LASP_ST_RUNNING  128u   /* (slot state only) fit not finished yet             */
+
+/* ---- arithmetic of the interpolator contraction and the normal equations ---- */
+#define LASP_PREC_FP32   0   /* FP32 CUDA-core contraction, FP32 normal equations      */
+#define LASP_PREC_TF32   1   /* tcgen05 TF32 contraction, FP32 accumulate               */
+#define LASP_PREC_BF16   2   /* tcgen05 BF16 contraction, FP32 accumulate               */
+#define LASP_PREC_TF32X3 3   /* tcgen05 3-pass split TF32 (about FP32 accurate)         */
+
+/* Interpolator description (Eq. 1 with one polynomial regime).
+ * The model grid is the observed ln-lambda grid extended by `pad` pixels on
+ * each side: n_model = n_pix + 2 pad.  The basis variables
+ * v = (log10 Teff, log g, [Fe/H]) are mapped onto [-1, 1] by
+ * u = 2 (v - basis_lo) / (basis_hi - basis_lo) - 1 and
+ * phi_k = u_T^a u_g^b u_f^c with (a, b, c) = exps[k].
+ * box_lo/box_hi bound the physical parameters; the fit works on x in [-1,1]^5
+ * mapped linearly onto the box (stage 8 rescaling). */
+typedef struct {
+    int K;                  /* basis terms, 1..32                                 */
+    int n_pix;              /* observed pixels p (>= 16)                          */
+    int pad;                /* H >= ceil(max|mu| + 5 max sigma) over the box      */
+    double dln;             /* ln-lambda step of the grid (> 0)                   */
+    const int8_t* exps;     /* host, K x 3 non-negative exponents (<= 8)          */
+    double basis_lo[3], basis_hi[3];
+    double box_lo[5], box_hi[5];
+} lasp_interp_desc;
+
+typedef struct lasp_interp_s* lasp_interp;   /* opaque, library-owned */
+
+/* Upload the interpolator table (Eq. 1) and build its device images.
+ * coeff: host, K x n_model float32 row-major (C_k,m).  Builds the FP32 table,
+ * the TF32 hi/lo and BF16 tile images used by the tensor-core contraction.
+ * Synchronous.  Errors: LASP_EINVAL (bad desc), LASP_EGRID (pad smaller than
+ * the widest kernel reachable in the box), LASP_ENOMEM, LASP_ECUDA,
+ * LASP_ENODEV.  On success *out owns device memory until lasp_free_interp. */
+int lasp_init_interp(const lasp_interp_desc* desc, const float* coeff, lasp_interp* out);
+void lasp_free_interp(lasp_interp h);
+
+/* A batch of N observed spectra on the interpolator's grid (device, row-major
+ * N x n_pix).  good: 1 = pixel used (the mask A of Eq. 8), 0 = masked.
+ * Pixels with good = 0, ivar <= 0 or non-finite values are not used.
+ * theta0: device, N x 5 physical initial parameters (clipped to the box). */
+typedef struct {
+    int N;
+    int n_pix;              /* must equal the descriptor's n_pix */
+    const float* flux;
+    const float* ivar;
+    const uint8_t* good;
+    const float* theta0;
+} lasp_batch;
+
+/* Fit options.  lasp_default_opts() gives the paper's settings: lr 0.1, Adam
+ * betas (0.9, 0.999), eps 1e-8, tol 1e-5 over a window of 50 steps, at most
+ * 5000 steps (stage 8), median weight (quantile 0.5, section 3.3), Legendre
+ * degree 6, no edge pixels dropped, FP32 arithmetic. */
+typedef struct {
+    float lr, beta1, beta2, eps, tol;
+    int window;             /* 1..64                                   */
+    int max_steps;          /* 0..1000000                              */
+    int legendre_deg;       /* D, one of 2, 4, 6, 8                    */
+    int edge_px;            /* pixels at each end left out of the loss */
+    float quantile;         /* w_i = this quantile of the used flux    */
+    int precision;          /* LASP_PREC_*                              */
+    int fp64_normal_eq;     /* 1: cross-warp sums and 7x7 solve in FP64 */
+} lasp_fit_opts;
+
+void lasp_default_opts(lasp_fit_opts* o);
+
+/* Results (device, caller-owned).  theta N x 5 physical, loss N (Eq. 9 per
+ * spectrum), steps N (updates taken), status N (LASP_ST_* bits).
+ * cont_coeff: N x (D+1) continuum coefficients b for the normalised flux
+ * y = flux / w, or NULL.  weight: N values of w, or NULL. */
+typedef struct {
+    float* theta;
+    float* loss;
+    int32_t* steps;
+    uint32_t* status;
+    float* cont_coeff;
+    float* weight;
+} lasp_result;
+
+/* Fit every spectrum of the batch to convergence (stage 8): one fused kernel
+ * runs all Adam steps of a spectrum on one CTA, so each spectrum stops on its
+ * own rule and its CTA is reused at once.  Asynchronous on `stream`. */
+int lasp_fit_batch(lasp_interp h, const lasp_batch* batch, const lasp_fit_opts* opts,
+                   lasp_result* result, void* stream);
+
+/* Stage 9 parameter uncertainties at theta (device, N x 5 physical, e.g. the
+ * fitted values): Jacobian J of the weighted residual sqrt(W) eps w.r.t. the
+ * physical parameters with the continuum re-solved (variable projection),
+ * cov = (r.r / (n - 5)) (J^T J)^{-1} with n the used pixels; J^T J is
+ * accumulated and inverted in FP64.  sigma: device N x 5 = sqrt(diag cov).
+ * cov: device N x 25 FP64 or NULL.  status: device N or NULL (LASP_ST_*). */
+int lasp_errors(lasp_interp h, const lasp_batch* batch, const lasp_fit_opts* opts,
+                const float* theta, float* sigma, double* cov, uint32_t* status,
+                void* stream);
+
+/* Forward model of Eqs. 1, 5, 6 without the fit: model = (P b) * (G (x) phi C).
+ * theta: device N x 5 physical; b: device N x (deg+1); model: device N x n_pix. */
+int lasp_forward(lasp_interp h, int N, const float* theta, const float* b, int deg,
+                 float* model, void* stream);
+
+/* Vector-Jacobian product of lasp_forward (the hand-written adjoint): given
+ * gmodel = dL/dmodel (device N x n_pix) returns gtheta (device N x 5, physical
+ * units) and gb (device N x (deg+1)). */
+int lasp_backward(lasp_interp h, int N, const float* theta, const float* b, int deg,
+                  const float* gmodel, float* gtheta, float* gb, void* stream);
+
+/* The interpolator contraction alone (Eq. 1): Fp = phi(theta) C, device
+ * N x n_model output, with the arithmetic of `precision` (LASP_PREC_*). */
+int lasp_interp_eval(lasp_interp h, int N, const float* theta, float* Fp, int precision,
+                     void* stream);
+
+/* Number of kernels the last call on this thread enqueued (for accounting). */
+int lasp_last_launches(void);
+
+const char* lasp_strerror(int code);
+int lasp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

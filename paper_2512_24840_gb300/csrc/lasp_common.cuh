@@ -1,0 +1,299 @@
+// Shared device helpers of the grouped spectral fit (sm_103a).
+//
+// Per-spectrum work is done by one CTA.  Pixel j of a spectrum is owned by
+// thread (j mod NT) of its CTA, so per-pixel state (F'', delta) stays in that
+// thread's registers; arrays read across threads (F', the residual adjoint)
+// live in shared memory, where consecutive threads touch consecutive words.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace lasp {
+
+constexpr int KMAX = 32;          // basis terms supported
+constexpr int WINMAX = 64;        // stop-rule window supported
+constexpr int HMAX = 47;          // kernel half width supported (2H+1 <= 96 taps)
+constexpr int TAPS_MAX = 2 * HMAX + 1;
+
+// Interpolator constants passed by value to every kernel.
+struct ModelDev {
+    const float* C;          // K x n_model, row-major, FP32
+    int K, n_pix, pad, n_model;
+    float kms_px;            // c * dln: km/s per pixel
+    float blo[3], bscale[3]; // u = (v - blo) * bscale - 1
+    float plo[5], phalf[5];  // theta = plo + (x + 1) * phalf
+    int8_t exps[KMAX * 3];
+};
+
+struct FitOpts {
+    float lr, beta1, beta2, eps, tol;
+    int window, max_steps, edge_px;
+    float quantile;
+    int fp64_ne;
+};
+
+__device__ __forceinline__ float ipowf(float u, int a) {
+    float r = 1.0f;
+    for (int i = 0; i < a; ++i) r *= u;
+    return r;
+}
+
+// Physical parameters from normalised x (stage 8 rescaling).
+__device__ __forceinline__ float phys_of(const ModelDev& M, int k, float x) {
+    return fmaf(x + 1.0f, M.phalf[k], M.plo[k]);
+}
+
+// Basis of Eq. 1 (one regime): phi_k and d phi_k / d(Teff, logg, FeH).
+// Called by lane k < K of one warp.
+__device__ __forceinline__ void basis_term(const ModelDev& M, int k, const float th[3],
+                                           float* phi, float* dphi) {
+    float u0 = (log10f(th[0]) - M.blo[0]) * M.bscale[0] - 1.0f;
+    float u1 = (th[1] - M.blo[1]) * M.bscale[1] - 1.0f;
+    float u2 = (th[2] - M.blo[2]) * M.bscale[2] - 1.0f;
+    int a = M.exps[3 * k], b = M.exps[3 * k + 1], c = M.exps[3 * k + 2];
+    float pa = ipowf(u0, a), pb = ipowf(u1, b), pc = ipowf(u2, c);
+    phi[k] = pa * pb * pc;
+    if (dphi) {
+        // d u_T / d Teff = bscale / (Teff ln 10)
+        float du0 = M.bscale[0] / (th[0] * 2.302585092994046f);
+        dphi[3 * k + 0] = a ? (float)a * ipowf(u0, a - 1) * pb * pc * du0 : 0.0f;
+        dphi[3 * k + 1] = b ? (float)b * pa * ipowf(u1, b - 1) * pc * M.bscale[1] : 0.0f;
+        dphi[3 * k + 2] = c ? (float)c * pa * pb * ipowf(u2, c - 1) * M.bscale[2] : 0.0f;
+    }
+}
+
+// Sampled Gaussian kernel of Eq. 5 on s = -H..H (index s + H), unit sum over
+// |s| <= h = ceil(|mu| + 5 sigma), zero beyond; with d g / d mu and
+// d g / d sigma.  Executed by one full warp; returns h (clamped to H).
+__device__ __forceinline__ int kernel_taps_warp(float mu, float sig, int H, float* g,
+                                                float* gmu, float* gsg) {
+    const int lane = threadIdx.x & 31;
+    int h = (int)ceilf(fabsf(mu) + 5.0f * sig);
+    h = h > H ? H : (h < 0 ? 0 : h);
+    const float inv2s2 = 0.5f / (sig * sig);
+    float e[3], d[3], q[3];
+    float Z = 0.0f;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        int i = lane + 32 * r;
+        int s = i - H;
+        float ds = (float)s - mu;
+        e[r] = (i <= 2 * H && s >= -h && s <= h) ? expf(-ds * ds * inv2s2) : 0.0f;
+        d[r] = ds / (sig * sig);
+        q[r] = ds * ds / (sig * sig * sig);
+        Z += e[r];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) Z += __shfl_xor_sync(0xffffffffu, Z, o);
+    float md = 0.0f, mq = 0.0f;
+    const float iZ = 1.0f / Z;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        e[r] *= iZ;
+        md += e[r] * d[r];
+        mq += e[r] * q[r];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        md += __shfl_xor_sync(0xffffffffu, md, o);
+        mq += __shfl_xor_sync(0xffffffffu, mq, o);
+    }
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        int i = lane + 32 * r;
+        if (i <= 2 * H) {
+            g[i] = e[r];
+            if (gmu) gmu[i] = e[r] * (d[r] - md);
+            if (gsg) gsg[i] = e[r] * (q[r] - mq);
+        }
+    }
+    return h;
+}
+
+// Legendre P_0..P_D at x (Bonnet recursion), Eq. 6 nodes x_j = -1 + 2 j / p.
+template <int D>
+__device__ __forceinline__ void legendre(float x, float (&P)[D + 1]) {
+    P[0] = 1.0f;
+    if (D >= 1) P[1] = x;
+#pragma unroll
+    for (int n = 1; n < D; ++n)
+        P[n + 1] = ((float)(2 * n + 1) * x * P[n] - (float)n * P[n - 1]) * (1.0f / (float)(n + 1));
+}
+
+__device__ __forceinline__ float legendre_node(int j, int p) {
+    return -1.0f + (2.0f * (float)j) / (float)p;
+}
+
+template <int D>
+struct Gram {
+    static constexpr int NB = D + 1;
+    static constexpr int NG = NB * (NB + 1) / 2;
+    static constexpr int NV = NG + NB;   // packed upper triangle + right-hand side
+    __device__ static constexpr int idx(int a, int b) { return a * NB - a * (a - 1) / 2 + (b - a); }
+};
+
+// Block-wide sum of NV floats per thread.  Partial sums per warp go to
+// red[warp * NV + i]; thread i < NV adds the warps in a fixed order, so the
+// result depends only on the data of this CTA.  out may alias nothing in red.
+template <int NV, int NT>
+__device__ __forceinline__ void block_sum(float (&v)[NV], float* red, float* out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        float s = v[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) red[warp * NV + i] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        float s = 0.0f;
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w) s += red[w * NV + threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+// Same, with the cross-warp stage in FP64 (outd) -- the mixed-precision
+// normal equations keep their inter-warp sums and the solve in FP64.
+template <int NV, int NT>
+__device__ __forceinline__ void block_sum_f64(float (&v)[NV], float* red, double* outd) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        float s = v[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) red[warp * NV + i] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w) s += (double)red[w * NV + threadIdx.x];
+        outd[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+// Cholesky solve of the packed (D+1)x(D+1) SPD system; returns false when a
+// pivot is not positive.  T = float or double.
+template <int D, typename T>
+__device__ bool chol_solve_packed(const T* packed, const T* rhs, T* b) {
+    constexpr int n = D + 1;
+    T L[n][n];
+    T t[n];
+    for (int i = 0; i < n; ++i) {
+        for (int j = 0; j <= i; ++j) {
+            T s = packed[Gram<D>::idx(j, i)];
+            for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
+            if (i == j) {
+                if (!(s > T(0))) return false;
+                L[i][i] = sqrt(s);
+            } else {
+                L[i][j] = s / L[j][j];
+            }
+        }
+    }
+    for (int i = 0; i < n; ++i) {
+        T s = rhs[i];
+        for (int k = 0; k < i; ++k) s -= L[i][k] * t[k];
+        t[i] = s / L[i][i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        T s = t[i];
+        for (int k = i + 1; k < n; ++k) s -= L[k][i] * b[k];
+        b[i] = s / L[i][i];
+    }
+    return true;
+}
+
+// Bitonic sort (ascending) of P2 floats in shared memory by the whole CTA.
+template <int NT>
+__device__ void block_bitonic_sort(float* buf, int P2) {
+    for (int k = 2; k <= P2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < P2; i += NT) {
+                int ixj = i ^ j;
+                if (ixj > i) {
+                    float a = buf[i], b = buf[ixj];
+                    bool up = (i & k) == 0;
+                    if ((a > b) == up) {
+                        buf[i] = b;
+                        buf[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__host__ __device__ constexpr int next_pow2(int n) {
+    int p = 1;
+    while (p < n) p <<= 1;
+    return p;
+}
+
+// Per-spectrum preprocessing (section 3.3 step 2; Eq. 9 weights):
+// w = quantile of the used flux (linear interpolation between order
+// statistics), y = flux / w, W = ivar / mean(ivar over used pixels), both zero
+// on masked, non-finite and edge pixels.  sortbuf holds next_pow2(p) floats.
+// Returns the count of pixels that enter the loss; *w_out is w.
+template <int NT>
+__device__ int prep_spectrum(const float* __restrict__ flux, const float* __restrict__ ivar,
+                             const uint8_t* __restrict__ good, int p, int edge_px, float quantile,
+                             float* y, float* W, float* sortbuf, float* red, float* w_out) {
+    const int P2 = next_pow2(p);
+    float cnt = 0.0f, isum = 0.0f;
+    for (int j = threadIdx.x; j < P2; j += NT) {
+        float v = INFINITY;
+        if (j < p) {
+            float f = flux[j], iv = ivar[j];
+            bool use = good[j] && iv > 0.0f && isfinite(f) && isfinite(iv);
+            if (use) {
+                v = f;
+                cnt += 1.0f;
+                isum += iv;
+            }
+        }
+        sortbuf[j] = v;
+    }
+    float acc[2] = {cnt, isum};
+    float* tot = red + (NT / 32) * 2;
+    block_sum<2, NT>(acc, red, tot);
+    const int n = (int)tot[0];
+    const float imean = n > 0 ? tot[1] / (float)n : 0.0f;
+    block_bitonic_sort<NT>(sortbuf, P2);
+    float w = NAN;
+    if (n > 0) {
+        double pos = (double)quantile * (double)(n - 1);
+        int lo = (int)floor(pos);
+        if (lo >= n - 1) w = sortbuf[n - 1];
+        else w = (float)((double)sortbuf[lo] + (pos - lo) * ((double)sortbuf[lo + 1] - (double)sortbuf[lo]));
+    }
+    __syncthreads();
+    float nobj = 0.0f;
+    for (int j = threadIdx.x; j < p; j += NT) {
+        float f = flux[j], iv = ivar[j];
+        bool use = good[j] && iv > 0.0f && isfinite(f) && isfinite(iv);
+        bool edge = j < edge_px || j >= p - edge_px;
+        if (use && !edge && w > 0.0f) {
+            y[j] = f / w;
+            W[j] = iv / imean;
+            nobj += 1.0f;
+        } else {
+            y[j] = 0.0f;
+            W[j] = 0.0f;
+        }
+    }
+    float acc1[1] = {nobj};
+    block_sum<1, NT>(acc1, red, tot);
+    *w_out = w;
+    return (int)tot[0];
+}
+
+}  // namespace lasp

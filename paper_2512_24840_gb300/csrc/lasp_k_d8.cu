@@ -1,0 +1,7 @@
+// FP32 CUDA-core kernels for Legendre degree D = 8.
+#define LASP_DEFINE_LAUNCHERS
+#include "lasp_launch.cuh"
+
+namespace lasp {
+LASP_INSTANTIATE(8)
+}  // namespace lasp

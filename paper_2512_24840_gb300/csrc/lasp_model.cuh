@@ -1,0 +1,458 @@
+// Forward model, its adjoint, the stage-9 Jacobian and the standalone basis
+// contraction (FP32 CUDA-core forms) -- sm_103a.
+#pragma once
+
+#include "lasp_common.cuh"
+
+namespace lasp {
+
+struct ModelParams {
+    ModelDev M;
+    int N, D;
+    const float* theta;   // N x 5 physical
+    const float* b;       // N x (D+1)
+    float* model;         // N x n_pix              (forward)
+    const float* gmodel;  // N x n_pix              (backward)
+    float* gtheta;        // N x 5                  (backward)
+    float* gb;            // N x (D+1)              (backward)
+};
+
+__host__ inline size_t model_smem_bytes(int p, int H, int n_model) {
+    return 4 * (size_t)(((n_model + 3) & ~3) + ((p + 4 * H + 3) & ~3) + 3 * 96 + 4 * KMAX + 16 * 64);
+}
+
+// Per-spectrum basis + taps + F' into shared memory (one CTA).
+template <int NT>
+__device__ __forceinline__ int cta_interp(const ModelDev& M, const float* th5, float* phi, float* dphi,
+                                          float* g, float* gmu, float* gsg, float* Fp, int* s_h) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp == 0) {
+        float th[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) th[k] = th5[k];
+        if (lane < M.K) basis_term(M, lane, th, phi, dphi);
+        int h = kernel_taps_warp(th[3] / M.kms_px, th[4] / M.kms_px, M.pad, g, gmu, gsg);
+        if (lane == 0) *s_h = h;
+    }
+    __syncthreads();
+    for (int mm = threadIdx.x; mm < M.n_model; mm += NT) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k)
+            if (k < M.K) acc = fmaf(phi[k], __ldg(M.C + (size_t)k * M.n_model + mm), acc);
+        Fp[mm] = acc;
+    }
+    __syncthreads();
+    return *s_h;
+}
+
+// model = (P b) * (G (x) phi C)  (Eqs. 1, 5, 6); one CTA per spectrum.
+template <int NT, int D>
+__global__ void __launch_bounds__(NT) forward_kernel(const ModelParams P) {
+    constexpr int NB = D + 1;
+    extern __shared__ __align__(16) float sm[];
+    const ModelDev& M = P.M;
+    const int p = M.n_pix, H = M.pad, i = blockIdx.x;
+    float* Fp = sm;
+    float* g = Fp + ((M.n_model + 3) & ~3) + ((p + 4 * H + 3) & ~3);
+    float* phi = g + 3 * 96;
+    __shared__ int s_h;
+    float th[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) th[k] = P.theta[5 * i + k];
+    const int h = cta_interp<NT>(M, th, phi, nullptr, g, nullptr, nullptr, Fp, &s_h);
+    float bl[NB];
+#pragma unroll
+    for (int a = 0; a < NB; ++a) bl[a] = P.b[(size_t)i * NB + a];
+    for (int j = threadIdx.x; j < p; j += NT) {
+        const float* src = Fp + j + H;
+        float f = 0.0f;
+        for (int s = -h; s <= h; ++s) f = fmaf(g[s + H], src[-s], f);
+        float Pl[NB];
+        legendre<D>(legendre_node(j, p), Pl);
+        float c = 0.0f;
+#pragma unroll
+        for (int a = 0; a < NB; ++a) c = fmaf(bl[a], Pl[a], c);
+        P.model[(size_t)i * p + j] = c * f;
+    }
+}
+
+// Hand-written adjoint of forward_kernel: gtheta (physical), gb.
+template <int NT, int D>
+__global__ void __launch_bounds__(NT) backward_kernel(const ModelParams P) {
+    constexpr int NB = D + 1;
+    constexpr int NV = NB + 2 + KMAX;
+    extern __shared__ __align__(16) float sm[];
+    const ModelDev& M = P.M;
+    const int p = M.n_pix, H = M.pad, nm = M.n_model, i = blockIdx.x;
+    float* Fp = sm;
+    float* Db = Fp + ((nm + 3) & ~3);
+    float* g = Db + ((p + 4 * H + 3) & ~3);
+    float* gmu = g + 96;
+    float* gsg = g + 192;
+    float* phi = g + 3 * 96;
+    float* dphi = phi + KMAX;
+    float* red = phi + 4 * KMAX;
+    float* out = red + (NT / 32) * NV;
+    __shared__ int s_h;
+    float th[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) th[k] = P.theta[5 * i + k];
+    for (int j = threadIdx.x; j < p + 4 * H; j += NT) Db[j] = 0.0f;
+    const int h = cta_interp<NT>(M, th, phi, dphi, g, gmu, gsg, Fp, &s_h);
+    float bl[NB];
+#pragma unroll
+    for (int a = 0; a < NB; ++a) bl[a] = P.b[(size_t)i * NB + a];
+    float acc[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) acc[q] = 0.0f;
+    // d model_j / d b_d = P_d F''_j ; dL/dF''_j = gm_j c_j
+    for (int j = threadIdx.x; j < p; j += NT) {
+        const float* src = Fp + j + H;
+        float f = 0.0f, am = 0.0f, as = 0.0f;
+        for (int s = -h; s <= h; ++s) {
+            const float fv = src[-s];
+            f = fmaf(g[s + H], fv, f);
+            am = fmaf(gmu[s + H], fv, am);
+            as = fmaf(gsg[s + H], fv, as);
+        }
+        float Pl[NB];
+        legendre<D>(legendre_node(j, p), Pl);
+        float c = 0.0f;
+#pragma unroll
+        for (int a = 0; a < NB; ++a) c = fmaf(bl[a], Pl[a], c);
+        const float gm = P.gmodel[(size_t)i * p + j];
+#pragma unroll
+        for (int a = 0; a < NB; ++a) acc[a] = fmaf(gm * f, Pl[a], acc[a]);
+        const float d = gm * c;
+        acc[NB] = fmaf(d, am, acc[NB]);
+        acc[NB + 1] = fmaf(d, as, acc[NB + 1]);
+        Db[j + 2 * H] = d;
+    }
+    __syncthreads();
+    for (int mm = threadIdx.x; mm < nm; mm += NT) {
+        const float* src = Db + mm + H;
+        float d = 0.0f;
+        for (int s = -h; s <= h; ++s) d = fmaf(g[s + H], src[s], d);
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k)
+            if (k < M.K) acc[NB + 2 + k] = fmaf(d, __ldg(M.C + (size_t)k * nm + mm), acc[NB + 2 + k]);
+    }
+    block_sum<NV, NT>(acc, red, out);
+    if (threadIdx.x < NB) P.gb[(size_t)i * NB + threadIdx.x] = out[threadIdx.x];
+    if (threadIdx.x < 3) {
+        float s = 0.0f;
+        for (int k = 0; k < M.K; ++k) s = fmaf(out[NB + 2 + k], dphi[3 * k + threadIdx.x], s);
+        P.gtheta[5 * i + threadIdx.x] = s;
+    }
+    if (threadIdx.x == 3) P.gtheta[5 * i + 3] = out[NB] / M.kms_px;
+    if (threadIdx.x == 4) P.gtheta[5 * i + 4] = out[NB + 1] / M.kms_px;
+}
+
+// Eq. 1 alone: Fp = phi(theta) C (N x n_model), FP32 CUDA cores.
+template <int NT>
+__global__ void __launch_bounds__(NT) interp_fp32_kernel(ModelDev M, const float* __restrict__ theta,
+                                                         float* __restrict__ Fp) {
+    __shared__ float phi[KMAX];
+    const int i = blockIdx.x;
+    if (threadIdx.x < 32) {
+        float th[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) th[k] = theta[5 * i + k];
+        if (threadIdx.x < M.K) basis_term(M, threadIdx.x, th, phi, nullptr);
+    }
+    __syncthreads();
+    const int mm = blockIdx.y * NT + threadIdx.x;
+    if (mm < M.n_model) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k)
+            if (k < M.K) acc = fmaf(phi[k], __ldg(M.C + (size_t)k * M.n_model + mm), acc);
+        Fp[(size_t)i * M.n_model + mm] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Stage 9 parameter errors.  J = d r / d theta of the weighted residual
+// r = sqrt(W) eps with the continuum b re-solved (variable projection), taken
+// analytically: dF''/dtheta from the basis derivatives and the kernel
+// derivatives; db/dtheta from the normal equations,
+//   db_k = G^-1 sum_j W_j P(x_j) dF''_jk (eps_j - F''_j c_j),
+//   J_jk = -sqrt(W_j) (c_j dF''_jk + F''_j (P db_k)_j).
+// cov = (r.r / (n - 5)) (J^T J)^-1; J^T J summed and inverted in FP64.
+
+struct ErrParams {
+    ModelDev M;
+    FitOpts O;
+    int N;
+    const float* flux;
+    const float* ivar;
+    const uint8_t* good;
+    const float* theta;
+    float* sigma;
+    double* cov;
+    uint32_t* status;
+};
+
+__host__ inline size_t err_smem_bytes(int p, int H, int n_model, int NT) {
+    size_t fl = (size_t)2 * ((p + 3) & ~3) + 4 * (size_t)((n_model + 3) & ~3) + 3 * 96 + 4 * KMAX +
+                (size_t)(NT / 32) * 48 + 256;
+    size_t sortb = (size_t)2 * ((p + 3) & ~3) + next_pow2(p);
+    return 4 * (fl > sortb ? fl : sortb);
+}
+
+template <int D>
+__device__ bool inv5_f64(const double* A, double* Ai) {
+    double a[5][10];
+    for (int r = 0; r < 5; ++r)
+        for (int c = 0; c < 10; ++c) a[r][c] = c < 5 ? A[r * 5 + c] : (c - 5 == r ? 1.0 : 0.0);
+    for (int c = 0; c < 5; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < 5; ++r)
+            if (fabs(a[r][c]) > fabs(a[piv][c])) piv = r;
+        if (!(fabs(a[piv][c]) > 0.0)) return false;
+        if (piv != c)
+            for (int k = 0; k < 10; ++k) {
+                double t = a[c][k];
+                a[c][k] = a[piv][k];
+                a[piv][k] = t;
+            }
+        double d = a[c][c];
+        for (int k = 0; k < 10; ++k) a[c][k] /= d;
+        for (int r = 0; r < 5; ++r) {
+            if (r == c) continue;
+            double f = a[r][c];
+            for (int k = 0; k < 10; ++k) a[r][k] -= f * a[c][k];
+        }
+    }
+    for (int r = 0; r < 5; ++r)
+        for (int c = 0; c < 5; ++c) Ai[r * 5 + c] = a[r][c + 5];
+    return true;
+}
+
+template <int NT, int D>
+__global__ void __launch_bounds__(NT) errors_kernel(const ErrParams P) {
+    using Gm = Gram<D>;
+    constexpr int NB = D + 1;
+    constexpr int NV = Gm::NV;
+    constexpr int PPT = 16;
+    extern __shared__ __align__(16) float sm[];
+    const ModelDev& M = P.M;
+    const int p = M.n_pix, H = M.pad, nm = M.n_model, K = M.K;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int i = blockIdx.x;
+    const int pa = (p + 3) & ~3, na = (nm + 3) & ~3;
+    float* y = sm;
+    float* W = y + pa;
+    float* Fp = W + pa;              // F', dF'/dTeff, dF'/dlogg, dF'/dFeH
+    float* g = Fp + 4 * na;
+    float* gmu = g + 96;
+    float* gsg = g + 192;
+    float* phi = g + 288;
+    float* dphi = phi + KMAX;
+    float* red = phi + 4 * KMAX;
+    float* outf = red + (NT / 32) * 48;
+    double* outd = reinterpret_cast<double*>(outf + ((((size_t)(outf - sm)) & 1) ? 1 : 0));
+    __shared__ double s_G[Gm::NV], s_b[NB], s_db[5 * NB], s_JJ[16];
+    __shared__ int s_h, s_ok;
+
+    const size_t row = (size_t)i * p;
+    float w;
+    const int n_obj = prep_spectrum<NT>(P.flux + row, P.ivar + row, P.good + row, p, P.O.edge_px,
+                                        P.O.quantile, y, W, Fp, red, &w);
+    if (n_obj <= 5 || !(w > 0.0f)) {
+        if (tid < 5) P.sigma[5 * i + tid] = NAN;
+        if (P.cov && tid < 25) P.cov[25 * (size_t)i + tid] = NAN;
+        if (P.status && tid == 0) P.status[i] = 64u;
+        return;
+    }
+    if (warp == 0) {
+        float th[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) th[k] = P.theta[5 * i + k];
+        if (lane < K) basis_term(M, lane, th, phi, dphi);
+        int h = kernel_taps_warp(th[3] / M.kms_px, th[4] / M.kms_px, H, g, gmu, gsg);
+        if (lane == 0) s_h = h;
+    }
+    __syncthreads();
+    const int h = s_h;
+    for (int mm = tid; mm < nm; mm += NT) {
+        float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+        for (int k = 0; k < K; ++k) {
+            const float c = __ldg(M.C + (size_t)k * nm + mm);
+            a0 = fmaf(phi[k], c, a0);
+            a1 = fmaf(dphi[3 * k + 0], c, a1);
+            a2 = fmaf(dphi[3 * k + 1], c, a2);
+            a3 = fmaf(dphi[3 * k + 2], c, a3);
+        }
+        Fp[mm] = a0;
+        Fp[na + mm] = a1;
+        Fp[2 * na + mm] = a2;
+        Fp[3 * na + mm] = a3;
+    }
+    __syncthreads();
+    // F'' and its five derivatives per owned pixel (registers)
+    float f[PPT], df[5][PPT];
+    float gacc[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) gacc[q] = 0.0f;
+    const float ikms = 1.0f / M.kms_px;
+#pragma unroll
+    for (int r = 0; r < PPT; ++r) {
+        const int j = tid + r * NT;
+        f[r] = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) df[k][r] = 0.0f;
+        if (j < p) {
+            float a0 = 0, a1 = 0, a2 = 0, a3 = 0, am = 0, as = 0;
+            for (int s = -h; s <= h; ++s) {
+                const int o = j + H - s;
+                const float gs = g[s + H];
+                const float fv = Fp[o];
+                a0 = fmaf(gs, fv, a0);
+                a1 = fmaf(gs, Fp[na + o], a1);
+                a2 = fmaf(gs, Fp[2 * na + o], a2);
+                a3 = fmaf(gs, Fp[3 * na + o], a3);
+                am = fmaf(gmu[s + H], fv, am);
+                as = fmaf(gsg[s + H], fv, as);
+            }
+            f[r] = a0;
+            df[0][r] = a1;
+            df[1][r] = a2;
+            df[2][r] = a3;
+            df[3][r] = am * ikms;
+            df[4][r] = as * ikms;
+            const float Wj = W[j];
+            if (Wj != 0.0f) {
+                float Pl[NB];
+                legendre<D>(legendre_node(j, p), Pl);
+                const float vv = Wj * a0 * a0, uu = Wj * a0 * y[j];
+#pragma unroll
+                for (int a = 0; a < NB; ++a) {
+#pragma unroll
+                    for (int b2 = a; b2 < NB; ++b2) gacc[Gm::idx(a, b2)] = fmaf(vv * Pl[a], Pl[b2], gacc[Gm::idx(a, b2)]);
+                    gacc[Gm::NG + a] = fmaf(uu, Pl[a], gacc[Gm::NG + a]);
+                }
+            }
+        }
+    }
+    block_sum_f64<NV, NT>(gacc, red, outd);
+    if (tid == 0) {
+        for (int q = 0; q < NV; ++q) s_G[q] = outd[q];
+        double bd[NB];
+        s_ok = chol_solve_packed<D, double>(s_G, s_G + Gm::NG, bd) ? 1 : 0;
+        for (int a = 0; a < NB; ++a) s_b[a] = bd[a];
+    }
+    __syncthreads();
+    if (!s_ok) {
+        if (tid < 5) P.sigma[5 * i + tid] = NAN;
+        if (P.cov && tid < 25) P.cov[25 * (size_t)i + tid] = NAN;
+        if (P.status && tid == 0) P.status[i] = 32u;
+        return;
+    }
+    // t_k[d] = sum_j W_j P_d dF''_jk (eps_j - F''_j c_j), and r.r
+    constexpr int NT2 = 5 * NB + 1;
+    float tacc[NT2];
+#pragma unroll
+    for (int q = 0; q < NT2; ++q) tacc[q] = 0.0f;
+    float bl[NB];
+#pragma unroll
+    for (int a = 0; a < NB; ++a) bl[a] = (float)s_b[a];
+    float cc[PPT];
+#pragma unroll
+    for (int r = 0; r < PPT; ++r) {
+        const int j = tid + r * NT;
+        cc[r] = 0.0f;
+        if (j < p && W[j] != 0.0f) {
+            float Pl[NB];
+            legendre<D>(legendre_node(j, p), Pl);
+            float c = 0.0f;
+#pragma unroll
+            for (int a = 0; a < NB; ++a) c = fmaf(bl[a], Pl[a], c);
+            cc[r] = c;
+            const float Wj = W[j];
+            const float e = y[j] - c * f[r];
+            const float q = Wj * (e - f[r] * c);
+#pragma unroll
+            for (int k = 0; k < 5; ++k)
+#pragma unroll
+                for (int a = 0; a < NB; ++a) tacc[k * NB + a] = fmaf(q * df[k][r], Pl[a], tacc[k * NB + a]);
+            tacc[5 * NB] = fmaf(Wj * e, e, tacc[5 * NB]);
+        }
+    }
+    block_sum_f64<NT2, NT>(tacc, red, outd);
+    if (tid < 5) {
+        // db_k = G^-1 t_k
+        double tk[NB], dbk[NB];
+        for (int a = 0; a < NB; ++a) tk[a] = outd[tid * NB + a];
+        chol_solve_packed<D, double>(s_G, tk, dbk);
+        for (int a = 0; a < NB; ++a) s_db[tid * NB + a] = dbk[a];
+    }
+    if (tid == 0) s_JJ[15] = outd[5 * NB];
+    __syncthreads();
+    // J_jk and J^T J (15 sums, per-thread FP64 accumulation)
+    float dbl[5][NB];
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+#pragma unroll
+        for (int a = 0; a < NB; ++a) dbl[k][a] = (float)s_db[k * NB + a];
+    double jj[15];
+#pragma unroll
+    for (int q = 0; q < 15; ++q) jj[q] = 0.0;
+#pragma unroll
+    for (int r = 0; r < PPT; ++r) {
+        const int j = tid + r * NT;
+        if (j < p && W[j] != 0.0f) {
+            float Pl[NB];
+            legendre<D>(legendre_node(j, p), Pl);
+            const float sw = sqrtf(W[j]);
+            float Jr[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                float dc = 0.0f;
+#pragma unroll
+                for (int a = 0; a < NB; ++a) dc = fmaf(dbl[k][a], Pl[a], dc);
+                Jr[k] = -sw * (cc[r] * df[k][r] + f[r] * dc);
+            }
+            int q = 0;
+#pragma unroll
+            for (int a = 0; a < 5; ++a)
+#pragma unroll
+                for (int b2 = a; b2 < 5; ++b2) jj[q++] += (double)Jr[a] * (double)Jr[b2];
+        }
+    }
+    // FP64 block reduction of the 15 sums
+    double* redd = reinterpret_cast<double*>(red + ((((size_t)(red - sm)) & 1) ? 1 : 0));
+#pragma unroll
+    for (int q = 0; q < 15; ++q) {
+        double s = jj[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) redd[warp * 15 + q] = s;
+    }
+    __syncthreads();
+    if (tid < 15) {
+        double s = 0.0;
+        for (int w2 = 0; w2 < NT / 32; ++w2) s += redd[w2 * 15 + tid];
+        s_JJ[tid] = s;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double A[25], Ai[25];
+        int q = 0;
+        for (int a = 0; a < 5; ++a)
+            for (int b2 = a; b2 < 5; ++b2) {
+                A[a * 5 + b2] = s_JJ[q];
+                A[b2 * 5 + a] = s_JJ[q];
+                ++q;
+            }
+        bool ok = inv5_f64<D>(A, Ai);
+        const double s2 = s_JJ[15] / (double)(n_obj - 5);
+        for (int k = 0; k < 5; ++k) P.sigma[5 * i + k] = ok ? (float)sqrt(s2 * Ai[k * 5 + k]) : NAN;
+        if (P.cov)
+            for (int k = 0; k < 25; ++k) P.cov[25 * (size_t)i + k] = ok ? s2 * Ai[k] : NAN;
+        if (P.status) P.status[i] = ok ? 0u : 32u;
+    }
+}
+
+}  // namespace lasp

@@ -1,0 +1,248 @@
+"""Python binding of liblasp.so (argument marshalling only).
+
+Every call goes through the C-ABI declared in include/lasp.h; all arithmetic
+of the fit runs in the library's CUDA kernels.  PyTorch provides device
+memory (tensors whose data pointers are passed down) and streams.  There is
+no CPU fallback: if the library cannot be loaded or no sm_103 device is
+present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import threading
+
+import numpy as np
+import torch
+
+from . import _build
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EGRID, ENODEV = 0, -1, -2, -3, -4, -5, -6
+ST_CONV_TOL, ST_CONV_RISE, ST_MAXSTEPS, ST_NONPOS = 1, 2, 4, 8
+ST_NONFINITE, ST_SINGULAR, ST_NODATA, ST_RUNNING = 16, 32, 64, 128
+PREC = {"fp32": 0, "tf32": 1, "bf16": 2, "tf32x3": 3}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class LaspError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+        self.code = code
+
+
+class InterpDesc(ct.Structure):
+    _fields_ = [("K", ct.c_int), ("n_pix", ct.c_int), ("pad", ct.c_int), ("dln", ct.c_double),
+                ("exps", ct.c_void_p), ("basis_lo", ct.c_double * 3),
+                ("basis_hi", ct.c_double * 3), ("box_lo", ct.c_double * 5),
+                ("box_hi", ct.c_double * 5)]
+
+
+class Batch(ct.Structure):
+    _fields_ = [("N", ct.c_int), ("n_pix", ct.c_int), ("flux", ct.c_void_p),
+                ("ivar", ct.c_void_p), ("good", ct.c_void_p), ("theta0", ct.c_void_p)]
+
+
+class FitOpts(ct.Structure):
+    _fields_ = [("lr", ct.c_float), ("beta1", ct.c_float), ("beta2", ct.c_float),
+                ("eps", ct.c_float), ("tol", ct.c_float), ("window", ct.c_int),
+                ("max_steps", ct.c_int), ("legendre_deg", ct.c_int), ("edge_px", ct.c_int),
+                ("quantile", ct.c_float), ("precision", ct.c_int), ("fp64_normal_eq", ct.c_int)]
+
+
+class Result(ct.Structure):
+    _fields_ = [("theta", ct.c_void_p), ("loss", ct.c_void_p), ("steps", ct.c_void_p),
+                ("status", ct.c_void_p), ("cont_coeff", ct.c_void_p), ("weight", ct.c_void_p)]
+
+
+EXPORTS = ["lasp_init_interp", "lasp_free_interp", "lasp_default_opts", "lasp_fit_batch",
+           "lasp_errors", "lasp_forward", "lasp_backward", "lasp_interp_eval",
+           "lasp_last_launches", "lasp_strerror", "lasp_version"]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build: bool = False):
+    """Load liblasp.so (building it first when build=True)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build() if build else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library {path} is not built; run __graft_entry__.build()")
+        lib = ct.CDLL(path)
+        P, I = ct.c_void_p, ct.c_int
+        lib.lasp_init_interp.argtypes = [P, P, P]
+        lib.lasp_init_interp.restype = I
+        lib.lasp_free_interp.argtypes = [P]
+        lib.lasp_default_opts.argtypes = [P]
+        lib.lasp_fit_batch.argtypes = [P, P, P, P, P]
+        lib.lasp_fit_batch.restype = I
+        lib.lasp_errors.argtypes = [P, P, P, P, P, P, P, P]
+        lib.lasp_errors.restype = I
+        lib.lasp_forward.argtypes = [P, I, P, P, I, P, P]
+        lib.lasp_forward.restype = I
+        lib.lasp_backward.argtypes = [P, I, P, P, I, P, P, P, P]
+        lib.lasp_backward.restype = I
+        lib.lasp_interp_eval.argtypes = [P, I, P, P, I, P]
+        lib.lasp_interp_eval.restype = I
+        lib.lasp_last_launches.restype = I
+        lib.lasp_strerror.argtypes = [I]
+        lib.lasp_strerror.restype = ct.c_char_p
+        lib.lasp_version.restype = I
+        _lib = lib
+        return lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return load().lasp_strerror(int(code)).decode()
+    except Exception:
+        return "unknown"
+
+
+def _check(code, what):
+    if code != OK:
+        raise LaspError(code, what)
+
+
+def _ptr(t):
+    return None if t is None else ct.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ct.c_void_p(s.cuda_stream)
+
+
+def _dev(t, dtype):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise TypeError(f"expected a contiguous CUDA {dtype} tensor")
+    return t
+
+
+def default_opts(**kw) -> FitOpts:
+    o = FitOpts()
+    load().lasp_default_opts(ct.byref(o))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = PREC[v]
+        if not hasattr(o, k):
+            raise TypeError(f"unknown fit option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def last_launches() -> int:
+    return int(load().lasp_last_launches())
+
+
+class Interp:
+    """Device-resident interpolator (Eq. 1 table) on one ln-lambda grid."""
+
+    def __init__(self, C, exps, n_pix, pad, dln, basis_lo, basis_hi, box_lo, box_hi):
+        lib = load()
+        C = np.ascontiguousarray(C, dtype=np.float32)
+        self._exps = np.ascontiguousarray(exps, dtype=np.int8)
+        K = self._exps.shape[0]
+        if C.shape != (K, n_pix + 2 * pad):
+            raise ValueError("table shape must be K x (n_pix + 2 pad)")
+        d = InterpDesc(K, int(n_pix), int(pad), float(dln), self._exps.ctypes.data,
+                       (ct.c_double * 3)(*basis_lo), (ct.c_double * 3)(*basis_hi),
+                       (ct.c_double * 5)(*box_lo), (ct.c_double * 5)(*box_hi))
+        h = ct.c_void_p()
+        _check(lib.lasp_init_interp(ct.byref(d), C.ctypes.data, ct.byref(h)), "lasp_init_interp")
+        self._h = h
+        self.K, self.n_pix, self.pad = K, int(n_pix), int(pad)
+        self.n_model = self.n_pix + 2 * self.pad
+        self.dln = float(dln)
+        self.box_lo, self.box_hi = np.asarray(box_lo, float), np.asarray(box_hi, float)
+
+    @classmethod
+    def from_grid(cls, grid, C, exps, basis_lo, basis_hi, box_lo, box_hi):
+        return cls(C, exps, grid.n_pix, grid.pad, grid.dln, basis_lo, basis_hi, box_lo, box_hi)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.lasp_free_interp(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ calls
+
+    def _batch(self, flux, ivar, good, theta0):
+        N = flux.shape[0]
+        _dev(flux, torch.float32), _dev(ivar, torch.float32), _dev(good, torch.uint8)
+        _dev(theta0, torch.float32)
+        if flux.shape != (N, self.n_pix) or ivar.shape != flux.shape or good.shape != flux.shape \
+                or theta0.shape != (N, 5):
+            raise ValueError("batch shapes must be N x n_pix (and N x 5 for theta0)")
+        return Batch(N, self.n_pix, flux.data_ptr(), ivar.data_ptr(), good.data_ptr(),
+                     theta0.data_ptr())
+
+    def fit(self, flux, ivar, good, theta0, out=None, stream=None, **opts):
+        """lasp_fit_batch: returns dict of device tensors theta, loss, steps,
+        status, cont (N x (D+1)), weight."""
+        o = default_opts(**opts)
+        b = self._batch(flux, ivar, good, theta0)
+        N, dev = b.N, flux.device
+        if out is None:
+            out = dict(theta=torch.empty((N, 5), device=dev),
+                       loss=torch.empty(N, device=dev),
+                       steps=torch.empty(N, device=dev, dtype=torch.int32),
+                       status=torch.empty(N, device=dev, dtype=torch.int32),
+                       cont=torch.empty((N, o.legendre_deg + 1), device=dev),
+                       weight=torch.empty(N, device=dev))
+        r = Result(out["theta"].data_ptr(), out["loss"].data_ptr(), out["steps"].data_ptr(),
+                   out["status"].data_ptr(),
+                   out["cont"].data_ptr() if out.get("cont") is not None else None,
+                   out["weight"].data_ptr() if out.get("weight") is not None else None)
+        _check(load().lasp_fit_batch(self._h, ct.byref(b), ct.byref(o), ct.byref(r),
+                                     _stream(stream)), "lasp_fit_batch")
+        return out
+
+    def errors(self, flux, ivar, good, theta, with_cov=True, stream=None, **opts):
+        o = default_opts(**opts)
+        _dev(theta, torch.float32)
+        b = self._batch(flux, ivar, good, theta)
+        N, dev = b.N, flux.device
+        sigma = torch.empty((N, 5), device=dev)
+        cov = torch.empty((N, 5, 5), device=dev, dtype=torch.float64) if with_cov else None
+        status = torch.empty(N, device=dev, dtype=torch.int32)
+        _check(load().lasp_errors(self._h, ct.byref(b), ct.byref(o), _ptr(theta), _ptr(sigma),
+                                  _ptr(cov), _ptr(status), _stream(stream)), "lasp_errors")
+        return dict(sigma=sigma, cov=cov, status=status)
+
+    def forward(self, theta, b, stream=None):
+        _dev(theta, torch.float32), _dev(b, torch.float32)
+        N, deg = theta.shape[0], b.shape[1] - 1
+        model = torch.empty((N, self.n_pix), device=theta.device)
+        _check(load().lasp_forward(self._h, N, _ptr(theta), _ptr(b), deg, _ptr(model),
+                                   _stream(stream)), "lasp_forward")
+        return model
+
+    def backward(self, theta, b, gmodel, stream=None):
+        _dev(theta, torch.float32), _dev(b, torch.float32), _dev(gmodel, torch.float32)
+        N, deg = theta.shape[0], b.shape[1] - 1
+        gtheta = torch.empty((N, 5), device=theta.device)
+        gb = torch.empty((N, deg + 1), device=theta.device)
+        _check(load().lasp_backward(self._h, N, _ptr(theta), _ptr(b), deg, _ptr(gmodel),
+                                    _ptr(gtheta), _ptr(gb), _stream(stream)), "lasp_backward")
+        return gtheta, gb
+
+    def interp_eval(self, theta, precision="fp32", stream=None):
+        _dev(theta, torch.float32)
+        N = theta.shape[0]
+        Fp = torch.empty((N, self.n_model), device=theta.device)
+        _check(load().lasp_interp_eval(self._h, N, _ptr(theta), _ptr(Fp), PREC[precision],
+                                       _stream(stream)), "lasp_interp_eval")
+        return Fp

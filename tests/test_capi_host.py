@@ -1,0 +1,96 @@
+"""Host-side checks of the C-ABI library (no GPU needed): it loads, exports
+every symbol include/lasp.h declares, and rejects bad arguments before any
+device work."""
+import ctypes as ct
+import os
+import re
+
+import numpy as np
+import pytest
+
+import lasp_synth as S
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lasp():
+    from paper_2512_24840_gb300 import lasp as L
+    L.load(build=True)
+    return L
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            names |= set(re.findall(r"\b(lasp_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+def test_exports_every_declared_symbol(lasp):
+    lib = lasp.load()
+    declared = _declared()
+    assert declared >= set(lasp.EXPORTS)
+    for name in sorted(declared):
+        assert hasattr(lib, name), name
+
+
+def test_strerror_and_defaults(lasp):
+    assert lasp.strerror(0) == "ok"
+    assert "invalid" in lasp.strerror(-1)
+    o = lasp.default_opts()
+    assert abs(o.lr - 0.1) < 1e-7 and o.window == 50 and o.max_steps == 5000
+    assert o.legendre_deg == 6 and abs(o.quantile - 0.5) < 1e-7 and abs(o.tol - 1e-5) < 1e-12
+
+
+def _desc(lasp, g, pad=None, K=None, exps=None):
+    exps = S.EXPS if exps is None else exps
+    return lasp.InterpDesc(len(exps) if K is None else K, g.n_pix, g.pad if pad is None else pad,
+                           g.dln, exps.ctypes.data, (ct.c_double * 3)(*S.BASIS_LO),
+                           (ct.c_double * 3)(*S.BASIS_HI), (ct.c_double * 5)(*S.BOX_LO),
+                           (ct.c_double * 5)(*S.BOX_HI))
+
+
+def test_init_validation(lasp):
+    lib = lasp.load()
+    g = S.SMALL
+    C = np.zeros((26, g.n_model), dtype=np.float32)
+    h = ct.c_void_p()
+    exps = np.ascontiguousarray(S.EXPS)
+    # pad smaller than the widest kernel of the box (Eq. 5)
+    d = _desc(lasp, g, pad=g.pad - 1, exps=exps)
+    assert lib.lasp_init_interp(ct.byref(d), C.ctypes.data, ct.byref(h)) == lasp.EGRID
+    d = _desc(lasp, g, K=0, exps=exps)
+    assert lib.lasp_init_interp(ct.byref(d), C.ctypes.data, ct.byref(h)) == lasp.EINVAL
+    bad = exps.copy()
+    bad[3, 0] = -1
+    d = _desc(lasp, g, exps=bad)
+    assert lib.lasp_init_interp(ct.byref(d), C.ctypes.data, ct.byref(h)) == lasp.EINVAL
+    assert lib.lasp_init_interp(None, C.ctypes.data, ct.byref(h)) == lasp.EINVAL
+
+
+def test_no_device_is_reported(lasp):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    lib = lasp.load()
+    g = S.SMALL
+    C = np.zeros((26, g.n_model), dtype=np.float32)
+    exps = np.ascontiguousarray(S.EXPS)
+    d = _desc(lasp, g, exps=exps)
+    h = ct.c_void_p()
+    assert lib.lasp_init_interp(ct.byref(d), C.ctypes.data, ct.byref(h)) == lasp.ENODEV
+
+
+def test_null_handle_calls_fail_cleanly(lasp):
+    lib = lasp.load()
+    o = lasp.default_opts()
+    b = lasp.Batch(4, 1024, None, None, None, None)
+    r = lasp.Result()
+    assert lib.lasp_fit_batch(None, ct.byref(b), ct.byref(o), ct.byref(r), None) == lasp.EINVAL
+    assert lib.lasp_forward(None, 1, None, None, 6, None, None) == lasp.EINVAL
+    assert lib.lasp_backward(None, 1, None, None, 6, None, None, None, None) == lasp.EINVAL
+    assert lib.lasp_interp_eval(None, 1, None, None, 0, None) == lasp.EINVAL
+    lib.lasp_free_interp(None)
