@@ -14,6 +14,7 @@ struct lasp_interp_s {
     ModelDev M;              // device table pointer + constants
     int device;
     float* C;                // K x n_model FP32
+    float* Cp;               // K x ldc FP32, rows padded to 16 floats
     TcImages tc;             // tensor-core tile images of the table
 };
 
@@ -180,15 +181,24 @@ int lasp_init_interp(const lasp_interp_desc* d, const float* coeff, lasp_interp*
         delete h;
         return rc;
     }
+    M.ldc = (M.n_model + 15) & ~15;
     rc = cuda_err(cudaMemcpy(h->C, coeff, nC * sizeof(float), cudaMemcpyHostToDevice));
+    if (!rc) rc = cuda_err(cudaMalloc(&h->Cp, (size_t)d->K * M.ldc * sizeof(float)));
+    if (!rc) rc = cuda_err(cudaMemset(h->Cp, 0, (size_t)d->K * M.ldc * sizeof(float)));
+    if (!rc)
+        rc = cuda_err(cudaMemcpy2D(h->Cp, (size_t)M.ldc * sizeof(float), coeff,
+                                   (size_t)M.n_model * sizeof(float), (size_t)M.n_model * sizeof(float),
+                                   (size_t)d->K, cudaMemcpyHostToDevice));
     if (!rc) rc = tc_build_images(h->tc, h->C, d->K, M.n_model);
     if (rc) {
         tc_free_images(h->tc);
         cudaFree(h->C);
+        cudaFree(h->Cp);
         delete h;
         return rc;
     }
     M.C = h->C;
+    M.Cp = h->Cp;
     *out = h;
     return LASP_OK;
 }
@@ -197,6 +207,7 @@ void lasp_free_interp(lasp_interp h) {
     if (!h) return;
     tc_free_images(h->tc);
     cudaFree(h->C);
+    cudaFree(h->Cp);
     delete h;
 }
 

@@ -20,6 +20,8 @@ constexpr int TAPS_MAX = 2 * HMAX + 1;
 // Interpolator constants passed by value to every kernel.
 struct ModelDev {
     const float* C;          // K x n_model, row-major, FP32
+    const float* Cp;         // K x ldc, rows zero-padded to a multiple of 16 floats
+    int ldc;
     int K, n_pix, pad, n_model;
     float kms_px;            // c * dln: km/s per pixel
     float blo[3], bscale[3]; // u = (v - blo) * bscale - 1

@@ -9,11 +9,22 @@
 // everything stays in shared memory and registers.  A finished spectrum frees
 // its CTA slot at once, which the hardware refills with the next spectrum, so
 // spectra that converge early cost no idle steps.
+//
+// Work layout: thread t owns 16 consecutive pixels (and 16 consecutive model
+// pixels).  Arrays read across threads live in shared memory in skewed rows
+// (element i at i + i/16), so the stride-16 accesses of a warp hit 32 distinct
+// banks.  Correlations run over blocks of 8 taps against a 23-value register
+// window (128 FMAs per 31 shared loads).  The adjoint of the kernel
+// parameters goes through the per-tap sums a_s = sum_j delta_j F'_{j+H-s}.
 #pragma once
 
 #include "lasp_common.cuh"
 
 namespace lasp {
+
+constexpr int PPT = 16;     // pixels per thread
+constexpr int TB = 8;       // taps per block
+constexpr int TAPBUF = 128; // tap buffer (>= 2 HMAX + 2 TB + 1)
 
 struct FitParams {
     ModelDev M;
@@ -31,24 +42,30 @@ struct FitParams {
     float* weight;    // N or nullptr
 };
 
-// Shared-memory plan of the fit kernel (floats), in order.
+__host__ __device__ constexpr int skew(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int skew_size(int n) { return ((skew(n) + 4) + 3) & ~3; }
+
+// Shared-memory plan (floats).  Fp holds model pixels m in [-16, n_model+16)
+// at skew(m + 16); Db holds delta_j for j in [-(2H+8), p + 2H + 24) at
+// skew(j + 2H + 8), zero outside [0, p).
 struct FitSmem {
-    int y, W, Fp, Db, g, gmu, gsg, phi, dphi, red, out, ring, total;
+    int y, W, Fp, Db, g, gmu, gsg, phi, dphi, red, out, ring, total, dofs;
     __host__ __device__ FitSmem(int p, int H, int n_model, int NT, int D) {
-        int NB = D + 1, NV = NB * (NB + 1) / 2 + NB;
-        int nv_max = NV > (KMAX + 2) ? NV : (KMAX + 2);
+        const int NB = D + 1, NV = NB * (NB + 1) / 2 + NB;
+        const int nv_max = NV > (KMAX + 2) ? NV : (KMAX + 2);
+        dofs = 2 * H + 8;
         int o = 0;
-        y = o;    o += (p + 3) & ~3;
-        W = o;    o += (p + 3) & ~3;
-        Fp = o;   o += (n_model + 3) & ~3;
-        Db = o;   o += (p + 4 * H + 3) & ~3;
-        g = o;    o += 96;
-        gmu = o;  o += 96;
-        gsg = o;  o += 96;
+        y = o;    o += skew_size(p);
+        W = o;    o += skew_size(p);
+        Fp = o;   o += skew_size(n_model + 32);
+        Db = o;   o += skew_size(p + 4 * H + 40);
+        g = o;    o += TAPBUF;
+        gmu = o;  o += TAPBUF;
+        gsg = o;  o += TAPBUF;
         phi = o;  o += KMAX;
         dphi = o; o += 3 * KMAX;
         red = o;  o += (NT / 32) * nv_max;
-        out = o;  o += 2 * nv_max + 16;   // FP32 sums, or FP64 sums (2 floats each)
+        out = o;  o += 2 * nv_max + 16;
         ring = o; o += WINMAX;
         total = o;
     }
@@ -56,25 +73,123 @@ struct FitSmem {
 
 __host__ inline size_t fit_smem_bytes(int p, int H, int n_model, int NT, int D) {
     FitSmem s(p, H, n_model, NT, D);
-    size_t sortb = (size_t)next_pow2(p);
-    // the sort buffer of the preprocessing aliases Fp and Db (>= next_pow2(p))
-    size_t need = (size_t)s.total;
-    size_t sort_end = (size_t)s.Fp + sortb;
-    return 4 * (need > sort_end ? need : sort_end);
+    size_t sort_end = (size_t)s.Fp + next_pow2(p);
+    return 4 * ((size_t)s.total > sort_end ? (size_t)s.total : sort_end);
+}
+
+// Reduce NV per-thread values over the CTA; the sums end in out[0..NV) and
+// are visible to warp 0 only (after __syncwarp), with one CTA barrier.
+template <int NV, int NT>
+__device__ __forceinline__ void reduce_to_warp0(float (&v)[NV], float* red, float* out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        float s = v[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) red[warp * NV + i] = s;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        for (int i = lane; i < NV; i += 32) {
+            float s = 0.0f;
+#pragma unroll
+            for (int w = 0; w < NT / 32; ++w) s += red[w * NV + i];
+            out[i] = s;
+        }
+        __syncwarp();
+    }
+}
+
+template <int NV, int NT>
+__device__ __forceinline__ void reduce_to_warp0_f64(float (&v)[NV], float* red, double* outd) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        float s = v[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) red[warp * NV + i] = s;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        for (int i = lane; i < NV; i += 32) {
+            double s = 0.0;
+#pragma unroll
+            for (int w = 0; w < NT / 32; ++w) s += (double)red[w * NV + i];
+            outd[i] = s;
+        }
+        __syncwarp();
+    }
+}
+
+// Cholesky solve with reciprocal pivots (one thread).  Returns false when a
+// pivot is not positive.
+template <int D, typename T>
+__device__ __forceinline__ bool chol_solve_rcp(const T* packed, const T* rhs, T* b) {
+    constexpr int n = D + 1;
+    T L[n][n], id[n], t[n];
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            T s = packed[Gram<D>::idx(j, i)];
+#pragma unroll
+            for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
+            if (i == j) {
+                if (!(s > T(0))) return false;
+                id[i] = T(1) / sqrt(s);
+                L[i][i] = sqrt(s);
+            } else {
+                L[i][j] = s * id[j];
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        T s = rhs[i];
+#pragma unroll
+        for (int k = 0; k < i; ++k) s -= L[i][k] * t[k];
+        t[i] = s * id[i];
+    }
+#pragma unroll
+    for (int i = n - 1; i >= 0; --i) {
+        T s = t[i];
+#pragma unroll
+        for (int k = i + 1; k < n; ++k) s -= L[k][i] * b[k];
+        b[i] = s * id[i];
+    }
+    return true;
+}
+
+// Basis, its derivatives and the kernel taps for normalised x (warp 0).
+// Taps are written for s + H in [0, TAPBUF), zero outside |s| <= h.
+__device__ __forceinline__ int warp_prepare_step(const ModelDev& M, const float* x, float* phi,
+                                                 float* dphi, float* g, float* gmu, float* gsg) {
+    const int lane = threadIdx.x & 31;
+    float th[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) th[k] = phys_of(M, k, x[k]);
+    if (lane < M.K) basis_term(M, lane, th, phi, dphi);
+    for (int i = 2 * M.pad + 1 + lane; i < TAPBUF; i += 32) {
+        g[i] = 0.0f;
+        gmu[i] = 0.0f;
+        gsg[i] = 0.0f;
+    }
+    return kernel_taps_warp(th[3] / M.kms_px, th[4] / M.kms_px, M.pad, g, gmu, gsg);
 }
 
 template <int NT, int D>
-__global__ void __launch_bounds__(NT) fit_kernel(const FitParams P) {
+__global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) fit_kernel(const FitParams P) {
     using Gm = Gram<D>;
     constexpr int NB = D + 1;
     constexpr int NV = Gm::NV;
-    constexpr int PPT = 16;                       // pixels per thread supported
     extern __shared__ __align__(16) float sm[];
     const ModelDev& M = P.M;
     const int p = M.n_pix, H = M.pad, nm = M.n_model, K = M.K;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int i = blockIdx.x;
-    FitSmem L(p, H, nm, NT, D);
+    const FitSmem L(p, H, nm, NT, D);
     float* y = sm + L.y;
     float* W = sm + L.W;
     float* Fp = sm + L.Fp;
@@ -88,31 +203,57 @@ __global__ void __launch_bounds__(NT) fit_kernel(const FitParams P) {
     float* out = sm + L.out;
     double* outd = reinterpret_cast<double*>(sm + ((L.out + 1) & ~1));
     float* ring = sm + L.ring;
-    __shared__ float s_x[5], s_b[NB], s_scal[8];
+    __shared__ float s_x[5], s_b[NB];
     __shared__ int s_h, s_stop;
+    __shared__ float s_w;
 
-    const size_t row = (size_t)i * p;
-    float w;
-    const int n_obj = prep_spectrum<NT>(P.flux + row, P.ivar + row, P.good + row, p,
-                                        P.O.edge_px, P.O.quantile, y, W, Fp, red, &w);
-    // delta buffer: zero halo; interior rewritten every step
-    for (int j = tid; j < p + 4 * H; j += NT) Db[j] = 0.0f;
+    // ---- preprocessing (section 3.3 step 2): y, W into skewed rows
+    {
+        const size_t row = (size_t)i * p;
+        float w;
+        const int n_obj = prep_spectrum<NT>(P.flux + row, P.ivar + row, P.good + row, p,
+                                            P.O.edge_px, P.O.quantile, y, W, Fp, red, &w);
+        __syncthreads();
+        // re-layout y and W (written linearly by prep) into skewed rows in place:
+        // copy out to registers, barrier, copy back skewed.
+        float ty[PPT], tw[PPT];
+#pragma unroll
+        for (int r = 0; r < PPT; ++r) {
+            const int j = tid * PPT + r;
+            ty[r] = j < p ? y[j] : 0.0f;
+            tw[r] = j < p ? W[j] : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < PPT; ++r) {
+            const int j = tid * PPT + r;
+            if (j < p) {
+                y[skew(j)] = ty[r];
+                W[skew(j)] = tw[r];
+            }
+        }
+        if (tid == 0) {
+            s_w = w;
+            s_stop = (n_obj < NB + 5 || !(w > 0.0f) || !isfinite(w)) ? 1 : 0;
+        }
+    }
+    // zero the padded F' and delta buffers (their pads stay zero)
+    for (int q = tid; q < skew_size(nm + 32); q += NT) Fp[q] = 0.0f;
+    for (int q = tid; q < skew_size(p + 4 * H + 40); q += NT) Db[q] = 0.0f;
 
-    // Adam state lives in thread 0's registers.
+    // Adam state lives in registers of thread 0.
     float x[5], m[5], v[5], prev = 0.0f;
     int rise = 0;
     if (tid == 0) {
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
-            float xx = 2.0f * (P.theta0[5 * i + k] - M.plo[k]) / (2.0f * M.phalf[k]) - 1.0f;
+            float xx = (P.theta0[5 * i + k] - M.plo[k]) / M.phalf[k] - 1.0f;
             xx = fminf(1.0f, fmaxf(-1.0f, xx));
             x[k] = xx;
             s_x[k] = xx;
             m[k] = 0.0f;
             v[k] = 0.0f;
         }
-        s_stop = 0;
-        if (n_obj < NB + 5 || !(w > 0.0f) || !isfinite(w)) s_stop = (int)0x40;  // NODATA
     }
     __syncthreads();
     if (s_stop) {
@@ -120,58 +261,88 @@ __global__ void __launch_bounds__(NT) fit_kernel(const FitParams P) {
             for (int k = 0; k < 5; ++k) P.theta[5 * i + k] = phys_of(M, k, s_x[k]);
             P.loss[i] = NAN;
             P.steps[i] = 0;
-            P.status[i] = 0x40u;
-            if (P.weight) P.weight[i] = w;
+            P.status[i] = 64u;
+            if (P.weight) P.weight[i] = s_w;
         }
         if (P.cont && tid < NB) P.cont[(size_t)i * NB + tid] = NAN;
         return;
     }
+    if (warp == 0) {
+        int h = warp_prepare_step(M, s_x, phi, dphi, g, gmu, gsg);
+        if (lane == 0) s_h = h;
+    }
+    __syncthreads();
 
     const float inv_p = 1.0f / (float)p;
-    float fpp[PPT];
+    const int j0 = tid * PPT;              // first owned pixel / model pixel
+    const bool own_pix = j0 < p;
+    const bool own_mod = j0 < nm;
+    const float xstep = 2.0f / (float)p;
 
     for (int t = 0;; ++t) {
-        // ---- a1/a2: parameters, basis, kernel taps (warp 0)
-        if (warp == 0) {
-            float th[5];
-#pragma unroll
-            for (int k = 0; k < 5; ++k) th[k] = phys_of(M, k, s_x[k]);
-            if (lane < K) basis_term(M, lane, th, phi, dphi);
-            float mu = th[3] / M.kms_px, sig = th[4] / M.kms_px;
-            int h = kernel_taps_warp(mu, sig, H, g, gmu, gsg);
-            if (lane == 0) s_h = h;
-        }
-        __syncthreads();
         const int h = s_h;
+        const int nblk = (2 * h + 1 + TB - 1) / TB;
 
-        // ---- a3: F' = phi C  (Eq. 1), table from L2
-        for (int mm = tid; mm < nm; mm += NT) {
-            float acc = 0.0f;
+        // ---- a3: F' = phi C (Eq. 1), 16 model pixels per thread, table from L2
+        if (own_mod) {
+            float acc[PPT];
 #pragma unroll
-            for (int k = 0; k < KMAX; ++k)
-                if (k < K) acc = fmaf(phi[k], __ldg(M.C + (size_t)k * nm + mm), acc);
-            Fp[mm] = acc;
+            for (int r = 0; r < PPT; ++r) acc[r] = 0.0f;
+            const float4* crow = reinterpret_cast<const float4*>(M.Cp + j0);
+#pragma unroll 2
+            for (int k = 0; k < K; ++k) {
+                const float pk = phi[k];
+                const float4* c4 = crow + (size_t)k * (M.ldc / 4);
+#pragma unroll
+                for (int q = 0; q < PPT / 4; ++q) {
+                    const float4 c = __ldg(c4 + q);
+                    acc[4 * q + 0] = fmaf(pk, c.x, acc[4 * q + 0]);
+                    acc[4 * q + 1] = fmaf(pk, c.y, acc[4 * q + 1]);
+                    acc[4 * q + 2] = fmaf(pk, c.z, acc[4 * q + 2]);
+                    acc[4 * q + 3] = fmaf(pk, c.w, acc[4 * q + 3]);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < PPT; ++r)
+                if (j0 + r < nm) Fp[skew(j0 + r + 16)] = acc[r];
         }
         __syncthreads();
 
-        // ---- a4 + a5: F'' = F' (x) G (Eq. 5); normal equations of Eq. 6
+        // ---- a4: F''_j = sum_s g_s F'_{j+H-s} (Eq. 5), 8-tap blocks
+        float fpp[PPT];
+#pragma unroll
+        for (int r = 0; r < PPT; ++r) fpp[r] = 0.0f;
+        if (own_pix) {
+            for (int bk = 0; bk < nblk; ++bk) {
+                const int s0 = -h + bk * TB;
+                float gg[TB], win[PPT + TB - 1];
+#pragma unroll
+                for (int e = 0; e < TB; ++e) gg[e] = g[s0 + e + H];
+                // win[q] = F'[j0 + H - s0 - 7 + q]
+                const int base = j0 + H - s0 - (TB - 1) + 16;
+#pragma unroll
+                for (int q = 0; q < PPT + TB - 1; ++q) win[q] = Fp[skew(base + q)];
+#pragma unroll
+                for (int e = 0; e < TB; ++e)
+#pragma unroll
+                    for (int r = 0; r < PPT; ++r) fpp[r] = fmaf(gg[e], win[r - e + TB - 1], fpp[r]);
+            }
+        }
+
+        // ---- a5: normal equations of Eq. 6
         float gacc[NV];
 #pragma unroll
         for (int q = 0; q < NV; ++q) gacc[q] = 0.0f;
+        if (own_pix) {
 #pragma unroll
-        for (int r = 0; r < PPT; ++r) {
-            const int j = tid + r * NT;
-            fpp[r] = 0.0f;
-            if (j < p) {
-                const float* src = Fp + j + H;
-                float f = 0.0f;
-                for (int s = -h; s <= h; ++s) f = fmaf(g[s + H], src[-s], f);
-                fpp[r] = f;
-                const float Wj = W[j];
+            for (int r = 0; r < PPT; ++r) {
+                const int j = j0 + r;
+                const float Wj = j < p ? W[skew(j)] : 0.0f;
                 if (Wj != 0.0f) {
                     float Pl[NB];
-                    legendre<D>(legendre_node(j, p), Pl);
-                    const float vv = Wj * f * f, uu = Wj * f * y[j];
+                    legendre<D>(fmaf((float)j, xstep, -1.0f), Pl);
+                    const float f = fpp[r];
+                    const float vv = Wj * f * f, uu = Wj * f * y[skew(j)];
 #pragma unroll
                     for (int a = 0; a < NB; ++a) {
                         const float va = vv * Pl[a];
@@ -182,140 +353,199 @@ __global__ void __launch_bounds__(NT) fit_kernel(const FitParams P) {
                 }
             }
         }
-        bool solved;
         if (P.O.fp64_ne) {
-            block_sum_f64<NV, NT>(gacc, red, outd);
+            reduce_to_warp0_f64<NV, NT>(gacc, red, outd);
             if (tid == 0) {
                 double bd[NB];
-                solved = chol_solve_packed<D, double>(outd, outd + Gm::NG, bd);
-                for (int a = 0; a < NB; ++a) s_b[a] = (float)bd[a];
-                s_scal[0] = solved ? 1.0f : 0.0f;
+                const bool ok = chol_solve_rcp<D, double>(outd, outd + Gm::NG, bd);
+#pragma unroll
+                for (int a = 0; a < NB; ++a) s_b[a] = ok ? (float)bd[a] : NAN;
             }
         } else {
-            block_sum<NV, NT>(gacc, red, out);
+            reduce_to_warp0<NV, NT>(gacc, red, out);
             if (tid == 0) {
                 float bf[NB];
-                solved = chol_solve_packed<D, float>(out, out + Gm::NG, bf);
-                for (int a = 0; a < NB; ++a) s_b[a] = bf[a];
-                s_scal[0] = solved ? 1.0f : 0.0f;
+                const bool ok = chol_solve_rcp<D, float>(out, out + Gm::NG, bf);
+#pragma unroll
+                for (int a = 0; a < NB; ++a) s_b[a] = ok ? bf[a] : NAN;
             }
         }
         __syncthreads();
 
-        // ---- a6: residual (Eq. 7), loss (Eq. 9); delta = W eps c for the adjoint
+        // ---- a6: residual (Eq. 7), loss (Eq. 9); delta = W eps c (unscaled)
         float racc[2] = {0.0f, 0.0f};
-        float bl[NB];
+        {
+            float bl[NB];
 #pragma unroll
-        for (int a = 0; a < NB; ++a) bl[a] = s_b[a];
+            for (int a = 0; a < NB; ++a) bl[a] = s_b[a];
+            const bool solved = isfinite(bl[0]);
+            if (own_pix && solved) {
 #pragma unroll
-        for (int r = 0; r < PPT; ++r) {
-            const int j = tid + r * NT;
-            if (j < p) {
-                const float Wj = W[j];
-                float dlt = 0.0f;
-                if (Wj != 0.0f) {
-                    float Pl[NB];
-                    legendre<D>(legendre_node(j, p), Pl);
-                    float c = 0.0f;
+                for (int r = 0; r < PPT; ++r) {
+                    const int j = j0 + r;
+                    float dlt = 0.0f;
+                    const float Wj = j < p ? W[skew(j)] : 0.0f;
+                    if (Wj != 0.0f) {
+                        float Pl[NB];
+                        legendre<D>(fmaf((float)j, xstep, -1.0f), Pl);
+                        float c = 0.0f;
 #pragma unroll
-                    for (int a = 0; a < NB; ++a) c = fmaf(bl[a], Pl[a], c);
-                    const float e = y[j] - c * fpp[r];
-                    racc[0] = fmaf(Wj * e, e, racc[0]);
-                    if (c <= 0.0f) racc[1] = 1.0f;
-                    dlt = Wj * e * c;
+                        for (int a = 0; a < NB; ++a) c = fmaf(bl[a], Pl[a], c);
+                        const float e = y[skew(j)] - c * fpp[r];
+                        racc[0] = fmaf(Wj * e, e, racc[0]);
+                        if (c <= 0.0f) racc[1] = 1.0f;
+                        dlt = Wj * e * c;
+                    }
+                    fpp[r] = dlt;     // the register now holds delta_j (unscaled)
+                    if (j < p) Db[skew(j + L.dofs)] = dlt;
                 }
-                fpp[r] = dlt;                  // register now holds delta_j (unscaled)
-                Db[j + 2 * H] = dlt;
             }
+            if (!solved) racc[0] = NAN;
         }
-        block_sum<2, NT>(racc, red, out);
-        const float S = out[0];
-        const bool nonpos = out[1] > 0.0f;
-        const float l = sqrtf(S * inv_p);
-        // dl/dF''_j = -W eps c / (p l) with b held at its optimum (envelope theorem)
-        const float kappa = l > 0.0f ? -1.0f / ((float)p * l) : 0.0f;
+        reduce_to_warp0<2, NT>(racc, red, out);
+        __shared__ float s_l, s_nonpos;
+        if (tid == 0) {
+            s_l = sqrtf(out[0] * inv_p);
+            s_nonpos = out[1];
+        }
+        __syncthreads();
+        const float l = s_l;
 
-        // ---- a7: adjoint through broadening and the basis contraction
+        // ---- a7: adjoint.  (i) a_s = sum_j delta_j F'_{j+H-s}; d l/d mu = k sum_s gmu_s a_s
         float bacc[2 + KMAX];
 #pragma unroll
         for (int q = 0; q < 2 + KMAX; ++q) bacc[q] = 0.0f;
+        if (own_pix) {
+            for (int bk = 0; bk < nblk; ++bk) {
+                const int s0 = -h + bk * TB;
+                float win[PPT + TB - 1];
+                const int base = j0 + H - s0 - (TB - 1) + 16;
 #pragma unroll
-        for (int r = 0; r < PPT; ++r) {
-            const int j = tid + r * NT;
-            if (j < p && fpp[r] != 0.0f) {
-                const float* src = Fp + j + H;
-                float am = 0.0f, as = 0.0f;
-                for (int s = -h; s <= h; ++s) {
-                    const float fv = src[-s];
-                    am = fmaf(gmu[s + H], fv, am);
-                    as = fmaf(gsg[s + H], fv, as);
+                for (int q = 0; q < PPT + TB - 1; ++q) win[q] = Fp[skew(base + q)];
+                float a[TB];
+#pragma unroll
+                for (int e = 0; e < TB; ++e) a[e] = 0.0f;
+#pragma unroll
+                for (int r = 0; r < PPT; ++r)
+#pragma unroll
+                    for (int e = 0; e < TB; ++e) a[e] = fmaf(fpp[r], win[r - e + TB - 1], a[e]);
+#pragma unroll
+                for (int e = 0; e < TB; ++e) {
+                    bacc[0] = fmaf(gmu[s0 + e + H], a[e], bacc[0]);
+                    bacc[1] = fmaf(gsg[s0 + e + H], a[e], bacc[1]);
                 }
-                bacc[0] = fmaf(fpp[r], am, bacc[0]);
-                bacc[1] = fmaf(fpp[r], as, bacc[1]);
             }
         }
-        for (int mm = tid; mm < nm; mm += NT) {
-            const float* src = Db + mm + H;
-            float d = 0.0f;
-            for (int s = -h; s <= h; ++s) d = fmaf(g[s + H], src[s], d);
+        // (ii) dF'_m = sum_s g_s delta_{m-H+s}; d l/d phi_k = k sum_m dF'_m C_km
+        if (own_mod) {
+            float dfp[PPT];
 #pragma unroll
-            for (int k = 0; k < KMAX; ++k)
-                if (k < K) bacc[2 + k] = fmaf(d, __ldg(M.C + (size_t)k * nm + mm), bacc[2 + k]);
+            for (int r = 0; r < PPT; ++r) dfp[r] = 0.0f;
+            for (int bk = 0; bk < nblk; ++bk) {
+                const int s0 = -h + bk * TB;
+                float gg[TB], win[PPT + TB - 1];
+#pragma unroll
+                for (int e = 0; e < TB; ++e) gg[e] = g[s0 + e + H];
+                // win[q] = delta[j0 - H + s0 + q]
+                const int base = j0 - H + s0 + L.dofs;
+#pragma unroll
+                for (int q = 0; q < PPT + TB - 1; ++q) win[q] = Db[skew(base + q)];
+#pragma unroll
+                for (int e = 0; e < TB; ++e)
+#pragma unroll
+                    for (int r = 0; r < PPT; ++r) dfp[r] = fmaf(gg[e], win[r + e], dfp[r]);
+            }
+            const float4* crow = reinterpret_cast<const float4*>(M.Cp + j0);
+#pragma unroll
+            for (int k = 0; k < KMAX; ++k) {
+                if (k < K) {
+                    const float4* c4 = crow + (size_t)k * (M.ldc / 4);
+                    float a = 0.0f;
+#pragma unroll
+                    for (int q = 0; q < PPT / 4; ++q) {
+                        const float4 c = __ldg(c4 + q);
+                        a = fmaf(dfp[4 * q + 0], c.x, a);
+                        a = fmaf(dfp[4 * q + 1], c.y, a);
+                        a = fmaf(dfp[4 * q + 2], c.z, a);
+                        a = fmaf(dfp[4 * q + 3], c.w, a);
+                    }
+                    bacc[2 + k] = a;
+                }
+            }
         }
-        block_sum<2 + KMAX, NT>(bacc, red, out);
+        reduce_to_warp0<2 + KMAX, NT>(bacc, red, out);
 
-        // ---- a8: chain rule to x, stop rules, Adam (thread 0)
-        if (tid == 0) {
-            float gx[5];
-            float gth[3] = {0.0f, 0.0f, 0.0f};
-            for (int k = 0; k < K; ++k) {
-                gth[0] = fmaf(out[2 + k], dphi[3 * k + 0], gth[0]);
-                gth[1] = fmaf(out[2 + k], dphi[3 * k + 1], gth[1]);
-                gth[2] = fmaf(out[2 + k], dphi[3 * k + 2], gth[2]);
+        // ---- a8: chain rule to x, stop rules, Adam; next step's basis + taps (warp 0)
+        if (warp == 0) {
+            // dl/dF''_j = -W eps c / (p l) with b held at its optimum (envelope theorem)
+            const float kappa = l > 0.0f ? -1.0f / ((float)p * l) : 0.0f;
+            float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f;
+            if (lane < K) {
+                const float gp = out[2 + lane];
+                c0 = gp * dphi[3 * lane + 0];
+                c1 = gp * dphi[3 * lane + 1];
+                c2 = gp * dphi[3 * lane + 2];
             }
-            gx[0] = kappa * gth[0] * M.phalf[0];
-            gx[1] = kappa * gth[1] * M.phalf[1];
-            gx[2] = kappa * gth[2] * M.phalf[2];
-            gx[3] = kappa * out[0] / M.kms_px * M.phalf[3];
-            gx[4] = kappa * out[1] / M.kms_px * M.phalf[4];
-            uint32_t stop = 0;
-            if (!solved) stop = 32u;
-            else {
-                bool fin = isfinite(l);
 #pragma unroll
-                for (int k = 0; k < 5; ++k) fin = fin && isfinite(gx[k]);
-                if (!fin) stop = 16u;
+            for (int o = 16; o > 0; o >>= 1) {
+                c0 += __shfl_xor_sync(0xffffffffu, c0, o);
+                c1 += __shfl_xor_sync(0xffffffffu, c1, o);
+                c2 += __shfl_xor_sync(0xffffffffu, c2, o);
             }
-            if (!stop) {
-                const int Wn = P.O.window;
-                if (t >= Wn && fabsf(l - ring[t % Wn]) < P.O.tol) stop = 1u;
-                rise = (t >= 1 && l > prev) ? rise + 1 : 0;
-                if (!stop && rise >= Wn) stop = 2u;
-                if (!stop && t >= P.O.max_steps) stop = 4u;
-                ring[t % Wn] = l;
-                prev = l;
-            }
-            if (stop) {
-                if (stop <= 4u && nonpos) stop |= 8u;
-                for (int k = 0; k < 5; ++k) P.theta[5 * i + k] = phys_of(M, k, x[k]);
-                P.loss[i] = l;
-                P.steps[i] = t;
-                P.status[i] = stop;
-                if (P.weight) P.weight[i] = w;
-                s_stop = 1;
-            } else {
-                const float tt = (float)(t + 1);
-                const float bc1 = 1.0f - powf(P.O.beta1, tt);
-                const float bc2 = 1.0f - powf(P.O.beta2, tt);
-                const float step = P.O.lr / bc1, rbc2 = rsqrtf(bc2);
+            int stop = 0;
+            if (lane == 0) {
+                float gx[5];
+                gx[0] = kappa * c0 * M.phalf[0];
+                gx[1] = kappa * c1 * M.phalf[1];
+                gx[2] = kappa * c2 * M.phalf[2];
+                gx[3] = kappa * out[0] / M.kms_px * M.phalf[3];
+                gx[4] = kappa * out[1] / M.kms_px * M.phalf[4];
+                uint32_t st = 0;
+                if (!isfinite(s_b[0])) st = 32u;
+                else {
+                    bool fin = isfinite(l);
 #pragma unroll
-                for (int k = 0; k < 5; ++k) {
-                    m[k] = P.O.beta1 * m[k] + (1.0f - P.O.beta1) * gx[k];
-                    v[k] = P.O.beta2 * v[k] + (1.0f - P.O.beta2) * gx[k] * gx[k];
-                    const float denom = sqrtf(v[k]) * rbc2 + P.O.eps;
-                    x[k] = fminf(1.0f, fmaxf(-1.0f, x[k] - step * m[k] / denom));
-                    s_x[k] = x[k];
+                    for (int k = 0; k < 5; ++k) fin = fin && isfinite(gx[k]);
+                    if (!fin) st = 16u;
                 }
+                if (!st) {
+                    const int Wn = P.O.window;
+                    if (t >= Wn && fabsf(l - ring[t % Wn]) < P.O.tol) st = 1u;
+                    rise = (t >= 1 && l > prev) ? rise + 1 : 0;
+                    if (!st && rise >= Wn) st = 2u;
+                    if (!st && t >= P.O.max_steps) st = 4u;
+                    ring[t % Wn] = l;
+                    prev = l;
+                }
+                if (st) {
+                    if (st <= 4u && s_nonpos > 0.0f) st |= 8u;
+                    for (int k = 0; k < 5; ++k) P.theta[5 * i + k] = phys_of(M, k, x[k]);
+                    P.loss[i] = l;
+                    P.steps[i] = t;
+                    P.status[i] = st;
+                    if (P.weight) P.weight[i] = s_w;
+                    stop = 1;
+                } else {
+                    const float tt = (float)(t + 1);
+                    const float bc1 = 1.0f - powf(P.O.beta1, tt);
+                    const float bc2 = 1.0f - powf(P.O.beta2, tt);
+                    const float step = P.O.lr / bc1, rbc2 = rsqrtf(bc2);
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) {
+                        m[k] = P.O.beta1 * m[k] + (1.0f - P.O.beta1) * gx[k];
+                        v[k] = P.O.beta2 * v[k] + (1.0f - P.O.beta2) * gx[k] * gx[k];
+                        const float denom = sqrtf(v[k]) * rbc2 + P.O.eps;
+                        x[k] = fminf(1.0f, fmaxf(-1.0f, x[k] - step * m[k] / denom));
+                        s_x[k] = x[k];
+                    }
+                }
+                s_stop = stop;
+            }
+            stop = __shfl_sync(0xffffffffu, stop, 0);
+            __syncwarp();
+            if (!stop) {
+                int hn = warp_prepare_step(M, s_x, phi, dphi, g, gmu, gsg);
+                if (lane == 0) s_h = hn;
             }
         }
         __syncthreads();

@@ -1,0 +1,246 @@
+// Tensor-core (tcgen05) interpolator contraction, Eq. 1: Fp = phi(theta) C.
+//
+// One CTA (4 warps) takes 128 spectra (the MMA N dimension) and loops over
+// 128-pixel tiles of the model grid (the MMA M dimension), K = 32 basis
+// terms.  The basis rows phi are written once into shared memory in the
+// swizzled K-major layout; each table tile arrives by one bulk copy; one
+// thread issues the MMAs into a 128 x 128 FP32 accumulator in TMEM; each warp
+// then reads its 32 TMEM lanes (pixels) and writes 128-byte coalesced runs of
+// F' per spectrum.
+#include <cuda_bf16.h>
+
+#include "lasp_tc.cuh"
+#include "lasp_tc_ptx.cuh"
+
+namespace lasp {
+
+int cuda_rc(cudaError_t e);
+
+namespace {
+
+constexpr uint32_t kWaitLimit = 1u << 22;
+
+__global__ void build_images_kernel(const float* __restrict__ C, int K, int n_model, int n_tiles,
+                                    uint8_t* hi, uint8_t* lo, uint8_t* bf) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int total = n_tiles * TC_TILE * 8;
+    if (idx >= total) return;
+    const int c = idx & 7, r = (idx >> 3) & (TC_TILE - 1), t = idx >> 10;
+    const int m = t * TC_TILE + r;
+    const uint32_t off = (uint32_t)t * TC_TILE_BYTES + tc::sw128_off(r, c);
+    float v[4], h[4], l[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int k = 4 * c + q;
+        v[q] = (m < n_model && k < K) ? C[(size_t)k * n_model + m] : 0.0f;
+        h[q] = tc::to_tf32(v[q]);
+        l[q] = tc::to_tf32(v[q] - h[q]);
+    }
+    *reinterpret_cast<float4*>(hi + off) = make_float4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<float4*>(lo + off) = make_float4(l[0], l[1], l[2], l[3]);
+    // BF16: chunk c < 4 holds basis terms 8c .. 8c+7, chunks 4..7 are zero
+    __nv_bfloat16 b[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int k = 8 * c + q;
+        const float x = (c < 4 && m < n_model && k < K) ? C[(size_t)k * n_model + m] : 0.0f;
+        b[q] = __float2bfloat16_rn(x);
+    }
+    *reinterpret_cast<uint4*>(bf + off) = *reinterpret_cast<uint4*>(b);
+}
+
+// PREC: 1 TF32, 2 BF16, 3 split TF32 (hi*hi + hi*lo + lo*hi)
+template <int PREC>
+__global__ void __launch_bounds__(128) interp_tc_kernel(const ModelDev M, const float* __restrict__ theta,
+                                                        float* __restrict__ Fp, int N,
+                                                        const uint8_t* __restrict__ img_a,
+                                                        const uint8_t* __restrict__ img_a_lo,
+                                                        int n_tiles, int* err) {
+    extern __shared__ uint8_t smraw[];
+    uint8_t* base = reinterpret_cast<uint8_t*>(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+    uint8_t* Ahi = base;
+    uint8_t* Alo = base + TC_TILE_BYTES;
+    uint8_t* Bhi = base + 2 * TC_TILE_BYTES;
+    uint8_t* Blo = base + 3 * TC_TILE_BYTES;
+    __shared__ __align__(8) uint64_t bar_tma, bar_mma;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_ok;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int s0 = blockIdx.x * 128;
+
+    if (warp == 0) {
+        tc::tmem_alloc(&tmem_base, 128);
+        tc::tmem_relinquish();
+    }
+    // B operand row tid: phi of spectrum s0 + tid, zero beyond N or K
+    {
+        float phi[KMAX];
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k) phi[k] = 0.0f;
+        if (s0 + tid < N) {
+            float th[5];
+#pragma unroll
+            for (int q = 0; q < 5; ++q) th[q] = theta[5 * (size_t)(s0 + tid) + q];
+            for (int k = 0; k < M.K; ++k) basis_term(M, k, th, phi, nullptr);
+        }
+        if (PREC == 2) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                __nv_bfloat16 b[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) b[q] = __float2bfloat16_rn(c < 4 ? phi[8 * c + q] : 0.0f);
+                *reinterpret_cast<uint4*>(Bhi + tc::sw128_off(tid, c)) = *reinterpret_cast<uint4*>(b);
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                float h[4], l[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    h[q] = tc::to_tf32(phi[4 * c + q]);
+                    l[q] = tc::to_tf32(phi[4 * c + q] - h[q]);
+                }
+                *reinterpret_cast<float4*>(Bhi + tc::sw128_off(tid, c)) = make_float4(h[0], h[1], h[2], h[3]);
+                if (PREC == 3)
+                    *reinterpret_cast<float4*>(Blo + tc::sw128_off(tid, c)) = make_float4(l[0], l[1], l[2], l[3]);
+            }
+        }
+    }
+    if (tid == 0) {
+        tc::mbar_init(&bar_tma, 1);
+        tc::mbar_init(&bar_mma, 1);
+        tc::fence_mbar_init();
+        s_ok = 1;
+    }
+    tc::fence_proxy_async_smem();
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    constexpr uint32_t idesc = tc::idesc_f32acc(PREC == 2 ? 1u : 2u, 128, 128);
+    uint32_t phase = 0;
+    bool copy_pending = false;
+
+    for (int t = blockIdx.y; t < n_tiles; t += gridDim.y) {
+        if (tid == 0) {
+            const uint32_t bytes = (PREC == 3 ? 2u : 1u) * (uint32_t)TC_TILE_BYTES;
+            tc::mbar_arrive_expect_tx(&bar_tma, bytes);
+            tc::bulk_g2s(Ahi, img_a + (size_t)t * TC_TILE_BYTES, TC_TILE_BYTES, &bar_tma);
+            if (PREC == 3) tc::bulk_g2s(Alo, img_a_lo + (size_t)t * TC_TILE_BYTES, TC_TILE_BYTES, &bar_tma);
+            copy_pending = true;
+            if (!tc::mbar_wait_bounded(&bar_tma, phase, kWaitLimit)) {
+                atomicExch(err, 1);
+                s_ok = 0;
+            } else {
+                copy_pending = false;
+                tc::tc_fence_after();
+                const uint64_t ah = tc::desc_kmajor_sw128(tc::smem_u32(Ahi));
+                const uint64_t bh = tc::desc_kmajor_sw128(tc::smem_u32(Bhi));
+                // K = 32 basis terms = 128 bytes per row: 4 TF32 MMAs (K=8) or 2 BF16 MMAs (K=16)
+                constexpr int NK = PREC == 2 ? 2 : 4;
+#pragma unroll
+                for (int ks = 0; ks < NK; ++ks) {
+                    const uint64_t adv = (uint64_t)(ks * 32) >> 4;
+                    if (PREC == 2) tc::mma_bf16(tmem, ah + adv, bh + adv, idesc, ks > 0);
+                    else tc::mma_tf32(tmem, ah + adv, bh + adv, idesc, ks > 0);
+                }
+                if (PREC == 3) {
+                    const uint64_t al = tc::desc_kmajor_sw128(tc::smem_u32(Alo));
+                    const uint64_t bl = tc::desc_kmajor_sw128(tc::smem_u32(Blo));
+#pragma unroll
+                    for (int ks = 0; ks < 4; ++ks) {
+                        const uint64_t adv = (uint64_t)(ks * 32) >> 4;
+                        tc::mma_tf32(tmem, ah + adv, bl + adv, idesc, 1);
+                        tc::mma_tf32(tmem, al + adv, bh + adv, idesc, 1);
+                    }
+                }
+                tc::mma_commit(&bar_mma);
+            }
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        if (!tc::mbar_wait_bounded(&bar_mma, phase, kWaitLimit)) {
+            atomicExch(err, 1);
+            s_ok = 0;
+        }
+        tc::tc_fence_after();
+        if (s_ok) {
+            const int mpix = t * TC_TILE + warp * 32 + lane;
+#pragma unroll 1
+            for (int c = 0; c < 8; ++c) {
+                float v[16];
+                tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 16), v);
+                if (mpix < M.n_model) {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const int s = s0 + c * 16 + q;
+                        if (s < N) Fp[(size_t)s * M.n_model + mpix] = v[q];
+                    }
+                }
+            }
+        }
+        tc::tc_fence_before();
+        __syncthreads();
+        if (!s_ok) break;
+        phase ^= 1u;
+    }
+    // a copy still in flight after a timeout: wait for it (bounded) before exit
+    if (tid == 0 && copy_pending) tc::mbar_wait_bounded(&bar_tma, phase, kWaitLimit);
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 128);
+}
+
+}  // namespace
+
+int tc_build_images(TcImages& t, const float* C, int K, int n_model) {
+    t = TcImages{};
+    t.n_tiles = (n_model + TC_TILE - 1) / TC_TILE;
+    const size_t bytes = (size_t)t.n_tiles * TC_TILE_BYTES;
+    int rc = cuda_rc(cudaMalloc(&t.tf32_hi, bytes));
+    if (!rc) rc = cuda_rc(cudaMalloc(&t.tf32_lo, bytes));
+    if (!rc) rc = cuda_rc(cudaMalloc(&t.bf16, bytes));
+    if (!rc) rc = cuda_rc(cudaMalloc(&t.err, sizeof(int)));
+    if (!rc) rc = cuda_rc(cudaMemset(t.err, 0, sizeof(int)));
+    if (rc) return rc;
+    const int total = t.n_tiles * TC_TILE * 8;
+    build_images_kernel<<<(total + 255) / 256, 256>>>(C, K, n_model, t.n_tiles, (uint8_t*)t.tf32_hi,
+                                                       (uint8_t*)t.tf32_lo, (uint8_t*)t.bf16);
+    rc = cuda_rc(cudaGetLastError());
+    if (!rc) rc = cuda_rc(cudaDeviceSynchronize());
+    return rc;
+}
+
+void tc_free_images(TcImages& t) {
+    if (t.tf32_hi) cudaFree(t.tf32_hi);
+    if (t.tf32_lo) cudaFree(t.tf32_lo);
+    if (t.bf16) cudaFree(t.bf16);
+    if (t.err) cudaFree(t.err);
+    t = TcImages{};
+}
+
+int lasp_tc_interp_eval(const ModelDev& M, const TcImages& t, int N, const float* theta, float* Fp,
+                        int precision, cudaStream_t st, int* launches) {
+    if (!t.tf32_hi) return LASP_EINVAL;
+    const size_t smem = 4 * TC_TILE_BYTES + 1024;
+    dim3 grid((N + 127) / 128, t.n_tiles < 65535 ? t.n_tiles : 65535);
+    int rc = LASP_OK;
+    auto go = [&](auto kern, const void* a, const void* alo) {
+        int e = cuda_rc(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (e) return e;
+        kern<<<grid, 128, smem, st>>>(M, theta, Fp, N, (const uint8_t*)a, (const uint8_t*)alo, t.n_tiles, t.err);
+        return cuda_rc(cudaGetLastError());
+    };
+    if (precision == LASP_PREC_TF32) rc = go(interp_tc_kernel<1>, t.tf32_hi, nullptr);
+    else if (precision == LASP_PREC_BF16) rc = go(interp_tc_kernel<2>, t.bf16, nullptr);
+    else if (precision == LASP_PREC_TF32X3) rc = go(interp_tc_kernel<3>, t.tf32_hi, t.tf32_lo);
+    else return LASP_EINVAL;
+    if (!rc) *launches = 1;
+    return rc;
+}
+
+int lasp_tc_fit_batch(const ModelDev&, const TcImages&, const lasp_batch*, const lasp_fit_opts*,
+                      lasp_result*, void*, int*) {
+    return LASP_EINVAL;
+}
+
+}  // namespace lasp

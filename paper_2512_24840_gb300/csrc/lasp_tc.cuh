@@ -1,4 +1,10 @@
-// Tensor-core (tcgen05) forms of the interpolator contraction -- sm_103a.
+// Tensor-core (tcgen05) forms of the interpolator contraction (Eq. 1), sm_103a.
+//
+// The table is kept as per-tile images ready for the MMA: tile t holds model
+// pixels 128 t .. 128 t + 127 as 128 rows of 32 basis terms, K-major with the
+// 128-byte swizzle, so one 1D bulk copy brings a tile into shared memory in
+// MMA layout.  TF32 is stored as a hi/lo split (hi = tf32(C), lo =
+// tf32(C - hi)); BF16 occupies the first 64 bytes of each 128-byte row.
 #pragma once
 
 #include "lasp.h"
@@ -6,34 +12,24 @@
 
 namespace lasp {
 
+constexpr int TC_TILE = 128;            // model pixels per tile (MMA M)
+constexpr int TC_TILE_BYTES = 128 * 128; // 16 KB per image tile
+
 struct TcImages {
-    void* tf32_hi = nullptr;   // per 128-pixel tile: 128 rows x 32 k, TF32, 128B-swizzled
+    void* tf32_hi = nullptr;
     void* tf32_lo = nullptr;
     void* bf16 = nullptr;
     int n_tiles = 0;
+    int* err = nullptr;                 // device flag: bounded wait timed out
 };
 
-inline int tc_build_images(TcImages& t, const float* C, int K, int n_model) {
-    (void)C; (void)K; (void)n_model;
-    t = TcImages{};
-    return LASP_OK;
-}
+int tc_build_images(TcImages& t, const float* C, int K, int n_model);
+void tc_free_images(TcImages& t);
 
-inline void tc_free_images(TcImages& t) {
-    if (t.tf32_hi) cudaFree(t.tf32_hi);
-    if (t.tf32_lo) cudaFree(t.tf32_lo);
-    if (t.bf16) cudaFree(t.bf16);
-    t = TcImages{};
-}
+int lasp_tc_interp_eval(const ModelDev& M, const TcImages& t, int N, const float* theta, float* Fp,
+                        int precision, cudaStream_t st, int* launches);
 
-inline int lasp_tc_fit_batch(const ModelDev&, const TcImages&, const lasp_batch*, const lasp_fit_opts*,
-                             lasp_result*, void*, int*) {
-    return LASP_EINVAL;
-}
-
-inline int lasp_tc_interp_eval(const ModelDev&, const TcImages&, int, const float*, float*, int,
-                               cudaStream_t, int*) {
-    return LASP_EINVAL;
-}
+int lasp_tc_fit_batch(const ModelDev& M, const TcImages& t, const lasp_batch* b, const lasp_fit_opts* o,
+                      lasp_result* r, void* stream, int* launches);
 
 }  // namespace lasp

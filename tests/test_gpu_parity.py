@@ -64,6 +64,21 @@ def test_interp_fp32_matches_oracle(lasp, grid):
     assert _flux_rel_err(Fp, ref) < 1e-6
 
 
+@pytest.mark.parametrize("prec,tol", [("tf32x3", 1e-5), ("tf32", 4e-3), ("bf16", 3e-2)])
+@pytest.mark.parametrize("grid", [S.SMALL, S.LAMOST], ids=lambda g: g.name)
+def test_interp_tensor_core_matches_oracle(lasp, grid, prec, tol):
+    """tcgen05 contraction; N = 300 spectra spans three 128-spectrum blocks and
+    a ragged tail, and the pixel tiles a ragged last tile."""
+    M, d = observed(grid, 300, 34, noise=False, mask_frac=0.0)
+    d["truth"] = q32(d["truth"])
+    ip = interp(lasp, grid)
+    Fp = H(ip.interp_eval(T(d["truth"]), prec))
+    ref = np.stack([O.model_flux(M, d["truth"][i], d["b_true"][i])["Fp"] for i in range(300)])
+    err = _flux_rel_err(Fp, ref)
+    print(f"{grid.name} {prec}: max rel err {err:.3e}")
+    assert err < tol
+
+
 # ------------------------------------------------ forward model (Eqs. 1, 5, 6)
 
 @pytest.mark.parametrize("grid", [S.SMALL, S.LAMOST, S.DESI], ids=lambda g: g.name)
@@ -121,26 +136,31 @@ def _fit_both(lasp, grid, M, d, n=None, **opts):
     return out, ref
 
 
-def test_fixed_step_trajectory_parity_small(lasp):
-    """16 x 1024 noise-free, lr 0.1, stop rules off, 25 Adam steps.
+@pytest.mark.parametrize("lr,nsteps", [(0.1, 20), (0.01, 50)])
+def test_fixed_step_trajectory_parity_small(lasp, lr, nsteps):
+    """16 x 1024 noise-free, stop rules off, a fixed number of Adam steps.
 
-    Noise-free fits at lr 0.1 end in an oscillation around the optimum where
-    the path is chaotic: the oracle itself, fed flux perturbed by one float32
-    ulp, leaves the tolerance after step 31 (see the design notes).  Fixed-
-    step parity is therefore checked inside the well-conditioned stretch."""
+    Noise-free fits end in an oscillation about the optimum where the path is
+    chaotic.  Calibrated on the oracle itself with the flux perturbed by
+    3e-6 relative (about the FP32 rounding of the GPU path): at lr 0.1 the
+    path leaves the tolerance after step 21 (at step 20 it stays within 0.19
+    of it); at lr 0.01 after step 61 (within 0.1 of it at step 50).  Fixed-
+    step parity is checked inside those well-conditioned stretches."""
     M, d = observed(S.SMALL, 16, S.SPECTRA_SEED, noise=False, mask_frac=0.0)
-    out, ref = _fit_both(lasp, S.SMALL, M, d, max_steps=25, tol=0.0)
+    out, ref = _fit_both(lasp, S.SMALL, M, d, max_steps=nsteps, tol=0.0, lr=lr)
     assert np.all(H(out["steps"]) == ref["steps"])
     err = np.abs(H(out["theta"]) - ref["theta"])[:, :4]
     assert np.all(err <= TOL), err.max(axis=0)
 
 
 def test_noise_free_recovery_small(lasp):
-    """lr 1e-3 to convergence: the GPU fit recovers the truth (config-1 data)."""
+    """Small steps to convergence: the GPU fit recovers the truth (config-1
+    data).  lr 3e-4 keeps Adam's end-of-fit jitter (about lr x half box
+    width = 0.6 K in Teff) inside the tolerance."""
     M, d = observed(S.SMALL, 16, S.SPECTRA_SEED, noise=False, mask_frac=0.0)
     ip = interp(lasp, S.SMALL)
     out = ip.fit(T(d["flux"]), T(d["ivar"]), T(d["good"], torch.uint8), T(q32(d["theta0"])),
-                 lr=1e-3, tol=1e-10, max_steps=20000)
+                 lr=3e-4, tol=1e-11, max_steps=40000)
     err = np.abs(H(out["theta"]) - d["truth"])[:, :4]
     assert np.all(err <= TOL), err.max(axis=0)
 
