@@ -164,6 +164,33 @@ int lasp_backward(lasp_interp h, int N, const float* theta, const float* b, int 
 int lasp_interp_eval(lasp_interp h, int N, const float* theta, float* Fp, int precision,
                      void* stream);
 
+/* Allocation-free form of lasp_interp_eval for the tensor-core precisions
+ * (LASP_PREC_TF32, LASP_PREC_BF16, LASP_PREC_TF32X3).  The paper has no
+ * counterpart: this entry point exists for callers that may not allocate
+ * device memory -- for example code running inside a framework that owns all
+ * device memory through its own pool, or a serving loop with a fixed memory
+ * budget, where a cudaMalloc would break the budget or stall other streams
+ * (cudaMalloc can synchronise the device).  It needs no lasp_interp handle
+ * (creating one allocates) and calls no cudaMalloc, cudaFree or allocating
+ * library routine.
+ *
+ * desc: host, as for lasp_init_interp.  coeff: device, K x n_model FP32 table
+ * (caller-owned input).  theta: device N x 5 physical.  Fp: device N x n_model
+ * output.  The swizzled table images and the kernel's wait-timeout flag live
+ * in one static device array of LASP_STATIC_MAX_MODEL_PIX / 128 tiles
+ * (3 MiB + 256 B per GPU that loads the library, held until exit); n_model
+ * above LASP_STATIC_MAX_MODEL_PIX is rejected with LASP_EINVAL.
+ *
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  Every
+ * call shares the array and rewrites it: calls whose work overlaps on the GPU
+ * (different streams, or different host threads on one device) race and must
+ * be serialised by the caller.  Errors: LASP_EINVAL, LASP_EGRID, LASP_ENODEV,
+ * LASP_ECUDA.  Asynchronous on `stream`. */
+#define LASP_STATIC_MAX_MODEL_PIX 8192
+int lasp_interp_eval_static(const lasp_interp_desc* desc, const float* coeff, int N,
+                            const float* theta, float* Fp, int precision, void* stream);
+
 /* Number of kernels the last call on this thread enqueued (for accounting). */
 int lasp_last_launches(void);
 

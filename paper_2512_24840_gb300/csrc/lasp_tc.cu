@@ -244,3 +244,127 @@ int lasp_tc_fit_batch(const ModelDev&, const TcImages&, const lasp_batch*, const
 }
 
 }  // namespace lasp
+
+// ---------------------------------------------------------------------------
+// Allocation-free form of the tensor-core contraction.
+//
+// The handle-based path keeps the swizzled table images and its wait-timeout
+// flag in memory that lasp_init_interp allocates.  Here the same kernel gets
+// that scratch from one file-scope __device__ array instead, so a call makes
+// no device allocation at all.  Every GPU that loads the library holds the
+// array (3 MiB + 256 B) until the process exits.
+
+#include <mutex>
+
+namespace lasp {
+namespace {
+
+constexpr int kStaticMaxTiles = LASP_STATIC_MAX_MODEL_PIX / TC_TILE;
+constexpr size_t kStaticImageBytes = (size_t)kStaticMaxTiles * TC_TILE_BYTES;
+constexpr size_t kStaticBytes = 3 * kStaticImageBytes + 256;
+
+// [TF32 hi image | TF32 lo image | BF16 image | timeout flag]
+static __device__ __align__(256) uint8_t g_static_scratch[kStaticBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+uint8_t* g_static_addr[kMaxDevices] = {};
+
+// Device address of g_static_scratch on the current device, looked up once
+// per device (with that device current).  Host code never touches the array
+// through its name: on the host the name is only a stand-in for the symbol.
+int static_scratch(uint8_t** out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LASP_ENODEV;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p) return LASP_ECUDA;
+        g_static_addr[dev] = static_cast<uint8_t*>(p);
+    }
+    *out = g_static_addr[dev];
+    return LASP_OK;
+}
+
+int static_model(const lasp_interp_desc* d, const float* coeff, ModelDev* M) {
+    if (d->K < 1 || d->K > KMAX || d->n_pix < 16 || d->pad < 0 || d->pad > HMAX || !(d->dln > 0.0) ||
+        !d->exps)
+        return LASP_EINVAL;
+    for (int k = 0; k < 3 * d->K; ++k)
+        if (d->exps[k] < 0 || d->exps[k] > 8) return LASP_EINVAL;
+    for (int k = 0; k < 3; ++k)
+        if (!(d->basis_hi[k] > d->basis_lo[k])) return LASP_EINVAL;
+    for (int k = 0; k < 5; ++k)
+        if (!(d->box_hi[k] > d->box_lo[k])) return LASP_EINVAL;
+    if (!(d->box_lo[0] > 0.0) || !(d->box_lo[4] > 0.0)) return LASP_EINVAL;
+    const double kms = 299792.458 * d->dln;
+    const double mumax = fmax(fabs(d->box_lo[3]), fabs(d->box_hi[3])) / kms;
+    if ((int)ceil(mumax + 5.0 * d->box_hi[4] / kms) > d->pad) return LASP_EGRID;
+    *M = ModelDev{};
+    M->C = coeff;
+    M->K = d->K;
+    M->n_pix = d->n_pix;
+    M->pad = d->pad;
+    M->n_model = d->n_pix + 2 * d->pad;
+    M->kms_px = (float)kms;
+    for (int k = 0; k < 3; ++k) {
+        M->blo[k] = (float)d->basis_lo[k];
+        M->bscale[k] = (float)(2.0 / (d->basis_hi[k] - d->basis_lo[k]));
+    }
+    for (int k = 0; k < 5; ++k) {
+        M->plo[k] = (float)d->box_lo[k];
+        M->phalf[k] = (float)(0.5 * (d->box_hi[k] - d->box_lo[k]));
+    }
+    for (int k = 0; k < 3 * d->K; ++k) M->exps[k] = d->exps[k];
+    return LASP_OK;
+}
+
+}  // namespace
+}  // namespace lasp
+
+extern "C" int lasp_interp_eval_static(const lasp_interp_desc* desc, const float* coeff, int N,
+                                       const float* theta, float* Fp, int precision, void* stream) {
+    using namespace lasp;
+    if (!desc || N < 0) return LASP_EINVAL;
+    if (precision != LASP_PREC_TF32 && precision != LASP_PREC_BF16 && precision != LASP_PREC_TF32X3)
+        return LASP_EINVAL;
+    ModelDev M;
+    int rc = static_model(desc, coeff, &M);
+    if (rc) return rc;
+    if (M.n_model > LASP_STATIC_MAX_MODEL_PIX) return LASP_EINVAL;
+    if (N == 0) return LASP_OK;
+    if (!coeff || !theta || !Fp) return LASP_EINVAL;
+    int dev = -1;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess ||
+        prop.major != 10 || prop.minor != 3)
+        return LASP_ENODEV;
+    uint8_t* base = nullptr;
+    rc = static_scratch(&base);
+    if (rc) return rc;
+    uint8_t* hi = base;
+    uint8_t* lo = base + kStaticImageBytes;
+    uint8_t* bf = base + 2 * kStaticImageBytes;
+    int* err = reinterpret_cast<int*>(base + 3 * kStaticImageBytes);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n_tiles = (M.n_model + TC_TILE - 1) / TC_TILE;
+    // the timeout flag keeps the previous call's value: clear it
+    rc = cuda_rc(cudaMemsetAsync(err, 0, sizeof(int), st));
+    if (rc) return rc;
+    const int total = n_tiles * TC_TILE * 8;
+    build_images_kernel<<<(total + 255) / 256, 256, 0, st>>>(coeff, M.K, M.n_model, n_tiles, hi, lo, bf);
+    rc = cuda_rc(cudaGetLastError());
+    if (rc) return rc;
+    const size_t smem = 4 * TC_TILE_BYTES + 1024;
+    dim3 grid((N + 127) / 128, n_tiles);
+    auto go = [&](auto kern, const uint8_t* a, const uint8_t* alo) {
+        int e = cuda_rc(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (e) return e;
+        kern<<<grid, 128, smem, st>>>(M, theta, Fp, N, a, alo, n_tiles, err);
+        return cuda_rc(cudaGetLastError());
+    };
+    if (precision == LASP_PREC_TF32) return go(interp_tc_kernel<1>, hi, nullptr);
+    if (precision == LASP_PREC_BF16) return go(interp_tc_kernel<2>, bf, nullptr);
+    return go(interp_tc_kernel<3>, hi, lo);
+}
