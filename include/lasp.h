@@ -138,6 +138,40 @@ typedef struct {
 int lasp_fit_batch(lasp_interp h, const lasp_batch* batch, const lasp_fit_opts* opts,
                    lasp_result* result, void* stream);
 
+/* Resumable fit slots, the device side of continuous batching (stage 8 run
+ * in chunks).  A slot pool owns, on the device, n_slots observation buffers
+ * (flux, ivar, good: n_pix each, theta0), the Adam state of each slot and its
+ * results, so a fit keeps its optimiser state resident between launches and a
+ * slot whose spectrum stops is refilled with the next one.  A fit split over
+ * several lasp_slots_step launches performs exactly the arithmetic of
+ * lasp_fit_batch: its result is bitwise the same and does not depend on the
+ * other slots.  Status of a slot: LASP_ST_RUNNING while fitting, the final
+ * LASP_ST_* bits once stopped, 0 when never used. */
+typedef struct lasp_slots_s* lasp_slots;          /* opaque, library-owned */
+
+/* Allocates the pool (device memory ~ n_slots x (9 n_pix + 480) bytes plus a
+ * staging copy of the observation buffers).  opts are copied.  Synchronous. */
+int lasp_slots_create(lasp_interp h, int n_slots, const lasp_fit_opts* opts, lasp_slots* out);
+void lasp_slots_free(lasp_slots s);
+
+/* Admit `count` spectra into the given slot indices (host int32, distinct,
+ * 0 <= idx < n_slots).  flux, ivar: host count x n_pix float32; good: host
+ * count x n_pix uint8; theta0: host count x 5 float32.  The rows are copied
+ * host -> device on `stream` (pinned host memory makes the copy asynchronous)
+ * and scattered into the slots, which become LASP_ST_RUNNING.  The host
+ * buffers must stay unchanged until the stream passes this call. */
+int lasp_slots_admit(lasp_slots s, int count, const int32_t* slot_idx, const float* flux,
+                     const float* ivar, const uint8_t* good, const float* theta0, void* stream);
+
+/* Run at most `budget` (>= 1) Adam steps on every running slot (one launch of
+ * the fused fit kernel; slots that stop write their results). */
+int lasp_slots_step(lasp_slots s, int budget, void* stream);
+
+/* Copy every slot's theta (n_slots x 5), loss, steps, status and weight to
+ * host buffers (any may be NULL) on `stream`. */
+int lasp_slots_fetch(lasp_slots s, float* theta, float* loss, int32_t* steps, uint32_t* status,
+                     float* weight, void* stream);
+
 /* Stage 9 parameter uncertainties at theta (device, N x 5 physical, e.g. the
  * fitted values): Jacobian J of the weighted residual sqrt(W) eps w.r.t. the
  * physical parameters with the continuum re-solved (variable projection),

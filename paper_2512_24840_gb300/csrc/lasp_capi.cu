@@ -221,7 +221,7 @@ int lasp_fit_batch(lasp_interp h, const lasp_batch* b, const lasp_fit_opts* o, l
     if (!r || (b->N > 0 && (!r->theta || !r->loss || !r->steps || !r->status))) return LASP_EINVAL;
     if (b->N == 0) return LASP_OK;
     if (o->precision != LASP_PREC_FP32) return lasp_tc_fit_batch(h->M, h->tc, b, o, r, stream, &g_last_launches);
-    FitParams P;
+    FitParams P{};
     P.M = h->M;
     P.O = to_dev(o);
     P.N = b->N;
@@ -332,6 +332,177 @@ int lasp_interp_eval(lasp_interp h, int N, const float* theta, float* Fp, int pr
     interp_fp32_kernel<256><<<grid, 256, 0, st>>>(h->M, theta, Fp);
     g_last_launches = 1;
     return cuda_err(cudaGetLastError());
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Resumable fit slots (continuous batching).
+
+namespace {
+
+__global__ void slots_scatter_kernel(int count, int n_pix, const int32_t* __restrict__ idx,
+                                     const float* __restrict__ f_st, const float* __restrict__ iv_st,
+                                     const uint8_t* __restrict__ g_st, const float* __restrict__ th_st,
+                                     float* flux, float* ivar, uint8_t* good, float* theta0, int* t,
+                                     uint32_t* status) {
+    const int r = blockIdx.x;
+    if (r >= count) return;
+    const int slot = idx[r];
+    const size_t src = (size_t)r * n_pix, dst = (size_t)slot * n_pix;
+    for (int j = threadIdx.x; j < n_pix; j += blockDim.x) {
+        flux[dst + j] = f_st[src + j];
+        ivar[dst + j] = iv_st[src + j];
+        good[dst + j] = g_st[src + j];
+    }
+    if (threadIdx.x < 5) theta0[5 * slot + threadIdx.x] = th_st[5 * r + threadIdx.x];
+    if (threadIdx.x == 0) {
+        t[slot] = -1;
+        status[slot] = LASP_ST_RUNNING;
+    }
+}
+
+}  // namespace
+
+struct lasp_slots_s {
+    lasp_interp h;
+    int n;
+    lasp_fit_opts opts;
+    float *flux, *ivar, *theta0;
+    uint8_t* good;
+    float *f_st, *iv_st, *th_st;
+    uint8_t* g_st;
+    int32_t* idx_st;
+    lasp::SlotState S;
+    float *theta, *loss, *cont, *weight;
+    int32_t* steps;
+    uint32_t* status;
+};
+
+extern "C" {
+
+void lasp_slots_free(lasp_slots s) {
+    if (!s) return;
+    void* ptrs[] = {s->flux, s->ivar, s->theta0, s->good, s->f_st, s->iv_st, s->th_st, s->g_st,
+                    s->idx_st, s->S.x, s->S.m, s->S.v, s->S.ring, s->S.prev, s->S.rise, s->S.t,
+                    s->S.w, s->S.imean, s->theta, s->loss, s->cont, s->weight, s->steps, s->status};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete s;
+}
+
+int lasp_slots_create(lasp_interp h, int n_slots, const lasp_fit_opts* o, lasp_slots* out) {
+    if (!h || !out || n_slots < 1) return LASP_EINVAL;
+    *out = nullptr;
+    int rc = check_opts(o, h->M.n_pix);
+    if (rc) return rc;
+    if (o->precision != LASP_PREC_FP32) return LASP_EINVAL;
+    lasp_slots_s* s = new (std::nothrow) lasp_slots_s();
+    if (!s) return LASP_ENOMEM;
+    s->h = h;
+    s->n = n_slots;
+    s->opts = *o;
+    const size_t n = (size_t)n_slots, p = (size_t)h->M.n_pix, NB = (size_t)o->legendre_deg + 1;
+    auto alloc = [&](auto** ptr, size_t bytes) {
+        if (rc) return;
+        rc = cuda_err(cudaMalloc((void**)ptr, bytes));
+        if (!rc) rc = cuda_err(cudaMemset(*ptr, 0, bytes));
+    };
+    alloc(&s->flux, n * p * 4);
+    alloc(&s->ivar, n * p * 4);
+    alloc(&s->good, n * p);
+    alloc(&s->theta0, n * 5 * 4);
+    alloc(&s->f_st, n * p * 4);
+    alloc(&s->iv_st, n * p * 4);
+    alloc(&s->g_st, n * p);
+    alloc(&s->th_st, n * 5 * 4);
+    alloc(&s->idx_st, n * 4);
+    alloc(&s->S.x, n * 5 * 4);
+    alloc(&s->S.m, n * 5 * 4);
+    alloc(&s->S.v, n * 5 * 4);
+    alloc(&s->S.ring, n * WINMAX * 4);
+    alloc(&s->S.prev, n * 4);
+    alloc(&s->S.rise, n * 4);
+    alloc(&s->S.t, n * 4);
+    alloc(&s->S.w, n * 4);
+    alloc(&s->S.imean, n * 4);
+    alloc(&s->theta, n * 5 * 4);
+    alloc(&s->loss, n * 4);
+    alloc(&s->cont, n * NB * 4);
+    alloc(&s->weight, n * 4);
+    alloc(&s->steps, n * 4);
+    alloc(&s->status, n * 4);
+    if (rc) {
+        lasp_slots_free(s);
+        return rc;
+    }
+    *out = s;
+    return LASP_OK;
+}
+
+int lasp_slots_admit(lasp_slots s, int count, const int32_t* slot_idx, const float* flux,
+                     const float* ivar, const uint8_t* good, const float* theta0, void* stream) {
+    g_last_launches = 0;
+    if (!s || count < 0 || count > s->n) return LASP_EINVAL;
+    if (count == 0) return LASP_OK;
+    if (!slot_idx || !flux || !ivar || !good || !theta0) return LASP_EINVAL;
+    for (int r = 0; r < count; ++r)
+        if (slot_idx[r] < 0 || slot_idx[r] >= s->n) return LASP_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t p = (size_t)s->h->M.n_pix, c = (size_t)count;
+    int rc = cuda_err(cudaMemcpyAsync(s->f_st, flux, c * p * 4, cudaMemcpyHostToDevice, st));
+    if (!rc) rc = cuda_err(cudaMemcpyAsync(s->iv_st, ivar, c * p * 4, cudaMemcpyHostToDevice, st));
+    if (!rc) rc = cuda_err(cudaMemcpyAsync(s->g_st, good, c * p, cudaMemcpyHostToDevice, st));
+    if (!rc) rc = cuda_err(cudaMemcpyAsync(s->th_st, theta0, c * 5 * 4, cudaMemcpyHostToDevice, st));
+    if (!rc) rc = cuda_err(cudaMemcpyAsync(s->idx_st, slot_idx, c * 4, cudaMemcpyHostToDevice, st));
+    if (rc) return rc;
+    slots_scatter_kernel<<<count, 256, 0, st>>>(count, (int)p, s->idx_st, s->f_st, s->iv_st, s->g_st,
+                                                 s->th_st, s->flux, s->ivar, s->good, s->theta0, s->S.t,
+                                                 s->status);
+    g_last_launches = 1;
+    return cuda_err(cudaGetLastError());
+}
+
+int lasp_slots_step(lasp_slots s, int budget, void* stream) {
+    g_last_launches = 0;
+    if (!s || budget < 1) return LASP_EINVAL;
+    FitParams P{};
+    P.M = s->h->M;
+    P.O = to_dev(&s->opts);
+    P.N = s->n;
+    P.S = s->S;
+    P.S.budget = budget;
+    P.flux = s->flux;
+    P.ivar = s->ivar;
+    P.good = s->good;
+    P.theta0 = s->theta0;
+    P.theta = s->theta;
+    P.loss = s->loss;
+    P.steps = s->steps;
+    P.status = s->status;
+    P.cont = s->cont;
+    P.weight = s->weight;
+    cudaStream_t st = (cudaStream_t)stream;
+    int e = dispatch_deg(s->opts.legendre_deg, [&](auto dd) {
+        constexpr int D = decltype(dd)::value;
+        return launch_fit<D>(P, st);
+    });
+    g_last_launches = e ? 0 : 1;
+    return e;
+}
+
+int lasp_slots_fetch(lasp_slots s, float* theta, float* loss, int32_t* steps, uint32_t* status,
+                     float* weight, void* stream) {
+    if (!s) return LASP_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = (size_t)s->n;
+    int rc = LASP_OK;
+    if (!rc && theta) rc = cuda_err(cudaMemcpyAsync(theta, s->theta, n * 5 * 4, cudaMemcpyDeviceToHost, st));
+    if (!rc && loss) rc = cuda_err(cudaMemcpyAsync(loss, s->loss, n * 4, cudaMemcpyDeviceToHost, st));
+    if (!rc && steps) rc = cuda_err(cudaMemcpyAsync(steps, s->steps, n * 4, cudaMemcpyDeviceToHost, st));
+    if (!rc && status) rc = cuda_err(cudaMemcpyAsync(status, s->status, n * 4, cudaMemcpyDeviceToHost, st));
+    if (!rc && weight) rc = cuda_err(cudaMemcpyAsync(weight, s->weight, n * 4, cudaMemcpyDeviceToHost, st));
+    return rc;
 }
 
 }  // extern "C"

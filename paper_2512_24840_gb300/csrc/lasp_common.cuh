@@ -248,7 +248,8 @@ __host__ __device__ constexpr int next_pow2(int n) {
 template <int NT>
 __device__ int prep_spectrum(const float* __restrict__ flux, const float* __restrict__ ivar,
                              const uint8_t* __restrict__ good, int p, int edge_px, float quantile,
-                             float* y, float* W, float* sortbuf, float* red, float* w_out) {
+                             float* y, float* W, float* sortbuf, float* red, float* w_out,
+                             float* imean_out = nullptr) {
     const int P2 = next_pow2(p);
     float cnt = 0.0f, isum = 0.0f;
     for (int j = threadIdx.x; j < P2; j += NT) {
@@ -295,6 +296,34 @@ __device__ int prep_spectrum(const float* __restrict__ flux, const float* __rest
     float acc1[1] = {nobj};
     block_sum<1, NT>(acc1, red, tot);
     *w_out = w;
+    if (imean_out) *imean_out = imean;
+    return (int)tot[0];
+}
+
+// y and W from a known weight w and mean inverse variance (a resumed fit):
+// the same arithmetic as prep_spectrum without the quantile.  Returns the
+// count of pixels that enter the loss.
+template <int NT>
+__device__ int refill_spectrum(const float* __restrict__ flux, const float* __restrict__ ivar,
+                               const uint8_t* __restrict__ good, int p, int edge_px, float w,
+                               float imean, float* y, float* W, float* red) {
+    float nobj = 0.0f;
+    for (int j = threadIdx.x; j < p; j += NT) {
+        float f = flux[j], iv = ivar[j];
+        bool use = good[j] && iv > 0.0f && isfinite(f) && isfinite(iv);
+        bool edge = j < edge_px || j >= p - edge_px;
+        if (use && !edge && w > 0.0f) {
+            y[j] = f / w;
+            W[j] = iv / imean;
+            nobj += 1.0f;
+        } else {
+            y[j] = 0.0f;
+            W[j] = 0.0f;
+        }
+    }
+    float acc1[1] = {nobj};
+    float* tot = red + (NT / 32) * 2;
+    block_sum<1, NT>(acc1, red, tot);
     return (int)tot[0];
 }
 

@@ -26,10 +26,28 @@ constexpr int PPT = 16;     // pixels per thread
 constexpr int TB = 8;       // taps per block
 constexpr int TAPBUF = 128; // tap buffer (>= 2 HMAX + 2 TB + 1)
 
+// Device-resident fit state of resumable slots (struct of arrays, S slots).
+// A launch in slot mode runs at most `budget` Adam steps per slot and saves
+// the state of slots that have not stopped; t = -1 marks a freshly admitted
+// slot (preprocessing and initial guess still to do).
+struct SlotState {
+    float* x;          // S x 5
+    float* m;          // S x 5
+    float* v;          // S x 5
+    float* ring;       // S x WINMAX
+    float* prev;       // S
+    int* rise;         // S
+    int* t;            // S
+    float* w;          // S  (weight, set at the first launch)
+    float* imean;      // S  (mean inverse variance)
+    int budget;
+};
+
 struct FitParams {
     ModelDev M;
     FitOpts O;
     int N;
+    SlotState S;       // S.x == nullptr: one launch fits every spectrum to its stop
     const float* flux;
     const float* ivar;
     const uint8_t* good;
@@ -207,14 +225,31 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) fit_kernel(const FitPar
     __shared__ int s_h, s_stop;
     __shared__ float s_w;
 
+    const bool slots = P.S.x != nullptr;
+    int t0 = 0;
+    if (slots) {
+        if (P.status[i] != 128u) return;          // slot not running (uniform per CTA)
+        t0 = P.S.t[i];
+    }
+    const bool fresh = !slots || t0 < 0;
+    if (t0 < 0) t0 = 0;
+
     // ---- preprocessing (section 3.3 step 2): y, W into skewed rows
     {
         const size_t row = (size_t)i * p;
-        float w;
-        const int n_obj = prep_spectrum<NT>(P.flux + row, P.ivar + row, P.good + row, p,
-                                            P.O.edge_px, P.O.quantile, y, W, Fp, red, &w);
+        float w, imean;
+        int n_obj;
+        if (fresh) {
+            n_obj = prep_spectrum<NT>(P.flux + row, P.ivar + row, P.good + row, p, P.O.edge_px,
+                                      P.O.quantile, y, W, Fp, red, &w, &imean);
+        } else {
+            w = P.S.w[i];
+            imean = P.S.imean[i];
+            n_obj = refill_spectrum<NT>(P.flux + row, P.ivar + row, P.good + row, p, P.O.edge_px, w,
+                                        imean, y, W, red);
+        }
         __syncthreads();
-        // re-layout y and W (written linearly by prep) into skewed rows in place:
+        // re-layout y and W (written linearly) into skewed rows in place:
         // copy out to registers, barrier, copy back skewed.
         float ty[PPT], tw[PPT];
 #pragma unroll
@@ -234,7 +269,11 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) fit_kernel(const FitPar
         }
         if (tid == 0) {
             s_w = w;
-            s_stop = (n_obj < NB + 5 || !(w > 0.0f) || !isfinite(w)) ? 1 : 0;
+            s_stop = (fresh && (n_obj < NB + 5 || !(w > 0.0f) || !isfinite(w))) ? 1 : 0;
+            if (slots && fresh) {
+                P.S.w[i] = w;
+                P.S.imean[i] = imean;
+            }
         }
     }
     // zero the padded F' and delta buffers (their pads stay zero)
@@ -245,16 +284,30 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) fit_kernel(const FitPar
     float x[5], m[5], v[5], prev = 0.0f;
     int rise = 0;
     if (tid == 0) {
+        if (fresh) {
 #pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            float xx = (P.theta0[5 * i + k] - M.plo[k]) / M.phalf[k] - 1.0f;
-            xx = fminf(1.0f, fmaxf(-1.0f, xx));
-            x[k] = xx;
-            s_x[k] = xx;
-            m[k] = 0.0f;
-            v[k] = 0.0f;
+            for (int k = 0; k < 5; ++k) {
+                float xx = (P.theta0[5 * i + k] - M.plo[k]) / M.phalf[k] - 1.0f;
+                xx = fminf(1.0f, fmaxf(-1.0f, xx));
+                x[k] = xx;
+                m[k] = 0.0f;
+                v[k] = 0.0f;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                x[k] = P.S.x[5 * i + k];
+                m[k] = P.S.m[5 * i + k];
+                v[k] = P.S.v[5 * i + k];
+            }
+            prev = P.S.prev[i];
+            rise = P.S.rise[i];
         }
+#pragma unroll
+        for (int k = 0; k < 5; ++k) s_x[k] = x[k];
     }
+    if (slots && !fresh)
+        for (int q = tid; q < WINMAX; q += NT) ring[q] = P.S.ring[(size_t)i * WINMAX + q];
     __syncthreads();
     if (s_stop) {
         if (tid == 0) {
@@ -279,7 +332,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) fit_kernel(const FitPar
     const bool own_mod = j0 < nm;
     const float xstep = 2.0f / (float)p;
 
-    for (int t = 0;; ++t) {
+    for (int t = t0;; ++t) {
         const int h = s_h;
         const int nblk = (2 * h + 1 + TB - 1) / TB;
 
@@ -538,6 +591,19 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) fit_kernel(const FitPar
                         x[k] = fminf(1.0f, fmaxf(-1.0f, x[k] - step * m[k] / denom));
                         s_x[k] = x[k];
                     }
+                    if (slots && t + 1 - t0 >= P.S.budget) {
+                        // suspend: save the slot state; the slot stays running
+#pragma unroll
+                        for (int k = 0; k < 5; ++k) {
+                            P.S.x[5 * i + k] = x[k];
+                            P.S.m[5 * i + k] = m[k];
+                            P.S.v[5 * i + k] = v[k];
+                        }
+                        P.S.prev[i] = prev;
+                        P.S.rise[i] = rise;
+                        P.S.t[i] = t + 1;
+                        stop = 2;
+                    }
                 }
                 s_stop = stop;
             }
@@ -550,6 +616,10 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) fit_kernel(const FitPar
         }
         __syncthreads();
         if (s_stop) break;
+    }
+    if (s_stop == 2) {
+        for (int q = tid; q < WINMAX; q += NT) P.S.ring[(size_t)i * WINMAX + q] = ring[q];
+        return;
     }
     if (P.cont && tid < NB) P.cont[(size_t)i * NB + tid] = s_b[tid];
 }

@@ -1,0 +1,59 @@
+"""Served fits: requests on two grids (LAMOST-like 3909 px and DESI-like
+7781 px) with uneven masks are admitted into small slot pools (forcing slot
+reuse) and stepped in chunks of 7 Adam steps on two streams.  Each result is
+bitwise the one the same spectrum gets when fitted alone with
+lasp_fit_batch -- alone and in the mix are the same."""
+import numpy as np
+import pytest
+
+import lasp_synth as S
+from oracle import oracle as O
+from tests.helpers import oracle_model, table
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _observed(grid, n, seed):
+    M = oracle_model(grid)
+    d = S.draw_batch(grid, n, seed, snr=(5, 100), mask_frac=0.0, mask_frac_max=0.2)
+    flux, ivar = S.finish_obs(O.model_batch(M, d["truth"], d["b_true"]), d)
+    th0 = np.asarray(d["theta0"], np.float32)
+    return flux, ivar, d["good"], th0
+
+
+def test_served_equals_alone():
+    from paper_2512_24840_gb300 import lasp
+    from paper_2512_24840_gb300.server import DevicePool, Server
+    lasp.load(build=True)
+    ips = {g.name: lasp.Interp.from_grid(g, table(g.name), S.EXPS, S.BASIS_LO, S.BASIS_HI,
+                                         S.BOX_LO, S.BOX_HI) for g in (S.LAMOST, S.DESI)}
+    data = {"lamost": _observed(S.LAMOST, 40, 61), "desi": _observed(S.DESI, 24, 62)}
+    pools = {"lamost": DevicePool(ips["lamost"], 16, max_steps=400),
+             "desi": DevicePool(ips["desi"], 8, max_steps=400)}
+    srv = Server(pools, chunk=7)
+    rids = {}
+    order = [("lamost", i) for i in range(40)] + [("desi", i) for i in range(24)]
+    np.random.default_rng(3).shuffle(order)
+    results = {}
+    for k, (lane, i) in enumerate(order):        # arrivals interleaved with ticks
+        f, iv, gd, th = data[lane]
+        rids[srv.submit(lane, f[i], iv[i], gd[i], th[i])] = (lane, i)
+        if k % 5 == 4:
+            for r in srv.tick():
+                results[r.rid] = r
+    for r in srv.run_until_idle():
+        results[r.rid] = r
+    assert len(results) == 64
+    dev = torch.device("cuda:0")
+    for lane in ("lamost", "desi"):
+        f, iv, gd, th = data[lane]
+        for i in range(len(f)):
+            one = ips[lane].fit(torch.tensor(f[i:i + 1], device=dev), torch.tensor(iv[i:i + 1], device=dev),
+                                torch.tensor(gd[i:i + 1], device=dev), torch.tensor(th[i:i + 1], device=dev),
+                                max_steps=400)
+            rid = [r for r, v in rids.items() if v == (lane, i)][0]
+            got = results[rid]
+            assert np.array_equal(got.theta, one["theta"][0].cpu().numpy()), (lane, i)
+            assert got.steps == int(one["steps"][0]) and got.status == int(one["status"][0])
+    srv.close()

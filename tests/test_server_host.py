@@ -1,0 +1,94 @@
+"""Host logic of the continuous-batching server, on a fake slot pool (CPU)."""
+import threading
+
+import numpy as np
+
+from paper_2512_24840_gb300.server import RUNNING, Server, latency_percentiles
+
+
+class FakePool:
+    """Each admitted request needs theta0[0] Adam steps; one step() runs at
+    most `budget` of them per slot."""
+
+    def __init__(self, n_slots):
+        self.n_slots = n_slots
+        self.need = np.zeros(n_slots, dtype=int)
+        self.done = np.zeros(n_slots, dtype=int)
+        self.status = np.zeros(n_slots, dtype=np.int32)
+        self.theta = np.zeros((n_slots, 5), dtype=np.float32)
+        self.admitted = []
+
+    def admit(self, slots, reqs):
+        for s, q in zip(slots, reqs):
+            assert self.status[s] != RUNNING
+            self.need[s] = int(q.theta0[0])
+            self.done[s] = 0
+            self.status[s] = RUNNING
+            self.theta[s] = q.theta0
+            self.admitted.append(q.rid)
+
+    def step(self, budget):
+        run = self.status == RUNNING
+        self.done[run] += np.minimum(budget, self.need[run] - self.done[run])
+        fin = run & (self.done >= self.need)
+        self.status[fin] = 1
+
+    def fetch(self):
+        pass
+
+    def wait(self):
+        return self.status.copy(), self.theta.copy(), np.zeros(self.n_slots), self.done.copy()
+
+
+def _req(steps):
+    th = np.zeros(5, dtype=np.float32)
+    th[0] = steps
+    return np.zeros(4), np.zeros(4), np.ones(4, np.uint8), th
+
+
+def test_admission_refill_and_retirement():
+    pools = {"a": FakePool(3), "b": FakePool(2)}
+    t = [0.0]
+    srv = Server(pools, chunk=10, clock=lambda: t[0])
+    steps = [5, 35, 10, 20, 15, 40, 5]
+    ids = [srv.submit("a" if k % 2 == 0 else "b", *_req(s)) for k, s in enumerate(steps)]
+    seen = {}
+    ticks = 0
+    while srv.pending():
+        t[0] += 1.0
+        for r in srv.tick():
+            seen[r.rid] = r
+        ticks += 1
+        assert ticks < 100
+        for name, p in pools.items():
+            lane = srv.lanes[name]
+            assert len(lane.busy) + len(lane.free) == p.n_slots
+    assert sorted(seen) == ids
+    for rid, r in seen.items():
+        assert r.steps == steps[rid] and r.status == 1
+        assert r.theta[0] == steps[rid]
+        # a request needing s steps spends ceil(s / chunk) ticks on a slot
+        assert r.latency >= np.ceil(steps[rid] / 10)
+    # FIFO admission per lane
+    assert pools["a"].admitted == [0, 2, 4, 6]
+    assert pools["b"].admitted == [1, 3, 5]
+
+
+def test_latency_percentiles_and_threaded_submit():
+    pools = {"a": FakePool(4)}
+    t = [0.0]
+    srv = Server(pools, chunk=3, clock=lambda: t[0])
+    ths = [threading.Thread(target=lambda k=k: [srv.submit("a", *_req(1 + (k + j) % 7))
+                                                 for j in range(25)]) for k in range(4)]
+    for th in ths:
+        th.start()
+    for th in ths:
+        th.join()
+    assert srv.pending() == 100
+    res = []
+    while srv.pending():
+        t[0] += 1.0
+        res += srv.tick()
+    assert len(res) == 100 and len({r.rid for r in res}) == 100
+    pct = latency_percentiles(res)
+    assert 0 < pct["p50_ms"] <= pct["p99_ms"]
