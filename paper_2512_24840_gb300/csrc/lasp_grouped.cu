@@ -1,0 +1,887 @@
+// Grouped tensor-core fit (mixed precision): every Adam step (stage 8) runs
+// over the whole active group of spectra as four kernels --
+//   K1  F' = phi(theta) C            tcgen05, M = 128 model pixels x N = 128 spectra
+//   K2  broadening, continuum WLS (FP32 or FP64 normal equations), residual,
+//       loss and the adjoint down to dF' (CUDA cores, one CTA per spectrum);
+//       dF' is written straight into the swizzled K-major operand image of K3
+//   K3  dphi = dF' C^T               tcgen05, M = 128 spectra x N = 32 terms,
+//       K = n_model pixels streamed through a 4-stage bulk-copy pipeline
+//   K4  chain rule, Adam, stop rules, next active list (one warp per spectrum)
+// -- so both contractions of Eq. 1 (forward and adjoint) run on the tensor
+// cores with the table shared by 128 spectra, and converged spectra leave the
+// active list at once.  Steps are replayed from CUDA graphs of 8 steps.
+#include <cuda_bf16.h>
+
+#include "lasp_fit.cuh"
+#include "lasp_tc.cuh"
+#include "lasp_tc_ptx.cuh"
+
+namespace lasp {
+
+int cuda_rc(cudaError_t e);
+
+namespace {
+
+constexpr uint32_t kWait = 1u << 22;
+constexpr int K3_STAGES = 4;
+constexpr int CHUNK_STEPS = 8;     // steps per captured graph (even)
+
+struct Grp {
+    ModelDev M;
+    FitOpts O;
+    int N, ldf, nch, nblk;        // spectra, F' row stride, K3 chunks, 128-spectrum blocks
+    int NB;                       // Legendre coefficients D + 1
+    // per spectrum state
+    float *x, *m, *v, *ring, *prev, *w, *imean, *loss, *gmu, *gsg, *b;
+    int *rise, *t, *flags;
+    // active lists (double buffered) and their counts
+    int* list[2];
+    int* count;                   // count[0], count[1]
+    float* Fp;                    // N x ldf
+    uint8_t *A_hi, *A_lo;         // K3 A images: nblk x nch x 16 KB
+    float* dphi;                  // list position x 32
+    int* err;
+    // inputs / outputs
+    const float *flux, *ivar, *theta0;
+    const uint8_t* good;
+    float *theta, *loss_out, *cont, *weight;
+    int32_t* steps;
+    uint32_t* status;
+};
+
+// ---------------------------------------------------------------- K0 prep
+template <int NT>
+__global__ void __launch_bounds__(NT) k0_prep(const Grp G) {
+    extern __shared__ __align__(16) float sm[];
+    const int i = blockIdx.x;
+    const int p = G.M.n_pix;
+    const int pa = (p + 3) & ~3;
+    float* y = sm;
+    float* W = sm + pa;
+    float* sortbuf = sm + 2 * pa;
+    float* red = sortbuf + next_pow2(p);
+    const size_t row = (size_t)i * p;
+    float w, imean;
+    const int n_obj = prep_spectrum<NT>(G.flux + row, G.ivar + row, G.good + row, p, G.O.edge_px,
+                                        G.O.quantile, y, W, sortbuf, red, &w, &imean);
+    if (threadIdx.x == 0) {
+        G.w[i] = w;
+        G.imean[i] = imean;
+        float x[5];
+        for (int k = 0; k < 5; ++k) {
+            float xx = (G.theta0[5 * i + k] - G.M.plo[k]) / G.M.phalf[k] - 1.0f;
+            x[k] = fminf(1.0f, fmaxf(-1.0f, xx));
+            G.x[5 * i + k] = x[k];
+            G.m[5 * i + k] = 0.0f;
+            G.v[5 * i + k] = 0.0f;
+        }
+        G.prev[i] = 0.0f;
+        G.rise[i] = 0;
+        G.t[i] = 0;
+        if (n_obj < G.NB + 5 || !(w > 0.0f) || !isfinite(w)) {
+            for (int k = 0; k < 5; ++k) G.theta[5 * i + k] = phys_of(G.M, k, x[k]);
+            G.loss_out[i] = NAN;
+            G.steps[i] = 0;
+            G.status[i] = LASP_ST_NODATA;
+            if (G.weight) G.weight[i] = w;
+            G.flags[i] = -1;
+        } else {
+            G.flags[i] = n_obj;
+            const int pos = atomicAdd(&G.count[0], 1);
+            G.list[0][pos] = i;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- K1 forward
+template <int PREC>
+__global__ void __launch_bounds__(128) k1_interp(const Grp G, int par, const uint8_t* __restrict__ img,
+                                                  const uint8_t* __restrict__ img_lo, int n_tiles) {
+    const int count = G.count[par];
+    const int s0 = blockIdx.x * 128;
+    if (s0 >= count) return;
+    extern __shared__ uint8_t smraw[];
+    uint8_t* base = reinterpret_cast<uint8_t*>(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+    uint8_t* Ahi = base;
+    uint8_t* Alo = base + TC_TILE_BYTES;
+    uint8_t* Bhi = base + 2 * TC_TILE_BYTES;
+    uint8_t* Blo = base + 3 * TC_TILE_BYTES;
+    __shared__ __align__(8) uint64_t bar_tma, bar_mma;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_ok, s_id[128];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const ModelDev& M = G.M;
+    if (warp == 0) {
+        tc::tmem_alloc(&tmem_base, 128);
+        tc::tmem_relinquish();
+    }
+    {
+        float phi[KMAX];
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k) phi[k] = 0.0f;
+        const int pos = s0 + tid;
+        int id = -1;
+        if (pos < count) {
+            id = G.list[par][pos];
+            float th[5];
+#pragma unroll
+            for (int q = 0; q < 5; ++q) th[q] = phys_of(M, q, G.x[5 * id + q]);
+            for (int k = 0; k < M.K; ++k) basis_term(M, k, th, phi, nullptr);
+        }
+        s_id[tid] = id;
+        if (PREC == 2) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                __nv_bfloat16 bb[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) bb[q] = __float2bfloat16_rn(c < 4 ? phi[8 * c + q] : 0.0f);
+                *reinterpret_cast<uint4*>(Bhi + tc::sw128_off(tid, c)) = *reinterpret_cast<uint4*>(bb);
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                float h[4], l[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    h[q] = tc::to_tf32(phi[4 * c + q]);
+                    l[q] = tc::to_tf32(phi[4 * c + q] - h[q]);
+                }
+                *reinterpret_cast<float4*>(Bhi + tc::sw128_off(tid, c)) = make_float4(h[0], h[1], h[2], h[3]);
+                if (PREC == 3)
+                    *reinterpret_cast<float4*>(Blo + tc::sw128_off(tid, c)) = make_float4(l[0], l[1], l[2], l[3]);
+            }
+        }
+    }
+    if (tid == 0) {
+        tc::mbar_init(&bar_tma, 1);
+        tc::mbar_init(&bar_mma, 1);
+        tc::fence_mbar_init();
+        s_ok = 1;
+    }
+    tc::fence_proxy_async_smem();
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    constexpr uint32_t idesc = tc::idesc_f32acc(PREC == 2 ? 1u : 2u, 128, 128);
+    const int t = blockIdx.y;
+    bool pending = false;
+    if (tid == 0) {
+        const uint32_t bytes = (PREC == 3 ? 2u : 1u) * (uint32_t)TC_TILE_BYTES;
+        tc::mbar_arrive_expect_tx(&bar_tma, bytes);
+        tc::bulk_g2s(Ahi, img + (size_t)t * TC_TILE_BYTES, TC_TILE_BYTES, &bar_tma);
+        if (PREC == 3) tc::bulk_g2s(Alo, img_lo + (size_t)t * TC_TILE_BYTES, TC_TILE_BYTES, &bar_tma);
+        pending = true;
+        if (!tc::mbar_wait_bounded(&bar_tma, 0, kWait)) {
+            atomicExch(G.err, 1);
+            s_ok = 0;
+        } else {
+            pending = false;
+            tc::tc_fence_after();
+            const uint64_t ah = tc::desc_kmajor_sw128(tc::smem_u32(Ahi));
+            const uint64_t bh = tc::desc_kmajor_sw128(tc::smem_u32(Bhi));
+            constexpr int NK = PREC == 2 ? 2 : 4;
+#pragma unroll
+            for (int ks = 0; ks < NK; ++ks) {
+                const uint64_t adv = (uint64_t)(ks * 32) >> 4;
+                if (PREC == 2) tc::mma_bf16(tmem, ah + adv, bh + adv, idesc, ks > 0);
+                else tc::mma_tf32(tmem, ah + adv, bh + adv, idesc, ks > 0);
+            }
+            if (PREC == 3) {
+                const uint64_t al = tc::desc_kmajor_sw128(tc::smem_u32(Alo));
+                const uint64_t bl = tc::desc_kmajor_sw128(tc::smem_u32(Blo));
+#pragma unroll
+                for (int ks = 0; ks < 4; ++ks) {
+                    const uint64_t adv = (uint64_t)(ks * 32) >> 4;
+                    tc::mma_tf32(tmem, ah + adv, bl + adv, idesc, 1);
+                    tc::mma_tf32(tmem, al + adv, bh + adv, idesc, 1);
+                }
+            }
+            tc::mma_commit(&bar_mma);
+        }
+    }
+    __syncthreads();
+    if (s_ok) {
+        if (!tc::mbar_wait_bounded(&bar_mma, 0, kWait)) {
+            atomicExch(G.err, 1);
+        } else {
+            tc::tc_fence_after();
+            const int mpix = t * TC_TILE + warp * 32 + lane;
+#pragma unroll 1
+            for (int c = 0; c < 8; ++c) {
+                if (s0 + c * 16 >= count) break;
+                float v[16];
+                tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 16), v);
+                if (mpix < M.n_model) {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const int id = s_id[c * 16 + q];
+                        if (id >= 0) G.Fp[(size_t)id * G.ldf + mpix] = v[q];
+                    }
+                }
+            }
+        }
+    }
+    if (tid == 0 && pending) tc::mbar_wait_bounded(&bar_tma, 0, kWait);
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 128);
+}
+
+// ---------------------------------------------------------------- K2 step body
+struct RestSmem {
+    int y, W, Fp, Db, g, gmu, gsg, red, out, total, dofs;
+    __host__ __device__ RestSmem(int p, int H, int n_model, int NT, int D) {
+        const int NB = D + 1, NV = NB * (NB + 1) / 2 + NB;
+        const int nv_max = NV > 4 ? NV : 4;
+        dofs = 2 * H + 8;
+        int o = 0;
+        y = o;    o += skew_size(p);
+        W = o;    o += skew_size(p);
+        Fp = o;   o += skew_size(n_model + 32);
+        Db = o;   o += skew_size(p + 4 * H + 40);
+        g = o;    o += TAPBUF;
+        gmu = o;  o += TAPBUF;
+        gsg = o;  o += TAPBUF;
+        red = o;  o += (NT / 32) * nv_max;
+        out = o;  o += 2 * nv_max + 16;
+        total = o;
+    }
+};
+
+template <int PREC>
+__device__ __forceinline__ void store_dfp(const Grp& G, int pos, int m0, const float (&d)[PPT]) {
+    // K3 A image of block pos/128: chunk of 32 (TF32) or 64 (BF16) model pixels,
+    // row pos%128, K-major with the 128-byte swizzle.
+    const int blk = pos >> 7, r = pos & 127;
+    if (PREC == 2) {
+        const int c = m0 >> 6;
+        uint8_t* tile = G.A_hi + ((size_t)blk * G.nch + c) * TC_TILE_BYTES;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int q = ((m0 & 63) >> 3) + h;
+            __nv_bfloat16 bb[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) bb[e] = __float2bfloat16_rn(d[8 * h + e]);
+            *reinterpret_cast<uint4*>(tile + tc::sw128_off(r, q)) = *reinterpret_cast<uint4*>(bb);
+        }
+    } else {
+        const int c = m0 >> 5;
+        const size_t toff = ((size_t)blk * G.nch + c) * TC_TILE_BYTES;
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int q = ((m0 & 31) >> 2) + h;
+            float hh[4], ll[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                hh[e] = tc::to_tf32(d[4 * h + e]);
+                ll[e] = tc::to_tf32(d[4 * h + e] - hh[e]);
+            }
+            *reinterpret_cast<float4*>(G.A_hi + toff + tc::sw128_off(r, q)) = make_float4(hh[0], hh[1], hh[2], hh[3]);
+            if (PREC == 3)
+                *reinterpret_cast<float4*>(G.A_lo + toff + tc::sw128_off(r, q)) =
+                    make_float4(ll[0], ll[1], ll[2], ll[3]);
+        }
+    }
+}
+
+template <int NT, int D, int PREC>
+__global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) k2_rest(const Grp G, int par) {
+    using Gm = Gram<D>;
+    constexpr int NB = D + 1;
+    constexpr int NV = Gm::NV;
+    const int pos = blockIdx.x;
+    if (pos >= G.count[par]) return;
+    const int id = G.list[par][pos];
+    extern __shared__ __align__(16) float sm[];
+    const ModelDev& M = G.M;
+    const int p = M.n_pix, H = M.pad, nm = M.n_model;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const RestSmem L(p, H, nm, NT, D);
+    float* y = sm + L.y;
+    float* W = sm + L.W;
+    float* Fp = sm + L.Fp;
+    float* Db = sm + L.Db;
+    float* g = sm + L.g;
+    float* gmu = sm + L.gmu;
+    float* gsg = sm + L.gsg;
+    float* red = sm + L.red;
+    float* out = sm + L.out;
+    double* outd = reinterpret_cast<double*>(sm + ((L.out + 1) & ~1));
+    __shared__ float s_b[NB], s_l;
+    __shared__ int s_h;
+
+    const int j0 = tid * PPT;
+    const bool own_pix = j0 < p;
+    const bool own_mod = j0 < nm;
+    // zero the padded buffers, then F' of this spectrum (K1 output) into skewed rows
+    for (int q = tid; q < skew_size(nm + 32); q += NT) Fp[q] = 0.0f;
+    for (int q = tid; q < skew_size(p + 4 * H + 40); q += NT) Db[q] = 0.0f;
+    {
+        const size_t row = (size_t)id * p;
+        refill_spectrum<NT>(G.flux + row, G.ivar + row, G.good + row, p, G.O.edge_px, G.w[id],
+                            G.imean[id], y, W, red);
+    }
+    __syncthreads();
+    {
+        float ty[PPT], tw[PPT];
+#pragma unroll
+        for (int r = 0; r < PPT; ++r) {
+            const int j = j0 + r;
+            ty[r] = j < p ? y[j] : 0.0f;
+            tw[r] = j < p ? W[j] : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < PPT; ++r) {
+            const int j = j0 + r;
+            if (j < p) {
+                y[skew(j)] = ty[r];
+                W[skew(j)] = tw[r];
+            }
+        }
+        if (own_mod) {
+            const float4* src = reinterpret_cast<const float4*>(G.Fp + (size_t)id * G.ldf + j0);
+#pragma unroll
+            for (int q = 0; q < PPT / 4; ++q) {
+                const float4 c = src[q];
+                const float cv[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (j0 + 4 * q + e < nm) Fp[skew(j0 + 4 * q + e + 16)] = cv[e];
+            }
+        }
+    }
+    if (warp == 0) {
+        float th[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) th[k] = phys_of(M, k, G.x[5 * id + k]);
+        for (int q = 2 * H + 1 + lane; q < TAPBUF; q += 32) {
+            g[q] = 0.0f;
+            gmu[q] = 0.0f;
+            gsg[q] = 0.0f;
+        }
+        const int h = kernel_taps_warp(th[3] / M.kms_px, th[4] / M.kms_px, H, g, gmu, gsg);
+        if (lane == 0) s_h = h;
+    }
+    __syncthreads();
+    const int h = s_h;
+    const int nblk = (2 * h + 1 + TB - 1) / TB;
+    const float xstep = 2.0f / (float)p;
+
+    // F'' (Eq. 5) and the normal equations (Eq. 6)
+    float fpp[PPT];
+#pragma unroll
+    for (int r = 0; r < PPT; ++r) fpp[r] = 0.0f;
+    if (own_pix) {
+        for (int bk = 0; bk < nblk; ++bk) {
+            const int s0 = -h + bk * TB;
+            float gg[TB], win[PPT + TB - 1];
+#pragma unroll
+            for (int e = 0; e < TB; ++e) gg[e] = g[s0 + e + H];
+            const int base = j0 + H - s0 - (TB - 1) + 16;
+#pragma unroll
+            for (int q = 0; q < PPT + TB - 1; ++q) win[q] = Fp[skew(base + q)];
+#pragma unroll
+            for (int e = 0; e < TB; ++e)
+#pragma unroll
+                for (int r = 0; r < PPT; ++r) fpp[r] = fmaf(gg[e], win[r - e + TB - 1], fpp[r]);
+        }
+    }
+    float gacc[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) gacc[q] = 0.0f;
+    if (own_pix) {
+#pragma unroll
+        for (int r = 0; r < PPT; ++r) {
+            const int j = j0 + r;
+            const float Wj = j < p ? W[skew(j)] : 0.0f;
+            if (Wj != 0.0f) {
+                float Pl[NB];
+                legendre<D>(fmaf((float)j, xstep, -1.0f), Pl);
+                const float f = fpp[r];
+                const float vv = Wj * f * f, uu = Wj * f * y[skew(j)];
+#pragma unroll
+                for (int a = 0; a < NB; ++a) {
+                    const float va = vv * Pl[a];
+#pragma unroll
+                    for (int b2 = a; b2 < NB; ++b2) gacc[Gm::idx(a, b2)] = fmaf(va, Pl[b2], gacc[Gm::idx(a, b2)]);
+                    gacc[Gm::NG + a] = fmaf(uu, Pl[a], gacc[Gm::NG + a]);
+                }
+            }
+        }
+    }
+    if (G.O.fp64_ne) {
+        reduce_to_warp0_f64<NV, NT>(gacc, red, outd);
+        if (tid == 0) {
+            double bd[NB];
+            const bool ok = chol_solve_rcp<D, double>(outd, outd + Gm::NG, bd);
+#pragma unroll
+            for (int a = 0; a < NB; ++a) s_b[a] = ok ? (float)bd[a] : NAN;
+        }
+    } else {
+        reduce_to_warp0<NV, NT>(gacc, red, out);
+        if (tid == 0) {
+            float bf[NB];
+            const bool ok = chol_solve_rcp<D, float>(out, out + Gm::NG, bf);
+#pragma unroll
+            for (int a = 0; a < NB; ++a) s_b[a] = ok ? bf[a] : NAN;
+        }
+    }
+    __syncthreads();
+    // residual (Eq. 7), loss (Eq. 9), delta = W eps c
+    float racc[2] = {0.0f, 0.0f};
+    {
+        float bl[NB];
+#pragma unroll
+        for (int a = 0; a < NB; ++a) bl[a] = s_b[a];
+        const bool solved = isfinite(bl[0]);
+        if (own_pix && solved) {
+#pragma unroll
+            for (int r = 0; r < PPT; ++r) {
+                const int j = j0 + r;
+                float dlt = 0.0f;
+                const float Wj = j < p ? W[skew(j)] : 0.0f;
+                if (Wj != 0.0f) {
+                    float Pl[NB];
+                    legendre<D>(fmaf((float)j, xstep, -1.0f), Pl);
+                    float c = 0.0f;
+#pragma unroll
+                    for (int a = 0; a < NB; ++a) c = fmaf(bl[a], Pl[a], c);
+                    const float e = y[skew(j)] - c * fpp[r];
+                    racc[0] = fmaf(Wj * e, e, racc[0]);
+                    if (c <= 0.0f) racc[1] = 1.0f;
+                    dlt = Wj * e * c;
+                }
+                fpp[r] = dlt;
+                if (j < p) Db[skew(j + L.dofs)] = dlt;
+            }
+        }
+        if (!solved) racc[0] = NAN;
+    }
+    reduce_to_warp0<2, NT>(racc, red, out);
+    if (tid == 0) {
+        s_l = sqrtf(out[0] / (float)p);
+        G.loss[id] = s_l;
+        G.flags[id] = (out[1] > 0.0f ? 1 : 0) | (isfinite(s_b[0]) ? 0 : 2);
+#pragma unroll
+        for (int a = 0; a < NB; ++a) G.b[(size_t)id * NB + a] = s_b[a];
+    }
+    __syncthreads();
+    // adjoint of the kernel parameters through a_s = sum_j delta_j F'_{j+H-s}
+    float bacc[2] = {0.0f, 0.0f};
+    if (own_pix) {
+        for (int bk = 0; bk < nblk; ++bk) {
+            const int s0 = -h + bk * TB;
+            float win[PPT + TB - 1];
+            const int base = j0 + H - s0 - (TB - 1) + 16;
+#pragma unroll
+            for (int q = 0; q < PPT + TB - 1; ++q) win[q] = Fp[skew(base + q)];
+            float a[TB];
+#pragma unroll
+            for (int e = 0; e < TB; ++e) a[e] = 0.0f;
+#pragma unroll
+            for (int r = 0; r < PPT; ++r)
+#pragma unroll
+                for (int e = 0; e < TB; ++e) a[e] = fmaf(fpp[r], win[r - e + TB - 1], a[e]);
+#pragma unroll
+            for (int e = 0; e < TB; ++e) {
+                bacc[0] = fmaf(gmu[s0 + e + H], a[e], bacc[0]);
+                bacc[1] = fmaf(gsg[s0 + e + H], a[e], bacc[1]);
+            }
+        }
+    }
+    // dF'_m = sum_s g_s delta_{m-H+s}, written as the K3 operand (zero beyond n_model)
+    const int kpix = PREC == 2 ? 64 * ((nm + 63) / 64) : 32 * ((nm + 31) / 32);
+    if (j0 < kpix) {
+        float dfp[PPT];
+#pragma unroll
+        for (int r = 0; r < PPT; ++r) dfp[r] = 0.0f;
+        if (own_mod) {
+            for (int bk = 0; bk < nblk; ++bk) {
+                const int s0 = -h + bk * TB;
+                float gg[TB], win[PPT + TB - 1];
+#pragma unroll
+                for (int e = 0; e < TB; ++e) gg[e] = g[s0 + e + H];
+                const int base = j0 - H + s0 + L.dofs;
+#pragma unroll
+                for (int q = 0; q < PPT + TB - 1; ++q) win[q] = Db[skew(base + q)];
+#pragma unroll
+                for (int e = 0; e < TB; ++e)
+#pragma unroll
+                    for (int r = 0; r < PPT; ++r) dfp[r] = fmaf(gg[e], win[r + e], dfp[r]);
+            }
+#pragma unroll
+            for (int r = 0; r < PPT; ++r)
+                if (j0 + r >= nm) dfp[r] = 0.0f;
+        }
+        store_dfp<PREC>(G, pos, j0, dfp);
+    }
+    reduce_to_warp0<2, NT>(bacc, red, out);
+    if (tid == 0) {
+        G.gmu[id] = out[0];
+        G.gsg[id] = out[1];
+    }
+}
+
+// ---------------------------------------------------------------- K3 backward contraction
+template <int PREC>
+__global__ void __launch_bounds__(128) k3_back(const Grp G, int par, const uint8_t* __restrict__ bk,
+                                               const uint8_t* __restrict__ bk_lo) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) G.count[par ^ 1] = 0;   // list K4 fills next
+    const int count = G.count[par];
+    const int s0 = blockIdx.x * 128;
+    if (s0 >= count) return;
+    extern __shared__ uint8_t smraw[];
+    uint8_t* base = reinterpret_cast<uint8_t*>(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+    // stage s: A hi (16 KB), A lo (16 KB), B hi (4 KB), B lo (4 KB)
+    constexpr int STAGE = 2 * TC_TILE_BYTES + 2 * TC_BK_CHUNK_BYTES;
+    __shared__ __align__(8) uint64_t full[K3_STAGES], empty[K3_STAGES], done;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_ok;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) {
+        tc::tmem_alloc(&tmem_base, 32);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int s = 0; s < K3_STAGES; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
+        tc::mbar_init(&done, 1);
+        tc::fence_mbar_init();
+        s_ok = 1;
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    constexpr uint32_t idesc = tc::idesc_f32acc(PREC == 2 ? 1u : 2u, 128, 32);
+    const int nch = G.nch;
+    const uint8_t* Ablk = G.A_hi + (size_t)blockIdx.x * nch * TC_TILE_BYTES;
+    const uint8_t* Ablk_lo = PREC == 3 ? G.A_lo + (size_t)blockIdx.x * nch * TC_TILE_BYTES : nullptr;
+    if (tid == 0) {
+        const uint32_t bytes = (PREC == 3 ? 2u : 1u) * (uint32_t)(TC_TILE_BYTES + TC_BK_CHUNK_BYTES);
+        auto issue = [&](int c) {
+            uint8_t* st = base + (c % K3_STAGES) * STAGE;
+            tc::mbar_arrive_expect_tx(&full[c % K3_STAGES], bytes);
+            tc::bulk_g2s(st, Ablk + (size_t)c * TC_TILE_BYTES, TC_TILE_BYTES, &full[c % K3_STAGES]);
+            tc::bulk_g2s(st + 2 * TC_TILE_BYTES, bk + (size_t)c * TC_BK_CHUNK_BYTES, TC_BK_CHUNK_BYTES,
+                         &full[c % K3_STAGES]);
+            if (PREC == 3) {
+                tc::bulk_g2s(st + TC_TILE_BYTES, Ablk_lo + (size_t)c * TC_TILE_BYTES, TC_TILE_BYTES,
+                             &full[c % K3_STAGES]);
+                tc::bulk_g2s(st + 2 * TC_TILE_BYTES + TC_BK_CHUNK_BYTES, bk_lo + (size_t)c * TC_BK_CHUNK_BYTES,
+                             TC_BK_CHUNK_BYTES, &full[c % K3_STAGES]);
+            }
+        };
+        const int pre = nch < K3_STAGES ? nch : K3_STAGES;
+        for (int c = 0; c < pre; ++c) issue(c);
+        int issued = pre;
+        bool ok = true;
+        for (int c = 0; c < nch && ok; ++c) {
+            const int s = c % K3_STAGES;
+            if (!tc::mbar_wait_bounded(&full[s], (uint32_t)((c / K3_STAGES) & 1), kWait)) {
+                ok = false;
+                break;
+            }
+            tc::tc_fence_after();
+            uint8_t* st = base + s * STAGE;
+            const uint64_t ah = tc::desc_kmajor_sw128(tc::smem_u32(st));
+            const uint64_t bh = tc::desc_kmajor_sw128(tc::smem_u32(st + 2 * TC_TILE_BYTES));
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {
+                const uint64_t adv = (uint64_t)(ks * 32) >> 4;
+                const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
+                if (PREC == 2) tc::mma_bf16(tmem, ah + adv, bh + adv, idesc, acc);
+                else tc::mma_tf32(tmem, ah + adv, bh + adv, idesc, acc);
+            }
+            if (PREC == 3) {
+                const uint64_t al = tc::desc_kmajor_sw128(tc::smem_u32(st + TC_TILE_BYTES));
+                const uint64_t bl = tc::desc_kmajor_sw128(tc::smem_u32(st + 2 * TC_TILE_BYTES + TC_BK_CHUNK_BYTES));
+#pragma unroll
+                for (int ks = 0; ks < 4; ++ks) {
+                    const uint64_t adv = (uint64_t)(ks * 32) >> 4;
+                    tc::mma_tf32(tmem, ah + adv, bl + adv, idesc, 1);
+                    tc::mma_tf32(tmem, al + adv, bh + adv, idesc, 1);
+                }
+            }
+            tc::mma_commit(&empty[s]);
+            // refill the stage of the previous chunk once its MMAs are done
+            if (c >= 1 && issued < nch) {
+                const int sp = (c - 1) % K3_STAGES;
+                if (!tc::mbar_wait_bounded(&empty[sp], (uint32_t)(((c - 1) / K3_STAGES) & 1), kWait)) {
+                    ok = false;
+                    break;
+                }
+                issue(issued++);
+            }
+        }
+        if (ok) tc::mma_commit(&done);
+        else {
+            atomicExch(G.err, 1);
+            s_ok = 0;
+            // let copies already issued land before the CTA exits
+            for (int c = 0; c < issued; ++c)
+                tc::mbar_wait_bounded(&full[c % K3_STAGES], (uint32_t)((c / K3_STAGES) & 1), kWait);
+        }
+    }
+    __syncthreads();
+    if (s_ok) {
+        if (!tc::mbar_wait_bounded(&done, 0, kWait)) {
+            atomicExch(G.err, 1);
+        } else {
+            tc::tc_fence_after();
+            const int pos = s0 + warp * 32 + lane;
+            float v0[16], v1[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16), v0);
+            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + 16u, v1);
+            if (pos < count) {
+                float4* dst = reinterpret_cast<float4*>(G.dphi + (size_t)pos * 32);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) dst[q] = make_float4(v0[4 * q], v0[4 * q + 1], v0[4 * q + 2], v0[4 * q + 3]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) dst[4 + q] = make_float4(v1[4 * q], v1[4 * q + 1], v1[4 * q + 2], v1[4 * q + 3]);
+            }
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 32);
+}
+
+// ---------------------------------------------------------------- K4 Adam + stop rules
+template <int D>
+__global__ void __launch_bounds__(256) k4_adam(const Grp G, int par) {
+    constexpr int NB = D + 1;
+    const int lane = threadIdx.x & 31;
+    const int pos = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (pos >= G.count[par]) return;
+    const int id = G.list[par][pos];
+    const ModelDev& M = G.M;
+    float th[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) th[k] = phys_of(M, k, G.x[5 * id + k]);
+    float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f;
+    if (lane < M.K) {
+        float phi[KMAX], dphi[3 * KMAX];
+        basis_term(M, lane, th, phi, dphi);
+        const float gp = G.dphi[(size_t)pos * 32 + lane];
+        c0 = gp * dphi[3 * lane + 0];
+        c1 = gp * dphi[3 * lane + 1];
+        c2 = gp * dphi[3 * lane + 2];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        c0 += __shfl_xor_sync(0xffffffffu, c0, o);
+        c1 += __shfl_xor_sync(0xffffffffu, c1, o);
+        c2 += __shfl_xor_sync(0xffffffffu, c2, o);
+    }
+    if (lane != 0) return;
+    const int p = M.n_pix;
+    const float l = G.loss[id];
+    const int flags = G.flags[id];
+    const float kappa = l > 0.0f ? -1.0f / ((float)p * l) : 0.0f;
+    float gx[5];
+    gx[0] = kappa * c0 * M.phalf[0];
+    gx[1] = kappa * c1 * M.phalf[1];
+    gx[2] = kappa * c2 * M.phalf[2];
+    gx[3] = kappa * G.gmu[id] / M.kms_px * M.phalf[3];
+    gx[4] = kappa * G.gsg[id] / M.kms_px * M.phalf[4];
+    const int t = G.t[id];
+    uint32_t st = 0;
+    if (flags & 2) st = LASP_ST_SINGULAR;
+    else {
+        bool fin = isfinite(l);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) fin = fin && isfinite(gx[k]);
+        if (!fin) st = LASP_ST_NONFINITE;
+    }
+    if (!st) {
+        const int Wn = G.O.window;
+        float* ring = G.ring + (size_t)id * WINMAX;
+        if (t >= Wn && fabsf(l - ring[t % Wn]) < G.O.tol) st = LASP_ST_CONV_TOL;
+        int rise = (t >= 1 && l > G.prev[id]) ? G.rise[id] + 1 : 0;
+        if (!st && rise >= Wn) st = LASP_ST_CONV_RISE;
+        if (!st && t >= G.O.max_steps) st = LASP_ST_MAXSTEPS;
+        ring[t % Wn] = l;
+        G.prev[id] = l;
+        G.rise[id] = rise;
+    }
+    if (st) {
+        if (st <= LASP_ST_MAXSTEPS && (flags & 1)) st |= LASP_ST_NONPOS;
+        for (int k = 0; k < 5; ++k) G.theta[5 * id + k] = th[k];
+        G.loss_out[id] = l;
+        G.steps[id] = t;
+        G.status[id] = st;
+        if (G.weight) G.weight[id] = G.w[id];
+        if (G.cont)
+            for (int a = 0; a < NB; ++a) G.cont[(size_t)id * NB + a] = G.b[(size_t)id * NB + a];
+        return;
+    }
+    const float tt = (float)(t + 1);
+    const float bc1 = 1.0f - powf(G.O.beta1, tt);
+    const float bc2 = 1.0f - powf(G.O.beta2, tt);
+    const float step = G.O.lr / bc1, rbc2 = rsqrtf(bc2);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        float mk = G.O.beta1 * G.m[5 * id + k] + (1.0f - G.O.beta1) * gx[k];
+        float vk = G.O.beta2 * G.v[5 * id + k] + (1.0f - G.O.beta2) * gx[k] * gx[k];
+        const float denom = sqrtf(vk) * rbc2 + G.O.eps;
+        const float xk = G.x[5 * id + k];
+        G.x[5 * id + k] = fminf(1.0f, fmaxf(-1.0f, xk - step * mk / denom));
+        G.m[5 * id + k] = mk;
+        G.v[5 * id + k] = vk;
+    }
+    G.t[id] = t + 1;
+    const int slot = atomicAdd(&G.count[par ^ 1], 1);
+    G.list[par ^ 1][slot] = id;
+}
+
+template <typename T>
+int amalloc(T** p, size_t bytes, cudaStream_t st) {
+    return cuda_rc(cudaMallocAsync((void**)p, bytes, st));
+}
+
+template <int D, int PREC, int NT>
+int run_grouped(Grp& G, const TcImages& tc, cudaStream_t st, int* launches) {
+    const int N = G.N;
+    const ModelDev& M = G.M;
+    // K0
+    {
+        const int pa = (M.n_pix + 3) & ~3;
+        const size_t smem = 4 * ((size_t)2 * pa + next_pow2(M.n_pix) + (NT / 32) * 4 + 16);
+        int e = cuda_rc(cudaFuncSetAttribute(k0_prep<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (e) return e;
+        k0_prep<NT><<<N, NT, smem, st>>>(G);
+        if ((e = cuda_rc(cudaGetLastError()))) return e;
+    }
+    const size_t smem1 = 4 * TC_TILE_BYTES + 1024;
+    const size_t smem3 = K3_STAGES * (2 * TC_TILE_BYTES + 2 * TC_BK_CHUNK_BYTES) + 1024;
+    const RestSmem RS(M.n_pix, M.pad, M.n_model, NT, D);
+    const size_t smem2 = 4 * (size_t)RS.total;
+    int e = cuda_rc(cudaFuncSetAttribute(k1_interp<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1));
+    if (!e) e = cuda_rc(cudaFuncSetAttribute(k2_rest<NT, D, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
+    if (!e) e = cuda_rc(cudaFuncSetAttribute(k3_back<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3));
+    if (e) return e;
+    const uint8_t* img = (const uint8_t*)(PREC == 2 ? tc.bf16 : tc.tf32_hi);
+    const uint8_t* img_lo = (const uint8_t*)tc.tf32_lo;
+    const uint8_t* bk = (const uint8_t*)(PREC == 2 ? tc.bk_bf : tc.bk_hi);
+    const uint8_t* bk_lo = (const uint8_t*)tc.bk_lo;
+    const dim3 g1((N + 127) / 128, tc.n_tiles);
+    const int g3 = (N + 127) / 128;
+    const int g4 = (N + 7) / 8;
+    auto one_step = [&](int par) {
+        k1_interp<PREC><<<g1, 128, smem1, st>>>(G, par, img, img_lo, tc.n_tiles);
+        k2_rest<NT, D, PREC><<<N, NT, smem2, st>>>(G, par);
+        k3_back<PREC><<<g3, 128, smem3, st>>>(G, par, bk, bk_lo);
+        k4_adam<D><<<g4, 256, 0, st>>>(G, par);
+    };
+    // capture CHUNK_STEPS steps (parities 0,1,0,1,...) into one graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap;
+    if ((e = cuda_rc(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)))) return e;
+    e = cuda_rc(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    if (!e) {
+        cudaStream_t keep = st;
+        st = cap;
+        for (int k = 0; k < CHUNK_STEPS; ++k) one_step(k & 1);
+        st = keep;
+        e = cuda_rc(cudaStreamEndCapture(cap, &graph));
+    }
+    if (!e) e = cuda_rc(cudaGraphInstantiate(&exec, graph, 0));
+    int h_count = 0;
+    int nlaunch = 1;
+    // every spectrum stops after at most max_steps + 1 evaluations
+    const int max_chunks = (G.O.max_steps + 1 + CHUNK_STEPS - 1) / CHUNK_STEPS + 1;
+    for (int c = 0; !e && c < max_chunks; ++c) {
+        e = cuda_rc(cudaGraphLaunch(exec, st));
+        nlaunch += 4 * CHUNK_STEPS;
+        if (!e) e = cuda_rc(cudaMemcpyAsync(&h_count, G.count, sizeof(int), cudaMemcpyDeviceToHost, st));
+        if (!e) e = cuda_rc(cudaStreamSynchronize(st));
+        if (!e && h_count == 0) break;
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cap);
+    *launches = nlaunch;
+    return e;
+}
+
+}  // namespace
+
+int lasp_tc_fit_batch(const ModelDev& M, const TcImages& tc, const lasp_batch* b, const lasp_fit_opts* o,
+                      lasp_result* r, void* stream, int* launches) {
+    *launches = 0;
+    if (!tc.tf32_hi || !tc.bk_hi) return LASP_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    Grp G{};
+    G.M = M;
+    G.O.lr = o->lr;
+    G.O.beta1 = o->beta1;
+    G.O.beta2 = o->beta2;
+    G.O.eps = o->eps;
+    G.O.tol = o->tol;
+    G.O.window = o->window;
+    G.O.max_steps = o->max_steps;
+    G.O.edge_px = o->edge_px;
+    G.O.quantile = o->quantile;
+    G.O.fp64_ne = o->fp64_normal_eq ? 1 : 0;
+    const int N = b->N;
+    const int NB = o->legendre_deg + 1;
+    G.N = N;
+    G.NB = NB;
+    G.ldf = (M.n_model + 15) & ~15;
+    G.nch = o->precision == LASP_PREC_BF16 ? tc.n_chunks_bf16 : tc.n_chunks_tf32;
+    G.nblk = (N + 127) / 128;
+    G.flux = b->flux;
+    G.ivar = b->ivar;
+    G.good = b->good;
+    G.theta0 = b->theta0;
+    G.theta = r->theta;
+    G.loss_out = r->loss;
+    G.steps = r->steps;
+    G.status = r->status;
+    G.cont = r->cont_coeff;
+    G.weight = r->weight;
+    G.err = tc.err;
+    const size_t n = (size_t)N;
+    int e = LASP_OK;
+    auto A = [&](auto** ptr, size_t bytes) {
+        if (!e) e = amalloc(ptr, bytes, st);
+    };
+    A(&G.x, n * 20); A(&G.m, n * 20); A(&G.v, n * 20); A(&G.ring, n * WINMAX * 4);
+    A(&G.prev, n * 4); A(&G.w, n * 4); A(&G.imean, n * 4); A(&G.loss, n * 4); A(&G.gmu, n * 4);
+    A(&G.gsg, n * 4); A(&G.b, n * NB * 4); A(&G.rise, n * 4); A(&G.t, n * 4); A(&G.flags, n * 4);
+    A(&G.list[0], n * 4); A(&G.list[1], n * 4); A(&G.count, 16);
+    A(&G.Fp, n * G.ldf * 4);
+    A(&G.A_hi, (size_t)G.nblk * G.nch * TC_TILE_BYTES);
+    if (o->precision == LASP_PREC_TF32X3) A(&G.A_lo, (size_t)G.nblk * G.nch * TC_TILE_BYTES);
+    A(&G.dphi, (size_t)G.nblk * 128 * 32 * 4);
+    if (!e) e = cuda_rc(cudaMemsetAsync(G.count, 0, 16, st));
+    if (!e) {
+        const int NT = M.n_pix <= 16 * 256 ? 256 : 512;
+        auto go = [&](auto dd) {
+            constexpr int D = decltype(dd)::value;
+            if (NT == 256) {
+                if (o->precision == LASP_PREC_TF32) return run_grouped<D, 1, 256>(G, tc, st, launches);
+                if (o->precision == LASP_PREC_BF16) return run_grouped<D, 2, 256>(G, tc, st, launches);
+                return run_grouped<D, 3, 256>(G, tc, st, launches);
+            }
+            if (o->precision == LASP_PREC_TF32) return run_grouped<D, 1, 512>(G, tc, st, launches);
+            if (o->precision == LASP_PREC_BF16) return run_grouped<D, 2, 512>(G, tc, st, launches);
+            return run_grouped<D, 3, 512>(G, tc, st, launches);
+        };
+        if (o->legendre_deg == 6) e = go(std::integral_constant<int, 6>{});
+        else e = LASP_EINVAL;
+    }
+    void* ptrs[] = {G.x, G.m, G.v, G.ring, G.prev, G.w, G.imean, G.loss, G.gmu, G.gsg, G.b, G.rise,
+                    G.t, G.flags, G.list[0], G.list[1], G.count, G.Fp, G.A_hi, G.A_lo, G.dphi};
+    for (void* p : ptrs)
+        if (p) cudaFreeAsync(p, st);
+    return e;
+}
+
+}  // namespace lasp

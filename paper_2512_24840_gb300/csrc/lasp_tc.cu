@@ -49,6 +49,35 @@ __global__ void build_images_kernel(const float* __restrict__ C, int K, int n_mo
     *reinterpret_cast<uint4*>(bf + off) = *reinterpret_cast<uint4*>(b);
 }
 
+// Backward table images: chunk c, row k (basis term), 16-byte piece q.
+__global__ void build_back_images_kernel(const float* __restrict__ C, int K, int n_model, int n_ch32,
+                                         int n_ch64, uint8_t* hi, uint8_t* lo, uint8_t* bf) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int total = n_ch32 * 32 * 8;
+    if (idx >= total) return;
+    const int q = idx & 7, k = (idx >> 3) & 31, c = idx >> 8;
+    const uint32_t off = (uint32_t)c * TC_BK_CHUNK_BYTES + tc::sw128_off(k, q);
+    float h[4], l[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int m = 32 * c + 4 * q + e;
+        const float v = (k < K && m < n_model) ? C[(size_t)k * n_model + m] : 0.0f;
+        h[e] = tc::to_tf32(v);
+        l[e] = tc::to_tf32(v - h[e]);
+    }
+    *reinterpret_cast<float4*>(hi + off) = make_float4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<float4*>(lo + off) = make_float4(l[0], l[1], l[2], l[3]);
+    if (c < n_ch64) {
+        __nv_bfloat16 b[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int m = 64 * c + 8 * q + e;
+            b[e] = __float2bfloat16_rn((k < K && m < n_model) ? C[(size_t)k * n_model + m] : 0.0f);
+        }
+        *reinterpret_cast<uint4*>(bf + off) = *reinterpret_cast<uint4*>(b);
+    }
+}
+
 // PREC: 1 TF32, 2 BF16, 3 split TF32 (hi*hi + hi*lo + lo*hi)
 template <int PREC>
 __global__ void __launch_bounds__(128) interp_tc_kernel(const ModelDev M, const float* __restrict__ theta,
@@ -206,11 +235,27 @@ int tc_build_images(TcImages& t, const float* C, int K, int n_model) {
     build_images_kernel<<<(total + 255) / 256, 256>>>(C, K, n_model, t.n_tiles, (uint8_t*)t.tf32_hi,
                                                        (uint8_t*)t.tf32_lo, (uint8_t*)t.bf16);
     rc = cuda_rc(cudaGetLastError());
+    if (rc) return rc;
+    t.n_chunks_tf32 = (n_model + 31) / 32;
+    t.n_chunks_bf16 = (n_model + 63) / 64;
+    const size_t bk = (size_t)t.n_chunks_tf32 * TC_BK_CHUNK_BYTES;
+    rc = cuda_rc(cudaMalloc(&t.bk_hi, bk));
+    if (!rc) rc = cuda_rc(cudaMalloc(&t.bk_lo, bk));
+    if (!rc) rc = cuda_rc(cudaMalloc(&t.bk_bf, bk));
+    if (rc) return rc;
+    const int tb = t.n_chunks_tf32 * 32 * 8;
+    build_back_images_kernel<<<(tb + 255) / 256, 256>>>(C, K, n_model, t.n_chunks_tf32, t.n_chunks_bf16,
+                                                         (uint8_t*)t.bk_hi, (uint8_t*)t.bk_lo,
+                                                         (uint8_t*)t.bk_bf);
+    rc = cuda_rc(cudaGetLastError());
     if (!rc) rc = cuda_rc(cudaDeviceSynchronize());
     return rc;
 }
 
 void tc_free_images(TcImages& t) {
+    if (t.bk_hi) cudaFree(t.bk_hi);
+    if (t.bk_lo) cudaFree(t.bk_lo);
+    if (t.bk_bf) cudaFree(t.bk_bf);
     if (t.tf32_hi) cudaFree(t.tf32_hi);
     if (t.tf32_lo) cudaFree(t.tf32_lo);
     if (t.bf16) cudaFree(t.bf16);
@@ -236,11 +281,6 @@ int lasp_tc_interp_eval(const ModelDev& M, const TcImages& t, int N, const float
     else return LASP_EINVAL;
     if (!rc) *launches = 1;
     return rc;
-}
-
-int lasp_tc_fit_batch(const ModelDev&, const TcImages&, const lasp_batch*, const lasp_fit_opts*,
-                      lasp_result*, void*, int*) {
-    return LASP_EINVAL;
 }
 
 }  // namespace lasp

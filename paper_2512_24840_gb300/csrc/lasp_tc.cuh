@@ -21,7 +21,16 @@ struct TcImages {
     void* bf16 = nullptr;
     int n_tiles = 0;
     int* err = nullptr;                 // device flag: bounded wait timed out
+    // Backward images (dphi = dF' C^T): per chunk of model pixels (32 for TF32,
+    // 64 for BF16) a 32-row (basis term) x 128-byte tile, K-major in pixels,
+    // 128-byte swizzle (4 KB per chunk).
+    void* bk_hi = nullptr;
+    void* bk_lo = nullptr;
+    void* bk_bf = nullptr;
+    int n_chunks_tf32 = 0;
+    int n_chunks_bf16 = 0;
 };
+constexpr int TC_BK_CHUNK_BYTES = 32 * 128;
 
 int tc_build_images(TcImages& t, const float* C, int K, int n_model);
 void tc_free_images(TcImages& t);
