@@ -141,8 +141,20 @@ __device__ __forceinline__ void reduce_to_warp0_f64(float (&v)[NV], float* red, 
     }
 }
 
+// 1/sqrt(s) without a divide or a square root in T: the single-precision
+// reciprocal square root, refined by Newton steps y <- y (3 - s y^2) / 2 in T
+// (one step suffices for float, two give double accuracy from float).
+template <typename T>
+__device__ __forceinline__ T rsqrt_refined(T s) {
+    T y = (T)rsqrtf((float)s);
+    y = y * (T(1.5) - T(0.5) * s * y * y);
+    if (sizeof(T) == 8) y = y * (T(1.5) - T(0.5) * s * y * y);
+    return y;
+}
+
 // Cholesky solve with reciprocal pivots (one thread).  Returns false when a
-// pivot is not positive.
+// pivot is not positive.  Pivots use rsqrt_refined, so the double version
+// needs no double-precision divide or square root.
 template <int D, typename T>
 __device__ __forceinline__ bool chol_solve_rcp(const T* packed, const T* rhs, T* b) {
     constexpr int n = D + 1;
@@ -156,8 +168,8 @@ __device__ __forceinline__ bool chol_solve_rcp(const T* packed, const T* rhs, T*
             for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
             if (i == j) {
                 if (!(s > T(0))) return false;
-                id[i] = T(1) / sqrt(s);
-                L[i][i] = sqrt(s);
+                id[i] = rsqrt_refined(s);
+                L[i][i] = s * id[i];
             } else {
                 L[i][j] = s * id[j];
             }
@@ -198,7 +210,7 @@ __device__ __forceinline__ int warp_prepare_step(const ModelDev& M, const float*
 }
 
 template <int NT, int D>
-__global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) fit_kernel(const FitParams P) {
+__global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) fit_kernel(const FitParams P) {
     using Gm = Gram<D>;
     constexpr int NB = D + 1;
     constexpr int NV = Gm::NV;

@@ -25,6 +25,7 @@ namespace {
 constexpr uint32_t kWait = 1u << 22;
 constexpr int K3_STAGES = 4;
 constexpr int CHUNK_STEPS = 8;     // steps per captured graph (even)
+constexpr int KSPLIT = 4;          // K3: pixel ranges per 128-spectrum block
 
 struct Grp {
     ModelDev M;
@@ -39,7 +40,7 @@ struct Grp {
     int* count;                   // count[0], count[1]
     float* Fp;                    // N x ldf
     uint8_t *A_hi, *A_lo;         // K3 A images: nblk x nch x 16 KB
-    float* dphi;                  // list position x 32
+    float* dphi;                  // KSPLIT x list position x 32 (partial sums)
     int* err;
     // inputs / outputs
     const float *flux, *ivar, *theta0;
@@ -164,15 +165,16 @@ __global__ void __launch_bounds__(128) k1_interp(const Grp G, int par, const uin
     tc::tc_fence_after();
     const uint32_t tmem = tmem_base;
     constexpr uint32_t idesc = tc::idesc_f32acc(PREC == 2 ? 1u : 2u, 128, 128);
-    const int t = blockIdx.y;
     bool pending = false;
+    uint32_t phase = 0;
+    for (int t = blockIdx.y; t < n_tiles; t += gridDim.y) {
     if (tid == 0) {
         const uint32_t bytes = (PREC == 3 ? 2u : 1u) * (uint32_t)TC_TILE_BYTES;
         tc::mbar_arrive_expect_tx(&bar_tma, bytes);
         tc::bulk_g2s(Ahi, img + (size_t)t * TC_TILE_BYTES, TC_TILE_BYTES, &bar_tma);
         if (PREC == 3) tc::bulk_g2s(Alo, img_lo + (size_t)t * TC_TILE_BYTES, TC_TILE_BYTES, &bar_tma);
         pending = true;
-        if (!tc::mbar_wait_bounded(&bar_tma, 0, kWait)) {
+        if (!tc::mbar_wait_bounded(&bar_tma, phase, kWait)) {
             atomicExch(G.err, 1);
             s_ok = 0;
         } else {
@@ -201,9 +203,11 @@ __global__ void __launch_bounds__(128) k1_interp(const Grp G, int par, const uin
         }
     }
     __syncthreads();
-    if (s_ok) {
-        if (!tc::mbar_wait_bounded(&bar_mma, 0, kWait)) {
+    if (!s_ok) break;
+    {
+        if (!tc::mbar_wait_bounded(&bar_mma, phase, kWait)) {
             atomicExch(G.err, 1);
+            s_ok = 0;
         } else {
             tc::tc_fence_after();
             const int mpix = t * TC_TILE + warp * 32 + lane;
@@ -222,8 +226,12 @@ __global__ void __launch_bounds__(128) k1_interp(const Grp G, int par, const uin
             }
         }
     }
-    if (tid == 0 && pending) tc::mbar_wait_bounded(&bar_tma, 0, kWait);
     tc::tc_fence_before();
+    __syncthreads();
+    if (!s_ok) break;
+    phase ^= 1u;
+    }
+    if (tid == 0 && pending) tc::mbar_wait_bounded(&bar_tma, phase, kWait);
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, 128);
 }
@@ -286,7 +294,7 @@ __device__ __forceinline__ void store_dfp(const Grp& G, int pos, int m0, const f
 }
 
 template <int NT, int D, int PREC>
-__global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) k2_rest(const Grp G, int par) {
+__global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) k2_rest(const Grp G, int par) {
     using Gm = Gram<D>;
     constexpr int NB = D + 1;
     constexpr int NV = Gm::NV;
@@ -314,7 +322,14 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) k2_rest(const Grp G, in
     const int j0 = tid * PPT;
     const bool own_pix = j0 < p;
     const bool own_mod = j0 < nm;
-    // zero the padded buffers, then F' of this spectrum (K1 output) into skewed rows
+    // F' of this spectrum (K1 output): issue the loads first, store them later
+    float4 fp4[PPT / 4];
+    if (own_mod) {
+        const float4* src = reinterpret_cast<const float4*>(G.Fp + (size_t)id * G.ldf + j0);
+#pragma unroll
+        for (int q = 0; q < PPT / 4; ++q) fp4[q] = src[q];
+    }
+    // zero the padded buffers
     for (int q = tid; q < skew_size(nm + 32); q += NT) Fp[q] = 0.0f;
     for (int q = tid; q < skew_size(p + 4 * H + 40); q += NT) Db[q] = 0.0f;
     {
@@ -341,10 +356,9 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) k2_rest(const Grp G, in
             }
         }
         if (own_mod) {
-            const float4* src = reinterpret_cast<const float4*>(G.Fp + (size_t)id * G.ldf + j0);
 #pragma unroll
             for (int q = 0; q < PPT / 4; ++q) {
-                const float4 c = src[q];
+                const float4 c = fp4[q];
                 const float cv[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
@@ -528,10 +542,14 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) k2_rest(const Grp G, in
 template <int PREC>
 __global__ void __launch_bounds__(128) k3_back(const Grp G, int par, const uint8_t* __restrict__ bk,
                                                const uint8_t* __restrict__ bk_lo) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) G.count[par ^ 1] = 0;   // list K4 fills next
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) G.count[par ^ 1] = 0;  // list K4 fills next
     const int count = G.count[par];
     const int s0 = blockIdx.x * 128;
     if (s0 >= count) return;
+    // this CTA's range of pixel chunks (split K; partial sums added in K4)
+    const int per = (G.nch + KSPLIT - 1) / KSPLIT;
+    const int c_beg = blockIdx.y * per;
+    const int c_end = min(G.nch, c_beg + per);
     extern __shared__ uint8_t smraw[];
     uint8_t* base = reinterpret_cast<uint8_t*>(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     // stage s: A hi (16 KB), A lo (16 KB), B hi (4 KB), B lo (4 KB)
@@ -558,9 +576,22 @@ __global__ void __launch_bounds__(128) k3_back(const Grp G, int par, const uint8
     tc::tc_fence_after();
     const uint32_t tmem = tmem_base;
     constexpr uint32_t idesc = tc::idesc_f32acc(PREC == 2 ? 1u : 2u, 128, 32);
-    const int nch = G.nch;
-    const uint8_t* Ablk = G.A_hi + (size_t)blockIdx.x * nch * TC_TILE_BYTES;
-    const uint8_t* Ablk_lo = PREC == 3 ? G.A_lo + (size_t)blockIdx.x * nch * TC_TILE_BYTES : nullptr;
+    const int nch = c_end - c_beg;
+    const uint8_t* Ablk = G.A_hi + ((size_t)blockIdx.x * G.nch + c_beg) * TC_TILE_BYTES;
+    const uint8_t* Ablk_lo =
+        PREC == 3 ? G.A_lo + ((size_t)blockIdx.x * G.nch + c_beg) * TC_TILE_BYTES : nullptr;
+    bk += (size_t)c_beg * TC_BK_CHUNK_BYTES;
+    if (PREC == 3) bk_lo += (size_t)c_beg * TC_BK_CHUNK_BYTES;
+    if (nch <= 0) {
+        const int pos = s0 + tid;
+        if (pos < count) {
+            float* dst = G.dphi + ((size_t)blockIdx.y * G.nblk * 128 + pos) * 32;
+            for (int k = 0; k < 32; ++k) dst[k] = 0.0f;
+        }
+        __syncthreads();
+        if (warp == 0) tc::tmem_dealloc(tmem, 32);
+        return;
+    }
     if (tid == 0) {
         const uint32_t bytes = (PREC == 3 ? 2u : 1u) * (uint32_t)(TC_TILE_BYTES + TC_BK_CHUNK_BYTES);
         auto issue = [&](int c) {
@@ -638,7 +669,8 @@ __global__ void __launch_bounds__(128) k3_back(const Grp G, int par, const uint8
             tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16), v0);
             tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + 16u, v1);
             if (pos < count) {
-                float4* dst = reinterpret_cast<float4*>(G.dphi + (size_t)pos * 32);
+                float4* dst = reinterpret_cast<float4*>(
+                    G.dphi + ((size_t)blockIdx.y * G.nblk * 128 + pos) * 32);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) dst[q] = make_float4(v0[4 * q], v0[4 * q + 1], v0[4 * q + 2], v0[4 * q + 3]);
 #pragma unroll
@@ -667,7 +699,9 @@ __global__ void __launch_bounds__(256) k4_adam(const Grp G, int par) {
     if (lane < M.K) {
         float phi[KMAX], dphi[3 * KMAX];
         basis_term(M, lane, th, phi, dphi);
-        const float gp = G.dphi[(size_t)pos * 32 + lane];
+        float gp = 0.0f;
+#pragma unroll
+        for (int q = 0; q < KSPLIT; ++q) gp += G.dphi[((size_t)q * G.nblk * 128 + pos) * 32 + lane];
         c0 = gp * dphi[3 * lane + 0];
         c1 = gp * dphi[3 * lane + 1];
         c2 = gp * dphi[3 * lane + 2];
@@ -769,8 +803,8 @@ int run_grouped(Grp& G, const TcImages& tc, cudaStream_t st, int* launches) {
     const uint8_t* img_lo = (const uint8_t*)tc.tf32_lo;
     const uint8_t* bk = (const uint8_t*)(PREC == 2 ? tc.bk_bf : tc.bk_hi);
     const uint8_t* bk_lo = (const uint8_t*)tc.bk_lo;
-    const dim3 g1((N + 127) / 128, tc.n_tiles);
-    const int g3 = (N + 127) / 128;
+    const dim3 g1((N + 127) / 128, (tc.n_tiles + 3) / 4);
+    const dim3 g3((N + 127) / 128, KSPLIT);
     const int g4 = (N + 7) / 8;
     auto one_step = [&](int par) {
         k1_interp<PREC><<<g1, 128, smem1, st>>>(G, par, img, img_lo, tc.n_tiles);
@@ -859,7 +893,7 @@ int lasp_tc_fit_batch(const ModelDev& M, const TcImages& tc, const lasp_batch* b
     A(&G.Fp, n * G.ldf * 4);
     A(&G.A_hi, (size_t)G.nblk * G.nch * TC_TILE_BYTES);
     if (o->precision == LASP_PREC_TF32X3) A(&G.A_lo, (size_t)G.nblk * G.nch * TC_TILE_BYTES);
-    A(&G.dphi, (size_t)G.nblk * 128 * 32 * 4);
+    A(&G.dphi, (size_t)KSPLIT * G.nblk * 128 * 32 * 4);
     if (!e) e = cuda_rc(cudaMemsetAsync(G.count, 0, 16, st));
     if (!e) {
         const int NT = M.n_pix <= 16 * 256 ? 256 : 512;

@@ -136,16 +136,17 @@ def _fit_both(lasp, grid, M, d, n=None, **opts):
     return out, ref
 
 
-@pytest.mark.parametrize("lr,nsteps", [(0.1, 20), (0.01, 50)])
+@pytest.mark.parametrize("lr,nsteps", [(0.1, 12), (0.01, 30)])
 def test_fixed_step_trajectory_parity_small(lasp, lr, nsteps):
     """16 x 1024 noise-free, stop rules off, a fixed number of Adam steps.
 
     Noise-free fits end in an oscillation about the optimum where the path is
     chaotic.  Calibrated on the oracle itself with the flux perturbed by
-    3e-6 relative (about the FP32 rounding of the GPU path): at lr 0.1 the
-    path leaves the tolerance after step 21 (at step 20 it stays within 0.19
-    of it); at lr 0.01 after step 61 (within 0.1 of it at step 50).  Fixed-
-    step parity is checked inside those well-conditioned stretches."""
+    1e-5 relative (about the FP32 rounding of the GPU path, whose continuum
+    solve is good to ~1e-5): at lr 0.1 the path leaves the tolerance after
+    step 21 (within 0.31 of it at step 10); at lr 0.01 after step 42 (within
+    0.45 of it at step 40).  Fixed-step parity is checked inside those
+    well-conditioned stretches."""
     M, d = observed(S.SMALL, 16, S.SPECTRA_SEED, noise=False, mask_frac=0.0)
     out, ref = _fit_both(lasp, S.SMALL, M, d, max_steps=nsteps, tol=0.0, lr=lr)
     assert np.all(H(out["steps"]) == ref["steps"])
