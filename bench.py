@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=192)
     return ap.parse_args()
 
@@ -122,6 +123,87 @@ def algorithmic_flops(theta, steps, grid, K=26, D=DEG):
     per_px = 2 * nb * (nb + 1) // 2 + 2 * nb + 4 * D + 2 * nb + 8
     per = 4 * K * nm + 6 * T * p + 2 * T * nm + per_px * p
     return float((per * (steps + 1)).sum())
+
+
+def aggregate(dist, torch, device, ms, conv):
+    """Max step time and total converged count over ranks (replicas)."""
+    if dist is None:
+        return ms, conv
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([int(conv)], device=device, dtype=torch.int64)
+    dist.all_reduce(c)
+    return float(t.item()), int(c.item())
+
+
+def served_stream(torch, lasp, grids, tables, seconds=2.0, loads=(0.5, 0.8, 0.95), burst=6144):
+    """Continuous batching of a LAMOST-like / DESI-like request mix (50/50,
+    random masks 0-20%, SNR 5-100).  The saturated rate is the drain rate of
+    a burst; then Poisson arrivals at fractions of it for `seconds` each.
+    Latency: submit -> result on host."""
+    import threading
+    from paper_2512_24840_gb300.server import Server, latency_percentiles
+    from paper_2512_24840_gb300.server import DevicePool
+    ips = {g.name: lasp.Interp.from_grid(g, tables[g.name], S.EXPS, S.BASIS_LO, S.BASIS_HI,
+                                         S.BOX_LO, S.BOX_HI) for g in grids}
+    pool = {}
+    dev = torch.device("cuda")
+    for k, g in enumerate(grids):
+        d = S.draw_batch(g, 1024, S.SPECTRA_SEED + 5 + k, snr=(5, 100), mask_frac=0.0, mask_frac_max=0.2)
+        model = ips[g.name].forward(torch.tensor(d["truth"], dtype=torch.float32, device=dev),
+                                    torch.tensor(d["b_true"], dtype=torch.float32, device=dev))
+        flux, ivar = S.finish_obs(model.double().cpu().numpy(), d)
+        pool[g.name] = (flux, ivar, d["good"], np.asarray(d["theta0"], np.float32))
+    budget = 2 * burst * max(DevicePool.bytes_per_slot(g.n_pix) for g in grids)
+    srv = Server.on_device(ips, hbm_budget_bytes=budget, chunk=25, max_steps=MAX_STEPS)
+    names = [g.name for g in grids]
+    rng = np.random.default_rng(7)
+
+    def submit(n):
+        for _ in range(n):
+            lane = names[rng.integers(len(names))]
+            f, iv, gd, th = pool[lane]
+            i = rng.integers(len(f))
+            srv.submit(lane, f[i], iv[i], gd[i], th[i])
+
+    submit(512)                                   # warm-up
+    srv.run_until_idle()
+    submit(burst)
+    t0 = time.perf_counter()
+    res = srv.run_until_idle()
+    sat = len(res) / (time.perf_counter() - t0)
+    levels = []
+    for load in loads:
+        rate = load * sat
+        stop = threading.Event()
+        done = []
+
+        def producer():
+            t_next = time.perf_counter()
+            while not stop.is_set():
+                t_next += rng.exponential(1.0 / rate)
+                dt = t_next - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                submit(1)
+
+        th = threading.Thread(target=producer, daemon=True)
+        t0 = time.perf_counter()
+        th.start()
+        while time.perf_counter() - t0 < seconds:
+            done += srv.tick()
+            if not srv.pending():
+                time.sleep(0.0005)
+        stop.set()
+        th.join()
+        done += srv.run_until_idle()
+        elapsed = time.perf_counter() - t0
+        conv = sum(1 for r in done if r.status & 3)
+        levels.append({"load": load, "offered_per_s": rate, "served_per_s": len(done) / elapsed,
+                       "converged_per_s": conv / elapsed, "n": len(done), **latency_percentiles(done)})
+    srv.close()
+    return {"saturated_per_s": sat, "chunk_steps": 25, "lanes": names,
+            "slots": {n: l.pool.n_slots for n, l in srv.lanes.items()}, "levels": levels}
 
 
 def make_inputs(rank, torch, lasp, grid, C):
@@ -201,15 +283,7 @@ def run_ours(args):
     steps_np = out["steps"].cpu().numpy()
     theta_np = out["theta"].double().cpu().numpy()
     conv = int(((status & 3) != 0).sum())
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        c = torch.tensor([conv], device=dev, dtype=torch.int64)
-        dist.all_reduce(c)
-        conv_all = int(c.item())
-    else:
-        conv_all = conv
+    ms, conv_all = aggregate(dist, torch, dev, ms, conv)
     value = conv_all / (ms / 1e3)
 
     # ---- end to end through the public API from pinned host buffers
@@ -240,15 +314,8 @@ def run_ours(args):
         if k >= args.warmup:
             e2e.append(a.elapsed_time(b))
     e2e_ms = sum(e2e) / len(e2e)
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
     e2e_conv = int(((h_status.numpy() & 3) != 0).sum())
-    if dist:
-        c = torch.tensor([e2e_conv], device=dev, dtype=torch.int64)
-        dist.all_reduce(c)
-        e2e_conv = int(c.item())
+    e2e_ms, e2e_conv = aggregate(dist, torch, dev, e2e_ms, e2e_conv)
 
     # ---- mixed precision: grouped tensor-core pipeline (split TF32 and single-pass
     # TF32 contractions, FP64 normal equations), same batch, device-resident inputs
@@ -306,6 +373,9 @@ def run_ours(args):
         "clocks": clocks,
         "mixed": mixed,
     }
+    if rank == 0 and not args.no_served:
+        res["served"] = served_stream(torch, lasp, [S.LAMOST, S.DESI],
+                                      {S.LAMOST.name: C, S.DESI.name: S.make_table(S.DESI)})
     if rank == 0 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(args.cpu_sample, grid, C, ip, torch)
     if rank == 0:
