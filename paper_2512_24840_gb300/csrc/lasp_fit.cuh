@@ -61,6 +61,7 @@ struct FitParams {
 };
 
 __host__ __device__ constexpr int skew(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int round32(int n) { return (n + 31) & ~31; }
 __host__ __device__ constexpr int skew_size(int n) { return ((skew(n) + 4) + 3) & ~3; }
 
 // Shared-memory plan (floats).  Fp holds model pixels m in [-16, n_model+16)
@@ -70,7 +71,7 @@ struct FitSmem {
     int y, W, Fp, Db, g, gmu, gsg, phi, dphi, red, out, ring, total, dofs;
     __host__ __device__ FitSmem(int p, int H, int n_model, int NT, int D) {
         const int NB = D + 1, NV = NB * (NB + 1) / 2 + NB;
-        const int nv_max = NV > (KMAX + 2) ? NV : (KMAX + 2);
+        const int nv_max = round32(NV > (KMAX + 4) ? NV : (KMAX + 4));
         dofs = 2 * H + 8;
         int o = 0;
         y = o;    o += skew_size(p);
@@ -95,25 +96,48 @@ __host__ inline size_t fit_smem_bytes(int p, int H, int n_model, int NT, int D) 
     return 4 * ((size_t)s.total > sort_end ? (size_t)s.total : sort_end);
 }
 
+// Warp reduce-scatter of 32 values (butterfly transpose): afterwards v[0] of
+// lane l holds the warp sum of value l.  31 shuffles instead of 5 x 32.
+__device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const bool up = (lane & w) != 0;
+#pragma unroll
+        for (int i = 0; i < w; ++i) {
+            const float send = up ? v[i] : v[i + w];
+            const float keep = up ? v[i + w] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+        }
+    }
+    return v[0];
+}
+
 // Reduce NV per-thread values over the CTA; the sums end in out[0..NV) and
-// are visible to warp 0 only (after __syncwarp), with one CTA barrier.
+// are visible to warp 0 only (after __syncwarp), with one CTA barrier.  Each
+// warp reduce-scatters groups of 32 values, then warp 0 adds the warps in a
+// fixed order, so the result depends only on this CTA's data.  red holds
+// (NT/32) x round32(NV) floats.
 template <int NV, int NT>
 __device__ __forceinline__ void reduce_to_warp0(float (&v)[NV], float* red, float* out) {
+    constexpr int NP = round32(NV);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int i = 0; i < NV; ++i) {
-        float s = v[i];
+    for (int g = 0; g < NP / 32; ++g) {
+        float t[32];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) red[warp * NV + i] = s;
+        for (int i = 0; i < 32; ++i) t[i] = (32 * g + i < NV) ? v[32 * g + i] : 0.0f;
+        red[warp * NP + 32 * g + lane] = warp_reduce_scatter32(t);
     }
     __syncthreads();
     if (warp == 0) {
-        for (int i = lane; i < NV; i += 32) {
+#pragma unroll
+        for (int g = 0; g < NP / 32; ++g) {
+            const int i = 32 * g + lane;
             float s = 0.0f;
 #pragma unroll
-            for (int w = 0; w < NT / 32; ++w) s += red[w * NV + i];
-            out[i] = s;
+            for (int w = 0; w < NT / 32; ++w) s += red[w * NP + i];
+            if (i < NV) out[i] = s;
         }
         __syncwarp();
     }
@@ -121,21 +145,24 @@ __device__ __forceinline__ void reduce_to_warp0(float (&v)[NV], float* red, floa
 
 template <int NV, int NT>
 __device__ __forceinline__ void reduce_to_warp0_f64(float (&v)[NV], float* red, double* outd) {
+    constexpr int NP = round32(NV);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int i = 0; i < NV; ++i) {
-        float s = v[i];
+    for (int g = 0; g < NP / 32; ++g) {
+        float t[32];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) red[warp * NV + i] = s;
+        for (int i = 0; i < 32; ++i) t[i] = (32 * g + i < NV) ? v[32 * g + i] : 0.0f;
+        red[warp * NP + 32 * g + lane] = warp_reduce_scatter32(t);
     }
     __syncthreads();
     if (warp == 0) {
-        for (int i = lane; i < NV; i += 32) {
+#pragma unroll
+        for (int g = 0; g < NP / 32; ++g) {
+            const int i = 32 * g + lane;
             double s = 0.0;
 #pragma unroll
-            for (int w = 0; w < NT / 32; ++w) s += (double)red[w * NV + i];
-            outd[i] = s;
+            for (int w = 0; w < NT / 32; ++w) s += (double)red[w * NP + i];
+            if (i < NV) outd[i] = s;
         }
         __syncwarp();
     }
@@ -467,19 +494,16 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) fit_kernel(const FitPar
             }
             if (!solved) racc[0] = NAN;
         }
-        reduce_to_warp0<2, NT>(racc, red, out);
-        __shared__ float s_l, s_nonpos;
-        if (tid == 0) {
-            s_l = sqrtf(out[0] * inv_p);
-            s_nonpos = out[1];
-        }
-        __syncthreads();
-        const float l = s_l;
+        __syncthreads();     // delta buffer complete
 
-        // ---- a7: adjoint.  (i) a_s = sum_j delta_j F'_{j+H-s}; d l/d mu = k sum_s gmu_s a_s
-        float bacc[2 + KMAX];
+        // ---- a7: adjoint, unscaled (dl/dF'' = kappa * delta with kappa = -1/(p l)
+        // applied after the reduction).  (i) a_s = sum_j delta_j F'_{j+H-s};
+        // d l/d mu = kappa sum_s gmu_s a_s.  bacc = [S, nonpos, mu, sigma, phi...]
+        float bacc[4 + KMAX];
+        bacc[0] = racc[0];
+        bacc[1] = racc[1];
 #pragma unroll
-        for (int q = 0; q < 2 + KMAX; ++q) bacc[q] = 0.0f;
+        for (int q = 2; q < 4 + KMAX; ++q) bacc[q] = 0.0f;
         if (own_pix) {
             for (int bk = 0; bk < nblk; ++bk) {
                 const int s0 = -h + bk * TB;
@@ -496,8 +520,8 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) fit_kernel(const FitPar
                     for (int e = 0; e < TB; ++e) a[e] = fmaf(fpp[r], win[r - e + TB - 1], a[e]);
 #pragma unroll
                 for (int e = 0; e < TB; ++e) {
-                    bacc[0] = fmaf(gmu[s0 + e + H], a[e], bacc[0]);
-                    bacc[1] = fmaf(gsg[s0 + e + H], a[e], bacc[1]);
+                    bacc[2] = fmaf(gmu[s0 + e + H], a[e], bacc[2]);
+                    bacc[3] = fmaf(gsg[s0 + e + H], a[e], bacc[3]);
                 }
             }
         }
@@ -534,19 +558,21 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) fit_kernel(const FitPar
                         a = fmaf(dfp[4 * q + 2], c.z, a);
                         a = fmaf(dfp[4 * q + 3], c.w, a);
                     }
-                    bacc[2 + k] = a;
+                    bacc[4 + k] = a;
                 }
             }
         }
-        reduce_to_warp0<2 + KMAX, NT>(bacc, red, out);
+        reduce_to_warp0<4 + KMAX, NT>(bacc, red, out);
 
         // ---- a8: chain rule to x, stop rules, Adam; next step's basis + taps (warp 0)
         if (warp == 0) {
             // dl/dF''_j = -W eps c / (p l) with b held at its optimum (envelope theorem)
+            const float l = sqrtf(out[0] * inv_p);
+            const bool nonpos = out[1] > 0.0f;
             const float kappa = l > 0.0f ? -1.0f / ((float)p * l) : 0.0f;
             float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f;
             if (lane < K) {
-                const float gp = out[2 + lane];
+                const float gp = out[4 + lane];
                 c0 = gp * dphi[3 * lane + 0];
                 c1 = gp * dphi[3 * lane + 1];
                 c2 = gp * dphi[3 * lane + 2];
@@ -563,8 +589,8 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) fit_kernel(const FitPar
                 gx[0] = kappa * c0 * M.phalf[0];
                 gx[1] = kappa * c1 * M.phalf[1];
                 gx[2] = kappa * c2 * M.phalf[2];
-                gx[3] = kappa * out[0] / M.kms_px * M.phalf[3];
-                gx[4] = kappa * out[1] / M.kms_px * M.phalf[4];
+                gx[3] = kappa * out[2] / M.kms_px * M.phalf[3];
+                gx[4] = kappa * out[3] / M.kms_px * M.phalf[4];
                 uint32_t st = 0;
                 if (!isfinite(s_b[0])) st = 32u;
                 else {
@@ -583,7 +609,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) fit_kernel(const FitPar
                     prev = l;
                 }
                 if (st) {
-                    if (st <= 4u && s_nonpos > 0.0f) st |= 8u;
+                    if (st <= 4u && nonpos) st |= 8u;
                     for (int k = 0; k < 5; ++k) P.theta[5 * i + k] = phys_of(M, k, x[k]);
                     P.loss[i] = l;
                     P.steps[i] = t;

@@ -241,7 +241,7 @@ struct RestSmem {
     int y, W, Fp, Db, g, gmu, gsg, red, out, total, dofs;
     __host__ __device__ RestSmem(int p, int H, int n_model, int NT, int D) {
         const int NB = D + 1, NV = NB * (NB + 1) / 2 + NB;
-        const int nv_max = NV > 4 ? NV : 4;
+        const int nv_max = round32(NV > 4 ? NV : 4);
         dofs = 2 * H + 8;
         int o = 0;
         y = o;    o += skew_size(p);
@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) k2_rest(const Grp G, in
     float* red = sm + L.red;
     float* out = sm + L.out;
     double* outd = reinterpret_cast<double*>(sm + ((L.out + 1) & ~1));
-    __shared__ float s_b[NB], s_l;
+    __shared__ float s_b[NB];
     __shared__ int s_h;
 
     const int j0 = tid * PPT;
@@ -329,30 +329,44 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) k2_rest(const Grp G, in
 #pragma unroll
         for (int q = 0; q < PPT / 4; ++q) fp4[q] = src[q];
     }
-    // zero the padded buffers
-    for (int q = tid; q < skew_size(nm + 32); q += NT) Fp[q] = 0.0f;
-    for (int q = tid; q < skew_size(p + 4 * H + 40); q += NT) Db[q] = 0.0f;
+    // kernel taps (warp 0) while the other warps set up the spectrum
+    if (warp == 0) {
+        float th[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) th[k] = phys_of(M, k, G.x[5 * id + k]);
+        for (int q = 2 * H + 1 + lane; q < TAPBUF; q += 32) {
+            g[q] = 0.0f;
+            gmu[q] = 0.0f;
+            gsg[q] = 0.0f;
+        }
+        const int h = kernel_taps_warp(th[3] / M.kms_px, th[4] / M.kms_px, H, g, gmu, gsg);
+        if (lane == 0) s_h = h;
+    }
+    // zero only the pads of F' (model pixels [-16, 0) and [nm, nm + 16)) and of
+    // the delta buffer (j outside [0, p)); the interiors are overwritten
+    for (int q = tid; q < 32; q += NT) {
+        const int mm = q < 16 ? q - 16 : nm + q - 16;
+        Fp[skew(mm + 16)] = 0.0f;
+    }
+    for (int q = tid; q < L.dofs + 2 * H + 32; q += NT) {
+        const int j = q < L.dofs ? q - L.dofs : p + q - L.dofs;
+        Db[skew(j + L.dofs)] = 0.0f;
+    }
+    // y = flux / w and W = ivar / mean(ivar) on the thread's own pixels (the
+    // arithmetic of the preprocessing), straight into skewed rows
     {
         const size_t row = (size_t)id * p;
-        refill_spectrum<NT>(G.flux + row, G.ivar + row, G.good + row, p, G.O.edge_px, G.w[id],
-                            G.imean[id], y, W, red);
-    }
-    __syncthreads();
-    {
-        float ty[PPT], tw[PPT];
-#pragma unroll
-        for (int r = 0; r < PPT; ++r) {
-            const int j = j0 + r;
-            ty[r] = j < p ? y[j] : 0.0f;
-            tw[r] = j < p ? W[j] : 0.0f;
-        }
-        __syncthreads();
+        const float w = G.w[id], imean = G.imean[id];
 #pragma unroll
         for (int r = 0; r < PPT; ++r) {
             const int j = j0 + r;
             if (j < p) {
-                y[skew(j)] = ty[r];
-                W[skew(j)] = tw[r];
+                const float f = G.flux[row + j], iv = G.ivar[row + j];
+                const bool use = G.good[row + j] && iv > 0.0f && isfinite(f) && isfinite(iv);
+                const bool edge = j < G.O.edge_px || j >= p - G.O.edge_px;
+                const bool ok = use && !edge && w > 0.0f;
+                y[skew(j)] = ok ? f / w : 0.0f;
+                W[skew(j)] = ok ? iv / imean : 0.0f;
             }
         }
         if (own_mod) {
@@ -365,18 +379,6 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) k2_rest(const Grp G, in
                     if (j0 + 4 * q + e < nm) Fp[skew(j0 + 4 * q + e + 16)] = cv[e];
             }
         }
-    }
-    if (warp == 0) {
-        float th[5];
-#pragma unroll
-        for (int k = 0; k < 5; ++k) th[k] = phys_of(M, k, G.x[5 * id + k]);
-        for (int q = 2 * H + 1 + lane; q < TAPBUF; q += 32) {
-            g[q] = 0.0f;
-            gmu[q] = 0.0f;
-            gsg[q] = 0.0f;
-        }
-        const int h = kernel_taps_warp(th[3] / M.kms_px, th[4] / M.kms_px, H, g, gmu, gsg);
-        if (lane == 0) s_h = h;
     }
     __syncthreads();
     const int h = s_h;
@@ -473,17 +475,10 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) k2_rest(const Grp G, in
         }
         if (!solved) racc[0] = NAN;
     }
-    reduce_to_warp0<2, NT>(racc, red, out);
-    if (tid == 0) {
-        s_l = sqrtf(out[0] / (float)p);
-        G.loss[id] = s_l;
-        G.flags[id] = (out[1] > 0.0f ? 1 : 0) | (isfinite(s_b[0]) ? 0 : 2);
-#pragma unroll
-        for (int a = 0; a < NB; ++a) G.b[(size_t)id * NB + a] = s_b[a];
-    }
-    __syncthreads();
-    // adjoint of the kernel parameters through a_s = sum_j delta_j F'_{j+H-s}
-    float bacc[2] = {0.0f, 0.0f};
+    __syncthreads();     // delta buffer complete
+    // adjoint of the kernel parameters through a_s = sum_j delta_j F'_{j+H-s};
+    // bacc = [S, nonpos, mu, sigma] reduced together at the end
+    float bacc[4] = {racc[0], racc[1], 0.0f, 0.0f};
     if (own_pix) {
         for (int bk = 0; bk < nblk; ++bk) {
             const int s0 = -h + bk * TB;
@@ -500,8 +495,8 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) k2_rest(const Grp G, in
                 for (int e = 0; e < TB; ++e) a[e] = fmaf(fpp[r], win[r - e + TB - 1], a[e]);
 #pragma unroll
             for (int e = 0; e < TB; ++e) {
-                bacc[0] = fmaf(gmu[s0 + e + H], a[e], bacc[0]);
-                bacc[1] = fmaf(gsg[s0 + e + H], a[e], bacc[1]);
+                bacc[2] = fmaf(gmu[s0 + e + H], a[e], bacc[2]);
+                bacc[3] = fmaf(gsg[s0 + e + H], a[e], bacc[3]);
             }
         }
     }
@@ -531,10 +526,14 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) k2_rest(const Grp G, in
         }
         store_dfp<PREC>(G, pos, j0, dfp);
     }
-    reduce_to_warp0<2, NT>(bacc, red, out);
+    reduce_to_warp0<4, NT>(bacc, red, out);
     if (tid == 0) {
-        G.gmu[id] = out[0];
-        G.gsg[id] = out[1];
+        G.loss[id] = sqrtf(out[0] / (float)p);
+        G.flags[id] = (out[1] > 0.0f ? 1 : 0) | (isfinite(s_b[0]) ? 0 : 2);
+#pragma unroll
+        for (int a = 0; a < NB; ++a) G.b[(size_t)id * NB + a] = s_b[a];
+        G.gmu[id] = out[2];
+        G.gsg[id] = out[3];
     }
 }
 
