@@ -225,6 +225,21 @@ int lasp_interp_eval(lasp_interp h, int N, const float* theta, float* Fp, int pr
 int lasp_interp_eval_static(const lasp_interp_desc* desc, const float* coeff, int N,
                             const float* theta, float* Fp, int precision, void* stream);
 
+/* Flux-conserving resampling of an interpolator table from a linear
+ * wavelength grid onto the library's ln-lambda grid (section 2.2 stage 3,
+ * Eqs. 2-4).  The operation is linear in the flux and does not depend on
+ * theta, so it is applied once to every table row and the resampled table is
+ * then passed to lasp_init_interp (zero cost per Adam step).
+ * coeff_lin: device K x q float32, model pixel k centred at lam1 + k dlam
+ * (Angstrom) with edges at +- dlam/2.  coeff_out: device K x n_out float32,
+ * output pixel i centred at exp(ln_lam0 + i dln) with edges at
+ * exp(ln_lam0 + (i +- 1/2) dln).  Each output is the mean flux of the
+ * piecewise-constant model over its bin -- exactly the difference of the
+ * cumulative integral interpolated at the bin edges (Eqs. 2-4) -- computed as
+ * overlap integrals in FP64; no flux outside the model range.  Asynchronous. */
+int lasp_resample_linear(int K, int q, double lam1, double dlam, const float* coeff_lin, int n_out,
+                         double ln_lam0, double dln, float* coeff_out, void* stream);
+
 /* Number of kernels the last call on this thread enqueued (for accounting). */
 int lasp_last_launches(void);
 

@@ -525,3 +525,33 @@ out:
     free(y); free(W); free(r0); free(rp); free(rm); free(J);
     return st;
 }
+
+void orc_resample(int q, double lam1, double dlam, const double* F, int n_out, double ln_lam0,
+                  double dln, double* out) {
+    /* Eq. 2: cumulative integral at the q + 1 model edges */
+    double* cum = malloc(sizeof(double) * (q + 1));
+    cum[0] = 0.0;
+    for (int k = 0; k < q; ++k) cum[k + 1] = cum[k] + F[k] * dlam;
+    double e0 = lam1 - 0.5 * dlam;
+    /* Eq. 3: linear interpolation of the cumulative integral at a target edge */
+    double* edge_val = malloc(sizeof(double) * (n_out + 1));
+    double* edge = malloc(sizeof(double) * (n_out + 1));
+    for (int i = 0; i <= n_out; ++i) {
+        double x = exp(ln_lam0 + (i - 0.5) * dln);
+        edge[i] = x;
+        double u = (x - e0) / dlam;            /* position in model-edge units */
+        if (u <= 0.0) edge_val[i] = cum[0];
+        else if (u >= q) edge_val[i] = cum[q];
+        else {
+            int k = (int)floor(u);
+            if (k >= q) k = q - 1;
+            double f = u - k;
+            edge_val[i] = cum[k] + f * (cum[k + 1] - cum[k]);
+        }
+    }
+    /* Eq. 4: difference over the edge spacing */
+    for (int i = 0; i < n_out; ++i) out[i] = (edge_val[i + 1] - edge_val[i]) / (edge[i + 1] - edge[i]);
+    free(cum);
+    free(edge_val);
+    free(edge);
+}

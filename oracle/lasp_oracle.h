@@ -113,6 +113,16 @@ unsigned orc_errors(const orc_model* M, const orc_opts* O, const float* flux,
                     const float* ivar, const unsigned char* good, const double* theta,
                     double* sigma, double* cov, double* jac_out);
 
+/* Flux-conserving resampling (section 2.2 stage 3, Eqs. 2-4) of a spectrum F
+ * on a linear grid lam_k = lam1 + k dlam (k = 0..q-1, pixel edges at
+ * lam_k -+ dlam/2) onto the ln grid ln(lam_i) = ln_lam0 + i dln (i = 0..n_out-1,
+ * bin edges at exp(ln_lam0 + (i -+ 1/2) dln)): cumulative integral of F at the
+ * model edges (Eq. 2), linear interpolation of it at the target edges (Eq. 3),
+ * difference over the edge spacing (Eq. 4).  Outside the model range the
+ * cumulative integral is held constant (no flux). */
+void orc_resample(int q, double lam1, double dlam, const double* F, int n_out, double ln_lam0,
+                  double dln, double* out);
+
 int orc_max_threads(void);
 
 #ifdef __cplusplus

@@ -77,6 +77,8 @@ def lib():
             _lib.orc_phys_from_x.argtypes = [P, P, P]
             _lib.orc_x_from_phys.argtypes = [P, P, P]
             _lib.orc_max_threads.restype = ct.c_int
+            _lib.orc_resample.argtypes = [ct.c_int, ct.c_double, ct.c_double, P, ct.c_int,
+                                          ct.c_double, ct.c_double, P]
         return _lib
 
 
@@ -245,3 +247,12 @@ def errors(M: Model, flux, ivar, good, theta, with_jac=False, **opts):
     st = lib().orc_errors(M.ref, ct.byref(O), _p(flux), _p(ivar), _p(good), _p(_f64(theta)),
                           _p(sig), _p(cov), _p(jac))
     return dict(sigma=sig, cov=cov.reshape(5, 5), status=int(st), jac=jac)
+
+
+def resample(F, lam1, dlam, n_out, ln_lam0, dln):
+    """Flux-conserving resampling of F (linear grid) onto a ln grid (Eqs. 2-4)."""
+    F = _f64(F)
+    out = np.zeros(int(n_out))
+    lib().orc_resample(len(F), float(lam1), float(dlam), _p(F), int(n_out), float(ln_lam0),
+                       float(dln), _p(out))
+    return out

@@ -506,3 +506,43 @@ int lasp_slots_fetch(lasp_slots s, float* theta, float* loss, int32_t* steps, ui
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Flux-conserving resampling (stage 3, Eqs. 2-4) as exact overlap integrals.
+
+namespace {
+
+__global__ void resample_kernel(int K, int q, double lam1, double dlam, const float* __restrict__ in,
+                                int n_out, double ln0, double dln, float* __restrict__ out) {
+    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)K * n_out) return;
+    const int k = (int)(idx / n_out), i = (int)(idx % n_out);
+    const double a = exp(ln0 + (i - 0.5) * dln), b = exp(ln0 + (i + 0.5) * dln);
+    const double e0 = lam1 - 0.5 * dlam;
+    long ka = (long)floor((a - e0) / dlam), kb = (long)floor((b - e0) / dlam);
+    if (ka < 0) ka = 0;
+    if (kb > q - 1) kb = q - 1;
+    double acc = 0.0;
+    const float* row = in + (size_t)k * q;
+    for (long m = ka; m <= kb; ++m) {
+        const double lo = fmax(a, e0 + m * dlam), hi = fmin(b, e0 + (m + 1) * dlam);
+        if (hi > lo) acc += (double)row[m] * (hi - lo);
+    }
+    out[(size_t)k * n_out + i] = (float)(acc / (b - a));
+}
+
+}  // namespace
+
+extern "C" int lasp_resample_linear(int K, int q, double lam1, double dlam, const float* coeff_lin,
+                                    int n_out, double ln_lam0, double dln, float* coeff_out,
+                                    void* stream) {
+    g_last_launches = 0;
+    if (K < 1 || q < 1 || n_out < 0 || !(dlam > 0.0) || !(dln > 0.0) || !(lam1 > 0.0)) return LASP_EINVAL;
+    if (n_out == 0) return LASP_OK;
+    if (!coeff_lin || !coeff_out) return LASP_EINVAL;
+    const long total = (long)K * n_out;
+    resample_kernel<<<(unsigned)((total + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+        K, q, lam1, dlam, coeff_lin, n_out, ln_lam0, dln, coeff_out);
+    g_last_launches = 1;
+    return cuda_err(cudaGetLastError());
+}

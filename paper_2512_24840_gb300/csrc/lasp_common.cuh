@@ -213,6 +213,57 @@ __device__ bool chol_solve_packed(const T* packed, const T* rhs, T* b) {
     return true;
 }
 
+// 1/sqrt(s) without a divide or a square root in T: the single-precision
+// reciprocal square root, refined by Newton steps y <- y (3 - s y^2) / 2 in T
+// (one step suffices for float, two give double accuracy from float).
+template <typename T>
+__device__ __forceinline__ T rsqrt_refined(T s) {
+    T y = (T)rsqrtf((float)s);
+    y = y * (T(1.5) - T(0.5) * s * y * y);
+    if (sizeof(T) == 8) y = y * (T(1.5) - T(0.5) * s * y * y);
+    return y;
+}
+
+// Cholesky solve with reciprocal pivots (one thread).  Returns false when a
+// pivot is not positive.  Pivots use rsqrt_refined, so the double version
+// needs no double-precision divide or square root.
+template <int D, typename T>
+__device__ __forceinline__ bool chol_solve_rcp(const T* packed, const T* rhs, T* b) {
+    constexpr int n = D + 1;
+    T L[n][n], id[n], t[n];
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            T s = packed[Gram<D>::idx(j, i)];
+#pragma unroll
+            for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
+            if (i == j) {
+                if (!(s > T(0))) return false;
+                id[i] = rsqrt_refined(s);
+                L[i][i] = s * id[i];
+            } else {
+                L[i][j] = s * id[j];
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        T s = rhs[i];
+#pragma unroll
+        for (int k = 0; k < i; ++k) s -= L[i][k] * t[k];
+        t[i] = s * id[i];
+    }
+#pragma unroll
+    for (int i = n - 1; i >= 0; --i) {
+        T s = t[i];
+#pragma unroll
+        for (int k = i + 1; k < n; ++k) s -= L[k][i] * b[k];
+        b[i] = s * id[i];
+    }
+    return true;
+}
+
 // Bitonic sort (ascending) of P2 floats in shared memory by the whole CTA.
 template <int NT>
 __device__ void block_bitonic_sort(float* buf, int P2) {

@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(NT) errors_kernel(const ErrParams P) {
     if (tid == 0) {
         for (int q = 0; q < NV; ++q) s_G[q] = outd[q];
         double bd[NB];
-        s_ok = chol_solve_packed<D, double>(s_G, s_G + Gm::NG, bd) ? 1 : 0;
+        s_ok = chol_solve_rcp<D, double>(s_G, s_G + Gm::NG, bd) ? 1 : 0;
         for (int a = 0; a < NB; ++a) s_b[a] = bd[a];
     }
     __syncthreads();
@@ -385,20 +385,20 @@ __global__ void __launch_bounds__(NT) errors_kernel(const ErrParams P) {
         // db_k = G^-1 t_k
         double tk[NB], dbk[NB];
         for (int a = 0; a < NB; ++a) tk[a] = outd[tid * NB + a];
-        chol_solve_packed<D, double>(s_G, tk, dbk);
+        chol_solve_rcp<D, double>(s_G, tk, dbk);
         for (int a = 0; a < NB; ++a) s_db[tid * NB + a] = dbk[a];
     }
     if (tid == 0) s_JJ[15] = outd[5 * NB];
     __syncthreads();
-    // J_jk and J^T J (15 sums, per-thread FP64 accumulation)
+    // J_jk and J^T J (15 sums: FP32 over the thread's 16 pixels, FP64 across threads)
     float dbl[5][NB];
 #pragma unroll
     for (int k = 0; k < 5; ++k)
 #pragma unroll
         for (int a = 0; a < NB; ++a) dbl[k][a] = (float)s_db[k * NB + a];
-    double jj[15];
+    float jj[15];
 #pragma unroll
-    for (int q = 0; q < 15; ++q) jj[q] = 0.0;
+    for (int q = 0; q < 15; ++q) jj[q] = 0.0f;
 #pragma unroll
     for (int r = 0; r < PPT; ++r) {
         const int j = tid + r * NT;
@@ -418,14 +418,14 @@ __global__ void __launch_bounds__(NT) errors_kernel(const ErrParams P) {
 #pragma unroll
             for (int a = 0; a < 5; ++a)
 #pragma unroll
-                for (int b2 = a; b2 < 5; ++b2) jj[q++] += (double)Jr[a] * (double)Jr[b2];
+                for (int b2 = a; b2 < 5; ++b2) { jj[q] = fmaf(Jr[a], Jr[b2], jj[q]); ++q; }
         }
     }
     // FP64 block reduction of the 15 sums
     double* redd = reinterpret_cast<double*>(red + ((((size_t)(red - sm)) & 1) ? 1 : 0));
 #pragma unroll
     for (int q = 0; q < 15; ++q) {
-        double s = jj[q];
+        double s = (double)jj[q];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) redd[warp * 15 + q] = s;

@@ -58,7 +58,9 @@ class Result(ct.Structure):
 
 EXPORTS = ["lasp_init_interp", "lasp_free_interp", "lasp_default_opts", "lasp_fit_batch",
            "lasp_errors", "lasp_forward", "lasp_backward", "lasp_interp_eval",
-           "lasp_last_launches", "lasp_strerror", "lasp_version"]
+           "lasp_last_launches", "lasp_strerror", "lasp_version", "lasp_resample_linear",
+           "lasp_slots_create", "lasp_slots_free", "lasp_slots_admit", "lasp_slots_step",
+           "lasp_slots_fetch", "lasp_interp_eval_static"]
 
 
 def library_path() -> str:
@@ -94,6 +96,9 @@ def load(build: bool = False):
         lib.lasp_strerror.argtypes = [I]
         lib.lasp_strerror.restype = ct.c_char_p
         lib.lasp_version.restype = I
+        D = ct.c_double
+        lib.lasp_resample_linear.argtypes = [I, I, D, D, P, I, D, D, P, P]
+        lib.lasp_resample_linear.restype = I
         _lib = lib
         return lib
 
@@ -141,6 +146,18 @@ def last_launches() -> int:
     return int(load().lasp_last_launches())
 
 
+def resample_linear(coeff_lin, lam1, dlam, n_out, ln_lam0, dln, stream=None):
+    """Flux-conserving resampling (Eqs. 2-4) of table rows (device K x q,
+    linear grid lam1 + k dlam) onto the ln grid exp(ln_lam0 + i dln)."""
+    _dev(coeff_lin, torch.float32)
+    K, q = coeff_lin.shape
+    out = torch.empty((K, int(n_out)), device=coeff_lin.device)
+    _check(load().lasp_resample_linear(K, q, float(lam1), float(dlam), _ptr(coeff_lin), int(n_out),
+                                       float(ln_lam0), float(dln), _ptr(out), _stream(stream)),
+           "lasp_resample_linear")
+    return out
+
+
 class Interp:
     """Device-resident interpolator (Eq. 1 table) on one ln-lambda grid."""
 
@@ -165,6 +182,18 @@ class Interp:
     @classmethod
     def from_grid(cls, grid, C, exps, basis_lo, basis_hi, box_lo, box_hi):
         return cls(C, exps, grid.n_pix, grid.pad, grid.dln, basis_lo, basis_hi, box_lo, box_hi)
+
+    @classmethod
+    def from_linear(cls, n_pix, pad, lam0, dln, C_lin, lam1, dlam, exps, basis_lo, basis_hi,
+                    box_lo, box_hi):
+        """Table given on a linear wavelength grid (lam1 + k dlam): resampled on
+        the GPU onto the ln grid of n_pix observed + 2 pad model pixels whose
+        observed pixel 0 is at lam0 (Eqs. 2-4), then uploaded."""
+        import math
+        Cl = torch.as_tensor(np.ascontiguousarray(C_lin, dtype=np.float32)).cuda()
+        n_model = int(n_pix) + 2 * int(pad)
+        Cr = resample_linear(Cl, lam1, dlam, n_model, math.log(lam0) - pad * dln, dln)
+        return cls(Cr.cpu().numpy(), exps, n_pix, pad, dln, basis_lo, basis_hi, box_lo, box_hi)
 
     def close(self):
         if getattr(self, "_h", None) is not None and _lib is not None:

@@ -374,3 +374,51 @@ def test_errors_match_monte_carlo_scatter():
                     for i in range(0, n, 8)])
     ratio = res["theta"].std(axis=0, ddof=1) / np.median(sig, axis=0)
     assert np.all((ratio > 0.7) & (ratio < 1.3)), ratio
+
+
+# ------------------------------------------- resampling (stage 3, Eqs. 2-4)
+
+def _bins(n_out, ln0, dln):
+    return np.exp(ln0 + (np.arange(n_out + 1) - 0.5) * dln)
+
+
+def _brute_resample(F, lam1, dlam, edges, sub=200):
+    """Average of the piecewise-constant model over each target bin by direct
+    numerical integration on a fine subgrid (independent of Eqs. 2-4)."""
+    out = np.zeros(len(edges) - 1)
+    for i in range(len(edges) - 1):
+        xs = np.linspace(edges[i], edges[i + 1], sub + 1)
+        mid = 0.5 * (xs[1:] + xs[:-1])
+        k = np.floor((mid - (lam1 - 0.5 * dlam)) / dlam).astype(int)
+        val = np.where((k >= 0) & (k < len(F)), F[np.clip(k, 0, len(F) - 1)], 0.0)
+        out[i] = val.mean()
+    return out
+
+
+def test_resample_conserves_flux_and_constants():
+    rng = np.random.default_rng(9)
+    lam1, dlam, q = 4100.0, 0.4, 5000               # linear model grid 4100-6100 A
+    F = 1.0 + 0.3 * rng.standard_normal(q)
+    ln0, dln = np.log(4300.0), 2.274544e-4           # LAMOST step, inside the model range
+    n_out = int(np.log(5900.0 / 4300.0) / dln)
+    out = O.resample(F, lam1, dlam, n_out, ln0, dln)
+    e = _bins(n_out, ln0, dln)
+    # integral over the covered range equals the model's integral there (telescoping)
+    k0 = (e[0] - (lam1 - 0.5 * dlam)) / dlam
+    k1 = (e[-1] - (lam1 - 0.5 * dlam)) / dlam
+    cum = np.concatenate([[0.0], np.cumsum(F * dlam)])
+    exact = np.interp(k1, np.arange(q + 1), cum) - np.interp(k0, np.arange(q + 1), cum)
+    assert abs((out * np.diff(e)).sum() - exact) < 1e-9 * abs(exact)
+    const = O.resample(np.full(q, 2.5), lam1, dlam, n_out, ln0, dln)
+    np.testing.assert_allclose(const, 2.5, rtol=1e-12)
+
+
+def test_resample_matches_brute_force_bin_averages():
+    rng = np.random.default_rng(10)
+    lam1, dlam, q = 5000.0, 0.7, 60
+    F = rng.uniform(0.2, 1.5, q)
+    ln0, dln = np.log(5003.0), 1.3e-4
+    n_out = 40
+    out = O.resample(F, lam1, dlam, n_out, ln0, dln)
+    ref = _brute_resample(F, lam1, dlam, _bins(n_out, ln0, dln), sub=4000)
+    np.testing.assert_allclose(out, ref, rtol=2e-3, atol=1e-3)
