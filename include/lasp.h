@@ -105,7 +105,13 @@ typedef struct {
 /* Fit options.  lasp_default_opts() gives the paper's settings: lr 0.1, Adam
  * betas (0.9, 0.999), eps 1e-8, tol 1e-5 over a window of 50 steps, at most
  * 5000 steps (stage 8), median weight (quantile 0.5, section 3.3), Legendre
- * degree 6, no edge pixels dropped, FP32 arithmetic. */
+ * degree 6, no edge pixels dropped, FP32 arithmetic, No Clean (Clean: mask
+ * updates every 30 steps, at most 11).
+ * Clean (stage 6): after evaluating step t = every, 2 every, ... (at most
+ * clean_max updates) the mask is recomputed from the weighted residual
+ * sqrt(W) eps and model sqrt(W) c F'' at x_t (f_shift 0.5 on the first
+ * update, 0.2 after; see lasp_clean_mask) starting from the pixels in use,
+ * and applies from step t + 1. */
 typedef struct {
     float lr, beta1, beta2, eps, tol;
     int window;             /* 1..64                                   */
@@ -115,6 +121,10 @@ typedef struct {
     float quantile;         /* w_i = this quantile of the used flux    */
     int precision;          /* LASP_PREC_*                              */
     int fp64_normal_eq;     /* 1: cross-warp sums and 7x7 solve in FP64 */
+    int clean;              /* 1: Clean outlier masking (stage 6, Eq. 8); FP32
+                               batch fits only                           */
+    int clean_every;        /* mask update every this many steps (30)   */
+    int clean_max;          /* at most this many updates (11)           */
 } lasp_fit_opts;
 
 void lasp_default_opts(lasp_fit_opts* o);
@@ -239,6 +249,20 @@ int lasp_interp_eval_static(const lasp_interp_desc* desc, const float* coeff, in
  * overlap integrals in FP64; no flux outside the model range.  Asynchronous. */
 int lasp_resample_linear(int K, int q, double lam1, double dlam, const float* coeff_lin, int n_out,
                          double ln_lam0, double dln, float* coeff_out, void* stream);
+
+/* Clean outlier mask (stage 6, Eq. 8) of N spectra from their weighted
+ * residual r = sqrt(W) eps and weighted model m = sqrt(W) c F'' (device
+ * N x p float32) and the pixels in use (device N x p uint8, 1 = used):
+ * sigma = std of r over used pixels; G_j = max |m_j - m_{j+-1}| (existing
+ * neighbours); B: |r| - fshift G > k sigma, k = 3 relaxed to 4, 5, 7 while
+ * more than 3% of the used pixels are flagged; C: neighbours of B outliers
+ * with |r| - fshift G > 2 sigma; D: neighbours j' of flagged pixels j with
+ * r_j r_j' > 0, |r_j'| <= |r_j| and |r_j'| - fshift G_j' > sigma' (std over
+ * used pixels not in B or C), repeated until unchanged, at most 20 passes.
+ * keep: device N x p uint8 = used and not flagged; k_used: device N int32
+ * (the k of B) or NULL.  p <= 8192.  Asynchronous. */
+int lasp_clean_mask(int N, int p, const float* r, const float* m, const uint8_t* used, float fshift,
+                    uint8_t* keep, int32_t* k_used, void* stream);
 
 /* Number of kernels the last call on this thread enqueued (for accounting). */
 int lasp_last_launches(void);

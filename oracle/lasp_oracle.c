@@ -366,12 +366,33 @@ unsigned orc_stop_rule(const double* hist, int t, int window, double tol, int ma
     return 0;
 }
 
+/* Clean update after evaluating at x_t (stage 6 schedule of stage 8): from
+ * the residual eps at x_t, the new mask takes effect from step t + 1. */
+static void clean_update(int p, const double* y, const double* Wb, const double* eps, int update,
+                         unsigned char* keep, double* W) {
+    float* r = malloc(sizeof(float) * p);
+    float* m = malloc(sizeof(float) * p);
+    unsigned char* used = malloc(p);
+    for (int j = 0; j < p; ++j) {
+        double s = sqrt(Wb[j]);
+        r[j] = (float)(s * eps[j]);
+        m[j] = (float)(s * (y[j] - eps[j]));
+        used[j] = Wb[j] > 0.0 && keep[j];
+    }
+    orc_clean_mask(p, r, m, used, update == 1 ? 0.5f : 0.2f, keep);
+    for (int j = 0; j < p; ++j) W[j] = keep[j] ? Wb[j] : 0.0;
+    free(r); free(m); free(used);
+}
+
 static void fit_one(const orc_model* M, const orc_opts* O, const float* flux, const float* ivar,
                     const unsigned char* good, const double* theta0, double* theta, double* loss,
                     int* steps, unsigned* status, double* b_out) {
     int p = M->n_pix, D = M->deg;
     double* y = malloc(sizeof(double) * p);
     double* W = malloc(sizeof(double) * p);
+    double* Wb = malloc(sizeof(double) * p);
+    double* eps = malloc(sizeof(double) * p);
+    unsigned char* keep = malloc(p);
     double* hist = malloc(sizeof(double) * (O->max_steps + 1));
     double w, x[5], m[5] = {0}, v[5] = {0}, g[5], b[8];
     int n_obj = orc_prep(p, flux, ivar, good, O->quantile, O->edge_px, y, W, &w);
@@ -384,9 +405,13 @@ static void fit_one(const orc_model* M, const orc_opts* O, const float* flux, co
     }
     orc_x_from_phys(M, theta0, x);
     for (int k = 0; k < 5; ++k) x[k] = x[k] < -1.0 ? -1.0 : (x[k] > 1.0 ? 1.0 : x[k]);
+    for (int j = 0; j < p; ++j) {
+        Wb[j] = W[j];
+        keep[j] = 1;
+    }
     for (int t = 0;; ++t) {
         double l;
-        unsigned st = orc_eval(M, y, W, x, &l, g, b, NULL, NULL);
+        unsigned st = orc_eval(M, y, W, x, &l, g, b, eps, NULL);
         if (st & (ORC_ST_SINGULAR | ORC_ST_NONFINITE)) {
             *status = st;
             *loss = l;
@@ -405,9 +430,12 @@ static void fit_one(const orc_model* M, const orc_opts* O, const float* flux, co
             break;
         }
         orc_adam_update(5, x, m, v, g, t + 1, O->lr, O->beta1, O->beta2, O->eps, 1);
+        if (O->clean && t > 0 && O->clean_every > 0 && t % O->clean_every == 0 &&
+            t / O->clean_every <= O->clean_max)
+            clean_update(p, y, Wb, eps, t / O->clean_every, keep, W);
     }
 out:
-    free(y); free(W); free(hist);
+    free(y); free(W); free(Wb); free(eps); free(keep); free(hist);
 }
 
 void orc_fit(const orc_model* M, const orc_opts* O, int n, const float* flux, const float* ivar,
@@ -554,4 +582,79 @@ void orc_resample(int q, double lam1, double dlam, const double* F, int n_out, d
     free(cum);
     free(edge_val);
     free(edge);
+}
+
+/* Population standard deviation of r over the pixels with sel[j] != 0, in
+ * float32 arithmetic with double-precision sums. */
+static float std_sel(int p, const float* r, const unsigned char* sel) {
+    double s1 = 0.0, s2 = 0.0;
+    int n = 0;
+    for (int j = 0; j < p; ++j)
+        if (sel[j]) { s1 += r[j]; s2 += (double)r[j] * r[j]; ++n; }
+    if (n == 0) return 0.0f;
+    double mean = s1 / n, var = s2 / n - mean * mean;
+    return (float)sqrt(var > 0.0 ? var : 0.0);
+}
+
+int orc_clean_mask(int p, const float* r, const float* m, const unsigned char* used, float fshift,
+                   unsigned char* keep) {
+    float* G = malloc(sizeof(float) * p);
+    float* lhs = malloc(sizeof(float) * p);
+    unsigned char* B = calloc(p, 1);
+    unsigned char* flag = calloc(p, 1);
+    unsigned char* sel = malloc(p);
+    for (int j = 0; j < p; ++j) {
+        float g = 0.0f;
+        if (j > 0) g = fabsf(m[j] - m[j - 1]);
+        if (j < p - 1 && fabsf(m[j] - m[j + 1]) > g) g = fabsf(m[j] - m[j + 1]);
+        G[j] = g;
+        lhs[j] = fabsf(r[j]) - fshift * G[j];
+    }
+    int n_used = 0;
+    for (int j = 0; j < p; ++j) n_used += used[j] ? 1 : 0;
+    const float sigma = std_sel(p, r, used);
+    /* B with k = 3, relaxed while more than 3% of the used pixels are flagged */
+    const float ks[4] = {3.0f, 4.0f, 5.0f, 7.0f};
+    int kk = 0;
+    for (; kk < 4; ++kk) {
+        int nb = 0;
+        for (int j = 0; j < p; ++j) {
+            B[j] = used[j] && lhs[j] > ks[kk] * sigma;
+            nb += B[j];
+        }
+        if (!(nb > 0.03 * n_used)) break;
+    }
+    if (kk == 4) kk = 3;
+    /* C: neighbours of B outliers */
+    for (int j = 0; j < p; ++j) flag[j] = B[j];
+    for (int j = 0; j < p; ++j) {
+        if (!used[j] || B[j]) continue;
+        int nbB = (j > 0 && B[j - 1]) || (j < p - 1 && B[j + 1]);
+        if (nbB && lhs[j] > 2.0f * sigma) flag[j] = 1;
+    }
+    /* sigma' over used pixels not in B or C */
+    for (int j = 0; j < p; ++j) sel[j] = used[j] && !flag[j];
+    const float sigp = std_sel(p, r, sel);
+    /* D: grow along same-sign, non-increasing residuals above sigma' */
+    unsigned char* nxt = malloc(p);
+    for (int it = 0; it < 20; ++it) {
+        int changed = 0;
+        for (int j = 0; j < p; ++j) {
+            nxt[j] = flag[j];
+            if (flag[j] || !used[j]) continue;
+            for (int d = -1; d <= 1; d += 2) {
+                int i = j + d;
+                if (i < 0 || i >= p || !flag[i]) continue;
+                if (r[i] * r[j] > 0.0f && fabsf(r[j]) <= fabsf(r[i]) && lhs[j] > sigp) {
+                    nxt[j] = 1;
+                    changed = 1;
+                }
+            }
+        }
+        for (int j = 0; j < p; ++j) flag[j] = nxt[j];
+        if (!changed) break;
+    }
+    for (int j = 0; j < p; ++j) keep[j] = used[j] && !flag[j];
+    free(G); free(lhs); free(B); free(flag); free(sel); free(nxt);
+    return (int)ks[kk];
 }

@@ -42,6 +42,9 @@ typedef struct {
     double lr, beta1, beta2, eps, tol;
     int window, max_steps, edge_px;
     double quantile;
+    int clean;          /* 1: Clean masking (Eq. 8) during the fit            */
+    int clean_every;    /* mask updates at t = every, 2 every, ... (30)       */
+    int clean_max;      /* at most this many updates (11)                     */
 } orc_opts;
 
 /* x in [-1,1]^5 -> physical parameters (linear box map). */
@@ -122,6 +125,21 @@ unsigned orc_errors(const orc_model* M, const orc_opts* O, const float* flux,
  * cumulative integral is held constant (no flux). */
 void orc_resample(int q, double lam1, double dlam, const double* F, int n_out, double ln_lam0,
                   double dln, double* out);
+
+/* Clean outlier mask (stage 6, Eq. 8) from the weighted residual r_j =
+ * sqrt(W_j) eps_j and the weighted model m_j = sqrt(W_j) c_j F''_j of one
+ * spectrum.  used[j] = 1 for pixels currently used (predefined mask and the
+ * previous Clean mask).  sigma = std of r over used pixels;
+ * G_j = max(|m_j - m_{j-1}|, |m_j - m_{j+1}|) (existing neighbours only);
+ * B: |r_j| - fshift G_j > k sigma, k = 3, relaxed to 4, 5, 7 while more than
+ * 3% of the used pixels are flagged; C: neighbours of B outliers with
+ * |r| - fshift G > 2 sigma; D: neighbours j' of flagged pixels j (B, C or D)
+ * with r_j r_j' > 0, |r_j'| <= |r_j| and |r_j'| - fshift G_j' > sigma', sigma'
+ * the std over used pixels not in B or C, repeated until unchanged (at most
+ * 20 passes).  keep[j] = used[j] and not flagged.  Decisions are taken in
+ * float32 on float32 inputs (the kernel's precision).  Returns the k used. */
+int orc_clean_mask(int p, const float* r, const float* m, const unsigned char* used, float fshift,
+                   unsigned char* keep);
 
 int orc_max_threads(void);
 

@@ -47,7 +47,8 @@ class _Model(ct.Structure):
 class _Opts(ct.Structure):
     _fields_ = [("lr", ct.c_double), ("beta1", ct.c_double), ("beta2", ct.c_double),
                 ("eps", ct.c_double), ("tol", ct.c_double), ("window", ct.c_int),
-                ("max_steps", ct.c_int), ("edge_px", ct.c_int), ("quantile", ct.c_double)]
+                ("max_steps", ct.c_int), ("edge_px", ct.c_int), ("quantile", ct.c_double),
+                ("clean", ct.c_int), ("clean_every", ct.c_int), ("clean_max", ct.c_int)]
 
 
 def lib():
@@ -79,6 +80,8 @@ def lib():
             _lib.orc_max_threads.restype = ct.c_int
             _lib.orc_resample.argtypes = [ct.c_int, ct.c_double, ct.c_double, P, ct.c_int,
                                           ct.c_double, ct.c_double, P]
+            _lib.orc_clean_mask.argtypes = [ct.c_int, P, P, P, ct.c_float, P]
+            _lib.orc_clean_mask.restype = ct.c_int
         return _lib
 
 
@@ -120,8 +123,9 @@ class Model:
 
 
 def make_opts(lr=0.1, beta1=0.9, beta2=0.999, eps=1e-8, tol=1e-5, window=50, max_steps=5000,
-              edge_px=0, quantile=0.5):
-    return _Opts(lr, beta1, beta2, eps, tol, window, max_steps, edge_px, quantile)
+              edge_px=0, quantile=0.5, clean=0, clean_every=30, clean_max=11):
+    return _Opts(lr, beta1, beta2, eps, tol, window, max_steps, edge_px, quantile, clean,
+                 clean_every, clean_max)
 
 
 def basis(M: Model, th):
@@ -256,3 +260,13 @@ def resample(F, lam1, dlam, n_out, ln_lam0, dln):
     lib().orc_resample(len(F), float(lam1), float(dlam), _p(F), int(n_out), float(ln_lam0),
                        float(dln), _p(out))
     return out
+
+
+def clean_mask(r, m, used, fshift):
+    """Clean outlier mask (Eq. 8) on float32 weighted residual r and model m."""
+    r = np.ascontiguousarray(r, dtype=np.float32)
+    m = np.ascontiguousarray(m, dtype=np.float32)
+    used = np.ascontiguousarray(used, dtype=np.uint8)
+    keep = np.zeros(len(r), dtype=np.uint8)
+    k = lib().orc_clean_mask(len(r), _p(r), _p(m), _p(used), float(fshift), _p(keep))
+    return keep, k

@@ -5,6 +5,7 @@
 #include <new>
 
 #include "lasp.h"
+#include "lasp_clean.cuh"
 #include "lasp_launch.cuh"
 #include "lasp_tc.cuh"
 
@@ -73,6 +74,7 @@ int check_opts(const lasp_fit_opts* o, int n_pix) {
     if (o->edge_px < 0 || 2 * o->edge_px >= n_pix) return LASP_EINVAL;
     if (!(o->quantile >= 0.0f && o->quantile <= 1.0f)) return LASP_EINVAL;
     if (o->precision < LASP_PREC_FP32 || o->precision > LASP_PREC_TF32X3) return LASP_EINVAL;
+    if (o->clean && (o->clean_every < 1 || o->clean_max < 0)) return LASP_EINVAL;
     return LASP_OK;
 }
 
@@ -88,6 +90,9 @@ FitOpts to_dev(const lasp_fit_opts* o) {
     d.edge_px = o->edge_px;
     d.quantile = o->quantile;
     d.fp64_ne = o->fp64_normal_eq ? 1 : 0;
+    d.clean = o->clean ? 1 : 0;
+    d.clean_every = o->clean_every;
+    d.clean_max = o->clean_max;
     return d;
 }
 
@@ -132,6 +137,9 @@ void lasp_default_opts(lasp_fit_opts* o) {
     o->quantile = 0.5f;
     o->precision = LASP_PREC_FP32;
     o->fp64_normal_eq = 0;
+    o->clean = 0;
+    o->clean_every = 30;
+    o->clean_max = 11;
 }
 
 int lasp_init_interp(const lasp_interp_desc* d, const float* coeff, lasp_interp* out) {
@@ -220,7 +228,10 @@ int lasp_fit_batch(lasp_interp h, const lasp_batch* b, const lasp_fit_opts* o, l
     if (rc) return rc;
     if (!r || (b->N > 0 && (!r->theta || !r->loss || !r->steps || !r->status))) return LASP_EINVAL;
     if (b->N == 0) return LASP_OK;
-    if (o->precision != LASP_PREC_FP32) return lasp_tc_fit_batch(h->M, h->tc, b, o, r, stream, &g_last_launches);
+    if (o->precision != LASP_PREC_FP32) {
+        if (o->clean) return LASP_EINVAL;          // Clean runs in the FP32 batch fit
+        return lasp_tc_fit_batch(h->M, h->tc, b, o, r, stream, &g_last_launches);
+    }
     FitParams P{};
     P.M = h->M;
     P.O = to_dev(o);
@@ -396,7 +407,7 @@ int lasp_slots_create(lasp_interp h, int n_slots, const lasp_fit_opts* o, lasp_s
     *out = nullptr;
     int rc = check_opts(o, h->M.n_pix);
     if (rc) return rc;
-    if (o->precision != LASP_PREC_FP32) return LASP_EINVAL;
+    if (o->precision != LASP_PREC_FP32 || o->clean) return LASP_EINVAL;
     lasp_slots_s* s = new (std::nothrow) lasp_slots_s();
     if (!s) return LASP_ENOMEM;
     s->h = h;
@@ -543,6 +554,68 @@ extern "C" int lasp_resample_linear(int K, int q, double lam1, double dlam, cons
     const long total = (long)K * n_out;
     resample_kernel<<<(unsigned)((total + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
         K, q, lam1, dlam, coeff_lin, n_out, ln_lam0, dln, coeff_out);
+    g_last_launches = 1;
+    return cuda_err(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// Clean mask of N spectra (stage 6, Eq. 8), one CTA per spectrum.
+
+namespace {
+
+template <int NT>
+__global__ void __launch_bounds__(NT) clean_mask_kernel(int p, const float* __restrict__ r,
+                                                        const float* __restrict__ m,
+                                                        const uint8_t* __restrict__ used, float fshift,
+                                                        uint8_t* keep, int32_t* k_used) {
+    extern __shared__ __align__(16) float sm[];
+    const int i = blockIdx.x, tid = threadIdx.x;
+    float* Rs = sm;
+    float* Ms = sm + skew_size(p + 32);
+    double* redd = reinterpret_cast<double*>(Ms + skew_size(p + 32));
+    double* tot = redd + 3 * (NT / 32);
+    __shared__ int s_k;
+    const size_t row = (size_t)i * p;
+    const int j0 = tid * PPT;
+    uint32_t ub = 0;
+    for (int q = 0; q < PPT; ++q) {
+        const int j = j0 + q;
+        if (j < p) {
+            Rs[skew(j + 16)] = r[row + j];
+            Ms[skew(j + 16)] = m[row + j];
+            if (used[row + j]) ub |= 1u << q;
+        }
+    }
+    __syncthreads();
+    const uint32_t kb = cta_clean_mask<NT, PPT>(p, j0, Rs, 16, Ms, 16, ub, fshift,
+                                                reinterpret_cast<uint8_t*>(Ms), redd, tot, &s_k);
+    for (int q = 0; q < PPT; ++q) {
+        const int j = j0 + q;
+        if (j < p) keep[row + j] = (kb >> q) & 1u;
+    }
+    if (tid == 0 && k_used) k_used[i] = s_k;
+}
+
+}  // namespace
+
+extern "C" int lasp_clean_mask(int N, int p, const float* r, const float* m, const uint8_t* used,
+                               float fshift, uint8_t* keep, int32_t* k_used, void* stream) {
+    g_last_launches = 0;
+    if (N < 0 || p < 1 || p > 16 * 512) return LASP_EINVAL;
+    if (N == 0) return LASP_OK;
+    if (!r || !m || !used || !keep) return LASP_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t smem = 4 * (2 * (size_t)skew_size(p + 32)) + 8 * (3 * 16 + 4);
+    int e;
+    if (p <= 16 * 256) {
+        e = cuda_err(cudaFuncSetAttribute(clean_mask_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (e) return e;
+        clean_mask_kernel<256><<<N, 256, smem, st>>>(p, r, m, used, fshift, keep, k_used);
+    } else {
+        e = cuda_err(cudaFuncSetAttribute(clean_mask_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (e) return e;
+        clean_mask_kernel<512><<<N, 512, smem, st>>>(p, r, m, used, fshift, keep, k_used);
+    }
     g_last_launches = 1;
     return cuda_err(cudaGetLastError());
 }

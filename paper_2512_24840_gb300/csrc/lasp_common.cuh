@@ -13,6 +13,7 @@
 namespace lasp {
 
 constexpr int KMAX = 32;          // basis terms supported
+constexpr int PPT = 16;           // pixels per thread of the per-spectrum kernels
 constexpr int WINMAX = 64;        // stop-rule window supported
 constexpr int HMAX = 47;          // kernel half width supported (2H+1 <= 96 taps)
 constexpr int TAPS_MAX = 2 * HMAX + 1;
@@ -34,7 +35,14 @@ struct FitOpts {
     int window, max_steps, edge_px;
     float quantile;
     int fp64_ne;
+    int clean, clean_every, clean_max;
 };
+
+// Skewed rows in shared memory: element i at i + i/16, so that the
+// stride-16 accesses of a warp (one 16-pixel run per thread) hit 32 banks.
+__host__ __device__ constexpr int skew(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int round32(int n) { return (n + 31) & ~31; }
+__host__ __device__ constexpr int skew_size(int n) { return ((skew(n) + 4) + 3) & ~3; }
 
 __device__ __forceinline__ float ipowf(float u, int a) {
     float r = 1.0f;

@@ -18,11 +18,11 @@
 // parameters goes through the per-tap sums a_s = sum_j delta_j F'_{j+H-s}.
 #pragma once
 
+#include "lasp_clean.cuh"
 #include "lasp_common.cuh"
 
 namespace lasp {
 
-constexpr int PPT = 16;     // pixels per thread
 constexpr int TB = 8;       // taps per block
 constexpr int TAPBUF = 128; // tap buffer (>= 2 HMAX + 2 TB + 1)
 
@@ -60,9 +60,6 @@ struct FitParams {
     float* weight;    // N or nullptr
 };
 
-__host__ __device__ constexpr int skew(int i) { return i + (i >> 4); }
-__host__ __device__ constexpr int round32(int n) { return (n + 31) & ~31; }
-__host__ __device__ constexpr int skew_size(int n) { return ((skew(n) + 4) + 3) & ~3; }
 
 // Shared-memory plan (floats).  Fp holds model pixels m in [-16, n_model+16)
 // at skew(m + 16); Db holds delta_j for j in [-(2H+8), p + 2H + 24) at
@@ -185,6 +182,12 @@ __device__ __forceinline__ int warp_prepare_step(const ModelDev& M, const float*
     return kernel_taps_warp(th[3] / M.kms_px, th[4] / M.kms_px, M.pad, g, gmu, gsg);
 }
 
+// Clean mask update after evaluating step t (stage 6 schedule): t = every,
+// 2 every, ..., at most clean_max updates.
+__device__ __forceinline__ bool clean_step(const FitOpts& O, int t) {
+    return O.clean && t > 0 && t % O.clean_every == 0 && t / O.clean_every <= O.clean_max;
+}
+
 template <int NT, int D>
 __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) fit_kernel(const FitParams P) {
     using Gm = Gram<D>;
@@ -211,7 +214,8 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) fit_kernel(const FitPar
     float* ring = sm + L.ring;
     __shared__ float s_x[5], s_b[NB];
     __shared__ int s_h, s_stop;
-    __shared__ float s_w;
+    __shared__ float s_w, s_imean;
+    __shared__ double s_redd[3 * (NT / 32)], s_tot[3];
 
     const bool slots = P.S.x != nullptr;
     int t0 = 0;
@@ -257,6 +261,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) fit_kernel(const FitPar
         }
         if (tid == 0) {
             s_w = w;
+            s_imean = imean;
             s_stop = (fresh && (n_obj < NB + 5 || !(w > 0.0f) || !isfinite(w))) ? 1 : 0;
             if (slots && fresh) {
                 P.S.w[i] = w;
@@ -596,13 +601,87 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) fit_kernel(const FitPar
             }
             stop = __shfl_sync(0xffffffffu, stop, 0);
             __syncwarp();
-            if (!stop) {
+            if (!stop && !clean_step(P.O, t)) {
                 int hn = warp_prepare_step(M, s_x, phi, dphi, g, gmu, gsg);
                 if (lane == 0) s_h = hn;
             }
         }
         __syncthreads();
         if (s_stop) break;
+        if (clean_step(P.O, t)) {
+            // ---- stage 6 Clean update from the residual at x_t (taps g and F' still of x_t)
+            const int upd = t / P.O.clean_every;
+#pragma unroll
+            for (int r = 0; r < PPT; ++r) fpp[r] = 0.0f;
+            if (own_pix) {
+                for (int bk = 0; bk < nblk; ++bk) {
+                    const int s0 = -h + bk * TB;
+                    float gg[TB], win[PPT + TB - 1];
+#pragma unroll
+                    for (int e = 0; e < TB; ++e) gg[e] = g[s0 + e + H];
+                    const int base = j0 + H - s0 - (TB - 1) + 16;
+#pragma unroll
+                    for (int q = 0; q < PPT + TB - 1; ++q) win[q] = Fp[skew(base + q)];
+#pragma unroll
+                    for (int e = 0; e < TB; ++e)
+#pragma unroll
+                        for (int r = 0; r < PPT; ++r) fpp[r] = fmaf(gg[e], win[r - e + TB - 1], fpp[r]);
+                }
+            }
+            float mm[PPT], wbv[PPT];
+            uint32_t used = 0;
+            {
+                float bl[NB];
+#pragma unroll
+                for (int a = 0; a < NB; ++a) bl[a] = s_b[a];
+                const size_t row = (size_t)i * p;
+#pragma unroll
+                for (int r = 0; r < PPT; ++r) {
+                    const int j = j0 + r;
+                    mm[r] = 0.0f;
+                    wbv[r] = 0.0f;
+                    if (j < p) {
+                        const float f = P.flux[row + j], iv = P.ivar[row + j];
+                        const bool use = P.good[row + j] && iv > 0.0f && isfinite(f) && isfinite(iv);
+                        const bool edge = j < P.O.edge_px || j >= p - P.O.edge_px;
+                        const float wb = (use && !edge && s_w > 0.0f) ? iv / s_imean : 0.0f;
+                        float Pl[NB];
+                        legendre<D>(fmaf((float)j, xstep, -1.0f), Pl);
+                        float c = 0.0f;
+#pragma unroll
+                        for (int a = 0; a < NB; ++a) c = fmaf(bl[a], Pl[a], c);
+                        const float model = c * fpp[r];
+                        const float sw = sqrtf(wb);
+                        Db[skew(j + L.dofs)] = sw * (y[skew(j)] - model);
+                        mm[r] = sw * model;
+                        wbv[r] = wb;
+                        if (W[skew(j)] > 0.0f) used |= 1u << r;
+                    }
+                }
+            }
+            __syncthreads();          // every thread is done reading F'
+#pragma unroll
+            for (int r = 0; r < PPT; ++r)
+                if (j0 + r < p) Fp[skew(j0 + r + 16)] = mm[r];
+            __syncthreads();
+            const uint32_t keep = cta_clean_mask<NT, PPT>(p, j0, Db, L.dofs, Fp, 16, used,
+                                                          upd == 1 ? 0.5f : 0.2f, reinterpret_cast<uint8_t*>(Fp),
+                                                          s_redd, s_tot, nullptr);
+#pragma unroll
+            for (int r = 0; r < PPT; ++r)
+                if (j0 + r < p) W[skew(j0 + r)] = ((keep >> r) & 1u) ? wbv[r] : 0.0f;
+            // F' pads were overwritten by the mask scratch: zero them again
+            for (int q = tid; q < 32; q += NT) {
+                const int mq = q < 16 ? q - 16 : nm + q - 16;
+                Fp[skew(mq + 16)] = 0.0f;
+            }
+            // the delta buffer pads are outside [0, p) and untouched
+            if (warp == 0) {
+                int hn = warp_prepare_step(M, s_x, phi, dphi, g, gmu, gsg);
+                if (lane == 0) s_h = hn;
+            }
+            __syncthreads();
+        }
     }
     if (s_stop == 2) {
         for (int q = tid; q < WINMAX; q += NT) P.S.ring[(size_t)i * WINMAX + q] = ring[q];

@@ -48,7 +48,8 @@ class FitOpts(ct.Structure):
     _fields_ = [("lr", ct.c_float), ("beta1", ct.c_float), ("beta2", ct.c_float),
                 ("eps", ct.c_float), ("tol", ct.c_float), ("window", ct.c_int),
                 ("max_steps", ct.c_int), ("legendre_deg", ct.c_int), ("edge_px", ct.c_int),
-                ("quantile", ct.c_float), ("precision", ct.c_int), ("fp64_normal_eq", ct.c_int)]
+                ("quantile", ct.c_float), ("precision", ct.c_int), ("fp64_normal_eq", ct.c_int),
+                ("clean", ct.c_int), ("clean_every", ct.c_int), ("clean_max", ct.c_int)]
 
 
 class Result(ct.Structure):
@@ -60,7 +61,7 @@ EXPORTS = ["lasp_init_interp", "lasp_free_interp", "lasp_default_opts", "lasp_fi
            "lasp_errors", "lasp_forward", "lasp_backward", "lasp_interp_eval",
            "lasp_last_launches", "lasp_strerror", "lasp_version", "lasp_resample_linear",
            "lasp_slots_create", "lasp_slots_free", "lasp_slots_admit", "lasp_slots_step",
-           "lasp_slots_fetch", "lasp_interp_eval_static"]
+           "lasp_slots_fetch", "lasp_interp_eval_static", "lasp_clean_mask"]
 
 
 def library_path() -> str:
@@ -99,6 +100,8 @@ def load(build: bool = False):
         D = ct.c_double
         lib.lasp_resample_linear.argtypes = [I, I, D, D, P, I, D, D, P, P]
         lib.lasp_resample_linear.restype = I
+        lib.lasp_clean_mask.argtypes = [I, I, P, P, P, ct.c_float, P, P, P]
+        lib.lasp_clean_mask.restype = I
         _lib = lib
         return lib
 
@@ -156,6 +159,18 @@ def resample_linear(coeff_lin, lam1, dlam, n_out, ln_lam0, dln, stream=None):
                                        float(ln_lam0), float(dln), _ptr(out), _stream(stream)),
            "lasp_resample_linear")
     return out
+
+
+def clean_mask(r, m, used, fshift, stream=None):
+    """Clean outlier mask (stage 6, Eq. 8) of N spectra: device float32 r, m
+    (N x p) and uint8 used; returns (keep uint8 N x p, k int32 N)."""
+    _dev(r, torch.float32), _dev(m, torch.float32), _dev(used, torch.uint8)
+    N, p = r.shape
+    keep = torch.empty((N, p), dtype=torch.uint8, device=r.device)
+    k = torch.empty(N, dtype=torch.int32, device=r.device)
+    _check(load().lasp_clean_mask(N, p, _ptr(r), _ptr(m), _ptr(used), float(fshift), _ptr(keep),
+                                  _ptr(k), _stream(stream)), "lasp_clean_mask")
+    return keep, k
 
 
 class Interp:

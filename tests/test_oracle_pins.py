@@ -422,3 +422,75 @@ def test_resample_matches_brute_force_bin_averages():
     out = O.resample(F, lam1, dlam, n_out, ln0, dln)
     ref = _brute_resample(F, lam1, dlam, _bins(n_out, ln0, dln), sub=4000)
     np.testing.assert_allclose(out, ref, rtol=2e-3, atol=1e-3)
+
+
+# ------------------------------------------------ Clean masking (stage 6, Eq. 8)
+
+def _base_noise(p):
+    # deterministic residual with mean 0 and population std 1: +-1 alternating
+    return np.where(np.arange(p) % 2 == 0, 1.0, -1.0).astype(np.float32)
+
+
+def test_clean_primary_adjacent_and_neighbourhood_masks():
+    p = 200
+    r = _base_noise(p)
+    m = np.zeros(p, np.float32)                      # flat model: G = 0
+    r[100] = 60.0                                    # B (primary outlier)
+    r[101] = 8.0                                     # C: next to B, > 2 sigma
+    r[102] = 6.0                                     # D: same sign, smaller, > sigma'
+    r[103] = 5.0                                     # D (second pass)
+    r[104] = -4.0                                    # opposite sign: kept
+    r[99] = 1.5                                      # below 2 sigma, same sign, > sigma' -> D
+    used = np.ones(p, np.uint8)
+    keep, k = O.clean_mask(r, m, used, 0.5)
+    # sigma of r over the used pixels, the B rule at k = 3
+    sig = r.astype(np.float64).std()
+    assert k == 3 and 60.0 > 3 * sig and 8.0 < 3 * sig
+    flagged = set(np.where(keep == 0)[0])
+    assert flagged == {99, 100, 101, 102, 103}, flagged
+
+
+def test_clean_flux_gradient_protects_sharp_model_features():
+    p = 200
+    r = _base_noise(p)
+    m = np.zeros(p, np.float32)
+    r[50] = 12.0
+    m[51] = 30.0                                     # steep model gradient at 50
+    keep, _ = O.clean_mask(r, m, np.ones(p, np.uint8), 0.5)
+    assert keep[50] == 1                             # |r| - 0.5 G = 12 - 15 < 3 sigma
+    keep2, _ = O.clean_mask(r, np.zeros(p, np.float32), np.ones(p, np.uint8), 0.5)
+    assert keep2[50] == 0
+
+
+def test_clean_threshold_relaxes_when_many_outliers():
+    p = 300
+    r = _base_noise(p)
+    idx = np.arange(5, 300, 25)                      # 12 outliers = 4% of the pixels
+    r[idx] = np.where(np.arange(len(idx)) % 2 == 0, 5.5, -5.5).astype(np.float32)
+    sig = r.astype(np.float64).std()
+    assert 5.5 > 3 * sig and 5.5 < 4 * sig
+    keep, k = O.clean_mask(r, np.zeros(p, np.float32), np.ones(p, np.uint8), 0.5)
+    assert k == 4 and np.all(keep[idx] == 1)         # at k = 4 none of them is primary
+
+
+def test_clean_ignores_unused_pixels_and_fit_with_outliers():
+    p = 100
+    r = _base_noise(p)
+    r[10] = 90.0
+    used = np.ones(p, np.uint8)
+    used[10] = 0                                     # already masked: not in sigma, stays masked
+    keep, _ = O.clean_mask(r, np.zeros(p, np.float32), used, 0.5)
+    assert keep[10] == 0 and keep.sum() == p - 1
+    # a fit with cosmic-ray spikes: Clean brings the parameters back near the clean-data fit
+    M, d = observed(G, 4, 22, noise=True, snr=(60, 60), mask_frac=0.0)
+    ref = O.fit(M, d["flux"], d["ivar"], d["good"], d["theta0"], max_steps=400)
+    spiky = d["flux"].copy()
+    rng = np.random.default_rng(1)
+    for i in range(4):
+        js = rng.choice(G.n_pix, 12, replace=False)
+        spiky[i, js] += 25.0 * np.median(d["flux"][i])
+    bad = O.fit(M, spiky, d["ivar"], d["good"], d["theta0"], max_steps=400)
+    cln = O.fit(M, spiky, d["ivar"], d["good"], d["theta0"], max_steps=400, clean=1)
+    e_bad = np.abs(bad["theta"] - ref["theta"])[:, 0]
+    e_cln = np.abs(cln["theta"] - ref["theta"])[:, 0]
+    assert np.median(e_cln) < 0.5 * np.median(e_bad), (e_cln, e_bad)
