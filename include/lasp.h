@@ -125,7 +125,21 @@ typedef struct {
                                batch fits only                           */
     int clean_every;        /* mask update every this many steps (30)   */
     int clean_max;          /* at most this many updates (11)           */
+    int optimizer;          /* LASP_OPT_ADAM (stage 8) or LASP_OPT_LM    */
 } lasp_fit_opts;
+
+/* Optimisers.  LASP_OPT_ADAM: the paper's Adam with the three stop rules.
+ * LASP_OPT_LM: the curvature-aware step of the paper's outlook (sec. 4.5):
+ * Levenberg-Marquardt on x for S = sum W eps^2 with the continuum re-solved,
+ * the Jacobian of sqrt(W) eps taken analytically (as for stage 9), FP64
+ * normal equations; parameters held on a bound by the gradient are frozen;
+ * Nielsen's damping rule.  The fit ends with status LASP_ST_CONV_TOL when the
+ * Gauss-Newton predicted decrease g^T A^-1 g falls to tol * S (1e-10 suits
+ * FP32 model values; the Adam default 1e-5 stops far too early) or when ten
+ * damped trials in a row fail, and with LASP_ST_MAXSTEPS after max_steps
+ * accepted steps (steps = accepted steps).  FP32 precision only; no Clean. */
+#define LASP_OPT_ADAM 0
+#define LASP_OPT_LM   1
 
 void lasp_default_opts(lasp_fit_opts* o);
 

@@ -658,3 +658,180 @@ int orc_clean_mask(int p, const float* r, const float* m, const unsigned char* u
     free(G); free(lhs); free(B); free(flag); free(sel); free(nxt);
     return (int)ks[kk];
 }
+
+/* S(x) and the weighted residual r = sqrt(W) eps at x (continuum re-solved). */
+static int lm_eval(const orc_model* M, const double* y, const double* W, const double* x, double* S,
+                   double* r) {
+    double l, g[5], b[8];
+    int p = M->n_pix;
+    double* eps = malloc(sizeof(double) * p);
+    unsigned st = orc_eval(M, y, W, x, &l, g, b, eps, NULL);
+    double s = 0.0;
+    for (int j = 0; j < p; ++j) {
+        double rj = sqrt(W[j]) * eps[j];
+        if (r) r[j] = rj;
+        s += rj * rj;
+    }
+    free(eps);
+    *S = s;
+    return !(st & ORC_ST_SINGULAR) && isfinite(s);
+}
+
+/* Gauss-Newton quantities at x: S, r, the central-difference Jacobian J of r
+ * w.r.t. x (step 1e-4), and the reduced system (Ar, gr) in which parameters
+ * held at a bound of the box by the gradient (x = -1 with g > 0, x = +1 with
+ * g < 0) are frozen (unit row and column, zero gradient).  pred0 = g^T A^-1 g
+ * is the decrease of S that the undamped Gauss-Newton step predicts
+ * (infinite when A is not positive definite).  Returns 0 when an evaluation
+ * fails. */
+static int lm_full(const orc_model* M, const double* y, const double* W, const double* x, double* r,
+                   double* rp, double* rm, double* J, double* S, double* Ar, double* gr, double* pred0) {
+    int p = M->n_pix;
+    if (!lm_eval(M, y, W, x, S, r)) return 0;
+    for (int k = 0; k < 5; ++k) {
+        double xp[5], xm[5], Sp, Sm, h = 1e-4;
+        for (int q = 0; q < 5; ++q) xp[q] = xm[q] = x[q];
+        xp[k] += h;
+        xm[k] -= h;
+        if (!lm_eval(M, y, W, xp, &Sp, rp) || !lm_eval(M, y, W, xm, &Sm, rm)) return 0;
+        for (int j = 0; j < p; ++j) J[(size_t)j * 5 + k] = (rp[j] - rm[j]) / (2.0 * h);
+    }
+    double A[25], g[5], d0[5];
+    int fr[5];
+    for (int a = 0; a < 5; ++a) {
+        g[a] = 0.0;
+        for (int j = 0; j < p; ++j) g[a] += J[(size_t)j * 5 + a] * r[j];
+        for (int c = 0; c < 5; ++c) {
+            double s = 0.0;
+            for (int j = 0; j < p; ++j) s += J[(size_t)j * 5 + a] * J[(size_t)j * 5 + c];
+            A[a * 5 + c] = s;
+        }
+    }
+    for (int a = 0; a < 5; ++a) fr[a] = !((x[a] <= -1.0 && g[a] > 0.0) || (x[a] >= 1.0 && g[a] < 0.0));
+    for (int a = 0; a < 5; ++a) {
+        gr[a] = fr[a] ? g[a] : 0.0;
+        for (int c = 0; c < 5; ++c) Ar[a * 5 + c] = (fr[a] && fr[c]) ? A[a * 5 + c] : (a == c ? 1.0 : 0.0);
+    }
+    double mg[5];
+    for (int a = 0; a < 5; ++a) mg[a] = -gr[a];
+    if (chol_solve(5, Ar, mg, d0)) {
+        double s = 0.0;
+        for (int a = 0; a < 5; ++a) s -= gr[a] * d0[a];
+        *pred0 = s;
+    } else {
+        *pred0 = INFINITY;
+    }
+    return 1;
+}
+
+static void lm_one(const orc_model* M, const orc_opts* O, const float* flux, const float* ivar,
+                   const unsigned char* good, const double* theta0, int max_iter, double rtol,
+                   double* theta, double* loss, int* iters, unsigned* status) {
+    /* S differences below this fraction of S are not trusted: there the
+     * trial is judged by the Gauss-Newton merit pred0 instead. */
+    const double eta = 1e-6;
+    int p = M->n_pix;
+    double* y = malloc(sizeof(double) * p);
+    double* W = malloc(sizeof(double) * p);
+    double* r = malloc(sizeof(double) * p);
+    double* rp = malloc(sizeof(double) * p);
+    double* rm = malloc(sizeof(double) * p);
+    double* J = malloc(sizeof(double) * (size_t)p * 5);
+    double w, x[5], S, Ar[25], gr[5], pred0, lam = 1e-3, nu = 2.0;
+    int n_obj = orc_prep(p, flux, ivar, good, O->quantile, O->edge_px, y, W, &w);
+    for (int k = 0; k < 5; ++k) theta[k] = theta0[k];
+    *loss = NAN;
+    *iters = 0;
+    *status = 0;
+    if (n_obj < M->deg + 1 + 5 || !(w > 0.0) || !isfinite(w)) {
+        *status = ORC_ST_NODATA;
+        goto out;
+    }
+    orc_x_from_phys(M, theta0, x);
+    for (int k = 0; k < 5; ++k) x[k] = x[k] < -1.0 ? -1.0 : (x[k] > 1.0 ? 1.0 : x[k]);
+    if (!lm_full(M, y, W, x, r, rp, rm, J, &S, Ar, gr, &pred0)) { *status = ORC_ST_SINGULAR; goto done; }
+    for (int it = 0;; ++it) {
+        *iters = it;
+        if (pred0 <= rtol * S) { *status = ORC_ST_CONV_TOL; break; }
+        if (it >= max_iter) { *status = ORC_ST_MAXSTEPS; break; }
+        int accepted = 0, have_full = 0;
+        double xn[5], Sn = S, An[25], gn[5], pn = pred0;
+        for (int trial = 0; trial < 10 && !accepted; ++trial) {
+            double Ad[25], rhs[5], d[5], rho = -1.0;
+            for (int q = 0; q < 25; ++q) Ad[q] = Ar[q];
+            for (int a = 0; a < 5; ++a) {
+                Ad[a * 5 + a] += lam * Ar[a * 5 + a];
+                rhs[a] = -gr[a];
+            }
+            if (chol_solve(5, Ad, rhs, d)) {
+                /* predicted decrease of S for d: -(2 g.d + d^T A d) */
+                double pred = 0.0;
+                for (int a = 0; a < 5; ++a) {
+                    double Adv = 0.0;
+                    for (int c = 0; c < 5; ++c) Adv += Ar[a * 5 + c] * d[c];
+                    pred -= 2.0 * gr[a] * d[a] + d[a] * Adv;
+                }
+                for (int q = 0; q < 5; ++q) {
+                    xn[q] = x[q] + d[q];
+                    xn[q] = xn[q] < -1.0 ? -1.0 : (xn[q] > 1.0 ? 1.0 : xn[q]);
+                }
+                if (pred >= eta * S) {
+                    /* gain ratio of S */
+                    double St;
+                    have_full = 0;
+                    if (lm_eval(M, y, W, xn, &St, NULL)) rho = (S - St) / pred;
+                } else {
+                    /* gain ratio of the merit pred0: the model's gradient after
+                     * the step is g + A d = lambda diag(A) d */
+                    have_full = 1;
+                    if (lm_full(M, y, W, xn, r, rp, rm, J, &Sn, An, gn, &pn) && Sn <= S * (1.0 + eta)) {
+                        double gm[5], z[5], pm = 0.0;
+                        for (int a = 0; a < 5; ++a) gm[a] = lam * Ar[a * 5 + a] * d[a];
+                        if (chol_solve(5, Ar, gm, z))
+                            for (int a = 0; a < 5; ++a) pm += gm[a] * z[a];
+                        double den = pred0 - pm > 0.0 ? pred0 - pm : pred0;
+                        rho = (pred0 - pn) / den;
+                    }
+                }
+            }
+            if (rho > 0.0) {
+                /* Nielsen's damping update */
+                double t = 2.0 * rho - 1.0, f = 1.0 - t * t * t;
+                lam *= f > 1.0 / 3.0 ? f : 1.0 / 3.0;
+                if (lam < 1e-12) lam = 1e-12;
+                nu = 2.0;
+                accepted = 1;
+            } else {
+                lam *= nu;
+                nu *= 2.0;
+            }
+        }
+        if (!accepted) { *status = ORC_ST_CONV_TOL; break; }
+        for (int q = 0; q < 5; ++q) x[q] = xn[q];
+        if (have_full) {
+            S = Sn;
+            pred0 = pn;
+            for (int q = 0; q < 25; ++q) Ar[q] = An[q];
+            for (int a = 0; a < 5; ++a) gr[a] = gn[a];
+        } else if (!lm_full(M, y, W, x, r, rp, rm, J, &S, Ar, gr, &pred0)) {
+            *status = ORC_ST_SINGULAR;
+            *iters = it + 1;
+            break;
+        }
+    }
+done:
+    orc_phys_from_x(M, x, theta);
+    *loss = sqrt(S / p);
+out:
+    free(y); free(W); free(r); free(rp); free(rm); free(J);
+}
+
+void orc_fit_lm(const orc_model* M, const orc_opts* O, int n, const float* flux, const float* ivar,
+                const unsigned char* good, const double* theta0, int max_iter, double rtol,
+                double* theta, double* loss, int* iters, unsigned* status, int threads) {
+    int p = M->n_pix;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(threads > 0 ? threads : 1)
+    for (int i = 0; i < n; ++i)
+        lm_one(M, O, flux + (size_t)i * p, ivar + (size_t)i * p, good + (size_t)i * p, theta0 + 5 * i,
+               max_iter, rtol, theta + 5 * i, loss + i, iters + i, status + i);
+}

@@ -141,6 +141,26 @@ void orc_resample(int q, double lam1, double dlam, const double* F, int n_out, d
 int orc_clean_mask(int p, const float* r, const float* m, const unsigned char* used, float fshift,
                    unsigned char* keep);
 
+/* Curvature-aware fit (the paper's outlook, sec. 4.5): Levenberg-Marquardt
+ * on x in [-1,1]^5 minimising S(x) = sum_j W_j eps_j^2 with the continuum
+ * re-solved at every point (the same objective as Eq. 9).  At each iterate:
+ * r = sqrt(W) eps, the Jacobian J of r w.r.t. x by central differences (step
+ * 1e-4, as stage 9), A = J^T J, g = J^T r; parameters held at a bound by the
+ * gradient are frozen; pred0 = g^T A^-1 g (the Gauss-Newton predicted
+ * decrease).  Converged (status 1) when pred0 <= rtol S.  Otherwise trial
+ * steps solve (A + lambda diag A) d = -g, x_t = clamp(x + d).  The gain ratio
+ * rho of a trial is (S - S(x_t)) / pred when the step's predicted decrease
+ * pred is at least 1e-6 S; below that S differences are not trusted and rho
+ * compares pred0(x_t) with the merit the model predicts (requiring also
+ * S(x_t) <= S(1 + 1e-6)).  rho > 0 accepts and scales lambda by
+ * max(1/3, 1 - (2 rho - 1)^3) (floor 1e-12), nu = 2; otherwise lambda x nu,
+ * nu x 2 (Nielsen's damping rule).  Ten rejections in a row stop (status 1);
+ * max_iter accepted steps stop (status 4).  Outputs as orc_fit (iters =
+ * accepted steps). */
+void orc_fit_lm(const orc_model* M, const orc_opts* O, int n, const float* flux, const float* ivar,
+                const unsigned char* good, const double* theta0, int max_iter, double rtol,
+                double* theta, double* loss, int* iters, unsigned* status, int threads);
+
 int orc_max_threads(void);
 
 #ifdef __cplusplus

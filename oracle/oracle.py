@@ -82,6 +82,8 @@ def lib():
                                           ct.c_double, ct.c_double, P]
             _lib.orc_clean_mask.argtypes = [ct.c_int, P, P, P, ct.c_float, P]
             _lib.orc_clean_mask.restype = ct.c_int
+            _lib.orc_fit_lm.argtypes = [P, P, ct.c_int, P, P, P, P, ct.c_int, ct.c_double, P, P, P,
+                                        P, ct.c_int]
         return _lib
 
 
@@ -270,3 +272,20 @@ def clean_mask(r, m, used, fshift):
     keep = np.zeros(len(r), dtype=np.uint8)
     k = lib().orc_clean_mask(len(r), _p(r), _p(m), _p(used), float(fshift), _p(keep))
     return keep, k
+
+
+def fit_lm(M: Model, flux, ivar, good, theta0, max_iter=50, rtol=1e-9, threads=None, **opts):
+    """Levenberg-Marquardt fit of the same objective (curvature-aware step)."""
+    flux = np.ascontiguousarray(flux, dtype=np.float32)
+    ivar = np.ascontiguousarray(ivar, dtype=np.float32)
+    good = np.ascontiguousarray(good, dtype=np.uint8)
+    theta0 = _f64(theta0)
+    n = flux.shape[0]
+    theta, loss = np.zeros((n, 5)), np.zeros(n)
+    iters, status = np.zeros(n, dtype=np.int32), np.zeros(n, dtype=np.uint32)
+    O = make_opts(**opts)
+    if threads is None:
+        threads = lib().orc_max_threads()
+    lib().orc_fit_lm(M.ref, ct.byref(O), n, _p(flux), _p(ivar), _p(good), _p(theta0), int(max_iter),
+                     float(rtol), _p(theta), _p(loss), _p(iters), _p(status), int(threads))
+    return dict(theta=theta, loss=loss, steps=iters, status=status)

@@ -75,6 +75,8 @@ int check_opts(const lasp_fit_opts* o, int n_pix) {
     if (!(o->quantile >= 0.0f && o->quantile <= 1.0f)) return LASP_EINVAL;
     if (o->precision < LASP_PREC_FP32 || o->precision > LASP_PREC_TF32X3) return LASP_EINVAL;
     if (o->clean && (o->clean_every < 1 || o->clean_max < 0)) return LASP_EINVAL;
+    if (o->optimizer != LASP_OPT_ADAM && o->optimizer != LASP_OPT_LM) return LASP_EINVAL;
+    if (o->optimizer == LASP_OPT_LM && (o->precision != LASP_PREC_FP32 || o->clean)) return LASP_EINVAL;
     return LASP_OK;
 }
 
@@ -140,6 +142,7 @@ void lasp_default_opts(lasp_fit_opts* o) {
     o->clean = 0;
     o->clean_every = 30;
     o->clean_max = 11;
+    o->optimizer = LASP_OPT_ADAM;
 }
 
 int lasp_init_interp(const lasp_interp_desc* d, const float* coeff, lasp_interp* out) {
@@ -231,6 +234,30 @@ int lasp_fit_batch(lasp_interp h, const lasp_batch* b, const lasp_fit_opts* o, l
     if (o->precision != LASP_PREC_FP32) {
         if (o->clean) return LASP_EINVAL;          // Clean runs in the FP32 batch fit
         return lasp_tc_fit_batch(h->M, h->tc, b, o, r, stream, &g_last_launches);
+    }
+    if (o->optimizer == LASP_OPT_LM) {
+        LmParams L{};
+        L.M = h->M;
+        L.O = to_dev(o);
+        L.N = b->N;
+        L.max_iter = o->max_steps;
+        L.rtol = o->tol;
+        L.flux = b->flux;
+        L.ivar = b->ivar;
+        L.good = b->good;
+        L.theta0 = b->theta0;
+        L.theta = r->theta;
+        L.loss = r->loss;
+        L.steps = r->steps;
+        L.status = r->status;
+        L.weight = r->weight;
+        cudaStream_t st = (cudaStream_t)stream;
+        int e = dispatch_deg(o->legendre_deg, [&](auto dd) {
+            constexpr int D = decltype(dd)::value;
+            return launch_lm<D>(L, st);
+        });
+        g_last_launches = e ? 0 : 1;
+        return e;
     }
     FitParams P{};
     P.M = h->M;

@@ -3,6 +3,7 @@
 #pragma once
 
 #include "lasp_fit.cuh"
+#include "lasp_lm.cuh"
 #include "lasp_model.cuh"
 
 namespace lasp {
@@ -13,6 +14,7 @@ template <int D> int launch_fit(const FitParams& P, cudaStream_t st);
 template <int D> int launch_errors(const ErrParams& P, cudaStream_t st);
 template <int D> int launch_forward(const ModelParams& P, cudaStream_t st);
 template <int D> int launch_backward(const ModelParams& P, cudaStream_t st);
+template <int D> int launch_lm(const LmParams& P, cudaStream_t st);
 
 #ifdef LASP_DEFINE_LAUNCHERS
 template <typename Kern>
@@ -87,11 +89,29 @@ int launch_backward(const ModelParams& P, cudaStream_t st) {
     return cuda_rc(cudaGetLastError());
 }
 
+template <int D>
+int launch_lm(const LmParams& P, cudaStream_t st) {
+    const int p = P.M.n_pix, H = P.M.pad, nm = P.M.n_model;
+    if (p <= 16 * 256) {
+        size_t smem = lm_smem_bytes(p, H, nm, 256);
+        int e = set_smem_attr(lm_kernel<256, D>, smem);
+        if (e) return e;
+        lm_kernel<256, D><<<P.N, 256, smem, st>>>(P);
+    } else {
+        size_t smem = lm_smem_bytes(p, H, nm, 512);
+        int e = set_smem_attr(lm_kernel<512, D>, smem);
+        if (e) return e;
+        lm_kernel<512, D><<<P.N, 512, smem, st>>>(P);
+    }
+    return cuda_rc(cudaGetLastError());
+}
+
 #define LASP_INSTANTIATE(D)                                                  \
     template int launch_fit<D>(const FitParams&, cudaStream_t);             \
     template int launch_errors<D>(const ErrParams&, cudaStream_t);          \
     template int launch_forward<D>(const ModelParams&, cudaStream_t);       \
-    template int launch_backward<D>(const ModelParams&, cudaStream_t);
+    template int launch_backward<D>(const ModelParams&, cudaStream_t);      \
+    template int launch_lm<D>(const LmParams&, cudaStream_t);
 #endif
 
 }  // namespace lasp

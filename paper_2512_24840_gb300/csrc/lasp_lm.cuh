@@ -1,0 +1,457 @@
+// Curvature-aware fit (the paper's outlook, sec. 4.5): Levenberg-Marquardt on
+// x in [-1,1]^5 for S(x) = sum_j W_j eps_j^2 with the continuum re-solved at
+// every point -- the objective of Eq. 9.  One CTA per spectrum.  A full
+// evaluation takes the Jacobian of r = sqrt(W) eps analytically (forward mode
+// through Eq. 5 and the normal equations, as for stage 9) and forms A = J^T J
+// and g = J^T r in FP64; parameters held on a bound by the gradient are
+// frozen, and pred0 = g^T A^-1 g (the Gauss-Newton predicted decrease) is
+// both the stop test (pred0 <= rtol S) and, where S differences fall below
+// what FP32 model values resolve (1e-6 S), the merit that judges a trial.
+// Damped steps (A + lambda diag A) d = -g follow Nielsen's damping rule.
+// Thread 0 runs the control logic; all threads evaluate.
+#pragma once
+
+#include "lasp.h"
+#include "lasp_common.cuh"
+
+namespace lasp {
+
+struct LmParams {
+    ModelDev M;
+    FitOpts O;
+    int N;
+    int max_iter;
+    double rtol;
+    const float* flux;
+    const float* ivar;
+    const uint8_t* good;
+    const float* theta0;
+    float* theta;
+    float* loss;
+    int32_t* steps;
+    uint32_t* status;
+    float* weight;
+};
+
+__host__ inline size_t lm_smem_bytes(int p, int H, int n_model, int NT) {
+    size_t fl = (size_t)2 * ((p + 3) & ~3) + 4 * (size_t)((n_model + 3) & ~3) + 3 * 96 + 4 * KMAX +
+                (size_t)(NT / 32) * 48 + 256;
+    size_t sortb = (size_t)2 * ((p + 3) & ~3) + next_pow2(p);
+    return 4 * (fl > sortb ? fl : sortb);
+}
+
+// Evaluate at physical theta (block-wide).  FULL: also the Jacobian sums
+// A (15, packed upper triangle, x units), g (5, x units).  Returns S in
+// s_S[0] (and s_ok: 1 if the normal equations were solvable).
+template <int NT, int D, bool FULL>
+__device__ void lm_eval(const ModelDev& M, const float* th, const float* y, const float* W, float* Fp,
+                        int na, float* g, float* gmu, float* gsg, float* phi, float* dphi, float* red,
+                        double* outd, double* s_G, double* s_b, double* s_db, double* s_sum, int* s_h,
+                        int* s_ok) {
+    using Gm = Gram<D>;
+    constexpr int NB = D + 1;
+    constexpr int NV = Gm::NV;
+    const int p = M.n_pix, H = M.pad, nm = M.n_model, K = M.K;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (warp == 0) {
+        if (lane < K) basis_term(M, lane, th, phi, FULL ? dphi : nullptr);
+        const int h = kernel_taps_warp(th[3] / M.kms_px, th[4] / M.kms_px, H, g, gmu, gsg);
+        if (lane == 0) *s_h = h;
+    }
+    __syncthreads();
+    const int h = *s_h;
+    for (int mm = tid; mm < nm; mm += NT) {
+        float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+        for (int k = 0; k < K; ++k) {
+            const float c = __ldg(M.C + (size_t)k * nm + mm);
+            a0 = fmaf(phi[k], c, a0);
+            if (FULL) {
+                a1 = fmaf(dphi[3 * k + 0], c, a1);
+                a2 = fmaf(dphi[3 * k + 1], c, a2);
+                a3 = fmaf(dphi[3 * k + 2], c, a3);
+            }
+        }
+        Fp[mm] = a0;
+        if (FULL) {
+            Fp[na + mm] = a1;
+            Fp[2 * na + mm] = a2;
+            Fp[3 * na + mm] = a3;
+        }
+    }
+    __syncthreads();
+    float f[PPT], df[FULL ? 5 : 1][PPT];
+    float gacc[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) gacc[q] = 0.0f;
+    const float ikms = 1.0f / M.kms_px;
+#pragma unroll
+    for (int r = 0; r < PPT; ++r) {
+        const int j = tid + r * NT;
+        f[r] = 0.0f;
+        if (FULL)
+#pragma unroll
+            for (int k = 0; k < 5; ++k) df[k][r] = 0.0f;
+        if (j < p) {
+            float a0 = 0, a1 = 0, a2 = 0, a3 = 0, am = 0, as = 0;
+            for (int s = -h; s <= h; ++s) {
+                const int o = j + H - s;
+                const float gs = g[s + H];
+                const float fv = Fp[o];
+                a0 = fmaf(gs, fv, a0);
+                if (FULL) {
+                    a1 = fmaf(gs, Fp[na + o], a1);
+                    a2 = fmaf(gs, Fp[2 * na + o], a2);
+                    a3 = fmaf(gs, Fp[3 * na + o], a3);
+                    am = fmaf(gmu[s + H], fv, am);
+                    as = fmaf(gsg[s + H], fv, as);
+                }
+            }
+            f[r] = a0;
+            if (FULL) {
+                df[0][r] = a1;
+                df[1][r] = a2;
+                df[2][r] = a3;
+                df[3][r] = am * ikms;
+                df[4][r] = as * ikms;
+            }
+            const float Wj = W[j];
+            if (Wj != 0.0f) {
+                float Pl[NB];
+                legendre<D>(legendre_node(j, p), Pl);
+                const float vv = Wj * a0 * a0, uu = Wj * a0 * y[j];
+#pragma unroll
+                for (int a = 0; a < NB; ++a) {
+#pragma unroll
+                    for (int b2 = a; b2 < NB; ++b2) gacc[Gm::idx(a, b2)] = fmaf(vv * Pl[a], Pl[b2], gacc[Gm::idx(a, b2)]);
+                    gacc[Gm::NG + a] = fmaf(uu, Pl[a], gacc[Gm::NG + a]);
+                }
+            }
+        }
+    }
+    block_sum_f64<NV, NT>(gacc, red, outd);
+    if (tid == 0) {
+        for (int q = 0; q < NV; ++q) s_G[q] = outd[q];
+        double bd[NB];
+        *s_ok = chol_solve_rcp<D, double>(s_G, s_G + Gm::NG, bd) ? 1 : 0;
+        for (int a = 0; a < NB; ++a) s_b[a] = bd[a];
+    }
+    __syncthreads();
+    if (!*s_ok) return;
+    float bl[NB];
+#pragma unroll
+    for (int a = 0; a < NB; ++a) bl[a] = (float)s_b[a];
+    if (!FULL) {
+        float sacc[1] = {0.0f};
+#pragma unroll
+        for (int r = 0; r < PPT; ++r) {
+            const int j = tid + r * NT;
+            if (j < p && W[j] != 0.0f) {
+                float Pl[NB];
+                legendre<D>(legendre_node(j, p), Pl);
+                float c = 0.0f;
+#pragma unroll
+                for (int a = 0; a < NB; ++a) c = fmaf(bl[a], Pl[a], c);
+                const float e = y[j] - c * f[r];
+                sacc[0] = fmaf(W[j] * e, e, sacc[0]);
+            }
+        }
+        block_sum_f64<1, NT>(sacc, red, outd);
+        if (tid == 0) s_sum[0] = outd[0];
+        __syncthreads();
+        return;
+    } else {
+        // d b / d theta_k = G^-1 sum_j W_j P_d dF''_jk (eps_j - F''_j c_j); S
+        constexpr int NT2 = 5 * NB + 1;
+        float tacc[NT2];
+#pragma unroll
+        for (int q = 0; q < NT2; ++q) tacc[q] = 0.0f;
+        float cc[PPT];
+#pragma unroll
+        for (int r = 0; r < PPT; ++r) {
+            const int j = tid + r * NT;
+            cc[r] = 0.0f;
+            if (j < p && W[j] != 0.0f) {
+                float Pl[NB];
+                legendre<D>(legendre_node(j, p), Pl);
+                float c = 0.0f;
+#pragma unroll
+                for (int a = 0; a < NB; ++a) c = fmaf(bl[a], Pl[a], c);
+                cc[r] = c;
+                const float Wj = W[j];
+                const float e = y[j] - c * f[r];
+                const float q = Wj * (e - f[r] * c);
+#pragma unroll
+                for (int k = 0; k < 5; ++k)
+#pragma unroll
+                    for (int a = 0; a < NB; ++a) tacc[k * NB + a] = fmaf(q * df[k][r], Pl[a], tacc[k * NB + a]);
+                tacc[5 * NB] = fmaf(Wj * e, e, tacc[5 * NB]);
+            }
+        }
+        block_sum_f64<NT2, NT>(tacc, red, outd);
+        if (tid < 5) {
+            double tk[NB], dbk[NB];
+            for (int a = 0; a < NB; ++a) tk[a] = outd[tid * NB + a];
+            chol_solve_rcp<D, double>(s_G, tk, dbk);
+            for (int a = 0; a < NB; ++a) s_db[tid * NB + a] = dbk[a];
+        }
+        if (tid == 0) s_sum[0] = outd[5 * NB];
+        __syncthreads();
+        float dbl[5][NB];
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+#pragma unroll
+            for (int a = 0; a < NB; ++a) dbl[k][a] = (float)s_db[k * NB + a];
+        // J in x units (physical J times the half box width), A = J^T J, g = J^T r
+        float jj[20];
+#pragma unroll
+        for (int q = 0; q < 20; ++q) jj[q] = 0.0f;
+#pragma unroll
+        for (int r = 0; r < PPT; ++r) {
+            const int j = tid + r * NT;
+            if (j < p && W[j] != 0.0f) {
+                float Pl[NB];
+                legendre<D>(legendre_node(j, p), Pl);
+                const float sw = sqrtf(W[j]);
+                const float rj = sw * (y[j] - cc[r] * f[r]);
+                float Jr[5];
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    float dc = 0.0f;
+#pragma unroll
+                    for (int a = 0; a < NB; ++a) dc = fmaf(dbl[k][a], Pl[a], dc);
+                    Jr[k] = -sw * (cc[r] * df[k][r] + f[r] * dc) * M.phalf[k];
+                }
+                int q = 0;
+#pragma unroll
+                for (int a = 0; a < 5; ++a)
+#pragma unroll
+                    for (int b2 = a; b2 < 5; ++b2) {
+                        jj[q] = fmaf(Jr[a], Jr[b2], jj[q]);
+                        ++q;
+                    }
+#pragma unroll
+                for (int a = 0; a < 5; ++a) jj[15 + a] = fmaf(Jr[a], rj, jj[15 + a]);
+            }
+        }
+        block_sum_f64<20, NT>(jj, red, outd);
+        if (tid < 20) s_sum[1 + tid] = outd[tid];
+        __syncthreads();
+    }
+}
+
+enum : int { LM_FULL_CUR = 0, LM_FULL_TRIAL = 1, LM_S_TRIAL = 2, LM_DONE = 3 };
+
+// Control state of one CTA (shared memory, touched by thread 0 only).
+struct LmCtl {
+    double S, pred0, lam, nu, pred;
+    double Ar[15], gr[5];   // reduced system at the current point
+    double An[15], gn[5];   // at the trial point (full trial evaluations)
+    double d[5];
+    double Sn, pn;
+    int it, trial, phase;
+    uint32_t status;
+};
+
+// Reduced system from the sums of a full evaluation at x: parameters on a
+// bound whose gradient points out of the box are frozen (unit row/column,
+// zero gradient); pred0 = g^T A^-1 g (infinite if A is not positive definite).
+__device__ inline void lm_reduce(const double* sum, const float* x, double* Ar, double* gr, double& S,
+                                 double& pred0) {
+    S = sum[0];
+    bool fr[5];
+    for (int a = 0; a < 5; ++a) {
+        const double ga = sum[16 + a];
+        fr[a] = !((x[a] <= -1.0f && ga > 0.0) || (x[a] >= 1.0f && ga < 0.0));
+        gr[a] = fr[a] ? ga : 0.0;
+    }
+    int q = 0;
+    for (int a = 0; a < 5; ++a)
+        for (int b = a; b < 5; ++b, ++q) Ar[q] = (fr[a] && fr[b]) ? sum[1 + q] : (a == b ? 1.0 : 0.0);
+    double mg[5], d0[5];
+    for (int a = 0; a < 5; ++a) mg[a] = -gr[a];
+    if (chol_solve_rcp<4, double>(Ar, mg, d0)) {
+        double s = 0.0;
+        for (int a = 0; a < 5; ++a) s -= gr[a] * d0[a];
+        pred0 = s;
+    } else {
+        pred0 = INFINITY;
+    }
+}
+
+// Next damped trial from the current point (after a rejection or a new
+// iterate).  Sets c.phase to the evaluation the trial needs, or LM_DONE after
+// ten rejections.
+__device__ inline void lm_start_trial(LmCtl& c, const float* x, float* xt) {
+    constexpr double kEta = 1e-6;
+    for (;;) {
+        if (c.trial >= 10) {
+            c.status = LASP_ST_CONV_TOL;
+            c.phase = LM_DONE;
+            return;
+        }
+        double Ad[15], rhs[5];
+        for (int q = 0; q < 15; ++q) Ad[q] = c.Ar[q];
+        for (int a = 0; a < 5; ++a) {
+            Ad[Gram<4>::idx(a, a)] += c.lam * c.Ar[Gram<4>::idx(a, a)];
+            rhs[a] = -c.gr[a];
+        }
+        if (chol_solve_rcp<4, double>(Ad, rhs, c.d)) break;
+        c.lam *= c.nu;
+        c.nu *= 2.0;
+        ++c.trial;
+    }
+    // predicted decrease of S: -(2 g.d + d^T A d)
+    double pred = 0.0;
+    for (int a = 0; a < 5; ++a) {
+        double Adv = 0.0;
+        for (int b = 0; b < 5; ++b) Adv += c.Ar[a <= b ? Gram<4>::idx(a, b) : Gram<4>::idx(b, a)] * c.d[b];
+        pred -= 2.0 * c.gr[a] * c.d[a] + c.d[a] * Adv;
+    }
+    c.pred = pred;
+    for (int k = 0; k < 5; ++k) xt[k] = fminf(1.0f, fmaxf(-1.0f, x[k] + (float)c.d[k]));
+    c.phase = pred >= kEta * c.S ? LM_S_TRIAL : LM_FULL_TRIAL;
+}
+
+__device__ inline void lm_new_iterate(LmCtl& c, const float* x, float* xt, int max_iter, double rtol) {
+    if (c.pred0 <= rtol * c.S) {
+        c.status = LASP_ST_CONV_TOL;
+        c.phase = LM_DONE;
+    } else if (c.it >= max_iter) {
+        c.status = LASP_ST_MAXSTEPS;
+        c.phase = LM_DONE;
+    } else {
+        c.trial = 0;
+        lm_start_trial(c, x, xt);
+    }
+}
+
+// Thread 0, after the evaluation of phase ph.
+static __device__ __noinline__ void lm_control(LmCtl& c, int ph, int ok, const double* sum, float* x, float* xt,
+                                        int max_iter, double rtol) {
+    constexpr double kEta = 1e-6;
+    if (ph == LM_FULL_CUR) {
+        if (!ok) {
+            c.status = LASP_ST_SINGULAR;
+            c.phase = LM_DONE;
+            return;
+        }
+        lm_reduce(sum, x, c.Ar, c.gr, c.S, c.pred0);
+        lm_new_iterate(c, x, xt, max_iter, rtol);
+        return;
+    }
+    double rho = -1.0;
+    if (ph == LM_S_TRIAL) {
+        const double St = sum[0];
+        if (ok && isfinite(St)) rho = (c.S - St) / c.pred;
+    } else if (ok) {
+        lm_reduce(sum, xt, c.An, c.gn, c.Sn, c.pn);
+        if (isfinite(c.Sn) && c.Sn <= c.S * (1.0 + kEta)) {
+            // merit the model predicts: its gradient after the step is lambda diag(A) d
+            double gm[5], z[5], pm = 0.0;
+            for (int a = 0; a < 5; ++a) gm[a] = c.lam * c.Ar[Gram<4>::idx(a, a)] * c.d[a];
+            if (chol_solve_rcp<4, double>(c.Ar, gm, z))
+                for (int a = 0; a < 5; ++a) pm += gm[a] * z[a];
+            const double den = c.pred0 - pm > 0.0 ? c.pred0 - pm : c.pred0;
+            rho = (c.pred0 - c.pn) / den;
+        }
+    }
+    if (rho > 0.0) {
+        const double t = 2.0 * rho - 1.0, f = 1.0 - t * t * t;
+        c.lam *= f > 1.0 / 3.0 ? f : 1.0 / 3.0;
+        if (c.lam < 1e-12) c.lam = 1e-12;
+        c.nu = 2.0;
+        for (int k = 0; k < 5; ++k) x[k] = xt[k];
+        ++c.it;
+        if (ph == LM_S_TRIAL) {
+            c.phase = LM_FULL_CUR;
+        } else {
+            c.S = c.Sn;
+            c.pred0 = c.pn;
+            for (int q = 0; q < 15; ++q) c.Ar[q] = c.An[q];
+            for (int a = 0; a < 5; ++a) c.gr[a] = c.gn[a];
+            lm_new_iterate(c, x, xt, max_iter, rtol);
+        }
+    } else {
+        c.lam *= c.nu;
+        c.nu *= 2.0;
+        ++c.trial;
+        lm_start_trial(c, x, xt);
+    }
+}
+
+template <int NT, int D>
+__global__ void __launch_bounds__(NT) lm_kernel(const LmParams P) {
+    extern __shared__ __align__(16) float sm[];
+    const ModelDev& M = P.M;
+    const int p = M.n_pix, nm = M.n_model;
+    const int tid = threadIdx.x;
+    const int i = blockIdx.x;
+    const int pa = (p + 3) & ~3, na = (nm + 3) & ~3;
+    float* y = sm;
+    float* W = y + pa;
+    float* Fp = W + pa;
+    float* g = Fp + 4 * na;
+    float* gmu = g + 96;
+    float* gsg = g + 192;
+    float* phi = g + 288;
+    float* dphi = phi + KMAX;
+    float* red = phi + 4 * KMAX;
+    float* outf = red + (NT / 32) * 48;
+    double* outd = reinterpret_cast<double*>(outf + ((((size_t)(outf - sm)) & 1) ? 1 : 0));
+    __shared__ double s_G[Gram<D>::NV], s_b[D + 1], s_db[5 * (D + 1)], s_sum[21];
+    __shared__ float s_x[5], s_xt[5];
+    __shared__ int s_h, s_ok;
+    __shared__ LmCtl c;
+    const size_t row = (size_t)i * p;
+    float w;
+    const int n_obj = prep_spectrum<NT>(P.flux + row, P.ivar + row, P.good + row, p, P.O.edge_px,
+                                        P.O.quantile, y, W, Fp, red, &w);
+    if (tid == 0) {
+        for (int k = 0; k < 5; ++k) {
+            float xx = (P.theta0[5 * i + k] - M.plo[k]) / M.phalf[k] - 1.0f;
+            s_x[k] = fminf(1.0f, fmaxf(-1.0f, xx));
+        }
+        if (P.weight) P.weight[i] = w;
+        c.lam = 1e-3;
+        c.nu = 2.0;
+        c.it = 0;
+        c.trial = 0;
+        c.status = 0;
+        c.S = NAN;
+        c.phase = LM_FULL_CUR;
+    }
+    __syncthreads();
+    if (n_obj < D + 1 + 5 || !(w > 0.0f) || !isfinite(w)) {
+        if (tid == 0) {
+            for (int k = 0; k < 5; ++k) P.theta[5 * i + k] = phys_of(M, k, s_x[k]);
+            P.loss[i] = NAN;
+            P.steps[i] = 0;
+            P.status[i] = LASP_ST_NODATA;
+        }
+        return;
+    }
+    for (;;) {
+        __syncthreads();
+        const int ph = c.phase;
+        if (ph == LM_DONE) break;
+        const float* xp = ph == LM_FULL_CUR ? s_x : s_xt;
+        float th[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) th[k] = phys_of(M, k, xp[k]);
+        if (ph == LM_S_TRIAL)
+            lm_eval<NT, D, false>(M, th, y, W, Fp, na, g, gmu, gsg, phi, dphi, red, outd, s_G, s_b, s_db,
+                                  s_sum, &s_h, &s_ok);
+        else
+            lm_eval<NT, D, true>(M, th, y, W, Fp, na, g, gmu, gsg, phi, dphi, red, outd, s_G, s_b, s_db,
+                                 s_sum, &s_h, &s_ok);
+        if (tid == 0) lm_control(c, ph, s_ok, s_sum, s_x, s_xt, P.max_iter, P.rtol);
+    }
+    if (tid == 0) {
+        for (int k = 0; k < 5; ++k) P.theta[5 * i + k] = phys_of(M, k, s_x[k]);
+        P.loss[i] = (float)sqrt(c.S / p);
+        P.steps[i] = c.it;
+        P.status[i] = c.status;
+    }
+}
+
+}  // namespace lasp

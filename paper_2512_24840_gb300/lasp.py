@@ -21,6 +21,7 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EGRID, ENODEV = 0, -1, -2, -3, -4, -5, -6
 ST_CONV_TOL, ST_CONV_RISE, ST_MAXSTEPS, ST_NONPOS = 1, 2, 4, 8
 ST_NONFINITE, ST_SINGULAR, ST_NODATA, ST_RUNNING = 16, 32, 64, 128
 PREC = {"fp32": 0, "tf32": 1, "bf16": 2, "tf32x3": 3}
+OPTIMIZER = {"adam": 0, "lm": 1}
 
 _lock = threading.Lock()
 _lib = None
@@ -49,7 +50,8 @@ class FitOpts(ct.Structure):
                 ("eps", ct.c_float), ("tol", ct.c_float), ("window", ct.c_int),
                 ("max_steps", ct.c_int), ("legendre_deg", ct.c_int), ("edge_px", ct.c_int),
                 ("quantile", ct.c_float), ("precision", ct.c_int), ("fp64_normal_eq", ct.c_int),
-                ("clean", ct.c_int), ("clean_every", ct.c_int), ("clean_max", ct.c_int)]
+                ("clean", ct.c_int), ("clean_every", ct.c_int), ("clean_max", ct.c_int),
+                ("optimizer", ct.c_int)]
 
 
 class Result(ct.Structure):
@@ -139,6 +141,8 @@ def default_opts(**kw) -> FitOpts:
     for k, v in kw.items():
         if k == "precision" and isinstance(v, str):
             v = PREC[v]
+        if k == "optimizer" and isinstance(v, str):
+            v = OPTIMIZER[v]
         if not hasattr(o, k):
             raise TypeError(f"unknown fit option {k}")
         setattr(o, k, v)

@@ -494,3 +494,44 @@ def test_clean_ignores_unused_pixels_and_fit_with_outliers():
     e_bad = np.abs(bad["theta"] - ref["theta"])[:, 0]
     e_cln = np.abs(cln["theta"] - ref["theta"])[:, 0]
     assert np.median(e_cln) < 0.5 * np.median(e_bad), (e_cln, e_bad)
+
+
+# ------------------------------------------ curvature-aware step (sec. 4.5 outlook)
+
+def test_lm_recovers_truth_and_reaches_a_stationary_point():
+    M, d = observed(G, 6, 23, noise=False, mask_frac=0.0)
+    res = O.fit_lm(M, d["flux"], d["ivar"], d["good"], d["theta0"], max_iter=60, rtol=1e-12)
+    err = np.abs(res["theta"] - d["truth"])[:, :4]
+    assert np.all(err <= np.array([0.05, 5e-4, 5e-4, 5e-3])), err
+    assert np.all(res["steps"] < 60)
+    # noisy: the LM point is stationary (analytic gradient ~ 0) and no worse than Adam's
+    M, d = observed(G, 4, 24, noise=True, snr=(30, 30), mask_frac=0.05)
+    lm = O.fit_lm(M, d["flux"], d["ivar"], d["good"], d["theta0"], max_iter=60, rtol=1e-12)
+    ad = O.fit(M, d["flux"], d["ivar"], d["good"], d["theta0"], max_steps=2000)
+    for i in range(4):
+        y, W, _, _ = O.prep(d["flux"][i], d["ivar"][i], d["good"][i])
+        r = O.evaluate(M, y, W, O.x_from_phys(M, lm["theta"][i]))
+        x = O.x_from_phys(M, lm["theta"][i])
+        inner = np.abs(x) < 0.999                     # components not on the box edge
+        assert np.all(np.abs(r["grad"][inner]) < 1e-5 * max(r["loss"], 1e-12) * 1e3)
+        assert lm["loss"][i] <= ad["loss"][i] * (1 + 1e-9)
+
+
+def test_lm_stops_at_a_kkt_point_of_the_box():
+    """Low signal-to-noise fits that end on the box edge: interior components
+    are stationary, edge components have a gradient pointing out of the box
+    (the first-order conditions of a bound-constrained minimum)."""
+    M, d = observed(G, 16, 25, noise=True, snr=(3, 6), mask_frac=0.05)
+    lm = O.fit_lm(M, d["flux"], d["ivar"], d["good"], d["theta0"], max_iter=200, rtol=1e-12)
+    assert np.all(lm["status"] == 1)
+    on_edge = 0
+    for i in range(16):
+        y, W, _, _ = O.prep(d["flux"][i], d["ivar"][i], d["good"][i])
+        x = O.x_from_phys(M, lm["theta"][i])
+        g = O.evaluate(M, y, W, x)["grad"]
+        lo, hi = x <= -1 + 1e-12, x >= 1 - 1e-12
+        on_edge += int(np.any(lo | hi))
+        scale = 1e-2 * lm["loss"][i]
+        assert np.all(np.abs(g[~(lo | hi)]) < scale), (i, g, x)
+        assert np.all(g[lo] > -scale) and np.all(g[hi] < scale), (i, g, x)
+    assert on_edge >= 1
