@@ -143,6 +143,73 @@ def make_table(grid: Grid, seed: int = TABLE_SEED, n_lines: int | None = None) -
     return C.astype(np.float32)
 
 
+# ---- piecewise emulator (Eq. 1 with Teff regimes f1..f5; section 3.1) ----
+# Three regimes ordered by Teff with the term counts of the paper's cold, warm
+# and hot models (25, 26, 19): all 20 monomials of total degree <= 3 plus five
+# quartic terms (cold), the 26 terms above (warm), the cubic set without the
+# pure [Fe/H]^3 term (hot).
+EXPS_COLD = np.ascontiguousarray(EXPS[:25])
+EXPS_WARM = EXPS
+EXPS_HOT = np.ascontiguousarray(np.array([e for e in EXPS[:20] if tuple(e) != (0, 0, 3)],
+                                         dtype=np.int8))
+PW_EXPS = (EXPS_COLD, EXPS_WARM, EXPS_HOT)
+assert [len(e) for e in PW_EXPS] == [25, 26, 19]
+# Blend intervals of Eq. 1: cold <= 4000 K < cold/warm <= 4550 K < warm
+# <= 7000 K < warm/hot <= 9000 K < hot.
+TEFF_BLEND = (4000.0, 4550.0, 7000.0, 9000.0)
+# Parameter box of the piecewise workloads (Teff spans all five ranges).
+PW_BOX_LO = np.array([3200.0, 0.5, -2.5, -300.0, 30.0])
+PW_BOX_HI = np.array([12000.0, 5.5, 1.0, 300.0, 200.0])
+# Basis box of each regime: its own Teff support, the common log g, [Fe/H].
+PW_BASIS_LO = tuple(np.array([math.log10(t), 0.5, -2.5]) for t in (3200.0, 4000.0, 7000.0))
+PW_BASIS_HI = tuple(np.array([math.log10(t), 5.5, 1.0]) for t in (4550.0, 9000.0, 12000.0))
+
+
+def make_piecewise_tables(grid: Grid, seed: int = TABLE_SEED + 1) -> list:
+    """Coefficient tables (K_r x n_model, float32) of a three-regime synthetic
+    emulator on the padded grid of `grid`, coolest first.  The regimes share
+    one line list (as emulators fitted to one spectral library would); lines
+    are deeper in the cold regime and shallower in the hot one, continua
+    redder to bluer, and each regime draws its own smooth depth polynomial, so
+    neighbouring regimes differ where they blend."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = grid.n_model
+    m = np.arange(n, dtype=np.float64)
+    t = 2.0 * m / (n - 1) - 1.0
+    lam_lo = math.exp(grid.ln_lambda0_model)
+    lam_hi = math.exp(grid.ln_lambda0_model + (n - 1) * grid.dln)
+    n_lines = int(round((lam_hi - lam_lo) / 10.0))
+    centres = rng.uniform(2.0, n - 3.0, size=n_lines)
+    widths = rng.uniform(10.0, 30.0, size=n_lines) / grid.kms_per_px
+    a0 = rng.uniform(0.05, 0.5, size=n_lines)
+    profs = []
+    for l in range(n_lines):
+        lo = max(0, int(centres[l] - 8 * widths[l] - 2))
+        hi = min(n, int(centres[l] + 8 * widths[l] + 3))
+        mm = m[lo:hi]
+        s2 = widths[l] * math.sqrt(2.0)
+        profs.append((lo, hi, widths[l] * math.sqrt(math.pi / 2.0) * (
+            erf((mm + 0.5 - centres[l]) / s2) - erf((mm - 0.5 - centres[l]) / s2))))
+    out = []
+    for exps, depth_scale, slope in zip(PW_EXPS, (1.3, 1.0, 0.5), (0.15, 0.0, -0.15)):
+        K = len(exps)
+        deg = np.maximum(exps.sum(axis=1), 1)
+        C = np.zeros((K, n))
+        C[0] = 1.0 + slope * t
+        for k in range(K):
+            amp = 0.05 if k == 0 else 0.02 / deg[k]
+            for d in range(1, 4):
+                C[k] += rng.normal(0.0, amp) * np.cos(math.pi * d * (t + 1.0) / 2.0)
+        depth = np.zeros((K, n_lines))
+        depth[0] = depth_scale * a0
+        for k in range(1, K):
+            depth[k] = rng.normal(0.0, 0.15 * depth_scale * a0 / deg[k])
+        for l, (lo, hi, prof) in enumerate(profs):
+            C[:, lo:hi] -= depth[:, l:l + 1] * prof[None, :]
+        out.append(C.astype(np.float32))
+    return out
+
+
 def _mask_runs(rng, grid: Grid, frac: float) -> np.ndarray:
     """1 = pixel used, 0 = masked.  Contiguous runs of 3-12 px until about
     `frac` of the pixels are masked, plus the Na D region 5885-5900 A, the
@@ -163,7 +230,7 @@ def _mask_runs(rng, grid: Grid, frac: float) -> np.ndarray:
 def draw_batch(grid: Grid, n_spec: int, seed: int, *, snr=(5.0, 100.0), mask_frac=0.05,
                mask_frac_max=None, init: str = "cfi", noise: bool = True,
                teff=(4000.0, 7000.0), logg=(1.0, 5.0), feh=(-2.0, 0.5),
-               rv=(-200.0, 200.0), sig=(50.0, 150.0)) -> dict:
+               rv=(-200.0, 200.0), sig=(50.0, 150.0), box=None) -> dict:
     """Random draws for `n_spec` spectra on `grid`.
 
     Returns truth (N x 5 physical), b_true (N x 7 continuum coefficients,
@@ -172,7 +239,9 @@ def draw_batch(grid: Grid, n_spec: int, seed: int, *, snr=(5.0, 100.0), mask_fra
     initial guess), snr (N), z (N x n_pix unit normals), good (N x n_pix mask,
     1 = used).  init='cfi' perturbs the truth by N(0, diag(200 K, 0.3, 0.2,
     15 km/s, 20 km/s)) and clips to the box (a stand-in for the CFI initial
-    values); init='fixed' is (7500 K, 3, -0.5, 0, 100) (section 4.2.1)."""
+    values); init='fixed' is (7500 K, 3, -0.5, 0, 100) (section 4.2.1).
+    box: (lo, hi) physical bounds that theta0 is clipped to (default the
+    single-regime box BOX_LO/BOX_HI)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     N, n = n_spec, grid.n_pix
     truth = np.stack([rng.uniform(*teff, N), rng.uniform(*logg, N), rng.uniform(*feh, N),
@@ -184,7 +253,8 @@ def draw_batch(grid: Grid, n_spec: int, seed: int, *, snr=(5.0, 100.0), mask_fra
     b_true = scale[:, None] * np.concatenate([np.ones((N, 1)), beta], axis=1)
     if init == "cfi":
         theta0 = truth + rng.normal(0.0, 1.0, (N, 5)) * np.array([200.0, 0.3, 0.2, 15.0, 20.0])
-        theta0 = np.clip(theta0, BOX_LO, BOX_HI)
+        blo, bhi = (BOX_LO, BOX_HI) if box is None else box
+        theta0 = np.clip(theta0, blo, bhi)
     elif init == "fixed":
         theta0 = np.tile(np.array([7500.0, 3.0, -0.5, 0.0, 100.0]), (N, 1))
     elif init == "truth":
@@ -230,5 +300,7 @@ def workload(name: str):
         "mixed65536": (LAMOST, 65536, 3, dict(snr=(5.0, 100.0), mask_frac=0.05)),
         "stream_lamost": (LAMOST, 4096, 4, dict(snr=(5.0, 100.0), mask_frac=0.0, mask_frac_max=0.2)),
         "stream_desi": (DESI, 4096, 4, dict(snr=(5.0, 100.0), mask_frac=0.0, mask_frac_max=0.2)),
+        "piecewise4096": (LAMOST, 4096, 5, dict(snr=(5.0, 100.0), mask_frac=0.05,
+                                                 teff=(3300.0, 11500.0), box=(PW_BOX_LO, PW_BOX_HI))),
     }
     return table[name]

@@ -51,23 +51,67 @@ static double ipow(double u, int a) {
     return r;
 }
 
-/* Eq. 1 with one polynomial regime: phi_k = u_T^a u_g^b u_f^c, the u's the
- * basis variables (log10 Teff, log g, [Fe/H]) mapped linearly onto [-1, 1]. */
-void orc_basis(const orc_model* M, const double* th, double* phi, double* dphi) {
-    double v[3] = {log10(th[0]), th[1], th[2]};
-    double u[3], du[3];
-    for (int i = 0; i < 3; ++i) {
-        u[i] = 2.0 * (v[i] - M->blo[i]) / (M->bhi[i] - M->blo[i]) - 1.0;
-        du[i] = 2.0 / (M->bhi[i] - M->blo[i]);
+/* Weight of regime r of the piecewise emulator at Teff T (Eq. 1: f1 = cold,
+ * f2 = cold-warm blend, f3 = warm, f4 = warm-hot blend, f5 = hot for three
+ * regimes) and its slope dw/dT.  The weight rises linearly from 0 to 1 across
+ * the blend interval shared with the cooler neighbour, is 1 up to the blend
+ * interval shared with the hotter neighbour, falls linearly to 0 across it,
+ * and is 0 beyond.  Intervals are open below and closed above. */
+static void regime_weight(const orc_model* M, int r, double T, double* w, double* dw) {
+    const double* tb = M->tblend;
+    *w = 0.0;
+    *dw = 0.0;
+    if (r > 0) {
+        double lo = tb[2 * r - 2], hi = tb[2 * r - 1];
+        if (T <= lo) return;
+        if (T <= hi) {
+            *w = (T - lo) / (hi - lo);
+            *dw = 1.0 / (hi - lo);
+            return;
+        }
     }
-    du[0] /= th[0] * log(10.0);           /* d log10(Teff) / d Teff */
-    for (int k = 0; k < M->K; ++k) {
-        int a = M->exps[3 * k], b = M->exps[3 * k + 1], c = M->exps[3 * k + 2];
-        phi[k] = ipow(u[0], a) * ipow(u[1], b) * ipow(u[2], c);
-        if (dphi) {
-            dphi[3 * k + 0] = a ? a * ipow(u[0], a - 1) * ipow(u[1], b) * ipow(u[2], c) * du[0] : 0.0;
-            dphi[3 * k + 1] = b ? b * ipow(u[0], a) * ipow(u[1], b - 1) * ipow(u[2], c) * du[1] : 0.0;
-            dphi[3 * k + 2] = c ? c * ipow(u[0], a) * ipow(u[1], b) * ipow(u[2], c - 1) * du[2] : 0.0;
+    if (r == M->n_reg - 1) {
+        *w = 1.0;
+        return;
+    }
+    double lo = tb[2 * r], hi = tb[2 * r + 1];
+    if (T <= lo) {
+        *w = 1.0;
+    } else if (T <= hi) {
+        *w = (hi - T) / (hi - lo);
+        *dw = -1.0 / (hi - lo);
+    }
+}
+
+/* Eq. 1: phi_k = w_r(Teff) u_T^a u_g^b u_f^c for row k of regime r, the u's
+ * the basis variables (log10 Teff, log g, [Fe/H]) mapped linearly onto
+ * [-1, 1] by the regime's box (one regime: w = 1, box blo/bhi). */
+void orc_basis(const orc_model* M, const double* th, double* phi, double* dphi) {
+    int n_reg = M->n_reg > 1 ? M->n_reg : 1;
+    double v[3] = {log10(th[0]), th[1], th[2]};
+    int k = 0;
+    for (int r = 0; r < n_reg; ++r) {
+        const double* lo = n_reg > 1 ? M->rblo[r] : M->blo;
+        const double* hi = n_reg > 1 ? M->rbhi[r] : M->bhi;
+        int Kr = n_reg > 1 ? M->reg_K[r] : M->K;
+        double w = 1.0, dw = 0.0;
+        if (n_reg > 1) regime_weight(M, r, th[0], &w, &dw);
+        double u[3], du[3];
+        for (int i = 0; i < 3; ++i) {
+            u[i] = 2.0 * (v[i] - lo[i]) / (hi[i] - lo[i]) - 1.0;
+            du[i] = 2.0 / (hi[i] - lo[i]);
+        }
+        du[0] /= th[0] * log(10.0);           /* d log10(Teff) / d Teff */
+        for (int q = 0; q < Kr; ++q, ++k) {
+            int a = M->exps[3 * k], b = M->exps[3 * k + 1], c = M->exps[3 * k + 2];
+            double mono = ipow(u[0], a) * ipow(u[1], b) * ipow(u[2], c);
+            phi[k] = w * mono;
+            if (dphi) {
+                double d0 = a ? a * ipow(u[0], a - 1) * ipow(u[1], b) * ipow(u[2], c) * du[0] : 0.0;
+                dphi[3 * k + 0] = w * d0 + dw * mono;
+                dphi[3 * k + 1] = b ? w * b * ipow(u[0], a) * ipow(u[1], b - 1) * ipow(u[2], c) * du[1] : 0.0;
+                dphi[3 * k + 2] = c ? w * c * ipow(u[0], a) * ipow(u[1], b) * ipow(u[2], c - 1) * du[2] : 0.0;
+            }
         }
     }
 }

@@ -36,6 +36,15 @@ typedef struct {
     int n_pix;                 /* p: observed pixels                         */
     int deg;                   /* Legendre degree D (D+1 coefficients)       */
     const double* C;           /* K x (n_pix + 2 pad) coefficient table      */
+    /* Piecewise emulator (Eq. 1 with Teff regimes f1..f5, sec. 3.1).  n_reg <= 1:
+     * one regime with the basis box blo/bhi.  n_reg = 2 or 3: the rows of C
+     * and exps are regime 0's reg_K[0] rows, then regime 1's, ...; regime r
+     * uses the basis box rblo[r]/rbhi[r]; regimes r and r+1 blend linearly in
+     * Teff on (tblend[2r], tblend[2r+1]]. */
+    int n_reg;
+    int reg_K[3];
+    double rblo[3][3], rbhi[3][3];
+    double tblend[4];
 } orc_model;
 
 typedef struct {
@@ -51,7 +60,9 @@ typedef struct {
 void orc_phys_from_x(const orc_model* M, const double* x, double* th);
 void orc_x_from_phys(const orc_model* M, const double* th, double* x);
 
-/* phi_k(theta) and d phi_k / d(Teff, logg, FeH) (K x 3, may be NULL). */
+/* phi_k(theta) and d phi_k / d(Teff, logg, FeH) (K x 3, may be NULL).  For a
+ * piecewise emulator each row is its regime's weight w_r(Teff) times its
+ * monomial, so the Teff derivative includes the weight's slope. */
 void orc_basis(const orc_model* M, const double* th, double* phi, double* dphi);
 
 /* Sampled Gaussian kernel of Eq. 5 on s = -H..H (zero for |s| > h).

@@ -41,7 +41,9 @@ class _Model(ct.Structure):
     _fields_ = [("K", ct.c_int), ("exps", ct.c_void_p), ("blo", ct.c_double * 3),
                 ("bhi", ct.c_double * 3), ("plo", ct.c_double * 5), ("phi", ct.c_double * 5),
                 ("dln", ct.c_double), ("pad", ct.c_int), ("n_pix", ct.c_int), ("deg", ct.c_int),
-                ("C", ct.c_void_p)]
+                ("C", ct.c_void_p), ("n_reg", ct.c_int), ("reg_K", ct.c_int * 3),
+                ("rblo", (ct.c_double * 3) * 3), ("rbhi", (ct.c_double * 3) * 3),
+                ("tblend", ct.c_double * 4)]
 
 
 class _Opts(ct.Structure):
@@ -96,9 +98,15 @@ def _f64(a):
 
 
 class Model:
-    """Interpolator table + grid + boxes, as the oracle sees them."""
+    """Interpolator table + grid + boxes, as the oracle sees them.
 
-    def __init__(self, C, exps, dln, pad, n_pix, deg, blo, bhi, plo, phi):
+    Piecewise emulator (Eq. 1 with Teff regimes): pass reg_K (terms per
+    regime, coolest first; the rows of C and exps stacked in that order),
+    reg_blo/reg_bhi (basis box per regime) and tblend (2 (n_reg - 1) Teff
+    bounds of the blend intervals); blo/bhi are then unused."""
+
+    def __init__(self, C, exps, dln, pad, n_pix, deg, blo, bhi, plo, phi, reg_K=None, reg_blo=None,
+                 reg_bhi=None, tblend=None):
         self.C = _f64(C)
         self.exps = np.ascontiguousarray(exps, dtype=np.int8)
         self.K = self.exps.shape[0]
@@ -106,10 +114,23 @@ class Model:
         self.dln, self.pad, self.n_pix, self.deg = float(dln), int(pad), int(n_pix), int(deg)
         self.blo, self.bhi = _f64(blo), _f64(bhi)
         self.plo, self.phi = _f64(plo), _f64(phi)
+        self.reg_K = None if reg_K is None else [int(k) for k in reg_K]
+        self.reg_blo, self.reg_bhi, self.tblend = reg_blo, reg_bhi, tblend
+        n_reg = 1 if reg_K is None else len(reg_K)
+        if n_reg > 1:
+            assert sum(self.reg_K) == self.K
         self._s = _Model(self.K, self.exps.ctypes.data, (ct.c_double * 3)(*self.blo),
                          (ct.c_double * 3)(*self.bhi), (ct.c_double * 5)(*self.plo),
                          (ct.c_double * 5)(*self.phi), self.dln, self.pad, self.n_pix,
-                         self.deg, self.C.ctypes.data)
+                         self.deg, self.C.ctypes.data, n_reg)
+        if n_reg > 1:
+            for r in range(n_reg):
+                self._s.reg_K[r] = self.reg_K[r]
+                for i in range(3):
+                    self._s.rblo[r][i] = float(reg_blo[r][i])
+                    self._s.rbhi[r][i] = float(reg_bhi[r][i])
+            for q, t in enumerate(tblend):
+                self._s.tblend[q] = float(t)
 
     @property
     def ref(self):
@@ -121,7 +142,7 @@ class Model:
 
     def with_table(self, C):
         return Model(C, self.exps, self.dln, self.pad, self.n_pix, self.deg, self.blo, self.bhi,
-                     self.plo, self.phi)
+                     self.plo, self.phi, self.reg_K, self.reg_blo, self.reg_bhi, self.tblend)
 
 
 def make_opts(lr=0.1, beta1=0.9, beta2=0.999, eps=1e-8, tol=1e-5, window=50, max_steps=5000,

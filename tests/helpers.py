@@ -31,9 +31,27 @@ def table(grid_name: str) -> np.ndarray:
     return S.make_table(_GRIDS[grid_name])
 
 
-def observed(grid, n, seed, **draw_kw):
-    """Draws + oracle-made observed flux/ivar for n spectra on grid."""
-    M = oracle_model(grid)
+@functools.lru_cache(maxsize=None)
+def pw_tables(grid_name: str):
+    return tuple(S.make_piecewise_tables(_GRIDS[grid_name]))
+
+
+def piecewise_model(grid, deg=DEG, tables=None) -> O.Model:
+    """Oracle model of the three-regime synthetic emulator on grid."""
+    if tables is None:
+        tables = pw_tables(grid.name)
+    C = np.concatenate(tables)
+    E = np.concatenate(S.PW_EXPS)
+    return O.Model(C, E, grid.dln, grid.pad, grid.n_pix, deg, S.PW_BASIS_LO[1], S.PW_BASIS_HI[1],
+                   S.PW_BOX_LO, S.PW_BOX_HI, reg_K=[len(e) for e in S.PW_EXPS],
+                   reg_blo=S.PW_BASIS_LO, reg_bhi=S.PW_BASIS_HI, tblend=S.TEFF_BLEND)
+
+
+def observed(grid, n, seed, M=None, **draw_kw):
+    """Draws + oracle-made observed flux/ivar for n spectra on grid (model M,
+    default the single-regime oracle model of grid)."""
+    if M is None:
+        M = oracle_model(grid)
     d = S.draw_batch(grid, n, seed, **draw_kw)
     model = O.model_batch(M, d["truth"], d["b_true"])
     flux, ivar = S.finish_obs(model, d)
