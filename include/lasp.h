@@ -60,7 +60,8 @@ extern "C" {
 #define LASP_PREC_BF16   2   /* tcgen05 BF16 contraction, FP32 accumulate               */
 #define LASP_PREC_TF32X3 3   /* tcgen05 3-pass split TF32 (about FP32 accurate)         */
 
-/* Interpolator description (Eq. 1 with one polynomial regime).
+/* Interpolator description (Eq. 1 with one polynomial regime; see
+ * lasp_piecewise_desc for Teff regimes).
  * The model grid is the observed ln-lambda grid extended by `pad` pixels on
  * each side: n_model = n_pix + 2 pad.  The basis variables
  * v = (log10 Teff, log g, [Fe/H]) are mapped onto [-1, 1] by
@@ -88,6 +89,40 @@ typedef struct lasp_interp_s* lasp_interp;   /* opaque, library-owned */
  * LASP_ENODEV.  On success *out owns device memory until lasp_free_interp. */
 int lasp_init_interp(const lasp_interp_desc* desc, const float* coeff, lasp_interp* out);
 void lasp_free_interp(lasp_interp h);
+
+/* Piecewise interpolator (Eq. 1 with Teff regimes; sec. 3.1): n_reg
+ * polynomial regimes ordered by Teff, coolest first (the paper's emulator has
+ * cold, warm and hot models with 25, 26 and 19 terms).  Regime r has K[r]
+ * terms, its own exponents and its own basis box.  Regimes r and r+1 overlap
+ * on (teff_blend[2r], teff_blend[2r+1]]: there the model is the linear blend
+ * in Teff, (1 - t) F_r + t F_{r+1} with t = (Teff - teff_blend[2r]) /
+ * (teff_blend[2r+1] - teff_blend[2r]); elsewhere it is the one regime whose
+ * range holds Teff (Teff <= teff_blend[0]: regime 0; (teff_blend[2r-1],
+ * teff_blend[2r]]: regime r; above the last bound: the last regime).  The
+ * paper's five ranges are teff_blend = {4000, 4550, 7000, 9000}.  The model is
+ * continuous in Teff; its Teff derivative jumps at the bounds.
+ * coeff: host, (K[0] + ... + K[n_reg-1]) x n_model float32, the regimes'
+ * tables stacked in order.  exps: host, the same rows x 3.  At most 96 rows
+ * in all.  Handles made here serve every FP32 entry point (fits, errors, LM,
+ * slots, forward/backward, lasp_interp_eval at LASP_PREC_FP32); the
+ * tensor-core paths (precision != LASP_PREC_FP32) return LASP_EINVAL for a
+ * handle with more than one regime.  Errors as lasp_init_interp, plus
+ * LASP_EINVAL for n_reg outside 1..3, a regime without terms, or bounds not
+ * strictly increasing. */
+typedef struct {
+    int n_reg;              /* 1..3                                            */
+    int K[3];               /* terms per regime, each >= 1, sum <= 96          */
+    int n_pix;              /* observed pixels p (>= 16)                       */
+    int pad;                /* H, as lasp_interp_desc                          */
+    double dln;             /* ln-lambda step of the grid (> 0)                */
+    const int8_t* exps;     /* host, (sum K) x 3 non-negative exponents (<= 8) */
+    double basis_lo[3][3], basis_hi[3][3];   /* per regime, as lasp_interp_desc */
+    double teff_blend[4];   /* 2 (n_reg - 1) strictly increasing Teff bounds   */
+    double box_lo[5], box_hi[5];
+} lasp_piecewise_desc;
+
+int lasp_init_interp_piecewise(const lasp_piecewise_desc* desc, const float* coeff,
+                               lasp_interp* out);
 
 /* A batch of N observed spectra on the interpolator's grid (device, row-major
  * N x n_pix).  good: 1 = pixel used (the mask A of Eq. 8), 0 = masked.

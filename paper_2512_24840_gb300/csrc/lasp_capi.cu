@@ -145,16 +145,24 @@ void lasp_default_opts(lasp_fit_opts* o) {
     o->optimizer = LASP_OPT_ADAM;
 }
 
-int lasp_init_interp(const lasp_interp_desc* d, const float* coeff, lasp_interp* out) {
+int lasp_init_interp_piecewise(const lasp_piecewise_desc* d, const float* coeff, lasp_interp* out) {
     if (!d || !coeff || !out) return LASP_EINVAL;
     *out = nullptr;
-    if (d->K < 1 || d->K > KMAX || d->n_pix < 16 || d->n_pix > 16 * 512 || d->pad < 0 ||
+    if (d->n_reg < 1 || d->n_reg > NREG || d->n_pix < 16 || d->n_pix > 16 * 512 || d->pad < 0 ||
         d->pad > HMAX || !(d->dln > 0.0) || !d->exps)
         return LASP_EINVAL;
-    for (int k = 0; k < 3 * d->K; ++k)
+    int K = 0;
+    for (int r = 0; r < d->n_reg; ++r) {
+        if (d->K[r] < 1) return LASP_EINVAL;
+        K += d->K[r];
+        for (int k = 0; k < 3; ++k)
+            if (!(d->basis_hi[r][k] > d->basis_lo[r][k])) return LASP_EINVAL;
+    }
+    if (K > KROWS || (d->n_reg == 1 && K > KMAX)) return LASP_EINVAL;
+    for (int q = 0; q + 1 < 2 * (d->n_reg - 1); ++q)
+        if (!(d->teff_blend[q + 1] > d->teff_blend[q])) return LASP_EINVAL;
+    for (int k = 0; k < 3 * K; ++k)
         if (d->exps[k] < 0 || d->exps[k] > 8) return LASP_EINVAL;
-    for (int k = 0; k < 3; ++k)
-        if (!(d->basis_hi[k] > d->basis_lo[k])) return LASP_EINVAL;
     for (int k = 0; k < 5; ++k)
         if (!(d->box_hi[k] > d->box_lo[k])) return LASP_EINVAL;
     if (!(d->box_lo[0] > 0.0) || !(d->box_lo[4] > 0.0)) return LASP_EINVAL;
@@ -171,22 +179,28 @@ int lasp_init_interp(const lasp_interp_desc* d, const float* coeff, lasp_interp*
     if (!h) return LASP_ENOMEM;
     h->device = dev;
     ModelDev& M = h->M;
-    M.K = d->K;
+    M.K = K;
     M.n_pix = d->n_pix;
     M.pad = d->pad;
     M.n_model = d->n_pix + 2 * d->pad;
     M.kms_px = (float)kms;
-    for (int k = 0; k < 3; ++k) {
-        M.blo[k] = (float)d->basis_lo[k];
-        M.bscale[k] = (float)(2.0 / (d->basis_hi[k] - d->basis_lo[k]));
+    M.n_reg = d->n_reg;
+    M.reg_row[0] = 0;
+    for (int r = 0; r < d->n_reg; ++r) {
+        M.reg_row[r + 1] = M.reg_row[r] + d->K[r];
+        for (int k = 0; k < 3; ++k) {
+            M.rblo[r][k] = (float)d->basis_lo[r][k];
+            M.rbscale[r][k] = (float)(2.0 / (d->basis_hi[r][k] - d->basis_lo[r][k]));
+        }
     }
+    for (int q = 0; q < 2 * (d->n_reg - 1); ++q) M.tb[q] = (float)d->teff_blend[q];
     for (int k = 0; k < 5; ++k) {
         M.plo[k] = (float)d->box_lo[k];
         M.phalf[k] = (float)(0.5 * (d->box_hi[k] - d->box_lo[k]));
     }
     std::memset(M.exps, 0, sizeof(M.exps));
-    for (int k = 0; k < 3 * d->K; ++k) M.exps[k] = d->exps[k];
-    const size_t nC = (size_t)d->K * M.n_model;
+    for (int k = 0; k < 3 * K; ++k) M.exps[k] = d->exps[k];
+    const size_t nC = (size_t)K * M.n_model;
     rc = cuda_err(cudaMalloc(&h->C, nC * sizeof(float)));
     if (rc) {
         delete h;
@@ -194,13 +208,14 @@ int lasp_init_interp(const lasp_interp_desc* d, const float* coeff, lasp_interp*
     }
     M.ldc = (M.n_model + 15) & ~15;
     rc = cuda_err(cudaMemcpy(h->C, coeff, nC * sizeof(float), cudaMemcpyHostToDevice));
-    if (!rc) rc = cuda_err(cudaMalloc(&h->Cp, (size_t)d->K * M.ldc * sizeof(float)));
-    if (!rc) rc = cuda_err(cudaMemset(h->Cp, 0, (size_t)d->K * M.ldc * sizeof(float)));
+    if (!rc) rc = cuda_err(cudaMalloc(&h->Cp, (size_t)K * M.ldc * sizeof(float)));
+    if (!rc) rc = cuda_err(cudaMemset(h->Cp, 0, (size_t)K * M.ldc * sizeof(float)));
     if (!rc)
         rc = cuda_err(cudaMemcpy2D(h->Cp, (size_t)M.ldc * sizeof(float), coeff,
                                    (size_t)M.n_model * sizeof(float), (size_t)M.n_model * sizeof(float),
-                                   (size_t)d->K, cudaMemcpyHostToDevice));
-    if (!rc) rc = tc_build_images(h->tc, h->C, d->K, M.n_model);
+                                   (size_t)K, cudaMemcpyHostToDevice));
+    // tensor-core tile images: single-regime tables of at most one K block
+    if (!rc && M.n_reg == 1) rc = tc_build_images(h->tc, h->C, K, M.n_model);
     if (rc) {
         tc_free_images(h->tc);
         cudaFree(h->C);
@@ -212,6 +227,28 @@ int lasp_init_interp(const lasp_interp_desc* d, const float* coeff, lasp_interp*
     M.Cp = h->Cp;
     *out = h;
     return LASP_OK;
+}
+
+int lasp_init_interp(const lasp_interp_desc* d, const float* coeff, lasp_interp* out) {
+    if (!d || !coeff || !out) return LASP_EINVAL;
+    *out = nullptr;
+    if (d->K < 1 || d->K > KMAX) return LASP_EINVAL;
+    lasp_piecewise_desc pd{};
+    pd.n_reg = 1;
+    pd.K[0] = d->K;
+    pd.n_pix = d->n_pix;
+    pd.pad = d->pad;
+    pd.dln = d->dln;
+    pd.exps = d->exps;
+    for (int k = 0; k < 3; ++k) {
+        pd.basis_lo[0][k] = d->basis_lo[k];
+        pd.basis_hi[0][k] = d->basis_hi[k];
+    }
+    for (int k = 0; k < 5; ++k) {
+        pd.box_lo[k] = d->box_lo[k];
+        pd.box_hi[k] = d->box_hi[k];
+    }
+    return lasp_init_interp_piecewise(&pd, coeff, out);
 }
 
 void lasp_free_interp(lasp_interp h) {
@@ -232,7 +269,7 @@ int lasp_fit_batch(lasp_interp h, const lasp_batch* b, const lasp_fit_opts* o, l
     if (!r || (b->N > 0 && (!r->theta || !r->loss || !r->steps || !r->status))) return LASP_EINVAL;
     if (b->N == 0) return LASP_OK;
     if (o->precision != LASP_PREC_FP32) {
-        if (o->clean) return LASP_EINVAL;          // Clean runs in the FP32 batch fit
+        if (o->clean || h->M.n_reg > 1) return LASP_EINVAL;          // Clean runs in the FP32 batch fit
         return lasp_tc_fit_batch(h->M, h->tc, b, o, r, stream, &g_last_launches);
     }
     if (o->optimizer == LASP_OPT_LM) {
@@ -364,6 +401,7 @@ int lasp_interp_eval(lasp_interp h, int N, const float* theta, float* Fp, int pr
     if (N == 0) return LASP_OK;
     if (!theta || !Fp) return LASP_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
+    if (precision != LASP_PREC_FP32 && h->M.n_reg > 1) return LASP_EINVAL;
     if (precision != LASP_PREC_FP32)
         return lasp_tc_interp_eval(h->M, h->tc, N, theta, Fp, precision, st, &g_last_launches);
     dim3 grid(N, (h->M.n_model + 255) / 256);

@@ -12,22 +12,31 @@
 
 namespace lasp {
 
-constexpr int KMAX = 32;          // basis terms supported
+constexpr int KMAX = 32;          // rows of one tensor-core K block (single-regime tables)
+constexpr int KROWS = 96;         // interpolator rows over all regimes (CUDA-core paths)
+constexpr int NREG = 3;           // Teff regimes of a piecewise interpolator
+constexpr int DPS = 4;            // stride of a basis-derivative row (Teff, logg, FeH, 0)
 constexpr int PPT = 16;           // pixels per thread of the per-spectrum kernels
 constexpr int WINMAX = 64;        // stop-rule window supported
 constexpr int HMAX = 47;          // kernel half width supported (2H+1 <= 96 taps)
 constexpr int TAPS_MAX = 2 * HMAX + 1;
 
-// Interpolator constants passed by value to every kernel.
+// Interpolator constants passed by value to every kernel.  A piecewise
+// interpolator (Eq. 1 with Teff regimes) stacks the rows of its regimes,
+// coolest first: regime r owns rows [reg_row[r], reg_row[r+1]) with its own
+// basis box; regimes r and r+1 overlap on (tb[2r], tb[2r+1]] in Teff.
 struct ModelDev {
     const float* C;          // K x n_model, row-major, FP32
     const float* Cp;         // K x ldc, rows zero-padded to a multiple of 16 floats
     int ldc;
     int K, n_pix, pad, n_model;
     float kms_px;            // c * dln: km/s per pixel
-    float blo[3], bscale[3]; // u = (v - blo) * bscale - 1
+    int n_reg;               // 1..NREG
+    int reg_row[NREG + 1];
+    float rblo[NREG][3], rbscale[NREG][3];  // u = (v - rblo) * rbscale - 1 per regime
+    float tb[2 * (NREG - 1)];               // blend bounds in Teff, increasing
     float plo[5], phalf[5];  // theta = plo + (x + 1) * phalf
-    int8_t exps[KMAX * 3];
+    int8_t exps[KROWS * 3];
 };
 
 struct FitOpts {
@@ -50,28 +59,114 @@ __device__ __forceinline__ float ipowf(float u, int a) {
     return r;
 }
 
+// 256-bit read-only global load of 8 floats (address 32-byte aligned): one
+// request per 32-byte sector instead of two 16-byte halves.
+__device__ __forceinline__ void ldg8(const float* p, float (&v)[8]) {
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]),
+                   "=f"(v[7])
+                 : "l"(p));
+}
+
 // Physical parameters from normalised x (stage 8 rescaling).
 __device__ __forceinline__ float phys_of(const ModelDev& M, int k, float x) {
     return fmaf(x + 1.0f, M.phalf[k], M.plo[k]);
 }
 
-// Basis of Eq. 1 (one regime): phi_k and d phi_k / d(Teff, logg, FeH).
-// Called by lane k < K of one warp.
+// Teff segment of a piecewise interpolator: the number of blend bounds below
+// Teff.  Even segment 2r: regime r alone; odd segment 2r+1: the blend of
+// regimes r and r+1 on (tb[2r], tb[2r+1]].
+__device__ __forceinline__ int teff_segment(const ModelDev& M, float teff) {
+    int s = 0;
+    for (int q = 0; q < 2 * (M.n_reg - 1); ++q) s += teff > M.tb[q] ? 1 : 0;
+    return s;
+}
+
+// Rows with a non-zero weight at teff: [k0, k1).
+__device__ __forceinline__ void active_rows(const ModelDev& M, float teff, int& k0, int& k1) {
+    const int s = teff_segment(M, teff);
+    const int r = s >> 1;
+    k0 = M.reg_row[r];
+    k1 = M.reg_row[(s & 1) ? r + 2 : r + 1];
+}
+
+// Monomial u_T^a u_g^b u_f^c of one row in a basis box (lo, scale) and its
+// derivatives with respect to (Teff, logg, FeH).
+__device__ __forceinline__ float monomial(const float* lo, const float* sc, const int8_t* e,
+                                          const float th[3], float* d) {
+    const float u0 = (log10f(th[0]) - lo[0]) * sc[0] - 1.0f;
+    const float u1 = (th[1] - lo[1]) * sc[1] - 1.0f;
+    const float u2 = (th[2] - lo[2]) * sc[2] - 1.0f;
+    const int a = e[0], b = e[1], c = e[2];
+    const float pa = ipowf(u0, a), pb = ipowf(u1, b), pc = ipowf(u2, c);
+    if (d) {
+        // d u_T / d Teff = scale / (Teff ln 10)
+        const float du0 = sc[0] / (th[0] * 2.302585092994046f);
+        d[0] = a ? (float)a * ipowf(u0, a - 1) * pb * pc * du0 : 0.0f;
+        d[1] = b ? (float)b * pa * ipowf(u1, b - 1) * pc * sc[1] : 0.0f;
+        d[2] = c ? (float)c * pa * pb * ipowf(u2, c - 1) * sc[2] : 0.0f;
+    }
+    return pa * pb * pc;
+}
+
+// Basis of Eq. 1: phi_k and d phi_k / d(Teff, logg, FeH) of row k (dphi row
+// k at DPS k: Teff, logg, FeH, 0), with the regime weight folded in.  Row k
+// of regime r is w_r(Teff) times its monomial in the regime's own basis box;
+// w_r is 1 inside the regime, falls or rises linearly in Teff across a blend
+// interval, and is 0 elsewhere, so d phi / d Teff carries the weight's slope.
 __device__ __forceinline__ void basis_term(const ModelDev& M, int k, const float th[3],
                                            float* phi, float* dphi) {
-    float u0 = (log10f(th[0]) - M.blo[0]) * M.bscale[0] - 1.0f;
-    float u1 = (th[1] - M.blo[1]) * M.bscale[1] - 1.0f;
-    float u2 = (th[2] - M.blo[2]) * M.bscale[2] - 1.0f;
-    int a = M.exps[3 * k], b = M.exps[3 * k + 1], c = M.exps[3 * k + 2];
-    float pa = ipowf(u0, a), pb = ipowf(u1, b), pc = ipowf(u2, c);
-    phi[k] = pa * pb * pc;
-    if (dphi) {
-        // d u_T / d Teff = bscale / (Teff ln 10)
-        float du0 = M.bscale[0] / (th[0] * 2.302585092994046f);
-        dphi[3 * k + 0] = a ? (float)a * ipowf(u0, a - 1) * pb * pc * du0 : 0.0f;
-        dphi[3 * k + 1] = b ? (float)b * pa * ipowf(u1, b - 1) * pc * M.bscale[1] : 0.0f;
-        dphi[3 * k + 2] = c ? (float)c * pa * pb * ipowf(u2, c - 1) * M.bscale[2] : 0.0f;
+    float d[3];
+    if (M.n_reg == 1) {
+        phi[k] = monomial(M.rblo[0], M.rbscale[0], M.exps + 3 * k, th, dphi ? d : nullptr);
+        if (dphi) {
+            dphi[DPS * k + 0] = d[0];
+            dphi[DPS * k + 1] = d[1];
+            dphi[DPS * k + 2] = d[2];
+            dphi[DPS * k + 3] = 0.0f;
+        }
+        return;
     }
+    int r = 0;
+    while (r + 1 < M.n_reg && k >= M.reg_row[r + 1]) ++r;
+    float w = 1.0f, dw = 0.0f;
+    const int s = teff_segment(M, th[0]);
+    if (s & 1) {
+        const int q = s >> 1;                          // blend of regimes q and q+1
+        const float lo = M.tb[s - 1], hi = M.tb[s];
+        const float inv = 1.0f / (hi - lo);
+        const float t = (th[0] - lo) * inv;
+        if (r == q) {
+            w = 1.0f - t;
+            dw = -inv;
+        } else if (r == q + 1) {
+            w = t;
+            dw = inv;
+        } else {
+            w = 0.0f;
+        }
+    } else if (r != (s >> 1)) {
+        w = 0.0f;
+    }
+    if (w == 0.0f && dw == 0.0f) {
+        phi[k] = 0.0f;
+        if (dphi) dphi[DPS * k] = dphi[DPS * k + 1] = dphi[DPS * k + 2] = dphi[DPS * k + 3] = 0.0f;
+        return;
+    }
+    const float mono = monomial(M.rblo[r], M.rbscale[r], M.exps + 3 * k, th, dphi ? d : nullptr);
+    phi[k] = w * mono;
+    if (dphi) {
+        dphi[DPS * k + 0] = fmaf(w, d[0], dw * mono);
+        dphi[DPS * k + 1] = w * d[1];
+        dphi[DPS * k + 2] = w * d[2];
+        dphi[DPS * k + 3] = 0.0f;
+    }
+}
+
+// Every row's basis term, spread over the lanes of one warp.
+__device__ __forceinline__ void warp_basis(const ModelDev& M, const float th[3], float* phi,
+                                           float* dphi) {
+    for (int k = (threadIdx.x & 31); k < M.K; k += 32) basis_term(M, k, th, phi, dphi);
 }
 
 // Sampled Gaussian kernel of Eq. 5 on s = -H..H (index s + H), unit sum over

@@ -25,6 +25,7 @@ namespace lasp {
 
 constexpr int TB = 8;       // taps per block
 constexpr int TAPBUF = 128; // tap buffer (>= 2 HMAX + 2 TB + 1)
+constexpr int NADJ = 7;     // end-of-step sums: S, nonpos, d/dmu, d/dsigma, d/d(Teff, logg, FeH)
 
 // Device-resident fit state of resumable slots (struct of arrays, S slots).
 // A launch in slot mode runs at most `budget` Adam steps per slot and saves
@@ -66,9 +67,9 @@ struct FitParams {
 // skew(j + 2H + 8), zero outside [0, p).
 struct FitSmem {
     int y, W, Fp, Db, g, gmu, gsg, phi, dphi, red, out, ring, total, dofs;
-    __host__ __device__ FitSmem(int p, int H, int n_model, int NT, int D) {
+    __host__ __device__ FitSmem(int p, int H, int n_model, int NT, int D, int K) {
         const int NB = D + 1, NV = NB * (NB + 1) / 2 + NB;
-        const int nv_max = round32(NV > (KMAX + 4) ? NV : (KMAX + 4));
+        const int nv_max = round32(NV > NADJ ? NV : NADJ);
         dofs = 2 * H + 8;
         int o = 0;
         y = o;    o += skew_size(p);
@@ -78,8 +79,8 @@ struct FitSmem {
         g = o;    o += TAPBUF;
         gmu = o;  o += TAPBUF;
         gsg = o;  o += TAPBUF;
-        phi = o;  o += KMAX;
-        dphi = o; o += 3 * KMAX;
+        phi = o;  o += round32(K);          // sized by the table: the SM's L1 keeps the rest
+        dphi = o; o += DPS * round32(K);
         red = o;  o += (NT / 32) * nv_max;
         out = o;  o += 2 * nv_max + 16;
         ring = o; o += WINMAX;
@@ -87,8 +88,8 @@ struct FitSmem {
     }
 };
 
-__host__ inline size_t fit_smem_bytes(int p, int H, int n_model, int NT, int D) {
-    FitSmem s(p, H, n_model, NT, D);
+__host__ inline size_t fit_smem_bytes(int p, int H, int n_model, int NT, int D, int K) {
+    FitSmem s(p, H, n_model, NT, D, K);
     size_t sort_end = (size_t)s.Fp + next_pow2(p);
     return 4 * ((size_t)s.total > sort_end ? (size_t)s.total : sort_end);
 }
@@ -165,15 +166,18 @@ __device__ __forceinline__ void reduce_to_warp0_f64(float (&v)[NV], float* red, 
     }
 }
 
-// Basis, its derivatives and the kernel taps for normalised x (warp 0).
-// Taps are written for s + H in [0, TAPBUF), zero outside |s| <= h.
+// Basis, its derivatives, the active table rows (s_k[0..1]) and the kernel
+// taps for normalised x (warp 0).  Taps are written for s + H in
+// [0, TAPBUF), zero outside |s| <= h.
 __device__ __forceinline__ int warp_prepare_step(const ModelDev& M, const float* x, float* phi,
-                                                 float* dphi, float* g, float* gmu, float* gsg) {
+                                                 float* dphi, float* g, float* gmu, float* gsg,
+                                                 int* s_k) {
     const int lane = threadIdx.x & 31;
     float th[5];
 #pragma unroll
     for (int k = 0; k < 5; ++k) th[k] = phys_of(M, k, x[k]);
-    if (lane < M.K) basis_term(M, lane, th, phi, dphi);
+    warp_basis(M, th, phi, dphi);
+    if (lane == 0) active_rows(M, th[0], s_k[0], s_k[1]);
     for (int i = 2 * M.pad + 1 + lane; i < TAPBUF; i += 32) {
         g[i] = 0.0f;
         gmu[i] = 0.0f;
@@ -195,10 +199,10 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) fit_kernel(const FitPar
     constexpr int NV = Gm::NV;
     extern __shared__ __align__(16) float sm[];
     const ModelDev& M = P.M;
-    const int p = M.n_pix, H = M.pad, nm = M.n_model, K = M.K;
+    const int p = M.n_pix, H = M.pad, nm = M.n_model;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int i = blockIdx.x;
-    const FitSmem L(p, H, nm, NT, D);
+    const FitSmem L(p, H, nm, NT, D, M.K);
     float* y = sm + L.y;
     float* W = sm + L.W;
     float* Fp = sm + L.Fp;
@@ -213,7 +217,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) fit_kernel(const FitPar
     double* outd = reinterpret_cast<double*>(sm + ((L.out + 1) & ~1));
     float* ring = sm + L.ring;
     __shared__ float s_x[5], s_b[NB];
-    __shared__ int s_h, s_stop;
+    __shared__ int s_h, s_stop, s_k[2];
     __shared__ float s_w, s_imean;
     __shared__ double s_redd[3 * (NT / 32)], s_tot[3];
 
@@ -314,7 +318,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) fit_kernel(const FitPar
         return;
     }
     if (warp == 0) {
-        int h = warp_prepare_step(M, s_x, phi, dphi, g, gmu, gsg);
+        int h = warp_prepare_step(M, s_x, phi, dphi, g, gmu, gsg, s_k);
         if (lane == 0) s_h = h;
     }
     __syncthreads();
@@ -328,24 +332,25 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) fit_kernel(const FitPar
     for (int t = t0;; ++t) {
         const int h = s_h;
         const int nblk = (2 * h + 1 + TB - 1) / TB;
+        const int k0 = s_k[0], k1 = s_k[1];
 
         // ---- a3: F' = phi C (Eq. 1), 16 model pixels per thread, table from L2
         if (own_mod) {
             float acc[PPT];
 #pragma unroll
             for (int r = 0; r < PPT; ++r) acc[r] = 0.0f;
-            const float4* crow = reinterpret_cast<const float4*>(M.Cp + j0);
+            // rows are padded to 16 floats and j0 is a multiple of 16: 32-byte aligned
+            const float* crow = M.Cp + j0;
 #pragma unroll 2
-            for (int k = 0; k < K; ++k) {
+            for (int k = k0; k < k1; ++k) {
                 const float pk = phi[k];
-                const float4* c4 = crow + (size_t)k * (M.ldc / 4);
+                const float* ck = crow + (size_t)k * M.ldc;
 #pragma unroll
-                for (int q = 0; q < PPT / 4; ++q) {
-                    const float4 c = __ldg(c4 + q);
-                    acc[4 * q + 0] = fmaf(pk, c.x, acc[4 * q + 0]);
-                    acc[4 * q + 1] = fmaf(pk, c.y, acc[4 * q + 1]);
-                    acc[4 * q + 2] = fmaf(pk, c.z, acc[4 * q + 2]);
-                    acc[4 * q + 3] = fmaf(pk, c.w, acc[4 * q + 3]);
+                for (int q = 0; q < PPT / 8; ++q) {
+                    float c[8];
+                    ldg8(ck + 8 * q, c);
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) acc[8 * q + e] = fmaf(pk, c[e], acc[8 * q + e]);
                 }
             }
 #pragma unroll
@@ -452,12 +457,12 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) fit_kernel(const FitPar
 
         // ---- a7: adjoint, unscaled (dl/dF'' = kappa * delta with kappa = -1/(p l)
         // applied after the reduction).  (i) a_s = sum_j delta_j F'_{j+H-s};
-        // d l/d mu = kappa sum_s gmu_s a_s.  bacc = [S, nonpos, mu, sigma, phi...]
-        float bacc[4 + KMAX];
+        // d l/d mu = kappa sum_s gmu_s a_s.  bacc = [S, nonpos, mu, sigma, Teff, logg, FeH]
+        float bacc[NADJ];
         bacc[0] = racc[0];
         bacc[1] = racc[1];
 #pragma unroll
-        for (int q = 2; q < 4 + KMAX; ++q) bacc[q] = 0.0f;
+        for (int q = 2; q < NADJ; ++q) bacc[q] = 0.0f;
         if (own_pix) {
             for (int bk = 0; bk < nblk; ++bk) {
                 const int s0 = -h + bk * TB;
@@ -479,7 +484,10 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) fit_kernel(const FitPar
                 }
             }
         }
-        // (ii) dF'_m = sum_s g_s delta_{m-H+s}; d l/d phi_k = k sum_m dF'_m C_km
+        // (ii) dF'_m = sum_s g_s delta_{m-H+s}; d l/d phi_k = kappa sum_m dF'_m C_km,
+        // folded into the three basis derivatives per thread (sum over k of
+        // dphi_k times the thread's partial sum), so the CTA reduces 3 values
+        // instead of one per row.
         if (own_mod) {
             float dfp[PPT];
 #pragma unroll
@@ -498,25 +506,25 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) fit_kernel(const FitPar
 #pragma unroll
                     for (int r = 0; r < PPT; ++r) dfp[r] = fmaf(gg[e], win[r + e], dfp[r]);
             }
-            const float4* crow = reinterpret_cast<const float4*>(M.Cp + j0);
+            const float* crow = M.Cp + j0;
+#pragma unroll 2
+            for (int k = k0; k < k1; ++k) {
+                const float* ck = crow + (size_t)k * M.ldc;
+                float a = 0.0f;
 #pragma unroll
-            for (int k = 0; k < KMAX; ++k) {
-                if (k < K) {
-                    const float4* c4 = crow + (size_t)k * (M.ldc / 4);
-                    float a = 0.0f;
+                for (int q = 0; q < PPT / 8; ++q) {
+                    float c[8];
+                    ldg8(ck + 8 * q, c);
 #pragma unroll
-                    for (int q = 0; q < PPT / 4; ++q) {
-                        const float4 c = __ldg(c4 + q);
-                        a = fmaf(dfp[4 * q + 0], c.x, a);
-                        a = fmaf(dfp[4 * q + 1], c.y, a);
-                        a = fmaf(dfp[4 * q + 2], c.z, a);
-                        a = fmaf(dfp[4 * q + 3], c.w, a);
-                    }
-                    bacc[4 + k] = a;
+                    for (int e = 0; e < 8; ++e) a = fmaf(dfp[8 * q + e], c[e], a);
                 }
+                const float4 dk = reinterpret_cast<const float4*>(dphi)[k];
+                bacc[4] = fmaf(dk.x, a, bacc[4]);
+                bacc[5] = fmaf(dk.y, a, bacc[5]);
+                bacc[6] = fmaf(dk.z, a, bacc[6]);
             }
         }
-        reduce_to_warp0<4 + KMAX, NT>(bacc, red, out);
+        reduce_to_warp0<NADJ, NT>(bacc, red, out);
 
         // ---- a8: chain rule to x, stop rules, Adam; next step's basis + taps (warp 0)
         if (warp == 0) {
@@ -524,19 +532,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) fit_kernel(const FitPar
             const float l = sqrtf(out[0] * inv_p);
             const bool nonpos = out[1] > 0.0f;
             const float kappa = l > 0.0f ? -1.0f / ((float)p * l) : 0.0f;
-            float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f;
-            if (lane < K) {
-                const float gp = out[4 + lane];
-                c0 = gp * dphi[3 * lane + 0];
-                c1 = gp * dphi[3 * lane + 1];
-                c2 = gp * dphi[3 * lane + 2];
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                c0 += __shfl_xor_sync(0xffffffffu, c0, o);
-                c1 += __shfl_xor_sync(0xffffffffu, c1, o);
-                c2 += __shfl_xor_sync(0xffffffffu, c2, o);
-            }
+            const float c0 = out[4], c1 = out[5], c2 = out[6];
             int stop = 0;
             if (lane == 0) {
                 float gx[5];
@@ -602,7 +598,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) fit_kernel(const FitPar
             stop = __shfl_sync(0xffffffffu, stop, 0);
             __syncwarp();
             if (!stop && !clean_step(P.O, t)) {
-                int hn = warp_prepare_step(M, s_x, phi, dphi, g, gmu, gsg);
+                int hn = warp_prepare_step(M, s_x, phi, dphi, g, gmu, gsg, s_k);
                 if (lane == 0) s_h = hn;
             }
         }
@@ -677,7 +673,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) fit_kernel(const FitPar
             }
             // the delta buffer pads are outside [0, p) and untouched
             if (warp == 0) {
-                int hn = warp_prepare_step(M, s_x, phi, dphi, g, gmu, gsg);
+                int hn = warp_prepare_step(M, s_x, phi, dphi, g, gmu, gsg, s_k);
                 if (lane == 0) s_h = hn;
             }
             __syncthreads();

@@ -696,14 +696,14 @@ __global__ void __launch_bounds__(256) k4_adam(const Grp G, int par) {
     for (int k = 0; k < 5; ++k) th[k] = phys_of(M, k, G.x[5 * id + k]);
     float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f;
     if (lane < M.K) {
-        float phi[KMAX], dphi[3 * KMAX];
+        float phi[KMAX], dphi[DPS * KMAX];
         basis_term(M, lane, th, phi, dphi);
         float gp = 0.0f;
 #pragma unroll
         for (int q = 0; q < KSPLIT; ++q) gp += G.dphi[((size_t)q * G.nblk * 128 + pos) * 32 + lane];
-        c0 = gp * dphi[3 * lane + 0];
-        c1 = gp * dphi[3 * lane + 1];
-        c2 = gp * dphi[3 * lane + 2];
+        c0 = gp * dphi[DPS * lane + 0];
+        c1 = gp * dphi[DPS * lane + 1];
+        c2 = gp * dphi[DPS * lane + 2];
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {

@@ -27,12 +27,12 @@ template <int D>
 int launch_fit(const FitParams& P, cudaStream_t st) {
     const int p = P.M.n_pix, H = P.M.pad, nm = P.M.n_model;
     if (p <= 16 * 256) {
-        size_t smem = fit_smem_bytes(p, H, nm, 256, D);
+        size_t smem = fit_smem_bytes(p, H, nm, 256, D, P.M.K);
         int e = set_smem_attr(fit_kernel<256, D>, smem);
         if (e) return e;
         fit_kernel<256, D><<<P.N, 256, smem, st>>>(P);
     } else {
-        size_t smem = fit_smem_bytes(p, H, nm, 512, D);
+        size_t smem = fit_smem_bytes(p, H, nm, 512, D, P.M.K);
         int e = set_smem_attr(fit_kernel<512, D>, smem);
         if (e) return e;
         fit_kernel<512, D><<<P.N, 512, smem, st>>>(P);

@@ -34,7 +34,7 @@ struct LmParams {
 };
 
 __host__ inline size_t lm_smem_bytes(int p, int H, int n_model, int NT) {
-    size_t fl = (size_t)2 * ((p + 3) & ~3) + 4 * (size_t)((n_model + 3) & ~3) + 3 * 96 + 4 * KMAX +
+    size_t fl = (size_t)2 * ((p + 3) & ~3) + 4 * (size_t)((n_model + 3) & ~3) + 3 * 96 + (1 + DPS) * KROWS +
                 (size_t)(NT / 32) * 48 + 256;
     size_t sortb = (size_t)2 * ((p + 3) & ~3) + next_pow2(p);
     return 4 * (fl > sortb ? fl : sortb);
@@ -51,24 +51,26 @@ __device__ void lm_eval(const ModelDev& M, const float* th, const float* y, cons
     using Gm = Gram<D>;
     constexpr int NB = D + 1;
     constexpr int NV = Gm::NV;
-    const int p = M.n_pix, H = M.pad, nm = M.n_model, K = M.K;
+    const int p = M.n_pix, H = M.pad, nm = M.n_model;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (warp == 0) {
-        if (lane < K) basis_term(M, lane, th, phi, FULL ? dphi : nullptr);
+        warp_basis(M, th, phi, FULL ? dphi : nullptr);
         const int h = kernel_taps_warp(th[3] / M.kms_px, th[4] / M.kms_px, H, g, gmu, gsg);
         if (lane == 0) *s_h = h;
     }
     __syncthreads();
     const int h = *s_h;
+    int k0, k1;
+    active_rows(M, th[0], k0, k1);
     for (int mm = tid; mm < nm; mm += NT) {
         float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
-        for (int k = 0; k < K; ++k) {
+        for (int k = k0; k < k1; ++k) {
             const float c = __ldg(M.C + (size_t)k * nm + mm);
             a0 = fmaf(phi[k], c, a0);
             if (FULL) {
-                a1 = fmaf(dphi[3 * k + 0], c, a1);
-                a2 = fmaf(dphi[3 * k + 1], c, a2);
-                a3 = fmaf(dphi[3 * k + 2], c, a3);
+                a1 = fmaf(dphi[DPS * k + 0], c, a1);
+                a2 = fmaf(dphi[DPS * k + 1], c, a2);
+                a3 = fmaf(dphi[DPS * k + 2], c, a3);
             }
         }
         Fp[mm] = a0;
@@ -394,8 +396,8 @@ __global__ void __launch_bounds__(NT) lm_kernel(const LmParams P) {
     float* gmu = g + 96;
     float* gsg = g + 192;
     float* phi = g + 288;
-    float* dphi = phi + KMAX;
-    float* red = phi + 4 * KMAX;
+    float* dphi = phi + KROWS;
+    float* red = phi + (1 + DPS) * KROWS;
     float* outf = red + (NT / 32) * 48;
     double* outd = reinterpret_cast<double*>(outf + ((((size_t)(outf - sm)) & 1) ? 1 : 0));
     __shared__ double s_G[Gram<D>::NV], s_b[D + 1], s_db[5 * (D + 1)], s_sum[21];

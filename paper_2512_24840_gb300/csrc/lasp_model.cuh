@@ -18,7 +18,7 @@ struct ModelParams {
 };
 
 __host__ inline size_t model_smem_bytes(int p, int H, int n_model) {
-    return 4 * (size_t)(((n_model + 3) & ~3) + ((p + 4 * H + 3) & ~3) + 3 * 96 + 4 * KMAX + 16 * 64);
+    return 4 * (size_t)(((n_model + 3) & ~3) + ((p + 4 * H + 3) & ~3) + 3 * 96 + (1 + DPS) * KROWS + 16 * 64);
 }
 
 // Per-spectrum basis + taps + F' into shared memory (one CTA).
@@ -30,16 +30,16 @@ __device__ __forceinline__ int cta_interp(const ModelDev& M, const float* th5, f
         float th[5];
 #pragma unroll
         for (int k = 0; k < 5; ++k) th[k] = th5[k];
-        if (lane < M.K) basis_term(M, lane, th, phi, dphi);
+        warp_basis(M, th, phi, dphi);
         int h = kernel_taps_warp(th[3] / M.kms_px, th[4] / M.kms_px, M.pad, g, gmu, gsg);
         if (lane == 0) *s_h = h;
     }
     __syncthreads();
+    int k0, k1;
+    active_rows(M, th5[0], k0, k1);
     for (int mm = threadIdx.x; mm < M.n_model; mm += NT) {
         float acc = 0.0f;
-#pragma unroll
-        for (int k = 0; k < KMAX; ++k)
-            if (k < M.K) acc = fmaf(phi[k], __ldg(M.C + (size_t)k * M.n_model + mm), acc);
+        for (int k = k0; k < k1; ++k) acc = fmaf(phi[k], __ldg(M.C + (size_t)k * M.n_model + mm), acc);
         Fp[mm] = acc;
     }
     __syncthreads();
@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(NT) forward_kernel(const ModelParams P) {
 template <int NT, int D>
 __global__ void __launch_bounds__(NT) backward_kernel(const ModelParams P) {
     constexpr int NB = D + 1;
-    constexpr int NV = NB + 2 + KMAX;
+    constexpr int NV = NB + 5;
     extern __shared__ __align__(16) float sm[];
     const ModelDev& M = P.M;
     const int p = M.n_pix, H = M.pad, nm = M.n_model, i = blockIdx.x;
@@ -91,8 +91,8 @@ __global__ void __launch_bounds__(NT) backward_kernel(const ModelParams P) {
     float* gmu = g + 96;
     float* gsg = g + 192;
     float* phi = g + 3 * 96;
-    float* dphi = phi + KMAX;
-    float* red = phi + 4 * KMAX;
+    float* dphi = phi + KROWS;
+    float* red = phi + (1 + DPS) * KROWS;
     float* out = red + (NT / 32) * NV;
     __shared__ int s_h;
     float th[5];
@@ -130,21 +130,27 @@ __global__ void __launch_bounds__(NT) backward_kernel(const ModelParams P) {
         Db[j + 2 * H] = d;
     }
     __syncthreads();
+    // dL/dtheta_c = sum_m dF'_m sum_k dphi_kc C_km (c = Teff, logg, FeH)
+    int k0, k1;
+    active_rows(M, th[0], k0, k1);
     for (int mm = threadIdx.x; mm < nm; mm += NT) {
         const float* src = Db + mm + H;
         float d = 0.0f;
         for (int s = -h; s <= h; ++s) d = fmaf(g[s + H], src[s], d);
-#pragma unroll
-        for (int k = 0; k < KMAX; ++k)
-            if (k < M.K) acc[NB + 2 + k] = fmaf(d, __ldg(M.C + (size_t)k * nm + mm), acc[NB + 2 + k]);
+        float e0 = 0.0f, e1 = 0.0f, e2 = 0.0f;
+        for (int k = k0; k < k1; ++k) {
+            const float c = __ldg(M.C + (size_t)k * nm + mm);
+            e0 = fmaf(dphi[DPS * k + 0], c, e0);
+            e1 = fmaf(dphi[DPS * k + 1], c, e1);
+            e2 = fmaf(dphi[DPS * k + 2], c, e2);
+        }
+        acc[NB + 2] = fmaf(d, e0, acc[NB + 2]);
+        acc[NB + 3] = fmaf(d, e1, acc[NB + 3]);
+        acc[NB + 4] = fmaf(d, e2, acc[NB + 4]);
     }
     block_sum<NV, NT>(acc, red, out);
     if (threadIdx.x < NB) P.gb[(size_t)i * NB + threadIdx.x] = out[threadIdx.x];
-    if (threadIdx.x < 3) {
-        float s = 0.0f;
-        for (int k = 0; k < M.K; ++k) s = fmaf(out[NB + 2 + k], dphi[3 * k + threadIdx.x], s);
-        P.gtheta[5 * i + threadIdx.x] = s;
-    }
+    if (threadIdx.x < 3) P.gtheta[5 * i + threadIdx.x] = out[NB + 2 + threadIdx.x];
     if (threadIdx.x == 3) P.gtheta[5 * i + 3] = out[NB] / M.kms_px;
     if (threadIdx.x == 4) P.gtheta[5 * i + 4] = out[NB + 1] / M.kms_px;
 }
@@ -153,21 +159,19 @@ __global__ void __launch_bounds__(NT) backward_kernel(const ModelParams P) {
 template <int NT>
 __global__ void __launch_bounds__(NT) interp_fp32_kernel(ModelDev M, const float* __restrict__ theta,
                                                          float* __restrict__ Fp) {
-    __shared__ float phi[KMAX];
+    __shared__ float phi[KROWS];
     const int i = blockIdx.x;
-    if (threadIdx.x < 32) {
-        float th[5];
+    float th[5];
 #pragma unroll
-        for (int k = 0; k < 5; ++k) th[k] = theta[5 * i + k];
-        if (threadIdx.x < M.K) basis_term(M, threadIdx.x, th, phi, nullptr);
-    }
+    for (int k = 0; k < 5; ++k) th[k] = theta[5 * i + k];
+    if (threadIdx.x < 32) warp_basis(M, th, phi, nullptr);
     __syncthreads();
+    int k0, k1;
+    active_rows(M, th[0], k0, k1);
     const int mm = blockIdx.y * NT + threadIdx.x;
     if (mm < M.n_model) {
         float acc = 0.0f;
-#pragma unroll
-        for (int k = 0; k < KMAX; ++k)
-            if (k < M.K) acc = fmaf(phi[k], __ldg(M.C + (size_t)k * M.n_model + mm), acc);
+        for (int k = k0; k < k1; ++k) acc = fmaf(phi[k], __ldg(M.C + (size_t)k * M.n_model + mm), acc);
         Fp[(size_t)i * M.n_model + mm] = acc;
     }
 }
@@ -195,7 +199,7 @@ struct ErrParams {
 };
 
 __host__ inline size_t err_smem_bytes(int p, int H, int n_model, int NT) {
-    size_t fl = (size_t)2 * ((p + 3) & ~3) + 4 * (size_t)((n_model + 3) & ~3) + 3 * 96 + 4 * KMAX +
+    size_t fl = (size_t)2 * ((p + 3) & ~3) + 4 * (size_t)((n_model + 3) & ~3) + 3 * 96 + (1 + DPS) * KROWS +
                 (size_t)(NT / 32) * 48 + 256;
     size_t sortb = (size_t)2 * ((p + 3) & ~3) + next_pow2(p);
     return 4 * (fl > sortb ? fl : sortb);
@@ -238,7 +242,7 @@ __global__ void __launch_bounds__(NT) errors_kernel(const ErrParams P) {
     constexpr int PPT = 16;
     extern __shared__ __align__(16) float sm[];
     const ModelDev& M = P.M;
-    const int p = M.n_pix, H = M.pad, nm = M.n_model, K = M.K;
+    const int p = M.n_pix, H = M.pad, nm = M.n_model;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int i = blockIdx.x;
     const int pa = (p + 3) & ~3, na = (nm + 3) & ~3;
@@ -249,8 +253,8 @@ __global__ void __launch_bounds__(NT) errors_kernel(const ErrParams P) {
     float* gmu = g + 96;
     float* gsg = g + 192;
     float* phi = g + 288;
-    float* dphi = phi + KMAX;
-    float* red = phi + 4 * KMAX;
+    float* dphi = phi + KROWS;
+    float* red = phi + (1 + DPS) * KROWS;
     float* outf = red + (NT / 32) * 48;
     double* outd = reinterpret_cast<double*>(outf + ((((size_t)(outf - sm)) & 1) ? 1 : 0));
     __shared__ double s_G[Gm::NV], s_b[NB], s_db[5 * NB], s_JJ[16];
@@ -270,20 +274,22 @@ __global__ void __launch_bounds__(NT) errors_kernel(const ErrParams P) {
         float th[5];
 #pragma unroll
         for (int k = 0; k < 5; ++k) th[k] = P.theta[5 * i + k];
-        if (lane < K) basis_term(M, lane, th, phi, dphi);
+        warp_basis(M, th, phi, dphi);
         int h = kernel_taps_warp(th[3] / M.kms_px, th[4] / M.kms_px, H, g, gmu, gsg);
         if (lane == 0) s_h = h;
     }
     __syncthreads();
     const int h = s_h;
+    int k0, k1;
+    active_rows(M, P.theta[5 * i], k0, k1);
     for (int mm = tid; mm < nm; mm += NT) {
         float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
-        for (int k = 0; k < K; ++k) {
+        for (int k = k0; k < k1; ++k) {
             const float c = __ldg(M.C + (size_t)k * nm + mm);
             a0 = fmaf(phi[k], c, a0);
-            a1 = fmaf(dphi[3 * k + 0], c, a1);
-            a2 = fmaf(dphi[3 * k + 1], c, a2);
-            a3 = fmaf(dphi[3 * k + 2], c, a3);
+            a1 = fmaf(dphi[DPS * k + 0], c, a1);
+            a2 = fmaf(dphi[DPS * k + 1], c, a2);
+            a3 = fmaf(dphi[DPS * k + 2], c, a3);
         }
         Fp[mm] = a0;
         Fp[na + mm] = a1;

@@ -348,9 +348,12 @@ int static_model(const lasp_interp_desc* d, const float* coeff, ModelDev* M) {
     M->pad = d->pad;
     M->n_model = d->n_pix + 2 * d->pad;
     M->kms_px = (float)kms;
+    M->n_reg = 1;
+    M->reg_row[0] = 0;
+    M->reg_row[1] = d->K;
     for (int k = 0; k < 3; ++k) {
-        M->blo[k] = (float)d->basis_lo[k];
-        M->bscale[k] = (float)(2.0 / (d->basis_hi[k] - d->basis_lo[k]));
+        M->rblo[0][k] = (float)d->basis_lo[k];
+        M->rbscale[0][k] = (float)(2.0 / (d->basis_hi[k] - d->basis_lo[k]));
     }
     for (int k = 0; k < 5; ++k) {
         M->plo[k] = (float)d->box_lo[k];

@@ -40,6 +40,14 @@ class InterpDesc(ct.Structure):
                 ("box_hi", ct.c_double * 5)]
 
 
+class PiecewiseDesc(ct.Structure):
+    _fields_ = [("n_reg", ct.c_int), ("K", ct.c_int * 3), ("n_pix", ct.c_int), ("pad", ct.c_int),
+                ("dln", ct.c_double), ("exps", ct.c_void_p),
+                ("basis_lo", (ct.c_double * 3) * 3), ("basis_hi", (ct.c_double * 3) * 3),
+                ("teff_blend", ct.c_double * 4), ("box_lo", ct.c_double * 5),
+                ("box_hi", ct.c_double * 5)]
+
+
 class Batch(ct.Structure):
     _fields_ = [("N", ct.c_int), ("n_pix", ct.c_int), ("flux", ct.c_void_p),
                 ("ivar", ct.c_void_p), ("good", ct.c_void_p), ("theta0", ct.c_void_p)]
@@ -63,7 +71,8 @@ EXPORTS = ["lasp_init_interp", "lasp_free_interp", "lasp_default_opts", "lasp_fi
            "lasp_errors", "lasp_forward", "lasp_backward", "lasp_interp_eval",
            "lasp_last_launches", "lasp_strerror", "lasp_version", "lasp_resample_linear",
            "lasp_slots_create", "lasp_slots_free", "lasp_slots_admit", "lasp_slots_step",
-           "lasp_slots_fetch", "lasp_interp_eval_static", "lasp_clean_mask"]
+           "lasp_slots_fetch", "lasp_interp_eval_static", "lasp_clean_mask",
+           "lasp_init_interp_piecewise"]
 
 
 def library_path() -> str:
@@ -83,6 +92,8 @@ def load(build: bool = False):
         P, I = ct.c_void_p, ct.c_int
         lib.lasp_init_interp.argtypes = [P, P, P]
         lib.lasp_init_interp.restype = I
+        lib.lasp_init_interp_piecewise.argtypes = [P, P, P]
+        lib.lasp_init_interp_piecewise.restype = I
         lib.lasp_free_interp.argtypes = [P]
         lib.lasp_default_opts.argtypes = [P]
         lib.lasp_fit_batch.argtypes = [P, P, P, P, P]
@@ -197,6 +208,42 @@ class Interp:
         self.n_model = self.n_pix + 2 * self.pad
         self.dln = float(dln)
         self.box_lo, self.box_hi = np.asarray(box_lo, float), np.asarray(box_hi, float)
+
+    @classmethod
+    def piecewise(cls, tables, exps, n_pix, pad, dln, basis_lo, basis_hi, teff_blend, box_lo,
+                  box_hi):
+        """Interpolator with Teff regimes (Eq. 1 with f1..f5): tables[r] (K_r x
+        n_model) and exps[r] (K_r x 3) per regime, coolest first, each with its
+        basis box basis_lo[r], basis_hi[r]; regimes r and r+1 blend linearly in
+        Teff on (teff_blend[2r], teff_blend[2r+1]]."""
+        lib = load()
+        n_reg = len(tables)
+        Ks = [int(np.asarray(e).shape[0]) for e in exps]
+        C = np.ascontiguousarray(np.concatenate([np.asarray(t, np.float32) for t in tables]), np.float32)
+        E = np.ascontiguousarray(np.concatenate([np.asarray(e, np.int8) for e in exps]), np.int8)
+        if C.shape != (sum(Ks), int(n_pix) + 2 * int(pad)):
+            raise ValueError("each table must be K_r x (n_pix + 2 pad)")
+        tb = list(teff_blend) + [0.0] * (4 - len(teff_blend))
+        d = PiecewiseDesc(n_reg, (ct.c_int * 3)(*(Ks + [0] * (3 - n_reg))), int(n_pix), int(pad),
+                          float(dln), E.ctypes.data)
+        for r in range(n_reg):
+            for k in range(3):
+                d.basis_lo[r][k] = float(basis_lo[r][k])
+                d.basis_hi[r][k] = float(basis_hi[r][k])
+        d.teff_blend = (ct.c_double * 4)(*tb)
+        d.box_lo = (ct.c_double * 5)(*box_lo)
+        d.box_hi = (ct.c_double * 5)(*box_hi)
+        h = ct.c_void_p()
+        _check(lib.lasp_init_interp_piecewise(ct.byref(d), C.ctypes.data, ct.byref(h)),
+               "lasp_init_interp_piecewise")
+        self = cls.__new__(cls)
+        self._h = h
+        self._exps = E
+        self.K, self.n_pix, self.pad = int(sum(Ks)), int(n_pix), int(pad)
+        self.n_model = self.n_pix + 2 * self.pad
+        self.dln = float(dln)
+        self.box_lo, self.box_hi = np.asarray(box_lo, float), np.asarray(box_hi, float)
+        return self
 
     @classmethod
     def from_grid(cls, grid, C, exps, basis_lo, basis_hi, box_lo, box_hi):
