@@ -36,6 +36,10 @@ METRIC = "converged spectra/s at fixed param tolerance, plain vs mixed; p50/p99 
 UNIT = "spectra/s"
 N_SPEC, MAX_STEPS, DEG = 4096, 500, 6
 FP32_LANES_PER_SM, N_SM = 128, 152
+# DRAM bytes of one fit_kernel<256,6> launch on this workload, from one ncu
+# capture of the current kernel source (reset to None whenever the kernel
+# changes until it is captured again).
+FIT_TRAFFIC_BYTES = 157_172_480
 
 
 def parse():
@@ -45,9 +49,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the mixed-precision, curvature-aware and piecewise entries")
     ap.add_argument("--no-served", action="store_true")
-    ap.add_argument("--cpu-sample", type=int, default=192)
+    ap.add_argument("--cpu-sample", type=int, default=2048,
+                    help="spectra in the oracle's timed CPU sample (about 16 s on 16 cores); "
+                         "the reference arm times an eighth of it per step")
     return ap.parse_args()
 
 
@@ -366,6 +373,42 @@ def run_ours(args):
               "loss_vs_adam_median_ratio": float(torch.median(lout["loss"] / out["loss"]).item()),
               "note": "Levenberg-Marquardt to the least-squares minimum (Gauss-Newton predicted decrease <= 1e-10 S)"}
 
+    # ---- piecewise Teff-regime emulator (Eq. 1 with f1..f5; 25/26/19-term cold,
+    # warm and hot regimes): its own 4096-spectrum batch over Teff 3300-11500 K
+    piecewise = {}
+    if not args.no_mixed:
+        tabs = S.make_piecewise_tables(grid)
+        ipw = lasp.Interp.piecewise(tabs, S.PW_EXPS, grid.n_pix, grid.pad, grid.dln, S.PW_BASIS_LO,
+                                    S.PW_BASIS_HI, S.TEFF_BLEND, S.PW_BOX_LO, S.PW_BOX_HI)
+        _, n_pw, off, kw = S.workload("piecewise4096")
+        dp = S.draw_batch(grid, n_pw, S.SPECTRA_SEED + off + 1000 * rank, **kw)
+        pmodel = ipw.forward(torch.tensor(dp["truth"], dtype=torch.float32, device=dev),
+                             torch.tensor(dp["b_true"], dtype=torch.float32, device=dev))
+        pf, pv = S.finish_obs(pmodel.double().cpu().numpy(), dp)
+        pin = [torch.tensor(pf, device=dev), torch.tensor(pv, device=dev),
+               torch.tensor(dp["good"], device=dev),
+               torch.tensor(dp["theta0"], dtype=torch.float32, device=dev)]
+        pout = ipw.fit(*pin, **opts)
+        torch.cuda.synchronize()
+        t_ms = []
+        for k in range(max(1, args.steps)):
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pout = ipw.fit(*pin, out=pout, **opts)
+            b.record(stream)
+            torch.cuda.synchronize()
+            t_ms.append(a.elapsed_time(b))
+        pst = pout["status"].cpu().numpy()
+        pconv = int(((pst & 3) != 0).sum())
+        perr = np.abs(pout["theta"].double().cpu().numpy() - dp["truth"])
+        piecewise = {"value": pconv / (sum(t_ms) / len(t_ms) / 1e3), "unit": UNIT,
+                     "fit_ms": sum(t_ms) / len(t_ms), "converged": pconv,
+                     "mean_steps": float(pout["steps"].float().mean()),
+                     "median_abs_teff_err_vs_truth_K": float(np.median(perr[:, 0])),
+                     "workload": "piecewise4096x3909_k25+26+19_teff3300-11500_snr5-100"}
+        ipw.close()
+
     pk, pk_kind = peaks()
     fit_avg = sum(fit_ms) / len(fit_ms)
     flops = algorithmic_flops(theta_np, steps_np, grid)
@@ -392,10 +435,13 @@ def run_ours(args):
                      "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
                      "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz "
                                     f"(sm_max_mhz, {pk_kind})",
-                     "traffic": None},
+                     "traffic": FIT_TRAFFIC_BYTES,
+                     "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one "
+                                     "fit_kernel<256,6> launch on this workload (ncu)"},
         "clocks": clocks,
         "mixed": mixed,
         "lm": lm,
+        "piecewise": piecewise,
     }
     if rank == 0 and not args.no_served:
         res["served"] = served_stream(torch, lasp, [S.LAMOST, S.DESI],
@@ -451,7 +497,7 @@ def run_reference(args):
         return
     grid = S.LAMOST
     C = S.make_table(grid)
-    n = args.cpu_sample
+    n = max(64, args.cpu_sample // 8)
     O, M, d, flux, ivar = _oracle_sample(n, grid, C, S.SPECTRA_SEED + 1)
     threads = O.lib().orc_max_threads()
     for _ in range(args.warmup):
