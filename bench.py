@@ -39,7 +39,7 @@ FP32_LANES_PER_SM, N_SM = 128, 152
 # DRAM bytes of one fit_kernel<256,6> launch on this workload, from one ncu
 # capture of the current kernel source (reset to None whenever the kernel
 # changes until it is captured again).
-FIT_TRAFFIC_BYTES = 157_172_480
+FIT_TRAFFIC_BYTES = None
 
 
 def parse():

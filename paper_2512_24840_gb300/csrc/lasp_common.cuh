@@ -53,9 +53,18 @@ __host__ __device__ constexpr int skew(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int round32(int n) { return (n + 31) & ~31; }
 __host__ __device__ constexpr int skew_size(int n) { return ((skew(n) + 4) + 3) & ~3; }
 
-__device__ __forceinline__ float ipowf(float u, int a) {
-    float r = 1.0f;
-    for (int i = 0; i < a; ++i) r *= u;
+// u^a and u^(a-1) (0 for a = 0) for 0 <= a <= 8 without a data-dependent
+// loop: eight predicated multiplies, so lanes with different exponents do not
+// diverge.  The products are taken in order u * u * ... from 1.
+__device__ __forceinline__ float pow_pair(float u, int a, float& am1) {
+    float r = 1.0f, rm = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const bool take = i < a;
+        rm = take ? r : rm;
+        r = take ? r * u : r;
+    }
+    am1 = rm;
     return r;
 }
 
@@ -98,13 +107,14 @@ __device__ __forceinline__ float monomial(const float* lo, const float* sc, cons
     const float u1 = (th[1] - lo[1]) * sc[1] - 1.0f;
     const float u2 = (th[2] - lo[2]) * sc[2] - 1.0f;
     const int a = e[0], b = e[1], c = e[2];
-    const float pa = ipowf(u0, a), pb = ipowf(u1, b), pc = ipowf(u2, c);
+    float qa, qb, qc;
+    const float pa = pow_pair(u0, a, qa), pb = pow_pair(u1, b, qb), pc = pow_pair(u2, c, qc);
     if (d) {
         // d u_T / d Teff = scale / (Teff ln 10)
         const float du0 = sc[0] / (th[0] * 2.302585092994046f);
-        d[0] = a ? (float)a * ipowf(u0, a - 1) * pb * pc * du0 : 0.0f;
-        d[1] = b ? (float)b * pa * ipowf(u1, b - 1) * pc * sc[1] : 0.0f;
-        d[2] = c ? (float)c * pa * pb * ipowf(u2, c - 1) * sc[2] : 0.0f;
+        d[0] = a ? (float)a * qa * pb * pc * du0 : 0.0f;
+        d[1] = b ? (float)b * pa * qb * pc * sc[1] : 0.0f;
+        d[2] = c ? (float)c * pa * pb * qc * sc[2] : 0.0f;
     }
     return pa * pb * pc;
 }
@@ -177,7 +187,8 @@ __device__ __forceinline__ int kernel_taps_warp(float mu, float sig, int H, floa
     const int lane = threadIdx.x & 31;
     int h = (int)ceilf(fabsf(mu) + 5.0f * sig);
     h = h > H ? H : (h < 0 ? 0 : h);
-    const float inv2s2 = 0.5f / (sig * sig);
+    const float is2 = 1.0f / (sig * sig), is3 = is2 / sig;
+    const float inv2s2 = 0.5f * is2;
     float e[3], d[3], q[3];
     float Z = 0.0f;
 #pragma unroll
@@ -186,8 +197,8 @@ __device__ __forceinline__ int kernel_taps_warp(float mu, float sig, int H, floa
         int s = i - H;
         float ds = (float)s - mu;
         e[r] = (i <= 2 * H && s >= -h && s <= h) ? expf(-ds * ds * inv2s2) : 0.0f;
-        d[r] = ds / (sig * sig);
-        q[r] = ds * ds / (sig * sig * sig);
+        d[r] = ds * is2;
+        q[r] = ds * ds * is3;
         Z += e[r];
     }
 #pragma unroll

@@ -277,31 +277,32 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) fit_kernel(const FitPar
     for (int q = tid; q < skew_size(nm + 32); q += NT) Fp[q] = 0.0f;
     for (int q = tid; q < skew_size(p + 4 * H + 40); q += NT) Db[q] = 0.0f;
 
-    // Adam state lives in registers of thread 0.
-    float x[5], m[5], v[5], prev = 0.0f;
-    int rise = 0;
-    if (tid == 0) {
-        if (fresh) {
-#pragma unroll
-            for (int k = 0; k < 5; ++k) {
-                float xx = (P.theta0[5 * i + k] - M.plo[k]) / M.phalf[k] - 1.0f;
-                xx = fminf(1.0f, fmaxf(-1.0f, xx));
-                x[k] = xx;
-                m[k] = 0.0f;
-                v[k] = 0.0f;
+    // Adam state: parameter k lives in registers of lane k of warp 0 (k < 5);
+    // lane 0 also keeps the stop-rule state.  beta^t are running products in
+    // FP64 (the bias corrections are taken in double, as PyTorch does).
+    float xk = 0.0f, mk = 0.0f, vk = 0.0f, prev = 0.0f;
+    int rise = 0, ri = t0 % P.O.window;   // ring slot of step t
+    double b1t = 1.0, b2t = 1.0;
+    if (warp == 0) {
+        if (t0 > 0) {
+            b1t = pow((double)P.O.beta1, (double)t0);
+            b2t = pow((double)P.O.beta2, (double)t0);
+        }
+        if (lane < 5) {
+            if (fresh) {
+                const float xx = (P.theta0[5 * i + lane] - M.plo[lane]) / M.phalf[lane] - 1.0f;
+                xk = fminf(1.0f, fmaxf(-1.0f, xx));
+            } else {
+                xk = P.S.x[5 * i + lane];
+                mk = P.S.m[5 * i + lane];
+                vk = P.S.v[5 * i + lane];
             }
-        } else {
-#pragma unroll
-            for (int k = 0; k < 5; ++k) {
-                x[k] = P.S.x[5 * i + k];
-                m[k] = P.S.m[5 * i + k];
-                v[k] = P.S.v[5 * i + k];
-            }
+            s_x[lane] = xk;
+        }
+        if (lane == 0 && !fresh) {
             prev = P.S.prev[i];
             rise = P.S.rise[i];
         }
-#pragma unroll
-        for (int k = 0; k < 5; ++k) s_x[k] = x[k];
     }
     if (slots && !fresh)
         for (int q = tid; q < WINMAX; q += NT) ring[q] = P.S.ring[(size_t)i * WINMAX + q];
@@ -532,70 +533,69 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) fit_kernel(const FitPar
             const float l = sqrtf(out[0] * inv_p);
             const bool nonpos = out[1] > 0.0f;
             const float kappa = l > 0.0f ? -1.0f / ((float)p * l) : 0.0f;
-            const float c0 = out[4], c1 = out[5], c2 = out[6];
-            int stop = 0;
+            // lane k < 5: dl/dx_k (Teff, logg, FeH from the basis sums; mu, sigma from the taps)
+            float gk = 0.0f;
+            if (lane < 5) {
+                const float src = lane < 3 ? out[4 + lane] : out[lane - 1] / M.kms_px;
+                gk = kappa * src * M.phalf[lane];
+            }
+            const bool fin = __all_sync(0xffffffffu, lane >= 5 || isfinite(gk));
+            uint32_t st = 0;
             if (lane == 0) {
-                float gx[5];
-                gx[0] = kappa * c0 * M.phalf[0];
-                gx[1] = kappa * c1 * M.phalf[1];
-                gx[2] = kappa * c2 * M.phalf[2];
-                gx[3] = kappa * out[2] / M.kms_px * M.phalf[3];
-                gx[4] = kappa * out[3] / M.kms_px * M.phalf[4];
-                uint32_t st = 0;
                 if (!isfinite(s_b[0])) st = 32u;
-                else {
-                    bool fin = isfinite(l);
-#pragma unroll
-                    for (int k = 0; k < 5; ++k) fin = fin && isfinite(gx[k]);
-                    if (!fin) st = 16u;
-                }
+                else if (!(fin && isfinite(l))) st = 16u;
                 if (!st) {
                     const int Wn = P.O.window;
-                    if (t >= Wn && fabsf(l - ring[t % Wn]) < P.O.tol) st = 1u;
+                    if (t >= Wn && fabsf(l - ring[ri]) < P.O.tol) st = 1u;
                     rise = (t >= 1 && l > prev) ? rise + 1 : 0;
                     if (!st && rise >= Wn) st = 2u;
                     if (!st && t >= P.O.max_steps) st = 4u;
-                    ring[t % Wn] = l;
+                    ring[ri] = l;
+                    ri = ri + 1 == Wn ? 0 : ri + 1;      // = (t + 1) mod window
                     prev = l;
                 }
-                if (st) {
-                    if (st <= 4u && nonpos) st |= 8u;
-                    for (int k = 0; k < 5; ++k) P.theta[5 * i + k] = phys_of(M, k, x[k]);
+                if (st && st <= 4u && nonpos) st |= 8u;
+            }
+            st = __shfl_sync(0xffffffffu, st, 0);
+            int stop = 0;
+            if (st) {
+                if (lane < 5) P.theta[5 * i + lane] = phys_of(M, lane, xk);
+                if (lane == 0) {
                     P.loss[i] = l;
                     P.steps[i] = t;
                     P.status[i] = st;
                     if (P.weight) P.weight[i] = s_w;
-                    stop = 1;
-                } else {
-                    const float tt = (float)(t + 1);
-                    const float bc1 = 1.0f - powf(P.O.beta1, tt);
-                    const float bc2 = 1.0f - powf(P.O.beta2, tt);
-                    const float step = P.O.lr / bc1, rbc2 = rsqrtf(bc2);
-#pragma unroll
-                    for (int k = 0; k < 5; ++k) {
-                        m[k] = P.O.beta1 * m[k] + (1.0f - P.O.beta1) * gx[k];
-                        v[k] = P.O.beta2 * v[k] + (1.0f - P.O.beta2) * gx[k] * gx[k];
-                        const float denom = sqrtf(v[k]) * rbc2 + P.O.eps;
-                        x[k] = fminf(1.0f, fmaxf(-1.0f, x[k] - step * m[k] / denom));
-                        s_x[k] = x[k];
+                }
+                stop = 1;
+            } else {
+                b1t *= (double)P.O.beta1;
+                b2t *= (double)P.O.beta2;
+                // 1 - beta^t in double (beta2^t is close to 1 early on), the rest in float
+                const float step = P.O.lr / (float)(1.0 - b1t);
+                const float bc2s = sqrtf((float)(1.0 - b2t));
+                if (lane < 5) {
+                    mk = P.O.beta1 * mk + (1.0f - P.O.beta1) * gk;
+                    vk = P.O.beta2 * vk + (1.0f - P.O.beta2) * gk * gk;
+                    const float denom = sqrtf(vk) / bc2s + P.O.eps;
+                    xk = fminf(1.0f, fmaxf(-1.0f, xk - step * mk / denom));
+                    s_x[lane] = xk;
+                }
+                if (slots && t + 1 - t0 >= P.S.budget) {
+                    // suspend: save the slot state; the slot stays running
+                    if (lane < 5) {
+                        P.S.x[5 * i + lane] = xk;
+                        P.S.m[5 * i + lane] = mk;
+                        P.S.v[5 * i + lane] = vk;
                     }
-                    if (slots && t + 1 - t0 >= P.S.budget) {
-                        // suspend: save the slot state; the slot stays running
-#pragma unroll
-                        for (int k = 0; k < 5; ++k) {
-                            P.S.x[5 * i + k] = x[k];
-                            P.S.m[5 * i + k] = m[k];
-                            P.S.v[5 * i + k] = v[k];
-                        }
+                    if (lane == 0) {
                         P.S.prev[i] = prev;
                         P.S.rise[i] = rise;
                         P.S.t[i] = t + 1;
-                        stop = 2;
                     }
+                    stop = 2;
                 }
-                s_stop = stop;
             }
-            stop = __shfl_sync(0xffffffffu, stop, 0);
+            if (lane == 0) s_stop = stop;
             __syncwarp();
             if (!stop && !clean_step(P.O, t)) {
                 int hn = warp_prepare_step(M, s_x, phi, dphi, g, gmu, gsg, s_k);
