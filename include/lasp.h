@@ -155,7 +155,10 @@ typedef struct {
     int edge_px;            /* pixels at each end left out of the loss */
     float quantile;         /* w_i = this quantile of the used flux    */
     int precision;          /* LASP_PREC_*                              */
-    int fp64_normal_eq;     /* 1: cross-warp sums and 7x7 solve in FP64 */
+    int fp64_normal_eq;     /* 1: normal equations at about FP64 precision: cross-warp
+                               sums exact in float-float, the 7x7 solve by an FP32
+                               Cholesky factor refined once with a float-float
+                               residual (no FP64 instructions on the step path) */
     int clean;              /* 1: Clean outlier masking (stage 6, Eq. 8); FP32
                                batch fits only                           */
     int clean_every;        /* mask update every this many steps (30)   */

@@ -378,6 +378,149 @@ __device__ __forceinline__ bool chol_solve_rcp(const T* packed, const T* rhs, T*
     return true;
 }
 
+// Solve of FP64 normal equations (packed upper triangle) with an FP32
+// Cholesky factor and one step of iterative refinement: x0 from the FP32
+// factor, r = rhs - G x0 in FP64, x = x0 + (FP32 solve of r).  For the
+// Legendre Gram matrices of Eq. 6 this matches an FP64 factorisation to FP64
+// rounding of the sums, with a handful of FP64 operations instead of a
+// serial FP64 factorisation (FP64 is slow on this part).
+template <int D>
+__device__ __forceinline__ bool chol_solve_refined(const double* packed, const double* rhs, double* b) {
+    constexpr int n = D + 1;
+    float L[n][n], id[n];
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            float s = (float)packed[Gram<D>::idx(j, i)];
+#pragma unroll
+            for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
+            if (i == j) {
+                if (!(s > 0.0f)) return false;
+                id[i] = rsqrt_refined(s);
+                L[i][i] = s * id[i];
+            } else {
+                L[i][j] = s * id[j];
+            }
+        }
+    }
+    auto solve = [&](const float (&r)[n], float (&x)[n]) {
+        float t[n];
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+            float s = r[i];
+#pragma unroll
+            for (int k = 0; k < i; ++k) s -= L[i][k] * t[k];
+            t[i] = s * id[i];
+        }
+#pragma unroll
+        for (int i = n - 1; i >= 0; --i) {
+            float s = t[i];
+#pragma unroll
+            for (int k = i + 1; k < n; ++k) s -= L[k][i] * x[k];
+            x[i] = s * id[i];
+        }
+    };
+    float rf[n], x0[n], dx[n];
+#pragma unroll
+    for (int i = 0; i < n; ++i) rf[i] = (float)rhs[i];
+    solve(rf, x0);
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        double r = rhs[i];
+#pragma unroll
+        for (int j = 0; j < n; ++j)
+            r -= packed[i <= j ? Gram<D>::idx(i, j) : Gram<D>::idx(j, i)] * (double)x0[j];
+        rf[i] = (float)r;
+    }
+    solve(rf, dx);
+#pragma unroll
+    for (int i = 0; i < n; ++i) b[i] = (double)x0[i] + (double)dx[i];
+    return true;
+}
+
+// ---- float-float (unevaluated sum hi + lo) arithmetic, for sums and
+// residuals that need about twice FP32 precision without FP64 instructions.
+// two_sum is Knuth's error-free addition; the product error uses one FMA.
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+    const float s = a + b;
+    const float bp = s - a;
+    const float ap = s - bp;
+    return make_float2(s, (a - ap) + (b - bp));
+}
+
+// a + b for a float-float a and a float b.
+__device__ __forceinline__ float2 ff_add(float2 a, float b) {
+    const float2 s = two_sum(a.x, b);
+    return two_sum(s.x, s.y + a.y);
+}
+
+// a - g x for float-float a and g, float x.
+__device__ __forceinline__ float2 ff_sub_mul(float2 a, float2 g, float x) {
+    const float p = g.x * x;
+    const float pe = fmaf(g.x, x, -p);       // g.x x = p + pe exactly
+    const float2 s = two_sum(a.x, -p);
+    return two_sum(s.x, s.y + a.y - pe - g.y * x);
+}
+
+// Solve of float-float normal equations (packed upper triangle) with an FP32
+// Cholesky factor of the leading parts and one step of iterative refinement
+// whose residual rhs - G x0 is taken in float-float.  For the Legendre Gram
+// matrices of Eq. 6 this matches a double-precision solve of the same sums.
+template <int D>
+__device__ __forceinline__ bool chol_solve_ff(const float2* packed, const float2* rhs, float* b) {
+    constexpr int n = D + 1;
+    float L[n][n], id[n];
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            float s = packed[Gram<D>::idx(j, i)].x;
+#pragma unroll
+            for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
+            if (i == j) {
+                if (!(s > 0.0f)) return false;
+                id[i] = rsqrt_refined(s);
+                L[i][i] = s * id[i];
+            } else {
+                L[i][j] = s * id[j];
+            }
+        }
+    }
+    auto solve = [&](const float (&r)[n], float (&x)[n]) {
+        float t[n];
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+            float s = r[i];
+#pragma unroll
+            for (int k = 0; k < i; ++k) s -= L[i][k] * t[k];
+            t[i] = s * id[i];
+        }
+#pragma unroll
+        for (int i = n - 1; i >= 0; --i) {
+            float s = t[i];
+#pragma unroll
+            for (int k = i + 1; k < n; ++k) s -= L[k][i] * x[k];
+            x[i] = s * id[i];
+        }
+    };
+    float rf[n], x0[n], dx[n];
+#pragma unroll
+    for (int i = 0; i < n; ++i) rf[i] = rhs[i].x + rhs[i].y;
+    solve(rf, x0);
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        float2 r = rhs[i];
+#pragma unroll
+        for (int j = 0; j < n; ++j) r = ff_sub_mul(r, packed[i <= j ? Gram<D>::idx(i, j) : Gram<D>::idx(j, i)], x0[j]);
+        rf[i] = r.x + r.y;
+    }
+    solve(rf, dx);
+#pragma unroll
+    for (int i = 0; i < n; ++i) b[i] = x0[i] + dx[i];
+    return true;
+}
+
 // Bitonic sort (ascending) of P2 floats in shared memory by the whole CTA.
 template <int NT>
 __device__ void block_bitonic_sort(float* buf, int P2) {

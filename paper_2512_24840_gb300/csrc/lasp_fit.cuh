@@ -141,8 +141,10 @@ __device__ __forceinline__ void reduce_to_warp0(float (&v)[NV], float* red, floa
     }
 }
 
+// As reduce_to_warp0, with the warps added in float-float (exact two-sums):
+// out[i] = (hi, lo).
 template <int NV, int NT>
-__device__ __forceinline__ void reduce_to_warp0_f64(float (&v)[NV], float* red, double* outd) {
+__device__ __forceinline__ void reduce_to_warp0_ff(float (&v)[NV], float* red, float2* outff) {
     constexpr int NP = round32(NV);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -157,10 +159,10 @@ __device__ __forceinline__ void reduce_to_warp0_f64(float (&v)[NV], float* red, 
 #pragma unroll
         for (int g = 0; g < NP / 32; ++g) {
             const int i = 32 * g + lane;
-            double s = 0.0;
+            float2 s = make_float2(0.0f, 0.0f);
 #pragma unroll
-            for (int w = 0; w < NT / 32; ++w) s += (double)red[w * NP + i];
-            if (i < NV) outd[i] = s;
+            for (int w = 0; w < NT / 32; ++w) s = ff_add(s, red[w * NP + i]);
+            if (i < NV) outff[i] = s;
         }
         __syncwarp();
     }
@@ -406,12 +408,13 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) fit_kernel(const FitPar
             }
         }
         if (P.O.fp64_ne) {
-            reduce_to_warp0_f64<NV, NT>(gacc, red, outd);
+            float2* outff = reinterpret_cast<float2*>(outd);
+            reduce_to_warp0_ff<NV, NT>(gacc, red, outff);
             if (tid == 0) {
-                double bd[NB];
-                const bool ok = chol_solve_rcp<D, double>(outd, outd + Gm::NG, bd);
+                float bf[NB];
+                const bool ok = chol_solve_ff<D>(outff, outff + Gm::NG, bf);
 #pragma unroll
-                for (int a = 0; a < NB; ++a) s_b[a] = ok ? (float)bd[a] : NAN;
+                for (int a = 0; a < NB; ++a) s_b[a] = ok ? bf[a] : NAN;
             }
         } else {
             reduce_to_warp0<NV, NT>(gacc, red, out);

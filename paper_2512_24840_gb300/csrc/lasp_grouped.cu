@@ -39,6 +39,8 @@ struct Grp {
     int* list[2];
     int* count;                   // count[0], count[1]
     float* Fp;                    // N x ldf
+    float *Y, *Wt;                // N x ldp: y = flux / w and W of section 3.3 step 2 (0 beyond p)
+    int ldp;                      // row stride of Y and Wt: n_pix rounded up to 16
     uint8_t *A_hi, *A_lo;         // K3 A images: nblk x nch x 16 KB
     float* dphi;                  // KSPLIT x list position x 32 (partial sums)
     int* err;
@@ -65,6 +67,12 @@ __global__ void __launch_bounds__(NT) k0_prep(const Grp G) {
     float w, imean;
     const int n_obj = prep_spectrum<NT>(G.flux + row, G.ivar + row, G.good + row, p, G.O.edge_px,
                                         G.O.quantile, y, W, sortbuf, red, &w, &imean);
+    __syncthreads();
+    // y and W for every step of K2, zero-padded to the row stride
+    for (int j = threadIdx.x; j < G.ldp; j += NT) {
+        G.Y[(size_t)i * G.ldp + j] = j < p ? y[j] : 0.0f;
+        G.Wt[(size_t)i * G.ldp + j] = j < p ? W[j] : 0.0f;
+    }
     if (threadIdx.x == 0) {
         G.w[i] = w;
         G.imean[i] = imean;
@@ -322,14 +330,23 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) k2_rest(const Grp G, in
     const int j0 = tid * PPT;
     const bool own_pix = j0 < p;
     const bool own_mod = j0 < nm;
-    // F' of this spectrum (K1 output): issue the loads first, store them later
-    float4 fp4[PPT / 4];
+    // F' of this spectrum (K1 output) and its y, W rows (K0 output): 256-bit
+    // loads issued first (rows are padded to 16 floats), stored after the taps
+    float fa[8], fb[8], ya[8], yb[8], wa[8], wb[8];
     if (own_mod) {
-        const float4* src = reinterpret_cast<const float4*>(G.Fp + (size_t)id * G.ldf + j0);
-#pragma unroll
-        for (int q = 0; q < PPT / 4; ++q) fp4[q] = src[q];
+        const float* src = G.Fp + (size_t)id * G.ldf + j0;
+        ldg8(src, fa);
+        ldg8(src + 8, fb);
     }
-    // kernel taps (warp 0) while the other warps set up the spectrum
+    if (own_pix) {
+        const float* ys = G.Y + (size_t)id * G.ldp + j0;
+        const float* ws = G.Wt + (size_t)id * G.ldp + j0;
+        ldg8(ys, ya);
+        ldg8(ys + 8, yb);
+        ldg8(ws, wa);
+        ldg8(ws + 8, wb);
+    }
+    // kernel taps (warp 0) while the loads are in flight
     if (warp == 0) {
         float th[5];
 #pragma unroll
@@ -352,33 +369,20 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) k2_rest(const Grp G, in
         const int j = q < L.dofs ? q - L.dofs : p + q - L.dofs;
         Db[skew(j + L.dofs)] = 0.0f;
     }
-    // y = flux / w and W = ivar / mean(ivar) on the thread's own pixels (the
-    // arithmetic of the preprocessing), straight into skewed rows
-    {
-        const size_t row = (size_t)id * p;
-        const float w = G.w[id], imean = G.imean[id];
+    if (own_pix) {
 #pragma unroll
         for (int r = 0; r < PPT; ++r) {
             const int j = j0 + r;
             if (j < p) {
-                const float f = G.flux[row + j], iv = G.ivar[row + j];
-                const bool use = G.good[row + j] && iv > 0.0f && isfinite(f) && isfinite(iv);
-                const bool edge = j < G.O.edge_px || j >= p - G.O.edge_px;
-                const bool ok = use && !edge && w > 0.0f;
-                y[skew(j)] = ok ? f / w : 0.0f;
-                W[skew(j)] = ok ? iv / imean : 0.0f;
+                y[skew(j)] = r < 8 ? ya[r & 7] : yb[r & 7];
+                W[skew(j)] = r < 8 ? wa[r & 7] : wb[r & 7];
             }
         }
-        if (own_mod) {
+    }
+    if (own_mod) {
 #pragma unroll
-            for (int q = 0; q < PPT / 4; ++q) {
-                const float4 c = fp4[q];
-                const float cv[4] = {c.x, c.y, c.z, c.w};
-#pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    if (j0 + 4 * q + e < nm) Fp[skew(j0 + 4 * q + e + 16)] = cv[e];
-            }
-        }
+        for (int r = 0; r < PPT; ++r)
+            if (j0 + r < nm) Fp[skew(j0 + r + 16)] = r < 8 ? fa[r & 7] : fb[r & 7];
     }
     __syncthreads();
     const int h = s_h;
@@ -428,12 +432,13 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) k2_rest(const Grp G, in
         }
     }
     if (G.O.fp64_ne) {
-        reduce_to_warp0_f64<NV, NT>(gacc, red, outd);
+        float2* outff = reinterpret_cast<float2*>(outd);
+        reduce_to_warp0_ff<NV, NT>(gacc, red, outff);
         if (tid == 0) {
-            double bd[NB];
-            const bool ok = chol_solve_rcp<D, double>(outd, outd + Gm::NG, bd);
+            float bf[NB];
+            const bool ok = chol_solve_ff<D>(outff, outff + Gm::NG, bf);
 #pragma unroll
-            for (int a = 0; a < NB; ++a) s_b[a] = ok ? (float)bd[a] : NAN;
+            for (int a = 0; a < NB; ++a) s_b[a] = ok ? bf[a] : NAN;
         }
     } else {
         reduce_to_warp0<NV, NT>(gacc, red, out);
@@ -867,6 +872,7 @@ int lasp_tc_fit_batch(const ModelDev& M, const TcImages& tc, const lasp_batch* b
     G.N = N;
     G.NB = NB;
     G.ldf = (M.n_model + 15) & ~15;
+    G.ldp = (M.n_pix + 15) & ~15;
     G.nch = o->precision == LASP_PREC_BF16 ? tc.n_chunks_bf16 : tc.n_chunks_tf32;
     G.nblk = (N + 127) / 128;
     G.flux = b->flux;
@@ -890,6 +896,8 @@ int lasp_tc_fit_batch(const ModelDev& M, const TcImages& tc, const lasp_batch* b
     A(&G.gsg, n * 4); A(&G.b, n * NB * 4); A(&G.rise, n * 4); A(&G.t, n * 4); A(&G.flags, n * 4);
     A(&G.list[0], n * 4); A(&G.list[1], n * 4); A(&G.count, 16);
     A(&G.Fp, n * G.ldf * 4);
+    A(&G.Y, n * G.ldp * 4);
+    A(&G.Wt, n * G.ldp * 4);
     A(&G.A_hi, (size_t)G.nblk * G.nch * TC_TILE_BYTES);
     if (o->precision == LASP_PREC_TF32X3) A(&G.A_lo, (size_t)G.nblk * G.nch * TC_TILE_BYTES);
     A(&G.dphi, (size_t)KSPLIT * G.nblk * 128 * 32 * 4);
@@ -911,7 +919,7 @@ int lasp_tc_fit_batch(const ModelDev& M, const TcImages& tc, const lasp_batch* b
         else e = LASP_EINVAL;
     }
     void* ptrs[] = {G.x, G.m, G.v, G.ring, G.prev, G.w, G.imean, G.loss, G.gmu, G.gsg, G.b, G.rise,
-                    G.t, G.flags, G.list[0], G.list[1], G.count, G.Fp, G.A_hi, G.A_lo, G.dphi};
+                    G.t, G.flags, G.list[0], G.list[1], G.count, G.Fp, G.Y, G.Wt, G.A_hi, G.A_lo, G.dphi};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, st);
     return e;

@@ -134,7 +134,7 @@ __device__ void lm_eval(const ModelDev& M, const float* th, const float* y, cons
     if (tid == 0) {
         for (int q = 0; q < NV; ++q) s_G[q] = outd[q];
         double bd[NB];
-        *s_ok = chol_solve_rcp<D, double>(s_G, s_G + Gm::NG, bd) ? 1 : 0;
+        *s_ok = chol_solve_refined<D>(s_G, s_G + Gm::NG, bd) ? 1 : 0;
         for (int a = 0; a < NB; ++a) s_b[a] = bd[a];
     }
     __syncthreads();
@@ -193,7 +193,7 @@ __device__ void lm_eval(const ModelDev& M, const float* th, const float* y, cons
         if (tid < 5) {
             double tk[NB], dbk[NB];
             for (int a = 0; a < NB; ++a) tk[a] = outd[tid * NB + a];
-            chol_solve_rcp<D, double>(s_G, tk, dbk);
+            chol_solve_refined<D>(s_G, tk, dbk);
             for (int a = 0; a < NB; ++a) s_db[tid * NB + a] = dbk[a];
         }
         if (tid == 0) s_sum[0] = outd[5 * NB];

@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(NT) errors_kernel(const ErrParams P) {
     if (tid == 0) {
         for (int q = 0; q < NV; ++q) s_G[q] = outd[q];
         double bd[NB];
-        s_ok = chol_solve_rcp<D, double>(s_G, s_G + Gm::NG, bd) ? 1 : 0;
+        s_ok = chol_solve_refined<D>(s_G, s_G + Gm::NG, bd) ? 1 : 0;
         for (int a = 0; a < NB; ++a) s_b[a] = bd[a];
     }
     __syncthreads();
@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(NT) errors_kernel(const ErrParams P) {
         // db_k = G^-1 t_k
         double tk[NB], dbk[NB];
         for (int a = 0; a < NB; ++a) tk[a] = outd[tid * NB + a];
-        chol_solve_rcp<D, double>(s_G, tk, dbk);
+        chol_solve_refined<D>(s_G, tk, dbk);
         for (int a = 0; a < NB; ++a) s_db[tid * NB + a] = dbk[a];
     }
     if (tid == 0) s_JJ[15] = outd[5 * NB];
