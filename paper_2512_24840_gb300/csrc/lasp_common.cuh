@@ -521,6 +521,93 @@ __device__ __forceinline__ bool chol_solve_ff(const float2* packed, const float2
     return true;
 }
 
+// Block-wide sum of NV floats per thread: FP32 within each warp, the warps
+// added in float-float (exact two-sums) by thread i < NV; out[i] = (hi, lo),
+// visible to every thread after the closing barrier.
+template <int NV, int NT>
+__device__ __forceinline__ void block_sum_ff(float (&v)[NV], float* red, float2* out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        float s = v[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) red[warp * NV + i] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        float2 s = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w) s = ff_add(s, red[w * NV + threadIdx.x]);
+        out[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+// Inverse of a 5x5 symmetric positive definite matrix given in float-float
+// (row-major): X0 from an FP32 Cholesky factor of the leading parts, then one
+// refinement X = X0 + X0 (I - A X0) with the residual in float-float.  One
+// thread.  Returns false when a pivot is not positive.
+__device__ __forceinline__ bool inv_spd5_ff(const float2 (&A)[25], float (&X)[25]) {
+    float L[5][5], id[5], X0[25];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            float s = A[i * 5 + j].x;
+#pragma unroll
+            for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
+            if (i == j) {
+                if (!(s > 0.0f)) return false;
+                id[i] = rsqrt_refined(s);
+                L[i][i] = s * id[i];
+            } else {
+                L[i][j] = s * id[j];
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+        float t[5], x[5];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            float s = i == c ? 1.0f : 0.0f;
+#pragma unroll
+            for (int k = 0; k < i; ++k) s -= L[i][k] * t[k];
+            t[i] = s * id[i];
+        }
+#pragma unroll
+        for (int i = 4; i >= 0; --i) {
+            float s = t[i];
+#pragma unroll
+            for (int k = i + 1; k < 5; ++k) s -= L[k][i] * x[k];
+            x[i] = s * id[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 5; ++i) X0[i * 5 + c] = x[i];
+    }
+    float R[25];
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            float2 r = make_float2(i == j ? 1.0f : 0.0f, 0.0f);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) r = ff_sub_mul(r, A[i * 5 + k], X0[k * 5 + j]);
+            R[i * 5 + j] = r.x + r.y;
+        }
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            float s = X0[i * 5 + j];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) s = fmaf(X0[i * 5 + k], R[k * 5 + j], s);
+            X[i * 5 + j] = s;
+        }
+    return true;
+}
+
 // Bitonic sort (ascending) of P2 floats in shared memory by the whole CTA.
 template <int NT>
 __device__ void block_bitonic_sort(float* buf, int P2) {

@@ -3,7 +3,7 @@
 // every point -- the objective of Eq. 9.  One CTA per spectrum.  A full
 // evaluation takes the Jacobian of r = sqrt(W) eps analytically (forward mode
 // through Eq. 5 and the normal equations, as for stage 9) and forms A = J^T J
-// and g = J^T r in FP64; parameters held on a bound by the gradient are
+// and g = J^T r with float-float sums; parameters held on a bound by the gradient are
 // frozen, and pred0 = g^T A^-1 g (the Gauss-Newton predicted decrease) is
 // both the stop test (pred0 <= rtol S) and, where S differences fall below
 // what FP32 model values resolve (1e-6 S), the merit that judges a trial.
@@ -42,11 +42,12 @@ __host__ inline size_t lm_smem_bytes(int p, int H, int n_model, int NT) {
 
 // Evaluate at physical theta (block-wide).  FULL: also the Jacobian sums
 // A (15, packed upper triangle, x units), g (5, x units).  Returns S in
-// s_S[0] (and s_ok: 1 if the normal equations were solvable).
+// s_sum[0] and the FULL sums in s_sum[1..20], all float-float (and s_ok: 1 if
+// the normal equations were solvable).
 template <int NT, int D, bool FULL>
 __device__ void lm_eval(const ModelDev& M, const float* th, const float* y, const float* W, float* Fp,
                         int na, float* g, float* gmu, float* gsg, float* phi, float* dphi, float* red,
-                        double* outd, double* s_G, double* s_b, double* s_db, double* s_sum, int* s_h,
+                        float2* outff, float2* s_G, float* s_b, float* s_db, float2* s_sum, int* s_h,
                         int* s_ok) {
     using Gm = Gram<D>;
     constexpr int NB = D + 1;
@@ -130,18 +131,19 @@ __device__ void lm_eval(const ModelDev& M, const float* th, const float* y, cons
             }
         }
     }
-    block_sum_f64<NV, NT>(gacc, red, outd);
+    block_sum_ff<NV, NT>(gacc, red, outff);
+    if (tid < NV) s_G[tid] = outff[tid];
+    __syncthreads();
     if (tid == 0) {
-        for (int q = 0; q < NV; ++q) s_G[q] = outd[q];
-        double bd[NB];
-        *s_ok = chol_solve_refined<D>(s_G, s_G + Gm::NG, bd) ? 1 : 0;
+        float bd[NB];
+        *s_ok = chol_solve_ff<D>(s_G, s_G + Gm::NG, bd) ? 1 : 0;
         for (int a = 0; a < NB; ++a) s_b[a] = bd[a];
     }
     __syncthreads();
     if (!*s_ok) return;
     float bl[NB];
 #pragma unroll
-    for (int a = 0; a < NB; ++a) bl[a] = (float)s_b[a];
+    for (int a = 0; a < NB; ++a) bl[a] = s_b[a];
     if (!FULL) {
         float sacc[1] = {0.0f};
 #pragma unroll
@@ -157,8 +159,8 @@ __device__ void lm_eval(const ModelDev& M, const float* th, const float* y, cons
                 sacc[0] = fmaf(W[j] * e, e, sacc[0]);
             }
         }
-        block_sum_f64<1, NT>(sacc, red, outd);
-        if (tid == 0) s_sum[0] = outd[0];
+        block_sum_ff<1, NT>(sacc, red, outff);
+        if (tid == 0) s_sum[0] = outff[0];
         __syncthreads();
         return;
     } else {
@@ -189,20 +191,19 @@ __device__ void lm_eval(const ModelDev& M, const float* th, const float* y, cons
                 tacc[5 * NB] = fmaf(Wj * e, e, tacc[5 * NB]);
             }
         }
-        block_sum_f64<NT2, NT>(tacc, red, outd);
+        block_sum_ff<NT2, NT>(tacc, red, outff);
         if (tid < 5) {
-            double tk[NB], dbk[NB];
-            for (int a = 0; a < NB; ++a) tk[a] = outd[tid * NB + a];
-            chol_solve_refined<D>(s_G, tk, dbk);
+            float dbk[NB];
+            chol_solve_ff<D>(s_G, outff + tid * NB, dbk);
             for (int a = 0; a < NB; ++a) s_db[tid * NB + a] = dbk[a];
         }
-        if (tid == 0) s_sum[0] = outd[5 * NB];
+        if (tid == 0) s_sum[0] = outff[5 * NB];
         __syncthreads();
         float dbl[5][NB];
 #pragma unroll
         for (int k = 0; k < 5; ++k)
 #pragma unroll
-            for (int a = 0; a < NB; ++a) dbl[k][a] = (float)s_db[k * NB + a];
+            for (int a = 0; a < NB; ++a) dbl[k][a] = s_db[k * NB + a];
         // J in x units (physical J times the half box width), A = J^T J, g = J^T r
         float jj[20];
 #pragma unroll
@@ -235,44 +236,53 @@ __device__ void lm_eval(const ModelDev& M, const float* th, const float* y, cons
                 for (int a = 0; a < 5; ++a) jj[15 + a] = fmaf(Jr[a], rj, jj[15 + a]);
             }
         }
-        block_sum_f64<20, NT>(jj, red, outd);
-        if (tid < 20) s_sum[1 + tid] = outd[tid];
+        block_sum_ff<20, NT>(jj, red, outff);
+        if (tid < 20) s_sum[1 + tid] = outff[tid];
         __syncthreads();
     }
 }
 
 enum : int { LM_FULL_CUR = 0, LM_FULL_TRIAL = 1, LM_S_TRIAL = 2, LM_DONE = 3 };
 
-// Control state of one CTA (shared memory, touched by thread 0 only).
+// Control state of one CTA (shared memory, touched by thread 0 only).  S is
+// float-float, so differences of S near convergence stay exact to about
+// twice FP32 precision; the 5x5 systems are solved in FP32.
 struct LmCtl {
-    double S, pred0, lam, nu, pred;
-    double Ar[15], gr[5];   // reduced system at the current point
-    double An[15], gn[5];   // at the trial point (full trial evaluations)
-    double d[5];
-    double Sn, pn;
+    float2 S, Sn;
+    float pred0, lam, nu, pred, pn;
+    float Ar[15], gr[5];   // reduced system at the current point
+    float An[15], gn[5];   // at the trial point (full trial evaluations)
+    float d[5];
     int it, trial, phase;
     uint32_t status;
 };
 
+// (a - b) of two float-float values, rounded to float.
+__device__ __forceinline__ float ff_diff(float2 a, float2 b) {
+    const float2 s = two_sum(a.x, -b.x);
+    return s.x + (s.y + (a.y - b.y));
+}
+
 // Reduced system from the sums of a full evaluation at x: parameters on a
 // bound whose gradient points out of the box are frozen (unit row/column,
 // zero gradient); pred0 = g^T A^-1 g (infinite if A is not positive definite).
-__device__ inline void lm_reduce(const double* sum, const float* x, double* Ar, double* gr, double& S,
-                                 double& pred0) {
+__device__ inline void lm_reduce(const float2* sum, const float* x, float* Ar, float* gr, float2& S,
+                                 float& pred0) {
     S = sum[0];
     bool fr[5];
     for (int a = 0; a < 5; ++a) {
-        const double ga = sum[16 + a];
-        fr[a] = !((x[a] <= -1.0f && ga > 0.0) || (x[a] >= 1.0f && ga < 0.0));
-        gr[a] = fr[a] ? ga : 0.0;
+        const float ga = sum[16 + a].x + sum[16 + a].y;
+        fr[a] = !((x[a] <= -1.0f && ga > 0.0f) || (x[a] >= 1.0f && ga < 0.0f));
+        gr[a] = fr[a] ? ga : 0.0f;
     }
     int q = 0;
     for (int a = 0; a < 5; ++a)
-        for (int b = a; b < 5; ++b, ++q) Ar[q] = (fr[a] && fr[b]) ? sum[1 + q] : (a == b ? 1.0 : 0.0);
-    double mg[5], d0[5];
+        for (int b = a; b < 5; ++b, ++q)
+            Ar[q] = (fr[a] && fr[b]) ? sum[1 + q].x + sum[1 + q].y : (a == b ? 1.0f : 0.0f);
+    float mg[5], d0[5];
     for (int a = 0; a < 5; ++a) mg[a] = -gr[a];
-    if (chol_solve_rcp<4, double>(Ar, mg, d0)) {
-        double s = 0.0;
+    if (chol_solve_rcp<4, float>(Ar, mg, d0)) {
+        float s = 0.0f;
         for (int a = 0; a < 5; ++a) s -= gr[a] * d0[a];
         pred0 = s;
     } else {
@@ -284,38 +294,39 @@ __device__ inline void lm_reduce(const double* sum, const float* x, double* Ar, 
 // iterate).  Sets c.phase to the evaluation the trial needs, or LM_DONE after
 // ten rejections.
 __device__ inline void lm_start_trial(LmCtl& c, const float* x, float* xt) {
-    constexpr double kEta = 1e-6;
+    constexpr float kEta = 1e-6f;
     for (;;) {
         if (c.trial >= 10) {
             c.status = LASP_ST_CONV_TOL;
             c.phase = LM_DONE;
             return;
         }
-        double Ad[15], rhs[5];
+        float Ad[15], rhs[5];
         for (int q = 0; q < 15; ++q) Ad[q] = c.Ar[q];
         for (int a = 0; a < 5; ++a) {
             Ad[Gram<4>::idx(a, a)] += c.lam * c.Ar[Gram<4>::idx(a, a)];
             rhs[a] = -c.gr[a];
         }
-        if (chol_solve_rcp<4, double>(Ad, rhs, c.d)) break;
+        if (chol_solve_rcp<4, float>(Ad, rhs, c.d)) break;
         c.lam *= c.nu;
-        c.nu *= 2.0;
+        c.nu *= 2.0f;
         ++c.trial;
     }
     // predicted decrease of S: -(2 g.d + d^T A d)
-    double pred = 0.0;
+    float pred = 0.0f;
     for (int a = 0; a < 5; ++a) {
-        double Adv = 0.0;
+        float Adv = 0.0f;
         for (int b = 0; b < 5; ++b) Adv += c.Ar[a <= b ? Gram<4>::idx(a, b) : Gram<4>::idx(b, a)] * c.d[b];
-        pred -= 2.0 * c.gr[a] * c.d[a] + c.d[a] * Adv;
+        pred -= 2.0f * c.gr[a] * c.d[a] + c.d[a] * Adv;
     }
     c.pred = pred;
-    for (int k = 0; k < 5; ++k) xt[k] = fminf(1.0f, fmaxf(-1.0f, x[k] + (float)c.d[k]));
-    c.phase = pred >= kEta * c.S ? LM_S_TRIAL : LM_FULL_TRIAL;
+    for (int k = 0; k < 5; ++k) xt[k] = fminf(1.0f, fmaxf(-1.0f, x[k] + c.d[k]));
+    const float S = c.S.x + c.S.y;
+    c.phase = pred >= kEta * S ? LM_S_TRIAL : LM_FULL_TRIAL;
 }
 
-__device__ inline void lm_new_iterate(LmCtl& c, const float* x, float* xt, int max_iter, double rtol) {
-    if (c.pred0 <= rtol * c.S) {
+__device__ inline void lm_new_iterate(LmCtl& c, const float* x, float* xt, int max_iter, float rtol) {
+    if (c.pred0 <= rtol * (c.S.x + c.S.y)) {
         c.status = LASP_ST_CONV_TOL;
         c.phase = LM_DONE;
     } else if (c.it >= max_iter) {
@@ -328,9 +339,9 @@ __device__ inline void lm_new_iterate(LmCtl& c, const float* x, float* xt, int m
 }
 
 // Thread 0, after the evaluation of phase ph.
-static __device__ __noinline__ void lm_control(LmCtl& c, int ph, int ok, const double* sum, float* x, float* xt,
-                                        int max_iter, double rtol) {
-    constexpr double kEta = 1e-6;
+static __device__ __noinline__ void lm_control(LmCtl& c, int ph, int ok, const float2* sum, float* x,
+                                               float* xt, int max_iter, float rtol) {
+    constexpr float kEta = 1e-6f;
     if (ph == LM_FULL_CUR) {
         if (!ok) {
             c.status = LASP_ST_SINGULAR;
@@ -341,27 +352,28 @@ static __device__ __noinline__ void lm_control(LmCtl& c, int ph, int ok, const d
         lm_new_iterate(c, x, xt, max_iter, rtol);
         return;
     }
-    double rho = -1.0;
+    float rho = -1.0f;
     if (ph == LM_S_TRIAL) {
-        const double St = sum[0];
-        if (ok && isfinite(St)) rho = (c.S - St) / c.pred;
+        const float2 St = sum[0];
+        if (ok && isfinite(St.x)) rho = ff_diff(c.S, St) / c.pred;
     } else if (ok) {
         lm_reduce(sum, xt, c.An, c.gn, c.Sn, c.pn);
-        if (isfinite(c.Sn) && c.Sn <= c.S * (1.0 + kEta)) {
+        const float S = c.S.x + c.S.y;
+        if (isfinite(c.Sn.x) && ff_diff(c.S, c.Sn) >= -kEta * S) {
             // merit the model predicts: its gradient after the step is lambda diag(A) d
-            double gm[5], z[5], pm = 0.0;
+            float gm[5], z[5], pm = 0.0f;
             for (int a = 0; a < 5; ++a) gm[a] = c.lam * c.Ar[Gram<4>::idx(a, a)] * c.d[a];
-            if (chol_solve_rcp<4, double>(c.Ar, gm, z))
+            if (chol_solve_rcp<4, float>(c.Ar, gm, z))
                 for (int a = 0; a < 5; ++a) pm += gm[a] * z[a];
-            const double den = c.pred0 - pm > 0.0 ? c.pred0 - pm : c.pred0;
+            const float den = c.pred0 - pm > 0.0f ? c.pred0 - pm : c.pred0;
             rho = (c.pred0 - c.pn) / den;
         }
     }
-    if (rho > 0.0) {
-        const double t = 2.0 * rho - 1.0, f = 1.0 - t * t * t;
-        c.lam *= f > 1.0 / 3.0 ? f : 1.0 / 3.0;
-        if (c.lam < 1e-12) c.lam = 1e-12;
-        c.nu = 2.0;
+    if (rho > 0.0f) {
+        const float t = 2.0f * rho - 1.0f, f = 1.0f - t * t * t;
+        c.lam *= f > 1.0f / 3.0f ? f : 1.0f / 3.0f;
+        if (c.lam < 1e-12f) c.lam = 1e-12f;
+        c.nu = 2.0f;
         for (int k = 0; k < 5; ++k) x[k] = xt[k];
         ++c.it;
         if (ph == LM_S_TRIAL) {
@@ -375,14 +387,16 @@ static __device__ __noinline__ void lm_control(LmCtl& c, int ph, int ok, const d
         }
     } else {
         c.lam *= c.nu;
-        c.nu *= 2.0;
+        c.nu *= 2.0f;
         ++c.trial;
         lm_start_trial(c, x, xt);
     }
 }
 
+// Two CTAs per SM at 256 threads (128 registers; the shared-memory plan of about
+// 100 KB allows two): a few spills cost far less than halving the resident warps.
 template <int NT, int D>
-__global__ void __launch_bounds__(NT) lm_kernel(const LmParams P) {
+__global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) lm_kernel(const LmParams P) {
     extern __shared__ __align__(16) float sm[];
     const ModelDev& M = P.M;
     const int p = M.n_pix, nm = M.n_model;
@@ -399,8 +413,9 @@ __global__ void __launch_bounds__(NT) lm_kernel(const LmParams P) {
     float* dphi = phi + KROWS;
     float* red = phi + (1 + DPS) * KROWS;
     float* outf = red + (NT / 32) * 48;
-    double* outd = reinterpret_cast<double*>(outf + ((((size_t)(outf - sm)) & 1) ? 1 : 0));
-    __shared__ double s_G[Gram<D>::NV], s_b[D + 1], s_db[5 * (D + 1)], s_sum[21];
+    float2* outff = reinterpret_cast<float2*>(outf + ((((size_t)(outf - sm)) & 1) ? 1 : 0));
+    __shared__ float2 s_G[Gram<D>::NV], s_sum[21];
+    __shared__ float s_b[D + 1], s_db[5 * (D + 1)];
     __shared__ float s_x[5], s_xt[5];
     __shared__ int s_h, s_ok;
     __shared__ LmCtl c;
@@ -414,12 +429,12 @@ __global__ void __launch_bounds__(NT) lm_kernel(const LmParams P) {
             s_x[k] = fminf(1.0f, fmaxf(-1.0f, xx));
         }
         if (P.weight) P.weight[i] = w;
-        c.lam = 1e-3;
-        c.nu = 2.0;
+        c.lam = 1e-3f;
+        c.nu = 2.0f;
         c.it = 0;
         c.trial = 0;
         c.status = 0;
-        c.S = NAN;
+        c.S = make_float2(NAN, 0.0f);
         c.phase = LM_FULL_CUR;
     }
     __syncthreads();
@@ -441,16 +456,16 @@ __global__ void __launch_bounds__(NT) lm_kernel(const LmParams P) {
 #pragma unroll
         for (int k = 0; k < 5; ++k) th[k] = phys_of(M, k, xp[k]);
         if (ph == LM_S_TRIAL)
-            lm_eval<NT, D, false>(M, th, y, W, Fp, na, g, gmu, gsg, phi, dphi, red, outd, s_G, s_b, s_db,
+            lm_eval<NT, D, false>(M, th, y, W, Fp, na, g, gmu, gsg, phi, dphi, red, outff, s_G, s_b, s_db,
                                   s_sum, &s_h, &s_ok);
         else
-            lm_eval<NT, D, true>(M, th, y, W, Fp, na, g, gmu, gsg, phi, dphi, red, outd, s_G, s_b, s_db,
+            lm_eval<NT, D, true>(M, th, y, W, Fp, na, g, gmu, gsg, phi, dphi, red, outff, s_G, s_b, s_db,
                                  s_sum, &s_h, &s_ok);
-        if (tid == 0) lm_control(c, ph, s_ok, s_sum, s_x, s_xt, P.max_iter, P.rtol);
+        if (tid == 0) lm_control(c, ph, s_ok, s_sum, s_x, s_xt, P.max_iter, (float)P.rtol);
     }
     if (tid == 0) {
         for (int k = 0; k < 5; ++k) P.theta[5 * i + k] = phys_of(M, k, s_x[k]);
-        P.loss[i] = (float)sqrt(c.S / p);
+        P.loss[i] = sqrtf((c.S.x + c.S.y) / (float)p);
         P.steps[i] = c.it;
         P.status[i] = c.status;
     }

@@ -205,37 +205,10 @@ __host__ inline size_t err_smem_bytes(int p, int H, int n_model, int NT) {
     return 4 * (fl > sortb ? fl : sortb);
 }
 
-template <int D>
-__device__ bool inv5_f64(const double* A, double* Ai) {
-    double a[5][10];
-    for (int r = 0; r < 5; ++r)
-        for (int c = 0; c < 10; ++c) a[r][c] = c < 5 ? A[r * 5 + c] : (c - 5 == r ? 1.0 : 0.0);
-    for (int c = 0; c < 5; ++c) {
-        int piv = c;
-        for (int r = c + 1; r < 5; ++r)
-            if (fabs(a[r][c]) > fabs(a[piv][c])) piv = r;
-        if (!(fabs(a[piv][c]) > 0.0)) return false;
-        if (piv != c)
-            for (int k = 0; k < 10; ++k) {
-                double t = a[c][k];
-                a[c][k] = a[piv][k];
-                a[piv][k] = t;
-            }
-        double d = a[c][c];
-        for (int k = 0; k < 10; ++k) a[c][k] /= d;
-        for (int r = 0; r < 5; ++r) {
-            if (r == c) continue;
-            double f = a[r][c];
-            for (int k = 0; k < 10; ++k) a[r][k] -= f * a[c][k];
-        }
-    }
-    for (int r = 0; r < 5; ++r)
-        for (int c = 0; c < 5; ++c) Ai[r * 5 + c] = a[r][c + 5];
-    return true;
-}
-
+// Two CTAs per SM at 256 threads (128 registers; the shared-memory plan of about
+// 100 KB allows two): a few spills cost far less than halving the resident warps.
 template <int NT, int D>
-__global__ void __launch_bounds__(NT) errors_kernel(const ErrParams P) {
+__global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) errors_kernel(const ErrParams P) {
     using Gm = Gram<D>;
     constexpr int NB = D + 1;
     constexpr int NV = Gm::NV;
@@ -256,8 +229,9 @@ __global__ void __launch_bounds__(NT) errors_kernel(const ErrParams P) {
     float* dphi = phi + KROWS;
     float* red = phi + (1 + DPS) * KROWS;
     float* outf = red + (NT / 32) * 48;
-    double* outd = reinterpret_cast<double*>(outf + ((((size_t)(outf - sm)) & 1) ? 1 : 0));
-    __shared__ double s_G[Gm::NV], s_b[NB], s_db[5 * NB], s_JJ[16];
+    float2* outff = reinterpret_cast<float2*>(outf + ((((size_t)(outf - sm)) & 1) ? 1 : 0));
+    __shared__ float2 s_G[Gm::NV], s_JJ[16];
+    __shared__ float s_b[NB], s_db[5 * NB];
     __shared__ int s_h, s_ok;
 
     const size_t row = (size_t)i * p;
@@ -342,11 +316,12 @@ __global__ void __launch_bounds__(NT) errors_kernel(const ErrParams P) {
             }
         }
     }
-    block_sum_f64<NV, NT>(gacc, red, outd);
+    block_sum_ff<NV, NT>(gacc, red, outff);
+    if (tid < NV) s_G[tid] = outff[tid];
+    __syncthreads();
     if (tid == 0) {
-        for (int q = 0; q < NV; ++q) s_G[q] = outd[q];
-        double bd[NB];
-        s_ok = chol_solve_refined<D>(s_G, s_G + Gm::NG, bd) ? 1 : 0;
+        float bd[NB];
+        s_ok = chol_solve_ff<D>(s_G, s_G + Gm::NG, bd) ? 1 : 0;
         for (int a = 0; a < NB; ++a) s_b[a] = bd[a];
     }
     __syncthreads();
@@ -363,7 +338,7 @@ __global__ void __launch_bounds__(NT) errors_kernel(const ErrParams P) {
     for (int q = 0; q < NT2; ++q) tacc[q] = 0.0f;
     float bl[NB];
 #pragma unroll
-    for (int a = 0; a < NB; ++a) bl[a] = (float)s_b[a];
+    for (int a = 0; a < NB; ++a) bl[a] = s_b[a];
     float cc[PPT];
 #pragma unroll
     for (int r = 0; r < PPT; ++r) {
@@ -386,22 +361,21 @@ __global__ void __launch_bounds__(NT) errors_kernel(const ErrParams P) {
             tacc[5 * NB] = fmaf(Wj * e, e, tacc[5 * NB]);
         }
     }
-    block_sum_f64<NT2, NT>(tacc, red, outd);
+    block_sum_ff<NT2, NT>(tacc, red, outff);
     if (tid < 5) {
         // db_k = G^-1 t_k
-        double tk[NB], dbk[NB];
-        for (int a = 0; a < NB; ++a) tk[a] = outd[tid * NB + a];
-        chol_solve_refined<D>(s_G, tk, dbk);
+        float dbk[NB];
+        chol_solve_ff<D>(s_G, outff + tid * NB, dbk);
         for (int a = 0; a < NB; ++a) s_db[tid * NB + a] = dbk[a];
     }
-    if (tid == 0) s_JJ[15] = outd[5 * NB];
+    if (tid == 0) s_JJ[15] = outff[5 * NB];
     __syncthreads();
     // J_jk and J^T J (15 sums: FP32 over the thread's 16 pixels, FP64 across threads)
     float dbl[5][NB];
 #pragma unroll
     for (int k = 0; k < 5; ++k)
 #pragma unroll
-        for (int a = 0; a < NB; ++a) dbl[k][a] = (float)s_db[k * NB + a];
+        for (int a = 0; a < NB; ++a) dbl[k][a] = s_db[k * NB + a];
     float jj[15];
 #pragma unroll
     for (int q = 0; q < 15; ++q) jj[q] = 0.0f;
@@ -427,24 +401,14 @@ __global__ void __launch_bounds__(NT) errors_kernel(const ErrParams P) {
                 for (int b2 = a; b2 < 5; ++b2) { jj[q] = fmaf(Jr[a], Jr[b2], jj[q]); ++q; }
         }
     }
-    // FP64 block reduction of the 15 sums
-    double* redd = reinterpret_cast<double*>(red + ((((size_t)(red - sm)) & 1) ? 1 : 0));
-#pragma unroll
-    for (int q = 0; q < 15; ++q) {
-        double s = (double)jj[q];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) redd[warp * 15 + q] = s;
-    }
-    __syncthreads();
-    if (tid < 15) {
-        double s = 0.0;
-        for (int w2 = 0; w2 < NT / 32; ++w2) s += redd[w2 * 15 + tid];
-        s_JJ[tid] = s;
-    }
+    // the 15 sums: FP32 within warps, float-float across them
+    __syncthreads();                     // the db solves are done reading outff
+    block_sum_ff<15, NT>(jj, red, outff);
+    if (tid < 15) s_JJ[tid] = outff[tid];
     __syncthreads();
     if (tid == 0) {
-        double A[25], Ai[25];
+        float2 A[25];
+        float Ai[25];
         int q = 0;
         for (int a = 0; a < 5; ++a)
             for (int b2 = a; b2 < 5; ++b2) {
@@ -452,11 +416,11 @@ __global__ void __launch_bounds__(NT) errors_kernel(const ErrParams P) {
                 A[b2 * 5 + a] = s_JJ[q];
                 ++q;
             }
-        bool ok = inv5_f64<D>(A, Ai);
-        const double s2 = s_JJ[15] / (double)(n_obj - 5);
-        for (int k = 0; k < 5; ++k) P.sigma[5 * i + k] = ok ? (float)sqrt(s2 * Ai[k * 5 + k]) : NAN;
+        const bool ok = inv_spd5_ff(A, Ai);
+        const float s2 = (s_JJ[15].x + s_JJ[15].y) / (float)(n_obj - 5);
+        for (int k = 0; k < 5; ++k) P.sigma[5 * i + k] = ok ? sqrtf(s2 * Ai[k * 5 + k]) : NAN;
         if (P.cov)
-            for (int k = 0; k < 25; ++k) P.cov[25 * (size_t)i + k] = ok ? s2 * Ai[k] : NAN;
+            for (int k = 0; k < 25; ++k) P.cov[25 * (size_t)i + k] = ok ? (double)(s2 * Ai[k]) : NAN;
         if (P.status) P.status[i] = ok ? 0u : 32u;
     }
 }
