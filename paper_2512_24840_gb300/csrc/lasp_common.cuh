@@ -273,28 +273,6 @@ __device__ __forceinline__ void block_sum(float (&v)[NV], float* red, float* out
     __syncthreads();
 }
 
-// Same, with the cross-warp stage in FP64 (outd) -- the mixed-precision
-// normal equations keep their inter-warp sums and the solve in FP64.
-template <int NV, int NT>
-__device__ __forceinline__ void block_sum_f64(float (&v)[NV], float* red, double* outd) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-        float s = v[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) red[warp * NV + i] = s;
-    }
-    __syncthreads();
-    if (threadIdx.x < NV) {
-        double s = 0.0;
-#pragma unroll
-        for (int w = 0; w < NT / 32; ++w) s += (double)red[w * NV + threadIdx.x];
-        outd[threadIdx.x] = s;
-    }
-    __syncthreads();
-}
-
 // Cholesky solve of the packed (D+1)x(D+1) SPD system; returns false when a
 // pivot is not positive.  T = float or double.
 template <int D, typename T>
@@ -378,67 +356,6 @@ __device__ __forceinline__ bool chol_solve_rcp(const T* packed, const T* rhs, T*
     return true;
 }
 
-// Solve of FP64 normal equations (packed upper triangle) with an FP32
-// Cholesky factor and one step of iterative refinement: x0 from the FP32
-// factor, r = rhs - G x0 in FP64, x = x0 + (FP32 solve of r).  For the
-// Legendre Gram matrices of Eq. 6 this matches an FP64 factorisation to FP64
-// rounding of the sums, with a handful of FP64 operations instead of a
-// serial FP64 factorisation (FP64 is slow on this part).
-template <int D>
-__device__ __forceinline__ bool chol_solve_refined(const double* packed, const double* rhs, double* b) {
-    constexpr int n = D + 1;
-    float L[n][n], id[n];
-#pragma unroll
-    for (int i = 0; i < n; ++i) {
-#pragma unroll
-        for (int j = 0; j <= i; ++j) {
-            float s = (float)packed[Gram<D>::idx(j, i)];
-#pragma unroll
-            for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
-            if (i == j) {
-                if (!(s > 0.0f)) return false;
-                id[i] = rsqrt_refined(s);
-                L[i][i] = s * id[i];
-            } else {
-                L[i][j] = s * id[j];
-            }
-        }
-    }
-    auto solve = [&](const float (&r)[n], float (&x)[n]) {
-        float t[n];
-#pragma unroll
-        for (int i = 0; i < n; ++i) {
-            float s = r[i];
-#pragma unroll
-            for (int k = 0; k < i; ++k) s -= L[i][k] * t[k];
-            t[i] = s * id[i];
-        }
-#pragma unroll
-        for (int i = n - 1; i >= 0; --i) {
-            float s = t[i];
-#pragma unroll
-            for (int k = i + 1; k < n; ++k) s -= L[k][i] * x[k];
-            x[i] = s * id[i];
-        }
-    };
-    float rf[n], x0[n], dx[n];
-#pragma unroll
-    for (int i = 0; i < n; ++i) rf[i] = (float)rhs[i];
-    solve(rf, x0);
-#pragma unroll
-    for (int i = 0; i < n; ++i) {
-        double r = rhs[i];
-#pragma unroll
-        for (int j = 0; j < n; ++j)
-            r -= packed[i <= j ? Gram<D>::idx(i, j) : Gram<D>::idx(j, i)] * (double)x0[j];
-        rf[i] = (float)r;
-    }
-    solve(rf, dx);
-#pragma unroll
-    for (int i = 0; i < n; ++i) b[i] = (double)x0[i] + (double)dx[i];
-    return true;
-}
-
 // ---- float-float (unevaluated sum hi + lo) arithmetic, for sums and
 // residuals that need about twice FP32 precision without FP64 instructions.
 // two_sum is Knuth's error-free addition; the product error uses one FMA.
@@ -463,14 +380,26 @@ __device__ __forceinline__ float2 ff_sub_mul(float2 a, float2 g, float x) {
     return two_sum(s.x, s.y + a.y - pe - g.y * x);
 }
 
-// Solve of float-float normal equations (packed upper triangle) with an FP32
-// Cholesky factor of the leading parts and one step of iterative refinement
-// whose residual rhs - G x0 is taken in float-float.  For the Legendre Gram
-// matrices of Eq. 6 this matches a double-precision solve of the same sums.
-template <int D>
-__device__ __forceinline__ bool chol_solve_ff(const float2* packed, const float2* rhs, float* b) {
+// Solve of float-float normal equations (packed upper triangle) for NR
+// right-hand sides by one warp (all 32 lanes call it; NR (D+1) <= 64): an
+// FP32 Cholesky factor of the leading parts and one step of iterative
+// refinement whose residual rhs - G x0 is taken in float-float.  For the
+// Legendre Gram matrices of Eq. 6 this matches a double-precision solve of
+// the same sums.  Every lane factors the leading parts in
+// FP32 (the same work as one thread, so no extra latency); lane l < NR solves
+// for right-hand side l; the float-float residual rows are spread over the
+// lanes (row i of system l on lane l (D+1) + i, and 32 further), so the
+// refinement costs one row instead of NR (D+1) rows of serial float-float
+// work.  Lane l < NR returns system l's solution in b; returns false (in every
+// lane) when a pivot is not positive.
+template <int D, int NR>
+__device__ __forceinline__ bool warp_chol_solve_ff(const float2* packed, const float2* const (&rhs)[NR],
+                                                   float (&b)[D + 1]) {
     constexpr int n = D + 1;
+    static_assert(NR * n <= 64, "two residual rows per lane at most");
+    const int lane = threadIdx.x & 31;
     float L[n][n], id[n];
+    bool ok = true;
 #pragma unroll
     for (int i = 0; i < n; ++i) {
 #pragma unroll
@@ -479,14 +408,15 @@ __device__ __forceinline__ bool chol_solve_ff(const float2* packed, const float2
 #pragma unroll
             for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
             if (i == j) {
-                if (!(s > 0.0f)) return false;
-                id[i] = rsqrt_refined(s);
+                ok = ok && s > 0.0f;
+                id[i] = rsqrt_refined(s > 0.0f ? s : 1.0f);
                 L[i][i] = s * id[i];
             } else {
                 L[i][j] = s * id[j];
             }
         }
     }
+    if (!ok) return false;
     auto solve = [&](const float (&r)[n], float (&x)[n]) {
         float t[n];
 #pragma unroll
@@ -504,17 +434,45 @@ __device__ __forceinline__ bool chol_solve_ff(const float2* packed, const float2
             x[i] = s * id[i];
         }
     };
-    float rf[n], x0[n], dx[n];
-#pragma unroll
-    for (int i = 0; i < n; ++i) rf[i] = rhs[i].x + rhs[i].y;
-    solve(rf, x0);
+    const int me = lane < NR ? lane : 0;          // right-hand side of this lane
+    float rf[n], x0[n];
 #pragma unroll
     for (int i = 0; i < n; ++i) {
-        float2 r = rhs[i];
+        float2 v = make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int j = 0; j < n; ++j) r = ff_sub_mul(r, packed[i <= j ? Gram<D>::idx(i, j) : Gram<D>::idx(j, i)], x0[j]);
-        rf[i] = r.x + r.y;
+        for (int l = 0; l < NR; ++l)
+            if (l == me) v = rhs[l][i];
+        rf[i] = v.x + v.y;
     }
+    solve(rf, x0);
+    // residual rows: pair q = lane (+32): system q / n, row q % n
+    float res[2] = {0.0f, 0.0f};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int q = lane + 32 * h;
+        const int l = q / n, i = q - (q / n) * n;
+        float xl[n];
+#pragma unroll
+        for (int j = 0; j < n; ++j) xl[j] = __shfl_sync(0xffffffffu, x0[j], l < NR ? l : 0);
+        if (q < NR * n) {
+            float2 r = make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int m = 0; m < NR; ++m)
+                if (m == l) r = rhs[m][i];
+#pragma unroll
+            for (int j = 0; j < n; ++j) r = ff_sub_mul(r, packed[i <= j ? Gram<D>::idx(i, j) : Gram<D>::idx(j, i)], xl[j]);
+            res[h] = r.x + r.y;
+        }
+    }
+    // gather system me's residual rows: row i sits on lane (me n + i) mod 32, half (me n + i) / 32
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        const int q = me * n + i;
+        const float r0 = __shfl_sync(0xffffffffu, res[0], q & 31);
+        const float r1 = __shfl_sync(0xffffffffu, res[1], q & 31);
+        rf[i] = q < 32 ? r0 : r1;
+    }
+    float dx[n];
     solve(rf, dx);
 #pragma unroll
     for (int i = 0; i < n; ++i) b[i] = x0[i] + dx[i];

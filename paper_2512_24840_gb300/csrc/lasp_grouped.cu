@@ -434,11 +434,13 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) k2_rest(const Grp G, in
     if (G.O.fp64_ne) {
         float2* outff = reinterpret_cast<float2*>(outd);
         reduce_to_warp0_ff<NV, NT>(gacc, red, outff);
-        if (tid == 0) {
+        if (warp == 0) {
+            const float2* const rh[1] = {outff + Gm::NG};
             float bf[NB];
-            const bool ok = chol_solve_ff<D>(outff, outff + Gm::NG, bf);
+            const bool ok = warp_chol_solve_ff<D, 1>(outff, rh, bf);
+            if (lane == 0)
 #pragma unroll
-            for (int a = 0; a < NB; ++a) s_b[a] = ok ? bf[a] : NAN;
+                for (int a = 0; a < NB; ++a) s_b[a] = ok ? bf[a] : NAN;
         }
     } else {
         reduce_to_warp0<NV, NT>(gacc, red, out);

@@ -134,10 +134,14 @@ __device__ void lm_eval(const ModelDev& M, const float* th, const float* y, cons
     block_sum_ff<NV, NT>(gacc, red, outff);
     if (tid < NV) s_G[tid] = outff[tid];
     __syncthreads();
-    if (tid == 0) {
+    if (warp == 0) {
+        const float2* const rh[1] = {s_G + Gm::NG};
         float bd[NB];
-        *s_ok = chol_solve_ff<D>(s_G, s_G + Gm::NG, bd) ? 1 : 0;
-        for (int a = 0; a < NB; ++a) s_b[a] = bd[a];
+        const bool ok = warp_chol_solve_ff<D, 1>(s_G, rh, bd);
+        if (lane == 0) {
+            *s_ok = ok ? 1 : 0;
+            for (int a = 0; a < NB; ++a) s_b[a] = bd[a];
+        }
     }
     __syncthreads();
     if (!*s_ok) return;
@@ -192,10 +196,12 @@ __device__ void lm_eval(const ModelDev& M, const float* th, const float* y, cons
             }
         }
         block_sum_ff<NT2, NT>(tacc, red, outff);
-        if (tid < 5) {
+        if (warp == 0) {
+            const float2* const rh[5] = {outff, outff + NB, outff + 2 * NB, outff + 3 * NB, outff + 4 * NB};
             float dbk[NB];
-            chol_solve_ff<D>(s_G, outff + tid * NB, dbk);
-            for (int a = 0; a < NB; ++a) s_db[tid * NB + a] = dbk[a];
+            warp_chol_solve_ff<D, 5>(s_G, rh, dbk);
+            if (lane < 5)
+                for (int a = 0; a < NB; ++a) s_db[lane * NB + a] = dbk[a];
         }
         if (tid == 0) s_sum[0] = outff[5 * NB];
         __syncthreads();
