@@ -39,7 +39,7 @@ FP32_LANES_PER_SM, N_SM = 128, 152
 # DRAM bytes of one fit_kernel<256,6> launch on this workload, from one ncu
 # capture of the current kernel source (reset to None whenever the kernel
 # changes until it is captured again).
-FIT_TRAFFIC_BYTES = None
+FIT_TRAFFIC_BYTES = 152_982_784
 
 
 def parse():
@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the 65536-spectra mixed-precision run")
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the mixed-precision, curvature-aware and piecewise entries")
     ap.add_argument("--no-served", action="store_true")
@@ -350,6 +352,55 @@ def run_ours(args):
                            "precision": prec + "+fp64_normal_eq",
                            "within_tol_of_fp32_fit_frac": float(agree.mean())}
 
+    # ---- mixed precision at the large configuration: 65536 LAMOST-like spectra,
+    # split-TF32 contractions + float-float normal equations; parameter error
+    # against the FP64 oracle on a sample of the batch
+    mixed_large = {}
+    if not args.no_mixed and not args.no_large:
+        _, n_big, off, kw = S.workload("mixed65536")
+        db = S.draw_batch(grid, n_big, S.SPECTRA_SEED + off + 1000 * rank, **kw)
+        bmodel = torch.empty((n_big, grid.n_pix), device=dev)
+        for c0 in range(0, n_big, 8192):
+            bmodel[c0:c0 + 8192] = ip.forward(
+                torch.tensor(db["truth"][c0:c0 + 8192], dtype=torch.float32, device=dev),
+                torch.tensor(db["b_true"][c0:c0 + 8192], dtype=torch.float32, device=dev))
+        bf, bv = S.finish_obs(bmodel.double().cpu().numpy(), db)
+        del bmodel
+        bin_ = [torch.tensor(bf, device=dev), torch.tensor(bv, device=dev),
+                torch.tensor(db["good"], device=dev),
+                torch.tensor(db["theta0"], dtype=torch.float32, device=dev)]
+        mo = dict(opts, precision="tf32x3", fp64_normal_eq=1)
+        bout = ip.fit(*bin_, **mo)
+        torch.cuda.synchronize()
+        t_ms = []
+        for k in range(max(1, min(args.steps, 2))):
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            bout = ip.fit(*bin_, out=bout, **mo)
+            b.record(stream)
+            torch.cuda.synchronize()
+            t_ms.append(a.elapsed_time(b))
+        bst = bout["status"].cpu().numpy()
+        bconv = int(((bst & 3) != 0).sum())
+        sample = np.arange(0, n_big, n_big // 64)[:64]
+        within = None
+        if not args.no_cpu_baseline:
+            from oracle import oracle as O
+            M = O.Model(C, S.EXPS, grid.dln, grid.pad, grid.n_pix, DEG, S.BASIS_LO, S.BASIS_HI,
+                        S.BOX_LO, S.BOX_HI)
+            th0 = np.asarray(db["theta0"][sample], np.float32).astype(np.float64)
+            ref = O.fit(M, bf[sample], bv[sample], db["good"][sample], th0,
+                        threads=O.lib().orc_max_threads(), max_steps=MAX_STEPS)
+            err = np.abs(bout["theta"].double().cpu().numpy()[sample] - ref["theta"])[:, :4]
+            within = float(np.all(err <= np.array([1.0, 0.005, 0.005, 0.1]), axis=1).mean())
+        mixed_large = {"value": bconv / (sum(t_ms) / len(t_ms) / 1e3), "unit": UNIT,
+                       "fit_ms": sum(t_ms) / len(t_ms), "converged": bconv, "n_spectra": n_big,
+                       "precision": "tf32x3+float-float normal equations",
+                       "within_tol_of_oracle_frac": within,
+                       "oracle_sample": f"{len(sample)} spectra (every {n_big // 64}th), FP64 oracle fit"}
+        del bin_, bout
+
     # ---- curvature-aware step (Levenberg-Marquardt, the paper's outlook): same batch
     lm = {}
     if not args.no_mixed:
@@ -430,6 +481,8 @@ def run_ours(args):
         "detail": {"fit_ms": fit_avg, "errors_ms": sum(err_ms) / len(err_ms),
                    "converged": conv, "n_spectra": N_SPEC,
                    "mean_steps": float(steps_np.mean()),
+                   "steps_p50_p90_p99_max": [float(np.percentile(steps_np, q)) for q in (50, 90, 99)]
+                                            + [int(steps_np.max())],
                    "spectrum_steps_per_s": float((steps_np + 1).sum() / (fit_avg / 1e3))},
         "roofline": {"kernel": "fit_kernel<256,6>", "bound": "alu", "achieved": achieved,
                      "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
@@ -440,6 +493,7 @@ def run_ours(args):
                                      "fit_kernel<256,6> launch on this workload (ncu)"},
         "clocks": clocks,
         "mixed": mixed,
+        "mixed_65536": mixed_large,
         "lm": lm,
         "piecewise": piecewise,
     }

@@ -173,6 +173,12 @@ __device__ __forceinline__ void basis_term(const ModelDev& M, int k, const float
     }
 }
 
+// Row k's basis term and its three derivatives in registers (single-regime
+// tables; used where rows are spread over lanes and no shared array is kept).
+__device__ __forceinline__ float basis_term_1r(const ModelDev& M, int k, const float th[3], float (&d)[3]) {
+    return monomial(M.rblo[0], M.rbscale[0], M.exps + 3 * k, th, d);
+}
+
 // Every row's basis term, spread over the lanes of one warp.
 __device__ __forceinline__ void warp_basis(const ModelDev& M, const float th[3], float* phi,
                                            float* dphi) {

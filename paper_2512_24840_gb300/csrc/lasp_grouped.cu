@@ -11,6 +11,8 @@
 // cores with the table shared by 128 spectra, and converged spectra leave the
 // active list at once.  Steps are replayed from CUDA graphs of 8 steps.
 #include <cuda_bf16.h>
+#include <cmath>
+#include <vector>
 
 #include "lasp_fit.cuh"
 #include "lasp_tc.cuh"
@@ -39,6 +41,9 @@ struct Grp {
     int* list[2];
     int* count;                   // count[0], count[1]
     float* Fp;                    // N x ldf
+    float* taps;                  // N x 3 x TAPBUF: g, dg/dmu, dg/dsigma of the spectrum's next step
+    int* hh;                      // N: kernel half width of those taps
+    const float2* bct;            // per step t: (lr / (1 - beta1^t), sqrt(1 - beta2^t)), from FP64
     float *Y, *Wt;                // N x ldp: y = flux / w and W of section 3.3 step 2 (0 beyond p)
     int ldp;                      // row stride of Y and Wt: n_pix rounded up to 16
     uint8_t *A_hi, *A_lo;         // K3 A images: nblk x nch x 16 KB
@@ -72,6 +77,19 @@ __global__ void __launch_bounds__(NT) k0_prep(const Grp G) {
     for (int j = threadIdx.x; j < G.ldp; j += NT) {
         G.Y[(size_t)i * G.ldp + j] = j < p ? y[j] : 0.0f;
         G.Wt[(size_t)i * G.ldp + j] = j < p ? W[j] : 0.0f;
+    }
+    if (threadIdx.x < 32) {
+        // kernel taps of the first step (x0), for K2
+        float th[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const float xx = (G.theta0[5 * i + k] - G.M.plo[k]) / G.M.phalf[k] - 1.0f;
+            th[k] = phys_of(G.M, k, fminf(1.0f, fmaxf(-1.0f, xx)));
+        }
+        float* tp = G.taps + (size_t)i * 3 * TAPBUF;
+        const int h = kernel_taps_warp(th[3] / G.M.kms_px, th[4] / G.M.kms_px, G.M.pad, tp, tp + TAPBUF,
+                                       tp + 2 * TAPBUF);
+        if (threadIdx.x == 0) G.hh[i] = h;
     }
     if (threadIdx.x == 0) {
         G.w[i] = w;
@@ -346,18 +364,14 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) k2_rest(const Grp G, in
         ldg8(ws, wa);
         ldg8(ws + 8, wb);
     }
-    // kernel taps (warp 0) while the loads are in flight
-    if (warp == 0) {
-        float th[5];
-#pragma unroll
-        for (int k = 0; k < 5; ++k) th[k] = phys_of(M, k, G.x[5 * id + k]);
-        for (int q = 2 * H + 1 + lane; q < TAPBUF; q += 32) {
-            g[q] = 0.0f;
-            gmu[q] = 0.0f;
-            gsg[q] = 0.0f;
+    // kernel taps of this step (written by K0 or the previous K4), zero past 2H
+    {
+        const float* tp = G.taps + (size_t)id * 3 * TAPBUF;
+        for (int q = tid; q < 3 * TAPBUF; q += NT) {
+            const int c = q / TAPBUF, s0 = q - c * TAPBUF;
+            g[c * TAPBUF + s0] = s0 <= 2 * H ? tp[q] : 0.0f;
         }
-        const int h = kernel_taps_warp(th[3] / M.kms_px, th[4] / M.kms_px, H, g, gmu, gsg);
-        if (lane == 0) s_h = h;
+        if (tid == 0) s_h = G.hh[id];
     }
     // zero only the pads of F' (model pixels [-16, 0) and [nm, nm + 16)) and of
     // the delta buffer (j outside [0, p)); the interiors are overwritten
@@ -698,19 +712,30 @@ __global__ void __launch_bounds__(256) k4_adam(const Grp G, int par) {
     if (pos >= G.count[par]) return;
     const int id = G.list[par][pos];
     const ModelDev& M = G.M;
-    float th[5];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) th[k] = phys_of(M, k, G.x[5 * id + k]);
-    float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f;
+    // loads first: parameter k's Adam state on lane k, the basis adjoint sums on lane k < K
+    float xk = 0.0f, mk = 0.0f, vk = 0.0f, gp = 0.0f;
+    if (lane < 5) {
+        xk = G.x[5 * id + lane];
+        mk = G.m[5 * id + lane];
+        vk = G.v[5 * id + lane];
+    }
     if (lane < M.K) {
-        float phi[KMAX], dphi[DPS * KMAX];
-        basis_term(M, lane, th, phi, dphi);
-        float gp = 0.0f;
 #pragma unroll
         for (int q = 0; q < KSPLIT; ++q) gp += G.dphi[((size_t)q * G.nblk * 128 + pos) * 32 + lane];
-        c0 = gp * dphi[DPS * lane + 0];
-        c1 = gp * dphi[DPS * lane + 1];
-        c2 = gp * dphi[DPS * lane + 2];
+    }
+    const float l = G.loss[id];
+    const int flags = G.flags[id];
+    const int t = G.t[id];
+    float th[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) th[k] = phys_of(M, k, __shfl_sync(0xffffffffu, xk, k));
+    float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f;
+    if (lane < M.K) {
+        float d[3];
+        basis_term_1r(M, lane, th, d);
+        c0 = gp * d[0];
+        c1 = gp * d[1];
+        c2 = gp * d[2];
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -718,65 +743,67 @@ __global__ void __launch_bounds__(256) k4_adam(const Grp G, int par) {
         c1 += __shfl_xor_sync(0xffffffffu, c1, o);
         c2 += __shfl_xor_sync(0xffffffffu, c2, o);
     }
-    if (lane != 0) return;
     const int p = M.n_pix;
-    const float l = G.loss[id];
-    const int flags = G.flags[id];
     const float kappa = l > 0.0f ? -1.0f / ((float)p * l) : 0.0f;
-    float gx[5];
-    gx[0] = kappa * c0 * M.phalf[0];
-    gx[1] = kappa * c1 * M.phalf[1];
-    gx[2] = kappa * c2 * M.phalf[2];
-    gx[3] = kappa * G.gmu[id] / M.kms_px * M.phalf[3];
-    gx[4] = kappa * G.gsg[id] / M.kms_px * M.phalf[4];
-    const int t = G.t[id];
+    float gk = 0.0f;
+    if (lane < 5) {
+        const float src = lane == 0 ? c0 : lane == 1 ? c1 : lane == 2 ? c2
+                        : (lane == 3 ? G.gmu[id] : G.gsg[id]) / M.kms_px;
+        gk = kappa * src * M.phalf[lane];
+    }
+    const bool fin = __all_sync(0xffffffffu, lane >= 5 || isfinite(gk));
     uint32_t st = 0;
-    if (flags & 2) st = LASP_ST_SINGULAR;
-    else {
-        bool fin = isfinite(l);
-#pragma unroll
-        for (int k = 0; k < 5; ++k) fin = fin && isfinite(gx[k]);
-        if (!fin) st = LASP_ST_NONFINITE;
+    if (lane == 0) {
+        if (flags & 2) st = LASP_ST_SINGULAR;
+        else if (!(fin && isfinite(l))) st = LASP_ST_NONFINITE;
+        if (!st) {
+            const int Wn = G.O.window;
+            float* ring = G.ring + (size_t)id * WINMAX;
+            const int ri = t % Wn;
+            if (t >= Wn && fabsf(l - ring[ri]) < G.O.tol) st = LASP_ST_CONV_TOL;
+            const int rise = (t >= 1 && l > G.prev[id]) ? G.rise[id] + 1 : 0;
+            if (!st && rise >= Wn) st = LASP_ST_CONV_RISE;
+            if (!st && t >= G.O.max_steps) st = LASP_ST_MAXSTEPS;
+            ring[ri] = l;
+            G.prev[id] = l;
+            G.rise[id] = rise;
+        }
+        if (st && st <= LASP_ST_MAXSTEPS && (flags & 1)) st |= LASP_ST_NONPOS;
     }
-    if (!st) {
-        const int Wn = G.O.window;
-        float* ring = G.ring + (size_t)id * WINMAX;
-        if (t >= Wn && fabsf(l - ring[t % Wn]) < G.O.tol) st = LASP_ST_CONV_TOL;
-        int rise = (t >= 1 && l > G.prev[id]) ? G.rise[id] + 1 : 0;
-        if (!st && rise >= Wn) st = LASP_ST_CONV_RISE;
-        if (!st && t >= G.O.max_steps) st = LASP_ST_MAXSTEPS;
-        ring[t % Wn] = l;
-        G.prev[id] = l;
-        G.rise[id] = rise;
-    }
+    st = __shfl_sync(0xffffffffu, st, 0);
     if (st) {
-        if (st <= LASP_ST_MAXSTEPS && (flags & 1)) st |= LASP_ST_NONPOS;
-        for (int k = 0; k < 5; ++k) G.theta[5 * id + k] = th[k];
-        G.loss_out[id] = l;
-        G.steps[id] = t;
-        G.status[id] = st;
-        if (G.weight) G.weight[id] = G.w[id];
-        if (G.cont)
-            for (int a = 0; a < NB; ++a) G.cont[(size_t)id * NB + a] = G.b[(size_t)id * NB + a];
+        if (lane < 5) G.theta[5 * id + lane] = phys_of(M, lane, xk);
+        if (lane == 0) {
+            G.loss_out[id] = l;
+            G.steps[id] = t;
+            G.status[id] = st;
+            if (G.weight) G.weight[id] = G.w[id];
+        }
+        if (G.cont && lane < NB) G.cont[(size_t)id * NB + lane] = G.b[(size_t)id * NB + lane];
         return;
     }
-    const float tt = (float)(t + 1);
-    const float bc1 = 1.0f - powf(G.O.beta1, tt);
-    const float bc2 = 1.0f - powf(G.O.beta2, tt);
-    const float step = G.O.lr / bc1, rbc2 = rsqrtf(bc2);
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        float mk = G.O.beta1 * G.m[5 * id + k] + (1.0f - G.O.beta1) * gx[k];
-        float vk = G.O.beta2 * G.v[5 * id + k] + (1.0f - G.O.beta2) * gx[k] * gx[k];
-        const float denom = sqrtf(vk) * rbc2 + G.O.eps;
-        const float xk = G.x[5 * id + k];
-        G.x[5 * id + k] = fminf(1.0f, fmaxf(-1.0f, xk - step * mk / denom));
-        G.m[5 * id + k] = mk;
-        G.v[5 * id + k] = vk;
+    // Adam (bias corrections from the FP64 table), parameter k on lane k
+    const float2 bc = G.bct[t + 1];
+    if (lane < 5) {
+        mk = G.O.beta1 * mk + (1.0f - G.O.beta1) * gk;
+        vk = G.O.beta2 * vk + (1.0f - G.O.beta2) * gk * gk;
+        const float denom = sqrtf(vk) / bc.y + G.O.eps;
+        xk = fminf(1.0f, fmaxf(-1.0f, xk - bc.x * mk / denom));
+        G.x[5 * id + lane] = xk;
+        G.m[5 * id + lane] = mk;
+        G.v[5 * id + lane] = vk;
     }
-    G.t[id] = t + 1;
-    const int slot = atomicAdd(&G.count[par ^ 1], 1);
-    G.list[par ^ 1][slot] = id;
+    if (lane == 0) {
+        G.t[id] = t + 1;
+        const int slot = atomicAdd(&G.count[par ^ 1], 1);
+        G.list[par ^ 1][slot] = id;
+    }
+    // kernel taps of the next step, for K2
+    const float mu = phys_of(M, 3, __shfl_sync(0xffffffffu, xk, 3)) / M.kms_px;
+    const float sg = phys_of(M, 4, __shfl_sync(0xffffffffu, xk, 4)) / M.kms_px;
+    float* tp = G.taps + (size_t)id * 3 * TAPBUF;
+    const int h = kernel_taps_warp(mu, sg, M.pad, tp, tp + TAPBUF, tp + 2 * TAPBUF);
+    if (lane == 0) G.hh[id] = h;
 }
 
 template <typename T>
@@ -898,6 +925,21 @@ int lasp_tc_fit_batch(const ModelDev& M, const TcImages& tc, const lasp_batch* b
     A(&G.gsg, n * 4); A(&G.b, n * NB * 4); A(&G.rise, n * 4); A(&G.t, n * 4); A(&G.flags, n * 4);
     A(&G.list[0], n * 4); A(&G.list[1], n * 4); A(&G.count, 16);
     A(&G.Fp, n * G.ldf * 4);
+    A(&G.taps, n * 3 * TAPBUF * 4);
+    A(&G.hh, n * 4);
+    float2* bct = nullptr;
+    A(&bct, ((size_t)o->max_steps + 2) * sizeof(float2));
+    if (!e) {
+        // bias corrections per step, in double as PyTorch's Adam takes them
+        std::vector<float2> hb((size_t)o->max_steps + 2);
+        for (size_t t = 0; t < hb.size(); ++t) {
+            const double b1t = std::pow((double)o->beta1, (double)t), b2t = std::pow((double)o->beta2, (double)t);
+            hb[t] = make_float2(t ? (float)((double)o->lr / (1.0 - b1t)) : 0.0f, t ? (float)std::sqrt(1.0 - b2t) : 1.0f);
+        }
+        e = cuda_rc(cudaMemcpyAsync(bct, hb.data(), hb.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
+        if (!e) e = cuda_rc(cudaStreamSynchronize(st));
+    }
+    G.bct = bct;
     A(&G.Y, n * G.ldp * 4);
     A(&G.Wt, n * G.ldp * 4);
     A(&G.A_hi, (size_t)G.nblk * G.nch * TC_TILE_BYTES);
@@ -921,7 +963,8 @@ int lasp_tc_fit_batch(const ModelDev& M, const TcImages& tc, const lasp_batch* b
         else e = LASP_EINVAL;
     }
     void* ptrs[] = {G.x, G.m, G.v, G.ring, G.prev, G.w, G.imean, G.loss, G.gmu, G.gsg, G.b, G.rise,
-                    G.t, G.flags, G.list[0], G.list[1], G.count, G.Fp, G.Y, G.Wt, G.A_hi, G.A_lo, G.dphi};
+                    G.t, G.flags, G.list[0], G.list[1], G.count, G.Fp, G.Y, G.Wt, G.A_hi, G.A_lo, G.dphi,
+                    G.taps, G.hh, bct};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, st);
     return e;
