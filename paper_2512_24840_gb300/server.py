@@ -12,6 +12,8 @@ lanes' work overlaps on the GPU.  One scheduler tick, per lane:
   3. copy the slots' status and results back and retire the finished ones,
      freeing their slots for the next tick.
 
+Submission copies a request into the lane's pinned ring at once, on the
+caller's thread, so admission is a host-to-device copy of ring ranges.
 A fit split into chunks performs exactly the arithmetic of a one-shot
 lasp_fit_batch, so a served result is bitwise the one the same spectrum gets
 alone.  Latency is measured from submit() to the tick that returns the
@@ -39,6 +41,7 @@ class Request:
     good: np.ndarray
     theta0: np.ndarray
     t_submit: float = 0.0
+    staged: int = -1          # index in the pool's pinned ring (-1: not staged)
 
 
 @dataclass
@@ -58,9 +61,14 @@ class Result:
 
 
 class DevicePool:
-    """A lasp_slots pool on the current CUDA device with pinned staging."""
+    """A lasp_slots pool on the current CUDA device with pinned staging.
 
-    def __init__(self, interp, n_slots: int, stream=None, **opts):
+    Requests are copied into a pinned ring when they are submitted (on the
+    submitting thread, off the scheduler's path); admission then copies
+    contiguous ring ranges to the device.  A request that finds the ring full
+    stays in host memory and is staged at admission instead."""
+
+    def __init__(self, interp, n_slots: int, stream=None, ring: int | None = None, **opts):
         import torch
         from . import lasp
         self._lasp = lasp
@@ -91,6 +99,19 @@ class DevicePool:
         self.o_loss = pin((n_slots,), torch.float32)
         self.o_steps = pin((n_slots,), torch.int32)
         self.o_status = pin((n_slots,), torch.int32)
+        # numpy views of the pinned buffers
+        self.n_flux, self.n_ivar = self.h_flux.numpy(), self.h_ivar.numpy()
+        self.n_good, self.n_th0, self.n_idx = self.h_good.numpy(), self.h_th0.numpy(), self.h_idx.numpy()
+        # submission ring: entries [released, staged) are in use
+        self.ring = int(ring if ring is not None else n_slots)
+        self.r_flux = pin((self.ring, self.n_pix), torch.float32)
+        self.r_ivar = pin((self.ring, self.n_pix), torch.float32)
+        self.r_good = pin((self.ring, self.n_pix), torch.uint8)
+        self.r_th0 = pin((self.ring, 5), torch.float32)
+        self.rn = (self.r_flux.numpy(), self.r_ivar.numpy(), self.r_good.numpy(), self.r_th0.numpy())
+        self.staged = 0         # next ring index to fill
+        self.released = 0       # ring entries before this may be overwritten
+        self._admitted_to = 0   # ring entries admitted (released after the next wait)
         import torch.cuda
         self.event = torch.cuda.Event()
 
@@ -98,20 +119,58 @@ class DevicePool:
     def bytes_per_slot(n_pix: int, deg: int = 6) -> int:
         return 2 * 9 * n_pix + 4 * (3 * 5 + 64 + 6 + 5 + 5 + deg + 1) + 8
 
-    def admit(self, slots: list[int], reqs: list[Request]):
-        c = len(slots)
-        for r, (s, q) in enumerate(zip(slots, reqs)):
-            self.h_idx[r] = s
-            self.h_flux[r].numpy()[:] = q.flux
-            self.h_ivar[r].numpy()[:] = q.ivar
-            self.h_good[r].numpy()[:] = q.good
-            self.h_th0[r].numpy()[:] = q.theta0
+    def stage(self, flux, ivar, good, theta0) -> int:
+        """Copy one request into the ring (caller serialises calls); returns
+        its ring index, or -1 when the ring is full."""
+        if self.staged - self.released >= self.ring:
+            return -1
+        k = self.staged % self.ring
+        self.rn[0][k] = flux
+        self.rn[1][k] = ivar
+        self.rn[2][k] = good
+        self.rn[3][k] = theta0
+        self.staged += 1
+        return self.staged - 1
+
+    def _admit_rows(self, c, idx_off, flux, ivar, good, th0):
         st = ct.c_void_p(self.stream.cuda_stream)
-        rc = self.lib.lasp_slots_admit(self._h, c, self.h_idx.data_ptr(), self.h_flux.data_ptr(),
-                                       self.h_ivar.data_ptr(), self.h_good.data_ptr(),
-                                       self.h_th0.data_ptr(), st)
+        rc = self.lib.lasp_slots_admit(self._h, c, self.h_idx.data_ptr() + 4 * idx_off, flux, ivar, good,
+                                       th0, st)
         if rc:
             raise self._lasp.LaspError(rc, "lasp_slots_admit")
+
+    def admit(self, slots: list[int], reqs: list[Request]):
+        c = len(slots)
+        ring = [(s, q.staged) for s, q in zip(slots, reqs) if q.staged >= 0]
+        rest = [(s, q) for s, q in zip(slots, reqs) if q.staged < 0]
+        off = 0
+        if ring:
+            # staged requests are admitted in staging order: one run of ring
+            # indices, at most two contiguous ranges
+            n = len(ring)
+            self.n_idx[:n] = [s for s, _ in ring]
+            first = ring[0][1]
+            assert ring[-1][1] == first + n - 1
+            done = 0
+            while done < n:
+                k = (first + done) % self.ring
+                m = min(n - done, self.ring - k)
+                self._admit_rows(m, done, self.r_flux[k].data_ptr(), self.r_ivar[k].data_ptr(),
+                                 self.r_good[k].data_ptr(), self.r_th0[k].data_ptr())
+                done += m
+            self._admitted_to = first + n
+            off = n
+        if rest:
+            # unstaged requests: one stacked copy per array into the staging rows
+            n = len(rest)
+            self.n_idx[off:off + n] = [s for s, _ in rest]
+            np.stack([q.flux for _, q in rest], out=self.n_flux[:n])
+            np.stack([q.ivar for _, q in rest], out=self.n_ivar[:n])
+            np.stack([q.good for _, q in rest], out=self.n_good[:n])
+            np.stack([q.theta0 for _, q in rest], out=self.n_th0[:n])
+            self._admit_rows(n, off, self.h_flux.data_ptr(), self.h_ivar.data_ptr(),
+                             self.h_good.data_ptr(), self.h_th0.data_ptr())
+        assert off + len(rest) == c
 
     def step(self, budget: int):
         rc = self.lib.lasp_slots_step(self._h, int(budget), ct.c_void_p(self.stream.cuda_stream))
@@ -128,6 +187,7 @@ class DevicePool:
 
     def wait(self):
         self.event.synchronize()
+        self.released = self._admitted_to      # their host-to-device copies are done
         return (self.o_status.numpy(), self.o_theta.numpy(), self.o_loss.numpy(),
                 self.o_steps.numpy())
 
@@ -173,8 +233,11 @@ class Server:
         with self._lock:
             rid = self._next
             self._next += 1
-            self.lanes[lane].waiting.append(
-                Request(rid, lane, flux, ivar, good, theta0, t_submit=self.clock()))
+            ln = self.lanes[lane]
+            stage = getattr(ln.pool, "stage", None)
+            k = stage(flux, ivar, good, theta0) if stage is not None else -1
+            keep = (None, None, None, None) if k >= 0 else (flux, ivar, good, theta0)
+            ln.waiting.append(Request(rid, lane, *keep, t_submit=self.clock(), staged=k))
         return rid
 
     def pending(self) -> int:
@@ -201,7 +264,8 @@ class Server:
         for lane in active:
             status, theta, loss, steps = lane.pool.wait()
             now = self.clock()
-            for s in [s for s in lane.busy if status[s] != RUNNING]:
+            busy = np.fromiter(lane.busy.keys(), dtype=np.int64, count=len(lane.busy))
+            for s in busy[status[busy] != RUNNING].tolist():
                 q = lane.busy.pop(s)
                 lane.free.append(s)
                 out.append(Result(q.rid, lane.name, theta[s].copy(), float(loss[s]),
