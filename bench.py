@@ -145,14 +145,15 @@ def aggregate(dist, torch, device, ms, conv):
     return float(t.item()), int(c.item())
 
 
-def served_stream(torch, lasp, grids, tables, seconds=2.0, loads=(0.5, 0.8, 0.95), burst=6144):
+def served_stream(torch, lasp, grids, tables, seconds=2.0, loads=(0.5, 0.8, 0.95), burst=6144,
+                  native=True):
     """Continuous batching of a LAMOST-like / DESI-like request mix (50/50,
     random masks 0-20%, SNR 5-100).  The saturated rate is the drain rate of
     a burst; then Poisson arrivals at fractions of it for `seconds` each.
     Latency: submit -> result on host."""
     import threading
     from paper_2512_24840_gb300.server import Server, latency_percentiles
-    from paper_2512_24840_gb300.server import DevicePool
+    from paper_2512_24840_gb300.server import DevicePool, NativeServer
     ips = {g.name: lasp.Interp.from_grid(g, tables[g.name], S.EXPS, S.BASIS_LO, S.BASIS_HI,
                                          S.BOX_LO, S.BOX_HI) for g in grids}
     pool = {}
@@ -164,7 +165,8 @@ def served_stream(torch, lasp, grids, tables, seconds=2.0, loads=(0.5, 0.8, 0.95
         flux, ivar = S.finish_obs(model.double().cpu().numpy(), d)
         pool[g.name] = (flux, ivar, d["good"], np.asarray(d["theta0"], np.float32))
     budget = 2 * burst * max(DevicePool.bytes_per_slot(g.n_pix) for g in grids)
-    srv = Server.on_device(ips, hbm_budget_bytes=budget, chunk=25, max_steps=MAX_STEPS)
+    cls = NativeServer if native else Server
+    srv = cls.on_device(ips, hbm_budget_bytes=budget, chunk=25, max_steps=MAX_STEPS)
     names = [g.name for g in grids]
     rng = np.random.default_rng(7)
 
@@ -210,9 +212,10 @@ def served_stream(torch, lasp, grids, tables, seconds=2.0, loads=(0.5, 0.8, 0.95
         conv = sum(1 for r in done if r.status & 3)
         levels.append({"load": load, "offered_per_s": rate, "served_per_s": len(done) / elapsed,
                        "converged_per_s": conv / elapsed, "n": len(done), **latency_percentiles(done)})
+    slots = srv.slots
     srv.close()
-    return {"saturated_per_s": sat, "chunk_steps": 25, "lanes": names,
-            "slots": {n: l.pool.n_slots for n, l in srv.lanes.items()}, "levels": levels}
+    return {"scheduler": "native (lasp_server_*)" if native else "python (server.Server over lasp_slots_*)",
+            "saturated_per_s": sat, "chunk_steps": 25, "lanes": names, "slots": slots, "levels": levels}
 
 
 def make_inputs(rank, torch, lasp, grid, C):
@@ -498,8 +501,9 @@ def run_ours(args):
         "piecewise": piecewise,
     }
     if rank == 0 and not args.no_served:
-        res["served"] = served_stream(torch, lasp, [S.LAMOST, S.DESI],
-                                      {S.LAMOST.name: C, S.DESI.name: S.make_table(S.DESI)})
+        tabs = {S.LAMOST.name: C, S.DESI.name: S.make_table(S.DESI)}
+        res["served"] = served_stream(torch, lasp, [S.LAMOST, S.DESI], tabs, native=True)
+        res["served_python"] = served_stream(torch, lasp, [S.LAMOST, S.DESI], tabs, native=False)
     if rank == 0 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(args.cpu_sample, grid, C, ip, torch)
     if rank == 0:

@@ -43,6 +43,7 @@ extern "C" {
 #define LASP_ETIMEOUT (-4)   /* a bounded device wait gave up                  */
 #define LASP_EGRID    (-5)   /* grid/table mismatch: pad too small for the box */
 #define LASP_ENODEV   (-6)   /* no usable sm_103 device                        */
+#define LASP_EBUSY    (-7)   /* a server ring is full: retry after a tick      */
 
 /* ---- per-spectrum status bits (lasp_result.status) ---- */
 #define LASP_ST_CONV_TOL   1u   /* |l_t - l_{t-window}| < tol (stage 8 rule 2)        */
@@ -234,11 +235,64 @@ int lasp_slots_step(lasp_slots s, int budget, void* stream);
 int lasp_slots_fetch(lasp_slots s, float* theta, float* loss, int32_t* steps, uint32_t* status,
                      float* weight, void* stream);
 
+/* ---- continuous-batching server: a native scheduler over slot pools ----
+ * One lane per interpolator (one wavelength grid): a slot pool, a CUDA stream
+ * and a pinned submission ring of `ring` requests.  lasp_server_submit copies
+ * one request (host arrays) into its lane's ring and may be called from any
+ * thread, also while another thread is inside lasp_server_tick.
+ * lasp_server_tick runs one scheduling round: on every lane it admits waiting
+ * requests (FIFO) into free slots, runs at most `chunk` Adam steps on the
+ * running slots (the lanes' streams overlap on the GPU), fetches status and
+ * results, waits for its lanes, and moves the finished fits to the result
+ * queue, freeing their slots.  Call tick from one thread at a time.
+ * lasp_server_poll pops up to `max` finished results.  A fit split into
+ * chunks does exactly the arithmetic of a one-shot lasp_fit_batch, so a
+ * served result is bitwise the one the same spectrum gets alone.  Times are
+ * steady-clock nanoseconds (submit and the end of the retiring tick).  The
+ * paper fits fixed groups; this request loop has no counterpart there. */
+typedef struct lasp_server_s* lasp_server;   /* opaque, library-owned */
+
+typedef struct {
+    int64_t tag;            /* the caller's tag given to lasp_server_submit */
+    int lane;
+    float theta[5];         /* physical parameters                       */
+    float loss;
+    int32_t steps;
+    uint32_t status;        /* LASP_ST_* */
+    int64_t t_submit_ns, t_done_ns;
+} lasp_served;
+
+/* n_lanes (1..8) lanes: interps[l] (handles stay owned by the caller and must
+ * outlive the server), n_slots[l] >= 1 slots and ring[l] >= 1 pinned request
+ * entries each; opts and chunk (>= 1 Adam steps per tick) apply to every
+ * lane.  Synchronous.  Errors: LASP_EINVAL, LASP_ENOMEM, LASP_ECUDA. */
+int lasp_server_create(int n_lanes, const lasp_interp* interps, const int* n_slots, const int* ring,
+                       const lasp_fit_opts* opts, int chunk, lasp_server* out);
+void lasp_server_destroy(lasp_server s);
+
+/* Copy one request into lane `lane`'s ring: flux, ivar (n_pix float32), good
+ * (n_pix uint8), theta0 (5 float32 physical), all host memory that may be
+ * reused on return.  `tag` is returned with the result.  LASP_EBUSY when the
+ * ring is full (nothing is copied). */
+int lasp_server_submit(lasp_server s, int lane, const float* flux, const float* ivar,
+                       const uint8_t* good, const float* theta0, int64_t tag);
+
+/* One scheduling round (see above); *n_finished (may be NULL) receives the
+ * number of fits retired in it.  Blocks until the round's GPU work is done. */
+int lasp_server_tick(lasp_server s, int* n_finished);
+
+/* Pop up to max finished results into out (host); *n receives the count. */
+int lasp_server_poll(lasp_server s, lasp_served* out, int max, int* n);
+
+/* Requests submitted and not yet retired (waiting in rings or running). */
+int lasp_server_pending(lasp_server s, int64_t* n);
+
 /* Stage 9 parameter uncertainties at theta (device, N x 5 physical, e.g. the
  * fitted values): Jacobian J of the weighted residual sqrt(W) eps w.r.t. the
  * physical parameters with the continuum re-solved (variable projection),
  * cov = (r.r / (n - 5)) (J^T J)^{-1} with n the used pixels; J^T J is
- * accumulated and inverted in FP64.  sigma: device N x 5 = sqrt(diag cov).
+ * summed in float-float and inverted by an FP32 Cholesky inverse refined with
+ * a float-float residual (about double precision without FP64 instructions).  sigma: device N x 5 = sqrt(diag cov).
  * cov: device N x 25 FP64 or NULL.  status: device N or NULL (LASP_ST_*). */
 int lasp_errors(lasp_interp h, const lasp_batch* batch, const lasp_fit_opts* opts,
                 const float* theta, float* sigma, double* cov, uint32_t* status,

@@ -455,6 +455,11 @@ struct lasp_slots_s {
     uint32_t* status;
 };
 
+namespace lasp {
+int slots_n_pix(lasp_slots s) { return s ? s->h->M.n_pix : 0; }
+}  // namespace lasp
+
+
 extern "C" {
 
 void lasp_slots_free(lasp_slots s) {

@@ -17,7 +17,7 @@ import torch
 
 from . import _build
 
-OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EGRID, ENODEV = 0, -1, -2, -3, -4, -5, -6
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EGRID, ENODEV, EBUSY = 0, -1, -2, -3, -4, -5, -6, -7
 ST_CONV_TOL, ST_CONV_RISE, ST_MAXSTEPS, ST_NONPOS = 1, 2, 4, 8
 ST_NONFINITE, ST_SINGULAR, ST_NODATA, ST_RUNNING = 16, 32, 64, 128
 PREC = {"fp32": 0, "tf32": 1, "bf16": 2, "tf32x3": 3}
@@ -72,7 +72,8 @@ EXPORTS = ["lasp_init_interp", "lasp_free_interp", "lasp_default_opts", "lasp_fi
            "lasp_last_launches", "lasp_strerror", "lasp_version", "lasp_resample_linear",
            "lasp_slots_create", "lasp_slots_free", "lasp_slots_admit", "lasp_slots_step",
            "lasp_slots_fetch", "lasp_interp_eval_static", "lasp_clean_mask",
-           "lasp_init_interp_piecewise"]
+           "lasp_init_interp_piecewise", "lasp_server_create", "lasp_server_destroy",
+           "lasp_server_submit", "lasp_server_tick", "lasp_server_poll", "lasp_server_pending"]
 
 
 def library_path() -> str:
@@ -94,6 +95,17 @@ def load(build: bool = False):
         lib.lasp_init_interp.restype = I
         lib.lasp_init_interp_piecewise.argtypes = [P, P, P]
         lib.lasp_init_interp_piecewise.restype = I
+        lib.lasp_server_create.argtypes = [I, P, P, P, P, I, P]
+        lib.lasp_server_create.restype = I
+        lib.lasp_server_destroy.argtypes = [P]
+        lib.lasp_server_submit.argtypes = [P, I, P, P, P, P, ct.c_int64]
+        lib.lasp_server_submit.restype = I
+        lib.lasp_server_tick.argtypes = [P, P]
+        lib.lasp_server_tick.restype = I
+        lib.lasp_server_poll.argtypes = [P, P, I, P]
+        lib.lasp_server_poll.restype = I
+        lib.lasp_server_pending.argtypes = [P, P]
+        lib.lasp_server_pending.restype = I
         lib.lasp_free_interp.argtypes = [P]
         lib.lasp_default_opts.argtypes = [P]
         lib.lasp_fit_batch.argtypes = [P, P, P, P, P]

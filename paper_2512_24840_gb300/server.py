@@ -244,6 +244,10 @@ class Server:
         with self._lock:
             return sum(len(l.waiting) + len(l.busy) for l in self.lanes.values())
 
+    @property
+    def slots(self) -> dict:
+        return {n: l.pool.n_slots for n, l in self.lanes.items()}
+
     def tick(self) -> list[Result]:
         """Admit, step and retire once on every lane; returns finished results."""
         active = []
@@ -290,3 +294,128 @@ class Server:
 def latency_percentiles(results, q=(50, 99)):
     lat = np.array([r.latency for r in results])
     return {f"p{int(x)}_ms": float(np.percentile(lat, x) * 1e3) for x in q} if len(lat) else {}
+
+
+class _Served(ct.Structure):
+    _fields_ = [("tag", ct.c_int64), ("lane", ct.c_int), ("theta", ct.c_float * 5), ("loss", ct.c_float),
+                ("steps", ct.c_int32), ("status", ct.c_uint32), ("t_submit_ns", ct.c_int64),
+                ("t_done_ns", ct.c_int64)]
+
+
+class NativeServer:
+    """The same request loop run by the library's native scheduler
+    (lasp_server_*): submission copies into a pinned ring in C, one tick
+    admits, steps, fetches and retires every lane without Python per-slot
+    work.  Same interface as Server; times are the scheduler's steady clock."""
+
+    def __init__(self, interps: dict, n_slots: dict, chunk: int = 25, ring: dict | None = None, **opts):
+        from . import lasp
+        self._lasp = lasp
+        self.lib = lasp.load()
+        self.names = list(interps)
+        self.n_pix = {k: interps[k].n_pix for k in self.names}
+        self.n_slots = {k: int(n_slots[k]) for k in self.names}
+        self._interps = interps                     # the handles must outlive the server
+        n = len(self.names)
+        hs = (ct.c_void_p * n)(*[interps[k]._h.value for k in self.names])
+        sl = (ct.c_int * n)(*[self.n_slots[k] for k in self.names])
+        rg = (ct.c_int * n)(*[int((ring or self.n_slots)[k]) for k in self.names])
+        self._opts = lasp.default_opts(**opts)
+        h = ct.c_void_p()
+        rc = self.lib.lasp_server_create(n, hs, sl, rg, ct.byref(self._opts), int(chunk), ct.byref(h))
+        if rc:
+            raise lasp.LaspError(rc, "lasp_server_create")
+        self._h = h
+        self._buf = (_Served * 4096)()
+        self._lock = threading.Lock()
+        self._overflow = collections.deque()        # requests that found their ring full
+        self._next = 0                              # request ids (passed to the library as tags)
+        self.done: list[Result] = []
+
+    @classmethod
+    def on_device(cls, interps: dict, hbm_budget_bytes: int, chunk: int = 25, **opts):
+        share = hbm_budget_bytes // max(1, len(interps))
+        slots = {k: max(1, share // DevicePool.bytes_per_slot(ip.n_pix, opts.get("legendre_deg", 6)))
+                 for k, ip in interps.items()}
+        return cls(interps, slots, chunk=chunk, **opts)
+
+    def _submit_now(self, li, rid, a):
+        return self.lib.lasp_server_submit(self._h, li, a[0].ctypes.data, a[1].ctypes.data, a[2].ctypes.data,
+                                           a[3].ctypes.data, rid)
+
+    def submit(self, lane: str, flux, ivar, good, theta0) -> int:
+        li = self.names.index(lane)
+        a = (np.ascontiguousarray(flux, np.float32), np.ascontiguousarray(ivar, np.float32),
+             np.ascontiguousarray(good, np.uint8), np.ascontiguousarray(theta0, np.float32))
+        with self._lock:
+            rid = self._next
+            self._next += 1
+            queued = bool(self._overflow)
+            if queued:
+                self._overflow.append((rid, li, a))
+        if queued:
+            return rid
+        # the library copy runs without the Python lock (ctypes drops the GIL)
+        rc = self._submit_now(li, rid, a)
+        if rc == self._lasp.EBUSY:
+            with self._lock:
+                self._overflow.append((rid, li, a))     # handed to the ring at a later tick
+        elif rc:
+            raise self._lasp.LaspError(rc, "lasp_server_submit")
+        return rid
+
+    @property
+    def slots(self) -> dict:
+        return dict(self.n_slots)
+
+    def pending(self) -> int:
+        n = ct.c_int64()
+        self.lib.lasp_server_pending(self._h, ct.byref(n))
+        with self._lock:
+            return int(n.value) + len(self._overflow)
+
+    def tick(self) -> list[Result]:
+        with self._lock:
+            while self._overflow:
+                rid, li, a = self._overflow[0]
+                rc = self._submit_now(li, rid, a)
+                if rc == self._lasp.EBUSY:
+                    break
+                if rc:
+                    raise self._lasp.LaspError(rc, "lasp_server_submit")
+                self._overflow.popleft()
+        nf = ct.c_int()
+        rc = self.lib.lasp_server_tick(self._h, ct.byref(nf))
+        if rc:
+            raise self._lasp.LaspError(rc, "lasp_server_tick")
+        out = []
+        while True:
+            got = ct.c_int()
+            self.lib.lasp_server_poll(self._h, self._buf, len(self._buf), ct.byref(got))
+            for r in self._buf[:got.value]:
+                out.append(Result(int(r.tag), self.names[r.lane], np.array(r.theta[:], np.float32),
+                                  float(r.loss), int(r.steps), int(r.status), r.t_submit_ns * 1e-9,
+                                  r.t_done_ns * 1e-9))
+            if got.value < len(self._buf):
+                break
+        self.done.extend(out)
+        return out
+
+    def run_until_idle(self, max_ticks: int = 100000) -> list[Result]:
+        res = []
+        for _ in range(max_ticks):
+            if not self.pending():
+                break
+            res += self.tick()
+        return res
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            self.lib.lasp_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -22,16 +22,24 @@ def _observed(grid, n, seed):
     return flux, ivar, d["good"], th0
 
 
-def test_served_equals_alone():
+@pytest.mark.parametrize("kind", ["python", "native", "native_small_ring"])
+def test_served_equals_alone(kind):
+    """The Python scheduler over slot pools and the library's native scheduler
+    (lasp_server_*; with a ring smaller than the arrivals its overflow path
+    and LASP_EBUSY are exercised too)."""
     from paper_2512_24840_gb300 import lasp
-    from paper_2512_24840_gb300.server import DevicePool, Server
+    from paper_2512_24840_gb300.server import DevicePool, NativeServer, Server
     lasp.load(build=True)
     ips = {g.name: lasp.Interp.from_grid(g, table(g.name), S.EXPS, S.BASIS_LO, S.BASIS_HI,
                                          S.BOX_LO, S.BOX_HI) for g in (S.LAMOST, S.DESI)}
     data = {"lamost": _observed(S.LAMOST, 40, 61), "desi": _observed(S.DESI, 24, 62)}
-    pools = {"lamost": DevicePool(ips["lamost"], 16, max_steps=400),
-             "desi": DevicePool(ips["desi"], 8, max_steps=400)}
-    srv = Server(pools, chunk=7)
+    if kind == "python":
+        pools = {"lamost": DevicePool(ips["lamost"], 16, max_steps=400),
+                 "desi": DevicePool(ips["desi"], 8, max_steps=400)}
+        srv = Server(pools, chunk=7)
+    else:
+        ring = {"lamost": 3, "desi": 2} if kind == "native_small_ring" else None
+        srv = NativeServer(ips, {"lamost": 16, "desi": 8}, chunk=7, ring=ring, max_steps=400)
     rids = {}
     order = [("lamost", i) for i in range(40)] + [("desi", i) for i in range(24)]
     np.random.default_rng(3).shuffle(order)
@@ -56,4 +64,7 @@ def test_served_equals_alone():
             got = results[rid]
             assert np.array_equal(got.theta, one["theta"][0].cpu().numpy()), (lane, i)
             assert got.steps == int(one["steps"][0]) and got.status == int(one["status"][0])
+    assert srv.pending() == 0
+    lat = np.array([r.latency for r in results.values()])
+    assert np.all(lat > 0)
     srv.close()
