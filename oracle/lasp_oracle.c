@@ -494,6 +494,85 @@ void orc_fit(const orc_model* M, const orc_opts* O, int n, const float* flux, co
     }
 }
 
+void orc_fit_joint(const orc_model* M, const orc_opts* O, int n, const float* flux, const float* ivar,
+                   const unsigned char* good, const double* theta0, double* theta, double* loss,
+                   int* steps, unsigned* status, double* loss_group, int threads) {
+    int p = M->n_pix, D = M->deg;
+    double* y = malloc(sizeof(double) * (size_t)n * p);
+    double* W = malloc(sizeof(double) * (size_t)n * p);
+    double* x = calloc((size_t)n * 5, sizeof(double));
+    double* m = calloc((size_t)n * 5, sizeof(double));
+    double* v = calloc((size_t)n * 5, sizeof(double));
+    double* g = calloc((size_t)n * 5, sizeof(double));
+    double* l = calloc((size_t)n, sizeof(double));
+    unsigned* st = calloc((size_t)n, sizeof(unsigned));
+    int* active = calloc((size_t)n, sizeof(int));
+    double* hist = malloc(sizeof(double) * (O->max_steps + 1));
+    *loss_group = NAN;
+    for (int i = 0; i < n; ++i) {
+        double w;
+        int n_obj = orc_prep(p, flux + (size_t)i * p, ivar + (size_t)i * p, good + (size_t)i * p,
+                             O->quantile, O->edge_px, y + (size_t)i * p, W + (size_t)i * p, &w);
+        for (int k = 0; k < 5; ++k) theta[5 * i + k] = theta0[5 * i + k];
+        loss[i] = NAN;
+        steps[i] = 0;
+        status[i] = 0;
+        if (n_obj < D + 1 + 5 || !(w > 0.0) || !isfinite(w)) {
+            status[i] = ORC_ST_NODATA;
+            continue;
+        }
+        orc_x_from_phys(M, theta0 + 5 * i, x + 5 * i);
+        for (int k = 0; k < 5; ++k) x[5 * i + k] = x[5 * i + k] < -1.0 ? -1.0 : (x[5 * i + k] > 1.0 ? 1.0 : x[5 * i + k]);
+        active[i] = 1;
+    }
+    for (int t = 0;; ++t) {
+#pragma omp parallel for schedule(dynamic, 4) num_threads(threads > 0 ? threads : 1)
+        for (int i = 0; i < n; ++i)
+            if (active[i])
+                st[i] = orc_eval(M, y + (size_t)i * p, W + (size_t)i * p, x + 5 * i, l + i, g + 5 * i, NULL,
+                                 NULL, NULL);
+        int na = 0;
+        double ssum = 0.0;
+        for (int i = 0; i < n; ++i) {
+            if (!active[i]) continue;
+            if (st[i] & (ORC_ST_SINGULAR | ORC_ST_NONFINITE)) {
+                status[i] = st[i];
+                loss[i] = l[i];
+                steps[i] = t;
+                orc_phys_from_x(M, x + 5 * i, theta + 5 * i);
+                active[i] = 0;
+                continue;
+            }
+            ++na;
+            ssum += (double)p * l[i] * l[i];
+        }
+        if (na == 0) break;
+        const double L = sqrt(ssum / ((double)na * p));
+        hist[t] = L;
+        unsigned stop = orc_stop_rule(hist, t, O->window, O->tol, O->max_steps);
+        if (stop) {
+            for (int i = 0; i < n; ++i) {
+                if (!active[i]) continue;
+                status[i] = stop | (st[i] & ORC_ST_NONPOS);
+                loss[i] = l[i];
+                steps[i] = t;
+                orc_phys_from_x(M, x + 5 * i, theta + 5 * i);
+            }
+            *loss_group = L;
+            break;
+        }
+        for (int i = 0; i < n; ++i) {
+            if (!active[i]) continue;
+            double gj[5];
+            const double c = l[i] / ((double)na * L);
+            for (int k = 0; k < 5; ++k) gj[k] = c * g[5 * i + k];
+            orc_adam_update(5, x + 5 * i, m + 5 * i, v + 5 * i, gj, t + 1, O->lr, O->beta1, O->beta2,
+                            O->eps, 1);
+        }
+    }
+    free(y); free(W); free(x); free(m); free(v); free(g); free(l); free(st); free(active); free(hist);
+}
+
 void orc_fit_trajectory(const orc_model* M, const orc_opts* O, const float* flux,
                         const float* ivar, const unsigned char* good, const double* theta0,
                         int nsteps, double* x_traj, double* loss_traj) {

@@ -112,6 +112,21 @@ void orc_fit(const orc_model* M, const orc_opts* O, int n, const float* flux,
              double* theta, double* loss, int* steps, unsigned* status, double* b,
              int threads);
 
+/* PAPER_JOINT reading of Eq. 9 (kept for comparison with the separable
+ * default): one RMS over the group, L = sqrt(sum_i S_i / (N p)) with S_i =
+ * sum_j W_ij eps_ij^2 over the N spectra still in the group.  Every
+ * spectrum's parameters take Adam steps on dL/dx_i = (l_i / (N L)) dl_i/dx_i
+ * (l_i the spectrum's own loss), and the stop rules run on L for the whole
+ * group: one step count and one stop status for every spectrum that is still
+ * in it.  A spectrum without data, or whose normal equations fail or whose
+ * loss or gradient is not finite, leaves the group with its own status at
+ * that step.  loss[i] = l_i at the stop; *loss_group = L at the stop.  The
+ * spectra are evaluated in parallel, L is summed in index order. */
+void orc_fit_joint(const orc_model* M, const orc_opts* O, int n, const float* flux,
+                   const float* ivar, const unsigned char* good, const double* theta0,
+                   double* theta, double* loss, int* steps, unsigned* status, double* loss_group,
+                   int threads);
+
 /* One spectrum: loss and gradient trajectory for a fixed number of steps with
  * the stop rules off (trajectory parity).  x_traj ((nsteps+1) x 5), loss_traj
  * (nsteps+1). */

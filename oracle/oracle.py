@@ -86,6 +86,7 @@ def lib():
             _lib.orc_clean_mask.restype = ct.c_int
             _lib.orc_fit_lm.argtypes = [P, P, ct.c_int, P, P, P, P, ct.c_int, ct.c_double, P, P, P,
                                         P, ct.c_int]
+            _lib.orc_fit_joint.argtypes = [P, P, ct.c_int, P, P, P, P, P, P, P, P, P, ct.c_int]
         return _lib
 
 
@@ -251,6 +252,25 @@ def fit(M: Model, flux, ivar, good, theta0, threads=None, **opts):
     lib().orc_fit(M.ref, ct.byref(O), n, _p(flux), _p(ivar), _p(good), _p(theta0), _p(theta),
                   _p(loss), _p(steps), _p(status), _p(b), int(threads))
     return dict(theta=theta, loss=loss, steps=steps, status=status, b=b)
+
+
+def fit_joint(M: Model, flux, ivar, good, theta0, threads=None, **opts):
+    """PAPER_JOINT reading of Eq. 9: one RMS over the group, group stop rules."""
+    flux = np.ascontiguousarray(flux, dtype=np.float32)
+    ivar = np.ascontiguousarray(ivar, dtype=np.float32)
+    good = np.ascontiguousarray(good, dtype=np.uint8)
+    theta0 = _f64(theta0)
+    n = flux.shape[0]
+    theta = np.zeros((n, 5))
+    loss = np.zeros(n)
+    steps = np.zeros(n, dtype=np.int32)
+    status = np.zeros(n, dtype=np.uint32)
+    lg = np.zeros(1)
+    th = lib().orc_max_threads() if threads is None else int(threads)
+    O = make_opts(**opts)
+    lib().orc_fit_joint(M.ref, ct.byref(O), n, _p(flux), _p(ivar), _p(good), _p(theta0), _p(theta),
+                        _p(loss), _p(steps), _p(status), _p(lg), th)
+    return dict(theta=theta, loss=loss, steps=steps, status=status, loss_group=float(lg[0]))
 
 
 def trajectory(M: Model, flux, ivar, good, theta0, nsteps, **opts):

@@ -535,3 +535,46 @@ def test_lm_stops_at_a_kkt_point_of_the_box():
         assert np.all(np.abs(g[~(lo | hi)]) < scale), (i, g, x)
         assert np.all(g[lo] > -scale) and np.all(g[hi] < scale), (i, g, x)
     assert on_edge >= 1
+
+
+# ---------------------------------------------------------------- joint loss (PAPER_JOINT)
+
+def test_joint_gradient_is_the_derivative_of_the_group_rms():
+    """The joint step direction (l_i / (N L)) dl_i/dx_i, written out, against
+    central differences of L = sqrt(sum_i p l_i^2 / (N p)) itself."""
+    M, d = observed(G, 3, 26, snr=(20, 40), mask_frac=0.05)
+    ys = [O.prep(d["flux"][i], d["ivar"][i], d["good"][i])[:2] for i in range(3)]
+    xs = [np.clip(O.x_from_phys(M, d["theta0"][i]), -1, 1) for i in range(3)]
+
+    def L(xx):
+        ls = [O.evaluate(M, ys[i][0], ys[i][1], xx[i])["loss"] for i in range(3)]
+        return math.sqrt(sum(M.n_pix * l * l for l in ls) / (3 * M.n_pix)), ls
+
+    L0, ls = L(xs)
+    for i in range(3):
+        gi = O.evaluate(M, ys[i][0], ys[i][1], xs[i])["grad"]
+        joint = ls[i] / (3 * L0) * gi
+        for k in range(5):
+            h = 1e-6
+            xp = [x.copy() for x in xs]
+            xm = [x.copy() for x in xs]
+            xp[i][k] += h
+            xm[i][k] -= h
+            fd = (L(xp)[0] - L(xm)[0]) / (2 * h)
+            assert abs(fd - joint[k]) <= 1e-6 * max(1e-3, abs(joint[k])), (i, k, fd, joint[k])
+
+
+def test_joint_fit_of_one_spectrum_is_the_separable_fit_and_groups_stop_together():
+    M, d = observed(G, 5, 27, snr=(10, 60), mask_frac=0.05)
+    sep = O.fit(M, d["flux"][:1], d["ivar"][:1], d["good"][:1], d["theta0"][:1], max_steps=300)
+    one = O.fit_joint(M, d["flux"][:1], d["ivar"][:1], d["good"][:1], d["theta0"][:1], max_steps=300)
+    assert one["steps"][0] == sep["steps"][0] and one["status"][0] == sep["status"][0]
+    np.testing.assert_allclose(one["theta"], sep["theta"], rtol=0, atol=1e-9 * np.abs(sep["theta"]).max())
+    # a group: one step count and status, L is the RMS of the members' losses
+    d["good"][3] = 0                                   # no data: leaves the group at once
+    grp = O.fit_joint(M, d["flux"], d["ivar"], d["good"], d["theta0"], max_steps=300)
+    assert grp["status"][3] == 64
+    members = [0, 1, 2, 4]
+    assert len(set(grp["steps"][members])) == 1 and len(set(grp["status"][members] & 7)) == 1
+    L = math.sqrt(np.mean(grp["loss"][members] ** 2))
+    assert abs(L - grp["loss_group"]) <= 1e-12 * L
