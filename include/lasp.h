@@ -165,6 +165,7 @@ typedef struct {
     int clean_every;        /* mask update every this many steps (30)   */
     int clean_max;          /* at most this many updates (11)           */
     int optimizer;          /* LASP_OPT_ADAM (stage 8) or LASP_OPT_LM    */
+    int loss_mode;          /* LASP_LOSS_SEPARABLE or LASP_LOSS_JOINT    */
 } lasp_fit_opts;
 
 /* Optimisers.  LASP_OPT_ADAM: the paper's Adam with the three stop rules.
@@ -179,6 +180,18 @@ typedef struct {
  * accepted steps (steps = accepted steps).  FP32 precision only; no Clean. */
 #define LASP_OPT_ADAM 0
 #define LASP_OPT_LM   1
+
+/* Loss modes.  LASP_LOSS_SEPARABLE (default): each spectrum minimises its own
+ * l_i = sqrt(sum_j W eps^2 / p) with its own stop rules, so its result does
+ * not depend on the batch.  LASP_LOSS_JOINT: Eq. 9 read literally, one RMS
+ * over the group L = sqrt(sum_i S_i / (N p)); spectrum i steps on dL/dx_i =
+ * (l_i / (N L)) dl_i/dx_i, and the stop rules run on L: every spectrum still
+ * in the group stops at the same step with the same status (spectra whose
+ * normal equations fail leave the group at that step).  JOINT needs a step
+ * over all spectra at once: it runs on the grouped tensor-core pipeline
+ * (precision != LASP_PREC_FP32, Adam, no Clean), else LASP_EINVAL. */
+#define LASP_LOSS_SEPARABLE 0
+#define LASP_LOSS_JOINT     1
 
 void lasp_default_opts(lasp_fit_opts* o);
 

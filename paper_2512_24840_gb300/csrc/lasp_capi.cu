@@ -77,6 +77,10 @@ int check_opts(const lasp_fit_opts* o, int n_pix) {
     if (o->clean && (o->clean_every < 1 || o->clean_max < 0)) return LASP_EINVAL;
     if (o->optimizer != LASP_OPT_ADAM && o->optimizer != LASP_OPT_LM) return LASP_EINVAL;
     if (o->optimizer == LASP_OPT_LM && (o->precision != LASP_PREC_FP32 || o->clean)) return LASP_EINVAL;
+    if (o->loss_mode != LASP_LOSS_SEPARABLE && o->loss_mode != LASP_LOSS_JOINT) return LASP_EINVAL;
+    if (o->loss_mode == LASP_LOSS_JOINT &&
+        (o->precision == LASP_PREC_FP32 || o->optimizer != LASP_OPT_ADAM || o->clean))
+        return LASP_EINVAL;
     return LASP_OK;
 }
 
@@ -95,6 +99,7 @@ FitOpts to_dev(const lasp_fit_opts* o) {
     d.clean = o->clean ? 1 : 0;
     d.clean_every = o->clean_every;
     d.clean_max = o->clean_max;
+    d.joint = o->loss_mode == LASP_LOSS_JOINT ? 1 : 0;
     return d;
 }
 
@@ -143,6 +148,7 @@ void lasp_default_opts(lasp_fit_opts* o) {
     o->clean_every = 30;
     o->clean_max = 11;
     o->optimizer = LASP_OPT_ADAM;
+    o->loss_mode = LASP_LOSS_SEPARABLE;
 }
 
 int lasp_init_interp_piecewise(const lasp_piecewise_desc* d, const float* coeff, lasp_interp* out) {

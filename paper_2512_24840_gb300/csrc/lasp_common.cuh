@@ -45,6 +45,7 @@ struct FitOpts {
     float quantile;
     int fp64_ne;
     int clean, clean_every, clean_max;
+    int joint;               // group RMS loss (grouped pipeline only)
 };
 
 // Skewed rows in shared memory: element i at i + i/16, so that the
@@ -376,6 +377,12 @@ __device__ __forceinline__ float2 two_sum(float a, float b) {
 __device__ __forceinline__ float2 ff_add(float2 a, float b) {
     const float2 s = two_sum(a.x, b);
     return two_sum(s.x, s.y + a.y);
+}
+
+// a + b for float-float a and b.
+__device__ __forceinline__ float2 ff_add2(float2 a, float2 b) {
+    const float2 s = two_sum(a.x, b.x);
+    return two_sum(s.x, s.y + (a.y + b.y));
 }
 
 // a - g x for float-float a and g, float x.

@@ -29,6 +29,19 @@ constexpr int K3_STAGES = 4;
 constexpr int CHUNK_STEPS = 8;     // steps per captured graph (even)
 constexpr int KSPLIT = 4;          // K3: pixel ranges per 128-spectrum block
 
+// Group state of the joint loss (LASP_LOSS_JOINT): the group RMS L of the
+// current step, its member count, the group stop status and the stop-rule
+// history, updated once per step by K3j.
+struct GroupState {
+    float L;
+    int n_act;
+    uint32_t status;
+    int step;
+    float prev;
+    int rise;
+    float ring[WINMAX];
+};
+
 struct Grp {
     ModelDev M;
     FitOpts O;
@@ -44,6 +57,10 @@ struct Grp {
     float* taps;                  // N x 3 x TAPBUF: g, dg/dmu, dg/dsigma of the spectrum's next step
     int* hh;                      // N: kernel half width of those taps
     const float2* bct;            // per step t: (lr / (1 - beta1^t), sqrt(1 - beta2^t)), from FP64
+    // joint loss: S_i of the step (K2), the step it belongs to, the group state (K3j)
+    float* Sstep;
+    int* act;
+    GroupState* gs;
     float *Y, *Wt;                // N x ldp: y = flux / w and W of section 3.3 step 2 (0 beyond p)
     int ldp;                      // row stride of Y and Wt: n_pix rounded up to 16
     uint8_t *A_hi, *A_lo;         // K3 A images: nblk x nch x 16 KB
@@ -555,6 +572,63 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) k2_rest(const Grp G, in
         for (int a = 0; a < NB; ++a) G.b[(size_t)id * NB + a] = s_b[a];
         G.gmu[id] = out[2];
         G.gsg[id] = out[3];
+        if (G.O.joint) {
+            G.Sstep[id] = out[0];
+            G.act[id] = G.t[id];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- K3j group loss
+// Joint loss: L = sqrt(sum_i S_i / (N p)) over the spectra stepped this step
+// with a finite S_i, summed in float-float in a fixed order (deterministic),
+// and the stop rules on L.  One CTA.
+template <int NTJ>
+__global__ void __launch_bounds__(NTJ) k3j_group(const Grp G) {
+    __shared__ float2 s_acc[NTJ];
+    __shared__ int s_cnt[NTJ];
+    GroupState* gs = G.gs;
+    const int step = gs->step;
+    const int tid = threadIdx.x;
+    float2 acc = make_float2(0.0f, 0.0f);
+    int cnt = 0;
+    for (int id = tid; id < G.N; id += NTJ) {
+        if (G.act[id] != step) continue;
+        const float S = G.Sstep[id];
+        if (isfinite(S)) {
+            acc = ff_add(acc, S);
+            ++cnt;
+        }
+    }
+    s_acc[tid] = acc;
+    s_cnt[tid] = cnt;
+    __syncthreads();
+    for (int off = NTJ / 2; off > 0; off >>= 1) {
+        if (tid < off) {
+            s_acc[tid] = ff_add2(s_acc[tid], s_acc[tid + off]);
+            s_cnt[tid] += s_cnt[tid + off];
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const int n = s_cnt[0];
+        const float L = n > 0 ? sqrtf((s_acc[0].x + s_acc[0].y) / ((float)n * (float)G.M.n_pix)) : NAN;
+        uint32_t st = 0;
+        if (n > 0) {
+            const int Wn = G.O.window;
+            const int ri = step % Wn;
+            if (step >= Wn && fabsf(L - gs->ring[ri]) < G.O.tol) st = LASP_ST_CONV_TOL;
+            const int rise = (step >= 1 && L > gs->prev) ? gs->rise + 1 : 0;
+            if (!st && rise >= Wn) st = LASP_ST_CONV_RISE;
+            if (!st && step >= G.O.max_steps) st = LASP_ST_MAXSTEPS;
+            gs->ring[ri] = L;
+            gs->prev = L;
+            gs->rise = rise;
+        }
+        gs->L = L;
+        gs->n_act = n;
+        gs->status = st;
+        gs->step = step + 1;
     }
 }
 
@@ -756,7 +830,9 @@ __global__ void __launch_bounds__(256) k4_adam(const Grp G, int par) {
     if (lane == 0) {
         if (flags & 2) st = LASP_ST_SINGULAR;
         else if (!(fin && isfinite(l))) st = LASP_ST_NONFINITE;
-        if (!st) {
+        if (!st && G.O.joint) {
+            st = G.gs->status;                   // the group's stop rules (K3j)
+        } else if (!st) {
             const int Wn = G.O.window;
             float* ring = G.ring + (size_t)id * WINMAX;
             const int ri = t % Wn;
@@ -782,8 +858,10 @@ __global__ void __launch_bounds__(256) k4_adam(const Grp G, int par) {
         if (G.cont && lane < NB) G.cont[(size_t)id * NB + lane] = G.b[(size_t)id * NB + lane];
         return;
     }
-    // Adam (bias corrections from the FP64 table), parameter k on lane k
+    // Adam (bias corrections from the FP64 table), parameter k on lane k; the
+    // joint loss scales the gradient by l_i / (N L)
     const float2 bc = G.bct[t + 1];
+    if (G.O.joint) gk *= l / ((float)G.gs->n_act * G.gs->L);
     if (lane < 5) {
         mk = G.O.beta1 * mk + (1.0f - G.O.beta1) * gk;
         vk = G.O.beta2 * vk + (1.0f - G.O.beta2) * gk * gk;
@@ -843,6 +921,7 @@ int run_grouped(Grp& G, const TcImages& tc, cudaStream_t st, int* launches) {
         k1_interp<PREC><<<g1, 128, smem1, st>>>(G, par, img, img_lo, tc.n_tiles);
         k2_rest<NT, D, PREC><<<N, NT, smem2, st>>>(G, par);
         k3_back<PREC><<<g3, 128, smem3, st>>>(G, par, bk, bk_lo);
+        if (G.O.joint) k3j_group<1024><<<1, 1024, 0, st>>>(G);
         k4_adam<D><<<g4, 256, 0, st>>>(G, par);
     };
     // capture CHUNK_STEPS steps (parities 0,1,0,1,...) into one graph
@@ -865,7 +944,7 @@ int run_grouped(Grp& G, const TcImages& tc, cudaStream_t st, int* launches) {
     const int max_chunks = (G.O.max_steps + 1 + CHUNK_STEPS - 1) / CHUNK_STEPS + 1;
     for (int c = 0; !e && c < max_chunks; ++c) {
         e = cuda_rc(cudaGraphLaunch(exec, st));
-        nlaunch += 4 * CHUNK_STEPS;
+        nlaunch += (G.O.joint ? 5 : 4) * CHUNK_STEPS;
         if (!e) e = cuda_rc(cudaMemcpyAsync(&h_count, G.count, sizeof(int), cudaMemcpyDeviceToHost, st));
         if (!e) e = cuda_rc(cudaStreamSynchronize(st));
         if (!e && h_count == 0) break;
@@ -896,6 +975,7 @@ int lasp_tc_fit_batch(const ModelDev& M, const TcImages& tc, const lasp_batch* b
     G.O.edge_px = o->edge_px;
     G.O.quantile = o->quantile;
     G.O.fp64_ne = o->fp64_normal_eq ? 1 : 0;
+    G.O.joint = o->loss_mode == LASP_LOSS_JOINT ? 1 : 0;
     const int N = b->N;
     const int NB = o->legendre_deg + 1;
     G.N = N;
@@ -927,6 +1007,13 @@ int lasp_tc_fit_batch(const ModelDev& M, const TcImages& tc, const lasp_batch* b
     A(&G.Fp, n * G.ldf * 4);
     A(&G.taps, n * 3 * TAPBUF * 4);
     A(&G.hh, n * 4);
+    if (o->loss_mode == LASP_LOSS_JOINT) {
+        A(&G.Sstep, n * 4);
+        A(&G.act, n * 4);
+        A(&G.gs, sizeof(GroupState));
+        if (!e) e = cuda_rc(cudaMemsetAsync(G.act, 0xff, n * 4, st));
+        if (!e) e = cuda_rc(cudaMemsetAsync(G.gs, 0, sizeof(GroupState), st));
+    }
     float2* bct = nullptr;
     A(&bct, ((size_t)o->max_steps + 2) * sizeof(float2));
     if (!e) {
@@ -964,7 +1051,7 @@ int lasp_tc_fit_batch(const ModelDev& M, const TcImages& tc, const lasp_batch* b
     }
     void* ptrs[] = {G.x, G.m, G.v, G.ring, G.prev, G.w, G.imean, G.loss, G.gmu, G.gsg, G.b, G.rise,
                     G.t, G.flags, G.list[0], G.list[1], G.count, G.Fp, G.Y, G.Wt, G.A_hi, G.A_lo, G.dphi,
-                    G.taps, G.hh, bct};
+                    G.taps, G.hh, bct, G.Sstep, G.act, G.gs};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, st);
     return e;

@@ -22,6 +22,7 @@ ST_CONV_TOL, ST_CONV_RISE, ST_MAXSTEPS, ST_NONPOS = 1, 2, 4, 8
 ST_NONFINITE, ST_SINGULAR, ST_NODATA, ST_RUNNING = 16, 32, 64, 128
 PREC = {"fp32": 0, "tf32": 1, "bf16": 2, "tf32x3": 3}
 OPTIMIZER = {"adam": 0, "lm": 1}
+LOSS_MODE = {"separable": 0, "joint": 1}
 
 _lock = threading.Lock()
 _lib = None
@@ -59,7 +60,7 @@ class FitOpts(ct.Structure):
                 ("max_steps", ct.c_int), ("legendre_deg", ct.c_int), ("edge_px", ct.c_int),
                 ("quantile", ct.c_float), ("precision", ct.c_int), ("fp64_normal_eq", ct.c_int),
                 ("clean", ct.c_int), ("clean_every", ct.c_int), ("clean_max", ct.c_int),
-                ("optimizer", ct.c_int)]
+                ("optimizer", ct.c_int), ("loss_mode", ct.c_int)]
 
 
 class Result(ct.Structure):
@@ -166,6 +167,8 @@ def default_opts(**kw) -> FitOpts:
             v = PREC[v]
         if k == "optimizer" and isinstance(v, str):
             v = OPTIMIZER[v]
+        if k == "loss_mode" and isinstance(v, str):
+            v = LOSS_MODE[v]
         if not hasattr(o, k):
             raise TypeError(f"unknown fit option {k}")
         setattr(o, k, v)
