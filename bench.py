@@ -146,7 +146,7 @@ def aggregate(dist, torch, device, ms, conv):
 
 
 def served_stream(torch, lasp, grids, tables, seconds=2.0, loads=(0.5, 0.8, 0.95), burst=6144,
-                  native=True):
+                  native=True, **fit_opts):
     """Continuous batching of a LAMOST-like / DESI-like request mix (50/50,
     random masks 0-20%, SNR 5-100).  The saturated rate is the drain rate of
     a burst; then Poisson arrivals at fractions of it for `seconds` each.
@@ -164,9 +164,10 @@ def served_stream(torch, lasp, grids, tables, seconds=2.0, loads=(0.5, 0.8, 0.95
                                     torch.tensor(d["b_true"], dtype=torch.float32, device=dev))
         flux, ivar = S.finish_obs(model.double().cpu().numpy(), d)
         pool[g.name] = (flux, ivar, d["good"], np.asarray(d["theta0"], np.float32))
-    budget = 2 * burst * max(DevicePool.bytes_per_slot(g.n_pix) for g in grids)
+    prec = fit_opts.get("precision", "fp32")
+    budget = 2 * burst * max(DevicePool.bytes_per_slot(g.n_pix, DEG, prec) for g in grids)
     cls = NativeServer if native else Server
-    srv = cls.on_device(ips, hbm_budget_bytes=budget, chunk=25, max_steps=MAX_STEPS)
+    srv = cls.on_device(ips, hbm_budget_bytes=budget, chunk=25, max_steps=MAX_STEPS, **fit_opts)
     names = [g.name for g in grids]
     rng = np.random.default_rng(7)
 
@@ -215,6 +216,7 @@ def served_stream(torch, lasp, grids, tables, seconds=2.0, loads=(0.5, 0.8, 0.95
     slots = srv.slots
     srv.close()
     return {"scheduler": "native (lasp_server_*)" if native else "python (server.Server over lasp_slots_*)",
+            "precision": prec + ("+float-float normal equations" if fit_opts.get("fp64_normal_eq") else ""),
             "saturated_per_s": sat, "chunk_steps": 25, "lanes": names, "slots": slots, "levels": levels}
 
 
@@ -530,6 +532,8 @@ def run_ours(args):
         tabs = {S.LAMOST.name: C, S.DESI.name: S.make_table(S.DESI)}
         res["served"] = served_stream(torch, lasp, [S.LAMOST, S.DESI], tabs, native=True)
         res["served_python"] = served_stream(torch, lasp, [S.LAMOST, S.DESI], tabs, native=False)
+        res["served_mixed"] = served_stream(torch, lasp, [S.LAMOST, S.DESI], tabs, native=True,
+                                            precision="tf32x3", fp64_normal_eq=1)
     if rank == 0 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(args.cpu_sample, grid, C, ip, torch)
     if rank == 0:

@@ -226,7 +226,12 @@ int lasp_fit_batch(lasp_interp h, const lasp_batch* batch, const lasp_fit_opts* 
 typedef struct lasp_slots_s* lasp_slots;          /* opaque, library-owned */
 
 /* Allocates the pool (device memory ~ n_slots x (9 n_pix + 480) bytes plus a
- * staging copy of the observation buffers).  opts are copied.  Synchronous. */
+ * staging copy of the observation buffers).  opts are copied.  Synchronous.
+ * opts->precision LASP_PREC_FP32: the fused FP32 fit kernel steps the slots.
+ * A tensor-core precision: the grouped pipeline runs over the slots (served
+ * mixed precision; single-regime tables, Legendre degree 6; about 50 n_pix
+ * more bytes per slot); its steps go in chunks of 8, so a step call's budget
+ * is rounded up to a multiple of 8.  Clean and the joint loss: LASP_EINVAL. */
 int lasp_slots_create(lasp_interp h, int n_slots, const lasp_fit_opts* opts, lasp_slots* out);
 void lasp_slots_free(lasp_slots s);
 

@@ -459,6 +459,7 @@ struct lasp_slots_s {
     float *theta, *loss, *cont, *weight;
     int32_t* steps;
     uint32_t* status;
+    lasp::GrpPool* grp = nullptr;   // tensor-core precisions: the grouped pipeline over the slots
 };
 
 namespace lasp {
@@ -470,6 +471,7 @@ extern "C" {
 
 void lasp_slots_free(lasp_slots s) {
     if (!s) return;
+    if (s->grp) grp_pool_free(s->grp);
     void* ptrs[] = {s->flux, s->ivar, s->theta0, s->good, s->f_st, s->iv_st, s->th_st, s->g_st,
                     s->idx_st, s->S.x, s->S.m, s->S.v, s->S.ring, s->S.prev, s->S.rise, s->S.t,
                     s->S.w, s->S.imean, s->theta, s->loss, s->cont, s->weight, s->steps, s->status};
@@ -483,7 +485,8 @@ int lasp_slots_create(lasp_interp h, int n_slots, const lasp_fit_opts* o, lasp_s
     *out = nullptr;
     int rc = check_opts(o, h->M.n_pix);
     if (rc) return rc;
-    if (o->precision != LASP_PREC_FP32 || o->clean) return LASP_EINVAL;
+    if (o->clean || o->loss_mode != LASP_LOSS_SEPARABLE) return LASP_EINVAL;
+    if (o->precision != LASP_PREC_FP32 && (h->M.n_reg > 1 || o->legendre_deg != 6)) return LASP_EINVAL;
     lasp_slots_s* s = new (std::nothrow) lasp_slots_s();
     if (!s) return LASP_ENOMEM;
     s->h = h;
@@ -519,6 +522,9 @@ int lasp_slots_create(lasp_interp h, int n_slots, const lasp_fit_opts* o, lasp_s
     alloc(&s->weight, n * 4);
     alloc(&s->steps, n * 4);
     alloc(&s->status, n * 4);
+    if (!rc && o->precision != LASP_PREC_FP32)
+        rc = grp_pool_create(h->M, h->tc, n_slots, o, s->flux, s->ivar, s->good, s->theta0, s->theta, s->loss,
+                             s->steps, s->status, s->cont, s->weight, &s->grp);
     if (rc) {
         lasp_slots_free(s);
         return rc;
@@ -547,12 +553,18 @@ int lasp_slots_admit(lasp_slots s, int count, const int32_t* slot_idx, const flo
                                                  s->th_st, s->flux, s->ivar, s->good, s->theta0, s->S.t,
                                                  s->status);
     g_last_launches = 1;
-    return cuda_err(cudaGetLastError());
+    rc = cuda_err(cudaGetLastError());
+    if (!rc && s->grp) {
+        rc = grp_pool_admit(s->grp, count, s->idx_st, st);     // prep + join the active list
+        g_last_launches = 2;
+    }
+    return rc;
 }
 
 int lasp_slots_step(lasp_slots s, int budget, void* stream) {
     g_last_launches = 0;
     if (!s || budget < 1) return LASP_EINVAL;
+    if (s->grp) return grp_pool_step(s->grp, budget, (cudaStream_t)stream, &g_last_launches);
     FitParams P{};
     P.M = s->h->M;
     P.O = to_dev(&s->opts);

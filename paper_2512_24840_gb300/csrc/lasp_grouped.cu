@@ -75,10 +75,12 @@ struct Grp {
 };
 
 // ---------------------------------------------------------------- K0 prep
+// One CTA per spectrum: blockIdx.x, or idx[blockIdx.x] for spectra admitted
+// into a persistent pool; spectra with data join the active list of parity 0.
 template <int NT>
-__global__ void __launch_bounds__(NT) k0_prep(const Grp G) {
+__global__ void __launch_bounds__(NT) k0_prep(const Grp G, const int32_t* __restrict__ idx) {
     extern __shared__ __align__(16) float sm[];
-    const int i = blockIdx.x;
+    const int i = idx ? idx[blockIdx.x] : blockIdx.x;
     const int p = G.M.n_pix;
     const int pa = (p + 3) & ~3;
     float* y = sm;
@@ -899,7 +901,7 @@ int run_grouped(Grp& G, const TcImages& tc, cudaStream_t st, int* launches) {
         const size_t smem = 4 * ((size_t)2 * pa + next_pow2(M.n_pix) + (NT / 32) * 4 + 16);
         int e = cuda_rc(cudaFuncSetAttribute(k0_prep<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         if (e) return e;
-        k0_prep<NT><<<N, NT, smem, st>>>(G);
+        k0_prep<NT><<<N, NT, smem, st>>>(G, nullptr);
         if ((e = cuda_rc(cudaGetLastError()))) return e;
     }
     const size_t smem1 = 4 * TC_TILE_BYTES + 1024;
@@ -1055,6 +1057,187 @@ int lasp_tc_fit_batch(const ModelDev& M, const TcImages& tc, const lasp_batch* b
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, st);
     return e;
+}
+
+// ---------------------------------------------------------------------------
+// Persistent grouped pipeline over slots (served mixed precision).  The state
+// of every slot lives in the Grp arrays; admission preps the admitted slots
+// and appends them to the active list of parity 0; a step replays the captured
+// graph of CHUNK_STEPS steps (so a chunk is rounded up to a multiple of it),
+// after which the parity is 0 again.  K4 writes each finished fit's results
+// into the slot outputs.
+
+struct GrpPool {
+    Grp G{};
+    TcImages tc{};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    float2* bct = nullptr;
+    int (*admit)(GrpPool*, int, const int32_t*, cudaStream_t) = nullptr;
+};
+
+namespace {
+
+template <int D, int PREC, int NT>
+int pool_setup(GrpPool* P) {
+    Grp& G = P->G;
+    const ModelDev& M = G.M;
+    const TcImages& tc = P->tc;
+    const int N = G.N;
+    const int pa = (M.n_pix + 3) & ~3;
+    const size_t smem0 = 4 * ((size_t)2 * pa + next_pow2(M.n_pix) + (NT / 32) * 4 + 16);
+    const size_t smem1 = 4 * TC_TILE_BYTES + 1024;
+    const size_t smem3 = K3_STAGES * (2 * TC_TILE_BYTES + 2 * TC_BK_CHUNK_BYTES) + 1024;
+    const RestSmem RS(M.n_pix, M.pad, M.n_model, NT, D);
+    const size_t smem2 = 4 * (size_t)RS.total;
+    int e = cuda_rc(cudaFuncSetAttribute(k0_prep<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem0));
+    if (!e) e = cuda_rc(cudaFuncSetAttribute(k1_interp<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1));
+    if (!e) e = cuda_rc(cudaFuncSetAttribute(k2_rest<NT, D, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
+    if (!e) e = cuda_rc(cudaFuncSetAttribute(k3_back<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3));
+    if (e) return e;
+    P->admit = [](GrpPool* Q, int count, const int32_t* idx, cudaStream_t st) -> int {
+        const int pq = (Q->G.M.n_pix + 3) & ~3;
+        const size_t sm0 = 4 * ((size_t)2 * pq + next_pow2(Q->G.M.n_pix) + (NT / 32) * 4 + 16);
+        k0_prep<NT><<<count, NT, sm0, st>>>(Q->G, idx);
+        return cuda_rc(cudaGetLastError());
+    };
+    const uint8_t* img = (const uint8_t*)(PREC == 2 ? tc.bf16 : tc.tf32_hi);
+    const uint8_t* img_lo = (const uint8_t*)tc.tf32_lo;
+    const uint8_t* bk = (const uint8_t*)(PREC == 2 ? tc.bk_bf : tc.bk_hi);
+    const uint8_t* bk_lo = (const uint8_t*)tc.bk_lo;
+    const dim3 g1((N + 127) / 128, (tc.n_tiles + 3) / 4);
+    const dim3 g3((N + 127) / 128, KSPLIT);
+    const int g4 = (N + 7) / 8;
+    cudaStream_t cap;
+    if ((e = cuda_rc(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)))) return e;
+    e = cuda_rc(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    if (!e) {
+        for (int k = 0; k < CHUNK_STEPS; ++k) {
+            const int par = k & 1;
+            k1_interp<PREC><<<g1, 128, smem1, cap>>>(G, par, img, img_lo, tc.n_tiles);
+            k2_rest<NT, D, PREC><<<N, NT, smem2, cap>>>(G, par);
+            k3_back<PREC><<<g3, 128, smem3, cap>>>(G, par, bk, bk_lo);
+            k4_adam<D><<<g4, 256, 0, cap>>>(G, par);
+        }
+        e = cuda_rc(cudaStreamEndCapture(cap, &P->graph));
+    }
+    if (!e) e = cuda_rc(cudaGraphInstantiate(&P->exec, P->graph, 0));
+    cudaStreamDestroy(cap);
+    return e;
+}
+
+}  // namespace
+
+void grp_pool_free(GrpPool* P) {
+    if (!P) return;
+    if (P->exec) cudaGraphExecDestroy(P->exec);
+    if (P->graph) cudaGraphDestroy(P->graph);
+    Grp& G = P->G;
+    void* ptrs[] = {G.x, G.m, G.v, G.ring, G.prev, G.w, G.imean, G.loss, G.gmu, G.gsg, G.b, G.rise,
+                    G.t, G.flags, G.list[0], G.list[1], G.count, G.Fp, G.Y, G.Wt, G.A_hi, G.A_lo, G.dphi,
+                    G.taps, G.hh, P->bct};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete P;
+}
+
+int grp_pool_create(const ModelDev& M, const TcImages& tc, int n, const lasp_fit_opts* o, float* flux,
+                    float* ivar, uint8_t* good, float* theta0, float* theta, float* loss, int32_t* steps,
+                    uint32_t* status, float* cont, float* weight, GrpPool** out) {
+    *out = nullptr;
+    if (!tc.tf32_hi || !tc.bk_hi || o->legendre_deg != 6) return LASP_EINVAL;
+    GrpPool* P = new (std::nothrow) GrpPool();
+    if (!P) return LASP_ENOMEM;
+    P->tc = tc;
+    Grp& G = P->G;
+    G.M = M;
+    G.O.lr = o->lr;
+    G.O.beta1 = o->beta1;
+    G.O.beta2 = o->beta2;
+    G.O.eps = o->eps;
+    G.O.tol = o->tol;
+    G.O.window = o->window;
+    G.O.max_steps = o->max_steps;
+    G.O.edge_px = o->edge_px;
+    G.O.quantile = o->quantile;
+    G.O.fp64_ne = o->fp64_normal_eq ? 1 : 0;
+    G.N = n;
+    G.NB = o->legendre_deg + 1;
+    G.ldf = (M.n_model + 15) & ~15;
+    G.ldp = (M.n_pix + 15) & ~15;
+    G.nch = o->precision == LASP_PREC_BF16 ? tc.n_chunks_bf16 : tc.n_chunks_tf32;
+    G.nblk = (n + 127) / 128;
+    G.flux = flux;
+    G.ivar = ivar;
+    G.good = good;
+    G.theta0 = theta0;
+    G.theta = theta;
+    G.loss_out = loss;
+    G.steps = steps;
+    G.status = status;
+    G.cont = cont;
+    G.weight = weight;
+    G.err = tc.err;
+    const size_t N = (size_t)n;
+    int e = LASP_OK;
+    auto A = [&](auto** ptr, size_t bytes) {
+        if (!e) e = cuda_rc(cudaMalloc((void**)ptr, bytes));
+        if (!e) e = cuda_rc(cudaMemset(*ptr, 0, bytes));
+    };
+    A(&G.x, N * 20); A(&G.m, N * 20); A(&G.v, N * 20); A(&G.ring, N * WINMAX * 4);
+    A(&G.prev, N * 4); A(&G.w, N * 4); A(&G.imean, N * 4); A(&G.loss, N * 4); A(&G.gmu, N * 4);
+    A(&G.gsg, N * 4); A(&G.b, N * G.NB * 4); A(&G.rise, N * 4); A(&G.t, N * 4); A(&G.flags, N * 4);
+    A(&G.list[0], N * 4); A(&G.list[1], N * 4); A(&G.count, 16);
+    A(&G.Fp, N * G.ldf * 4);
+    A(&G.Y, N * G.ldp * 4);
+    A(&G.Wt, N * G.ldp * 4);
+    A(&G.taps, N * 3 * TAPBUF * 4);
+    A(&G.hh, N * 4);
+    A(&G.A_hi, (size_t)G.nblk * G.nch * TC_TILE_BYTES);
+    if (o->precision == LASP_PREC_TF32X3) A(&G.A_lo, (size_t)G.nblk * G.nch * TC_TILE_BYTES);
+    A(&G.dphi, (size_t)KSPLIT * G.nblk * 128 * 32 * 4);
+    A(&P->bct, ((size_t)o->max_steps + 2) * sizeof(float2));
+    if (!e) {
+        std::vector<float2> hb((size_t)o->max_steps + 2);
+        for (size_t t = 0; t < hb.size(); ++t) {
+            const double b1t = std::pow((double)o->beta1, (double)t), b2t = std::pow((double)o->beta2, (double)t);
+            hb[t] = make_float2(t ? (float)((double)o->lr / (1.0 - b1t)) : 0.0f, t ? (float)std::sqrt(1.0 - b2t) : 1.0f);
+        }
+        e = cuda_rc(cudaMemcpy(P->bct, hb.data(), hb.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    }
+    G.bct = P->bct;
+    if (!e) {
+        const int NT = M.n_pix <= 16 * 256 ? 256 : 512;
+        if (NT == 256) {
+            e = o->precision == LASP_PREC_TF32   ? pool_setup<6, 1, 256>(P)
+                : o->precision == LASP_PREC_BF16 ? pool_setup<6, 2, 256>(P)
+                                                 : pool_setup<6, 3, 256>(P);
+        } else {
+            e = o->precision == LASP_PREC_TF32   ? pool_setup<6, 1, 512>(P)
+                : o->precision == LASP_PREC_BF16 ? pool_setup<6, 2, 512>(P)
+                                                 : pool_setup<6, 3, 512>(P);
+        }
+    }
+    if (e) {
+        grp_pool_free(P);
+        return e;
+    }
+    *out = P;
+    return LASP_OK;
+}
+
+int grp_pool_admit(GrpPool* P, int count, const int32_t* idx_dev, cudaStream_t st) {
+    return count > 0 ? P->admit(P, count, idx_dev, st) : LASP_OK;
+}
+
+int grp_pool_step(GrpPool* P, int budget, cudaStream_t st, int* launches) {
+    const int replays = (budget + CHUNK_STEPS - 1) / CHUNK_STEPS;
+    for (int r = 0; r < replays; ++r) {
+        const int e = cuda_rc(cudaGraphLaunch(P->exec, st));
+        if (e) return e;
+    }
+    *launches = replays * 4 * CHUNK_STEPS;
+    return LASP_OK;
 }
 
 }  // namespace lasp

@@ -38,6 +38,16 @@ void tc_free_images(TcImages& t);
 int lasp_tc_interp_eval(const ModelDev& M, const TcImages& t, int N, const float* theta, float* Fp,
                         int precision, cudaStream_t st, int* launches);
 
+// Persistent grouped pipeline over the slot arrays of a lasp_slots pool
+// (served fits at tensor-core precision); see lasp_grouped.cu.
+struct GrpPool;
+int grp_pool_create(const ModelDev& M, const TcImages& tc, int n, const lasp_fit_opts* o, float* flux,
+                    float* ivar, uint8_t* good, float* theta0, float* theta, float* loss, int32_t* steps,
+                    uint32_t* status, float* cont, float* weight, GrpPool** out);
+int grp_pool_admit(GrpPool* P, int count, const int32_t* idx_dev, cudaStream_t st);
+int grp_pool_step(GrpPool* P, int budget, cudaStream_t st, int* launches);
+void grp_pool_free(GrpPool* P);
+
 int lasp_tc_fit_batch(const ModelDev& M, const TcImages& t, const lasp_batch* b, const lasp_fit_opts* o,
                       lasp_result* r, void* stream, int* launches);
 

@@ -116,8 +116,14 @@ class DevicePool:
         self.event = torch.cuda.Event()
 
     @staticmethod
-    def bytes_per_slot(n_pix: int, deg: int = 6) -> int:
-        return 2 * 9 * n_pix + 4 * (3 * 5 + 64 + 6 + 5 + 5 + deg + 1) + 8
+    def bytes_per_slot(n_pix: int, deg: int = 6, precision="fp32") -> int:
+        """Device bytes of one slot: the observation and its staging copy, the
+        optimiser state; at tensor-core precisions also the grouped pipeline's
+        F', y, W, operand images and taps (about 20 n_pix + 2 KB)."""
+        b = 2 * 9 * n_pix + 4 * (3 * 5 + 64 + 6 + 5 + 5 + deg + 1) + 8
+        if precision not in ("fp32", 0):
+            b += 20 * n_pix + 2048
+        return b
 
     def stage(self, flux, ivar, good, theta0) -> int:
         """Copy one request into the ring (caller serialises calls); returns
@@ -225,7 +231,8 @@ class Server:
         pools = {}
         share = hbm_budget_bytes // max(1, len(interps))
         for name, ip in interps.items():
-            n = max(1, share // DevicePool.bytes_per_slot(ip.n_pix, opts.get("legendre_deg", 6)))
+            n = max(1, share // DevicePool.bytes_per_slot(ip.n_pix, opts.get("legendre_deg", 6),
+                                                          opts.get("precision", "fp32")))
             pools[name] = DevicePool(ip, int(n), **opts)
         return cls(pools, chunk=chunk)
 
@@ -335,7 +342,8 @@ class NativeServer:
     @classmethod
     def on_device(cls, interps: dict, hbm_budget_bytes: int, chunk: int = 25, **opts):
         share = hbm_budget_bytes // max(1, len(interps))
-        slots = {k: max(1, share // DevicePool.bytes_per_slot(ip.n_pix, opts.get("legendre_deg", 6)))
+        slots = {k: max(1, share // DevicePool.bytes_per_slot(ip.n_pix, opts.get("legendre_deg", 6),
+                                                              opts.get("precision", "fp32")))
                  for k, ip in interps.items()}
         return cls(interps, slots, chunk=chunk, **opts)
 

@@ -22,7 +22,8 @@ def _observed(grid, n, seed):
     return flux, ivar, d["good"], th0
 
 
-@pytest.mark.parametrize("kind", ["python", "native", "native_small_ring"])
+@pytest.mark.parametrize("kind", ["python", "native", "native_small_ring", "native_tf32x3",
+                                  "python_tf32x3"])
 def test_served_equals_alone(kind):
     """The Python scheduler over slot pools and the library's native scheduler
     (lasp_server_*; with a ring smaller than the arrivals its overflow path
@@ -33,13 +34,17 @@ def test_served_equals_alone(kind):
     ips = {g.name: lasp.Interp.from_grid(g, table(g.name), S.EXPS, S.BASIS_LO, S.BASIS_HI,
                                          S.BOX_LO, S.BOX_HI) for g in (S.LAMOST, S.DESI)}
     data = {"lamost": _observed(S.LAMOST, 40, 61), "desi": _observed(S.DESI, 24, 62)}
-    if kind == "python":
-        pools = {"lamost": DevicePool(ips["lamost"], 16, max_steps=400),
-                 "desi": DevicePool(ips["desi"], 8, max_steps=400)}
+    # served mixed precision: the grouped tensor-core pipeline runs over the slots
+    fo = dict(max_steps=400)
+    if kind.endswith("tf32x3"):
+        fo.update(precision="tf32x3", fp64_normal_eq=1)
+    if kind.startswith("python"):
+        pools = {"lamost": DevicePool(ips["lamost"], 16, **fo),
+                 "desi": DevicePool(ips["desi"], 8, **fo)}
         srv = Server(pools, chunk=7)
     else:
         ring = {"lamost": 3, "desi": 2} if kind == "native_small_ring" else None
-        srv = NativeServer(ips, {"lamost": 16, "desi": 8}, chunk=7, ring=ring, max_steps=400)
+        srv = NativeServer(ips, {"lamost": 16, "desi": 8}, chunk=7, ring=ring, **fo)
     rids = {}
     order = [("lamost", i) for i in range(40)] + [("desi", i) for i in range(24)]
     np.random.default_rng(3).shuffle(order)
@@ -59,7 +64,7 @@ def test_served_equals_alone(kind):
         for i in range(len(f)):
             one = ips[lane].fit(torch.tensor(f[i:i + 1], device=dev), torch.tensor(iv[i:i + 1], device=dev),
                                 torch.tensor(gd[i:i + 1], device=dev), torch.tensor(th[i:i + 1], device=dev),
-                                max_steps=400)
+                                **fo)
             rid = [r for r, v in rids.items() if v == (lane, i)][0]
             got = results[rid]
             assert np.array_equal(got.theta, one["theta"][0].cpu().numpy()), (lane, i)
