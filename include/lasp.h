@@ -85,7 +85,8 @@ typedef struct lasp_interp_s* lasp_interp;   /* opaque, library-owned */
 /* Upload the interpolator table (Eq. 1) and build its device images.
  * coeff: host, K x n_model float32 row-major (C_k,m).  Builds the FP32 table,
  * the TF32 hi/lo and BF16 tile images used by the tensor-core contraction.
- * Synchronous.  Errors: LASP_EINVAL (bad desc), LASP_EGRID (pad smaller than
+ * Synchronous: returns once the table is on the device, so the handle may be
+ * used on any stream.  Errors: LASP_EINVAL (bad desc), LASP_EGRID (pad smaller than
  * the widest kernel reachable in the box), LASP_ENOMEM, LASP_ECUDA,
  * LASP_ENODEV.  On success *out owns device memory until lasp_free_interp. */
 int lasp_init_interp(const lasp_interp_desc* desc, const float* coeff, lasp_interp* out);
@@ -226,12 +227,17 @@ int lasp_fit_batch(lasp_interp h, const lasp_batch* batch, const lasp_fit_opts* 
 typedef struct lasp_slots_s* lasp_slots;          /* opaque, library-owned */
 
 /* Allocates the pool (device memory ~ n_slots x (9 n_pix + 480) bytes plus a
- * staging copy of the observation buffers).  opts are copied.  Synchronous.
+ * staging copy of the observation buffers).  opts are copied.  Synchronous:
+ * returns once the pool's device memory is initialised, so the first admit
+ * may go on any stream, a non-blocking one included.
  * opts->precision LASP_PREC_FP32: the fused FP32 fit kernel steps the slots.
  * A tensor-core precision: the grouped pipeline runs over the slots (served
  * mixed precision; single-regime tables, Legendre degree 6; about 50 n_pix
  * more bytes per slot); its steps go in chunks of 8, so a step call's budget
- * is rounded up to a multiple of 8.  Clean and the joint loss: LASP_EINVAL. */
+ * is rounded up to a multiple of 8.  Clean (FP32 pools only): each slot keeps
+ * its Clean mask in device memory between steps (n_pix / 8 bytes per slot), so
+ * the updates fall on the same steps as in a one-shot fit.  The joint loss:
+ * LASP_EINVAL. */
 int lasp_slots_create(lasp_interp h, int n_slots, const lasp_fit_opts* opts, lasp_slots* out);
 void lasp_slots_free(lasp_slots s);
 

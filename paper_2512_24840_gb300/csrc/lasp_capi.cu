@@ -222,6 +222,8 @@ int lasp_init_interp_piecewise(const lasp_piecewise_desc* d, const float* coeff,
                                    (size_t)K, cudaMemcpyHostToDevice));
     // tensor-core tile images: single-regime tables of at most one K block
     if (!rc && M.n_reg == 1) rc = tc_build_images(h->tc, h->C, K, M.n_model);
+    // the copies above run on the legacy default stream; finish them before a fit on another stream
+    if (!rc) rc = cuda_err(cudaStreamSynchronize(cudaStreamLegacy));
     if (rc) {
         tc_free_images(h->tc);
         cudaFree(h->C);
@@ -474,7 +476,8 @@ void lasp_slots_free(lasp_slots s) {
     if (s->grp) grp_pool_free(s->grp);
     void* ptrs[] = {s->flux, s->ivar, s->theta0, s->good, s->f_st, s->iv_st, s->th_st, s->g_st,
                     s->idx_st, s->S.x, s->S.m, s->S.v, s->S.ring, s->S.prev, s->S.rise, s->S.t,
-                    s->S.w, s->S.imean, s->theta, s->loss, s->cont, s->weight, s->steps, s->status};
+                    s->S.w, s->S.imean, s->S.cmask, s->theta, s->loss, s->cont, s->weight, s->steps,
+                    s->status};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete s;
@@ -485,8 +488,9 @@ int lasp_slots_create(lasp_interp h, int n_slots, const lasp_fit_opts* o, lasp_s
     *out = nullptr;
     int rc = check_opts(o, h->M.n_pix);
     if (rc) return rc;
-    if (o->clean || o->loss_mode != LASP_LOSS_SEPARABLE) return LASP_EINVAL;
-    if (o->precision != LASP_PREC_FP32 && (h->M.n_reg > 1 || o->legendre_deg != 6)) return LASP_EINVAL;
+    if (o->loss_mode != LASP_LOSS_SEPARABLE) return LASP_EINVAL;
+    if (o->precision != LASP_PREC_FP32 && (h->M.n_reg > 1 || o->legendre_deg != 6 || o->clean))
+        return LASP_EINVAL;
     lasp_slots_s* s = new (std::nothrow) lasp_slots_s();
     if (!s) return LASP_ENOMEM;
     s->h = h;
@@ -516,6 +520,7 @@ int lasp_slots_create(lasp_interp h, int n_slots, const lasp_fit_opts* o, lasp_s
     alloc(&s->S.t, n * 4);
     alloc(&s->S.w, n * 4);
     alloc(&s->S.imean, n * 4);
+    if (o->clean) alloc(&s->S.cmask, n * (size_t)((p + 15) / 16) * 2);
     alloc(&s->theta, n * 5 * 4);
     alloc(&s->loss, n * 4);
     alloc(&s->cont, n * NB * 4);
@@ -525,6 +530,9 @@ int lasp_slots_create(lasp_interp h, int n_slots, const lasp_fit_opts* o, lasp_s
     if (!rc && o->precision != LASP_PREC_FP32)
         rc = grp_pool_create(h->M, h->tc, n_slots, o, s->flux, s->ivar, s->good, s->theta0, s->theta, s->loss,
                              s->steps, s->status, s->cont, s->weight, &s->grp);
+    // the zero fills above are queued on the legacy default stream, which a caller's non-blocking
+    // stream does not wait for: finish them before the pool can be admitted into
+    if (!rc) rc = cuda_err(cudaStreamSynchronize(cudaStreamLegacy));
     if (rc) {
         lasp_slots_free(s);
         return rc;

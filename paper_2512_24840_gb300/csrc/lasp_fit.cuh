@@ -41,6 +41,7 @@ struct SlotState {
     int* t;            // S
     float* w;          // S  (weight, set at the first launch)
     float* imean;      // S  (mean inverse variance)
+    uint16_t* cmask;   // S x ceil(p / 16) zero-weight bits of each thread's 16 pixels (Clean), or nullptr
     int budget;
 };
 
@@ -257,12 +258,15 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) fit_kernel(const FitPar
             tw[r] = j < p ? W[j] : 0.0f;
         }
         __syncthreads();
+        // a resumed Clean fit keeps the pixels its mask updates removed
+        const uint32_t cm = (!fresh && P.S.cmask && tid * PPT < p)
+                                ? P.S.cmask[(size_t)i * ((p + PPT - 1) / PPT) + tid] : 0u;
 #pragma unroll
         for (int r = 0; r < PPT; ++r) {
             const int j = tid * PPT + r;
             if (j < p) {
                 y[skew(j)] = ty[r];
-                W[skew(j)] = tw[r];
+                W[skew(j)] = ((cm >> r) & 1u) ? 0.0f : tw[r];
             }
         }
         if (tid == 0) {
@@ -608,7 +612,9 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) fit_kernel(const FitPar
             }
         }
         __syncthreads();
-        if (s_stop) break;
+        if (s_stop == 1) break;
+        // a chunk that suspends on a Clean step still applies that step's mask update,
+        // as the one-shot fit does
         if (clean_step(P.O, t)) {
             // ---- stage 6 Clean update from the residual at x_t (taps g and F' still of x_t)
             const int upd = t / P.O.clean_every;
@@ -683,9 +689,17 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) fit_kernel(const FitPar
             }
             __syncthreads();
         }
+        if (s_stop) break;
     }
     if (s_stop == 2) {
         for (int q = tid; q < WINMAX; q += NT) P.S.ring[(size_t)i * WINMAX + q] = ring[q];
+        if (P.S.cmask && j0 < p) {
+            uint32_t bits = 0;
+#pragma unroll
+            for (int r = 0; r < PPT; ++r)
+                if (j0 + r < p && W[skew(j0 + r)] == 0.0f) bits |= 1u << r;
+            P.S.cmask[(size_t)i * ((p + PPT - 1) / PPT) + tid] = (uint16_t)bits;
+        }
         return;
     }
     if (P.cont && tid < NB) P.cont[(size_t)i * NB + tid] = s_b[tid];

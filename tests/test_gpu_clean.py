@@ -87,3 +87,32 @@ def test_clean_rejected_where_unsupported():
     with pytest.raises(lasp.LaspError):
         ip.fit(z, z, torch.ones((2, g.n_pix), dtype=torch.uint8, device=DEV),
                torch.zeros((2, 5), device=DEV), precision="tf32", clean=1)
+
+
+@pytest.mark.parametrize("chunk", [7, 31])
+def test_served_clean_equals_one_shot(chunk):
+    """Clean in served fits: each slot keeps its mask between chunks; with
+    chunk 31 a chunk ends exactly on the first mask update (step 30), which
+    still has to be applied before the slot is suspended."""
+    from paper_2512_24840_gb300 import lasp
+    from paper_2512_24840_gb300.server import NativeServer
+    lasp.load(build=True)
+    g = S.SMALL
+    M, d = observed(g, 12, 92, snr=(30, 100), mask_frac=0.0)
+    rng = np.random.default_rng(3)
+    flux = d["flux"].copy()
+    for i in range(12):
+        med = np.median(flux[i])
+        for c in rng.choice(g.n_pix - 8, 8, replace=False):
+            flux[i, c:c + 3] += med * rng.uniform(0.5, 3.0) * np.array([1.0, 0.5, 0.2], np.float32)
+    th0 = np.asarray(d["theta0"], np.float32)
+    ip = lasp.Interp.from_grid(g, table(g.name), S.EXPS, S.BASIS_LO, S.BASIS_HI, S.BOX_LO, S.BOX_HI)
+    T = lambda a, dt=torch.float32: torch.as_tensor(np.ascontiguousarray(a)).to(DEV, dt)
+    one = ip.fit(T(flux), T(d["ivar"]), T(d["good"], torch.uint8), T(th0), max_steps=400, clean=1)
+    srv = NativeServer({"s": ip}, {"s": 5}, chunk=chunk, max_steps=400, clean=1)
+    ids = [srv.submit("s", flux[i], d["ivar"][i], d["good"][i], th0[i]) for i in range(12)]
+    res = {r.rid: r for r in srv.run_until_idle()}
+    srv.close()
+    for k, rid in enumerate(ids):
+        assert np.array_equal(res[rid].theta, one["theta"][k].cpu().numpy()), k
+        assert res[rid].steps == int(one["steps"][k]) and res[rid].status == int(one["status"][k])

@@ -73,3 +73,27 @@ def test_served_equals_alone(kind):
     lat = np.array([r.latency for r in results.values()])
     assert np.all(lat > 0)
     srv.close()
+
+
+def test_server_created_while_a_fit_runs():
+    """A pool made while a one-shot fit is still running on the default
+    stream: its zero fills must be done before the scheduler's non-blocking
+    lane streams admit into it, or the first admitted spectra are wiped."""
+    from paper_2512_24840_gb300 import lasp
+    from paper_2512_24840_gb300.server import NativeServer
+    lasp.load(build=True)
+    g = S.LAMOST
+    ip = lasp.Interp.from_grid(g, table(g.name), S.EXPS, S.BASIS_LO, S.BASIS_HI, S.BOX_LO, S.BOX_HI)
+    f, iv, gd, th = _observed(g, 8, 63)
+    dev = torch.device("cuda:0")
+    big = np.repeat(f, 256, axis=0)              # 2048 spectra keep the default stream busy
+    T = lambda a: torch.tensor(a, device=dev)
+    busy = ip.fit(T(big), T(np.repeat(iv, 256, axis=0)), T(np.repeat(gd, 256, axis=0)),
+                  T(np.repeat(th, 256, axis=0)), max_steps=400)
+    srv = NativeServer({"l": ip}, {"l": 8}, chunk=7, max_steps=400)   # no host sync before this
+    rids = [srv.submit("l", f[i], iv[i], gd[i], th[i]) for i in range(8)]
+    res = {r.rid: r for r in srv.run_until_idle()}
+    srv.close()
+    for i, rid in enumerate(rids):
+        assert np.array_equal(res[rid].theta, busy["theta"][256 * i].cpu().numpy()), i
+        assert res[rid].status == int(busy["status"][256 * i])
