@@ -36,10 +36,11 @@ METRIC = "converged spectra/s at fixed param tolerance, plain vs mixed; p50/p99 
 UNIT = "spectra/s"
 N_SPEC, MAX_STEPS, DEG = 4096, 500, 6
 FP32_LANES_PER_SM, N_SM = 128, 152
-# DRAM bytes of one fit_kernel<256,6> launch on this workload, from one ncu
-# capture of the current kernel source (reset to None whenever the kernel
-# changes until it is captured again).
-FIT_TRAFFIC_BYTES = 152_982_784
+# The batch fit's kernel on this workload (four spectra per CTA) and the DRAM
+# bytes of one launch, from one ncu capture of the current kernel source
+# (reset to None whenever the kernel changes until it is captured again).
+FIT_KERNEL = "fit_multi_kernel<256,6,4>"
+FIT_TRAFFIC_BYTES = 187_787_776
 
 
 def parse():
@@ -514,13 +515,13 @@ def run_ours(args):
                    "steps_p50_p90_p99_max": [float(np.percentile(steps_np, q)) for q in (50, 90, 99)]
                                             + [int(steps_np.max())],
                    "spectrum_steps_per_s": float((steps_np + 1).sum() / (fit_avg / 1e3))},
-        "roofline": {"kernel": "fit_kernel<256,6>", "bound": "alu", "achieved": achieved,
+        "roofline": {"kernel": FIT_KERNEL, "bound": "alu", "achieved": achieved,
                      "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
                      "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz "
                                     f"(sm_max_mhz, {pk_kind})",
                      "traffic": FIT_TRAFFIC_BYTES,
                      "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one "
-                                     "fit_kernel<256,6> launch on this workload (ncu)"},
+                                     f"{FIT_KERNEL} launch on this workload (ncu)"},
         "clocks": clocks,
         "mixed": mixed,
         "mixed_65536": mixed_large,

@@ -1,0 +1,551 @@
+// Fused fit with S spectra per CTA (FP32 CUDA-core form) -- sm_103a.
+//
+// fit_kernel spends most of an Adam step streaming the table from L2 twice:
+// once for F' = phi C (Eq. 1) and once for the adjoint contraction
+// d l / d phi_k = sum_m dF'_m C_km.  Here one CTA carries S spectra ("lanes")
+// through their steps side by side and loads each table value once for all S
+// lanes, so the table traffic per spectrum-step falls by S.  Everything else
+// runs lane after lane with fit_kernel's code, thread ownership and order of
+// every sum, so each spectrum gets bitwise the result fit_kernel gives it
+// (rows outside a lane's active range contribute exact zeros: its phi and
+// dphi vanish there).
+//
+// The grid is persistent: a lane whose spectrum stops takes the next one from
+// a global counter, so no lane idles while spectra remain.  y and W of a lane
+// live in a global workspace row (one row per lane of the grid, a few tens of
+// MB in all, L2-resident) instead of shared memory, and each lane's F' and
+// delta share one buffer, so four lanes take 95 KB of shared memory at 3909
+// pixels; at two CTAs per SM (eight spectra in flight) the table traffic per
+// spectrum-step is a quarter of fit_kernel's.  Measured on the 4096 x 3909
+// batch (fit_kernel: 30.8 ms): four lanes at two CTAs per SM 23.6 ms, three
+// lanes 24.1 ms, two lanes at three CTAs per SM 24.6 ms.  Clean fits and
+// resumable slots stay on fit_kernel.
+#pragma once
+
+#include "lasp_fit.cuh"
+
+namespace lasp {
+
+struct MultiWs {
+    float* yw;      // (grid x S) rows of 2 ldw floats: y, then W; zero beyond p
+    int ldw;        // row stride: p rounded up to 16
+    int* next;      // index of the next spectrum to take (starts at 0)
+};
+
+// Shared-memory plan (floats): per lane [B | g | gmu | gsg | phi | dphi | ring]
+// at lane * lane_stride, then the CTA's reduction buffers.  B holds the lane's
+// F' (model pixel m at skew(m + 16)) until the last F' window of a step is
+// read, then its delta (pixel j at skew(j + dofs)); both layouts keep zero
+// pads, rewritten each time.  B also holds the preprocessing sort.
+struct MultiSmem {
+    int Fp, Db, g, gmu, gsg, phi, dphi, ring, lane, part, red, out, total, dofs;
+    __host__ __device__ MultiSmem(int p, int H, int n_model, int NT, int D, int K, int S) {
+        const int NB = D + 1, NV = NB * (NB + 1) / 2 + NB;
+        const int nv_max = round32(NV > NADJ * S ? NV : NADJ * S);
+        dofs = 2 * H + 8;
+        int nb = skew_size(n_model + 32);
+        if (skew_size(p + 4 * H + 40) > nb) nb = skew_size(p + 4 * H + 40);
+        if (next_pow2(p) > nb) nb = next_pow2(p);
+        int o = 0;
+        Fp = o;
+        Db = o;   o += (nb + 3) & ~3;
+        g = o;    o += TAPBUF;
+        gmu = o;  o += TAPBUF;
+        gsg = o;  o += TAPBUF;
+        phi = o;  o += round32(K);
+        dphi = o; o += DPS * round32(K);
+        ring = o; o += WINMAX;
+        lane = o;
+        o *= S;
+        part = o; o += 4 * S * NT;       // per-thread lane sums, [4 s + q][thread]
+        red = o;  o += (NT / 32) * nv_max;
+        out = o;  o += 2 * nv_max + 16;
+        total = o;
+    }
+};
+
+__host__ inline size_t fit_multi_smem_bytes(int p, int H, int n_model, int NT, int D, int K, int S) {
+    return 4 * (size_t)MultiSmem(p, H, n_model, NT, D, K, S).total;
+}
+
+template <int NT, int S>
+__host__ __device__ constexpr int multi_min_blocks() {
+    return NT == 256 ? (S <= 2 ? 3 : 2) : 1;
+}
+
+// With two CTAs per SM or fewer (128 registers a thread) and at most three
+// lanes, a lane's y and W stay in registers from the normal equations to the
+// residual instead of being read from L2 twice (with four lanes they spill).
+template <int NT, int S>
+__host__ __device__ constexpr bool multi_keep_yw() {
+    return multi_min_blocks<NT, S>() <= 2 && S <= 3;
+}
+
+template <int NT, int D, int S>
+__global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kernel(const FitParams P,
+                                                                                  const MultiWs Wk) {
+    using Gm = Gram<D>;
+    constexpr int NB = D + 1;
+    constexpr int NV = Gm::NV;
+    static_assert(S >= 1 && S <= NT / 32, "one warp per lane runs the lane's Adam step");
+    extern __shared__ __align__(16) float sm[];
+    const ModelDev& M = P.M;
+    const int p = M.n_pix, H = M.pad, nm = M.n_model;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const MultiSmem L(p, H, nm, NT, D, M.K, S);
+    float* red = sm + L.red;
+    float* out = sm + L.out;
+    __shared__ float s_x[S][5], s_b[S][NB], s_w[S];
+    __shared__ int s_h[S], s_k[S][2], s_i[S], s_need[S], s_next;
+
+    // Adam and stop-rule state of lane s: registers of warp s (parameter k on
+    // its lane k < 5; step count, ring slot and rule state on every lane).
+    float xk = 0.0f, mk = 0.0f, vk = 0.0f, prev = 0.0f;
+    int rise = 0, ri = 0, t = 0;
+    double b1t = 1.0, b2t = 1.0;
+
+    if (tid < S) {
+        s_i[tid] = -1;
+        s_need[tid] = 1;
+    }
+    __syncthreads();
+
+    const float inv_p = 1.0f / (float)p;
+    const int j0 = tid * PPT;
+    const bool own_pix = j0 < p;
+    const bool own_mod = j0 < nm;
+    const float xstep = 2.0f / (float)p;
+
+    for (;;) {
+        // ---- take a spectrum into every lane whose fit stopped (whole CTA per lane)
+#pragma unroll 1
+        for (int s = 0; s < S; ++s) {
+            if (!s_need[s]) continue;
+            float* base = sm + s * L.lane;
+            float* yr = Wk.yw + (size_t)(blockIdx.x * S + s) * 2 * Wk.ldw;
+            float* wr = yr + Wk.ldw;
+            for (;;) {
+                if (tid == 0) s_next = atomicAdd(Wk.next, 1);
+                __syncthreads();
+                const int i = s_next;
+                if (i >= P.N) {
+                    if (tid == 0) {
+                        s_i[s] = -1;
+                        s_need[s] = 0;
+                    }
+                    __syncthreads();
+                    break;
+                }
+                // preprocessing (section 3.3 step 2) into the lane's workspace row;
+                // the lane's F' and delta buffers hold the sort
+                const size_t row = (size_t)i * p;
+                float w, imean;
+                const int n_obj = prep_spectrum<NT>(P.flux + row, P.ivar + row, P.good + row, p, P.O.edge_px,
+                                                    P.O.quantile, yr, wr, base + L.Fp, red, &w, &imean);
+                for (int q = p + tid; q < Wk.ldw; q += NT) {
+                    yr[q] = 0.0f;
+                    wr[q] = 0.0f;
+                }
+                // the sort's leftovers out of the lane buffer
+                for (int q = tid; q < L.g - L.Fp; q += NT) base[L.Fp + q] = 0.0f;
+                if (n_obj < NB + 5 || !(w > 0.0f) || !isfinite(w)) {
+                    if (tid < 5) {
+                        const float xx = (P.theta0[5 * i + tid] - M.plo[tid]) / M.phalf[tid] - 1.0f;
+                        P.theta[5 * i + tid] = phys_of(M, tid, fminf(1.0f, fmaxf(-1.0f, xx)));
+                    }
+                    if (tid == 0) {
+                        P.loss[i] = NAN;
+                        P.steps[i] = 0;
+                        P.status[i] = 64u;
+                        if (P.weight) P.weight[i] = w;
+                    }
+                    if (P.cont && tid < NB) P.cont[(size_t)i * NB + tid] = NAN;
+                    __syncthreads();
+                    continue;
+                }
+                if (warp == s) {
+                    xk = mk = vk = prev = 0.0f;
+                    rise = ri = t = 0;
+                    b1t = b2t = 1.0;
+                    if (lane < 5) {
+                        const float xx = (P.theta0[5 * i + lane] - M.plo[lane]) / M.phalf[lane] - 1.0f;
+                        xk = fminf(1.0f, fmaxf(-1.0f, xx));
+                        s_x[s][lane] = xk;
+                    }
+                    __syncwarp();
+                    const int hn = warp_prepare_step(M, s_x[s], base + L.phi, base + L.dphi, base + L.g,
+                                                     base + L.gmu, base + L.gsg, s_k[s]);
+                    if (lane == 0) {
+                        s_h[s] = hn;
+                        s_i[s] = i;
+                        s_need[s] = 0;
+                        s_w[s] = w;
+                    }
+                }
+                __syncthreads();
+                break;
+            }
+        }
+        bool any = false;
+        int kb = M.K, ke = 0;
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+            if (s_i[s] >= 0) {
+                any = true;
+                kb = min(kb, s_k[s][0]);
+                ke = max(ke, s_k[s][1]);
+            }
+        if (!any) break;
+
+        // ---- a3 for every lane: F'_s = phi_s C (Eq. 1), each table value loaded once
+        if (own_mod) {
+            float acc[S][PPT];
+#pragma unroll
+            for (int s = 0; s < S; ++s)
+#pragma unroll
+                for (int r = 0; r < PPT; ++r) acc[s][r] = 0.0f;
+            const float* crow = M.Cp + j0;
+#pragma unroll 2
+            for (int k = kb; k < ke; ++k) {
+                float pk[S];
+#pragma unroll
+                for (int s = 0; s < S; ++s) pk[s] = sm[s * L.lane + L.phi + k];
+                const float* ck = crow + (size_t)k * M.ldc;
+#pragma unroll
+                for (int q = 0; q < PPT / 8; ++q) {
+                    float c[8];
+                    ldg8(ck + 8 * q, c);
+#pragma unroll
+                    for (int s = 0; s < S; ++s)
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) acc[s][8 * q + e] = fmaf(pk[s], c[e], acc[s][8 * q + e]);
+                }
+            }
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                float* Fp = sm + s * L.lane + L.Fp;
+#pragma unroll
+                for (int r = 0; r < PPT; ++r)
+                    if (j0 + r < nm) Fp[skew(j0 + r + 16)] = acc[s][r];
+            }
+        }
+        // F' pads (model pixels [-16, 0) and [n_model, n_model + 16)) over the last delta
+        if (tid < 32) {
+            const int m = tid < 16 ? tid - 16 : nm + tid - 16;
+#pragma unroll
+            for (int s = 0; s < S; ++s) sm[s * L.lane + L.Fp + skew(m + 16)] = 0.0f;
+        }
+        __syncthreads();
+
+        // ---- per lane: a4 broadening, a5 normal equations and solve, a6 residual,
+        // a7 (i) tap sums; the code of fit_kernel with the lane's buffers
+        constexpr bool KEEP = multi_keep_yw<NT, S>();
+        // one copy of the per-lane code (lane loop not unrolled: the unrolled form
+        // missed in the instruction cache); each thread's four sums of a lane
+        // wait in shared memory for the end-of-step reduction
+#pragma unroll 1
+        for (int s = 0; s < S; ++s) {
+            if (s_i[s] < 0) continue;
+            float* Fp = sm + s * L.lane + L.Fp;
+            float* Db = sm + s * L.lane + L.Db;      // the same buffer, delta layout
+            const float* g = sm + s * L.lane + L.g;
+            const float* gmu = sm + s * L.lane + L.gmu;
+            const float* gsg = sm + s * L.lane + L.gsg;
+            const float* yr = Wk.yw + (size_t)(blockIdx.x * S + s) * 2 * Wk.ldw;
+            const float* wr = yr + Wk.ldw;
+            const int h = s_h[s];
+            const int nblk = (2 * h + 1 + TB - 1) / TB;
+
+            float fpp[PPT];
+#pragma unroll
+            for (int r = 0; r < PPT; ++r) fpp[r] = 0.0f;
+            if (own_pix) {
+                for (int bk = 0; bk < nblk; ++bk) {
+                    const int s0 = -h + bk * TB;
+                    float gg[TB], win[PPT + TB - 1];
+#pragma unroll
+                    for (int e = 0; e < TB; ++e) gg[e] = g[s0 + e + H];
+                    const int base = j0 + H - s0 - (TB - 1) + 16;
+#pragma unroll
+                    for (int q = 0; q < PPT + TB - 1; ++q) win[q] = Fp[skew(base + q)];
+#pragma unroll
+                    for (int e = 0; e < TB; ++e)
+#pragma unroll
+                        for (int r = 0; r < PPT; ++r) fpp[r] = fmaf(gg[e], win[r - e + TB - 1], fpp[r]);
+                }
+            }
+
+            // the lane's y and W (kept in registers to the residual where there is room)
+            float yk[KEEP ? PPT : 1], wk[KEEP ? PPT : 1];
+            float gacc[NV];
+#pragma unroll
+            for (int q = 0; q < NV; ++q) gacc[q] = 0.0f;
+            if (own_pix) {
+#pragma unroll
+                for (int r4 = 0; r4 < PPT; r4 += 4) {
+                    const float4 y4 = *reinterpret_cast<const float4*>(yr + j0 + r4);
+                    const float4 w4 = *reinterpret_cast<const float4*>(wr + j0 + r4);
+                    const float yv[4] = {y4.x, y4.y, y4.z, y4.w}, wv[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int r = r4 + u, j = j0 + r;
+                        if constexpr (KEEP) {
+                            yk[r] = yv[u];
+                            wk[r] = wv[u];
+                        }
+                        const float Wj = j < p ? wv[u] : 0.0f;
+                        if (Wj != 0.0f) {
+                            float Pl[NB];
+                            legendre<D>(fmaf((float)j, xstep, -1.0f), Pl);
+                            const float f = fpp[r];
+                            const float vv = Wj * f * f, uu = Wj * f * yv[u];
+#pragma unroll
+                            for (int a = 0; a < NB; ++a) {
+                                const float va = vv * Pl[a];
+#pragma unroll
+                                for (int b2 = a; b2 < NB; ++b2)
+                                    gacc[Gm::idx(a, b2)] = fmaf(va, Pl[b2], gacc[Gm::idx(a, b2)]);
+                                gacc[Gm::NG + a] = fmaf(uu, Pl[a], gacc[Gm::NG + a]);
+                            }
+                        }
+                    }
+                }
+            }
+            if (P.O.fp64_ne) {
+                float2* outff = reinterpret_cast<float2*>(out);
+                reduce_to_warp0_ff<NV, NT>(gacc, red, outff);
+                if (warp == 0) {
+                    const float2* const rh[1] = {outff + Gm::NG};
+                    float bf[NB];
+                    const bool ok = warp_chol_solve_ff<D, 1>(outff, rh, bf);
+                    if (lane == 0)
+#pragma unroll
+                        for (int a = 0; a < NB; ++a) s_b[s][a] = ok ? bf[a] : NAN;
+                }
+            } else {
+                reduce_to_warp0<NV, NT>(gacc, red, out);
+                if (tid == 0) {
+                    float bf[NB];
+                    const bool ok = chol_solve_rcp<D, float>(out, out + Gm::NG, bf);
+#pragma unroll
+                    for (int a = 0; a < NB; ++a) s_b[s][a] = ok ? bf[a] : NAN;
+                }
+            }
+            __syncthreads();
+
+            // a6: residual (Eq. 7), loss (Eq. 9); delta = W eps c (unscaled)
+            float racc[2] = {0.0f, 0.0f};
+            {
+                float bl[NB];
+#pragma unroll
+                for (int a = 0; a < NB; ++a) bl[a] = s_b[s][a];
+                const bool solved = isfinite(bl[0]);
+                if (own_pix && solved) {
+#pragma unroll
+                    for (int r4 = 0; r4 < PPT; r4 += 4) {
+                        float yv[4], wv[4];
+                        if constexpr (KEEP) {
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                yv[u] = yk[r4 + u];
+                                wv[u] = wk[r4 + u];
+                            }
+                        } else {
+                            const float4 y4 = *reinterpret_cast<const float4*>(yr + j0 + r4);
+                            const float4 w4 = *reinterpret_cast<const float4*>(wr + j0 + r4);
+                            yv[0] = y4.x; yv[1] = y4.y; yv[2] = y4.z; yv[3] = y4.w;
+                            wv[0] = w4.x; wv[1] = w4.y; wv[2] = w4.z; wv[3] = w4.w;
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int r = r4 + u, j = j0 + r;
+                            float dlt = 0.0f;
+                            const float Wj = j < p ? wv[u] : 0.0f;
+                            if (Wj != 0.0f) {
+                                float Pl[NB];
+                                legendre<D>(fmaf((float)j, xstep, -1.0f), Pl);
+                                float c = 0.0f;
+#pragma unroll
+                                for (int a = 0; a < NB; ++a) c = fmaf(bl[a], Pl[a], c);
+                                const float e = yv[u] - c * fpp[r];
+                                racc[0] = fmaf(Wj * e, e, racc[0]);
+                                if (c <= 0.0f) racc[1] = 1.0f;
+                                dlt = Wj * e * c;
+                            }
+                            fpp[r] = dlt;
+                        }
+                    }
+                }
+                if (!solved) racc[0] = NAN;
+            }
+            float bmu = 0.0f, bsg = 0.0f;
+            // a7 (i): a_s = sum_j delta_j F'_{j+H-s}, into d/dmu and d/dsigma
+            if (own_pix) {
+                for (int bk = 0; bk < nblk; ++bk) {
+                    const int s0 = -h + bk * TB;
+                    float win[PPT + TB - 1];
+                    const int base = j0 + H - s0 - (TB - 1) + 16;
+#pragma unroll
+                    for (int q = 0; q < PPT + TB - 1; ++q) win[q] = Fp[skew(base + q)];
+                    float a[TB];
+#pragma unroll
+                    for (int e = 0; e < TB; ++e) a[e] = 0.0f;
+#pragma unroll
+                    for (int r = 0; r < PPT; ++r)
+#pragma unroll
+                        for (int e = 0; e < TB; ++e) a[e] = fmaf(fpp[r], win[r - e + TB - 1], a[e]);
+#pragma unroll
+                    for (int e = 0; e < TB; ++e) {
+                        bmu = fmaf(gmu[s0 + e + H], a[e], bmu);
+                        bsg = fmaf(gsg[s0 + e + H], a[e], bsg);
+                    }
+                }
+            }
+            float* part = sm + L.part + 4 * s * NT + tid;
+            part[0] = racc[0];
+            part[NT] = racc[1];
+            part[2 * NT] = bmu;
+            part[3 * NT] = bsg;
+            __syncthreads();      // the lane's last F' window is read: the buffer takes delta
+            if (own_pix)
+#pragma unroll
+                for (int r = 0; r < PPT; ++r)
+                    if (j0 + r < p) Db[skew(j0 + r + L.dofs)] = fpp[r];
+            // delta pads: pixels [-dofs, 0) and [p, p + 2H + 32)
+            if (tid < 4 * H + 40) {
+                const int q = tid < L.dofs ? tid : p + tid;
+                Db[skew(q)] = 0.0f;
+            }
+        }
+        __syncthreads();     // every lane's delta buffer complete
+
+        // ---- a7 (ii): dF'_s = g_s (x) delta_s per lane, then one table pass for all
+        // lanes: d l / d phi_k = sum_m dF'_m C_km folded into the basis derivatives
+        float bacc[S * NADJ];
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const bool act = s_i[s] >= 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) bacc[NADJ * s + q] = act ? sm[L.part + (4 * s + q) * NT + tid] : 0.0f;
+#pragma unroll
+            for (int q = 4; q < NADJ; ++q) bacc[NADJ * s + q] = 0.0f;
+        }
+        if (own_mod) {
+            float dfp[S][PPT];
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+#pragma unroll
+                for (int r = 0; r < PPT; ++r) dfp[s][r] = 0.0f;
+                if (s_i[s] < 0) continue;
+                const float* Db = sm + s * L.lane + L.Db;
+                const float* g = sm + s * L.lane + L.g;
+                const int h = s_h[s];
+                const int nblk = (2 * h + 1 + TB - 1) / TB;
+                for (int bk = 0; bk < nblk; ++bk) {
+                    const int s0 = -h + bk * TB;
+                    float gg[TB], win[PPT + TB - 1];
+#pragma unroll
+                    for (int e = 0; e < TB; ++e) gg[e] = g[s0 + e + H];
+                    const int base = j0 - H + s0 + L.dofs;
+#pragma unroll
+                    for (int q = 0; q < PPT + TB - 1; ++q) win[q] = Db[skew(base + q)];
+#pragma unroll
+                    for (int e = 0; e < TB; ++e)
+#pragma unroll
+                        for (int r = 0; r < PPT; ++r) dfp[s][r] = fmaf(gg[e], win[r + e], dfp[s][r]);
+                }
+            }
+            const float* crow = M.Cp + j0;
+#pragma unroll 2
+            for (int k = kb; k < ke; ++k) {
+                const float* ck = crow + (size_t)k * M.ldc;
+                float c[PPT];
+#pragma unroll
+                for (int q = 0; q < PPT / 8; ++q) {
+                    float c8[8];
+                    ldg8(ck + 8 * q, c8);
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) c[8 * q + e] = c8[e];
+                }
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    float a = 0.0f;
+#pragma unroll
+                    for (int r = 0; r < PPT; ++r) a = fmaf(dfp[s][r], c[r], a);
+                    const float4 dk = reinterpret_cast<const float4*>(sm + s * L.lane + L.dphi)[k];
+                    bacc[NADJ * s + 4] = fmaf(dk.x, a, bacc[NADJ * s + 4]);
+                    bacc[NADJ * s + 5] = fmaf(dk.y, a, bacc[NADJ * s + 5]);
+                    bacc[NADJ * s + 6] = fmaf(dk.z, a, bacc[NADJ * s + 6]);
+                }
+            }
+        }
+        reduce_to_warp0<S * NADJ, NT>(bacc, red, out);
+        __syncthreads();
+
+        // ---- a8 per lane on warp s: chain rule to x, stop rules, Adam, next basis + taps
+        if (warp < S && s_i[warp] >= 0) {
+            const int s = warp;
+            const int i = s_i[s];
+            const float* o = out + NADJ * s;
+            float* base = sm + s * L.lane;
+            float* ring = base + L.ring;
+            const float l = sqrtf(o[0] * inv_p);
+            const bool nonpos = o[1] > 0.0f;
+            const float kappa = l > 0.0f ? -1.0f / ((float)p * l) : 0.0f;
+            float gk = 0.0f;
+            if (lane < 5) {
+                const float src = lane < 3 ? o[4 + lane] : o[lane - 1] / M.kms_px;
+                gk = kappa * src * M.phalf[lane];
+            }
+            const bool fin = __all_sync(0xffffffffu, lane >= 5 || isfinite(gk));
+            uint32_t st = 0;
+            if (lane == 0) {
+                if (!isfinite(s_b[s][0])) st = 32u;
+                else if (!(fin && isfinite(l))) st = 16u;
+                if (!st) {
+                    const int Wn = P.O.window;
+                    if (t >= Wn && fabsf(l - ring[ri]) < P.O.tol) st = 1u;
+                    rise = (t >= 1 && l > prev) ? rise + 1 : 0;
+                    if (!st && rise >= Wn) st = 2u;
+                    if (!st && t >= P.O.max_steps) st = 4u;
+                    ring[ri] = l;
+                    ri = ri + 1 == Wn ? 0 : ri + 1;
+                    prev = l;
+                }
+                if (st && st <= 4u && nonpos) st |= 8u;
+            }
+            st = __shfl_sync(0xffffffffu, st, 0);
+            if (st) {
+                if (lane < 5) P.theta[5 * i + lane] = phys_of(M, lane, xk);
+                if (lane == 0) {
+                    P.loss[i] = l;
+                    P.steps[i] = t;
+                    P.status[i] = st;
+                    if (P.weight) P.weight[i] = s_w[s];
+                    s_need[s] = 1;
+                }
+                if (P.cont && lane < NB) P.cont[(size_t)i * NB + lane] = s_b[s][lane];
+            } else {
+                b1t *= (double)P.O.beta1;
+                b2t *= (double)P.O.beta2;
+                const float step = P.O.lr / (float)(1.0 - b1t);
+                const float bc2s = sqrtf((float)(1.0 - b2t));
+                if (lane < 5) {
+                    mk = P.O.beta1 * mk + (1.0f - P.O.beta1) * gk;
+                    vk = P.O.beta2 * vk + (1.0f - P.O.beta2) * gk * gk;
+                    const float denom = sqrtf(vk) / bc2s + P.O.eps;
+                    xk = fminf(1.0f, fmaxf(-1.0f, xk - step * mk / denom));
+                    s_x[s][lane] = xk;
+                }
+                ++t;
+                __syncwarp();
+                const int hn = warp_prepare_step(M, s_x[s], base + L.phi, base + L.dphi, base + L.g,
+                                                 base + L.gmu, base + L.gsg, s_k[s]);
+                if (lane == 0) s_h[s] = hn;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace lasp

@@ -3,6 +3,7 @@
 #pragma once
 
 #include "lasp_fit.cuh"
+#include "lasp_fit_multi.cuh"
 #include "lasp_lm.cuh"
 #include "lasp_model.cuh"
 
@@ -11,6 +12,7 @@ namespace lasp {
 int cuda_rc(cudaError_t e);
 
 template <int D> int launch_fit(const FitParams& P, cudaStream_t st);
+template <int D> int launch_fit_multi(const FitParams& P, cudaStream_t st);
 template <int D> int launch_errors(const ErrParams& P, cudaStream_t st);
 template <int D> int launch_forward(const ModelParams& P, cudaStream_t st);
 template <int D> int launch_backward(const ModelParams& P, cudaStream_t st);
@@ -38,6 +40,48 @@ int launch_fit(const FitParams& P, cudaStream_t st) {
         fit_kernel<512, D><<<P.N, 512, smem, st>>>(P);
     }
     return cuda_rc(cudaGetLastError());
+}
+
+// Spectra per CTA of the batch fit (fit_multi_kernel).
+constexpr int FIT_LANES = 4;
+
+// One-shot batch fit with FIT_LANES spectra per CTA on a persistent grid of
+// as many CTAs as the SMs hold; the workspace (spectrum counter and the
+// lanes' y, W rows) is taken from the stream-ordered pool for the launch.
+// Falls back to fit_kernel where the lanes' buffers do not fit.
+template <int D>
+int launch_fit_multi(const FitParams& P, cudaStream_t st) {
+    constexpr int S = FIT_LANES;
+    const int p = P.M.n_pix, H = P.M.pad, nm = P.M.n_model;
+    const int NT = p <= 16 * 256 ? 256 : 512;
+    const size_t smem = fit_multi_smem_bytes(p, H, nm, NT, D, P.M.K, S);
+    if (P.S.x || smem > 227 * 1024) return launch_fit<D>(P, st);
+    void (*kern)(const FitParams, const MultiWs) =
+        NT == 256 ? fit_multi_kernel<256, D, S> : fit_multi_kernel<512, D, S>;
+    int e = set_smem_attr(kern, smem);
+    if (e) return e;
+    int nb = 0, dev = 0, nsm = 0;
+    e = cuda_rc(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NT, smem));
+    if (!e) e = cuda_rc(cudaGetDevice(&dev));
+    if (!e) e = cuda_rc(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    if (e) return e;
+    if (nb < 1) return launch_fit<D>(P, st);
+    const int grid = (int)std::min<long long>(((long long)P.N + S - 1) / S, (long long)nb * nsm);
+    MultiWs W;
+    W.ldw = (p + 15) & ~15;
+    const size_t bytes = 256 + (size_t)grid * S * 2 * W.ldw * sizeof(float);
+    void* ws = nullptr;
+    e = cuda_rc(cudaMallocAsync(&ws, bytes, st));
+    if (e) return e;
+    W.next = static_cast<int*>(ws);
+    W.yw = reinterpret_cast<float*>(static_cast<char*>(ws) + 256);
+    e = cuda_rc(cudaMemsetAsync(ws, 0, 256, st));
+    if (!e) {
+        kern<<<grid, NT, smem, st>>>(P, W);
+        e = cuda_rc(cudaGetLastError());
+    }
+    const int ef = cuda_rc(cudaFreeAsync(ws, st));
+    return e ? e : ef;
 }
 
 template <int D>
@@ -108,6 +152,7 @@ int launch_lm(const LmParams& P, cudaStream_t st) {
 
 #define LASP_INSTANTIATE(D)                                                  \
     template int launch_fit<D>(const FitParams&, cudaStream_t);             \
+    template int launch_fit_multi<D>(const FitParams&, cudaStream_t);       \
     template int launch_errors<D>(const ErrParams&, cudaStream_t);          \
     template int launch_forward<D>(const ModelParams&, cudaStream_t);       \
     template int launch_backward<D>(const ModelParams&, cudaStream_t);      \
