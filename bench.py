@@ -508,7 +508,7 @@ def run_ours(args):
                    "l2": "flushed (256 MB write) between steps; inputs 144 MB > L2"},
         "e2e": {"value": e2e_conv / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": 3 * args.steps,
         "detail": {"fit_ms": fit_avg, "errors_ms": sum(err_ms) / len(err_ms),
                    "converged": conv, "n_spectra": N_SPEC,
                    "mean_steps": float(steps_np.mean()),

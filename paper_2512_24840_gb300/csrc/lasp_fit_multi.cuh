@@ -11,9 +11,11 @@
 // dphi vanish there).
 //
 // The grid is persistent: a lane whose spectrum stops takes the next one from
-// a global counter, so no lane idles while spectra remain.  y and W of a lane
-// live in a global workspace row (one row per lane of the grid, a few tens of
-// MB in all, L2-resident) instead of shared memory, and each lane's F' and
+// a global counter, so no lane idles while spectra remain.  The per-spectrum
+// preprocessing (the weight quantile sorts the spectrum) runs before, in
+// fit_prep_kernel at full occupancy, instead of stalling a CTA at each refill;
+// it leaves y and W in a global workspace row per spectrum, which the fit
+// reads from L2 each step instead of keeping it in shared memory, and each lane's F' and
 // delta share one buffer, so four lanes take 95 KB of shared memory at 3909
 // pixels; at two CTAs per SM (eight spectra in flight) the table traffic per
 // spectrum-step is a quarter of fit_kernel's.  Measured on the 4096 x 3909
@@ -27,7 +29,8 @@
 namespace lasp {
 
 struct MultiWs {
-    float* yw;      // (grid x S) rows of 2 ldw floats: y, then W; zero beyond p
+    float* yw;      // N rows of 2 ldw floats: y, then W; zero beyond p
+    float* wq;      // N: the weight w of each spectrum, NaN where preprocessing decided the fit
     int ldw;        // row stride: p rounded up to 16
     int* next;      // index of the next spectrum to take (starts at 0)
 };
@@ -35,8 +38,8 @@ struct MultiWs {
 // Shared-memory plan (floats): per lane [B | g | gmu | gsg | phi | dphi | ring]
 // at lane * lane_stride, then the CTA's reduction buffers.  B holds the lane's
 // F' (model pixel m at skew(m + 16)) until the last F' window of a step is
-// read, then its delta (pixel j at skew(j + dofs)); both layouts keep zero
-// pads, rewritten each time.  B also holds the preprocessing sort.
+// read, then its delta (pixel j at skew(j + dofs)); each step rewrites every
+// position either layout reads, pads included.
 struct MultiSmem {
     int Fp, Db, g, gmu, gsg, phi, dphi, ring, lane, part, red, out, total, dofs;
     __host__ __device__ MultiSmem(int p, int H, int n_model, int NT, int D, int K, int S) {
@@ -45,7 +48,6 @@ struct MultiSmem {
         dofs = 2 * H + 8;
         int nb = skew_size(n_model + 32);
         if (skew_size(p + 4 * H + 40) > nb) nb = skew_size(p + 4 * H + 40);
-        if (next_pow2(p) > nb) nb = next_pow2(p);
         int o = 0;
         Fp = o;
         Db = o;   o += (nb + 3) & ~3;
@@ -66,6 +68,45 @@ struct MultiSmem {
 
 __host__ inline size_t fit_multi_smem_bytes(int p, int H, int n_model, int NT, int D, int K, int S) {
     return 4 * (size_t)MultiSmem(p, H, n_model, NT, D, K, S).total;
+}
+
+// Preprocessing of every spectrum before the fit (section 3.3 step 2), one CTA
+// per spectrum at full occupancy: y and W into the spectrum's workspace row,
+// w into wq, and the final result of spectra with too few usable pixels
+// (status LASP_ST_NODATA, as fit_kernel writes it).  Shared memory:
+// fit_prep_smem_bytes.
+__host__ __device__ inline int fit_prep_smem_floats(int p, int NT) { return next_pow2(p) + (NT / 32) * 2 + 8; }
+
+template <int NT, int D>
+__global__ void __launch_bounds__(NT) fit_prep_kernel(const FitParams P, const MultiWs Wk) {
+    constexpr int NB = D + 1;
+    extern __shared__ __align__(16) float sm[];
+    const ModelDev& M = P.M;
+    const int p = M.n_pix, tid = threadIdx.x, i = blockIdx.x;
+    float* yr = Wk.yw + (size_t)i * 2 * Wk.ldw;
+    float* wr = yr + Wk.ldw;
+    const size_t row = (size_t)i * p;
+    float w, imean;
+    const int n_obj = prep_spectrum<NT>(P.flux + row, P.ivar + row, P.good + row, p, P.O.edge_px,
+                                        P.O.quantile, yr, wr, sm, sm + next_pow2(p), &w, &imean);
+    for (int q = p + tid; q < Wk.ldw; q += NT) {
+        yr[q] = 0.0f;
+        wr[q] = 0.0f;
+    }
+    const bool nodata = n_obj < NB + 5 || !(w > 0.0f) || !isfinite(w);
+    if (tid == 0) Wk.wq[i] = nodata ? NAN : w;
+    if (!nodata) return;
+    if (tid < 5) {
+        const float xx = (P.theta0[5 * i + tid] - M.plo[tid]) / M.phalf[tid] - 1.0f;
+        P.theta[5 * i + tid] = phys_of(M, tid, fminf(1.0f, fmaxf(-1.0f, xx)));
+    }
+    if (tid == 0) {
+        P.loss[i] = NAN;
+        P.steps[i] = 0;
+        P.status[i] = 64u;
+        if (P.weight) P.weight[i] = w;
+    }
+    if (P.cont && tid < NB) P.cont[(size_t)i * NB + tid] = NAN;
 }
 
 template <int NT, int S>
@@ -108,6 +149,7 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
         s_i[tid] = -1;
         s_need[tid] = 1;
     }
+    for (int q = tid; q < S * L.lane; q += NT) sm[q] = 0.0f;
     __syncthreads();
 
     const float inv_p = 1.0f / (float)p;
@@ -117,13 +159,11 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
     const float xstep = 2.0f / (float)p;
 
     for (;;) {
-        // ---- take a spectrum into every lane whose fit stopped (whole CTA per lane)
+        // ---- take the next spectrum into every lane whose fit stopped
 #pragma unroll 1
         for (int s = 0; s < S; ++s) {
             if (!s_need[s]) continue;
             float* base = sm + s * L.lane;
-            float* yr = Wk.yw + (size_t)(blockIdx.x * S + s) * 2 * Wk.ldw;
-            float* wr = yr + Wk.ldw;
             for (;;) {
                 if (tid == 0) s_next = atomicAdd(Wk.next, 1);
                 __syncthreads();
@@ -136,30 +176,8 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
                     __syncthreads();
                     break;
                 }
-                // preprocessing (section 3.3 step 2) into the lane's workspace row;
-                // the lane's F' and delta buffers hold the sort
-                const size_t row = (size_t)i * p;
-                float w, imean;
-                const int n_obj = prep_spectrum<NT>(P.flux + row, P.ivar + row, P.good + row, p, P.O.edge_px,
-                                                    P.O.quantile, yr, wr, base + L.Fp, red, &w, &imean);
-                for (int q = p + tid; q < Wk.ldw; q += NT) {
-                    yr[q] = 0.0f;
-                    wr[q] = 0.0f;
-                }
-                // the sort's leftovers out of the lane buffer
-                for (int q = tid; q < L.g - L.Fp; q += NT) base[L.Fp + q] = 0.0f;
-                if (n_obj < NB + 5 || !(w > 0.0f) || !isfinite(w)) {
-                    if (tid < 5) {
-                        const float xx = (P.theta0[5 * i + tid] - M.plo[tid]) / M.phalf[tid] - 1.0f;
-                        P.theta[5 * i + tid] = phys_of(M, tid, fminf(1.0f, fmaxf(-1.0f, xx)));
-                    }
-                    if (tid == 0) {
-                        P.loss[i] = NAN;
-                        P.steps[i] = 0;
-                        P.status[i] = 64u;
-                        if (P.weight) P.weight[i] = w;
-                    }
-                    if (P.cont && tid < NB) P.cont[(size_t)i * NB + tid] = NAN;
+                const float w = Wk.wq[i];
+                if (isnan(w)) {           // result already written by the preprocessing
                     __syncthreads();
                     continue;
                 }
@@ -251,7 +269,7 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
             const float* g = sm + s * L.lane + L.g;
             const float* gmu = sm + s * L.lane + L.gmu;
             const float* gsg = sm + s * L.lane + L.gsg;
-            const float* yr = Wk.yw + (size_t)(blockIdx.x * S + s) * 2 * Wk.ldw;
+            const float* yr = Wk.yw + (size_t)s_i[s] * 2 * Wk.ldw;
             const float* wr = yr + Wk.ldw;
             const int h = s_h[s];
             const int nblk = (2 * h + 1 + TB - 1) / TB;
@@ -421,15 +439,11 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
 
         // ---- a7 (ii): dF'_s = g_s (x) delta_s per lane, then one table pass for all
         // lanes: d l / d phi_k = sum_m dF'_m C_km folded into the basis derivatives
-        float bacc[S * NADJ];
+        // basis sums d l / d(Teff, logg, FeH) of each lane; the lane's other four
+        // sums join them from shared memory after the table pass
+        float bph[S][3];
 #pragma unroll
-        for (int s = 0; s < S; ++s) {
-            const bool act = s_i[s] >= 0;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) bacc[NADJ * s + q] = act ? sm[L.part + (4 * s + q) * NT + tid] : 0.0f;
-#pragma unroll
-            for (int q = 4; q < NADJ; ++q) bacc[NADJ * s + q] = 0.0f;
-        }
+        for (int s = 0; s < S; ++s) bph[s][0] = bph[s][1] = bph[s][2] = 0.0f;
         if (own_mod) {
             float dfp[S][PPT];
 #pragma unroll
@@ -473,11 +487,20 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
 #pragma unroll
                     for (int r = 0; r < PPT; ++r) a = fmaf(dfp[s][r], c[r], a);
                     const float4 dk = reinterpret_cast<const float4*>(sm + s * L.lane + L.dphi)[k];
-                    bacc[NADJ * s + 4] = fmaf(dk.x, a, bacc[NADJ * s + 4]);
-                    bacc[NADJ * s + 5] = fmaf(dk.y, a, bacc[NADJ * s + 5]);
-                    bacc[NADJ * s + 6] = fmaf(dk.z, a, bacc[NADJ * s + 6]);
+                    bph[s][0] = fmaf(dk.x, a, bph[s][0]);
+                    bph[s][1] = fmaf(dk.y, a, bph[s][1]);
+                    bph[s][2] = fmaf(dk.z, a, bph[s][2]);
                 }
             }
+        }
+        float bacc[S * NADJ];
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const bool act = s_i[s] >= 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) bacc[NADJ * s + q] = act ? sm[L.part + (4 * s + q) * NT + tid] : 0.0f;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) bacc[NADJ * s + 4 + q] = bph[s][q];
         }
         reduce_to_warp0<S * NADJ, NT>(bacc, red, out);
         __syncthreads();

@@ -45,20 +45,25 @@ int launch_fit(const FitParams& P, cudaStream_t st) {
 // Spectra per CTA of the batch fit (fit_multi_kernel).
 constexpr int FIT_LANES = 4;
 
-// One-shot batch fit with FIT_LANES spectra per CTA on a persistent grid of
-// as many CTAs as the SMs hold; the workspace (spectrum counter and the
-// lanes' y, W rows) is taken from the stream-ordered pool for the launch.
-// Falls back to fit_kernel where the lanes' buffers do not fit.
+// One-shot batch fit: fit_prep_kernel (one CTA per spectrum), then FIT_LANES
+// spectra per CTA on a persistent grid of as many CTAs as the SMs hold.  The
+// workspace (spectrum counter, w and the y, W rows of every spectrum: about
+// 8 p bytes a spectrum) is taken from the stream-ordered pool for the launch.
+// Falls back to fit_kernel where the lanes' buffers or the workspace do not fit.
 template <int D>
 int launch_fit_multi(const FitParams& P, cudaStream_t st) {
     constexpr int S = FIT_LANES;
     const int p = P.M.n_pix, H = P.M.pad, nm = P.M.n_model;
     const int NT = p <= 16 * 256 ? 256 : 512;
     const size_t smem = fit_multi_smem_bytes(p, H, nm, NT, D, P.M.K, S);
-    if (P.S.x || smem > 227 * 1024) return launch_fit<D>(P, st);
+    const size_t smem_prep = 4 * (size_t)fit_prep_smem_floats(p, NT);
+    if (P.S.x || smem > 227 * 1024 || smem_prep > 227 * 1024) return launch_fit<D>(P, st);
     void (*kern)(const FitParams, const MultiWs) =
         NT == 256 ? fit_multi_kernel<256, D, S> : fit_multi_kernel<512, D, S>;
+    void (*prep)(const FitParams, const MultiWs) =
+        NT == 256 ? fit_prep_kernel<256, D> : fit_prep_kernel<512, D>;
     int e = set_smem_attr(kern, smem);
+    if (!e) e = set_smem_attr(prep, smem_prep);
     if (e) return e;
     int nb = 0, dev = 0, nsm = 0;
     e = cuda_rc(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NT, smem));
@@ -69,13 +74,21 @@ int launch_fit_multi(const FitParams& P, cudaStream_t st) {
     const int grid = (int)std::min<long long>(((long long)P.N + S - 1) / S, (long long)nb * nsm);
     MultiWs W;
     W.ldw = (p + 15) & ~15;
-    const size_t bytes = 256 + (size_t)grid * S * 2 * W.ldw * sizeof(float);
+    const size_t rows = (size_t)P.N * 2 * W.ldw * sizeof(float);
+    const size_t wq = ((size_t)P.N * sizeof(float) + 255) & ~(size_t)255;
     void* ws = nullptr;
-    e = cuda_rc(cudaMallocAsync(&ws, bytes, st));
-    if (e) return e;
+    if (cudaMallocAsync(&ws, 256 + wq + rows, st) != cudaSuccess) {
+        cudaGetLastError();
+        return launch_fit<D>(P, st);          // no room for the workspace: one spectrum per CTA
+    }
     W.next = static_cast<int*>(ws);
-    W.yw = reinterpret_cast<float*>(static_cast<char*>(ws) + 256);
+    W.wq = reinterpret_cast<float*>(static_cast<char*>(ws) + 256);
+    W.yw = reinterpret_cast<float*>(static_cast<char*>(ws) + 256 + wq);
     e = cuda_rc(cudaMemsetAsync(ws, 0, 256, st));
+    if (!e) {
+        prep<<<P.N, NT, smem_prep, st>>>(P, W);
+        e = cuda_rc(cudaGetLastError());
+    }
     if (!e) {
         kern<<<grid, NT, smem, st>>>(P, W);
         e = cuda_rc(cudaGetLastError());
