@@ -112,6 +112,31 @@ __device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32]) {
     return v[0];
 }
 
+// Warp sums of values 32 g .. 32 g + 31 of v (zero past NV): lane l returns the
+// warp sum of value 32 g + l.  Eight values or fewer go through xor butterflies
+// with the levels in the scatter's order (16, 8, 4, 2, 1), which pair the same
+// lanes at every level, so the sums are bitwise those of the scatter.
+template <int NV>
+__device__ __forceinline__ float warp_sums_group(const float (&v)[NV], int g) {
+    const int lane = threadIdx.x & 31;
+    if (NV - 32 * g > 8) {
+        float t[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) t[i] = (32 * g + i < NV) ? v[32 * g + i] : 0.0f;
+        return warp_reduce_scatter32(t);
+    }
+    float mine = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        if (32 * g + i < NV) {
+            float s = v[32 * g + i];
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == i) mine = s;
+        }
+    return mine;
+}
+
 // Reduce NV per-thread values over the CTA; the sums end in out[0..NV) and
 // are visible to warp 0 only (after __syncwarp), with one CTA barrier.  Each
 // warp reduce-scatters groups of 32 values, then warp 0 adds the warps in a
@@ -122,12 +147,7 @@ __device__ __forceinline__ void reduce_to_warp0(float (&v)[NV], float* red, floa
     constexpr int NP = round32(NV);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int g = 0; g < NP / 32; ++g) {
-        float t[32];
-#pragma unroll
-        for (int i = 0; i < 32; ++i) t[i] = (32 * g + i < NV) ? v[32 * g + i] : 0.0f;
-        red[warp * NP + 32 * g + lane] = warp_reduce_scatter32(t);
-    }
+    for (int g = 0; g < NP / 32; ++g) red[warp * NP + 32 * g + lane] = warp_sums_group<NV>(v, g);
     __syncthreads();
     if (warp == 0) {
 #pragma unroll
@@ -149,12 +169,7 @@ __device__ __forceinline__ void reduce_to_warp0_ff(float (&v)[NV], float* red, f
     constexpr int NP = round32(NV);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int g = 0; g < NP / 32; ++g) {
-        float t[32];
-#pragma unroll
-        for (int i = 0; i < 32; ++i) t[i] = (32 * g + i < NV) ? v[32 * g + i] : 0.0f;
-        red[warp * NP + 32 * g + lane] = warp_reduce_scatter32(t);
-    }
+    for (int g = 0; g < NP / 32; ++g) red[warp * NP + 32 * g + lane] = warp_sums_group<NV>(v, g);
     __syncthreads();
     if (warp == 0) {
 #pragma unroll
