@@ -36,11 +36,13 @@ METRIC = "converged spectra/s at fixed param tolerance, plain vs mixed; p50/p99 
 UNIT = "spectra/s"
 N_SPEC, MAX_STEPS, DEG = 4096, 500, 6
 FP32_LANES_PER_SM, N_SM = 128, 152
-# The batch fit's kernel on this workload (four spectra per CTA) and the DRAM
-# bytes of one launch, from one ncu capture of the current kernel source
-# (reset to None whenever the kernel changes until it is captured again).
+# The batch fit's main kernel on this workload (four spectra per CTA, after
+# fit_prep_kernel) and the DRAM bytes of one launch, from one ncu capture of
+# the current kernel source (reset to None whenever the kernel changes until it
+# is captured again): it reads the prepared y, W rows (8 B a pixel) and the
+# table, and writes the results.
 FIT_KERNEL = "fit_multi_kernel<256,6,4>"
-FIT_TRAFFIC_BYTES = 187_787_776
+FIT_TRAFFIC_BYTES = 136_976_640
 
 
 def parse():

@@ -582,55 +582,129 @@ __device__ __forceinline__ bool inv_spd5_ff(const float2 (&A)[25], float (&X)[25
     return true;
 }
 
-// Bitonic sort (ascending) of P2 floats in shared memory by the whole CTA.
-template <int NT>
-__device__ void block_bitonic_sort(float* buf, int P2) {
-    for (int k = 2; k <= P2; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < P2; i += NT) {
-                int ixj = i ^ j;
-                if (ixj > i) {
-                    float a = buf[i], b = buf[ixj];
-                    bool up = (i & k) == 0;
-                    if ((a > b) == up) {
-                        buf[i] = b;
-                        buf[ixj] = a;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
+// Shared scratch prep_spectrum needs in `red` (floats): the select histogram.
+constexpr int PREP_RED = 272;
+
+// Order-preserving map of non-NaN floats to unsigned keys, and its inverse.
+__device__ __forceinline__ uint32_t order_key(float f) {
+    const uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float key_value(uint32_t k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
 
-__host__ __device__ constexpr int next_pow2(int n) {
-    int p = 1;
-    while (p < n) p <<= 1;
-    return p;
+// The k-th smallest (0-based) key of vals[0..n) by most-significant-digit
+// radix select: four passes of 8-bit digit histograms in shared memory (hist:
+// 258 ints), each counting only the keys that share the digits chosen so
+// far.  Lanes of a warp with equal digits add their count in one atomic.
+// Requires 0 <= k < n; every thread returns the key.
+template <int NT>
+__device__ uint32_t block_select_key(const float* vals, int n, int k, int* hist) {
+    const int lane = threadIdx.x & 31;
+    uint32_t prefix = 0, mask = 0;
+    int kk = k;
+#pragma unroll 1
+    for (int shift = 24; shift >= 0; shift -= 8) {
+        for (int b = threadIdx.x; b < 256; b += NT) hist[b] = 0;
+        __syncthreads();
+        for (int j0 = threadIdx.x - lane; j0 < n; j0 += NT) {
+            const int j = j0 + lane;
+            int d = -1;
+            if (j < n) {
+                const uint32_t key = order_key(vals[j]);
+                if ((key & mask) == prefix) d = (int)((key >> shift) & 255u);
+            }
+            const unsigned same = __match_any_sync(0xffffffffu, d);
+            if (d >= 0 && lane == __ffs(same) - 1) atomicAdd(&hist[d], __popc(same));
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            int c[8], tot = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                c[q] = hist[8 * lane + q];
+                tot += c[q];
+            }
+            int incl = tot;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            int run = incl - tot;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                if (run <= kk && kk < run + c[q]) {
+                    hist[256] = 8 * lane + q;
+                    hist[257] = kk - run;
+                }
+                run += c[q];
+            }
+        }
+        __syncthreads();
+        prefix |= (uint32_t)hist[256] << shift;
+        mask |= 255u << shift;
+        kk = hist[257];
+    }
+    return prefix;
+}
+
+// For a key K of vals[0..n): the count of keys <= K and the smallest key
+// above K (0xffffffff if none), on every thread.  hist: 2 (NT/32) + 2 ints.
+template <int NT>
+__device__ void block_next_key(const float* vals, int n, uint32_t K, int* hist, int* cnt_le, uint32_t* next) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int cnt = 0;
+    uint32_t mn = 0xffffffffu;
+    for (int j = threadIdx.x; j < n; j += NT) {
+        const uint32_t key = order_key(vals[j]);
+        cnt += key <= K ? 1 : 0;
+        if (key > K && key < mn) mn = key;
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        mn = min(mn, (uint32_t)__shfl_xor_sync(0xffffffffu, mn, o));
+    }
+    __syncthreads();                       // the select's last reads of hist are done
+    if (lane == 0) {
+        hist[2 * warp] = cnt;
+        hist[2 * warp + 1] = (int)mn;
+    }
+    __syncthreads();
+    int c = 0;
+    uint32_t m = 0xffffffffu;
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) {
+        c += hist[2 * w];
+        m = min(m, (uint32_t)hist[2 * w + 1]);
+    }
+    *cnt_le = c;
+    *next = m;
 }
 
 // Per-spectrum preprocessing (section 3.3 step 2; Eq. 9 weights):
 // w = quantile of the used flux (linear interpolation between order
 // statistics), y = flux / w, W = ivar / mean(ivar over used pixels), both zero
-// on masked, non-finite and edge pixels.  sortbuf holds next_pow2(p) floats.
+// on masked, non-finite and edge pixels.  The two order statistics come from
+// a radix select over sortbuf (p floats; unused pixels enter as +inf, above
+// every used one), the same values a sort gives; red holds PREP_RED floats.
 // Returns the count of pixels that enter the loss; *w_out is w.
 template <int NT>
 __device__ int prep_spectrum(const float* __restrict__ flux, const float* __restrict__ ivar,
                              const uint8_t* __restrict__ good, int p, int edge_px, float quantile,
                              float* y, float* W, float* sortbuf, float* red, float* w_out,
                              float* imean_out = nullptr) {
-    const int P2 = next_pow2(p);
     float cnt = 0.0f, isum = 0.0f;
-    for (int j = threadIdx.x; j < P2; j += NT) {
+    for (int j = threadIdx.x; j < p; j += NT) {
         float v = INFINITY;
-        if (j < p) {
-            float f = flux[j], iv = ivar[j];
-            bool use = good[j] && iv > 0.0f && isfinite(f) && isfinite(iv);
-            if (use) {
-                v = f;
-                cnt += 1.0f;
-                isum += iv;
-            }
+        float f = flux[j], iv = ivar[j];
+        bool use = good[j] && iv > 0.0f && isfinite(f) && isfinite(iv);
+        if (use) {
+            v = f;
+            cnt += 1.0f;
+            isum += iv;
         }
         sortbuf[j] = v;
     }
@@ -639,13 +713,23 @@ __device__ int prep_spectrum(const float* __restrict__ flux, const float* __rest
     block_sum<2, NT>(acc, red, tot);
     const int n = (int)tot[0];
     const float imean = n > 0 ? tot[1] / (float)n : 0.0f;
-    block_bitonic_sort<NT>(sortbuf, P2);
+    __syncthreads();                       // tot is read: red becomes the select's scratch
     float w = NAN;
     if (n > 0) {
-        double pos = (double)quantile * (double)(n - 1);
-        int lo = (int)floor(pos);
-        if (lo >= n - 1) w = sortbuf[n - 1];
-        else w = (float)((double)sortbuf[lo] + (pos - lo) * ((double)sortbuf[lo + 1] - (double)sortbuf[lo]));
+        int* hist = reinterpret_cast<int*>(red);
+        const double pos = (double)quantile * (double)(n - 1);
+        const int lo = (int)floor(pos);
+        const uint32_t klo = block_select_key<NT>(sortbuf, p, lo, hist);
+        const float vlo = key_value(klo);
+        if (lo >= n - 1) {
+            w = vlo;
+        } else {
+            int cle;
+            uint32_t knext;
+            block_next_key<NT>(sortbuf, p, klo, hist, &cle, &knext);
+            const float vhi = cle >= lo + 2 ? vlo : key_value(knext);
+            w = (float)((double)vlo + (pos - lo) * ((double)vhi - (double)vlo));
+        }
     }
     __syncthreads();
     float nobj = 0.0f;

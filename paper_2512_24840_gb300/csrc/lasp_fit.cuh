@@ -82,7 +82,7 @@ struct FitSmem {
         gsg = o;  o += TAPBUF;
         phi = o;  o += round32(K);          // sized by the table: the SM's L1 keeps the rest
         dphi = o; o += DPS * round32(K);
-        red = o;  o += (NT / 32) * nv_max;
+        red = o;  o += (NT / 32) * nv_max > PREP_RED ? (NT / 32) * nv_max : PREP_RED;
         out = o;  o += 2 * nv_max + 16;
         ring = o; o += WINMAX;
         total = o;
@@ -91,7 +91,7 @@ struct FitSmem {
 
 __host__ inline size_t fit_smem_bytes(int p, int H, int n_model, int NT, int D, int K) {
     FitSmem s(p, H, n_model, NT, D, K);
-    size_t sort_end = (size_t)s.Fp + next_pow2(p);
+    size_t sort_end = (size_t)s.Fp + p;         // the preprocessing's select buffer
     return 4 * ((size_t)s.total > sort_end ? (size_t)s.total : sort_end);
 }
 

@@ -75,7 +75,7 @@ __host__ inline size_t fit_multi_smem_bytes(int p, int H, int n_model, int NT, i
 // w into wq, and the final result of spectra with too few usable pixels
 // (status LASP_ST_NODATA, as fit_kernel writes it).  Shared memory:
 // fit_prep_smem_bytes.
-__host__ __device__ inline int fit_prep_smem_floats(int p, int NT) { return next_pow2(p) + (NT / 32) * 2 + 8; }
+__host__ __device__ inline int fit_prep_smem_floats(int p) { return ((p + 3) & ~3) + PREP_RED; }
 
 template <int NT, int D>
 __global__ void __launch_bounds__(NT) fit_prep_kernel(const FitParams P, const MultiWs Wk) {
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(NT) fit_prep_kernel(const FitParams P, const M
     const size_t row = (size_t)i * p;
     float w, imean;
     const int n_obj = prep_spectrum<NT>(P.flux + row, P.ivar + row, P.good + row, p, P.O.edge_px,
-                                        P.O.quantile, yr, wr, sm, sm + next_pow2(p), &w, &imean);
+                                        P.O.quantile, yr, wr, sm, sm + ((p + 3) & ~3), &w, &imean);
     for (int q = p + tid; q < Wk.ldw; q += NT) {
         yr[q] = 0.0f;
         wr[q] = 0.0f;

@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(NT) k0_prep(const Grp G, const int32_t* __rest
     float* y = sm;
     float* W = sm + pa;
     float* sortbuf = sm + 2 * pa;
-    float* red = sortbuf + next_pow2(p);
+    float* red = sortbuf + pa;
     const size_t row = (size_t)i * p;
     float w, imean;
     const int n_obj = prep_spectrum<NT>(G.flux + row, G.ivar + row, G.good + row, p, G.O.edge_px,
@@ -898,7 +898,7 @@ int run_grouped(Grp& G, const TcImages& tc, cudaStream_t st, int* launches) {
     // K0
     {
         const int pa = (M.n_pix + 3) & ~3;
-        const size_t smem = 4 * ((size_t)2 * pa + next_pow2(M.n_pix) + (NT / 32) * 4 + 16);
+        const size_t smem = 4 * ((size_t)3 * pa + PREP_RED);
         int e = cuda_rc(cudaFuncSetAttribute(k0_prep<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         if (e) return e;
         k0_prep<NT><<<N, NT, smem, st>>>(G, nullptr);
@@ -1085,7 +1085,7 @@ int pool_setup(GrpPool* P) {
     const TcImages& tc = P->tc;
     const int N = G.N;
     const int pa = (M.n_pix + 3) & ~3;
-    const size_t smem0 = 4 * ((size_t)2 * pa + next_pow2(M.n_pix) + (NT / 32) * 4 + 16);
+    const size_t smem0 = 4 * ((size_t)3 * pa + PREP_RED);
     const size_t smem1 = 4 * TC_TILE_BYTES + 1024;
     const size_t smem3 = K3_STAGES * (2 * TC_TILE_BYTES + 2 * TC_BK_CHUNK_BYTES) + 1024;
     const RestSmem RS(M.n_pix, M.pad, M.n_model, NT, D);
@@ -1097,7 +1097,7 @@ int pool_setup(GrpPool* P) {
     if (e) return e;
     P->admit = [](GrpPool* Q, int count, const int32_t* idx, cudaStream_t st) -> int {
         const int pq = (Q->G.M.n_pix + 3) & ~3;
-        const size_t sm0 = 4 * ((size_t)2 * pq + next_pow2(Q->G.M.n_pix) + (NT / 32) * 4 + 16);
+        const size_t sm0 = 4 * ((size_t)3 * pq + PREP_RED);
         k0_prep<NT><<<count, NT, sm0, st>>>(Q->G, idx);
         return cuda_rc(cudaGetLastError());
     };

@@ -56,7 +56,7 @@ int launch_fit_multi(const FitParams& P, cudaStream_t st) {
     const int p = P.M.n_pix, H = P.M.pad, nm = P.M.n_model;
     const int NT = p <= 16 * 256 ? 256 : 512;
     const size_t smem = fit_multi_smem_bytes(p, H, nm, NT, D, P.M.K, S);
-    const size_t smem_prep = 4 * (size_t)fit_prep_smem_floats(p, NT);
+    const size_t smem_prep = 4 * (size_t)fit_prep_smem_floats(p);
     if (P.S.x || smem > 227 * 1024 || smem_prep > 227 * 1024) return launch_fit<D>(P, st);
     void (*kern)(const FitParams, const MultiWs) =
         NT == 256 ? fit_multi_kernel<256, D, S> : fit_multi_kernel<512, D, S>;

@@ -36,7 +36,7 @@ struct LmParams {
 __host__ inline size_t lm_smem_bytes(int p, int H, int n_model, int NT) {
     size_t fl = (size_t)2 * ((p + 3) & ~3) + 4 * (size_t)((n_model + 3) & ~3) + 3 * 96 + (1 + DPS) * KROWS +
                 (size_t)(NT / 32) * 48 + 256;
-    size_t sortb = (size_t)2 * ((p + 3) & ~3) + next_pow2(p);
+    size_t sortb = (size_t)3 * ((p + 3) & ~3);
     return 4 * (fl > sortb ? fl : sortb);
 }
 

@@ -201,7 +201,7 @@ struct ErrParams {
 __host__ inline size_t err_smem_bytes(int p, int H, int n_model, int NT) {
     size_t fl = (size_t)2 * ((p + 3) & ~3) + 4 * (size_t)((n_model + 3) & ~3) + 3 * 96 + (1 + DPS) * KROWS +
                 (size_t)(NT / 32) * 48 + 256;
-    size_t sortb = (size_t)2 * ((p + 3) & ~3) + next_pow2(p);
+    size_t sortb = (size_t)3 * ((p + 3) & ~3);
     return 4 * (fl > sortb ? fl : sortb);
 }
 
@@ -256,19 +256,38 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) errors_kernel(const Err
     const int h = s_h;
     int k0, k1;
     active_rows(M, P.theta[5 * i], k0, k1);
-    for (int mm = tid; mm < nm; mm += NT) {
-        float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+    // F' and its three basis derivatives: 16 consecutive model pixels per thread,
+    // the table rows (padded to 16 floats) from L2 with 256-bit loads, two rows
+    // in flight, each load feeding the four contractions
+    for (int m0 = tid * 16; m0 < nm; m0 += NT * 16) {
+        float a[4][16];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int r = 0; r < 16; ++r) a[q][r] = 0.0f;
+        const float* crow = M.Cp + m0;
+#pragma unroll 2
         for (int k = k0; k < k1; ++k) {
-            const float c = __ldg(M.C + (size_t)k * nm + mm);
-            a0 = fmaf(phi[k], c, a0);
-            a1 = fmaf(dphi[DPS * k + 0], c, a1);
-            a2 = fmaf(dphi[DPS * k + 1], c, a2);
-            a3 = fmaf(dphi[DPS * k + 2], c, a3);
+            const float* ck = crow + (size_t)k * M.ldc;
+            const float pk = phi[k], d0 = dphi[DPS * k + 0], d1 = dphi[DPS * k + 1], d2 = dphi[DPS * k + 2];
+#pragma unroll
+            for (int h8 = 0; h8 < 2; ++h8) {
+                float c[8];
+                ldg8(ck + 8 * h8, c);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    a[0][8 * h8 + e] = fmaf(pk, c[e], a[0][8 * h8 + e]);
+                    a[1][8 * h8 + e] = fmaf(d0, c[e], a[1][8 * h8 + e]);
+                    a[2][8 * h8 + e] = fmaf(d1, c[e], a[2][8 * h8 + e]);
+                    a[3][8 * h8 + e] = fmaf(d2, c[e], a[3][8 * h8 + e]);
+                }
+            }
         }
-        Fp[mm] = a0;
-        Fp[na + mm] = a1;
-        Fp[2 * na + mm] = a2;
-        Fp[3 * na + mm] = a3;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int r = 0; r < 16; ++r)
+                if (m0 + r < nm) Fp[q * na + m0 + r] = a[q][r];
     }
     __syncthreads();
     // F'' and its five derivatives per owned pixel (registers)

@@ -220,6 +220,38 @@ def test_fit_loss_and_weight_outputs(lasp):
     np.testing.assert_allclose(H(out["cont"]), ref["b"], rtol=1e-3, atol=1e-4)
 
 
+@pytest.mark.parametrize("q", [0.0, 0.25, 0.5, 0.9, 1.0])
+def test_weight_quantile_exact(lasp, q):
+    """w, the flux quantile that scales Eq. 9's data, interpolates between two
+    order statistics of the used pixels.  The kernels select those two values
+    (radix select) where the oracle sorts, so w is float32 of the oracle's w
+    exactly, including ties, negative values, zeros of both signs, spectra of
+    one repeated value and masked or zero-ivar pixels.  Spectra whose w is not
+    positive stop with LASP_ST_NODATA and still report w."""
+    grid = S.SMALL
+    n, p = 7, grid.n_pix
+    rng = np.random.default_rng(77)
+    flux = rng.normal(1.0, 0.3, (n, p)).astype(np.float32)
+    flux[1] = np.round(flux[1] * 4.0) / 4.0          # heavy ties
+    flux[2] -= 1.0                                   # about half negative
+    flux[3, 0::3] = 0.0
+    flux[3, 1::3] = -0.0                             # zeros of both signs
+    flux[4] = 2.5                                    # one repeated value
+    flux[5] = rng.lognormal(0.0, 2.0, p)             # a wide range of exponents
+    ivar = np.ones((n, p), np.float32)
+    good = np.ones((n, p), np.uint8)
+    good[6, : p // 2] = 0
+    ivar[6, p // 2: p // 2 + 17] = 0.0               # masked and zero-ivar pixels
+    theta0 = np.asarray(S.draw_batch(grid, n, 78)["theta0"], np.float32)
+    ip = interp(lasp, grid)
+    out = ip.fit(T(flux), T(ivar), T(good, torch.uint8), T(theta0), max_steps=0, quantile=q)
+    got = H(out["weight"])
+    for i in range(n):
+        # the options carry the quantile as float32: the oracle gets that value
+        _, _, w, _ = O.prep(flux[i], ivar[i], good[i], quantile=float(np.float32(q)))
+        assert got[i] == np.float32(w), (i, got[i], w)
+
+
 def test_batch_invariance_bitwise(lasp):
     """A spectrum's result does not depend on the batch it is fitted in."""
     grid = S.LAMOST
