@@ -215,19 +215,24 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
             }
         if (!any) break;
 
-        // ---- a3 for every lane: F'_s = phi_s C (Eq. 1), each table value loaded once
+        // ---- a3 for every lane: F'_s = phi_s C (Eq. 1), each table value loaded once.
+        // Adjacent model pixels go through one packed FMA (__ffma2_rn: two IEEE
+        // fmas, the same results as fmaf), halving the FMA instructions.
         if (own_mod) {
-            float acc[S][PPT];
+            float2 acc[S][PPT / 2];
 #pragma unroll
             for (int s = 0; s < S; ++s)
 #pragma unroll
-                for (int r = 0; r < PPT; ++r) acc[s][r] = 0.0f;
+                for (int r = 0; r < PPT / 2; ++r) acc[s][r] = make_float2(0.0f, 0.0f);
             const float* crow = M.Cp + j0;
 #pragma unroll 2
             for (int k = kb; k < ke; ++k) {
-                float pk[S];
+                float2 pk[S];
 #pragma unroll
-                for (int s = 0; s < S; ++s) pk[s] = sm[s * L.lane + L.phi + k];
+                for (int s = 0; s < S; ++s) {
+                    const float v = sm[s * L.lane + L.phi + k];
+                    pk[s] = make_float2(v, v);
+                }
                 const float* ck = crow + (size_t)k * M.ldc;
 #pragma unroll
                 for (int q = 0; q < PPT / 8; ++q) {
@@ -236,7 +241,8 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
 #pragma unroll
                     for (int s = 0; s < S; ++s)
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) acc[s][8 * q + e] = fmaf(pk[s], c[e], acc[s][8 * q + e]);
+                        for (int e = 0; e < 4; ++e)
+                            acc[s][4 * q + e] = __ffma2_rn(pk[s], make_float2(c[2 * e], c[2 * e + 1]), acc[s][4 * q + e]);
                 }
             }
 #pragma unroll
@@ -244,7 +250,7 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
                 float* Fp = sm + s * L.lane + L.Fp;
 #pragma unroll
                 for (int r = 0; r < PPT; ++r)
-                    if (j0 + r < nm) Fp[skew(j0 + r + 16)] = acc[s][r];
+                    if (j0 + r < nm) Fp[skew(j0 + r + 16)] = (r & 1) ? acc[s][r >> 1].y : acc[s][r >> 1].x;
             }
         }
         // F' pads (model pixels [-16, 0) and [n_model, n_model + 16)) over the last delta
@@ -469,6 +475,15 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
                         for (int r = 0; r < PPT; ++r) dfp[s][r] = fmaf(gg[e], win[r + e], dfp[s][r]);
                 }
             }
+            // lanes in pairs: one packed FMA carries the dot products of lanes
+            // 2u and 2u + 1 (each the same sequence of fmas as alone)
+            constexpr int SP = (S + 1) / 2;
+            float2 dpair[SP][PPT];
+#pragma unroll
+            for (int u = 0; u < SP; ++u)
+#pragma unroll
+                for (int r = 0; r < PPT; ++r)
+                    dpair[u][r] = make_float2(dfp[2 * u][r], 2 * u + 1 < S ? dfp[2 * u + 1][r] : 0.0f);
             const float* crow = M.Cp + j0;
 #pragma unroll 2
             for (int k = kb; k < ke; ++k) {
@@ -482,14 +497,20 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
                     for (int e = 0; e < 8; ++e) c[8 * q + e] = c8[e];
                 }
 #pragma unroll
-                for (int s = 0; s < S; ++s) {
-                    float a = 0.0f;
+                for (int u = 0; u < SP; ++u) {
+                    float2 a2 = make_float2(0.0f, 0.0f);
 #pragma unroll
-                    for (int r = 0; r < PPT; ++r) a = fmaf(dfp[s][r], c[r], a);
-                    const float4 dk = reinterpret_cast<const float4*>(sm + s * L.lane + L.dphi)[k];
-                    bph[s][0] = fmaf(dk.x, a, bph[s][0]);
-                    bph[s][1] = fmaf(dk.y, a, bph[s][1]);
-                    bph[s][2] = fmaf(dk.z, a, bph[s][2]);
+                    for (int r = 0; r < PPT; ++r) a2 = __ffma2_rn(dpair[u][r], make_float2(c[r], c[r]), a2);
+#pragma unroll
+                    for (int h2 = 0; h2 < 2; ++h2) {
+                        const int s = 2 * u + h2;
+                        if (s >= S) continue;
+                        const float a = h2 ? a2.y : a2.x;
+                        const float4 dk = reinterpret_cast<const float4*>(sm + s * L.lane + L.dphi)[k];
+                        bph[s][0] = fmaf(dk.x, a, bph[s][0]);
+                        bph[s][1] = fmaf(dk.y, a, bph[s][1]);
+                        bph[s][2] = fmaf(dk.z, a, bph[s][2]);
+                    }
                 }
             }
         }
