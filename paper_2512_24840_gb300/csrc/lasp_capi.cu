@@ -319,11 +319,10 @@ int lasp_fit_batch(lasp_interp h, const lasp_batch* b, const lasp_fit_opts* o, l
     P.cont = r->cont_coeff;
     P.weight = r->weight;
     cudaStream_t st = (cudaStream_t)stream;
-    // Clean fits keep their mask in the one-spectrum kernel's shared memory;
-    // the rest run several spectra per CTA (the same result, bit for bit)
+    // several spectra per CTA (the same result as fit_kernel, bit for bit)
     int e = dispatch_deg(o->legendre_deg, [&](auto dd) {
         constexpr int D = decltype(dd)::value;
-        return o->clean ? launch_fit<D>(P, st) : launch_fit_multi<D>(P, st);
+        return launch_fit_multi<D>(P, st);
     });
     g_last_launches = e ? 0 : 1;
     return e;

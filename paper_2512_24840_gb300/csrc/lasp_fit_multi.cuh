@@ -20,10 +20,11 @@
 // pixels; at two CTAs per SM (eight spectra in flight) the table traffic per
 // spectrum-step is a quarter of fit_kernel's.  Measured on the 4096 x 3909
 // batch (fit_kernel: 30.8 ms): four lanes at two CTAs per SM 23.6 ms, three
-// lanes 24.1 ms, two lanes at three CTAs per SM 24.6 ms.  Clean fits and
-// resumable slots stay on fit_kernel.
+// lanes 24.1 ms, two lanes at three CTAs per SM 24.6 ms.  A lane's Clean mask
+// (stage 6) lives in its W row; resumable slots stay on fit_kernel.
 #pragma once
 
+#include "lasp_clean.cuh"
 #include "lasp_fit.cuh"
 
 namespace lasp {
@@ -31,6 +32,7 @@ namespace lasp {
 struct MultiWs {
     float* yw;      // N rows of 2 ldw floats: y, then W; zero beyond p
     float* wq;      // N: the weight w of each spectrum, NaN where preprocessing decided the fit
+    float* im;      // N: the mean inverse variance of each spectrum (Clean's base weights)
     int ldw;        // row stride: p rounded up to 16
     int* next;      // index of the next spectrum to take (starts at 0)
 };
@@ -94,7 +96,10 @@ __global__ void __launch_bounds__(NT) fit_prep_kernel(const FitParams P, const M
         wr[q] = 0.0f;
     }
     const bool nodata = n_obj < NB + 5 || !(w > 0.0f) || !isfinite(w);
-    if (tid == 0) Wk.wq[i] = nodata ? NAN : w;
+    if (tid == 0) {
+        Wk.wq[i] = nodata ? NAN : w;
+        Wk.im[i] = imean;
+    }
     if (!nodata) return;
     if (tid < 5) {
         const float xx = (P.theta0[5 * i + tid] - M.plo[tid]) / M.phalf[tid] - 1.0f;
@@ -137,7 +142,8 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
     float* red = sm + L.red;
     float* out = sm + L.out;
     __shared__ float s_x[S][5], s_b[S][NB], s_w[S];
-    __shared__ int s_h[S], s_k[S][2], s_i[S], s_need[S], s_next;
+    __shared__ int s_h[S], s_k[S][2], s_i[S], s_need[S], s_next, s_cln[S];
+    __shared__ double s_redd[3 * (NT / 32)], s_tot[3];
 
     // Adam and stop-rule state of lane s: registers of warp s (parameter k on
     // its lane k < 5; step count, ring slot and rule state on every lane).
@@ -148,6 +154,7 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
     if (tid < S) {
         s_i[tid] = -1;
         s_need[tid] = 1;
+        s_cln[tid] = -1;
     }
     for (int q = tid; q < S * L.lane; q += NT) sm[q] = 0.0f;
     __syncthreads();
@@ -581,14 +588,131 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
                     xk = fminf(1.0f, fmaxf(-1.0f, xk - step * mk / denom));
                     s_x[s][lane] = xk;
                 }
-                ++t;
                 __syncwarp();
-                const int hn = warp_prepare_step(M, s_x[s], base + L.phi, base + L.dphi, base + L.g,
-                                                 base + L.gmu, base + L.gsg, s_k[s]);
-                if (lane == 0) s_h[s] = hn;
+                if (clean_step(P.O, t)) {
+                    // the Clean update below needs the basis and taps of x_t
+                    if (lane == 0) s_cln[s] = t;
+                } else {
+                    const int hn = warp_prepare_step(M, s_x[s], base + L.phi, base + L.dphi, base + L.g,
+                                                     base + L.gmu, base + L.gsg, s_k[s]);
+                    if (lane == 0) s_h[s] = hn;
+                }
+                ++t;
             }
         }
         __syncthreads();
+
+        // ---- stage 6 Clean update of every lane that evaluated a Clean step,
+        // from the residual at x_t (the code of fit_kernel's update).  The lane's
+        // F' of x_t was overwritten by its delta, so one table pass recomputes
+        // it; two other lanes' buffers, free between steps, hold r and m.
+        if constexpr (S >= 3) {
+            if (P.O.clean) {
+#pragma unroll 1
+                for (int s = 0; s < S; ++s) {
+                    const int tc = s_cln[s];
+                    if (tc < 0) continue;
+                    const int i = s_i[s];
+                    float* base = sm + s * L.lane;
+                    float* Fp = base + L.Fp;
+                    float* Rb = sm + ((s + 1) % S) * L.lane + L.Fp;
+                    float* Mb = sm + ((s + 2) % S) * L.lane + L.Fp;
+                    if (own_mod) {
+                        float acc[PPT];
+#pragma unroll
+                        for (int r = 0; r < PPT; ++r) acc[r] = 0.0f;
+                        const float* crow = M.Cp + j0;
+#pragma unroll 2
+                        for (int k = s_k[s][0]; k < s_k[s][1]; ++k) {
+                            const float pk = base[L.phi + k];
+                            const float* ck = crow + (size_t)k * M.ldc;
+#pragma unroll
+                            for (int q = 0; q < PPT / 8; ++q) {
+                                float c[8];
+                                ldg8(ck + 8 * q, c);
+#pragma unroll
+                                for (int e = 0; e < 8; ++e) acc[8 * q + e] = fmaf(pk, c[e], acc[8 * q + e]);
+                            }
+                        }
+#pragma unroll
+                        for (int r = 0; r < PPT; ++r)
+                            if (j0 + r < nm) Fp[skew(j0 + r + 16)] = acc[r];
+                    }
+                    if (tid < 32) Fp[skew((tid < 16 ? tid - 16 : nm + tid - 16) + 16)] = 0.0f;
+                    __syncthreads();
+                    const int h = s_h[s];
+                    const int nblk = (2 * h + 1 + TB - 1) / TB;
+                    const float* g = base + L.g;
+                    float fpp[PPT];
+#pragma unroll
+                    for (int r = 0; r < PPT; ++r) fpp[r] = 0.0f;
+                    if (own_pix) {
+                        for (int bk = 0; bk < nblk; ++bk) {
+                            const int s0 = -h + bk * TB;
+                            float gg[TB], win[PPT + TB - 1];
+#pragma unroll
+                            for (int e = 0; e < TB; ++e) gg[e] = g[s0 + e + H];
+                            const int wb0 = j0 + H - s0 - (TB - 1) + 16;
+#pragma unroll
+                            for (int q = 0; q < PPT + TB - 1; ++q) win[q] = Fp[skew(wb0 + q)];
+#pragma unroll
+                            for (int e = 0; e < TB; ++e)
+#pragma unroll
+                                for (int r = 0; r < PPT; ++r) fpp[r] = fmaf(gg[e], win[r - e + TB - 1], fpp[r]);
+                        }
+                    }
+                    const float* yr = Wk.yw + (size_t)i * 2 * Wk.ldw;
+                    float* wr = Wk.yw + (size_t)i * 2 * Wk.ldw + Wk.ldw;
+                    const float imean = Wk.im[i], wgt = s_w[s];
+                    const size_t row = (size_t)i * p;
+                    float bl[NB];
+#pragma unroll
+                    for (int a = 0; a < NB; ++a) bl[a] = s_b[s][a];
+                    float wbv[PPT];
+                    uint32_t used = 0;
+#pragma unroll
+                    for (int r = 0; r < PPT; ++r) {
+                        const int j = j0 + r;
+                        wbv[r] = 0.0f;
+                        if (j < p) {
+                            const float f = P.flux[row + j], iv = P.ivar[row + j];
+                            const bool use = P.good[row + j] && iv > 0.0f && isfinite(f) && isfinite(iv);
+                            const bool edge = j < P.O.edge_px || j >= p - P.O.edge_px;
+                            const float wb = (use && !edge && wgt > 0.0f) ? iv / imean : 0.0f;
+                            float Pl[NB];
+                            legendre<D>(fmaf((float)j, xstep, -1.0f), Pl);
+                            float c = 0.0f;
+#pragma unroll
+                            for (int a = 0; a < NB; ++a) c = fmaf(bl[a], Pl[a], c);
+                            const float model = c * fpp[r];
+                            const float sw = sqrtf(wb);
+                            Rb[skew(j + L.dofs)] = sw * (yr[j] - model);
+                            Mb[skew(j + 16)] = sw * model;
+                            wbv[r] = wb;
+                            if (wr[j] > 0.0f) used |= 1u << r;
+                        }
+                    }
+                    __syncthreads();
+                    const int upd = tc / P.O.clean_every;
+                    const uint32_t keep = cta_clean_mask<NT, PPT>(p, j0, Rb, L.dofs, Mb, 16, used,
+                                                                  upd == 1 ? 0.5f : 0.2f,
+                                                                  reinterpret_cast<uint8_t*>(Mb), s_redd,
+                                                                  s_tot, nullptr);
+#pragma unroll
+                    for (int r = 0; r < PPT; ++r)
+                        if (j0 + r < p) wr[j0 + r] = ((keep >> r) & 1u) ? wbv[r] : 0.0f;
+                    if (warp == s) {
+                        const int hn = warp_prepare_step(M, s_x[s], base + L.phi, base + L.dphi, base + L.g,
+                                                         base + L.gmu, base + L.gsg, s_k[s]);
+                        if (lane == 0) {
+                            s_h[s] = hn;
+                            s_cln[s] = -1;
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+        }
     }
 }
 

@@ -47,8 +47,9 @@ constexpr int FIT_LANES = 4;
 
 // One-shot batch fit: fit_prep_kernel (one CTA per spectrum), then FIT_LANES
 // spectra per CTA on a persistent grid of as many CTAs as the SMs hold.  The
-// workspace (spectrum counter, w and the y, W rows of every spectrum: about
-// 8 p bytes a spectrum) is taken from the stream-ordered pool for the launch.
+// workspace (spectrum counter, w, mean ivar and the y, W rows of every
+// spectrum: about 8 p bytes a spectrum) is taken from the stream-ordered pool
+// for the launch.
 // Falls back to fit_kernel where the lanes' buffers or the workspace do not fit.
 template <int D>
 int launch_fit_multi(const FitParams& P, cudaStream_t st) {
@@ -57,7 +58,8 @@ int launch_fit_multi(const FitParams& P, cudaStream_t st) {
     const int NT = p <= 16 * 256 ? 256 : 512;
     const size_t smem = fit_multi_smem_bytes(p, H, nm, NT, D, P.M.K, S);
     const size_t smem_prep = 4 * (size_t)fit_prep_smem_floats(p);
-    if (P.S.x || smem > 227 * 1024 || smem_prep > 227 * 1024) return launch_fit<D>(P, st);
+    // resumable slots, and Clean with too few lanes for its scratch, stay on fit_kernel
+    if (P.S.x || (P.O.clean && S < 3) || smem > 227 * 1024 || smem_prep > 227 * 1024) return launch_fit<D>(P, st);
     void (*kern)(const FitParams, const MultiWs) =
         NT == 256 ? fit_multi_kernel<256, D, S> : fit_multi_kernel<512, D, S>;
     void (*prep)(const FitParams, const MultiWs) =
@@ -75,15 +77,16 @@ int launch_fit_multi(const FitParams& P, cudaStream_t st) {
     MultiWs W;
     W.ldw = (p + 15) & ~15;
     const size_t rows = (size_t)P.N * 2 * W.ldw * sizeof(float);
-    const size_t wq = ((size_t)P.N * sizeof(float) + 255) & ~(size_t)255;
+    const size_t wq = ((size_t)P.N * sizeof(float) + 255) & ~(size_t)255;   // w, then the mean ivar
     void* ws = nullptr;
-    if (cudaMallocAsync(&ws, 256 + wq + rows, st) != cudaSuccess) {
+    if (cudaMallocAsync(&ws, 256 + 2 * wq + rows, st) != cudaSuccess) {
         cudaGetLastError();
         return launch_fit<D>(P, st);          // no room for the workspace: one spectrum per CTA
     }
     W.next = static_cast<int*>(ws);
     W.wq = reinterpret_cast<float*>(static_cast<char*>(ws) + 256);
-    W.yw = reinterpret_cast<float*>(static_cast<char*>(ws) + 256 + wq);
+    W.im = reinterpret_cast<float*>(static_cast<char*>(ws) + 256 + wq);
+    W.yw = reinterpret_cast<float*>(static_cast<char*>(ws) + 256 + 2 * wq);
     e = cuda_rc(cudaMemsetAsync(ws, 0, 256, st));
     if (!e) {
         prep<<<P.N, NT, smem_prep, st>>>(P, W);
