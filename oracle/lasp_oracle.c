@@ -28,6 +28,7 @@
 #endif
 
 #define C_KMS 299792.458
+#define NB_MAX 9               /* Legendre continuum terms supported: degree <= 8 */
 
 int orc_max_threads(void) {
 #ifdef _OPENMP
@@ -286,7 +287,7 @@ int orc_prep(int n_pix, const float* flux, const float* ivar, const unsigned cha
 /* Cholesky solve of the (n x n) SPD system A z = r.  Returns 0 if A is not
  * numerically positive definite. */
 static int chol_solve(int n, const double* A, const double* r, double* z) {
-    double L[64], t[8];
+    double L[NB_MAX * NB_MAX], t[NB_MAX];
     for (int i = 0; i < n; ++i) {
         for (int j = 0; j <= i; ++j) {
             double s = A[i * n + j];
@@ -316,7 +317,7 @@ static int chol_solve(int n, const double* A, const double* r, double* z) {
 static int solve_continuum(int p, int D, const double* P, const double* Fpp, const double* y,
                            const double* W, double* b) {
     int n = D + 1;
-    double G[64], r[8];
+    double G[NB_MAX * NB_MAX], r[NB_MAX];
     for (int a = 0; a < n; ++a) {
         r[a] = 0.0;
         for (int c = 0; c < n; ++c) G[a * n + c] = 0.0;
@@ -335,8 +336,8 @@ unsigned orc_eval(const orc_model* M, const double* y, const double* W, const do
                   double* loss, double* grad_x, double* b_out, double* eps_out, double* cont_out) {
     int H = M->pad, p = M->n_pix, nm = p + 2 * H, D = M->deg;
     unsigned st = 0;
-    double th[5], b[8];
-    for (int d = 0; d < 8; ++d) b[d] = NAN;
+    double th[5], b[NB_MAX];
+    for (int d = 0; d < NB_MAX; ++d) b[d] = NAN;
     double* Fp = malloc(sizeof(double) * nm);
     double* Fpp = malloc(sizeof(double) * p);
     double* g = malloc(sizeof(double) * (2 * H + 1));
@@ -438,7 +439,7 @@ static void fit_one(const orc_model* M, const orc_opts* O, const float* flux, co
     double* eps = malloc(sizeof(double) * p);
     unsigned char* keep = malloc(p);
     double* hist = malloc(sizeof(double) * (O->max_steps + 1));
-    double w, x[5], m[5] = {0}, v[5] = {0}, g[5], b[8];
+    double w, x[5], m[5] = {0}, v[5] = {0}, g[5], b[NB_MAX];
     int n_obj = orc_prep(p, flux, ivar, good, O->quantile, O->edge_px, y, W, &w);
     for (int k = 0; k < 5; ++k) theta[k] = theta0[k];
     *loss = NAN;
@@ -596,7 +597,7 @@ void orc_fit_trajectory(const orc_model* M, const orc_opts* O, const float* flux
 /* Weighted residual r = sqrt(W) eps at physical theta with b re-solved. */
 static int weighted_resid(const orc_model* M, const double* y, const double* W,
                           const double* th, double* r) {
-    double x[5], l, g[5], b[8];
+    double x[5], l, g[5], b[NB_MAX];
     int p = M->n_pix;
     double* eps = malloc(sizeof(double) * p);
     orc_x_from_phys(M, th, x);
@@ -785,7 +786,7 @@ int orc_clean_mask(int p, const float* r, const float* m, const unsigned char* u
 /* S(x) and the weighted residual r = sqrt(W) eps at x (continuum re-solved). */
 static int lm_eval(const orc_model* M, const double* y, const double* W, const double* x, double* S,
                    double* r) {
-    double l, g[5], b[8];
+    double l, g[5], b[NB_MAX];
     int p = M->n_pix;
     double* eps = malloc(sizeof(double) * p);
     unsigned st = orc_eval(M, y, W, x, &l, g, b, eps, NULL);

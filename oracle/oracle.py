@@ -113,6 +113,8 @@ class Model:
         self.K = self.exps.shape[0]
         assert self.C.shape == (self.K, n_pix + 2 * pad)
         self.dln, self.pad, self.n_pix, self.deg = float(dln), int(pad), int(n_pix), int(deg)
+        if not 0 <= self.deg <= 8:
+            raise ValueError("Legendre continuum degree must be 0..8")
         self.blo, self.bhi = _f64(blo), _f64(bhi)
         self.plo, self.phi = _f64(plo), _f64(phi)
         self.reg_K = None if reg_K is None else [int(k) for k in reg_K]

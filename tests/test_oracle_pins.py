@@ -150,15 +150,20 @@ def test_broadening_moments_add():
 
 # --------------------------------------------------------- continuum (Eq. 6)
 
-def test_legendre_matches_numpy():
-    p, D = 1024, DEG
+@pytest.mark.parametrize("D", [2, 4, 6, 8])
+def test_legendre_matches_numpy(D):
+    p = 1024
     x = -1.0 + 2.0 * np.arange(p) / p
     np.testing.assert_allclose(O.legendre(p, D), np.polynomial.legendre.legvander(x, D),
                                atol=1e-13)
 
 
-def test_wls_matches_lstsq_and_envelope():
+@pytest.mark.parametrize("DEG", [2, 4, 6, 8])
+def test_wls_matches_lstsq_and_envelope(DEG):
+    """Every continuum degree the CUDA path supports (degree 8 fills the
+    oracle's largest normal-equation buffers)."""
     M, d = observed(G, 3, 11, noise=True, snr=(20, 20), mask_frac=0.05)
+    M = oracle_model(G, deg=DEG)
     for i in range(3):
         y, W, w, _ = O.prep(d["flux"][i], d["ivar"][i], d["good"][i])
         x = O.x_from_phys(M, d["theta0"][i])
