@@ -230,13 +230,15 @@ typedef struct lasp_slots_s* lasp_slots;          /* opaque, library-owned */
  * staging copy of the observation buffers).  opts are copied.  Synchronous:
  * returns once the pool's device memory is initialised, so the first admit
  * may go on any stream, a non-blocking one included.
- * opts->precision LASP_PREC_FP32: the fused FP32 fit kernel steps the slots.
+ * opts->precision LASP_PREC_FP32: the fused FP32 fit kernel steps the slots,
+ * four per CTA; each slot also keeps its preprocessed y, W rows (8 bytes a
+ * pixel, n_pix rounded up to 16), written when the slot is admitted.
  * A tensor-core precision: the grouped pipeline runs over the slots (served
  * mixed precision; single-regime tables, Legendre degree 6; about 50 n_pix
  * more bytes per slot); its steps go in chunks of 8, so a step call's budget
  * is rounded up to a multiple of 8.  Clean (FP32 pools only): each slot keeps
- * its Clean mask in device memory between steps (n_pix / 8 bytes per slot), so
- * the updates fall on the same steps as in a one-shot fit.  The joint loss:
+ * its Clean mask in device memory between steps (in its W row), so the updates
+ * fall on the same steps as in a one-shot fit.  The joint loss:
  * LASP_EINVAL. */
 int lasp_slots_create(lasp_interp h, int n_slots, const lasp_fit_opts* opts, lasp_slots* out);
 void lasp_slots_free(lasp_slots s);
@@ -245,14 +247,23 @@ void lasp_slots_free(lasp_slots s);
  * 0 <= idx < n_slots).  flux, ivar: host count x n_pix float32; good: host
  * count x n_pix uint8; theta0: host count x 5 float32.  The rows are copied
  * host -> device on `stream` (pinned host memory makes the copy asynchronous)
- * and scattered into the slots, which become LASP_ST_RUNNING.  The host
- * buffers must stay unchanged until the stream passes this call. */
+ * and scattered into the slots, which become LASP_ST_RUNNING; an FP32 pool
+ * also preprocesses them there (a spectrum with too few usable pixels gets its
+ * final LASP_ST_NODATA result at once).  The host buffers must stay unchanged
+ * until the stream passes this call. */
 int lasp_slots_admit(lasp_slots s, int count, const int32_t* slot_idx, const float* flux,
                      const float* ivar, const uint8_t* good, const float* theta0, void* stream);
 
 /* Run at most `budget` (>= 1) Adam steps on every running slot (one launch of
- * the fused fit kernel; slots that stop write their results). */
+ * the fused fit kernel, whose lanes take the running slots in turn; slots that
+ * stop write their results). */
 int lasp_slots_step(lasp_slots s, int budget, void* stream);
+
+/* As lasp_slots_step, with the caller's count of running slots: the launch is
+ * sized to it, so a lightly used pool leaves the other SMs free (for another
+ * pool's step on another stream).  Any n_running >= 1 gives the same results;
+ * the true count gives the best schedule.  LASP_EINVAL for n_running < 1. */
+int lasp_slots_step_running(lasp_slots s, int budget, int n_running, void* stream);
 
 /* Copy every slot's theta (n_slots x 5), loss, steps, status and weight to
  * host buffers (any may be NULL) on `stream`. */

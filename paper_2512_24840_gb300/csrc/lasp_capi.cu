@@ -463,7 +463,46 @@ struct lasp_slots_s {
     int32_t* steps;
     uint32_t* status;
     lasp::GrpPool* grp = nullptr;   // tensor-core precisions: the grouped pipeline over the slots
+    // FP32 pools on fit_multi_kernel: y, W rows of 2 ldw floats per slot (Clean
+    // masks included) and the lanes' slot counter; otherwise fit_kernel
+    bool multi = false;
+    int ldw = 0;
+    float* yw = nullptr;
+    int* ctr = nullptr;
+    int* list = nullptr;             // the running slots of a step
 };
+
+namespace {
+
+lasp::FitParams slot_params(const lasp_slots_s* s) {
+    lasp::FitParams P{};
+    P.M = s->h->M;
+    P.O = to_dev(&s->opts);
+    P.N = s->n;
+    P.S = s->S;
+    P.flux = s->flux;
+    P.ivar = s->ivar;
+    P.good = s->good;
+    P.theta0 = s->theta0;
+    P.theta = s->theta;
+    P.loss = s->loss;
+    P.steps = s->steps;
+    P.status = s->status;
+    P.cont = s->cont;
+    P.weight = s->weight;
+    return P;
+}
+
+lasp::MultiWs slot_ws(const lasp_slots_s* s) {
+    lasp::MultiWs W{};
+    W.yw = s->yw;
+    W.ldw = s->ldw;
+    W.next = s->ctr;
+    W.list = s->list;
+    return W;
+}
+
+}  // namespace
 
 namespace lasp {
 int slots_n_pix(lasp_slots s) { return s ? s->h->M.n_pix : 0; }
@@ -478,7 +517,7 @@ void lasp_slots_free(lasp_slots s) {
     void* ptrs[] = {s->flux, s->ivar, s->theta0, s->good, s->f_st, s->iv_st, s->th_st, s->g_st,
                     s->idx_st, s->S.x, s->S.m, s->S.v, s->S.ring, s->S.prev, s->S.rise, s->S.t,
                     s->S.w, s->S.imean, s->S.cmask, s->theta, s->loss, s->cont, s->weight, s->steps,
-                    s->status};
+                    s->status, s->yw, s->ctr, s->list};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete s;
@@ -521,7 +560,17 @@ int lasp_slots_create(lasp_interp h, int n_slots, const lasp_fit_opts* o, lasp_s
     alloc(&s->S.t, n * 4);
     alloc(&s->S.w, n * 4);
     alloc(&s->S.imean, n * 4);
-    if (o->clean) alloc(&s->S.cmask, n * (size_t)((p + 15) / 16) * 2);
+    const lasp::ModelDev& M = h->M;
+    s->multi = o->precision == LASP_PREC_FP32 &&
+               fit_multi_slots_ok(M.n_pix, M.pad, M.n_model, M.K, o->legendre_deg);
+    if (s->multi) {
+        s->ldw = (int)((p + 15) & ~(size_t)15);
+        alloc(&s->yw, n * 2 * (size_t)s->ldw * 4);
+        alloc(&s->ctr, 256);
+        alloc(&s->list, n * 4);
+    } else if (o->clean) {
+        alloc(&s->S.cmask, n * (size_t)((p + 15) / 16) * 2);
+    }
     alloc(&s->theta, n * 5 * 4);
     alloc(&s->loss, n * 4);
     alloc(&s->cont, n * NB * 4);
@@ -567,33 +616,33 @@ int lasp_slots_admit(lasp_slots s, int count, const int32_t* slot_idx, const flo
         rc = grp_pool_admit(s->grp, count, s->idx_st, st);     // prep + join the active list
         g_last_launches = 2;
     }
+    if (!rc && s->multi) {
+        const FitParams P = slot_params(s);
+        const MultiWs W = slot_ws(s);
+        rc = dispatch_deg(s->opts.legendre_deg, [&](auto dd) {
+            constexpr int D = decltype(dd)::value;
+            return launch_fit_prep_slots<D>(P, W, s->idx_st, count, st);
+        });
+        g_last_launches = 2;
+    }
     return rc;
 }
 
 int lasp_slots_step(lasp_slots s, int budget, void* stream) {
+    return lasp_slots_step_running(s, budget, s ? s->n : 1, stream);
+}
+
+int lasp_slots_step_running(lasp_slots s, int budget, int n_running, void* stream) {
     g_last_launches = 0;
-    if (!s || budget < 1) return LASP_EINVAL;
+    if (!s || budget < 1 || n_running < 1) return LASP_EINVAL;
     if (s->grp) return grp_pool_step(s->grp, budget, (cudaStream_t)stream, &g_last_launches);
-    FitParams P{};
-    P.M = s->h->M;
-    P.O = to_dev(&s->opts);
-    P.N = s->n;
-    P.S = s->S;
+    FitParams P = slot_params(s);
     P.S.budget = budget;
-    P.flux = s->flux;
-    P.ivar = s->ivar;
-    P.good = s->good;
-    P.theta0 = s->theta0;
-    P.theta = s->theta;
-    P.loss = s->loss;
-    P.steps = s->steps;
-    P.status = s->status;
-    P.cont = s->cont;
-    P.weight = s->weight;
+    const MultiWs W = slot_ws(s);
     cudaStream_t st = (cudaStream_t)stream;
     int e = dispatch_deg(s->opts.legendre_deg, [&](auto dd) {
         constexpr int D = decltype(dd)::value;
-        return launch_fit<D>(P, st);
+        return s->multi ? launch_fit_multi_slots<D>(P, W, n_running, st) : launch_fit<D>(P, st);
     });
     g_last_launches = e ? 0 : 1;
     return e;

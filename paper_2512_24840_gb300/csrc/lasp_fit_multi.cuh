@@ -34,8 +34,17 @@ struct MultiWs {
     float* wq;      // N: the weight w of each spectrum, NaN where preprocessing decided the fit
     float* im;      // N: the mean inverse variance of each spectrum (Clean's base weights)
     int ldw;        // row stride: p rounded up to 16
-    int* next;      // index of the next spectrum to take (starts at 0)
+    int* next;      // index of the next spectrum to take (starts at 0); with a
+                    // slot list, next[1] is the list's length
+    const int* list;  // resumable slots: the running slots of this step, else nullptr
 };
+
+// The running slots of a pool, compacted into list[0 .. next[1]) (any order;
+// next[0..1] cleared before).  One thread per slot.
+static __global__ void slots_running_list(int n, const uint32_t* __restrict__ status, int* list, int* next) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && status[i] == 128u) list[atomicAdd(&next[1], 1)] = i;
+}
 
 // Shared-memory plan (floats): per lane [B | g | gmu | gsg | phi | dphi | ring]
 // at lane * lane_stride, then the CTA's reduction buffers.  B holds the lane's
@@ -114,6 +123,55 @@ __global__ void __launch_bounds__(NT) fit_prep_kernel(const FitParams P, const M
     if (P.cont && tid < NB) P.cont[(size_t)i * NB + tid] = NAN;
 }
 
+// Preprocessing of spectra admitted into resumable slots (idx: their slot
+// indices): y and W into the slots' workspace rows, w and the mean ivar into
+// the slot state, the initial Adam state, and the final result of spectra
+// with too few usable pixels (status LASP_ST_NODATA).
+template <int NT, int D>
+__global__ void __launch_bounds__(NT) fit_prep_slots_kernel(const FitParams P, const MultiWs Wk,
+                                                            const int32_t* __restrict__ idx) {
+    constexpr int NB = D + 1;
+    extern __shared__ __align__(16) float sm[];
+    const ModelDev& M = P.M;
+    const int p = M.n_pix, tid = threadIdx.x, i = idx[blockIdx.x];
+    float* yr = Wk.yw + (size_t)i * 2 * Wk.ldw;
+    float* wr = yr + Wk.ldw;
+    const size_t row = (size_t)i * p;
+    float w, imean;
+    const int n_obj = prep_spectrum<NT>(P.flux + row, P.ivar + row, P.good + row, p, P.O.edge_px,
+                                        P.O.quantile, yr, wr, sm, sm + ((p + 3) & ~3), &w, &imean);
+    for (int q = p + tid; q < Wk.ldw; q += NT) {
+        yr[q] = 0.0f;
+        wr[q] = 0.0f;
+    }
+    const bool nodata = n_obj < NB + 5 || !(w > 0.0f) || !isfinite(w);
+    if (tid < 5) {
+        const float xx = fminf(1.0f, fmaxf(-1.0f, (P.theta0[5 * i + tid] - M.plo[tid]) / M.phalf[tid] - 1.0f));
+        if (nodata) {
+            P.theta[5 * i + tid] = phys_of(M, tid, xx);
+        } else {
+            P.S.x[5 * i + tid] = xx;
+            P.S.m[5 * i + tid] = 0.0f;
+            P.S.v[5 * i + tid] = 0.0f;
+        }
+    }
+    if (tid == 0) {
+        P.S.w[i] = w;
+        P.S.imean[i] = imean;
+        if (nodata) {
+            P.loss[i] = NAN;
+            P.steps[i] = 0;
+            P.status[i] = 64u;
+            if (P.weight) P.weight[i] = w;
+        } else {
+            P.S.prev[i] = 0.0f;
+            P.S.rise[i] = 0;
+            P.S.t[i] = 0;
+        }
+    }
+    if (nodata && P.cont && tid < NB) P.cont[(size_t)i * NB + tid] = NAN;
+}
+
 template <int NT, int S>
 __host__ __device__ constexpr int multi_min_blocks() {
     return NT == 256 ? (S <= 2 ? 3 : 2) : 1;
@@ -148,8 +206,11 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
     // Adam and stop-rule state of lane s: registers of warp s (parameter k on
     // its lane k < 5; step count, ring slot and rule state on every lane).
     float xk = 0.0f, mk = 0.0f, vk = 0.0f, prev = 0.0f;
-    int rise = 0, ri = 0, t = 0;
+    int rise = 0, ri = 0, t = 0, t0 = 0;
     double b1t = 1.0, b2t = 1.0;
+    // resumable slots (P.S.x set): a lane takes running slots, resumes each from
+    // its saved state and suspends it after P.S.budget steps
+    const bool slots = P.S.x != nullptr;
 
     if (tid < S) {
         s_i[tid] = -1;
@@ -172,7 +233,10 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
             if (!s_need[s]) continue;
             float* base = sm + s * L.lane;
             for (;;) {
-                if (tid == 0) s_next = atomicAdd(Wk.next, 1);
+                if (tid == 0) {
+                    const int q = atomicAdd(Wk.next, 1);
+                    s_next = Wk.list ? (q < Wk.next[1] ? Wk.list[q] : P.N) : q;
+                }
                 __syncthreads();
                 const int i = s_next;
                 if (i >= P.N) {
@@ -183,20 +247,36 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
                     __syncthreads();
                     break;
                 }
-                const float w = Wk.wq[i];
-                if (isnan(w)) {           // result already written by the preprocessing
+                const bool take = slots ? P.status[i] == 128u : !isnan(Wk.wq[i]);
+                if (!take) {              // slot not running, or result written by the preprocessing
                     __syncthreads();
                     continue;
                 }
+                const float w = slots ? P.S.w[i] : Wk.wq[i];
                 if (warp == s) {
-                    xk = mk = vk = prev = 0.0f;
-                    rise = ri = t = 0;
-                    b1t = b2t = 1.0;
-                    if (lane < 5) {
-                        const float xx = (P.theta0[5 * i + lane] - M.plo[lane]) / M.phalf[lane] - 1.0f;
-                        xk = fminf(1.0f, fmaxf(-1.0f, xx));
-                        s_x[s][lane] = xk;
+                    if (slots) {
+                        t0 = t = P.S.t[i];
+                        ri = t0 % P.O.window;
+                        prev = P.S.prev[i];
+                        rise = P.S.rise[i];
+                        b1t = t0 > 0 ? pow((double)P.O.beta1, (double)t0) : 1.0;
+                        b2t = t0 > 0 ? pow((double)P.O.beta2, (double)t0) : 1.0;
+                        if (lane < 5) {
+                            xk = P.S.x[5 * i + lane];
+                            mk = P.S.m[5 * i + lane];
+                            vk = P.S.v[5 * i + lane];
+                        }
+                        for (int q = lane; q < WINMAX; q += 32) base[L.ring + q] = P.S.ring[(size_t)i * WINMAX + q];
+                    } else {
+                        mk = vk = prev = 0.0f;
+                        rise = ri = t = t0 = 0;
+                        b1t = b2t = 1.0;
+                        if (lane < 5) {
+                            const float xx = (P.theta0[5 * i + lane] - M.plo[lane]) / M.phalf[lane] - 1.0f;
+                            xk = fminf(1.0f, fmaxf(-1.0f, xx));
+                        }
                     }
+                    if (lane < 5) s_x[s][lane] = xk;
                     __syncwarp();
                     const int hn = warp_prepare_step(M, s_x[s], base + L.phi, base + L.dphi, base + L.g,
                                                      base + L.gmu, base + L.gsg, s_k[s]);
@@ -589,6 +669,22 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
                     s_x[s][lane] = xk;
                 }
                 __syncwarp();
+                if (slots && t + 1 - t0 >= P.S.budget) {
+                    // suspend: save the slot state; the slot stays running (a Clean
+                    // update of this step still follows below)
+                    if (lane < 5) {
+                        P.S.x[5 * i + lane] = xk;
+                        P.S.m[5 * i + lane] = mk;
+                        P.S.v[5 * i + lane] = vk;
+                    }
+                    if (lane == 0) {
+                        P.S.prev[i] = prev;
+                        P.S.rise[i] = rise;
+                        P.S.t[i] = t + 1;
+                        s_need[s] = 1;
+                    }
+                    for (int q = lane; q < WINMAX; q += 32) P.S.ring[(size_t)i * WINMAX + q] = ring[q];
+                }
                 if (clean_step(P.O, t)) {
                     // the Clean update below needs the basis and taps of x_t
                     if (lane == 0) s_cln[s] = t;
@@ -663,7 +759,7 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
                     }
                     const float* yr = Wk.yw + (size_t)i * 2 * Wk.ldw;
                     float* wr = Wk.yw + (size_t)i * 2 * Wk.ldw + Wk.ldw;
-                    const float imean = Wk.im[i], wgt = s_w[s];
+                    const float imean = slots ? P.S.imean[i] : Wk.im[i], wgt = s_w[s];
                     const size_t row = (size_t)i * p;
                     float bl[NB];
 #pragma unroll

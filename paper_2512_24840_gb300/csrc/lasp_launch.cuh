@@ -13,10 +13,24 @@ int cuda_rc(cudaError_t e);
 
 template <int D> int launch_fit(const FitParams& P, cudaStream_t st);
 template <int D> int launch_fit_multi(const FitParams& P, cudaStream_t st);
+template <int D> int launch_fit_multi_slots(const FitParams& P, const MultiWs& W, int n_running, cudaStream_t st);
+template <int D> int launch_fit_prep_slots(const FitParams& P, const MultiWs& W, const int32_t* idx, int count,
+                                           cudaStream_t st);
 template <int D> int launch_errors(const ErrParams& P, cudaStream_t st);
 template <int D> int launch_forward(const ModelParams& P, cudaStream_t st);
 template <int D> int launch_backward(const ModelParams& P, cudaStream_t st);
 template <int D> int launch_lm(const LmParams& P, cudaStream_t st);
+
+// Spectra per CTA of the batch fit (fit_multi_kernel).
+constexpr int FIT_LANES = 4;
+
+// Whether resumable slots of this table and degree run on fit_multi_kernel
+// (its shared memory fits), with y, W rows of 2 ldw floats per slot.
+inline bool fit_multi_slots_ok(int p, int H, int nm, int K, int D) {
+    const int NT = p <= 16 * 256 ? 256 : 512;
+    return fit_multi_smem_bytes(p, H, nm, NT, D, K, FIT_LANES) <= 227 * 1024 &&
+           4 * (size_t)fit_prep_smem_floats(p) <= 227 * 1024;
+}
 
 #ifdef LASP_DEFINE_LAUNCHERS
 template <typename Kern>
@@ -42,8 +56,6 @@ int launch_fit(const FitParams& P, cudaStream_t st) {
     return cuda_rc(cudaGetLastError());
 }
 
-// Spectra per CTA of the batch fit (fit_multi_kernel).
-constexpr int FIT_LANES = 4;
 
 // One-shot batch fit: fit_prep_kernel (one CTA per spectrum), then FIT_LANES
 // spectra per CTA on a persistent grid of as many CTAs as the SMs hold.  The
@@ -74,7 +86,7 @@ int launch_fit_multi(const FitParams& P, cudaStream_t st) {
     if (e) return e;
     if (nb < 1) return launch_fit<D>(P, st);
     const int grid = (int)std::min<long long>(((long long)P.N + S - 1) / S, (long long)nb * nsm);
-    MultiWs W;
+    MultiWs W{};
     W.ldw = (p + 15) & ~15;
     const size_t rows = (size_t)P.N * 2 * W.ldw * sizeof(float);
     const size_t wq = ((size_t)P.N * sizeof(float) + 255) & ~(size_t)255;   // w, then the mean ivar
@@ -98,6 +110,53 @@ int launch_fit_multi(const FitParams& P, cudaStream_t st) {
     }
     const int ef = cuda_rc(cudaFreeAsync(ws, st));
     return e ? e : ef;
+}
+
+// One step launch of a slot pool on fit_multi_kernel: a persistent grid whose
+// lanes take the running slots through W.next (cleared here), at most one
+// CTA per FIT_LANES of the caller's running count.
+template <int D>
+int launch_fit_multi_slots(const FitParams& P, const MultiWs& W, int n_running, cudaStream_t st) {
+    constexpr int S = FIT_LANES;
+    const int p = P.M.n_pix, H = P.M.pad, nm = P.M.n_model;
+    const int NT = p <= 16 * 256 ? 256 : 512;
+    const size_t smem = fit_multi_smem_bytes(p, H, nm, NT, D, P.M.K, S);
+    void (*kern)(const FitParams, const MultiWs) =
+        NT == 256 ? fit_multi_kernel<256, D, S> : fit_multi_kernel<512, D, S>;
+    int e = set_smem_attr(kern, smem);
+    if (e) return e;
+    int nb = 0, dev = 0, nsm = 0;
+    e = cuda_rc(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NT, smem));
+    if (!e) e = cuda_rc(cudaGetDevice(&dev));
+    if (!e) e = cuda_rc(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    if (e) return e;
+    if (nb < 1) return cuda_rc(cudaErrorLaunchOutOfResources);
+    const long long nr = std::min(P.N, std::max(1, n_running));
+    const int grid = (int)std::min<long long>((nr + S - 1) / S, (long long)nb * nsm);
+    // the running slots first, so that lanes take work without scanning idle
+    // slots and CTAs left without work end at once (freeing their SMs)
+    e = cuda_rc(cudaMemsetAsync(W.next, 0, 2 * sizeof(int), st));
+    if (e) return e;
+    slots_running_list<<<(P.N + 255) / 256, 256, 0, st>>>(P.N, P.status, const_cast<int*>(W.list), W.next);
+    e = cuda_rc(cudaGetLastError());
+    if (e) return e;
+    kern<<<grid, NT, smem, st>>>(P, W);
+    return cuda_rc(cudaGetLastError());
+}
+
+// Preprocessing of `count` freshly admitted slots (idx: device slot indices).
+template <int D>
+int launch_fit_prep_slots(const FitParams& P, const MultiWs& W, const int32_t* idx, int count,
+                          cudaStream_t st) {
+    const int p = P.M.n_pix;
+    const int NT = p <= 16 * 256 ? 256 : 512;
+    const size_t smem = 4 * (size_t)fit_prep_smem_floats(p);
+    void (*prep)(const FitParams, const MultiWs, const int32_t*) =
+        NT == 256 ? fit_prep_slots_kernel<256, D> : fit_prep_slots_kernel<512, D>;
+    int e = set_smem_attr(prep, smem);
+    if (e) return e;
+    prep<<<count, NT, smem, st>>>(P, W, idx);
+    return cuda_rc(cudaGetLastError());
 }
 
 template <int D>
@@ -169,6 +228,8 @@ int launch_lm(const LmParams& P, cudaStream_t st) {
 #define LASP_INSTANTIATE(D)                                                  \
     template int launch_fit<D>(const FitParams&, cudaStream_t);             \
     template int launch_fit_multi<D>(const FitParams&, cudaStream_t);       \
+    template int launch_fit_multi_slots<D>(const FitParams&, const MultiWs&, int, cudaStream_t); \
+    template int launch_fit_prep_slots<D>(const FitParams&, const MultiWs&, const int32_t*, int, cudaStream_t); \
     template int launch_errors<D>(const ErrParams&, cudaStream_t);          \
     template int launch_forward<D>(const ModelParams&, cudaStream_t);       \
     template int launch_backward<D>(const ModelParams&, cudaStream_t);      \

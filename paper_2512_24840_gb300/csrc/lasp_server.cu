@@ -115,7 +115,7 @@ int launch_lane(Lane* L, int chunk) {
         done += m;
     }
     if (L->busy == 0) return LASP_OK;
-    int rc = lasp_slots_step(L->pool, chunk, L->stream);
+    int rc = lasp_slots_step_running(L->pool, chunk, L->busy, L->stream);
     if (!rc)
         rc = lasp_slots_fetch(L->pool, L->o_theta, L->o_loss, L->o_steps, L->o_status, nullptr, L->stream);
     if (!rc) rc = cuda_e(cudaEventRecord(L->done, L->stream));

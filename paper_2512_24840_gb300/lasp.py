@@ -72,6 +72,7 @@ EXPORTS = ["lasp_init_interp", "lasp_free_interp", "lasp_default_opts", "lasp_fi
            "lasp_errors", "lasp_forward", "lasp_backward", "lasp_interp_eval",
            "lasp_last_launches", "lasp_strerror", "lasp_version", "lasp_resample_linear",
            "lasp_slots_create", "lasp_slots_free", "lasp_slots_admit", "lasp_slots_step",
+           "lasp_slots_step_running",
            "lasp_slots_fetch", "lasp_interp_eval_static", "lasp_clean_mask",
            "lasp_init_interp_piecewise", "lasp_server_create", "lasp_server_destroy",
            "lasp_server_submit", "lasp_server_tick", "lasp_server_poll", "lasp_server_pending"]

@@ -83,6 +83,7 @@ class DevicePool:
         self.lib.lasp_slots_free.argtypes = [P]
         self.lib.lasp_slots_admit.argtypes = [P, ct.c_int, P, P, P, P, P, P]
         self.lib.lasp_slots_step.argtypes = [P, ct.c_int, P]
+        self.lib.lasp_slots_step_running.argtypes = [P, ct.c_int, ct.c_int, P]
         self.lib.lasp_slots_fetch.argtypes = [P, P, P, P, P, P, P]
         h = ct.c_void_p()
         rc = self.lib.lasp_slots_create(interp._h, n_slots, ct.byref(self.opts), ct.byref(h))
@@ -118,10 +119,13 @@ class DevicePool:
     @staticmethod
     def bytes_per_slot(n_pix: int, deg: int = 6, precision="fp32") -> int:
         """Device bytes of one slot: the observation and its staging copy, the
-        optimiser state; at tensor-core precisions also the grouped pipeline's
+        optimiser state; at FP32 the slot's y, W rows (8 bytes a pixel, n_pix
+        rounded up to 16); at tensor-core precisions the grouped pipeline's
         F', y, W, operand images and taps (about 20 n_pix + 2 KB)."""
         b = 2 * 9 * n_pix + 4 * (3 * 5 + 64 + 6 + 5 + 5 + deg + 1) + 8
-        if precision not in ("fp32", 0):
+        if precision in ("fp32", 0):
+            b += 8 * ((n_pix + 15) // 16 * 16)
+        else:
             b += 20 * n_pix + 2048
         return b
 
@@ -178,8 +182,14 @@ class DevicePool:
                              self.h_good.data_ptr(), self.h_th0.data_ptr())
         assert off + len(rest) == c
 
-    def step(self, budget: int):
-        rc = self.lib.lasp_slots_step(self._h, int(budget), ct.c_void_p(self.stream.cuda_stream))
+    def step(self, budget: int, n_running: int | None = None):
+        """lasp_slots_step; with n_running (the caller's count of running
+        slots) the launch is sized to it."""
+        if n_running is None:
+            rc = self.lib.lasp_slots_step(self._h, int(budget), ct.c_void_p(self.stream.cuda_stream))
+        else:
+            rc = self.lib.lasp_slots_step_running(self._h, int(budget), max(1, int(n_running)),
+                                                  ct.c_void_p(self.stream.cuda_stream))
         if rc:
             raise self._lasp.LaspError(rc, "lasp_slots_step")
 
@@ -268,7 +278,7 @@ class Server:
                 for s, q in zip(slots, reqs):
                     lane.busy[s] = q
             if lane.busy:
-                lane.pool.step(self.chunk)
+                lane.pool.step(self.chunk, len(lane.busy))
                 lane.pool.fetch()
                 active.append(lane)
         out = []

@@ -154,6 +154,34 @@ def test_fixed_step_trajectory_parity_small(lasp, lr, nsteps):
     assert np.all(err <= TOL), err.max(axis=0)
 
 
+@pytest.mark.parametrize("deg", [2, 4, 8])
+def test_fit_other_continuum_degrees(lasp, deg):
+    """Legendre continua of degree 2, 4 and 8 (the FP32 path's other degrees):
+    fixed-step parity with the oracle's fit of the same degree on a batch of
+    seven (fewer spectra than two CTAs of the batch fit carry), and the served
+    form (one spectrum per CTA, resumed every 7 steps) bitwise equal to it."""
+    M, d = observed(S.SMALL, 7, 46, noise=False, mask_frac=0.0)
+    d["theta0"] = q32(d["theta0"])
+    ip = interp(lasp, S.SMALL)
+    args = (T(d["flux"]), T(d["ivar"]), T(d["good"], torch.uint8), T(d["theta0"]))
+    out = ip.fit(*args, max_steps=12, tol=0.0, legendre_deg=deg)
+    torch.cuda.synchronize()
+    ref = O.fit(oracle_model(S.SMALL, deg=deg), d["flux"], d["ivar"], d["good"], d["theta0"],
+                max_steps=12, tol=0.0)
+    assert np.all(H(out["steps"]) == ref["steps"])
+    err = np.abs(H(out["theta"]) - ref["theta"])[:, :4]
+    assert np.all(err <= TOL), err.max(axis=0)
+    from paper_2512_24840_gb300.server import DevicePool, Server
+    one = ip.fit(*args, max_steps=60, legendre_deg=deg)
+    srv = Server({"s": DevicePool(ip, 3, max_steps=60, legendre_deg=deg)}, chunk=7)
+    ids = [srv.submit("s", d["flux"][i], d["ivar"][i], d["good"][i], d["theta0"][i]) for i in range(7)]
+    res = {r.rid: r for r in srv.run_until_idle()}
+    srv.close()
+    for k, rid in enumerate(ids):
+        assert np.array_equal(res[rid].theta, H(one["theta"])[k]), k
+        assert res[rid].steps == int(H(one["steps"])[k])
+
+
 def test_noise_free_recovery_small(lasp):
     """Small steps to convergence: the GPU fit recovers the truth (config-1
     data).  lr 3e-4 keeps Adam's end-of-fit jitter (about lr x half box
