@@ -27,8 +27,10 @@ class FakePool:
             self.theta[s] = q.theta0
             self.admitted.append(q.rid)
 
-    def step(self, budget):
+    def step(self, budget, n_running=None):
         run = self.status == RUNNING
+        # the scheduler sizes the launch by its count of running slots
+        assert n_running is None or n_running == int(run.sum())
         self.done[run] += np.minimum(budget, self.need[run] - self.done[run])
         fin = run & (self.done >= self.need)
         self.status[fin] = 1
