@@ -41,8 +41,8 @@ FP32_LANES_PER_SM, N_SM = 128, 152
 # the current kernel source (reset to None whenever the kernel changes until it
 # is captured again): it reads the prepared y, W rows (8 B a pixel) and the
 # table, and writes the results.
-FIT_KERNEL = "fit_multi_kernel<256,6,4>"
-FIT_TRAFFIC_BYTES = 136_976_640
+FIT_KERNEL = "fit_multi_kernel<256,6,4,false>"
+FIT_TRAFFIC_BYTES = 136_868_608
 
 
 def parse():

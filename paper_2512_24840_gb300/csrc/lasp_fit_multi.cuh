@@ -185,7 +185,9 @@ __host__ __device__ constexpr bool multi_keep_yw() {
     return multi_min_blocks<NT, S>() <= 2 && S <= 3;
 }
 
-template <int NT, int D, int S>
+// FULL: with the Clean update and resumable slots; the plain batch fit
+// instantiates FULL = false, whose lighter register use spills less.
+template <int NT, int D, int S, bool FULL>
 __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kernel(const FitParams P,
                                                                                   const MultiWs Wk) {
     using Gm = Gram<D>;
@@ -210,7 +212,7 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
     double b1t = 1.0, b2t = 1.0;
     // resumable slots (P.S.x set): a lane takes running slots, resumes each from
     // its saved state and suspends it after P.S.budget steps
-    const bool slots = P.S.x != nullptr;
+    const bool slots = FULL && P.S.x != nullptr;
 
     if (tid < S) {
         s_i[tid] = -1;
@@ -685,7 +687,7 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
                     }
                     for (int q = lane; q < WINMAX; q += 32) P.S.ring[(size_t)i * WINMAX + q] = ring[q];
                 }
-                if (clean_step(P.O, t)) {
+                if (FULL && clean_step(P.O, t)) {
                     // the Clean update below needs the basis and taps of x_t
                     if (lane == 0) s_cln[s] = t;
                 } else {
@@ -702,7 +704,7 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
         // from the residual at x_t (the code of fit_kernel's update).  The lane's
         // F' of x_t was overwritten by its delta, so one table pass recomputes
         // it; two other lanes' buffers, free between steps, hold r and m.
-        if constexpr (S >= 3) {
+        if constexpr (FULL && S >= 3) {
             if (P.O.clean) {
 #pragma unroll 1
                 for (int s = 0; s < S; ++s) {

@@ -73,7 +73,8 @@ int launch_fit_multi(const FitParams& P, cudaStream_t st) {
     // resumable slots, and Clean with too few lanes for its scratch, stay on fit_kernel
     if (P.S.x || (P.O.clean && S < 3) || smem > 227 * 1024 || smem_prep > 227 * 1024) return launch_fit<D>(P, st);
     void (*kern)(const FitParams, const MultiWs) =
-        NT == 256 ? fit_multi_kernel<256, D, S> : fit_multi_kernel<512, D, S>;
+        P.O.clean ? (NT == 256 ? fit_multi_kernel<256, D, S, true> : fit_multi_kernel<512, D, S, true>)
+                  : (NT == 256 ? fit_multi_kernel<256, D, S, false> : fit_multi_kernel<512, D, S, false>);
     void (*prep)(const FitParams, const MultiWs) =
         NT == 256 ? fit_prep_kernel<256, D> : fit_prep_kernel<512, D>;
     int e = set_smem_attr(kern, smem);
@@ -122,7 +123,7 @@ int launch_fit_multi_slots(const FitParams& P, const MultiWs& W, int n_running, 
     const int NT = p <= 16 * 256 ? 256 : 512;
     const size_t smem = fit_multi_smem_bytes(p, H, nm, NT, D, P.M.K, S);
     void (*kern)(const FitParams, const MultiWs) =
-        NT == 256 ? fit_multi_kernel<256, D, S> : fit_multi_kernel<512, D, S>;
+        NT == 256 ? fit_multi_kernel<256, D, S, true> : fit_multi_kernel<512, D, S, true>;
     int e = set_smem_attr(kern, smem);
     if (e) return e;
     int nb = 0, dev = 0, nsm = 0;

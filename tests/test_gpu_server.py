@@ -97,3 +97,33 @@ def test_server_created_while_a_fit_runs():
     for i, rid in enumerate(rids):
         assert np.array_equal(res[rid].theta, busy["theta"][256 * i].cpu().numpy()), i
         assert res[rid].status == int(busy["status"][256 * i])
+
+
+@pytest.mark.parametrize("hint", ["one", "true", "too_many"])
+def test_step_running_hint_only_sizes_the_launch(hint):
+    """lasp_slots_step_running sizes the launch from the caller's count of
+    running slots; a wrong count (1, or more than the pool holds) changes the
+    schedule, never a result."""
+    from paper_2512_24840_gb300 import lasp
+    from paper_2512_24840_gb300.server import DevicePool, Request
+    lasp.load(build=True)
+    g = S.LAMOST
+    ip = lasp.Interp.from_grid(g, table(g.name), S.EXPS, S.BASIS_LO, S.BASIS_HI, S.BOX_LO, S.BOX_HI)
+    f, iv, gd, th = _observed(g, 24, 64)
+    dev = torch.device("cuda:0")
+    one = ip.fit(torch.tensor(f, device=dev), torch.tensor(iv, device=dev), torch.tensor(gd, device=dev),
+                 torch.tensor(th, device=dev), max_steps=400)
+    pool = DevicePool(ip, 40, max_steps=400)
+    slots = list(range(3, 27))
+    pool.admit(slots, [Request(k, "l", f[k], iv[k], gd[k], th[k]) for k in range(24)])
+    n_hint = {"one": 1, "true": 24, "too_many": 1000}[hint]
+    for _ in range(40):
+        pool.step(11, n_hint)
+        pool.fetch()
+        status, theta, loss, steps = pool.wait()
+        if not np.any(status[slots] == lasp.ST_RUNNING):
+            break
+    for k, s in enumerate(slots):
+        assert np.array_equal(theta[s], one["theta"][k].cpu().numpy()), k
+        assert steps[s] == int(one["steps"][k])
+    pool.close()
