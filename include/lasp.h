@@ -209,9 +209,13 @@ typedef struct {
     float* weight;
 } lasp_result;
 
-/* Fit every spectrum of the batch to convergence (stage 8): one fused kernel
- * runs all Adam steps of a spectrum on one CTA, so each spectrum stops on its
- * own rule and its CTA is reused at once.  Asynchronous on `stream`. */
+/* Fit every spectrum of the batch to convergence (stage 8).  At
+ * LASP_PREC_FP32 a preprocessing kernel prepares every spectrum, then one
+ * fused persistent kernel runs all Adam steps with four spectra per CTA
+ * (each table value loaded once for the four); each spectrum stops on its own
+ * rule and its place goes to the next spectrum at once.  Device workspace of
+ * about 8 n_pix bytes a spectrum comes from the stream's memory pool for the
+ * call.  Asynchronous on `stream`. */
 int lasp_fit_batch(lasp_interp h, const lasp_batch* batch, const lasp_fit_opts* opts,
                    lasp_result* result, void* stream);
 
