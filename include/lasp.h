@@ -161,8 +161,8 @@ typedef struct {
                                sums exact in float-float, the 7x7 solve by an FP32
                                Cholesky factor refined once with a float-float
                                residual (no FP64 instructions on the step path) */
-    int clean;              /* 1: Clean outlier masking (stage 6, Eq. 8); FP32
-                               batch fits only                           */
+    int clean;              /* 1: Clean outlier masking (stage 6, Eq. 8); Adam
+                               fits with the separable loss, every precision */
     int clean_every;        /* mask update every this many steps (30)   */
     int clean_max;          /* at most this many updates (11)           */
     int optimizer;          /* LASP_OPT_ADAM (stage 8) or LASP_OPT_LM    */
@@ -240,9 +240,9 @@ typedef struct lasp_slots_s* lasp_slots;          /* opaque, library-owned */
  * A tensor-core precision: the grouped pipeline runs over the slots (served
  * mixed precision; single-regime tables, Legendre degree 6; about 50 n_pix
  * more bytes per slot); its steps go in chunks of 8, so a step call's budget
- * is rounded up to a multiple of 8.  Clean (FP32 pools only): each slot keeps
- * its Clean mask in device memory between steps (in its W row), so the updates
- * fall on the same steps as in a one-shot fit.  The joint loss:
+ * is rounded up to a multiple of 8.  Clean: each slot keeps its Clean mask in
+ * device memory between steps (in its W row), so the updates fall on the same
+ * steps as in a one-shot fit at the same precision.  The joint loss:
  * LASP_EINVAL. */
 int lasp_slots_create(lasp_interp h, int n_slots, const lasp_fit_opts* opts, lasp_slots* out);
 void lasp_slots_free(lasp_slots s);

@@ -277,7 +277,7 @@ int lasp_fit_batch(lasp_interp h, const lasp_batch* b, const lasp_fit_opts* o, l
     if (!r || (b->N > 0 && (!r->theta || !r->loss || !r->steps || !r->status))) return LASP_EINVAL;
     if (b->N == 0) return LASP_OK;
     if (o->precision != LASP_PREC_FP32) {
-        if (o->clean || h->M.n_reg > 1) return LASP_EINVAL;          // Clean runs in the FP32 batch fit
+        if (h->M.n_reg > 1) return LASP_EINVAL;                       // single-regime tensor-core images
         return lasp_tc_fit_batch(h->M, h->tc, b, o, r, stream, &g_last_launches);
     }
     if (o->optimizer == LASP_OPT_LM) {
@@ -529,7 +529,7 @@ int lasp_slots_create(lasp_interp h, int n_slots, const lasp_fit_opts* o, lasp_s
     int rc = check_opts(o, h->M.n_pix);
     if (rc) return rc;
     if (o->loss_mode != LASP_LOSS_SEPARABLE) return LASP_EINVAL;
-    if (o->precision != LASP_PREC_FP32 && (h->M.n_reg > 1 || o->legendre_deg != 6 || o->clean))
+    if (o->precision != LASP_PREC_FP32 && (h->M.n_reg > 1 || o->legendre_deg != 6))
         return LASP_EINVAL;
     lasp_slots_s* s = new (std::nothrow) lasp_slots_s();
     if (!s) return LASP_ENOMEM;

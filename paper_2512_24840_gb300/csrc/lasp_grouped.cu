@@ -14,6 +14,7 @@
 #include <cmath>
 #include <vector>
 
+#include "lasp_clean.cuh"
 #include "lasp_fit.cuh"
 #include "lasp_tc.cuh"
 #include "lasp_tc_ptx.cuh"
@@ -301,6 +302,99 @@ struct RestSmem {
         total = o;
     }
 };
+
+// Stage 6 Clean update in the grouped pipeline, between K3 and K4 of a step:
+// for every active spectrum whose evaluated step t is a Clean step, the mask
+// update from the residual at x_t (K1's F', K2's continuum b, and the taps of
+// x_t, which K4 has not replaced yet), written into its W row for the steps
+// that follow.  The same rules as the fused kernels' update; other spectra
+// return at once.  Shared memory: RestSmem.
+template <int NT, int D>
+__global__ void __launch_bounds__(NT) kc_clean(const Grp G, int par) {
+    constexpr int NB = D + 1;
+    const int pos = blockIdx.x;
+    if (pos >= G.count[par]) return;
+    const int id = G.list[par][pos];
+    const int t = G.t[id];
+    if (!clean_step(G.O, t)) return;
+    extern __shared__ __align__(16) float sm[];
+    const ModelDev& M = G.M;
+    const int p = M.n_pix, H = M.pad, nm = M.n_model;
+    const int tid = threadIdx.x;
+    const RestSmem L(p, H, nm, NT, D);
+    float* Fp = sm + L.Fp;
+    float* Rb = sm + L.Db;
+    float* Mb = sm + L.W;
+    float* g = sm + L.g;
+    __shared__ double s_redd[3 * (NT / 32)], s_tot[3];
+    const int j0 = tid * PPT;
+    const bool own_pix = j0 < p;
+    for (int q = tid; q < skew_size(nm + 32); q += NT) Fp[q] = 0.0f;
+    __syncthreads();
+    for (int m = tid; m < nm; m += NT) Fp[skew(m + 16)] = G.Fp[(size_t)id * G.ldf + m];
+    const float* tp = G.taps + (size_t)id * 3 * TAPBUF;
+    for (int q = tid; q < TAPBUF; q += NT) g[q] = tp[q];
+    __syncthreads();
+    const int h = G.hh[id];
+    const int nblk = (2 * h + 1 + TB - 1) / TB;
+    float fpp[PPT];
+#pragma unroll
+    for (int r = 0; r < PPT; ++r) fpp[r] = 0.0f;
+    if (own_pix) {
+        for (int bk = 0; bk < nblk; ++bk) {
+            const int s0 = -h + bk * TB;
+            float gg[TB], win[PPT + TB - 1];
+#pragma unroll
+            for (int e = 0; e < TB; ++e) gg[e] = g[s0 + e + H];
+            const int base = j0 + H - s0 - (TB - 1) + 16;
+#pragma unroll
+            for (int q = 0; q < PPT + TB - 1; ++q) win[q] = Fp[skew(base + q)];
+#pragma unroll
+            for (int e = 0; e < TB; ++e)
+#pragma unroll
+                for (int r = 0; r < PPT; ++r) fpp[r] = fmaf(gg[e], win[r - e + TB - 1], fpp[r]);
+        }
+    }
+    float bl[NB];
+#pragma unroll
+    for (int a = 0; a < NB; ++a) bl[a] = G.b[(size_t)id * NB + a];
+    const float imean = G.imean[id], wgt = G.w[id];
+    const size_t row = (size_t)id * p;
+    const float* yr = G.Y + (size_t)id * G.ldp;
+    float* wr = G.Wt + (size_t)id * G.ldp;
+    const float xstep = 2.0f / (float)p;
+    float wbv[PPT];
+    uint32_t used = 0;
+#pragma unroll
+    for (int r = 0; r < PPT; ++r) {
+        const int j = j0 + r;
+        wbv[r] = 0.0f;
+        if (j < p) {
+            const float f = G.flux[row + j], iv = G.ivar[row + j];
+            const bool use = G.good[row + j] && iv > 0.0f && isfinite(f) && isfinite(iv);
+            const bool edge = j < G.O.edge_px || j >= p - G.O.edge_px;
+            const float wb = (use && !edge && wgt > 0.0f) ? iv / imean : 0.0f;
+            float Pl[NB];
+            legendre<D>(fmaf((float)j, xstep, -1.0f), Pl);
+            float c = 0.0f;
+#pragma unroll
+            for (int a = 0; a < NB; ++a) c = fmaf(bl[a], Pl[a], c);
+            const float model = c * fpp[r];
+            const float sw = sqrtf(wb);
+            Rb[skew(j + L.dofs)] = sw * (yr[j] - model);
+            Mb[skew(j)] = sw * model;
+            wbv[r] = wb;
+            if (wr[j] > 0.0f) used |= 1u << r;
+        }
+    }
+    __syncthreads();
+    const int upd = t / G.O.clean_every;
+    const uint32_t keep = cta_clean_mask<NT, PPT>(p, j0, Rb, L.dofs, Mb, 0, used, upd == 1 ? 0.5f : 0.2f,
+                                                  reinterpret_cast<uint8_t*>(Mb), s_redd, s_tot, nullptr);
+#pragma unroll
+    for (int r = 0; r < PPT; ++r)
+        if (j0 + r < p) wr[j0 + r] = ((keep >> r) & 1u) ? wbv[r] : 0.0f;
+}
 
 template <int PREC>
 __device__ __forceinline__ void store_dfp(const Grp& G, int pos, int m0, const float (&d)[PPT]) {
@@ -911,6 +1005,8 @@ int run_grouped(Grp& G, const TcImages& tc, cudaStream_t st, int* launches) {
     int e = cuda_rc(cudaFuncSetAttribute(k1_interp<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1));
     if (!e) e = cuda_rc(cudaFuncSetAttribute(k2_rest<NT, D, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
     if (!e) e = cuda_rc(cudaFuncSetAttribute(k3_back<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3));
+    if (!e && G.O.clean)
+        e = cuda_rc(cudaFuncSetAttribute(kc_clean<NT, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
     if (e) return e;
     const uint8_t* img = (const uint8_t*)(PREC == 2 ? tc.bf16 : tc.tf32_hi);
     const uint8_t* img_lo = (const uint8_t*)tc.tf32_lo;
@@ -924,6 +1020,7 @@ int run_grouped(Grp& G, const TcImages& tc, cudaStream_t st, int* launches) {
         k2_rest<NT, D, PREC><<<N, NT, smem2, st>>>(G, par);
         k3_back<PREC><<<g3, 128, smem3, st>>>(G, par, bk, bk_lo);
         if (G.O.joint) k3j_group<1024><<<1, 1024, 0, st>>>(G);
+        if (G.O.clean) kc_clean<NT, D><<<N, NT, smem2, st>>>(G, par);
         k4_adam<D><<<g4, 256, 0, st>>>(G, par);
     };
     // capture CHUNK_STEPS steps (parities 0,1,0,1,...) into one graph
@@ -946,7 +1043,7 @@ int run_grouped(Grp& G, const TcImages& tc, cudaStream_t st, int* launches) {
     const int max_chunks = (G.O.max_steps + 1 + CHUNK_STEPS - 1) / CHUNK_STEPS + 1;
     for (int c = 0; !e && c < max_chunks; ++c) {
         e = cuda_rc(cudaGraphLaunch(exec, st));
-        nlaunch += (G.O.joint ? 5 : 4) * CHUNK_STEPS;
+        nlaunch += (G.O.joint || G.O.clean ? 5 : 4) * CHUNK_STEPS;
         if (!e) e = cuda_rc(cudaMemcpyAsync(&h_count, G.count, sizeof(int), cudaMemcpyDeviceToHost, st));
         if (!e) e = cuda_rc(cudaStreamSynchronize(st));
         if (!e && h_count == 0) break;
@@ -978,6 +1075,9 @@ int lasp_tc_fit_batch(const ModelDev& M, const TcImages& tc, const lasp_batch* b
     G.O.quantile = o->quantile;
     G.O.fp64_ne = o->fp64_normal_eq ? 1 : 0;
     G.O.joint = o->loss_mode == LASP_LOSS_JOINT ? 1 : 0;
+    G.O.clean = o->clean ? 1 : 0;
+    G.O.clean_every = o->clean_every;
+    G.O.clean_max = o->clean_max;
     const int N = b->N;
     const int NB = o->legendre_deg + 1;
     G.N = N;
@@ -1094,6 +1194,8 @@ int pool_setup(GrpPool* P) {
     if (!e) e = cuda_rc(cudaFuncSetAttribute(k1_interp<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1));
     if (!e) e = cuda_rc(cudaFuncSetAttribute(k2_rest<NT, D, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
     if (!e) e = cuda_rc(cudaFuncSetAttribute(k3_back<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3));
+    if (!e && G.O.clean)
+        e = cuda_rc(cudaFuncSetAttribute(kc_clean<NT, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
     if (e) return e;
     P->admit = [](GrpPool* Q, int count, const int32_t* idx, cudaStream_t st) -> int {
         const int pq = (Q->G.M.n_pix + 3) & ~3;
@@ -1117,6 +1219,7 @@ int pool_setup(GrpPool* P) {
             k1_interp<PREC><<<g1, 128, smem1, cap>>>(G, par, img, img_lo, tc.n_tiles);
             k2_rest<NT, D, PREC><<<N, NT, smem2, cap>>>(G, par);
             k3_back<PREC><<<g3, 128, smem3, cap>>>(G, par, bk, bk_lo);
+            if (G.O.clean) kc_clean<NT, D><<<N, NT, smem2, cap>>>(G, par);
             k4_adam<D><<<g4, 256, 0, cap>>>(G, par);
         }
         e = cuda_rc(cudaStreamEndCapture(cap, &P->graph));
@@ -1161,6 +1264,9 @@ int grp_pool_create(const ModelDev& M, const TcImages& tc, int n, const lasp_fit
     G.O.edge_px = o->edge_px;
     G.O.quantile = o->quantile;
     G.O.fp64_ne = o->fp64_normal_eq ? 1 : 0;
+    G.O.clean = o->clean ? 1 : 0;
+    G.O.clean_every = o->clean_every;
+    G.O.clean_max = o->clean_max;
     G.N = n;
     G.NB = o->legendre_deg + 1;
     G.ldf = (M.n_model + 15) & ~15;
@@ -1236,7 +1342,7 @@ int grp_pool_step(GrpPool* P, int budget, cudaStream_t st, int* launches) {
         const int e = cuda_rc(cudaGraphLaunch(P->exec, st));
         if (e) return e;
     }
-    *launches = replays * 4 * CHUNK_STEPS;
+    *launches = replays * (P->G.O.clean ? 5 : 4) * CHUNK_STEPS;
     return LASP_OK;
 }
 
