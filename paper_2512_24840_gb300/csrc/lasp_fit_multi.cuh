@@ -12,16 +12,21 @@
 //
 // The grid is persistent: a lane whose spectrum stops takes the next one from
 // a global counter, so no lane idles while spectra remain.  The per-spectrum
-// preprocessing (the weight quantile sorts the spectrum) runs before, in
-// fit_prep_kernel at full occupancy, instead of stalling a CTA at each refill;
-// it leaves y and W in a global workspace row per spectrum, which the fit
-// reads from L2 each step instead of keeping it in shared memory, and each lane's F' and
-// delta share one buffer, so four lanes take 95 KB of shared memory at 3909
-// pixels; at two CTAs per SM (eight spectra in flight) the table traffic per
-// spectrum-step is a quarter of fit_kernel's.  Measured on the 4096 x 3909
-// batch (fit_kernel: 30.8 ms): four lanes at two CTAs per SM 23.6 ms, three
-// lanes 24.1 ms, two lanes at three CTAs per SM 24.6 ms.  A lane's Clean mask
-// (stage 6) lives in its W row; resumable slots stay on fit_kernel.
+// preprocessing (y, W and the weight quantile) runs before, in fit_prep_kernel
+// at full occupancy, instead of stalling a CTA at each refill; it leaves y and
+// W in a global workspace row per spectrum, which the fit reads from L2 each
+// step instead of keeping it in shared memory.  Each lane's F' and delta share
+// one buffer, so four lanes take 95 KB of shared memory at 3909 pixels; at two
+// CTAs per SM (eight spectra in flight) the table traffic per spectrum-step is
+// a quarter of fit_kernel's.  Measured on the 4096 x 3909 batch (fit_kernel:
+// 30.8 ms): four lanes at two CTAs per SM 23.6 ms, three lanes 24.1 ms, two
+// lanes at three CTAs per SM 24.6 ms (before the later refinements, which
+// brought four lanes to 21.0 ms).
+//
+// The FULL variant adds the Clean update (stage 6; a lane's mask lives in its
+// W row) and resumable slots (a lane resumes a running slot from its saved
+// state, suspends it after the step budget, and takes the next one from a
+// list of running slots); the plain batch fit runs the lighter variant.
 #pragma once
 
 #include "lasp_clean.cuh"
