@@ -182,14 +182,6 @@ __host__ __device__ constexpr int multi_min_blocks() {
     return NT == 256 ? (S <= 2 ? 3 : 2) : 1;
 }
 
-// With two CTAs per SM or fewer (128 registers a thread) and at most three
-// lanes, a lane's y and W stay in registers from the normal equations to the
-// residual instead of being read from L2 twice (with four lanes they spill).
-template <int NT, int S>
-__host__ __device__ constexpr bool multi_keep_yw() {
-    return multi_min_blocks<NT, S>() <= 2 && S <= 3;
-}
-
 // FULL: with the Clean update and resumable slots; the plain batch fit
 // instantiates FULL = false, whose lighter register use spills less.
 template <int NT, int D, int S, bool FULL>
@@ -357,7 +349,6 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
 
         // ---- per lane: a4 broadening, a5 normal equations and solve, a6 residual,
         // a7 (i) tap sums; the code of fit_kernel with the lane's buffers
-        constexpr bool KEEP = multi_keep_yw<NT, S>();
         // one copy of the per-lane code (lane loop not unrolled: the unrolled form
         // missed in the instruction cache); each thread's four sums of a lane
         // wait in shared memory for the end-of-step reduction
@@ -393,8 +384,8 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
                 }
             }
 
-            // the lane's y and W (kept in registers to the residual where there is room)
-            float yk[KEEP ? PPT : 1], wk[KEEP ? PPT : 1];
+            // the lane's y and W, read from its workspace row (L2) here and again
+            // for the residual: with four lanes there is no room to keep them
             float gacc[NV];
 #pragma unroll
             for (int q = 0; q < NV; ++q) gacc[q] = 0.0f;
@@ -407,10 +398,6 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         const int r = r4 + u, j = j0 + r;
-                        if constexpr (KEEP) {
-                            yk[r] = yv[u];
-                            wk[r] = wv[u];
-                        }
                         const float Wj = j < p ? wv[u] : 0.0f;
                         if (Wj != 0.0f) {
                             float Pl[NB];
@@ -461,19 +448,9 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
                 if (own_pix && solved) {
 #pragma unroll
                     for (int r4 = 0; r4 < PPT; r4 += 4) {
-                        float yv[4], wv[4];
-                        if constexpr (KEEP) {
-#pragma unroll
-                            for (int u = 0; u < 4; ++u) {
-                                yv[u] = yk[r4 + u];
-                                wv[u] = wk[r4 + u];
-                            }
-                        } else {
-                            const float4 y4 = *reinterpret_cast<const float4*>(yr + j0 + r4);
-                            const float4 w4 = *reinterpret_cast<const float4*>(wr + j0 + r4);
-                            yv[0] = y4.x; yv[1] = y4.y; yv[2] = y4.z; yv[3] = y4.w;
-                            wv[0] = w4.x; wv[1] = w4.y; wv[2] = w4.z; wv[3] = w4.w;
-                        }
+                        const float4 y4 = *reinterpret_cast<const float4*>(yr + j0 + r4);
+                        const float4 w4 = *reinterpret_cast<const float4*>(wr + j0 + r4);
+                        const float yv[4] = {y4.x, y4.y, y4.z, y4.w}, wv[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             const int r = r4 + u, j = j0 + r;
