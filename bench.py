@@ -337,203 +337,221 @@ def run_ours(args):
     # ---- mixed precision: grouped tensor-core pipeline (split TF32 and single-pass
     # TF32 contractions, FP64 normal equations), same batch, device-resident inputs
     mixed = {}
-    if not args.no_mixed:
-        for prec in ("tf32x3", "tf32"):
-            mo = dict(opts, precision=prec, fp64_normal_eq=1)
-            mout = ip.fit(g_flux, g_ivar, g_good, g_th0, **mo)          # warm-up
+    try:
+        if not args.no_mixed:
+            for prec in ("tf32x3", "tf32"):
+                mo = dict(opts, precision=prec, fp64_normal_eq=1)
+                mout = ip.fit(g_flux, g_ivar, g_good, g_th0, **mo)          # warm-up
+                torch.cuda.synchronize()
+                t_ms = []
+                for k in range(max(1, args.steps)):
+                    flush.fill_(float(k))
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    mout = ip.fit(g_flux, g_ivar, g_good, g_th0, out=mout, **mo)
+                    b.record(stream)
+                    torch.cuda.synchronize()
+                    t_ms.append(a.elapsed_time(b))
+                mst = mout["status"].cpu().numpy()
+                mth = mout["theta"].double().cpu().numpy()
+                mconv = int(((mst & 3) != 0).sum())
+                agree = np.all(np.abs(mth - theta_np)[:, :4] <= np.array([1.0, 0.005, 0.005, 0.1]), axis=1)
+                mixed[prec] = {"value": mconv / (sum(t_ms) / len(t_ms) / 1e3), "unit": UNIT,
+                               "fit_ms": sum(t_ms) / len(t_ms), "converged": mconv,
+                               "precision": prec + "+fp64_normal_eq",
+                               "within_tol_of_fp32_fit_frac": float(agree.mean())}
+    except Exception as e:       # a failed extra is reported; the headline still prints
+        mixed = {"error": f"{type(e).__name__}: {e}"}
+
+    # ---- the paper's joint loss (one RMS over the group, group stop rules), split TF32
+    joint = {}
+    try:
+        if not args.no_mixed:
+            jo = dict(opts, precision="tf32x3", fp64_normal_eq=1, loss_mode="joint")
+            jout = ip.fit(g_flux, g_ivar, g_good, g_th0, **jo)
             torch.cuda.synchronize()
             t_ms = []
             for k in range(max(1, args.steps)):
                 flush.fill_(float(k))
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record(stream)
-                mout = ip.fit(g_flux, g_ivar, g_good, g_th0, out=mout, **mo)
+                jout = ip.fit(g_flux, g_ivar, g_good, g_th0, out=jout, **jo)
                 b.record(stream)
                 torch.cuda.synchronize()
                 t_ms.append(a.elapsed_time(b))
-            mst = mout["status"].cpu().numpy()
-            mth = mout["theta"].double().cpu().numpy()
-            mconv = int(((mst & 3) != 0).sum())
-            agree = np.all(np.abs(mth - theta_np)[:, :4] <= np.array([1.0, 0.005, 0.005, 0.1]), axis=1)
-            mixed[prec] = {"value": mconv / (sum(t_ms) / len(t_ms) / 1e3), "unit": UNIT,
-                           "fit_ms": sum(t_ms) / len(t_ms), "converged": mconv,
-                           "precision": prec + "+fp64_normal_eq",
-                           "within_tol_of_fp32_fit_frac": float(agree.mean())}
-
-    # ---- the paper's joint loss (one RMS over the group, group stop rules), split TF32
-    joint = {}
-    if not args.no_mixed:
-        jo = dict(opts, precision="tf32x3", fp64_normal_eq=1, loss_mode="joint")
-        jout = ip.fit(g_flux, g_ivar, g_good, g_th0, **jo)
-        torch.cuda.synchronize()
-        t_ms = []
-        for k in range(max(1, args.steps)):
-            flush.fill_(float(k))
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            jout = ip.fit(g_flux, g_ivar, g_good, g_th0, out=jout, **jo)
-            b.record(stream)
-            torch.cuda.synchronize()
-            t_ms.append(a.elapsed_time(b))
-        jst = jout["status"].cpu().numpy()
-        jconv = int(((jst & 3) != 0).sum())
-        jth = jout["theta"].double().cpu().numpy()
-        agree = np.all(np.abs(jth - theta_np)[:, :4] <= np.array([1.0, 0.005, 0.005, 0.1]), axis=1)
-        joint = {"value": jconv / (sum(t_ms) / len(t_ms) / 1e3), "unit": UNIT,
-                 "fit_ms": sum(t_ms) / len(t_ms), "converged": jconv,
-                 "group_steps": int(jout["steps"].max().item()),
-                 "within_tol_of_separable_fp32_fit_frac": float(agree.mean()),
-                 "note": "Eq. 9 read literally: one RMS over the 4096-spectrum group, group stop rules"}
+            jst = jout["status"].cpu().numpy()
+            jconv = int(((jst & 3) != 0).sum())
+            jth = jout["theta"].double().cpu().numpy()
+            agree = np.all(np.abs(jth - theta_np)[:, :4] <= np.array([1.0, 0.005, 0.005, 0.1]), axis=1)
+            joint = {"value": jconv / (sum(t_ms) / len(t_ms) / 1e3), "unit": UNIT,
+                     "fit_ms": sum(t_ms) / len(t_ms), "converged": jconv,
+                     "group_steps": int(jout["steps"].max().item()),
+                     "within_tol_of_separable_fp32_fit_frac": float(agree.mean()),
+                     "note": "Eq. 9 read literally: one RMS over the 4096-spectrum group, group stop rules"}
+    except Exception as e:       # a failed extra is reported; the headline still prints
+        joint = {"error": f"{type(e).__name__}: {e}"}
 
     # ---- mixed precision at the large configuration: 65536 LAMOST-like spectra,
     # split-TF32 contractions + float-float normal equations; parameter error
     # against the FP64 oracle on a sample of the batch
     mixed_large = {}
-    if not args.no_mixed and not args.no_large:
-        _, n_big, off, kw = S.workload("mixed65536")
-        db = S.draw_batch(grid, n_big, S.SPECTRA_SEED + off + 1000 * rank, **kw)
-        bmodel = torch.empty((n_big, grid.n_pix), device=dev)
-        for c0 in range(0, n_big, 8192):
-            bmodel[c0:c0 + 8192] = ip.forward(
-                torch.tensor(db["truth"][c0:c0 + 8192], dtype=torch.float32, device=dev),
-                torch.tensor(db["b_true"][c0:c0 + 8192], dtype=torch.float32, device=dev))
-        bf, bv = S.finish_obs(bmodel.double().cpu().numpy(), db)
-        del bmodel
-        bin_ = [torch.tensor(bf, device=dev), torch.tensor(bv, device=dev),
-                torch.tensor(db["good"], device=dev),
-                torch.tensor(db["theta0"], dtype=torch.float32, device=dev)]
-        mo = dict(opts, precision="tf32x3", fp64_normal_eq=1)
-        bout = ip.fit(*bin_, **mo)
-        torch.cuda.synchronize()
-        t_ms = []
-        for k in range(max(1, min(args.steps, 2))):
-            flush.fill_(float(k))
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            bout = ip.fit(*bin_, out=bout, **mo)
-            b.record(stream)
+    try:
+        if not args.no_mixed and not args.no_large:
+            _, n_big, off, kw = S.workload("mixed65536")
+            db = S.draw_batch(grid, n_big, S.SPECTRA_SEED + off + 1000 * rank, **kw)
+            bmodel = torch.empty((n_big, grid.n_pix), device=dev)
+            for c0 in range(0, n_big, 8192):
+                bmodel[c0:c0 + 8192] = ip.forward(
+                    torch.tensor(db["truth"][c0:c0 + 8192], dtype=torch.float32, device=dev),
+                    torch.tensor(db["b_true"][c0:c0 + 8192], dtype=torch.float32, device=dev))
+            bf, bv = S.finish_obs(bmodel.double().cpu().numpy(), db)
+            del bmodel
+            bin_ = [torch.tensor(bf, device=dev), torch.tensor(bv, device=dev),
+                    torch.tensor(db["good"], device=dev),
+                    torch.tensor(db["theta0"], dtype=torch.float32, device=dev)]
+            mo = dict(opts, precision="tf32x3", fp64_normal_eq=1)
+            bout = ip.fit(*bin_, **mo)
             torch.cuda.synchronize()
-            t_ms.append(a.elapsed_time(b))
-        bst = bout["status"].cpu().numpy()
-        bconv = int(((bst & 3) != 0).sum())
-        sample = np.arange(0, n_big, n_big // 512)[:512]
-        within = None
-        if not args.no_cpu_baseline:
-            from oracle import oracle as O
-            M = O.Model(C, S.EXPS, grid.dln, grid.pad, grid.n_pix, DEG, S.BASIS_LO, S.BASIS_HI,
-                        S.BOX_LO, S.BOX_HI)
-            th0 = np.asarray(db["theta0"][sample], np.float32).astype(np.float64)
-            ref = O.fit(M, bf[sample], bv[sample], db["good"][sample], th0,
-                        threads=O.lib().orc_max_threads(), max_steps=MAX_STEPS)
-            err = np.abs(bout["theta"].double().cpu().numpy()[sample] - ref["theta"])[:, :4]
-            within = float(np.all(err <= np.array([1.0, 0.005, 0.005, 0.1]), axis=1).mean())
-        mixed_large = {"value": bconv / (sum(t_ms) / len(t_ms) / 1e3), "unit": UNIT,
-                       "fit_ms": sum(t_ms) / len(t_ms), "converged": bconv, "n_spectra": n_big,
-                       "precision": "tf32x3+float-float normal equations",
-                       "within_tol_of_oracle_frac": within,
-                       "oracle_sample": f"{len(sample)} spectra (every {n_big // 512}th), FP64 oracle fit"}
-        del bin_, bout
+            t_ms = []
+            for k in range(max(1, min(args.steps, 2))):
+                flush.fill_(float(k))
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                bout = ip.fit(*bin_, out=bout, **mo)
+                b.record(stream)
+                torch.cuda.synchronize()
+                t_ms.append(a.elapsed_time(b))
+            bst = bout["status"].cpu().numpy()
+            bconv = int(((bst & 3) != 0).sum())
+            sample = np.arange(0, n_big, n_big // 512)[:512]
+            within = None
+            if not args.no_cpu_baseline:
+                from oracle import oracle as O
+                M = O.Model(C, S.EXPS, grid.dln, grid.pad, grid.n_pix, DEG, S.BASIS_LO, S.BASIS_HI,
+                            S.BOX_LO, S.BOX_HI)
+                th0 = np.asarray(db["theta0"][sample], np.float32).astype(np.float64)
+                ref = O.fit(M, bf[sample], bv[sample], db["good"][sample], th0,
+                            threads=O.lib().orc_max_threads(), max_steps=MAX_STEPS)
+                err = np.abs(bout["theta"].double().cpu().numpy()[sample] - ref["theta"])[:, :4]
+                within = float(np.all(err <= np.array([1.0, 0.005, 0.005, 0.1]), axis=1).mean())
+            mixed_large = {"value": bconv / (sum(t_ms) / len(t_ms) / 1e3), "unit": UNIT,
+                           "fit_ms": sum(t_ms) / len(t_ms), "converged": bconv, "n_spectra": n_big,
+                           "precision": "tf32x3+float-float normal equations",
+                           "within_tol_of_oracle_frac": within,
+                           "oracle_sample": f"{len(sample)} spectra (every {n_big // 512}th), FP64 oracle fit"}
+            del bin_, bout
+    except Exception as e:       # a failed extra is reported; the headline still prints
+        mixed_large = {"error": f"{type(e).__name__}: {e}"}
 
     # ---- curvature-aware step (Levenberg-Marquardt, the paper's outlook): same batch
     lm = {}
-    if not args.no_mixed:
-        lo = dict(max_steps=100, tol=1e-10, legendre_deg=DEG, optimizer="lm")
-        lout = ip.fit(g_flux, g_ivar, g_good, g_th0, **lo)
-        torch.cuda.synchronize()
-        t_ms = []
-        for k in range(max(1, args.steps)):
-            flush.fill_(float(k))
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            lout = ip.fit(g_flux, g_ivar, g_good, g_th0, out=lout, **lo)
-            b.record(stream)
+    try:
+        if not args.no_mixed:
+            lo = dict(max_steps=100, tol=1e-10, legendre_deg=DEG, optimizer="lm")
+            lout = ip.fit(g_flux, g_ivar, g_good, g_th0, **lo)
             torch.cuda.synchronize()
-            t_ms.append(a.elapsed_time(b))
-        lst = lout["status"].cpu().numpy()
-        lconv = int(((lst & 3) != 0).sum())
-        lm = {"value": lconv / (sum(t_ms) / len(t_ms) / 1e3), "unit": UNIT,
-              "fit_ms": sum(t_ms) / len(t_ms), "converged": lconv,
-              "mean_iterations": float(lout["steps"].float().mean()),
-              "loss_vs_adam_median_ratio": float(torch.median(lout["loss"] / out["loss"]).item()),
-              "note": "Levenberg-Marquardt to the least-squares minimum (Gauss-Newton predicted decrease <= 1e-10 S)"}
+            t_ms = []
+            for k in range(max(1, args.steps)):
+                flush.fill_(float(k))
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                lout = ip.fit(g_flux, g_ivar, g_good, g_th0, out=lout, **lo)
+                b.record(stream)
+                torch.cuda.synchronize()
+                t_ms.append(a.elapsed_time(b))
+            lst = lout["status"].cpu().numpy()
+            lconv = int(((lst & 3) != 0).sum())
+            lm = {"value": lconv / (sum(t_ms) / len(t_ms) / 1e3), "unit": UNIT,
+                  "fit_ms": sum(t_ms) / len(t_ms), "converged": lconv,
+                  "mean_iterations": float(lout["steps"].float().mean()),
+                  "loss_vs_adam_median_ratio": float(torch.median(lout["loss"] / out["loss"]).item()),
+                  "note": "Levenberg-Marquardt to the least-squares minimum (Gauss-Newton predicted decrease <= 1e-10 S)"}
+    except Exception as e:       # a failed extra is reported; the headline still prints
+        lm = {"error": f"{type(e).__name__}: {e}"}
 
     # ---- Clean outlier masking (stage 6, Eq. 8): the same batch with eight
     # cosmic-ray-like three-pixel spikes added to every spectrum; mask updates
     # every 30 steps (at most 11), as the paper's Clean strategy
     clean = {}
-    if not args.no_mixed:
-        rs = np.random.default_rng(S.SPECTRA_SEED + 77 + 1000 * rank)
-        n_sp = 8
-        rows = np.repeat(np.arange(N_SPEC), n_sp)
-        cols = rs.integers(0, grid.n_pix - 3, size=N_SPEC * n_sp)
-        med = np.median(flux, axis=1)
-        amp = (med[rows] * rs.uniform(0.5, 3.0, size=N_SPEC * n_sp)).astype(np.float32)
-        spiky = flux.copy()
-        for o, f in enumerate((1.0, 0.5, 0.2)):
-            np.add.at(spiky, (rows, cols + o), amp * np.float32(f))
-        c_flux = torch.tensor(spiky, device=dev)
-        co = dict(opts, clean=1)
-        cout = ip.fit(c_flux, g_ivar, g_good, g_th0, **co)          # warm-up
-        torch.cuda.synchronize()
-        t_ms = []
-        for k in range(max(1, args.steps)):
-            flush.fill_(float(k))
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            cout = ip.fit(c_flux, g_ivar, g_good, g_th0, out=cout, **co)
-            b.record(stream)
+    try:
+        if not args.no_mixed:
+            rs = np.random.default_rng(S.SPECTRA_SEED + 77 + 1000 * rank)
+            n_sp = 8
+            rows = np.repeat(np.arange(N_SPEC), n_sp)
+            cols = rs.integers(0, grid.n_pix - 3, size=N_SPEC * n_sp)
+            med = np.median(flux, axis=1)
+            amp = (med[rows] * rs.uniform(0.5, 3.0, size=N_SPEC * n_sp)).astype(np.float32)
+            spiky = flux.copy()
+            for o, f in enumerate((1.0, 0.5, 0.2)):
+                np.add.at(spiky, (rows, cols + o), amp * np.float32(f))
+            c_flux = torch.tensor(spiky, device=dev)
+            co = dict(opts, clean=1)
+            cout = ip.fit(c_flux, g_ivar, g_good, g_th0, **co)          # warm-up
             torch.cuda.synchronize()
-            t_ms.append(a.elapsed_time(b))
-        nout = ip.fit(c_flux, g_ivar, g_good, g_th0, **opts)         # same spiky data, no Clean
-        torch.cuda.synchronize()
-        cst = cout["status"].cpu().numpy()
-        cconv = int(((cst & 3) != 0).sum())
-        ref_t = out["theta"][:, 0].cpu().numpy()                       # spike-free fit
-        dc = np.abs(cout["theta"][:, 0].cpu().numpy() - ref_t)
-        dn = np.abs(nout["theta"][:, 0].cpu().numpy() - ref_t)
-        clean = {"value": cconv / (sum(t_ms) / len(t_ms) / 1e3), "unit": UNIT,
-                 "fit_ms": sum(t_ms) / len(t_ms), "converged": cconv, "n_spectra": N_SPEC,
-                 "mean_steps": float(cout["steps"].float().mean()),
-                 "median_abs_dteff_vs_spike_free_fit_K": {"clean": float(np.median(dc)),
-                                                          "no_clean": float(np.median(dn))},
-                 "workload": "lamost4096x3909 + 8 three-pixel spikes per spectrum, Clean every 30 steps"}
-        del c_flux
+            t_ms = []
+            for k in range(max(1, args.steps)):
+                flush.fill_(float(k))
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                cout = ip.fit(c_flux, g_ivar, g_good, g_th0, out=cout, **co)
+                b.record(stream)
+                torch.cuda.synchronize()
+                t_ms.append(a.elapsed_time(b))
+            nout = ip.fit(c_flux, g_ivar, g_good, g_th0, **opts)         # same spiky data, no Clean
+            torch.cuda.synchronize()
+            cst = cout["status"].cpu().numpy()
+            cconv = int(((cst & 3) != 0).sum())
+            ref_t = out["theta"][:, 0].cpu().numpy()                       # spike-free fit
+            dc = np.abs(cout["theta"][:, 0].cpu().numpy() - ref_t)
+            dn = np.abs(nout["theta"][:, 0].cpu().numpy() - ref_t)
+            clean = {"value": cconv / (sum(t_ms) / len(t_ms) / 1e3), "unit": UNIT,
+                     "fit_ms": sum(t_ms) / len(t_ms), "converged": cconv, "n_spectra": N_SPEC,
+                     "mean_steps": float(cout["steps"].float().mean()),
+                     "median_abs_dteff_vs_spike_free_fit_K": {"clean": float(np.median(dc)),
+                                                              "no_clean": float(np.median(dn))},
+                     "workload": "lamost4096x3909 + 8 three-pixel spikes per spectrum, Clean every 30 steps"}
+            del c_flux
+    except Exception as e:       # a failed extra is reported; the headline still prints
+        clean = {"error": f"{type(e).__name__}: {e}"}
 
     # ---- piecewise Teff-regime emulator (Eq. 1 with f1..f5; 25/26/19-term cold,
     # warm and hot regimes): its own 4096-spectrum batch over Teff 3300-11500 K
     piecewise = {}
-    if not args.no_mixed:
-        tabs = S.make_piecewise_tables(grid)
-        ipw = lasp.Interp.piecewise(tabs, S.PW_EXPS, grid.n_pix, grid.pad, grid.dln, S.PW_BASIS_LO,
-                                    S.PW_BASIS_HI, S.TEFF_BLEND, S.PW_BOX_LO, S.PW_BOX_HI)
-        _, n_pw, off, kw = S.workload("piecewise4096")
-        dp = S.draw_batch(grid, n_pw, S.SPECTRA_SEED + off + 1000 * rank, **kw)
-        pmodel = ipw.forward(torch.tensor(dp["truth"], dtype=torch.float32, device=dev),
-                             torch.tensor(dp["b_true"], dtype=torch.float32, device=dev))
-        pf, pv = S.finish_obs(pmodel.double().cpu().numpy(), dp)
-        pin = [torch.tensor(pf, device=dev), torch.tensor(pv, device=dev),
-               torch.tensor(dp["good"], device=dev),
-               torch.tensor(dp["theta0"], dtype=torch.float32, device=dev)]
-        pout = ipw.fit(*pin, **opts)
-        torch.cuda.synchronize()
-        t_ms = []
-        for k in range(max(1, args.steps)):
-            flush.fill_(float(k))
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            pout = ipw.fit(*pin, out=pout, **opts)
-            b.record(stream)
+    try:
+        if not args.no_mixed:
+            tabs = S.make_piecewise_tables(grid)
+            ipw = lasp.Interp.piecewise(tabs, S.PW_EXPS, grid.n_pix, grid.pad, grid.dln, S.PW_BASIS_LO,
+                                        S.PW_BASIS_HI, S.TEFF_BLEND, S.PW_BOX_LO, S.PW_BOX_HI)
+            _, n_pw, off, kw = S.workload("piecewise4096")
+            dp = S.draw_batch(grid, n_pw, S.SPECTRA_SEED + off + 1000 * rank, **kw)
+            pmodel = ipw.forward(torch.tensor(dp["truth"], dtype=torch.float32, device=dev),
+                                 torch.tensor(dp["b_true"], dtype=torch.float32, device=dev))
+            pf, pv = S.finish_obs(pmodel.double().cpu().numpy(), dp)
+            pin = [torch.tensor(pf, device=dev), torch.tensor(pv, device=dev),
+                   torch.tensor(dp["good"], device=dev),
+                   torch.tensor(dp["theta0"], dtype=torch.float32, device=dev)]
+            pout = ipw.fit(*pin, **opts)
             torch.cuda.synchronize()
-            t_ms.append(a.elapsed_time(b))
-        pst = pout["status"].cpu().numpy()
-        pconv = int(((pst & 3) != 0).sum())
-        perr = np.abs(pout["theta"].double().cpu().numpy() - dp["truth"])
-        piecewise = {"value": pconv / (sum(t_ms) / len(t_ms) / 1e3), "unit": UNIT,
-                     "fit_ms": sum(t_ms) / len(t_ms), "converged": pconv,
-                     "mean_steps": float(pout["steps"].float().mean()),
-                     "median_abs_teff_err_vs_truth_K": float(np.median(perr[:, 0])),
-                     "workload": "piecewise4096x3909_k25+26+19_teff3300-11500_snr5-100"}
-        ipw.close()
+            t_ms = []
+            for k in range(max(1, args.steps)):
+                flush.fill_(float(k))
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                pout = ipw.fit(*pin, out=pout, **opts)
+                b.record(stream)
+                torch.cuda.synchronize()
+                t_ms.append(a.elapsed_time(b))
+            pst = pout["status"].cpu().numpy()
+            pconv = int(((pst & 3) != 0).sum())
+            perr = np.abs(pout["theta"].double().cpu().numpy() - dp["truth"])
+            piecewise = {"value": pconv / (sum(t_ms) / len(t_ms) / 1e3), "unit": UNIT,
+                         "fit_ms": sum(t_ms) / len(t_ms), "converged": pconv,
+                         "mean_steps": float(pout["steps"].float().mean()),
+                         "median_abs_teff_err_vs_truth_K": float(np.median(perr[:, 0])),
+                         "workload": "piecewise4096x3909_k25+26+19_teff3300-11500_snr5-100"}
+            ipw.close()
+    except Exception as e:       # a failed extra is reported; the headline still prints
+        piecewise = {"error": f"{type(e).__name__}: {e}"}
 
     pk, pk_kind = peaks()
     fit_avg = sum(fit_ms) / len(fit_ms)
@@ -576,12 +594,17 @@ def run_ours(args):
     }
     if rank == 0 and not args.no_served:
         tabs = {S.LAMOST.name: C, S.DESI.name: S.make_table(S.DESI)}
-        res["served"] = served_stream(torch, lasp, [S.LAMOST, S.DESI], tabs, native=True)
-        res["served_python"] = served_stream(torch, lasp, [S.LAMOST, S.DESI], tabs, native=False)
-        res["served_mixed"] = served_stream(torch, lasp, [S.LAMOST, S.DESI], tabs, native=True,
-                                            precision="tf32x3", fp64_normal_eq=1)
+        for key, kw in (("served", dict(native=True)), ("served_python", dict(native=False)),
+                        ("served_mixed", dict(native=True, precision="tf32x3", fp64_normal_eq=1))):
+            try:
+                res[key] = served_stream(torch, lasp, [S.LAMOST, S.DESI], tabs, **kw)
+            except Exception as e:   # a failed extra is reported; the headline still prints
+                res[key] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0 and not args.no_cpu_baseline:
-        res["cpu_baseline"] = cpu_baseline(args.cpu_sample, grid, C, ip, torch)
+        try:
+            res["cpu_baseline"] = cpu_baseline(args.cpu_sample, grid, C, ip, torch)
+        except Exception as e:
+            res["cpu_baseline"] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0:
         print(json.dumps(res))
     if dist:
