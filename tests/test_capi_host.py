@@ -94,3 +94,19 @@ def test_null_handle_calls_fail_cleanly(lasp):
     assert lib.lasp_backward(None, 1, None, None, 6, None, None, None, None) == lasp.EINVAL
     assert lib.lasp_interp_eval(None, 1, None, None, 0, None) == lasp.EINVAL
     lib.lasp_free_interp(None)
+    # slot pools and the native server: null handles and bad counts
+    P = ct.c_void_p
+    lib.lasp_slots_step.argtypes = [P, ct.c_int, P]
+    lib.lasp_slots_step_running.argtypes = [P, ct.c_int, ct.c_int, P]
+    lib.lasp_slots_admit.argtypes = [P, ct.c_int, P, P, P, P, P, P]
+    lib.lasp_slots_fetch.argtypes = [P, P, P, P, P, P, P]
+    assert lib.lasp_slots_step(None, 25, None) == lasp.EINVAL
+    assert lib.lasp_slots_step_running(None, 25, 10, None) == lasp.EINVAL
+    assert lib.lasp_slots_admit(None, 1, None, None, None, None, None, None) == lasp.EINVAL
+    assert lib.lasp_slots_fetch(None, None, None, None, None, None, None) == lasp.EINVAL
+    lib.lasp_slots_free(None)
+    n = ct.c_int(-1)
+    lib.lasp_server_tick.argtypes = [P, ct.POINTER(ct.c_int)]
+    assert lib.lasp_server_tick(None, ct.byref(n)) == lasp.EINVAL and n.value == 0
+    lib.lasp_server_pending.argtypes = [P, ct.POINTER(ct.c_int64)]
+    assert lib.lasp_server_pending(None, ct.byref(ct.c_int64())) == lasp.EINVAL
