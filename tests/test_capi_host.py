@@ -110,3 +110,24 @@ def test_null_handle_calls_fail_cleanly(lasp):
     assert lib.lasp_server_tick(None, ct.byref(n)) == lasp.EINVAL and n.value == 0
     lib.lasp_server_pending.argtypes = [P, ct.POINTER(ct.c_int64)]
     assert lib.lasp_server_pending(None, ct.byref(ct.c_int64())) == lasp.EINVAL
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/lasp.h is a C header: a C99 translation unit using it compiles
+    cleanly (-Wall -Wextra -pedantic -Werror)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    src = tmp_path / "use_lasp.c"
+    src.write_text('#include "lasp.h"\n'
+                   "int main(void) {\n"
+                   "    lasp_fit_opts o;\n"
+                   "    lasp_default_opts(&o);\n"
+                   "    return lasp_version() > 0 && o.window == 50 ? 0 : 1;\n"
+                   "}\n")
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-c",
+                        f"-I{inc}", str(src), "-o", str(tmp_path / "use_lasp.o")],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
