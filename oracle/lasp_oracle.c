@@ -412,19 +412,20 @@ unsigned orc_stop_rule(const double* hist, int t, int window, double tol, int ma
 }
 
 /* Clean update after evaluating at x_t (stage 6 schedule of stage 8): from
- * the residual eps at x_t, the new mask takes effect from step t + 1. */
+ * the residual eps at x_t, the new mask takes effect from step t + 1.  The
+ * weighted residual and model enter the mask rules in double precision. */
 static void clean_update(int p, const double* y, const double* Wb, const double* eps, int update,
                          unsigned char* keep, double* W) {
-    float* r = malloc(sizeof(float) * p);
-    float* m = malloc(sizeof(float) * p);
+    double* r = malloc(sizeof(double) * p);
+    double* m = malloc(sizeof(double) * p);
     unsigned char* used = malloc(p);
     for (int j = 0; j < p; ++j) {
         double s = sqrt(Wb[j]);
-        r[j] = (float)(s * eps[j]);
-        m[j] = (float)(s * (y[j] - eps[j]));
+        r[j] = s * eps[j];
+        m[j] = s * (y[j] - eps[j]);
         used[j] = Wb[j] > 0.0 && keep[j];
     }
-    orc_clean_mask(p, r, m, used, update == 1 ? 0.5f : 0.2f, keep);
+    orc_clean_mask(p, r, m, used, update == 1 ? 0.5 : 0.2, keep);
     for (int j = 0; j < p; ++j) W[j] = keep[j] ? Wb[j] : 0.0;
     free(r); free(m); free(used);
 }
@@ -708,37 +709,43 @@ void orc_resample(int q, double lam1, double dlam, const double* F, int n_out, d
     free(edge);
 }
 
-/* Population standard deviation of r over the pixels with sel[j] != 0, in
- * float32 arithmetic with double-precision sums. */
-static float std_sel(int p, const float* r, const unsigned char* sel) {
+/* Population standard deviation of r over the pixels with sel[j] != 0
+ * (double precision throughout). */
+static double std_sel(int p, const double* r, const unsigned char* sel) {
     double s1 = 0.0, s2 = 0.0;
     int n = 0;
     for (int j = 0; j < p; ++j)
-        if (sel[j]) { s1 += r[j]; s2 += (double)r[j] * r[j]; ++n; }
-    if (n == 0) return 0.0f;
+        if (sel[j]) { s1 += r[j]; s2 += r[j] * r[j]; ++n; }
+    if (n == 0) return 0.0;
     double mean = s1 / n, var = s2 / n - mean * mean;
-    return (float)sqrt(var > 0.0 ? var : 0.0);
+    return sqrt(var > 0.0 ? var : 0.0);
 }
 
-int orc_clean_mask(int p, const float* r, const float* m, const unsigned char* used, float fshift,
+/* Clean mask of stage 6 (Eq. 8), every quantity and comparison in double
+ * precision.  B: |r_j| - f G_j > k sigma with G_j the larger model jump to an
+ * existing neighbour, k = 3 raised to 4, 5, 7 while more than 3% of the used
+ * pixels are flagged; C: used neighbours of B pixels above 2 sigma; D:
+ * same-sign neighbours with no larger |r| above sigma' (the std over used
+ * pixels in neither B nor C), grown until unchanged, at most 20 passes. */
+int orc_clean_mask(int p, const double* r, const double* m, const unsigned char* used, double fshift,
                    unsigned char* keep) {
-    float* G = malloc(sizeof(float) * p);
-    float* lhs = malloc(sizeof(float) * p);
+    double* G = malloc(sizeof(double) * p);
+    double* lhs = malloc(sizeof(double) * p);
     unsigned char* B = calloc(p, 1);
     unsigned char* flag = calloc(p, 1);
     unsigned char* sel = malloc(p);
     for (int j = 0; j < p; ++j) {
-        float g = 0.0f;
-        if (j > 0) g = fabsf(m[j] - m[j - 1]);
-        if (j < p - 1 && fabsf(m[j] - m[j + 1]) > g) g = fabsf(m[j] - m[j + 1]);
+        double g = 0.0;
+        if (j > 0) g = fabs(m[j] - m[j - 1]);
+        if (j < p - 1 && fabs(m[j] - m[j + 1]) > g) g = fabs(m[j] - m[j + 1]);
         G[j] = g;
-        lhs[j] = fabsf(r[j]) - fshift * G[j];
+        lhs[j] = fabs(r[j]) - fshift * G[j];
     }
     int n_used = 0;
     for (int j = 0; j < p; ++j) n_used += used[j] ? 1 : 0;
-    const float sigma = std_sel(p, r, used);
+    const double sigma = std_sel(p, r, used);
     /* B with k = 3, relaxed while more than 3% of the used pixels are flagged */
-    const float ks[4] = {3.0f, 4.0f, 5.0f, 7.0f};
+    const double ks[4] = {3.0, 4.0, 5.0, 7.0};
     int kk = 0;
     for (; kk < 4; ++kk) {
         int nb = 0;
@@ -754,11 +761,11 @@ int orc_clean_mask(int p, const float* r, const float* m, const unsigned char* u
     for (int j = 0; j < p; ++j) {
         if (!used[j] || B[j]) continue;
         int nbB = (j > 0 && B[j - 1]) || (j < p - 1 && B[j + 1]);
-        if (nbB && lhs[j] > 2.0f * sigma) flag[j] = 1;
+        if (nbB && lhs[j] > 2.0 * sigma) flag[j] = 1;
     }
     /* sigma' over used pixels not in B or C */
     for (int j = 0; j < p; ++j) sel[j] = used[j] && !flag[j];
-    const float sigp = std_sel(p, r, sel);
+    const double sigp = std_sel(p, r, sel);
     /* D: grow along same-sign, non-increasing residuals above sigma' */
     unsigned char* nxt = malloc(p);
     for (int it = 0; it < 20; ++it) {
@@ -769,7 +776,7 @@ int orc_clean_mask(int p, const float* r, const float* m, const unsigned char* u
             for (int d = -1; d <= 1; d += 2) {
                 int i = j + d;
                 if (i < 0 || i >= p || !flag[i]) continue;
-                if (r[i] * r[j] > 0.0f && fabsf(r[j]) <= fabsf(r[i]) && lhs[j] > sigp) {
+                if (r[i] * r[j] > 0.0 && fabs(r[j]) <= fabs(r[i]) && lhs[j] > sigp) {
                     nxt[j] = 1;
                     changed = 1;
                 }

@@ -162,9 +162,9 @@ void orc_resample(int q, double lam1, double dlam, const double* F, int n_out, d
  * |r| - fshift G > 2 sigma; D: neighbours j' of flagged pixels j (B, C or D)
  * with r_j r_j' > 0, |r_j'| <= |r_j| and |r_j'| - fshift G_j' > sigma', sigma'
  * the std over used pixels not in B or C, repeated until unchanged (at most
- * 20 passes).  keep[j] = used[j] and not flagged.  Decisions are taken in
- * float32 on float32 inputs (the kernel's precision).  Returns the k used. */
-int orc_clean_mask(int p, const float* r, const float* m, const unsigned char* used, float fshift,
+ * 20 passes).  keep[j] = used[j] and not flagged.  Every quantity and every
+ * comparison is in double precision.  Returns the k used. */
+int orc_clean_mask(int p, const double* r, const double* m, const unsigned char* used, double fshift,
                    unsigned char* keep);
 
 /* Curvature-aware fit (the paper's outlook, sec. 4.5): Levenberg-Marquardt

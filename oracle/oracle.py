@@ -82,7 +82,7 @@ def lib():
             _lib.orc_max_threads.restype = ct.c_int
             _lib.orc_resample.argtypes = [ct.c_int, ct.c_double, ct.c_double, P, ct.c_int,
                                           ct.c_double, ct.c_double, P]
-            _lib.orc_clean_mask.argtypes = [ct.c_int, P, P, P, ct.c_float, P]
+            _lib.orc_clean_mask.argtypes = [ct.c_int, P, P, P, ct.c_double, P]
             _lib.orc_clean_mask.restype = ct.c_int
             _lib.orc_fit_lm.argtypes = [P, P, ct.c_int, P, P, P, P, ct.c_int, ct.c_double, P, P, P,
                                         P, ct.c_int]
@@ -308,9 +308,10 @@ def resample(F, lam1, dlam, n_out, ln_lam0, dln):
 
 
 def clean_mask(r, m, used, fshift):
-    """Clean outlier mask (Eq. 8) on float32 weighted residual r and model m."""
-    r = np.ascontiguousarray(r, dtype=np.float32)
-    m = np.ascontiguousarray(m, dtype=np.float32)
+    """Clean outlier mask (Eq. 8) of the weighted residual r and model m, with
+    every quantity and decision in double precision."""
+    r = _f64(r)
+    m = _f64(m)
     used = np.ascontiguousarray(used, dtype=np.uint8)
     keep = np.zeros(len(r), dtype=np.uint8)
     k = lib().orc_clean_mask(len(r), _p(r), _p(m), _p(used), float(fshift), _p(keep))

@@ -1,12 +1,14 @@
 """Clean outlier masking (stage 6, Eq. 8) on the GPU against the FP64
-oracle: the mask itself on identical float32 inputs (bit-exact decisions,
-taken in float32 on both sides), and Clean fits of spectra with cosmic-ray
-spikes and sky-like residual runs."""
+oracle: the mask itself on identical float32 inputs (the kernel decides in
+float32, the oracle in double precision; differences only at borderline
+comparisons), and Clean fits of spectra with cosmic-ray spikes and sky-like
+residual runs."""
 import numpy as np
 import pytest
 
 import lasp_synth as S
 from oracle import oracle as O
+from tests import clean_check as CC
 from tests.helpers import TOL, observed, table
 
 torch = pytest.importorskip("torch")
@@ -34,19 +36,30 @@ def _residuals(N, p, seed):
 
 
 @pytest.mark.parametrize("p", [1024, 3909, 7781])
-def test_clean_mask_matches_oracle(p):
+@pytest.mark.parametrize("fshift", [0.5, 0.2])
+def test_clean_mask_matches_oracle(p, fshift):
+    """The kernel takes every Clean decision in float32, the oracle in double
+    precision.  Where the masks differ, every differing pixel must be
+    explained by a comparison within float32 rounding of its threshold (and
+    the spread of such a flip along a flagged run); any other difference
+    fails.  The borderline count is printed."""
     from paper_2512_24840_gb300 import lasp
     lasp.load(build=True)
     N = 24
     r, m, used = _residuals(N, p, 90 + p)
     keep, k = lasp.clean_mask(torch.tensor(r, device=DEV), torch.tensor(m, device=DEV),
-                              torch.tensor(used, device=DEV), 0.5)
+                              torch.tensor(used, device=DEV), fshift)
     keep, k = keep.cpu().numpy(), k.cpu().numpy()
-    for fshift in (0.5,):
-        for i in range(N):
-            ref, kr = O.clean_mask(r[i], m[i], used[i], fshift)
-            assert k[i] == kr, (i, k[i], kr)
-            assert np.array_equal(keep[i], ref), (i, np.where(keep[i] != ref)[0])
+    n_diff = n_border = 0
+    for i in range(N):
+        ref, kr = O.clean_mask(r[i], m[i], used[i], fshift)
+        ok, nb, why = CC.check(r[i], m[i], used[i], fshift, keep[i], int(k[i]), ref, kr)
+        assert ok, (i, why)
+        if k[i] != kr or not np.array_equal(keep[i], ref):
+            n_diff += 1
+            n_border += nb
+    print(f"clean mask p={p} f_shift={fshift}: {n_diff} of {N} spectra differ from the FP64 "
+          f"oracle, {n_border} borderline pixels")
     assert np.any(k == 4) or np.any(k == 5) or np.any(k == 7)
 
 
