@@ -24,6 +24,12 @@
  *  - Row-major layouts.  Physical parameters theta are ordered
  *    (Teff [K], log g [dex], [Fe/H] [dex], RV [km/s], sigma_v [km/s]).
  *  - Per-spectrum outcomes are reported in status bits, not return codes.
+ *  - Bounded waits.  The tensor-core kernels wait on memory barriers for their
+ *    bulk copies and MMAs; every such wait gives up after a fixed number of
+ *    polls (far longer than any correct wait), sets a device flag, lets its
+ *    copies and MMAs in flight complete and returns.  Where the flag is read
+ *    back is stated per call; it surfaces as LASP_ETIMEOUT, and fits stepped
+ *    after it get LASP_ST_TIMEOUT instead of a converged status.
  */
 #ifndef LASP_H
 #define LASP_H
@@ -54,6 +60,9 @@ extern "C" {
 #define LASP_ST_SINGULAR  32u   /* continuum normal equations not positive definite  */
 #define LASP_ST_NODATA    64u   /* fewer than D+1+5 usable pixels, or weight <= 0    */
 #define LASP_ST_RUNNING  128u   /* (slot state only) fit not finished yet             */
+#define LASP_ST_TIMEOUT  256u   /* a bounded device wait gave up while this fit was
+                                   stepped: the fit ended there, its result is not
+                                   valid (theta = the last parameters, loss NaN)     */
 
 /* ---- arithmetic of the interpolator contraction and the normal equations ---- */
 #define LASP_PREC_FP32   0   /* FP32 CUDA-core contraction, FP32 normal equations      */
@@ -215,7 +224,11 @@ typedef struct {
  * (each table value loaded once for the four); each spectrum stops on its own
  * rule and its place goes to the next spectrum at once.  Device workspace of
  * about 8 n_pix bytes a spectrum comes from the stream's memory pool for the
- * call.  Asynchronous on `stream`. */
+ * call.  Asynchronous on `stream` at LASP_PREC_FP32.  At a tensor-core
+ * precision the steps run as replays of a captured graph of 8 steps, and the
+ * call reads the active count (and the timeout flag) after each replay, so
+ * it returns when the fit is done; LASP_ETIMEOUT when a bounded wait gave up
+ * (the fits stepped from then on carry LASP_ST_TIMEOUT). */
 int lasp_fit_batch(lasp_interp h, const lasp_batch* batch, const lasp_fit_opts* opts,
                    lasp_result* result, void* stream);
 
@@ -270,7 +283,10 @@ int lasp_slots_step(lasp_slots s, int budget, void* stream);
 int lasp_slots_step_running(lasp_slots s, int budget, int n_running, void* stream);
 
 /* Copy every slot's theta (n_slots x 5), loss, steps, status and weight to
- * host buffers (any may be NULL) on `stream`. */
+ * host buffers (any may be NULL) on `stream`.  In a tensor-core pool a
+ * bounded wait that gave up during a step call ends every fit that call
+ * stepped with status LASP_ST_TIMEOUT (the flag is cleared at the start of
+ * each step call). */
 int lasp_slots_fetch(lasp_slots s, float* theta, float* loss, int32_t* steps, uint32_t* status,
                      float* weight, void* stream);
 
@@ -317,7 +333,9 @@ int lasp_server_submit(lasp_server s, int lane, const float* flux, const float* 
                        const uint8_t* good, const float* theta0, int64_t tag);
 
 /* One scheduling round (see above); *n_finished (may be NULL) receives the
- * number of fits retired in it.  Blocks until the round's GPU work is done. */
+ * number of fits retired in it.  Blocks until the round's GPU work is done.
+ * Returns LASP_ETIMEOUT when a fit retired in this round carries
+ * LASP_ST_TIMEOUT (its result is still queued, with that status). */
 int lasp_server_tick(lasp_server s, int* n_finished);
 
 /* Pop up to max finished results into out (host); *n receives the count. */
@@ -349,7 +367,10 @@ int lasp_backward(lasp_interp h, int N, const float* theta, const float* b, int 
                   const float* gmodel, float* gtheta, float* gb, void* stream);
 
 /* The interpolator contraction alone (Eq. 1): Fp = phi(theta) C, device
- * N x n_model output, with the arithmetic of `precision` (LASP_PREC_*). */
+ * N x n_model output, with the arithmetic of `precision` (LASP_PREC_*).
+ * At LASP_PREC_FP32 asynchronous.  At a tensor-core precision synchronous:
+ * the call waits for its kernel and returns LASP_ETIMEOUT when a bounded
+ * wait gave up; the outputs of the tiles not computed are then NaN. */
 int lasp_interp_eval(lasp_interp h, int N, const float* theta, float* Fp, int precision,
                      void* stream);
 
@@ -371,11 +392,16 @@ int lasp_interp_eval(lasp_interp h, int N, const float* theta, float* Fp, int pr
  * above LASP_STATIC_MAX_MODEL_PIX is rejected with LASP_EINVAL.
  *
  * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  Every
- * call shares the array and rewrites it: calls whose work overlaps on the GPU
- * (different streams, or different host threads on one device) race and must
- * be serialised by the caller.  Errors: LASP_EINVAL, LASP_EGRID, LASP_ENODEV,
- * LASP_ECUDA.  Asynchronous on `stream`. */
+ * device current) and zeroes its timeout flag; make that first call before
+ * any stream capture.  Every call shares the array and rewrites it: calls
+ * whose work overlaps on the GPU (different streams, or different host
+ * threads on one device) race and must be serialised by the caller.
+ * A bounded wait that gives up writes NaN into the outputs of the tiles it
+ * did not compute and leaves the flag set; the next call made outside stream
+ * capture reads the flag after the work already on `stream` (a host wait on
+ * that stream), clears it and returns LASP_ETIMEOUT without doing its own
+ * work.  Errors: LASP_EINVAL, LASP_EGRID, LASP_ENODEV, LASP_ECUDA,
+ * LASP_ETIMEOUT.  Its kernels run asynchronously on `stream`. */
 #define LASP_STATIC_MAX_MODEL_PIX 8192
 int lasp_interp_eval_static(const lasp_interp_desc* desc, const float* coeff, int N,
                             const float* theta, float* Fp, int precision, void* stream);
@@ -411,6 +437,13 @@ int lasp_clean_mask(int N, int p, const float* r, const float* m, const uint8_t*
 
 /* Number of kernels the last call on this thread enqueued (for accounting). */
 int lasp_last_launches(void);
+
+/* Testing hook for the timeout path: with polls >= 0 the first table-copy
+ * wait of every CTA of the tensor-core kernels launched (or captured) from
+ * then on gives up after `polls` polls -- a wait issued before any MMA, whose
+ * copy is then drained under the normal limit before the CTA exits; polls < 0
+ * restores the normal limits.  Process-wide.  Always LASP_OK. */
+int lasp_test_wait_limit(int polls);
 
 const char* lasp_strerror(int code);
 int lasp_version(void);

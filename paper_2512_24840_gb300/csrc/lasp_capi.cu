@@ -1,4 +1,5 @@
 // C-ABI of liblasp.so: validation, interpolator handle, launches.
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -19,17 +20,29 @@ struct lasp_interp_s {
     TcImages tc;             // tensor-core tile images of the table
 };
 
+namespace {
+
+thread_local int g_last_launches = 0;
+std::atomic<int> g_test_wait0{-1};      // lasp_test_wait_limit: -1 = normal limits
+
+}  // namespace
+
 namespace lasp {
 int cuda_rc(cudaError_t e) {
     if (e == cudaSuccess) return LASP_OK;
     if (e == cudaErrorMemoryAllocation) return LASP_ENOMEM;
     return LASP_ECUDA;
 }
+
+uint32_t first_wait_limit(uint32_t normal) {
+    const int w = g_test_wait0.load(std::memory_order_relaxed);
+    return w >= 0 ? (uint32_t)w : normal;
+}
+
+void set_last_launches(int n) { g_last_launches = n; }
 }  // namespace lasp
 
 namespace {
-
-thread_local int g_last_launches = 0;
 
 constexpr double kCkms = 299792.458;
 
@@ -44,13 +57,13 @@ int check_device(int* dev) {
         return LASP_ENODEV;
     }
     if (cudaGetDevice(dev) != cudaSuccess) return LASP_ENODEV;
-    cudaDeviceProp prop;
-    if (cudaGetDeviceProperties(&prop, *dev) != cudaSuccess) return LASP_ENODEV;
-    if (prop.major != 10 || prop.minor != 3) return LASP_ENODEV;   // built for sm_103a only
+    int major = 0, minor = 0;
+    if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, *dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, *dev) != cudaSuccess)
+        return LASP_ENODEV;
+    if (major != 10 || minor != 3) return LASP_ENODEV;   // built for sm_103a only
     return LASP_OK;
 }
-
-int threads_for(int n_pix) { return n_pix <= 16 * 256 ? 256 : 512; }
 
 template <typename F>
 int dispatch_deg(int D, F&& f) {
@@ -116,6 +129,11 @@ extern "C" {
 int lasp_version(void) { return 1; }
 
 int lasp_last_launches(void) { return g_last_launches; }
+
+int lasp_test_wait_limit(int polls) {
+    g_test_wait0.store(polls < 0 ? -1 : polls, std::memory_order_relaxed);
+    return LASP_OK;
+}
 
 const char* lasp_strerror(int code) {
     switch (code) {

@@ -53,7 +53,7 @@ struct Grp {
     int *rise, *t, *flags;
     // active lists (double buffered) and their counts
     int* list[2];
-    int* count;                   // count[0], count[1]
+    int* count;                   // count[0], count[1]: active list lengths; count[2]: err
     float* Fp;                    // N x ldf
     float* taps;                  // N x 3 x TAPBUF: g, dg/dmu, dg/dsigma of the spectrum's next step
     int* hh;                      // N: kernel half width of those taps
@@ -66,7 +66,9 @@ struct Grp {
     int ldp;                      // row stride of Y and Wt: n_pix rounded up to 16
     uint8_t *A_hi, *A_lo;         // K3 A images: nblk x nch x 16 KB
     float* dphi;                  // KSPLIT x list position x 32 (partial sums)
-    int* err;
+    int* err;                     // count[2]: set when a bounded wait gives up (K1, K3); K4 then
+                                  // ends every fit it steps with LASP_ST_TIMEOUT
+    uint32_t wait0;               // poll limit of each K1 CTA's first table-copy wait
     // inputs / outputs
     const float *flux, *ivar, *theta0;
     const uint8_t* good;
@@ -211,7 +213,7 @@ __global__ void __launch_bounds__(128) k1_interp(const Grp G, int par, const uin
     tc::tc_fence_after();
     const uint32_t tmem = tmem_base;
     constexpr uint32_t idesc = tc::idesc_f32acc(PREC == 2 ? 1u : 2u, 128, 128);
-    bool pending = false;
+    bool pending = false, mma_pending = false;
     uint32_t phase = 0;
     for (int t = blockIdx.y; t < n_tiles; t += gridDim.y) {
     if (tid == 0) {
@@ -220,7 +222,8 @@ __global__ void __launch_bounds__(128) k1_interp(const Grp G, int par, const uin
         tc::bulk_g2s(Ahi, img + (size_t)t * TC_TILE_BYTES, TC_TILE_BYTES, &bar_tma);
         if (PREC == 3) tc::bulk_g2s(Alo, img_lo + (size_t)t * TC_TILE_BYTES, TC_TILE_BYTES, &bar_tma);
         pending = true;
-        if (!tc::mbar_wait_bounded(&bar_tma, phase, kWait)) {
+        // the CTA's first wait comes before any MMA: its limit may be shortened for tests
+        if (!tc::mbar_wait_bounded(&bar_tma, phase, t == (int)blockIdx.y ? G.wait0 : kWait)) {
             atomicExch(G.err, 1);
             s_ok = 0;
         } else {
@@ -246,6 +249,7 @@ __global__ void __launch_bounds__(128) k1_interp(const Grp G, int par, const uin
                 }
             }
             tc::mma_commit(&bar_mma);
+            mma_pending = true;
         }
     }
     __syncthreads();
@@ -275,9 +279,12 @@ __global__ void __launch_bounds__(128) k1_interp(const Grp G, int par, const uin
     tc::tc_fence_before();
     __syncthreads();
     if (!s_ok) break;
+    if (tid == 0) mma_pending = false;
     phase ^= 1u;
     }
+    // after a timeout: the copy and the MMAs still in flight complete (bounded) before exit
     if (tid == 0 && pending) tc::mbar_wait_bounded(&bar_tma, phase, kWait);
+    if (tid == 0 && mma_pending) tc::mbar_wait_bounded(&bar_mma, phase, kWait);
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, 128);
 }
@@ -839,19 +846,21 @@ __global__ void __launch_bounds__(128) k3_back(const Grp G, int par, const uint8
                 issue(issued++);
             }
         }
-        if (ok) tc::mma_commit(&done);
-        else {
+        tc::mma_commit(&done);        // arrives once every MMA issued so far has completed
+        if (!ok) {
             atomicExch(G.err, 1);
             s_ok = 0;
-            // let copies already issued land before the CTA exits
+            // let copies already issued and the MMAs in flight finish before the CTA exits
             for (int c = 0; c < issued; ++c)
                 tc::mbar_wait_bounded(&full[c % K3_STAGES], (uint32_t)((c / K3_STAGES) & 1), kWait);
+            tc::mbar_wait_bounded(&done, 0, kWait);
         }
     }
     __syncthreads();
     if (s_ok) {
         if (!tc::mbar_wait_bounded(&done, 0, kWait)) {
             atomicExch(G.err, 1);
+            if (tid == 0) tc::mbar_wait_bounded(&done, 0, kWait);   // MMAs in flight: once more
         } else {
             tc::tc_fence_after();
             const int pos = s0 + warp * 32 + lane;
@@ -882,6 +891,19 @@ __global__ void __launch_bounds__(256) k4_adam(const Grp G, int par) {
     if (pos >= G.count[par]) return;
     const int id = G.list[par][pos];
     const ModelDev& M = G.M;
+    if (*(volatile int*)G.err) {
+        // a bounded wait of this step gave up: the step's values are not valid,
+        // so the fit ends here with LASP_ST_TIMEOUT (never reported converged)
+        if (lane < 5) G.theta[5 * id + lane] = phys_of(M, lane, G.x[5 * id + lane]);
+        if (lane == 0) {
+            G.loss_out[id] = NAN;
+            G.steps[id] = G.t[id];
+            G.status[id] = LASP_ST_TIMEOUT;
+            if (G.weight) G.weight[id] = G.w[id];
+        }
+        if (G.cont && lane < NB) G.cont[(size_t)id * NB + lane] = NAN;
+        return;
+    }
     // loads first: parameter k's Adam state on lane k, the basis adjoint sums on lane k < K
     float xk = 0.0f, mk = 0.0f, vk = 0.0f, gp = 0.0f;
     if (lane < 5) {
@@ -1037,17 +1059,19 @@ int run_grouped(Grp& G, const TcImages& tc, cudaStream_t st, int* launches) {
         e = cuda_rc(cudaStreamEndCapture(cap, &graph));
     }
     if (!e) e = cuda_rc(cudaGraphInstantiate(&exec, graph, 0));
-    int h_count = 0;
+    int h_cnt[3] = {0, 0, 0};       // active count, (other parity), timeout flag
     int nlaunch = 1;
     // every spectrum stops after at most max_steps + 1 evaluations
     const int max_chunks = (G.O.max_steps + 1 + CHUNK_STEPS - 1) / CHUNK_STEPS + 1;
     for (int c = 0; !e && c < max_chunks; ++c) {
         e = cuda_rc(cudaGraphLaunch(exec, st));
         nlaunch += (G.O.joint || G.O.clean ? 5 : 4) * CHUNK_STEPS;
-        if (!e) e = cuda_rc(cudaMemcpyAsync(&h_count, G.count, sizeof(int), cudaMemcpyDeviceToHost, st));
+        if (!e) e = cuda_rc(cudaMemcpyAsync(h_cnt, G.count, sizeof(h_cnt), cudaMemcpyDeviceToHost, st));
         if (!e) e = cuda_rc(cudaStreamSynchronize(st));
-        if (!e && h_count == 0) break;
+        if (!e && h_cnt[0] == 0) break;
     }
+    // a timeout ended every fit it touched (K4): report it
+    if (!e && h_cnt[2]) e = LASP_ETIMEOUT;
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     cudaStreamDestroy(cap);
@@ -1096,7 +1120,7 @@ int lasp_tc_fit_batch(const ModelDev& M, const TcImages& tc, const lasp_batch* b
     G.status = r->status;
     G.cont = r->cont_coeff;
     G.weight = r->weight;
-    G.err = tc.err;
+    G.wait0 = first_wait_limit(kWait);
     const size_t n = (size_t)N;
     int e = LASP_OK;
     auto A = [&](auto** ptr, size_t bytes) {
@@ -1135,6 +1159,7 @@ int lasp_tc_fit_batch(const ModelDev& M, const TcImages& tc, const lasp_batch* b
     if (o->precision == LASP_PREC_TF32X3) A(&G.A_lo, (size_t)G.nblk * G.nch * TC_TILE_BYTES);
     A(&G.dphi, (size_t)KSPLIT * G.nblk * 128 * 32 * 4);
     if (!e) e = cuda_rc(cudaMemsetAsync(G.count, 0, 16, st));
+    G.err = G.count + 2;
     if (!e) {
         const int NT = M.n_pix <= 16 * 256 ? 256 : 512;
         auto go = [&](auto dd) {
@@ -1283,7 +1308,7 @@ int grp_pool_create(const ModelDev& M, const TcImages& tc, int n, const lasp_fit
     G.status = status;
     G.cont = cont;
     G.weight = weight;
-    G.err = tc.err;
+    G.wait0 = first_wait_limit(kWait);
     const size_t N = (size_t)n;
     int e = LASP_OK;
     auto A = [&](auto** ptr, size_t bytes) {
@@ -1294,6 +1319,7 @@ int grp_pool_create(const ModelDev& M, const TcImages& tc, int n, const lasp_fit
     A(&G.prev, N * 4); A(&G.w, N * 4); A(&G.imean, N * 4); A(&G.loss, N * 4); A(&G.gmu, N * 4);
     A(&G.gsg, N * 4); A(&G.b, N * G.NB * 4); A(&G.rise, N * 4); A(&G.t, N * 4); A(&G.flags, N * 4);
     A(&G.list[0], N * 4); A(&G.list[1], N * 4); A(&G.count, 16);
+    G.err = G.count + 2;
     A(&G.Fp, N * G.ldf * 4);
     A(&G.Y, N * G.ldp * 4);
     A(&G.Wt, N * G.ldp * 4);
@@ -1338,6 +1364,9 @@ int grp_pool_admit(GrpPool* P, int count, const int32_t* idx_dev, cudaStream_t s
 
 int grp_pool_step(GrpPool* P, int budget, cudaStream_t st, int* launches) {
     const int replays = (budget + CHUNK_STEPS - 1) / CHUNK_STEPS;
+    // a timeout ends only the fits stepped while it was set (LASP_ST_TIMEOUT)
+    int e0 = cuda_rc(cudaMemsetAsync(P->G.err, 0, sizeof(int), st));
+    if (e0) return e0;
     for (int r = 0; r < replays; ++r) {
         const int e = cuda_rc(cudaGraphLaunch(P->exec, st));
         if (e) return e;

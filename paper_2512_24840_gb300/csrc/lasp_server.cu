@@ -84,18 +84,39 @@ void free_lane(Lane* L) {
 }
 
 // Admit waiting ring entries into free slots and launch one chunk (lane stream).
+// The slot bookkeeping is committed only once every admission call has been
+// accepted; a failed admission leaves the slots free and the entries waiting.
 int launch_lane(Lane* L, int chunk) {
     int64_t first, count;
     {
         std::lock_guard<std::mutex> g(L->mu);
         first = L->admitted;
         count = L->staged - L->admitted;
-        if (count > (int64_t)L->free_slots.size()) count = (int64_t)L->free_slots.size();
+    }
+    if (count > (int64_t)L->free_slots.size()) count = (int64_t)L->free_slots.size();
+    // the slots taken, from the back of the free list
+    for (int64_t r = 0; r < count; ++r) L->h_idx[r] = L->free_slots[L->free_slots.size() - 1 - (size_t)r];
+    int64_t done = 0;
+    while (done < count) {
+        const int64_t e = (first + done) % L->ring;
+        const int64_t m = std::min(count - done, (int64_t)L->ring - e);
+        const size_t p = (size_t)L->n_pix;
+        int rc = lasp_slots_admit(L->pool, (int)m, L->h_idx + done, L->r_flux + e * p, L->r_ivar + e * p,
+                                  L->r_good + e * p, L->r_th0 + e * 5, L->stream);
+        if (rc) {
+            // nothing is committed: the slots stay free and the entries wait for the next tick
+            // (slots whose admission was already enqueued are overwritten when reused)
+            L->admitted_this_tick = first;
+            return rc;
+        }
+        done += m;
+    }
+    {
+        std::lock_guard<std::mutex> g(L->mu);
         for (int64_t r = 0; r < count; ++r) {
             const int s = L->free_slots.back();
             L->free_slots.pop_back();
             const int64_t e = (first + r) % L->ring;
-            L->h_idx[r] = s;
             L->slot_id[s] = L->r_id[e];
             L->slot_tsub[s] = L->r_tsub[e];
             L->slot_busy[s] = 1;
@@ -104,16 +125,6 @@ int launch_lane(Lane* L, int chunk) {
     }
     L->admitted_this_tick = first + count;
     L->busy.fetch_add((int)count);
-    int64_t done = 0;
-    while (done < count) {
-        const int64_t e = (first + done) % L->ring;
-        const int64_t m = std::min(count - done, (int64_t)L->ring - e);
-        const size_t p = (size_t)L->n_pix;
-        int rc = lasp_slots_admit(L->pool, (int)m, L->h_idx + done, L->r_flux + e * p, L->r_ivar + e * p,
-                                  L->r_good + e * p, L->r_th0 + e * 5, L->stream);
-        if (rc) return rc;
-        done += m;
-    }
     if (L->busy == 0) return LASP_OK;
     int rc = lasp_slots_step_running(L->pool, chunk, L->busy, L->stream);
     if (!rc)
@@ -217,6 +228,7 @@ int lasp_server_tick(lasp_server S, int* n_finished) {
     for (Lane* L : S->lanes)
         if (!rc) rc = launch_lane(L, S->chunk);
     int fin = 0;
+    bool timed_out = false;
     for (size_t l = 0; l < S->lanes.size(); ++l) {
         Lane* L = S->lanes[l];
         if (L->busy == 0) {
@@ -244,6 +256,7 @@ int lasp_server_tick(lasp_server S, int* n_finished) {
             r.status = L->o_status[s];
             r.t_submit_ns = L->slot_tsub[s];
             r.t_done_ns = t;
+            if (r.status & LASP_ST_TIMEOUT) timed_out = true;
             done.push_back(r);
             L->slot_busy[s] = 0;
             L->free_slots.push_back(s);
@@ -254,6 +267,9 @@ int lasp_server_tick(lasp_server S, int* n_finished) {
         for (const lasp_served& r : done) S->out.push_back(r);
     }
     if (n_finished) *n_finished = fin;
+    // a bounded device wait gave up in this round: its fits are retired with
+    // LASP_ST_TIMEOUT, and the round reports it
+    if (!rc && timed_out) rc = LASP_ETIMEOUT;
     return rc;
 }
 

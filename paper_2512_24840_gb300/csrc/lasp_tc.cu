@@ -78,13 +78,17 @@ __global__ void build_back_images_kernel(const float* __restrict__ C, int K, int
     }
 }
 
-// PREC: 1 TF32, 2 BF16, 3 split TF32 (hi*hi + hi*lo + lo*hi)
+// PREC: 1 TF32, 2 BF16, 3 split TF32 (hi*hi + hi*lo + lo*hi).  Every wait is
+// bounded; when one gives up the CTA sets *err, writes NaN into every output of
+// the tiles it has not finished, lets its own copies and MMAs in flight
+// complete (bounded again), frees its TMEM and returns.  wait0 bounds the
+// first table-copy wait of the CTA (no MMA issued yet).
 template <int PREC>
 __global__ void __launch_bounds__(128) interp_tc_kernel(const ModelDev M, const float* __restrict__ theta,
                                                         float* __restrict__ Fp, int N,
                                                         const uint8_t* __restrict__ img_a,
                                                         const uint8_t* __restrict__ img_a_lo,
-                                                        int n_tiles, int* err) {
+                                                        int n_tiles, int* err, uint32_t wait0) {
     extern __shared__ uint8_t smraw[];
     uint8_t* base = reinterpret_cast<uint8_t*>(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     uint8_t* Ahi = base;
@@ -148,16 +152,17 @@ __global__ void __launch_bounds__(128) interp_tc_kernel(const ModelDev M, const 
     const uint32_t tmem = tmem_base;
     constexpr uint32_t idesc = tc::idesc_f32acc(PREC == 2 ? 1u : 2u, 128, 128);
     uint32_t phase = 0;
-    bool copy_pending = false;
+    bool copy_pending = false, mma_pending = false;
+    int t = blockIdx.y;
 
-    for (int t = blockIdx.y; t < n_tiles; t += gridDim.y) {
+    for (; t < n_tiles; t += gridDim.y) {
         if (tid == 0) {
             const uint32_t bytes = (PREC == 3 ? 2u : 1u) * (uint32_t)TC_TILE_BYTES;
             tc::mbar_arrive_expect_tx(&bar_tma, bytes);
             tc::bulk_g2s(Ahi, img_a + (size_t)t * TC_TILE_BYTES, TC_TILE_BYTES, &bar_tma);
             if (PREC == 3) tc::bulk_g2s(Alo, img_a_lo + (size_t)t * TC_TILE_BYTES, TC_TILE_BYTES, &bar_tma);
             copy_pending = true;
-            if (!tc::mbar_wait_bounded(&bar_tma, phase, kWaitLimit)) {
+            if (!tc::mbar_wait_bounded(&bar_tma, phase, t == (int)blockIdx.y ? wait0 : kWaitLimit)) {
                 atomicExch(err, 1);
                 s_ok = 0;
             } else {
@@ -184,6 +189,7 @@ __global__ void __launch_bounds__(128) interp_tc_kernel(const ModelDev M, const 
                     }
                 }
                 tc::mma_commit(&bar_mma);
+                mma_pending = true;
             }
         }
         __syncthreads();
@@ -211,10 +217,20 @@ __global__ void __launch_bounds__(128) interp_tc_kernel(const ModelDev M, const 
         tc::tc_fence_before();
         __syncthreads();
         if (!s_ok) break;
+        if (tid == 0) mma_pending = false;
         phase ^= 1u;
     }
-    // a copy still in flight after a timeout: wait for it (bounded) before exit
-    if (tid == 0 && copy_pending) tc::mbar_wait_bounded(&bar_tma, phase, kWaitLimit);
+    if (!s_ok) {
+        // the tiles from t on are not computed: NaN marks them in the output
+        for (int tt = t; tt < n_tiles; tt += gridDim.y) {
+            const int mpix = tt * TC_TILE + tid;
+            if (mpix < M.n_model)
+                for (int s = s0; s < N && s < s0 + 128; ++s) Fp[(size_t)s * M.n_model + mpix] = NAN;
+        }
+        // copies and MMAs still in flight complete before the CTA's memory goes
+        if (tid == 0 && copy_pending) tc::mbar_wait_bounded(&bar_tma, phase, kWaitLimit);
+        if (tid == 0 && mma_pending) tc::mbar_wait_bounded(&bar_mma, phase, kWaitLimit);
+    }
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, 128);
 }
@@ -228,8 +244,6 @@ int tc_build_images(TcImages& t, const float* C, int K, int n_model) {
     int rc = cuda_rc(cudaMalloc(&t.tf32_hi, bytes));
     if (!rc) rc = cuda_rc(cudaMalloc(&t.tf32_lo, bytes));
     if (!rc) rc = cuda_rc(cudaMalloc(&t.bf16, bytes));
-    if (!rc) rc = cuda_rc(cudaMalloc(&t.err, sizeof(int)));
-    if (!rc) rc = cuda_rc(cudaMemset(t.err, 0, sizeof(int)));
     if (rc) return rc;
     const int total = t.n_tiles * TC_TILE * 8;
     build_images_kernel<<<(total + 255) / 256, 256>>>(C, K, n_model, t.n_tiles, (uint8_t*)t.tf32_hi,
@@ -259,27 +273,43 @@ void tc_free_images(TcImages& t) {
     if (t.tf32_hi) cudaFree(t.tf32_hi);
     if (t.tf32_lo) cudaFree(t.tf32_lo);
     if (t.bf16) cudaFree(t.bf16);
-    if (t.err) cudaFree(t.err);
     t = TcImages{};
 }
 
+// Synchronous: the call waits for its kernel and reads back the kernel's
+// timeout flag (a stream-ordered allocation of this call).
 int lasp_tc_interp_eval(const ModelDev& M, const TcImages& t, int N, const float* theta, float* Fp,
                         int precision, cudaStream_t st, int* launches) {
     if (!t.tf32_hi) return LASP_EINVAL;
     const size_t smem = 4 * TC_TILE_BYTES + 1024;
     dim3 grid((N + 127) / 128, t.n_tiles < 65535 ? t.n_tiles : 65535);
-    int rc = LASP_OK;
+    int* err = nullptr;
+    int rc = cuda_rc(cudaMallocAsync((void**)&err, sizeof(int), st));
+    if (rc) return rc;
+    rc = cuda_rc(cudaMemsetAsync(err, 0, sizeof(int), st));
+    const uint32_t wait0 = first_wait_limit(kWaitLimit);
     auto go = [&](auto kern, const void* a, const void* alo) {
         int e = cuda_rc(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         if (e) return e;
-        kern<<<grid, 128, smem, st>>>(M, theta, Fp, N, (const uint8_t*)a, (const uint8_t*)alo, t.n_tiles, t.err);
+        kern<<<grid, 128, smem, st>>>(M, theta, Fp, N, (const uint8_t*)a, (const uint8_t*)alo, t.n_tiles, err,
+                                      wait0);
         return cuda_rc(cudaGetLastError());
     };
-    if (precision == LASP_PREC_TF32) rc = go(interp_tc_kernel<1>, t.tf32_hi, nullptr);
-    else if (precision == LASP_PREC_BF16) rc = go(interp_tc_kernel<2>, t.bf16, nullptr);
-    else if (precision == LASP_PREC_TF32X3) rc = go(interp_tc_kernel<3>, t.tf32_hi, t.tf32_lo);
-    else return LASP_EINVAL;
-    if (!rc) *launches = 1;
+    if (!rc) {
+        if (precision == LASP_PREC_TF32) rc = go(interp_tc_kernel<1>, t.tf32_hi, nullptr);
+        else if (precision == LASP_PREC_BF16) rc = go(interp_tc_kernel<2>, t.bf16, nullptr);
+        else if (precision == LASP_PREC_TF32X3) rc = go(interp_tc_kernel<3>, t.tf32_hi, t.tf32_lo);
+        else rc = LASP_EINVAL;
+    }
+    int h_err = 0;
+    if (!rc) {
+        *launches = 1;
+        rc = cuda_rc(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    }
+    const int rf = cuda_rc(cudaFreeAsync(err, st));
+    if (!rc) rc = rf;
+    if (!rc) rc = cuda_rc(cudaStreamSynchronize(st));
+    if (!rc && h_err) rc = LASP_ETIMEOUT;
     return rc;
 }
 
@@ -303,26 +333,40 @@ constexpr int kStaticMaxTiles = LASP_STATIC_MAX_MODEL_PIX / TC_TILE;
 constexpr size_t kStaticImageBytes = (size_t)kStaticMaxTiles * TC_TILE_BYTES;
 constexpr size_t kStaticBytes = 3 * kStaticImageBytes + 256;
 
-// [TF32 hi image | TF32 lo image | BF16 image | timeout flag]
+// [TF32 hi image | TF32 lo image | BF16 image | timeout flag]; the flag is
+// zero at load (static storage) and cleared when a call reports it
 static __device__ __align__(256) uint8_t g_static_scratch[kStaticBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
 uint8_t* g_static_addr[kMaxDevices] = {};
+bool g_static_sm103[kMaxDevices] = {};
 
 // Device address of g_static_scratch on the current device, looked up once
-// per device (with that device current).  Host code never touches the array
-// through its name: on the host the name is only a stand-in for the symbol.
+// per device (with that device current), together with the check that the
+// device is an sm_103 part.  Host code never touches the array through its
+// name: on the host the name is only a stand-in for the symbol.
 int static_scratch(uint8_t** out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LASP_ENODEV;
     std::lock_guard<std::mutex> lock(g_static_mu);
     if (!g_static_addr[dev]) {
+        int major = 0, minor = 0;
+        if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess)
+            return LASP_ENODEV;
+        g_static_sm103[dev] = major == 10 && minor == 3;
+        if (!g_static_sm103[dev]) return LASP_ENODEV;
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess || !p) return LASP_ECUDA;
+        // the timeout flag starts at zero: set once, finished before the first call goes on
+        uint8_t* flag = static_cast<uint8_t*>(p) + 3 * kStaticImageBytes;
+        if (cudaMemset(flag, 0, 256) != cudaSuccess || cudaStreamSynchronize(cudaStreamLegacy) != cudaSuccess)
+            return LASP_ECUDA;
         g_static_addr[dev] = static_cast<uint8_t*>(p);
     }
+    if (!g_static_sm103[dev]) return LASP_ENODEV;
     *out = g_static_addr[dev];
     return LASP_OK;
 }
@@ -369,6 +413,7 @@ int static_model(const lasp_interp_desc* d, const float* coeff, ModelDev* M) {
 extern "C" int lasp_interp_eval_static(const lasp_interp_desc* desc, const float* coeff, int N,
                                        const float* theta, float* Fp, int precision, void* stream) {
     using namespace lasp;
+    set_last_launches(0);
     if (!desc || N < 0) return LASP_EINVAL;
     if (precision != LASP_PREC_TF32 && precision != LASP_PREC_BF16 && precision != LASP_PREC_TF32X3)
         return LASP_EINVAL;
@@ -378,11 +423,6 @@ extern "C" int lasp_interp_eval_static(const lasp_interp_desc* desc, const float
     if (M.n_model > LASP_STATIC_MAX_MODEL_PIX) return LASP_EINVAL;
     if (N == 0) return LASP_OK;
     if (!coeff || !theta || !Fp) return LASP_EINVAL;
-    int dev = -1;
-    cudaDeviceProp prop;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess ||
-        prop.major != 10 || prop.minor != 3)
-        return LASP_ENODEV;
     uint8_t* base = nullptr;
     rc = static_scratch(&base);
     if (rc) return rc;
@@ -391,23 +431,40 @@ extern "C" int lasp_interp_eval_static(const lasp_interp_desc* desc, const float
     uint8_t* bf = base + 2 * kStaticImageBytes;
     int* err = reinterpret_cast<int*>(base + 3 * kStaticImageBytes);
     cudaStream_t st = (cudaStream_t)stream;
-    const int n_tiles = (M.n_model + TC_TILE - 1) / TC_TILE;
-    // the timeout flag keeps the previous call's value: clear it
-    rc = cuda_rc(cudaMemsetAsync(err, 0, sizeof(int), st));
+    // A wait that gave up in an earlier call left its flag set (and NaN in the
+    // rows it did not compute).  Outside stream capture the flag is read after
+    // the stream's earlier work, cleared, and reported here; during capture it
+    // stays set for the next call made outside capture.
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    rc = cuda_rc(cudaStreamIsCapturing(st, &cs));
     if (rc) return rc;
+    if (cs == cudaStreamCaptureStatusNone) {
+        int prev = 0;
+        rc = cuda_rc(cudaMemcpyAsync(&prev, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        if (!rc) rc = cuda_rc(cudaStreamSynchronize(st));
+        if (!rc && prev) {
+            rc = cuda_rc(cudaMemsetAsync(err, 0, sizeof(int), st));
+            return rc ? rc : LASP_ETIMEOUT;
+        }
+        if (rc) return rc;
+    }
+    const int n_tiles = (M.n_model + TC_TILE - 1) / TC_TILE;
     const int total = n_tiles * TC_TILE * 8;
     build_images_kernel<<<(total + 255) / 256, 256, 0, st>>>(coeff, M.K, M.n_model, n_tiles, hi, lo, bf);
     rc = cuda_rc(cudaGetLastError());
     if (rc) return rc;
     const size_t smem = 4 * TC_TILE_BYTES + 1024;
     dim3 grid((N + 127) / 128, n_tiles);
+    const uint32_t wait0 = first_wait_limit(kWaitLimit);
     auto go = [&](auto kern, const uint8_t* a, const uint8_t* alo) {
         int e = cuda_rc(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         if (e) return e;
-        kern<<<grid, 128, smem, st>>>(M, theta, Fp, N, a, alo, n_tiles, err);
+        kern<<<grid, 128, smem, st>>>(M, theta, Fp, N, a, alo, n_tiles, err, wait0);
         return cuda_rc(cudaGetLastError());
     };
-    if (precision == LASP_PREC_TF32) return go(interp_tc_kernel<1>, hi, nullptr);
-    if (precision == LASP_PREC_BF16) return go(interp_tc_kernel<2>, bf, nullptr);
-    return go(interp_tc_kernel<3>, hi, lo);
+    if (precision == LASP_PREC_TF32) rc = go(interp_tc_kernel<1>, hi, nullptr);
+    else if (precision == LASP_PREC_BF16) rc = go(interp_tc_kernel<2>, bf, nullptr);
+    else rc = go(interp_tc_kernel<3>, hi, lo);
+    if (!rc) set_last_launches(2);
+    return rc;
 }

@@ -20,7 +20,6 @@ struct TcImages {
     void* tf32_lo = nullptr;
     void* bf16 = nullptr;
     int n_tiles = 0;
-    int* err = nullptr;                 // device flag: bounded wait timed out
     // Backward images (dphi = dF' C^T): per chunk of model pixels (32 for TF32,
     // 64 for BF16) a 32-row (basis term) x 128-byte tile, K-major in pixels,
     // 128-byte swizzle (4 KB per chunk).
@@ -33,6 +32,13 @@ struct TcImages {
 constexpr int TC_BK_CHUNK_BYTES = 32 * 128;
 
 int tc_build_images(TcImages& t, const float* C, int K, int n_model);
+
+// Poll limit of the first bounded wait of each CTA of a tensor-core kernel
+// (a table-copy wait, issued before any MMA): `normal`, unless the testing hook
+// lasp_test_wait_limit has set a shorter one.
+uint32_t first_wait_limit(uint32_t normal);
+// Kernel count reported by lasp_last_launches for the calling thread.
+void set_last_launches(int n);
 void tc_free_images(TcImages& t);
 
 int lasp_tc_interp_eval(const ModelDev& M, const TcImages& t, int N, const float* theta, float* Fp,

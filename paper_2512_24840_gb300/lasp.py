@@ -20,6 +20,7 @@ from . import _build
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EGRID, ENODEV, EBUSY = 0, -1, -2, -3, -4, -5, -6, -7
 ST_CONV_TOL, ST_CONV_RISE, ST_MAXSTEPS, ST_NONPOS = 1, 2, 4, 8
 ST_NONFINITE, ST_SINGULAR, ST_NODATA, ST_RUNNING = 16, 32, 64, 128
+ST_TIMEOUT = 256
 PREC = {"fp32": 0, "tf32": 1, "bf16": 2, "tf32x3": 3}
 OPTIMIZER = {"adam": 0, "lm": 1}
 LOSS_MODE = {"separable": 0, "joint": 1}
@@ -75,7 +76,8 @@ EXPORTS = ["lasp_init_interp", "lasp_free_interp", "lasp_default_opts", "lasp_fi
            "lasp_slots_step_running",
            "lasp_slots_fetch", "lasp_interp_eval_static", "lasp_clean_mask",
            "lasp_init_interp_piecewise", "lasp_server_create", "lasp_server_destroy",
-           "lasp_server_submit", "lasp_server_tick", "lasp_server_poll", "lasp_server_pending"]
+           "lasp_server_submit", "lasp_server_tick", "lasp_server_poll", "lasp_server_pending",
+           "lasp_test_wait_limit"]
 
 
 def library_path() -> str:
@@ -129,6 +131,8 @@ def load(build: bool = False):
         lib.lasp_resample_linear.restype = I
         lib.lasp_clean_mask.argtypes = [I, I, P, P, P, ct.c_float, P, P, P]
         lib.lasp_clean_mask.restype = I
+        lib.lasp_test_wait_limit.argtypes = [I]
+        lib.lasp_test_wait_limit.restype = I
         _lib = lib
         return lib
 
@@ -178,6 +182,12 @@ def default_opts(**kw) -> FitOpts:
 
 def last_launches() -> int:
     return int(load().lasp_last_launches())
+
+
+def test_wait_limit(polls: int) -> None:
+    """Testing hook: the first table-copy wait of every CTA of the tensor-core
+    kernels launched from now on gives up after `polls` polls (< 0: normal)."""
+    _check(load().lasp_test_wait_limit(int(polls)), "lasp_test_wait_limit")
 
 
 def resample_linear(coeff_lin, lam1, dlam, n_out, ln_lam0, dln, stream=None):
