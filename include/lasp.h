@@ -70,6 +70,16 @@ extern "C" {
 #define LASP_PREC_BF16   2   /* tcgen05 BF16 contraction, FP32 accumulate               */
 #define LASP_PREC_TF32X3 3   /* tcgen05 3-pass split TF32 (about FP32 accurate)         */
 
+/* ---- precision of the per-spectrum normal equations (lasp_fit_opts.fp64_normal_eq) ----
+ * Each thread forms the products of its own pixels in FP32 and sums them in
+ * FP32 (16 pixels a thread); the options differ in how those partial sums are
+ * added across the CTA and how the (D+1)x(D+1) system is solved. */
+#define LASP_NE_FP32 0   /* FP32 sums, FP32 Cholesky solve                          */
+#define LASP_NE_FF   1   /* float-float: warps added in exact two-sums (~48 bits);
+                            FP32 Cholesky refined once with a float-float residual */
+#define LASP_NE_FP64 2   /* FP64: the partial sums widened to double, added by
+                            double shuffles, Cholesky solve in double            */
+
 /* Interpolator description (Eq. 1 with one polynomial regime; see
  * lasp_piecewise_desc for Teff regimes).
  * The model grid is the observed ln-lambda grid extended by `pad` pixels on
@@ -166,10 +176,11 @@ typedef struct {
     int edge_px;            /* pixels at each end left out of the loss */
     float quantile;         /* w_i = this quantile of the used flux    */
     int precision;          /* LASP_PREC_*                              */
-    int fp64_normal_eq;     /* 1: normal equations at about FP64 precision: cross-warp
-                               sums exact in float-float, the 7x7 solve by an FP32
-                               Cholesky factor refined once with a float-float
-                               residual (no FP64 instructions on the step path) */
+    int fp64_normal_eq;     /* precision of the continuum normal equations (Eq. 6) and
+                               of the stage-9 sums, LASP_NE_*: FP32 (0), float-float
+                               (1, about 48 bits without FP64 instructions) or FP64
+                               (2).  The name is kept for the ABI; only
+                               LASP_NE_FP64 issues FP64 instructions. */
     int clean;              /* 1: Clean outlier masking (stage 6, Eq. 8); Adam
                                fits with the separable loss, every precision */
     int clean_every;        /* mask update every this many steps (30)   */
@@ -347,9 +358,10 @@ int lasp_server_pending(lasp_server s, int64_t* n);
 /* Stage 9 parameter uncertainties at theta (device, N x 5 physical, e.g. the
  * fitted values): Jacobian J of the weighted residual sqrt(W) eps w.r.t. the
  * physical parameters with the continuum re-solved (variable projection),
- * cov = (r.r / (n - 5)) (J^T J)^{-1} with n the used pixels; J^T J is
- * summed in float-float and inverted by an FP32 Cholesky inverse refined with
- * a float-float residual (about double precision without FP64 instructions).  sigma: device N x 5 = sqrt(diag cov).
+ * cov = (r.r / (n - 5)) (J^T J)^{-1} with n the used pixels.  The sums (the
+ * normal equations, J^T J, r.r) are added across the CTA in float-float, or
+ * in FP64 when opts->fp64_normal_eq is LASP_NE_FP64; the 5x5 inverse and the
+ * scale are computed in FP64.  sigma: device N x 5 = sqrt(diag cov).
  * cov: device N x 25 FP64 or NULL.  status: device N or NULL (LASP_ST_*). */
 int lasp_errors(lasp_interp h, const lasp_batch* batch, const lasp_fit_opts* opts,
                 const float* theta, float* sigma, double* cov, uint32_t* status,

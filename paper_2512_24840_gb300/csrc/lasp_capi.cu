@@ -87,6 +87,7 @@ int check_opts(const lasp_fit_opts* o, int n_pix) {
     if (o->edge_px < 0 || 2 * o->edge_px >= n_pix) return LASP_EINVAL;
     if (!(o->quantile >= 0.0f && o->quantile <= 1.0f)) return LASP_EINVAL;
     if (o->precision < LASP_PREC_FP32 || o->precision > LASP_PREC_TF32X3) return LASP_EINVAL;
+    if (o->fp64_normal_eq < LASP_NE_FP32 || o->fp64_normal_eq > LASP_NE_FP64) return LASP_EINVAL;
     if (o->clean && (o->clean_every < 1 || o->clean_max < 0)) return LASP_EINVAL;
     if (o->optimizer != LASP_OPT_ADAM && o->optimizer != LASP_OPT_LM) return LASP_EINVAL;
     if (o->optimizer == LASP_OPT_LM && (o->precision != LASP_PREC_FP32 || o->clean)) return LASP_EINVAL;
@@ -108,7 +109,7 @@ FitOpts to_dev(const lasp_fit_opts* o) {
     d.max_steps = o->max_steps;
     d.edge_px = o->edge_px;
     d.quantile = o->quantile;
-    d.fp64_ne = o->fp64_normal_eq ? 1 : 0;
+    d.fp64_ne = o->fp64_normal_eq;
     d.clean = o->clean ? 1 : 0;
     d.clean_every = o->clean_every;
     d.clean_max = o->clean_max;

@@ -11,6 +11,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "lasp.h"
+
 namespace lasp {
 
 constexpr int KMAX = 32;          // rows of one tensor-core K block (single-regime tables)
@@ -516,6 +518,74 @@ __device__ __forceinline__ void block_sum_ff(float (&v)[NV], float* red, float2*
         out[threadIdx.x] = s;
     }
     __syncthreads();
+}
+
+// Block-wide sum of NV floats per thread with every addition in FP64: each
+// thread's value is widened to double, the warp adds by xor shuffles, thread
+// i < NV adds the warps in a fixed order.  redd: (NT/32) NV doubles; outd[i]
+// is visible to every thread after the closing barrier.
+template <int NV, int NT>
+__device__ __forceinline__ void block_sum_f64(const float (&v)[NV], double* redd, double* outd) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        double s = (double)v[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) redd[warp * NV + i] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w) s += redd[w * NV + threadIdx.x];
+        outd[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+// Inverse of a 5x5 symmetric positive definite matrix in FP64 (one thread):
+// Cholesky factor A = L L^T, then X = L^-T L^-1 column by column.  Returns
+// false when a pivot is not positive.
+__device__ __forceinline__ bool inv_spd5_f64(const double (&A)[25], double (&X)[25]) {
+    double L[5][5], id[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            double s = A[i * 5 + j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
+            if (i == j) {
+                if (!(s > 0.0)) return false;
+                L[i][i] = sqrt(s);
+                id[i] = 1.0 / L[i][i];
+            } else {
+                L[i][j] = s * id[j];
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+        double t[5], x[5];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            double s = i == c ? 1.0 : 0.0;
+#pragma unroll
+            for (int k = 0; k < i; ++k) s -= L[i][k] * t[k];
+            t[i] = s * id[i];
+        }
+#pragma unroll
+        for (int i = 4; i >= 0; --i) {
+            double s = t[i];
+#pragma unroll
+            for (int k = i + 1; k < 5; ++k) s -= L[k][i] * x[k];
+            x[i] = s * id[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 5; ++i) X[i * 5 + c] = x[i];
+    }
+    return true;
 }
 
 // Inverse of a 5x5 symmetric positive definite matrix given in float-float

@@ -82,7 +82,8 @@ struct FitSmem {
         gsg = o;  o += TAPBUF;
         phi = o;  o += round32(K);          // sized by the table: the SM's L1 keeps the rest
         dphi = o; o += DPS * round32(K);
-        red = o;  o += (NT / 32) * nv_max > PREP_RED ? (NT / 32) * nv_max : PREP_RED;
+        const int red_n = (NT / 32) * (nv_max > 2 * round32(NV) ? nv_max : 2 * round32(NV));
+        red = o;  o += red_n > PREP_RED ? red_n : PREP_RED;
         out = o;  o += 2 * nv_max + 16;
         ring = o; o += WINMAX;
         total = o;
@@ -182,6 +183,81 @@ __device__ __forceinline__ void reduce_to_warp0_ff(float (&v)[NV], float* red, f
         }
         __syncwarp();
     }
+}
+
+// As reduce_to_warp0 with every partial sum in FP64: each thread's FP32 sum
+// over its own pixels is widened to double, the warp adds by xor shuffles in
+// double and warp 0 adds the warps in double.  redd: (NT/32) NV doubles;
+// outd[i] is visible to warp 0 on return.
+template <int NV, int NT>
+__device__ __forceinline__ void reduce_to_warp0_f64(const float (&v)[NV], double* redd, double* outd) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        double s = (double)v[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) redd[warp * NV + i] = s;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        for (int i = lane; i < NV; i += 32) {
+            double s = 0.0;
+#pragma unroll
+            for (int w = 0; w < NT / 32; ++w) s += redd[w * NV + i];
+            outd[i] = s;
+        }
+        __syncwarp();
+    }
+}
+
+// Continuum coefficients b of Eq. 6 from each thread's FP32 partial sums of
+// the normal equations (packed upper triangle of G, then r), in the precision
+// the fit options ask for: FP32 (sums and solve in FP32), float-float (warps
+// added in exact two-sums, FP32 Cholesky refined once with a float-float
+// residual), or FP64 (every partial sum beyond the thread's own pixels and the
+// Cholesky solve in double).  sb[a] is b_a, or NaN where G is not positive
+// definite, visible to every thread after the closing barrier.  red: the
+// shared reduction buffer (2 (NT/32) round32(NV) floats), out: 2 NV floats,
+// both 8-byte aligned.
+// F64: whether the FP64 form is compiled in (kernels whose register budget is
+// tight leave it out and are not launched with LASP_NE_FP64).
+template <int D, int NT, bool F64 = true>
+__device__ __forceinline__ void solve_continuum(float (&gacc)[Gram<D>::NV], int prec, float* red, float* out,
+                                                float* sb) {
+    using Gm = Gram<D>;
+    constexpr int NB = D + 1, NV = Gm::NV;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (F64 && prec == LASP_NE_FP64) {
+        double* outd = reinterpret_cast<double*>(out);
+        reduce_to_warp0_f64<NV, NT>(gacc, reinterpret_cast<double*>(red), outd);
+        if (tid == 0) {
+            double bd[NB];
+            const bool ok = chol_solve_rcp<D, double>(outd, outd + Gm::NG, bd);
+#pragma unroll
+            for (int a = 0; a < NB; ++a) sb[a] = ok ? (float)bd[a] : NAN;
+        }
+    } else if (prec == LASP_NE_FF) {
+        float2* outff = reinterpret_cast<float2*>(out);
+        reduce_to_warp0_ff<NV, NT>(gacc, red, outff);
+        if (warp == 0) {
+            const float2* const rh[1] = {outff + Gm::NG};
+            float bf[NB];
+            const bool ok = warp_chol_solve_ff<D, 1>(outff, rh, bf);
+            if (lane == 0)
+#pragma unroll
+                for (int a = 0; a < NB; ++a) sb[a] = ok ? bf[a] : NAN;
+        }
+    } else {
+        reduce_to_warp0<NV, NT>(gacc, red, out);
+        if (tid == 0) {
+            float bf[NB];
+            const bool ok = chol_solve_rcp<D, float>(out, out + Gm::NG, bf);
+#pragma unroll
+            for (int a = 0; a < NB; ++a) sb[a] = ok ? bf[a] : NAN;
+        }
+    }
+    __syncthreads();
 }
 
 // Basis, its derivatives, the active table rows (s_k[0..1]) and the kernel
@@ -426,27 +502,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) fit_kernel(const FitPar
                 }
             }
         }
-        if (P.O.fp64_ne) {
-            float2* outff = reinterpret_cast<float2*>(outd);
-            reduce_to_warp0_ff<NV, NT>(gacc, red, outff);
-            if (warp == 0) {
-                const float2* const rh[1] = {outff + Gm::NG};
-                float bf[NB];
-                const bool ok = warp_chol_solve_ff<D, 1>(outff, rh, bf);
-                if (lane == 0)
-#pragma unroll
-                    for (int a = 0; a < NB; ++a) s_b[a] = ok ? bf[a] : NAN;
-            }
-        } else {
-            reduce_to_warp0<NV, NT>(gacc, red, out);
-            if (tid == 0) {
-                float bf[NB];
-                const bool ok = chol_solve_rcp<D, float>(out, out + Gm::NG, bf);
-#pragma unroll
-                for (int a = 0; a < NB; ++a) s_b[a] = ok ? bf[a] : NAN;
-            }
-        }
-        __syncthreads();
+        solve_continuum<D, NT>(gacc, P.O.fp64_ne, red, out, s_b);
 
         // ---- a6: residual (Eq. 7), loss (Eq. 9); delta = W eps c (unscaled)
         float racc[2] = {0.0f, 0.0f};

@@ -24,9 +24,10 @@
 // brought four lanes to 21.0 ms).
 //
 // The FULL variant adds the Clean update (stage 6; a lane's mask lives in its
-// W row) and resumable slots (a lane resumes a running slot from its saved
+// W row), resumable slots (a lane resumes a running slot from its saved
 // state, suspends it after the step budget, and takes the next one from a
-// list of running slots); the plain batch fit runs the lighter variant.
+// list of running slots) and the FP64 normal equations; the plain batch fit
+// runs the lighter variant.
 #pragma once
 
 #include "lasp_clean.cuh"
@@ -61,6 +62,7 @@ struct MultiSmem {
     __host__ __device__ MultiSmem(int p, int H, int n_model, int NT, int D, int K, int S) {
         const int NB = D + 1, NV = NB * (NB + 1) / 2 + NB;
         const int nv_max = round32(NV > NADJ * S ? NV : NADJ * S);
+        const int red_w = nv_max > 2 * round32(NV) ? nv_max : 2 * round32(NV);   // floats a warp
         dofs = 2 * H + 8;
         int nb = skew_size(n_model + 32);
         if (skew_size(p + 4 * H + 40) > nb) nb = skew_size(p + 4 * H + 40);
@@ -76,7 +78,7 @@ struct MultiSmem {
         lane = o;
         o *= S;
         part = o; o += 4 * S * NT;       // per-thread lane sums, [4 s + q][thread]
-        red = o;  o += (NT / 32) * nv_max;
+        red = o;  o += (NT / 32) * red_w;
         out = o;  o += 2 * nv_max + 16;
         total = o;
     }
@@ -416,27 +418,7 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
                     }
                 }
             }
-            if (P.O.fp64_ne) {
-                float2* outff = reinterpret_cast<float2*>(out);
-                reduce_to_warp0_ff<NV, NT>(gacc, red, outff);
-                if (warp == 0) {
-                    const float2* const rh[1] = {outff + Gm::NG};
-                    float bf[NB];
-                    const bool ok = warp_chol_solve_ff<D, 1>(outff, rh, bf);
-                    if (lane == 0)
-#pragma unroll
-                        for (int a = 0; a < NB; ++a) s_b[s][a] = ok ? bf[a] : NAN;
-                }
-            } else {
-                reduce_to_warp0<NV, NT>(gacc, red, out);
-                if (tid == 0) {
-                    float bf[NB];
-                    const bool ok = chol_solve_rcp<D, float>(out, out + Gm::NG, bf);
-#pragma unroll
-                    for (int a = 0; a < NB; ++a) s_b[s][a] = ok ? bf[a] : NAN;
-                }
-            }
-            __syncthreads();
+            solve_continuum<D, NT, FULL>(gacc, P.O.fp64_ne, red, out, s_b[s]);
 
             // a6: residual (Eq. 7), loss (Eq. 9); delta = W eps c (unscaled)
             float racc[2] = {0.0f, 0.0f};

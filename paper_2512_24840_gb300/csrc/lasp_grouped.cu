@@ -304,7 +304,7 @@ struct RestSmem {
         g = o;    o += TAPBUF;
         gmu = o;  o += TAPBUF;
         gsg = o;  o += TAPBUF;
-        red = o;  o += (NT / 32) * nv_max;
+        red = o;  o += (NT / 32) * (nv_max > 2 * round32(NV) ? nv_max : 2 * round32(NV));
         out = o;  o += 2 * nv_max + 16;
         total = o;
     }
@@ -439,7 +439,9 @@ __device__ __forceinline__ void store_dfp(const Grp& G, int pos, int m0, const f
     }
 }
 
-template <int NT, int D, int PREC>
+// NE64: the FP64 normal equations (LASP_NE_FP64) compiled in; without it the
+// step body keeps the register budget of three CTAs per SM.
+template <int NT, int D, int PREC, bool NE64 = false>
 __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) k2_rest(const Grp G, int par) {
     using Gm = Gram<D>;
     constexpr int NB = D + 1;
@@ -565,27 +567,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) k2_rest(const Grp G, in
             }
         }
     }
-    if (G.O.fp64_ne) {
-        float2* outff = reinterpret_cast<float2*>(outd);
-        reduce_to_warp0_ff<NV, NT>(gacc, red, outff);
-        if (warp == 0) {
-            const float2* const rh[1] = {outff + Gm::NG};
-            float bf[NB];
-            const bool ok = warp_chol_solve_ff<D, 1>(outff, rh, bf);
-            if (lane == 0)
-#pragma unroll
-                for (int a = 0; a < NB; ++a) s_b[a] = ok ? bf[a] : NAN;
-        }
-    } else {
-        reduce_to_warp0<NV, NT>(gacc, red, out);
-        if (tid == 0) {
-            float bf[NB];
-            const bool ok = chol_solve_rcp<D, float>(out, out + Gm::NG, bf);
-#pragma unroll
-            for (int a = 0; a < NB; ++a) s_b[a] = ok ? bf[a] : NAN;
-        }
-    }
-    __syncthreads();
+    solve_continuum<D, NT, NE64>(gacc, G.O.fp64_ne, red, reinterpret_cast<float*>(outd), s_b);
     // residual (Eq. 7), loss (Eq. 9), delta = W eps c
     float racc[2] = {0.0f, 0.0f};
     {
@@ -1007,7 +989,7 @@ int amalloc(T** p, size_t bytes, cudaStream_t st) {
     return cuda_rc(cudaMallocAsync((void**)p, bytes, st));
 }
 
-template <int D, int PREC, int NT>
+template <int D, int PREC, int NT, bool NE64 = false>
 int run_grouped(Grp& G, const TcImages& tc, cudaStream_t st, int* launches) {
     const int N = G.N;
     const ModelDev& M = G.M;
@@ -1025,7 +1007,7 @@ int run_grouped(Grp& G, const TcImages& tc, cudaStream_t st, int* launches) {
     const RestSmem RS(M.n_pix, M.pad, M.n_model, NT, D);
     const size_t smem2 = 4 * (size_t)RS.total;
     int e = cuda_rc(cudaFuncSetAttribute(k1_interp<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1));
-    if (!e) e = cuda_rc(cudaFuncSetAttribute(k2_rest<NT, D, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
+    if (!e) e = cuda_rc(cudaFuncSetAttribute(k2_rest<NT, D, PREC, NE64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
     if (!e) e = cuda_rc(cudaFuncSetAttribute(k3_back<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3));
     if (!e && G.O.clean)
         e = cuda_rc(cudaFuncSetAttribute(kc_clean<NT, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
@@ -1039,7 +1021,7 @@ int run_grouped(Grp& G, const TcImages& tc, cudaStream_t st, int* launches) {
     const int g4 = (N + 7) / 8;
     auto one_step = [&](int par) {
         k1_interp<PREC><<<g1, 128, smem1, st>>>(G, par, img, img_lo, tc.n_tiles);
-        k2_rest<NT, D, PREC><<<N, NT, smem2, st>>>(G, par);
+        k2_rest<NT, D, PREC, NE64><<<N, NT, smem2, st>>>(G, par);
         k3_back<PREC><<<g3, 128, smem3, st>>>(G, par, bk, bk_lo);
         if (G.O.joint) k3j_group<1024><<<1, 1024, 0, st>>>(G);
         if (G.O.clean) kc_clean<NT, D><<<N, NT, smem2, st>>>(G, par);
@@ -1085,6 +1067,8 @@ int lasp_tc_fit_batch(const ModelDev& M, const TcImages& tc, const lasp_batch* b
                       lasp_result* r, void* stream, int* launches) {
     *launches = 0;
     if (!tc.tf32_hi || !tc.bk_hi) return LASP_EINVAL;
+    // FP64 normal equations are compiled into the split-TF32 step body only
+    if (o->fp64_normal_eq == LASP_NE_FP64 && o->precision != LASP_PREC_TF32X3) return LASP_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     Grp G{};
     G.M = M;
@@ -1097,7 +1081,7 @@ int lasp_tc_fit_batch(const ModelDev& M, const TcImages& tc, const lasp_batch* b
     G.O.max_steps = o->max_steps;
     G.O.edge_px = o->edge_px;
     G.O.quantile = o->quantile;
-    G.O.fp64_ne = o->fp64_normal_eq ? 1 : 0;
+    G.O.fp64_ne = o->fp64_normal_eq;
     G.O.joint = o->loss_mode == LASP_LOSS_JOINT ? 1 : 0;
     G.O.clean = o->clean ? 1 : 0;
     G.O.clean_every = o->clean_every;
@@ -1167,10 +1151,12 @@ int lasp_tc_fit_batch(const ModelDev& M, const TcImages& tc, const lasp_batch* b
             if (NT == 256) {
                 if (o->precision == LASP_PREC_TF32) return run_grouped<D, 1, 256>(G, tc, st, launches);
                 if (o->precision == LASP_PREC_BF16) return run_grouped<D, 2, 256>(G, tc, st, launches);
+                if (o->fp64_normal_eq == LASP_NE_FP64) return run_grouped<D, 3, 256, true>(G, tc, st, launches);
                 return run_grouped<D, 3, 256>(G, tc, st, launches);
             }
             if (o->precision == LASP_PREC_TF32) return run_grouped<D, 1, 512>(G, tc, st, launches);
             if (o->precision == LASP_PREC_BF16) return run_grouped<D, 2, 512>(G, tc, st, launches);
+            if (o->fp64_normal_eq == LASP_NE_FP64) return run_grouped<D, 3, 512, true>(G, tc, st, launches);
             return run_grouped<D, 3, 512>(G, tc, st, launches);
         };
         if (o->legendre_deg == 6) e = go(std::integral_constant<int, 6>{});
@@ -1273,7 +1259,8 @@ int grp_pool_create(const ModelDev& M, const TcImages& tc, int n, const lasp_fit
                     float* ivar, uint8_t* good, float* theta0, float* theta, float* loss, int32_t* steps,
                     uint32_t* status, float* cont, float* weight, GrpPool** out) {
     *out = nullptr;
-    if (!tc.tf32_hi || !tc.bk_hi || o->legendre_deg != 6) return LASP_EINVAL;
+    // served tensor-core pools: float-float or FP32 normal equations
+    if (!tc.tf32_hi || !tc.bk_hi || o->legendre_deg != 6 || o->fp64_normal_eq == LASP_NE_FP64) return LASP_EINVAL;
     GrpPool* P = new (std::nothrow) GrpPool();
     if (!P) return LASP_ENOMEM;
     P->tc = tc;
@@ -1288,7 +1275,7 @@ int grp_pool_create(const ModelDev& M, const TcImages& tc, int n, const lasp_fit
     G.O.max_steps = o->max_steps;
     G.O.edge_px = o->edge_px;
     G.O.quantile = o->quantile;
-    G.O.fp64_ne = o->fp64_normal_eq ? 1 : 0;
+    G.O.fp64_ne = o->fp64_normal_eq;
     G.O.clean = o->clean ? 1 : 0;
     G.O.clean_every = o->clean_every;
     G.O.clean_max = o->clean_max;

@@ -72,9 +72,10 @@ int launch_fit_multi(const FitParams& P, cudaStream_t st) {
     const size_t smem_prep = 4 * (size_t)fit_prep_smem_floats(p);
     // resumable slots, and Clean with too few lanes for its scratch, stay on fit_kernel
     if (P.S.x || (P.O.clean && S < 3) || smem > 227 * 1024 || smem_prep > 227 * 1024) return launch_fit<D>(P, st);
+    const bool full = P.O.clean || P.O.fp64_ne == LASP_NE_FP64;
     void (*kern)(const FitParams, const MultiWs) =
-        P.O.clean ? (NT == 256 ? fit_multi_kernel<256, D, S, true> : fit_multi_kernel<512, D, S, true>)
-                  : (NT == 256 ? fit_multi_kernel<256, D, S, false> : fit_multi_kernel<512, D, S, false>);
+        full ? (NT == 256 ? fit_multi_kernel<256, D, S, true> : fit_multi_kernel<512, D, S, true>)
+             : (NT == 256 ? fit_multi_kernel<256, D, S, false> : fit_multi_kernel<512, D, S, false>);
     void (*prep)(const FitParams, const MultiWs) =
         NT == 256 ? fit_prep_kernel<256, D> : fit_prep_kernel<512, D>;
     int e = set_smem_attr(kern, smem);
@@ -163,17 +164,17 @@ int launch_fit_prep_slots(const FitParams& P, const MultiWs& W, const int32_t* i
 template <int D>
 int launch_errors(const ErrParams& P, cudaStream_t st) {
     const int p = P.M.n_pix, H = P.M.pad, nm = P.M.n_model;
-    if (p <= 16 * 256) {
-        size_t smem = err_smem_bytes(p, H, nm, 256);
-        int e = set_smem_attr(errors_kernel<256, D>, smem);
-        if (e) return e;
-        errors_kernel<256, D><<<P.N, 256, smem, st>>>(P);
-    } else {
-        size_t smem = err_smem_bytes(p, H, nm, 512);
-        int e = set_smem_attr(errors_kernel<512, D>, smem);
-        if (e) return e;
-        errors_kernel<512, D><<<P.N, 512, smem, st>>>(P);
-    }
+    const bool f64 = P.O.fp64_ne == LASP_NE_FP64;
+    auto go = [&](auto kern, int NT) {
+        const size_t smem = err_smem_bytes(p, H, nm, NT);
+        int e = set_smem_attr(kern, smem);
+        if (!e) kern<<<P.N, NT, smem, st>>>(P);
+        return e;
+    };
+    int e;
+    if (p <= 16 * 256) e = f64 ? go(errors_kernel<256, D, true>, 256) : go(errors_kernel<256, D, false>, 256);
+    else e = f64 ? go(errors_kernel<512, D, true>, 512) : go(errors_kernel<512, D, false>, 512);
+    if (e) return e;
     return cuda_rc(cudaGetLastError());
 }
 

@@ -183,7 +183,12 @@ __global__ void __launch_bounds__(NT) interp_fp32_kernel(ModelDev M, const float
 // derivatives; db/dtheta from the normal equations,
 //   db_k = G^-1 sum_j W_j P(x_j) dF''_jk (eps_j - F''_j c_j),
 //   J_jk = -sqrt(W_j) (c_j dF''_jk + F''_j (P db_k)_j).
-// cov = (r.r / (n - 5)) (J^T J)^-1; J^T J summed and inverted in FP64.
+// cov = (r.r / (n - 5)) (J^T J)^-1: J^T J summed in float-float (or FP64 with
+// the FP64 normal-equation option), its 5x5 inverse and the scale in FP64.
+
+// Shared reduction space of the errors kernel, floats a warp: 64 doubles
+// (every block sum there has at most 64 values for Legendre degrees <= 8).
+constexpr int ERR_RED_W = 128;
 
 struct ErrParams {
     ModelDev M;
@@ -200,14 +205,16 @@ struct ErrParams {
 
 __host__ inline size_t err_smem_bytes(int p, int H, int n_model, int NT) {
     size_t fl = (size_t)2 * ((p + 3) & ~3) + 4 * (size_t)((n_model + 3) & ~3) + 3 * 96 + (1 + DPS) * KROWS +
-                (size_t)(NT / 32) * 48 + 256;
+                (size_t)(NT / 32) * ERR_RED_W + 256;
     size_t sortb = (size_t)3 * ((p + 3) & ~3);
     return 4 * (fl > sortb ? fl : sortb);
 }
 
 // Two CTAs per SM at 256 threads (128 registers; the shared-memory plan of about
 // 100 KB allows two): a few spills cost far less than halving the resident warps.
-template <int NT, int D>
+// F64: the sums added across the CTA and the 7x7 solves in FP64 (the
+// LASP_NE_FP64 option), else in float-float.
+template <int NT, int D, bool F64>
 __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) errors_kernel(const ErrParams P) {
     using Gm = Gram<D>;
     constexpr int NB = D + 1;
@@ -228,9 +235,13 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) errors_kernel(const Err
     float* phi = g + 288;
     float* dphi = phi + KROWS;
     float* red = phi + (1 + DPS) * KROWS;
-    float* outf = red + (NT / 32) * 48;
+    float* outf = red + (NT / 32) * ERR_RED_W;
     float2* outff = reinterpret_cast<float2*>(outf + ((((size_t)(outf - sm)) & 1) ? 1 : 0));
-    __shared__ float2 s_G[Gm::NV], s_JJ[16];
+    __shared__ float2 s_G[Gm::NV];
+    __shared__ double s_Gd[Gm::NV], s_JJ[16];
+    double* outd = reinterpret_cast<double*>(outff);
+    double* redd = reinterpret_cast<double*>(red);
+    constexpr bool f64 = F64;
     __shared__ float s_b[NB], s_db[5 * NB];
     __shared__ int s_h, s_ok;
 
@@ -335,16 +346,29 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) errors_kernel(const Err
             }
         }
     }
-    block_sum_ff<NV, NT>(gacc, red, outff);
-    if (tid < NV) s_G[tid] = outff[tid];
-    __syncthreads();
-    if (warp == 0) {
-        const float2* const rh[1] = {s_G + Gm::NG};
-        float bd[NB];
-        const bool ok = warp_chol_solve_ff<D, 1>(s_G, rh, bd);
-        if (lane == 0) {
+    // the continuum of Eq. 6 at theta: float-float sums and solve, or FP64
+    if constexpr (f64) {
+        block_sum_f64<NV, NT>(gacc, redd, outd);
+        if (tid < NV) s_Gd[tid] = outd[tid];
+        __syncthreads();
+        if (tid == 0) {
+            double bd[NB];
+            const bool ok = chol_solve_rcp<D, double>(s_Gd, s_Gd + Gm::NG, bd);
             s_ok = ok ? 1 : 0;
-            for (int a = 0; a < NB; ++a) s_b[a] = bd[a];
+            for (int a = 0; a < NB; ++a) s_b[a] = (float)bd[a];
+        }
+    } else {
+        block_sum_ff<NV, NT>(gacc, red, outff);
+        if (tid < NV) s_G[tid] = outff[tid];
+        __syncthreads();
+        if (warp == 0) {
+            const float2* const rh[1] = {s_G + Gm::NG};
+            float bd[NB];
+            const bool ok = warp_chol_solve_ff<D, 1>(s_G, rh, bd);
+            if (lane == 0) {
+                s_ok = ok ? 1 : 0;
+                for (int a = 0; a < NB; ++a) s_b[a] = bd[a];
+            }
         }
     }
     __syncthreads();
@@ -384,16 +408,27 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) errors_kernel(const Err
             tacc[5 * NB] = fmaf(Wj * e, e, tacc[5 * NB]);
         }
     }
-    block_sum_ff<NT2, NT>(tacc, red, outff);
-    if (warp == 0) {
-        // db_k = G^-1 t_k, the five systems on lanes 0..4
-        const float2* const rh[5] = {outff, outff + NB, outff + 2 * NB, outff + 3 * NB, outff + 4 * NB};
-        float dbk[NB];
-        warp_chol_solve_ff<D, 5>(s_G, rh, dbk);
-        if (lane < 5)
-            for (int a = 0; a < NB; ++a) s_db[lane * NB + a] = dbk[a];
+    if constexpr (f64) {
+        block_sum_f64<NT2, NT>(tacc, redd, outd);
+        if (tid < 5) {
+            // db_k = G^-1 t_k, system k on thread k
+            double dbk[NB];
+            chol_solve_rcp<D, double>(s_Gd, outd + tid * NB, dbk);
+            for (int a = 0; a < NB; ++a) s_db[tid * NB + a] = (float)dbk[a];
+        }
+        if (tid == 0) s_JJ[15] = outd[5 * NB];
+    } else {
+        block_sum_ff<NT2, NT>(tacc, red, outff);
+        if (warp == 0) {
+            // db_k = G^-1 t_k, the five systems on lanes 0..4
+            const float2* const rh[5] = {outff, outff + NB, outff + 2 * NB, outff + 3 * NB, outff + 4 * NB};
+            float dbk[NB];
+            warp_chol_solve_ff<D, 5>(s_G, rh, dbk);
+            if (lane < 5)
+                for (int a = 0; a < NB; ++a) s_db[lane * NB + a] = dbk[a];
+        }
+        if (tid == 0) s_JJ[15] = (double)outff[5 * NB].x + (double)outff[5 * NB].y;
     }
-    if (tid == 0) s_JJ[15] = outff[5 * NB];
     __syncthreads();
     // J_jk and J^T J (15 sums: FP32 over the thread's 16 pixels, FP64 across threads)
     float dbl[5][NB];
@@ -426,14 +461,19 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) errors_kernel(const Err
                 for (int b2 = a; b2 < 5; ++b2) { jj[q] = fmaf(Jr[a], Jr[b2], jj[q]); ++q; }
         }
     }
-    // the 15 sums: FP32 within warps, float-float across them
+    // the 15 sums: FP32 within each thread, then float-float or FP64 across threads
     __syncthreads();                     // the db solves are done reading outff
-    block_sum_ff<15, NT>(jj, red, outff);
-    if (tid < 15) s_JJ[tid] = outff[tid];
+    if constexpr (f64) {
+        block_sum_f64<15, NT>(jj, redd, outd);
+        if (tid < 15) s_JJ[tid] = outd[tid];
+    } else {
+        block_sum_ff<15, NT>(jj, red, outff);
+        if (tid < 15) s_JJ[tid] = (double)outff[tid].x + (double)outff[tid].y;
+    }
     __syncthreads();
     if (tid == 0) {
-        float2 A[25];
-        float Ai[25];
+        // cov = s^2 (J^T J)^-1: the 5x5 inverse and the scale in FP64
+        double A[25], Ai[25];
         int q = 0;
         for (int a = 0; a < 5; ++a)
             for (int b2 = a; b2 < 5; ++b2) {
@@ -441,11 +481,11 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) errors_kernel(const Err
                 A[b2 * 5 + a] = s_JJ[q];
                 ++q;
             }
-        const bool ok = inv_spd5_ff(A, Ai);
-        const float s2 = (s_JJ[15].x + s_JJ[15].y) / (float)(n_obj - 5);
-        for (int k = 0; k < 5; ++k) P.sigma[5 * i + k] = ok ? sqrtf(s2 * Ai[k * 5 + k]) : NAN;
+        const bool ok = inv_spd5_f64(A, Ai);
+        const double s2 = s_JJ[15] / (double)(n_obj - 5);
+        for (int k = 0; k < 5; ++k) P.sigma[5 * i + k] = ok ? (float)sqrt(s2 * Ai[k * 5 + k]) : NAN;
         if (P.cov)
-            for (int k = 0; k < 25; ++k) P.cov[25 * (size_t)i + k] = ok ? (double)(s2 * Ai[k]) : NAN;
+            for (int k = 0; k < 25; ++k) P.cov[25 * (size_t)i + k] = ok ? s2 * Ai[k] : NAN;
         if (P.status) P.status[i] = ok ? 0u : 32u;
     }
 }

@@ -76,6 +76,27 @@ def test_fp32_with_fp64_normal_equations_matches_oracle(lasp, lamost_case):
     assert ok.mean() >= 0.95
 
 
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+def test_fp64_normal_equations_match_oracle(lasp, lamost_case, prec):
+    """LASP_NE_FP64: the partial sums of the continuum normal equations added
+    across the CTA in double and the 7x7 system solved in double."""
+    M, d, ref = lamost_case
+    out = _fit(lasp, S.LAMOST, d, max_steps=500, precision=prec, fp64_normal_eq=2)
+    assert out["status"][7] == lasp.ST_NODATA
+    use = np.arange(300) != 7
+    err = np.abs(out["theta"] - ref["theta"])[use, :4]
+    ok = np.all(err <= TOL, axis=1)
+    print(f"{prec}+FP64 normal equations: within tolerance {ok.mean():.4f}")
+    assert ok.mean() >= 0.95
+
+
+def test_fp64_normal_equations_only_with_split_tf32(lasp):
+    g = S.SMALL
+    M, d = observed(g, 4, 73, snr=(30, 100), mask_frac=0.0)
+    with pytest.raises(lasp.LaspError):
+        _fit(lasp, g, d, max_steps=10, precision="tf32", fp64_normal_eq=2)
+
+
 def test_mixed_desi_grid_and_max_steps(lasp):
     M, d = observed(S.DESI, 40, 72, snr=(10, 100), mask_frac=0.0, mask_frac_max=0.2)
     d["theta0"] = np.asarray(d["theta0"], np.float32).astype(np.float64)

@@ -296,14 +296,22 @@ def test_batch_invariance_bitwise(lasp):
 # ------------------------------------------------ errors (stage 9)
 
 @pytest.mark.parametrize("grid", [S.SMALL, S.LAMOST], ids=lambda g: g.name)
-def test_errors_match_oracle(lasp, grid):
+@pytest.mark.parametrize("ne", [1, 2], ids=["float-float", "fp64"])
+def test_errors_match_oracle(lasp, grid, ne):
     M, d = observed(grid, 12, 46, snr=(10, 100), mask_frac=0.05)
     d["theta0"] = q32(d["theta0"])
     ip = interp(lasp, grid)
-    e = ip.errors(T(d["flux"]), T(d["ivar"]), T(d["good"], torch.uint8), T(d["theta0"]))
+    e = ip.errors(T(d["flux"]), T(d["ivar"]), T(d["good"], torch.uint8), T(d["theta0"]), fp64_normal_eq=ne)
     sig = H(e["sigma"])
     ref = np.stack([O.errors(M, d["flux"][i], d["ivar"][i], d["good"][i], d["theta0"][i])["sigma"]
                     for i in range(12)])
     rel = np.abs(sig - ref) / ref
+    print(f"stage-9 sigma ({'FP64' if ne == 2 else 'float-float'} sums): median rel. error "
+          f"{np.median(rel):.2e} vs the oracle's central differences")
     assert np.median(rel) < 1e-3 and np.mean(rel < 1e-2) >= 0.95, rel.max(axis=0)
     assert np.all(H(e["status"]) == 0)
+    # the covariance is symmetric positive definite and its diagonal gives sigma
+    cov = e["cov"].cpu().numpy()
+    assert np.allclose(cov, np.transpose(cov, (0, 2, 1)), rtol=1e-12, atol=0)
+    assert np.all(np.linalg.eigvalsh(cov) > 0)
+    np.testing.assert_allclose(np.sqrt(np.diagonal(cov, axis1=1, axis2=2)), sig, rtol=1e-6)
