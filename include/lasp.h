@@ -450,6 +450,23 @@ int lasp_clean_mask(int N, int p, const float* r, const float* m, const uint8_t*
 /* Number of kernels the last call on this thread enqueued (for accounting). */
 int lasp_last_launches(void);
 
+/* Per-kernel device time, for measurement.  lasp_profile(1) switches it on
+ * (process-wide; 0 switches it off).  While it is on, lasp_fit_batch,
+ * lasp_errors and the curvature-aware fit bracket each kernel they launch
+ * with CUDA events on their stream and wait for it, so every kernel is timed
+ * on its own (the tensor-core fit then launches its steps one by one instead
+ * of replaying the step graph); calls become synchronous.  lasp_profile_read
+ * copies up to `max` entries (one per kernel name: launches and total device
+ * milliseconds since the last read) into out, *n the count, and clears the
+ * table. */
+typedef struct {
+    char name[48];
+    int32_t launches;
+    double ms;
+} lasp_kernel_time;
+int lasp_profile(int on);
+int lasp_profile_read(lasp_kernel_time* out, int max, int* n);
+
 /* Testing hook for the timeout path: with polls >= 0 the first table-copy
  * wait of every CTA of the tensor-core kernels launched (or captured) from
  * then on gives up after `polls` polls -- a wait issued before any MMA, whose

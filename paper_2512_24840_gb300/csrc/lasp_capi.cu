@@ -1,6 +1,8 @@
 // C-ABI of liblasp.so: validation, interpolator handle, launches.
 #include <atomic>
 #include <cmath>
+#include <mutex>
+#include <vector>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -8,6 +10,7 @@
 #include "lasp.h"
 #include "lasp_clean.cuh"
 #include "lasp_launch.cuh"
+#include "lasp_prof.cuh"
 #include "lasp_tc.cuh"
 
 using namespace lasp;
@@ -25,7 +28,31 @@ namespace {
 thread_local int g_last_launches = 0;
 std::atomic<int> g_test_wait0{-1};      // lasp_test_wait_limit: -1 = normal limits
 
+// lasp_profile: per-kernel launch counts and device milliseconds since the last read
+std::atomic<int> g_prof{0};
+std::mutex g_prof_mu;
+std::vector<lasp_kernel_time> g_prof_tab;
+
 }  // namespace
+
+namespace lasp {
+bool prof_on() { return g_prof.load(std::memory_order_relaxed) != 0; }
+
+void prof_add(const char* name, float ms) {
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    for (lasp_kernel_time& k : g_prof_tab)
+        if (std::strncmp(k.name, name, sizeof(k.name)) == 0) {
+            k.launches += 1;
+            k.ms += ms;
+            return;
+        }
+    lasp_kernel_time k{};
+    std::strncpy(k.name, name, sizeof(k.name) - 1);
+    k.launches = 1;
+    k.ms = ms;
+    g_prof_tab.push_back(k);
+}
+}  // namespace lasp
 
 namespace lasp {
 int cuda_rc(cudaError_t e) {
@@ -130,6 +157,21 @@ extern "C" {
 int lasp_version(void) { return 1; }
 
 int lasp_last_launches(void) { return g_last_launches; }
+
+int lasp_profile(int on) {
+    g_prof.store(on ? 1 : 0, std::memory_order_relaxed);
+    return LASP_OK;
+}
+
+int lasp_profile_read(lasp_kernel_time* out, int max, int* n) {
+    if (!n || max < 0 || (max > 0 && !out)) return LASP_EINVAL;
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    int k = 0;
+    for (; k < max && k < (int)g_prof_tab.size(); ++k) out[k] = g_prof_tab[k];
+    *n = k;
+    g_prof_tab.clear();
+    return LASP_OK;
+}
 
 int lasp_test_wait_limit(int polls) {
     g_test_wait0.store(polls < 0 ? -1 : polls, std::memory_order_relaxed);

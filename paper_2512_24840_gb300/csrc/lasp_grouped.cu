@@ -16,6 +16,7 @@
 
 #include "lasp_clean.cuh"
 #include "lasp_fit.cuh"
+#include "lasp_prof.cuh"
 #include "lasp_tc.cuh"
 #include "lasp_tc_ptx.cuh"
 
@@ -999,8 +1000,11 @@ int run_grouped(Grp& G, const TcImages& tc, cudaStream_t st, int* launches) {
         const size_t smem = 4 * ((size_t)3 * pa + PREP_RED);
         int e = cuda_rc(cudaFuncSetAttribute(k0_prep<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         if (e) return e;
-        k0_prep<NT><<<N, NT, smem, st>>>(G, nullptr);
-        if ((e = cuda_rc(cudaGetLastError()))) return e;
+        e = prof_time("k0_prep", st, [&]() {
+            k0_prep<NT><<<N, NT, smem, st>>>(G, nullptr);
+            return cuda_rc(cudaGetLastError());
+        });
+        if (e) return e;
     }
     const size_t smem1 = 4 * TC_TILE_BYTES + 1024;
     const size_t smem3 = K3_STAGES * (2 * TC_TILE_BYTES + 2 * TC_BK_CHUNK_BYTES) + 1024;
@@ -1027,6 +1031,38 @@ int run_grouped(Grp& G, const TcImages& tc, cudaStream_t st, int* launches) {
         if (G.O.clean) kc_clean<NT, D><<<N, NT, smem2, st>>>(G, par);
         k4_adam<D><<<g4, 256, 0, st>>>(G, par);
     };
+    // every spectrum stops after at most max_steps + 1 evaluations
+    const int max_chunks = (G.O.max_steps + 1 + CHUNK_STEPS - 1) / CHUNK_STEPS + 1;
+    if (prof_on()) {
+        // measurement mode: the same steps launched one by one without the
+        // graph, each kernel timed on its own (lasp_profile)
+        auto T = [&](const char* name, auto launch) {
+            return prof_time(name, st, [&]() {
+                launch();
+                return cuda_rc(cudaGetLastError());
+            });
+        };
+        int h_cnt[3] = {0, 0, 0};
+        int nl = 1;
+        for (int c = 0; !e && c < max_chunks; ++c) {
+            for (int k = 0; !e && k < CHUNK_STEPS; ++k) {
+                const int par = k & 1;
+                e = T("k1_interp", [&] { k1_interp<PREC><<<g1, 128, smem1, st>>>(G, par, img, img_lo, tc.n_tiles); });
+                if (!e) e = T("k2_rest", [&] { k2_rest<NT, D, PREC, NE64><<<N, NT, smem2, st>>>(G, par); });
+                if (!e) e = T("k3_back", [&] { k3_back<PREC><<<g3, 128, smem3, st>>>(G, par, bk, bk_lo); });
+                if (!e && G.O.joint) e = T("k3j_group", [&] { k3j_group<1024><<<1, 1024, 0, st>>>(G); });
+                if (!e && G.O.clean) e = T("kc_clean", [&] { kc_clean<NT, D><<<N, NT, smem2, st>>>(G, par); });
+                if (!e) e = T("k4_adam", [&] { k4_adam<D><<<g4, 256, 0, st>>>(G, par); });
+                nl += (G.O.joint || G.O.clean ? 5 : 4);
+            }
+            if (!e) e = cuda_rc(cudaMemcpyAsync(h_cnt, G.count, sizeof(h_cnt), cudaMemcpyDeviceToHost, st));
+            if (!e) e = cuda_rc(cudaStreamSynchronize(st));
+            if (!e && h_cnt[0] == 0) break;
+        }
+        if (!e && h_cnt[2]) e = LASP_ETIMEOUT;
+        *launches = nl;
+        return e;
+    }
     // capture CHUNK_STEPS steps (parities 0,1,0,1,...) into one graph
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -1043,8 +1079,6 @@ int run_grouped(Grp& G, const TcImages& tc, cudaStream_t st, int* launches) {
     if (!e) e = cuda_rc(cudaGraphInstantiate(&exec, graph, 0));
     int h_cnt[3] = {0, 0, 0};       // active count, (other parity), timeout flag
     int nlaunch = 1;
-    // every spectrum stops after at most max_steps + 1 evaluations
-    const int max_chunks = (G.O.max_steps + 1 + CHUNK_STEPS - 1) / CHUNK_STEPS + 1;
     for (int c = 0; !e && c < max_chunks; ++c) {
         e = cuda_rc(cudaGraphLaunch(exec, st));
         nlaunch += (G.O.joint || G.O.clean ? 5 : 4) * CHUNK_STEPS;

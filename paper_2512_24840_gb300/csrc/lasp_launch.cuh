@@ -6,6 +6,7 @@
 #include "lasp_fit_multi.cuh"
 #include "lasp_lm.cuh"
 #include "lasp_model.cuh"
+#include "lasp_prof.cuh"
 
 namespace lasp {
 
@@ -42,18 +43,20 @@ static int set_smem_attr(Kern k, size_t bytes) {
 template <int D>
 int launch_fit(const FitParams& P, cudaStream_t st) {
     const int p = P.M.n_pix, H = P.M.pad, nm = P.M.n_model;
-    if (p <= 16 * 256) {
-        size_t smem = fit_smem_bytes(p, H, nm, 256, D, P.M.K);
-        int e = set_smem_attr(fit_kernel<256, D>, smem);
-        if (e) return e;
-        fit_kernel<256, D><<<P.N, 256, smem, st>>>(P);
-    } else {
-        size_t smem = fit_smem_bytes(p, H, nm, 512, D, P.M.K);
-        int e = set_smem_attr(fit_kernel<512, D>, smem);
-        if (e) return e;
-        fit_kernel<512, D><<<P.N, 512, smem, st>>>(P);
-    }
-    return cuda_rc(cudaGetLastError());
+    return prof_time("fit_kernel", st, [&]() {
+        if (p <= 16 * 256) {
+            size_t smem = fit_smem_bytes(p, H, nm, 256, D, P.M.K);
+            int e = set_smem_attr(fit_kernel<256, D>, smem);
+            if (e) return e;
+            fit_kernel<256, D><<<P.N, 256, smem, st>>>(P);
+        } else {
+            size_t smem = fit_smem_bytes(p, H, nm, 512, D, P.M.K);
+            int e = set_smem_attr(fit_kernel<512, D>, smem);
+            if (e) return e;
+            fit_kernel<512, D><<<P.N, 512, smem, st>>>(P);
+        }
+        return cuda_rc(cudaGetLastError());
+    });
 }
 
 
@@ -102,14 +105,14 @@ int launch_fit_multi(const FitParams& P, cudaStream_t st) {
     W.im = reinterpret_cast<float*>(static_cast<char*>(ws) + 256 + wq);
     W.yw = reinterpret_cast<float*>(static_cast<char*>(ws) + 256 + 2 * wq);
     e = cuda_rc(cudaMemsetAsync(ws, 0, 256, st));
-    if (!e) {
-        prep<<<P.N, NT, smem_prep, st>>>(P, W);
-        e = cuda_rc(cudaGetLastError());
-    }
-    if (!e) {
-        kern<<<grid, NT, smem, st>>>(P, W);
-        e = cuda_rc(cudaGetLastError());
-    }
+    if (!e) e = prof_time("fit_prep_kernel", st, [&]() {
+            prep<<<P.N, NT, smem_prep, st>>>(P, W);
+            return cuda_rc(cudaGetLastError());
+        });
+    if (!e) e = prof_time(full ? "fit_multi_kernel<full>" : "fit_multi_kernel", st, [&]() {
+            kern<<<grid, NT, smem, st>>>(P, W);
+            return cuda_rc(cudaGetLastError());
+        });
     const int ef = cuda_rc(cudaFreeAsync(ws, st));
     return e ? e : ef;
 }
@@ -171,11 +174,12 @@ int launch_errors(const ErrParams& P, cudaStream_t st) {
         if (!e) kern<<<P.N, NT, smem, st>>>(P);
         return e;
     };
-    int e;
-    if (p <= 16 * 256) e = f64 ? go(errors_kernel<256, D, true>, 256) : go(errors_kernel<256, D, false>, 256);
-    else e = f64 ? go(errors_kernel<512, D, true>, 512) : go(errors_kernel<512, D, false>, 512);
-    if (e) return e;
-    return cuda_rc(cudaGetLastError());
+    return prof_time(f64 ? "errors_kernel<fp64>" : "errors_kernel", st, [&]() {
+        int e;
+        if (p <= 16 * 256) e = f64 ? go(errors_kernel<256, D, true>, 256) : go(errors_kernel<256, D, false>, 256);
+        else e = f64 ? go(errors_kernel<512, D, true>, 512) : go(errors_kernel<512, D, false>, 512);
+        return e ? e : cuda_rc(cudaGetLastError());
+    });
 }
 
 template <int D>
@@ -213,18 +217,20 @@ int launch_backward(const ModelParams& P, cudaStream_t st) {
 template <int D>
 int launch_lm(const LmParams& P, cudaStream_t st) {
     const int p = P.M.n_pix, H = P.M.pad, nm = P.M.n_model;
-    if (p <= 16 * 256) {
-        size_t smem = lm_smem_bytes(p, H, nm, 256);
-        int e = set_smem_attr(lm_kernel<256, D>, smem);
-        if (e) return e;
-        lm_kernel<256, D><<<P.N, 256, smem, st>>>(P);
-    } else {
-        size_t smem = lm_smem_bytes(p, H, nm, 512);
-        int e = set_smem_attr(lm_kernel<512, D>, smem);
-        if (e) return e;
-        lm_kernel<512, D><<<P.N, 512, smem, st>>>(P);
-    }
-    return cuda_rc(cudaGetLastError());
+    return prof_time("lm_kernel", st, [&]() {
+        if (p <= 16 * 256) {
+            size_t smem = lm_smem_bytes(p, H, nm, 256);
+            int e = set_smem_attr(lm_kernel<256, D>, smem);
+            if (e) return e;
+            lm_kernel<256, D><<<P.N, 256, smem, st>>>(P);
+        } else {
+            size_t smem = lm_smem_bytes(p, H, nm, 512);
+            int e = set_smem_attr(lm_kernel<512, D>, smem);
+            if (e) return e;
+            lm_kernel<512, D><<<P.N, 512, smem, st>>>(P);
+        }
+        return cuda_rc(cudaGetLastError());
+    });
 }
 
 #define LASP_INSTANTIATE(D)                                                  \

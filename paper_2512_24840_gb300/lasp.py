@@ -77,7 +77,7 @@ EXPORTS = ["lasp_init_interp", "lasp_free_interp", "lasp_default_opts", "lasp_fi
            "lasp_slots_fetch", "lasp_interp_eval_static", "lasp_clean_mask",
            "lasp_init_interp_piecewise", "lasp_server_create", "lasp_server_destroy",
            "lasp_server_submit", "lasp_server_tick", "lasp_server_poll", "lasp_server_pending",
-           "lasp_test_wait_limit"]
+           "lasp_test_wait_limit", "lasp_profile", "lasp_profile_read"]
 
 
 def library_path() -> str:
@@ -133,6 +133,10 @@ def load(build: bool = False):
         lib.lasp_clean_mask.restype = I
         lib.lasp_test_wait_limit.argtypes = [I]
         lib.lasp_test_wait_limit.restype = I
+        lib.lasp_profile.argtypes = [I]
+        lib.lasp_profile.restype = I
+        lib.lasp_profile_read.argtypes = [P, I, P]
+        lib.lasp_profile_read.restype = I
         _lib = lib
         return lib
 
@@ -182,6 +186,23 @@ def default_opts(**kw) -> FitOpts:
 
 def last_launches() -> int:
     return int(load().lasp_last_launches())
+
+
+class KernelTime(ct.Structure):
+    _fields_ = [("name", ct.c_char * 48), ("launches", ct.c_int32), ("ms", ct.c_double)]
+
+
+def profile(on: bool) -> None:
+    """Per-kernel device timing on (calls become synchronous) or off."""
+    _check(load().lasp_profile(1 if on else 0), "lasp_profile")
+
+
+def profile_read() -> dict:
+    """{kernel name: (launches, total ms)} since the last read; clears it."""
+    buf = (KernelTime * 64)()
+    n = ct.c_int()
+    _check(load().lasp_profile_read(buf, 64, ct.byref(n)), "lasp_profile_read")
+    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].ms)) for i in range(n.value)}
 
 
 def test_wait_limit(polls: int) -> None:
