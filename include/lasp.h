@@ -124,10 +124,10 @@ void lasp_free_interp(lasp_interp h);
  * continuous in Teff; its Teff derivative jumps at the bounds.
  * coeff: host, (K[0] + ... + K[n_reg-1]) x n_model float32, the regimes'
  * tables stacked in order.  exps: host, the same rows x 3.  At most 96 rows
- * in all.  Handles made here serve every FP32 entry point (fits, errors, LM,
- * slots, forward/backward, lasp_interp_eval at LASP_PREC_FP32); the
- * tensor-core paths (precision != LASP_PREC_FP32) return LASP_EINVAL for a
- * handle with more than one regime.  Errors as lasp_init_interp, plus
+ * in all.  Handles made here serve every entry point that takes a handle:
+ * the tensor-core paths stack the regimes' rows into up to three K blocks of
+ * 32 terms (the rows of regimes inactive at a spectrum's Teff enter with zero
+ * weight, a masked grouped contraction).  Errors as lasp_init_interp, plus
  * LASP_EINVAL for n_reg outside 1..3, a regime without terms, or bounds not
  * strictly increasing. */
 typedef struct {
@@ -262,9 +262,9 @@ typedef struct lasp_slots_s* lasp_slots;          /* opaque, library-owned */
  * four per CTA; each slot also keeps its preprocessed y, W rows (8 bytes a
  * pixel, n_pix rounded up to 16), written when the slot is admitted.
  * A tensor-core precision: the grouped pipeline runs over the slots (served
- * mixed precision; single-regime tables, Legendre degree 6; about 50 n_pix
- * more bytes per slot); its steps go in chunks of 8, so a step call's budget
- * is rounded up to a multiple of 8.  Clean: each slot keeps its Clean mask in
+ * mixed precision; Legendre degree 6, FP32 or float-float normal equations;
+ * about 50 n_pix more bytes per slot); its steps go in chunks of 8, so a step
+ * call's budget is rounded up to a multiple of 8.  Clean: each slot keeps its Clean mask in
  * device memory between steps (in its W row), so the updates fall on the same
  * steps as in a one-shot fit at the same precision.  The joint loss:
  * LASP_EINVAL. */

@@ -281,8 +281,8 @@ int lasp_init_interp_piecewise(const lasp_piecewise_desc* d, const float* coeff,
         rc = cuda_err(cudaMemcpy2D(h->Cp, (size_t)M.ldc * sizeof(float), coeff,
                                    (size_t)M.n_model * sizeof(float), (size_t)M.n_model * sizeof(float),
                                    (size_t)K, cudaMemcpyHostToDevice));
-    // tensor-core tile images: single-regime tables of at most one K block
-    if (!rc && M.n_reg == 1) rc = tc_build_images(h->tc, h->C, K, M.n_model);
+    // tensor-core tile images: the rows in K blocks of 32 terms (three at most)
+    if (!rc) rc = tc_build_images(h->tc, h->C, K, M.n_model);
     // the copies above run on the legacy default stream; finish them before a fit on another stream
     if (!rc) rc = cuda_err(cudaStreamSynchronize(cudaStreamLegacy));
     if (rc) {
@@ -338,7 +338,6 @@ int lasp_fit_batch(lasp_interp h, const lasp_batch* b, const lasp_fit_opts* o, l
     if (!r || (b->N > 0 && (!r->theta || !r->loss || !r->steps || !r->status))) return LASP_EINVAL;
     if (b->N == 0) return LASP_OK;
     if (o->precision != LASP_PREC_FP32) {
-        if (h->M.n_reg > 1) return LASP_EINVAL;                       // single-regime tensor-core images
         return lasp_tc_fit_batch(h->M, h->tc, b, o, r, stream, &g_last_launches);
     }
     if (o->optimizer == LASP_OPT_LM) {
@@ -471,7 +470,6 @@ int lasp_interp_eval(lasp_interp h, int N, const float* theta, float* Fp, int pr
     if (N == 0) return LASP_OK;
     if (!theta || !Fp) return LASP_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
-    if (precision != LASP_PREC_FP32 && h->M.n_reg > 1) return LASP_EINVAL;
     if (precision != LASP_PREC_FP32)
         return lasp_tc_interp_eval(h->M, h->tc, N, theta, Fp, precision, st, &g_last_launches);
     dim3 grid(N, (h->M.n_model + 255) / 256);
@@ -590,7 +588,7 @@ int lasp_slots_create(lasp_interp h, int n_slots, const lasp_fit_opts* o, lasp_s
     int rc = check_opts(o, h->M.n_pix);
     if (rc) return rc;
     if (o->loss_mode != LASP_LOSS_SEPARABLE) return LASP_EINVAL;
-    if (o->precision != LASP_PREC_FP32 && (h->M.n_reg > 1 || o->legendre_deg != 6))
+    if (o->precision != LASP_PREC_FP32 && o->legendre_deg != 6)
         return LASP_EINVAL;
     lasp_slots_s* s = new (std::nothrow) lasp_slots_s();
     if (!s) return LASP_ENOMEM;

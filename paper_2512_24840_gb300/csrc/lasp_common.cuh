@@ -125,24 +125,13 @@ __device__ __forceinline__ float monomial(const float* lo, const float* sc, cons
     return pa * pb * pc;
 }
 
-// Basis of Eq. 1: phi_k and d phi_k / d(Teff, logg, FeH) of row k (dphi row
-// k at DPS k: Teff, logg, FeH, 0), with the regime weight folded in.  Row k
-// of regime r is w_r(Teff) times its monomial in the regime's own basis box;
-// w_r is 1 inside the regime, falls or rises linearly in Teff across a blend
-// interval, and is 0 elsewhere, so d phi / d Teff carries the weight's slope.
-__device__ __forceinline__ void basis_term(const ModelDev& M, int k, const float th[3],
-                                           float* phi, float* dphi) {
-    float d[3];
-    if (M.n_reg == 1) {
-        phi[k] = monomial(M.rblo[0], M.rbscale[0], M.exps + 3 * k, th, dphi ? d : nullptr);
-        if (dphi) {
-            dphi[DPS * k + 0] = d[0];
-            dphi[DPS * k + 1] = d[1];
-            dphi[DPS * k + 2] = d[2];
-            dphi[DPS * k + 3] = 0.0f;
-        }
-        return;
-    }
+// Row k of the basis of Eq. 1 with the regime weight folded in, and its
+// derivatives d[0..2] with respect to (Teff, logg, FeH).  Row k of regime r is
+// w_r(Teff) times its monomial in the regime's own basis box; w_r is 1 inside
+// the regime, falls or rises linearly in Teff across a blend interval, and is
+// 0 elsewhere, so d phi / d Teff carries the weight's slope.
+__device__ __forceinline__ float basis_term_one(const ModelDev& M, int k, const float th[3], float (&d)[3]) {
+    if (M.n_reg == 1) return monomial(M.rblo[0], M.rbscale[0], M.exps + 3 * k, th, d);
     int r = 0;
     while (r + 1 < M.n_reg && k >= M.reg_row[r + 1]) ++r;
     float w = 1.0f, dw = 0.0f;
@@ -165,24 +154,37 @@ __device__ __forceinline__ void basis_term(const ModelDev& M, int k, const float
         w = 0.0f;
     }
     if (w == 0.0f && dw == 0.0f) {
-        phi[k] = 0.0f;
-        if (dphi) dphi[DPS * k] = dphi[DPS * k + 1] = dphi[DPS * k + 2] = dphi[DPS * k + 3] = 0.0f;
-        return;
+        d[0] = d[1] = d[2] = 0.0f;
+        return 0.0f;
     }
-    const float mono = monomial(M.rblo[r], M.rbscale[r], M.exps + 3 * k, th, dphi ? d : nullptr);
-    phi[k] = w * mono;
-    if (dphi) {
-        dphi[DPS * k + 0] = fmaf(w, d[0], dw * mono);
-        dphi[DPS * k + 1] = w * d[1];
-        dphi[DPS * k + 2] = w * d[2];
-        dphi[DPS * k + 3] = 0.0f;
-    }
+    float dm[3];
+    const float mono = monomial(M.rblo[r], M.rbscale[r], M.exps + 3 * k, th, dm);
+    d[0] = fmaf(w, dm[0], dw * mono);
+    d[1] = w * dm[1];
+    d[2] = w * dm[2];
+    return w * mono;
 }
 
-// Row k's basis term and its three derivatives in registers (single-regime
-// tables; used where rows are spread over lanes and no shared array is kept).
-__device__ __forceinline__ float basis_term_1r(const ModelDev& M, int k, const float th[3], float (&d)[3]) {
-    return monomial(M.rblo[0], M.rbscale[0], M.exps + 3 * k, th, d);
+// Basis of Eq. 1: phi_k and d phi_k / d(Teff, logg, FeH) of row k (dphi row
+// k at DPS k: Teff, logg, FeH, 0), with the regime weight folded in.
+__device__ __forceinline__ void basis_term(const ModelDev& M, int k, const float th[3],
+                                           float* phi, float* dphi) {
+    if (!dphi) {
+        // value only: the monomial without its derivatives
+        if (M.n_reg == 1) {
+            phi[k] = monomial(M.rblo[0], M.rbscale[0], M.exps + 3 * k, th, nullptr);
+            return;
+        }
+        float d[3];
+        phi[k] = basis_term_one(M, k, th, d);
+        return;
+    }
+    float d[3];
+    phi[k] = basis_term_one(M, k, th, d);
+    dphi[DPS * k + 0] = d[0];
+    dphi[DPS * k + 1] = d[1];
+    dphi[DPS * k + 2] = d[2];
+    dphi[DPS * k + 3] = 0.0f;
 }
 
 // Every row's basis term, spread over the lanes of one warp.

@@ -1,0 +1,6 @@
+// The grouped tensor-core fit at Legendre degree 2 (its own translation unit).
+#include "lasp_grouped.cuh"
+
+namespace lasp {
+template int grp_run_deg<2>(Grp&, const TcImages&, const lasp_fit_opts*, cudaStream_t, int*);
+}  // namespace lasp

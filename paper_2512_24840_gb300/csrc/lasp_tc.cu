@@ -20,43 +20,46 @@ namespace {
 
 constexpr uint32_t kWaitLimit = 1u << 22;
 
-__global__ void build_images_kernel(const float* __restrict__ C, int K, int n_model, int n_tiles,
+// Forward images: tile t, K block b, row r (model pixel), 16-byte piece c.
+__global__ void build_images_kernel(const float* __restrict__ C, int K, int n_model, int n_tiles, int n_kb,
                                     uint8_t* hi, uint8_t* lo, uint8_t* bf) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    const int total = n_tiles * TC_TILE * 8;
+    const int total = n_tiles * n_kb * TC_TILE * 8;
     if (idx >= total) return;
-    const int c = idx & 7, r = (idx >> 3) & (TC_TILE - 1), t = idx >> 10;
+    const int c = idx & 7, r = (idx >> 3) & (TC_TILE - 1), tb = idx >> 10;
+    const int t = tb / n_kb, b = tb - t * n_kb;
     const int m = t * TC_TILE + r;
-    const uint32_t off = (uint32_t)t * TC_TILE_BYTES + tc::sw128_off(r, c);
+    const uint32_t off = (uint32_t)tb * TC_TILE_BYTES + tc::sw128_off(r, c);
     float v[4], h[4], l[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        const int k = 4 * c + q;
+        const int k = 32 * b + 4 * c + q;
         v[q] = (m < n_model && k < K) ? C[(size_t)k * n_model + m] : 0.0f;
         h[q] = tc::to_tf32(v[q]);
         l[q] = tc::to_tf32(v[q] - h[q]);
     }
     *reinterpret_cast<float4*>(hi + off) = make_float4(h[0], h[1], h[2], h[3]);
     *reinterpret_cast<float4*>(lo + off) = make_float4(l[0], l[1], l[2], l[3]);
-    // BF16: chunk c < 4 holds basis terms 8c .. 8c+7, chunks 4..7 are zero
-    __nv_bfloat16 b[8];
+    // BF16: piece c < 4 holds basis terms 32 b + 8c .. 32 b + 8c + 7, pieces 4..7 are zero
+    __nv_bfloat16 bv[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-        const int k = 8 * c + q;
+        const int k = 32 * b + 8 * c + q;
         const float x = (c < 4 && m < n_model && k < K) ? C[(size_t)k * n_model + m] : 0.0f;
-        b[q] = __float2bfloat16_rn(x);
+        bv[q] = __float2bfloat16_rn(x);
     }
-    *reinterpret_cast<uint4*>(bf + off) = *reinterpret_cast<uint4*>(b);
+    *reinterpret_cast<uint4*>(bf + off) = *reinterpret_cast<uint4*>(bv);
 }
 
-// Backward table images: chunk c, row k (basis term), 16-byte piece q.
+// Backward table images: chunk c, row k (basis term, 32 n_kb rows), 16-byte piece q.
 __global__ void build_back_images_kernel(const float* __restrict__ C, int K, int n_model, int n_ch32,
-                                         int n_ch64, uint8_t* hi, uint8_t* lo, uint8_t* bf) {
+                                         int n_ch64, int n_kb, uint8_t* hi, uint8_t* lo, uint8_t* bf) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    const int total = n_ch32 * 32 * 8;
+    const int rows = 32 * n_kb;
+    const int total = n_ch32 * rows * 8;
     if (idx >= total) return;
-    const int q = idx & 7, k = (idx >> 3) & 31, c = idx >> 8;
-    const uint32_t off = (uint32_t)c * TC_BK_CHUNK_BYTES + tc::sw128_off(k, q);
+    const int q = idx & 7, k = (idx >> 3) % rows, c = (idx >> 3) / rows;
+    const uint32_t off = (uint32_t)c * n_kb * TC_BK_CHUNK_BYTES + tc::sw128_off(k, q);
     float h[4], l[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -78,23 +81,25 @@ __global__ void build_back_images_kernel(const float* __restrict__ C, int K, int
     }
 }
 
-// PREC: 1 TF32, 2 BF16, 3 split TF32 (hi*hi + hi*lo + lo*hi).  Every wait is
-// bounded; when one gives up the CTA sets *err, writes NaN into every output of
-// the tiles it has not finished, lets its own copies and MMAs in flight
-// complete (bounded again), frees its TMEM and returns.  wait0 bounds the
-// first table-copy wait of the CTA (no MMA issued yet).
+// PREC: 1 TF32, 2 BF16, 3 split TF32 (hi*hi + hi*lo + lo*hi).  n_kb K
+// blocks of 32 basis terms accumulate into one 128 x 128 accumulator.  Every
+// wait is bounded; when one gives up the CTA sets *err, writes NaN into every
+// output of the tiles it has not finished, lets its own copies and MMAs in
+// flight complete (bounded again), frees its TMEM and returns.  wait0 bounds
+// the first table-copy wait of the CTA (no MMA issued yet).
 template <int PREC>
 __global__ void __launch_bounds__(128) interp_tc_kernel(const ModelDev M, const float* __restrict__ theta,
                                                         float* __restrict__ Fp, int N,
                                                         const uint8_t* __restrict__ img_a,
                                                         const uint8_t* __restrict__ img_a_lo,
-                                                        int n_tiles, int* err, uint32_t wait0) {
+                                                        int n_tiles, int n_kb, int* err, uint32_t wait0) {
     extern __shared__ uint8_t smraw[];
     uint8_t* base = reinterpret_cast<uint8_t*>(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+    const uint32_t blk_bytes = (uint32_t)n_kb * TC_TILE_BYTES;
     uint8_t* Ahi = base;
-    uint8_t* Alo = base + TC_TILE_BYTES;
-    uint8_t* Bhi = base + 2 * TC_TILE_BYTES;
-    uint8_t* Blo = base + 3 * TC_TILE_BYTES;
+    uint8_t* Alo = base + blk_bytes;
+    uint8_t* Bhi = base + 2 * blk_bytes;
+    uint8_t* Blo = base + 3 * blk_bytes;
     __shared__ __align__(8) uint64_t bar_tma, bar_mma;
     __shared__ uint32_t tmem_base;
     __shared__ int s_ok;
@@ -107,35 +112,38 @@ __global__ void __launch_bounds__(128) interp_tc_kernel(const ModelDev M, const 
     }
     // B operand row tid: phi of spectrum s0 + tid, zero beyond N or K
     {
-        float phi[KMAX];
-#pragma unroll
-        for (int k = 0; k < KMAX; ++k) phi[k] = 0.0f;
+        float phi[KROWS];
+        for (int k = 0; k < 32 * n_kb; ++k) phi[k] = 0.0f;
         if (s0 + tid < N) {
             float th[5];
 #pragma unroll
             for (int q = 0; q < 5; ++q) th[q] = theta[5 * (size_t)(s0 + tid) + q];
             for (int k = 0; k < M.K; ++k) basis_term(M, k, th, phi, nullptr);
         }
-        if (PREC == 2) {
+        for (int b = 0; b < n_kb; ++b) {
+            uint8_t* bh = Bhi + b * TC_TILE_BYTES;
+            uint8_t* bl = Blo + b * TC_TILE_BYTES;
+            if (PREC == 2) {
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                __nv_bfloat16 b[8];
+                for (int c = 0; c < 8; ++c) {
+                    __nv_bfloat16 bv[8];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) b[q] = __float2bfloat16_rn(c < 4 ? phi[8 * c + q] : 0.0f);
-                *reinterpret_cast<uint4*>(Bhi + tc::sw128_off(tid, c)) = *reinterpret_cast<uint4*>(b);
-            }
-        } else {
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                float h[4], l[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    h[q] = tc::to_tf32(phi[4 * c + q]);
-                    l[q] = tc::to_tf32(phi[4 * c + q] - h[q]);
+                    for (int q = 0; q < 8; ++q) bv[q] = __float2bfloat16_rn(c < 4 ? phi[32 * b + 8 * c + q] : 0.0f);
+                    *reinterpret_cast<uint4*>(bh + tc::sw128_off(tid, c)) = *reinterpret_cast<uint4*>(bv);
                 }
-                *reinterpret_cast<float4*>(Bhi + tc::sw128_off(tid, c)) = make_float4(h[0], h[1], h[2], h[3]);
-                if (PREC == 3)
-                    *reinterpret_cast<float4*>(Blo + tc::sw128_off(tid, c)) = make_float4(l[0], l[1], l[2], l[3]);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    float h[4], l[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        h[q] = tc::to_tf32(phi[32 * b + 4 * c + q]);
+                        l[q] = tc::to_tf32(phi[32 * b + 4 * c + q] - h[q]);
+                    }
+                    *reinterpret_cast<float4*>(bh + tc::sw128_off(tid, c)) = make_float4(h[0], h[1], h[2], h[3]);
+                    if (PREC == 3)
+                        *reinterpret_cast<float4*>(bl + tc::sw128_off(tid, c)) = make_float4(l[0], l[1], l[2], l[3]);
+                }
             }
         }
     }
@@ -157,10 +165,10 @@ __global__ void __launch_bounds__(128) interp_tc_kernel(const ModelDev M, const 
 
     for (; t < n_tiles; t += gridDim.y) {
         if (tid == 0) {
-            const uint32_t bytes = (PREC == 3 ? 2u : 1u) * (uint32_t)TC_TILE_BYTES;
+            const uint32_t bytes = (PREC == 3 ? 2u : 1u) * blk_bytes;
             tc::mbar_arrive_expect_tx(&bar_tma, bytes);
-            tc::bulk_g2s(Ahi, img_a + (size_t)t * TC_TILE_BYTES, TC_TILE_BYTES, &bar_tma);
-            if (PREC == 3) tc::bulk_g2s(Alo, img_a_lo + (size_t)t * TC_TILE_BYTES, TC_TILE_BYTES, &bar_tma);
+            tc::bulk_g2s(Ahi, img_a + (size_t)t * blk_bytes, blk_bytes, &bar_tma);
+            if (PREC == 3) tc::bulk_g2s(Alo, img_a_lo + (size_t)t * blk_bytes, blk_bytes, &bar_tma);
             copy_pending = true;
             if (!tc::mbar_wait_bounded(&bar_tma, phase, t == (int)blockIdx.y ? wait0 : kWaitLimit)) {
                 atomicExch(err, 1);
@@ -168,24 +176,27 @@ __global__ void __launch_bounds__(128) interp_tc_kernel(const ModelDev M, const 
             } else {
                 copy_pending = false;
                 tc::tc_fence_after();
-                const uint64_t ah = tc::desc_kmajor_sw128(tc::smem_u32(Ahi));
-                const uint64_t bh = tc::desc_kmajor_sw128(tc::smem_u32(Bhi));
-                // K = 32 basis terms = 128 bytes per row: 4 TF32 MMAs (K=8) or 2 BF16 MMAs (K=16)
-                constexpr int NK = PREC == 2 ? 2 : 4;
+                for (int b = 0; b < n_kb; ++b) {
+                    const uint64_t ah = tc::desc_kmajor_sw128(tc::smem_u32(Ahi + b * TC_TILE_BYTES));
+                    const uint64_t bh = tc::desc_kmajor_sw128(tc::smem_u32(Bhi + b * TC_TILE_BYTES));
+                    // K = 32 basis terms = 128 bytes per row: 4 TF32 MMAs (K=8) or 2 BF16 MMAs (K=16)
+                    constexpr int NK = PREC == 2 ? 2 : 4;
 #pragma unroll
-                for (int ks = 0; ks < NK; ++ks) {
-                    const uint64_t adv = (uint64_t)(ks * 32) >> 4;
-                    if (PREC == 2) tc::mma_bf16(tmem, ah + adv, bh + adv, idesc, ks > 0);
-                    else tc::mma_tf32(tmem, ah + adv, bh + adv, idesc, ks > 0);
-                }
-                if (PREC == 3) {
-                    const uint64_t al = tc::desc_kmajor_sw128(tc::smem_u32(Alo));
-                    const uint64_t bl = tc::desc_kmajor_sw128(tc::smem_u32(Blo));
-#pragma unroll
-                    for (int ks = 0; ks < 4; ++ks) {
+                    for (int ks = 0; ks < NK; ++ks) {
                         const uint64_t adv = (uint64_t)(ks * 32) >> 4;
-                        tc::mma_tf32(tmem, ah + adv, bl + adv, idesc, 1);
-                        tc::mma_tf32(tmem, al + adv, bh + adv, idesc, 1);
+                        const uint32_t acc = (b > 0 || ks > 0) ? 1u : 0u;
+                        if (PREC == 2) tc::mma_bf16(tmem, ah + adv, bh + adv, idesc, acc);
+                        else tc::mma_tf32(tmem, ah + adv, bh + adv, idesc, acc);
+                    }
+                    if (PREC == 3) {
+                        const uint64_t al = tc::desc_kmajor_sw128(tc::smem_u32(Alo + b * TC_TILE_BYTES));
+                        const uint64_t bl = tc::desc_kmajor_sw128(tc::smem_u32(Blo + b * TC_TILE_BYTES));
+#pragma unroll
+                        for (int ks = 0; ks < 4; ++ks) {
+                            const uint64_t adv = (uint64_t)(ks * 32) >> 4;
+                            tc::mma_tf32(tmem, ah + adv, bl + adv, idesc, 1);
+                            tc::mma_tf32(tmem, al + adv, bh + adv, idesc, 1);
+                        }
                     }
                 }
                 tc::mma_commit(&bar_mma);
@@ -240,25 +251,26 @@ __global__ void __launch_bounds__(128) interp_tc_kernel(const ModelDev M, const 
 int tc_build_images(TcImages& t, const float* C, int K, int n_model) {
     t = TcImages{};
     t.n_tiles = (n_model + TC_TILE - 1) / TC_TILE;
-    const size_t bytes = (size_t)t.n_tiles * TC_TILE_BYTES;
+    t.n_kb = (K + 31) / 32;
+    const size_t bytes = (size_t)t.n_tiles * t.n_kb * TC_TILE_BYTES;
     int rc = cuda_rc(cudaMalloc(&t.tf32_hi, bytes));
     if (!rc) rc = cuda_rc(cudaMalloc(&t.tf32_lo, bytes));
     if (!rc) rc = cuda_rc(cudaMalloc(&t.bf16, bytes));
     if (rc) return rc;
-    const int total = t.n_tiles * TC_TILE * 8;
-    build_images_kernel<<<(total + 255) / 256, 256>>>(C, K, n_model, t.n_tiles, (uint8_t*)t.tf32_hi,
+    const int total = t.n_tiles * t.n_kb * TC_TILE * 8;
+    build_images_kernel<<<(total + 255) / 256, 256>>>(C, K, n_model, t.n_tiles, t.n_kb, (uint8_t*)t.tf32_hi,
                                                        (uint8_t*)t.tf32_lo, (uint8_t*)t.bf16);
     rc = cuda_rc(cudaGetLastError());
     if (rc) return rc;
     t.n_chunks_tf32 = (n_model + 31) / 32;
     t.n_chunks_bf16 = (n_model + 63) / 64;
-    const size_t bk = (size_t)t.n_chunks_tf32 * TC_BK_CHUNK_BYTES;
+    const size_t bk = (size_t)t.n_chunks_tf32 * t.n_kb * TC_BK_CHUNK_BYTES;
     rc = cuda_rc(cudaMalloc(&t.bk_hi, bk));
     if (!rc) rc = cuda_rc(cudaMalloc(&t.bk_lo, bk));
     if (!rc) rc = cuda_rc(cudaMalloc(&t.bk_bf, bk));
     if (rc) return rc;
-    const int tb = t.n_chunks_tf32 * 32 * 8;
-    build_back_images_kernel<<<(tb + 255) / 256, 256>>>(C, K, n_model, t.n_chunks_tf32, t.n_chunks_bf16,
+    const int tb = t.n_chunks_tf32 * 32 * t.n_kb * 8;
+    build_back_images_kernel<<<(tb + 255) / 256, 256>>>(C, K, n_model, t.n_chunks_tf32, t.n_chunks_bf16, t.n_kb,
                                                          (uint8_t*)t.bk_hi, (uint8_t*)t.bk_lo,
                                                          (uint8_t*)t.bk_bf);
     rc = cuda_rc(cudaGetLastError());
@@ -281,7 +293,7 @@ void tc_free_images(TcImages& t) {
 int lasp_tc_interp_eval(const ModelDev& M, const TcImages& t, int N, const float* theta, float* Fp,
                         int precision, cudaStream_t st, int* launches) {
     if (!t.tf32_hi) return LASP_EINVAL;
-    const size_t smem = 4 * TC_TILE_BYTES + 1024;
+    const size_t smem = 4 * (size_t)t.n_kb * TC_TILE_BYTES + 1024;
     dim3 grid((N + 127) / 128, t.n_tiles < 65535 ? t.n_tiles : 65535);
     int* err = nullptr;
     int rc = cuda_rc(cudaMallocAsync((void**)&err, sizeof(int), st));
@@ -291,8 +303,8 @@ int lasp_tc_interp_eval(const ModelDev& M, const TcImages& t, int N, const float
     auto go = [&](auto kern, const void* a, const void* alo) {
         int e = cuda_rc(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         if (e) return e;
-        kern<<<grid, 128, smem, st>>>(M, theta, Fp, N, (const uint8_t*)a, (const uint8_t*)alo, t.n_tiles, err,
-                                      wait0);
+        kern<<<grid, 128, smem, st>>>(M, theta, Fp, N, (const uint8_t*)a, (const uint8_t*)alo, t.n_tiles, t.n_kb,
+                                      err, wait0);
         return cuda_rc(cudaGetLastError());
     };
     if (!rc) {
@@ -450,7 +462,7 @@ extern "C" int lasp_interp_eval_static(const lasp_interp_desc* desc, const float
     }
     const int n_tiles = (M.n_model + TC_TILE - 1) / TC_TILE;
     const int total = n_tiles * TC_TILE * 8;
-    build_images_kernel<<<(total + 255) / 256, 256, 0, st>>>(coeff, M.K, M.n_model, n_tiles, hi, lo, bf);
+    build_images_kernel<<<(total + 255) / 256, 256, 0, st>>>(coeff, M.K, M.n_model, n_tiles, 1, hi, lo, bf);
     rc = cuda_rc(cudaGetLastError());
     if (rc) return rc;
     const size_t smem = 4 * TC_TILE_BYTES + 1024;
@@ -459,7 +471,7 @@ extern "C" int lasp_interp_eval_static(const lasp_interp_desc* desc, const float
     auto go = [&](auto kern, const uint8_t* a, const uint8_t* alo) {
         int e = cuda_rc(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         if (e) return e;
-        kern<<<grid, 128, smem, st>>>(M, theta, Fp, N, a, alo, n_tiles, err, wait0);
+        kern<<<grid, 128, smem, st>>>(M, theta, Fp, N, a, alo, n_tiles, 1, err, wait0);
         return cuda_rc(cudaGetLastError());
     };
     if (precision == LASP_PREC_TF32) rc = go(interp_tc_kernel<1>, hi, nullptr);

@@ -1,10 +1,12 @@
 // Tensor-core (tcgen05) forms of the interpolator contraction (Eq. 1), sm_103a.
 //
 // The table is kept as per-tile images ready for the MMA: tile t holds model
-// pixels 128 t .. 128 t + 127 as 128 rows of 32 basis terms, K-major with the
-// 128-byte swizzle, so one 1D bulk copy brings a tile into shared memory in
-// MMA layout.  TF32 is stored as a hi/lo split (hi = tf32(C), lo =
-// tf32(C - hi)); BF16 occupies the first 64 bytes of each 128-byte row.
+// pixels 128 t .. 128 t + 127 as 128 rows of 32 basis terms per K block
+// (n_kb blocks of 32 terms: one for a single regime, up to three for the
+// stacked rows of a piecewise interpolator), K-major with the 128-byte
+// swizzle, so one 1D bulk copy brings a tile into shared memory in MMA layout.
+// TF32 is stored as a hi/lo split (hi = tf32(C), lo = tf32(C - hi)); BF16
+// occupies the first 64 bytes of each 128-byte row.
 #pragma once
 
 #include "lasp.h"
@@ -16,13 +18,14 @@ constexpr int TC_TILE = 128;            // model pixels per tile (MMA M)
 constexpr int TC_TILE_BYTES = 128 * 128; // 16 KB per image tile
 
 struct TcImages {
-    void* tf32_hi = nullptr;
+    void* tf32_hi = nullptr;          // tile t, block b at (t n_kb + b) 16 KB
     void* tf32_lo = nullptr;
     void* bf16 = nullptr;
     int n_tiles = 0;
+    int n_kb = 1;                     // K blocks of 32 basis terms
     // Backward images (dphi = dF' C^T): per chunk of model pixels (32 for TF32,
-    // 64 for BF16) a 32-row (basis term) x 128-byte tile, K-major in pixels,
-    // 128-byte swizzle (4 KB per chunk).
+    // 64 for BF16) a (32 n_kb)-row (basis term) x 128-byte tile, K-major in
+    // pixels, 128-byte swizzle (4 KB per K block, the blocks contiguous).
     void* bk_hi = nullptr;
     void* bk_lo = nullptr;
     void* bk_bf = nullptr;

@@ -9,7 +9,7 @@ import pytest
 
 import lasp_synth as S
 from oracle import oracle as O
-from tests.helpers import TOL, observed, table
+from tests.helpers import TOL, observed, oracle_model, table
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -95,6 +95,21 @@ def test_fp64_normal_equations_only_with_split_tf32(lasp):
     M, d = observed(g, 4, 73, snr=(30, 100), mask_frac=0.0)
     with pytest.raises(lasp.LaspError):
         _fit(lasp, g, d, max_steps=10, precision="tf32", fp64_normal_eq=2)
+
+
+@pytest.mark.parametrize("deg", [2, 4, 8])
+def test_grouped_fit_other_legendre_degrees(lasp, deg):
+    """The continuum of Eq. 6 at degrees 2, 4 and 8 on the grouped tensor-core
+    fit against the oracle at the same degree."""
+    g = S.SMALL
+    M, d = observed(g, 64, 74 + deg, snr=(20, 100), mask_frac=0.05)
+    d["theta0"] = np.asarray(d["theta0"], np.float32).astype(np.float64)
+    ref = O.fit(oracle_model(g, deg=deg), d["flux"], d["ivar"], d["good"], d["theta0"], max_steps=400)
+    out = _fit(lasp, g, d, max_steps=400, legendre_deg=deg, precision="tf32x3", fp64_normal_eq=1)
+    ok = np.all(np.abs(out["theta"] - ref["theta"])[:, :4] <= TOL, axis=1)
+    print(f"grouped tf32x3 at Legendre degree {deg}: {ok.mean():.3f} within tolerance")
+    assert ok.mean() >= 0.9
+    assert out["cont"].shape[1] == deg + 1
 
 
 def test_mixed_desi_grid_and_max_steps(lasp):

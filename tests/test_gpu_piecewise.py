@@ -143,16 +143,38 @@ def test_errors_parity(lasp):
     assert np.median(rel) < 1e-3 and np.mean(rel < 1e-2) >= 0.9, rel.max(axis=0)
 
 
-def test_tensor_core_paths_reject_piecewise(lasp):
-    ip = pw_interp(lasp, S.SMALL)
-    th = T(spread_thetas(4, 67))
-    with pytest.raises(lasp.LaspError) as e:
-        ip.interp_eval(th, "tf32")
-    assert e.value.code == lasp.EINVAL
-    _, d = _inputs(S.SMALL, 4, 68)
-    with pytest.raises(lasp.LaspError) as e:
-        _gpu(lasp, S.SMALL, d, precision="tf32x3")
-    assert e.value.code == lasp.EINVAL
+@pytest.mark.parametrize("prec,tol", [("tf32x3", 1e-5), ("tf32", 4e-3), ("bf16", 3e-2)])
+def test_tensor_core_interp_all_ranges(lasp, prec, tol):
+    """Eq. 1 with the Teff regimes on tcgen05: the stacked rows of the three
+    regimes in three K blocks of 32 terms, the rows of inactive regimes
+    weighted zero (a masked grouped contraction)."""
+    grid = S.LAMOST
+    M = piecewise_model(grid)
+    th = spread_thetas(150, 67)
+    Fp = H(pw_interp(lasp, grid).interp_eval(T(th), prec))
+    b = np.tile(np.r_[1.0, np.zeros(DEG)], (len(th), 1))
+    ref = np.stack([O.model_flux(M, th[i], b[i])["Fp"] for i in range(len(th))])
+    err = rel_err(Fp, ref)
+    print(f"piecewise {prec} contraction: max rel err {err:.3e}")
+    assert err < tol
+
+
+def test_tensor_core_adam_fit_parity(lasp):
+    """The grouped tensor-core fit (split TF32, float-float normal equations)
+    on the piecewise emulator against the oracle, all five Teff ranges."""
+    M, d = _inputs(S.LAMOST, 96, 63, snr=(5, 100), mask_frac=0.05)
+    out = _gpu(lasp, S.LAMOST, d, max_steps=500, precision="tf32x3", fp64_normal_eq=1)
+    ref = O.fit(M, d["flux"], d["ivar"], d["good"], d["theta0"], max_steps=500)
+    err = np.abs(out["theta"] - ref["theta"])[:, :4]
+    ok = np.all(err <= TOL, axis=1)
+    print(f"piecewise tf32x3 Adam parity {ok.mean():.3f}, same steps {(out['steps'] == ref['steps']).mean():.3f}")
+    assert ok.mean() >= 0.9
+    assert np.all((out["status"].astype(np.int64) & 7) != 0)
+    # and against the FP32 fit of the same spectra
+    fp = _gpu(lasp, S.LAMOST, d, max_steps=500)
+    same = np.all(np.abs(out["theta"] - fp["theta"])[:, :4] <= TOL, axis=1)
+    print(f"piecewise tf32x3 vs FP32 fit: {same.mean():.3f} within tolerance")
+    assert same.mean() >= 0.9
 
 
 def test_one_regime_piecewise_handle_equals_plain_handle(lasp):
