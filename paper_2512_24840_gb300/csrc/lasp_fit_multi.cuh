@@ -59,10 +59,11 @@ static __global__ void slots_running_list(int n, const uint32_t* __restrict__ st
 // position either layout reads, pads included.
 struct MultiSmem {
     int Fp, Db, g, gmu, gsg, phi, dphi, ring, lane, part, red, out, total, dofs;
-    __host__ __device__ MultiSmem(int p, int H, int n_model, int NT, int D, int K, int S) {
+    // full: the FULL variant, whose FP64 normal equations need 2 NV floats a warp in red
+    __host__ __device__ MultiSmem(int p, int H, int n_model, int NT, int D, int K, int S, bool full) {
         const int NB = D + 1, NV = NB * (NB + 1) / 2 + NB;
         const int nv_max = round32(NV > NADJ * S ? NV : NADJ * S);
-        const int red_w = nv_max > 2 * round32(NV) ? nv_max : 2 * round32(NV);   // floats a warp
+        const int red_w = full && 2 * round32(NV) > nv_max ? 2 * round32(NV) : nv_max;   // floats a warp
         dofs = 2 * H + 8;
         int nb = skew_size(n_model + 32);
         if (skew_size(p + 4 * H + 40) > nb) nb = skew_size(p + 4 * H + 40);
@@ -84,8 +85,8 @@ struct MultiSmem {
     }
 };
 
-__host__ inline size_t fit_multi_smem_bytes(int p, int H, int n_model, int NT, int D, int K, int S) {
-    return 4 * (size_t)MultiSmem(p, H, n_model, NT, D, K, S).total;
+__host__ inline size_t fit_multi_smem_bytes(int p, int H, int n_model, int NT, int D, int K, int S, bool full) {
+    return 4 * (size_t)MultiSmem(p, H, n_model, NT, D, K, S, full).total;
 }
 
 // Preprocessing of every spectrum before the fit (section 3.3 step 2), one CTA
@@ -197,7 +198,7 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
     const ModelDev& M = P.M;
     const int p = M.n_pix, H = M.pad, nm = M.n_model;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const MultiSmem L(p, H, nm, NT, D, M.K, S);
+    const MultiSmem L(p, H, nm, NT, D, M.K, S, FULL);
     float* red = sm + L.red;
     float* out = sm + L.out;
     __shared__ float s_x[S][5], s_b[S][NB], s_w[S];

@@ -29,7 +29,7 @@ constexpr int FIT_LANES = 4;
 // (its shared memory fits), with y, W rows of 2 ldw floats per slot.
 inline bool fit_multi_slots_ok(int p, int H, int nm, int K, int D) {
     const int NT = p <= 16 * 256 ? 256 : 512;
-    return fit_multi_smem_bytes(p, H, nm, NT, D, K, FIT_LANES) <= 227 * 1024 &&
+    return fit_multi_smem_bytes(p, H, nm, NT, D, K, FIT_LANES, true) <= 227 * 1024 &&
            4 * (size_t)fit_prep_smem_floats(p) <= 227 * 1024;
 }
 
@@ -71,11 +71,11 @@ int launch_fit_multi(const FitParams& P, cudaStream_t st) {
     constexpr int S = FIT_LANES;
     const int p = P.M.n_pix, H = P.M.pad, nm = P.M.n_model;
     const int NT = p <= 16 * 256 ? 256 : 512;
-    const size_t smem = fit_multi_smem_bytes(p, H, nm, NT, D, P.M.K, S);
+    const bool full = P.O.clean || P.O.fp64_ne == LASP_NE_FP64;
+    const size_t smem = fit_multi_smem_bytes(p, H, nm, NT, D, P.M.K, S, full);
     const size_t smem_prep = 4 * (size_t)fit_prep_smem_floats(p);
     // resumable slots, and Clean with too few lanes for its scratch, stay on fit_kernel
     if (P.S.x || (P.O.clean && S < 3) || smem > 227 * 1024 || smem_prep > 227 * 1024) return launch_fit<D>(P, st);
-    const bool full = P.O.clean || P.O.fp64_ne == LASP_NE_FP64;
     void (*kern)(const FitParams, const MultiWs) =
         full ? (NT == 256 ? fit_multi_kernel<256, D, S, true> : fit_multi_kernel<512, D, S, true>)
              : (NT == 256 ? fit_multi_kernel<256, D, S, false> : fit_multi_kernel<512, D, S, false>);
@@ -125,7 +125,7 @@ int launch_fit_multi_slots(const FitParams& P, const MultiWs& W, int n_running, 
     constexpr int S = FIT_LANES;
     const int p = P.M.n_pix, H = P.M.pad, nm = P.M.n_model;
     const int NT = p <= 16 * 256 ? 256 : 512;
-    const size_t smem = fit_multi_smem_bytes(p, H, nm, NT, D, P.M.K, S);
+    const size_t smem = fit_multi_smem_bytes(p, H, nm, NT, D, P.M.K, S, true);
     void (*kern)(const FitParams, const MultiWs) =
         NT == 256 ? fit_multi_kernel<256, D, S, true> : fit_multi_kernel<512, D, S, true>;
     int e = set_smem_attr(kern, smem);
