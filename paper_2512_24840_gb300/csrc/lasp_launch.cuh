@@ -142,11 +142,15 @@ int launch_fit_multi_slots(const FitParams& P, const MultiWs& W, int n_running, 
     // slots and CTAs left without work end at once (freeing their SMs)
     e = cuda_rc(cudaMemsetAsync(W.next, 0, 2 * sizeof(int), st));
     if (e) return e;
-    slots_running_list<<<(P.N + 255) / 256, 256, 0, st>>>(P.N, P.status, const_cast<int*>(W.list), W.next);
-    e = cuda_rc(cudaGetLastError());
+    e = prof_time("slots_running_list", st, [&]() {
+        slots_running_list<<<(P.N + 255) / 256, 256, 0, st>>>(P.N, P.status, const_cast<int*>(W.list), W.next);
+        return cuda_rc(cudaGetLastError());
+    });
     if (e) return e;
-    kern<<<grid, NT, smem, st>>>(P, W);
-    return cuda_rc(cudaGetLastError());
+    return prof_time("fit_multi_kernel<slots>", st, [&]() {
+        kern<<<grid, NT, smem, st>>>(P, W);
+        return cuda_rc(cudaGetLastError());
+    });
 }
 
 // Preprocessing of `count` freshly admitted slots (idx: device slot indices).
@@ -160,8 +164,10 @@ int launch_fit_prep_slots(const FitParams& P, const MultiWs& W, const int32_t* i
         NT == 256 ? fit_prep_slots_kernel<256, D> : fit_prep_slots_kernel<512, D>;
     int e = set_smem_attr(prep, smem);
     if (e) return e;
-    prep<<<count, NT, smem, st>>>(P, W, idx);
-    return cuda_rc(cudaGetLastError());
+    return prof_time("fit_prep_slots_kernel", st, [&]() {
+        prep<<<count, NT, smem, st>>>(P, W, idx);
+        return cuda_rc(cudaGetLastError());
+    });
 }
 
 template <int D>

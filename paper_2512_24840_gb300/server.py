@@ -319,6 +319,14 @@ class _Served(ct.Structure):
                 ("t_done_ns", ct.c_int64)]
 
 
+# numpy view of a lasp_served array (same field offsets as the C struct), so a
+# tick's results are unpacked column by column instead of field by field
+_SERVED_DT = np.dtype({"names": [f[0] for f in _Served._fields_],
+                       "formats": ["<i8", "<i4", ("<f4", (5,)), "<f4", "<i4", "<u4", "<i8", "<i8"],
+                       "offsets": [getattr(_Served, f[0]).offset for f in _Served._fields_],
+                       "itemsize": ct.sizeof(_Served)})
+
+
 class NativeServer:
     """The same request loop run by the library's native scheduler
     (lasp_server_*): submission copies into a pinned ring in C, one tick
@@ -410,11 +418,16 @@ class NativeServer:
         while True:
             got = ct.c_int()
             self.lib.lasp_server_poll(self._h, self._buf, len(self._buf), ct.byref(got))
-            for r in self._buf[:got.value]:
-                out.append(Result(int(r.tag), self.names[r.lane], np.array(r.theta[:], np.float32),
-                                  float(r.loss), int(r.steps), int(r.status), r.t_submit_ns * 1e-9,
-                                  r.t_done_ns * 1e-9))
-            if got.value < len(self._buf):
+            n = got.value
+            if n:
+                a = np.frombuffer(self._buf, dtype=_SERVED_DT, count=n).copy()
+                tags, lanes = a["tag"].tolist(), a["lane"].tolist()
+                loss, steps, st = a["loss"].tolist(), a["steps"].tolist(), a["status"].tolist()
+                ts, td = (a["t_submit_ns"] * 1e-9).tolist(), (a["t_done_ns"] * 1e-9).tolist()
+                th = a["theta"]
+                out += [Result(tags[i], self.names[lanes[i]], th[i], loss[i], steps[i], st[i], ts[i], td[i])
+                        for i in range(n)]
+            if n < len(self._buf):
                 break
         self.done.extend(out)
         return out
