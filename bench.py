@@ -43,7 +43,7 @@ FP32_LANES_PER_SM, N_SM = 128, 152
 # is captured again): it reads the prepared y, W rows (8 B a pixel) and the
 # table, and writes the results.
 FIT_KERNEL = "fit_multi_kernel<256,6,4,false>"
-FIT_TRAFFIC_BYTES = 136_868_608
+FIT_TRAFFIC_BYTES = 130_102_528 + 3_329_024
 
 
 def parse():
