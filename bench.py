@@ -287,11 +287,16 @@ def served_stream(torch, lasp, grids, tables, seconds=2.0, loads=(0.5, 0.8, 0.95
             i = rng.integers(len(f))
             srv.submit(lane, f[i], iv[i], gd[i], th[i])
 
+    # the native scheduler hands back each tick's finished fits as one array
+    arrays = native
+    drain = srv.run_until_idle_arrays if arrays else srv.run_until_idle
+    tick = srv.tick_arrays if arrays else srv.tick
+
     submit(512)                                   # warm-up
-    srv.run_until_idle()
+    drain()
     submit(burst)
     t0 = time.perf_counter()
-    res = srv.run_until_idle()
+    res = drain()
     sat = len(res) / (time.perf_counter() - t0)
     one_shot = None
     if len(grids) == 1:
@@ -328,16 +333,25 @@ def served_stream(torch, lasp, grids, tables, seconds=2.0, loads=(0.5, 0.8, 0.95
             t0 = time.perf_counter()
             th.start()
             while time.perf_counter() - t0 < seconds:
-                done += srv.tick()
+                done.append(tick()) if arrays else done.extend(tick())
                 if not srv.pending():
                     time.sleep(0.0005)
             stop.set()
             th.join()
-            done += srv.run_until_idle()
+            done.append(drain()) if arrays else done.extend(drain())
             elapsed = time.perf_counter() - t0
-            conv = sum(1 for r in done if r.status & 3)
-            wins.append({"served_per_s": len(done) / elapsed, "converged_per_s": conv / elapsed,
-                         "n": len(done), **latency_percentiles(done)})
+            if arrays:
+                a = np.concatenate(done)
+                conv = int(((a["status"] & 3) != 0).sum())
+                lat = (a["t_done_ns"] - a["t_submit_ns"]) * 1e-6
+                pct = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))} if len(a) else {}
+                n_done = len(a)
+            else:
+                conv = sum(1 for r in done if r.status & 3)
+                pct = latency_percentiles(done)
+                n_done = len(done)
+            wins.append({"served_per_s": n_done / elapsed, "converged_per_s": conv / elapsed,
+                         "n": n_done, **pct})
         lv = {"load": load, "offered_per_s": rate}
         for key in ("served_per_s", "converged_per_s", "p50_ms", "p99_ms"):
             vals = sorted(w[key] for w in wins if w.get(key) is not None)

@@ -33,9 +33,13 @@ struct LmParams {
     float* weight;
 };
 
+// Shared reduction space, floats a warp: every block sum of an evaluation has
+// at most 64 values (54 normal-equation sums at Legendre degree 8).
+constexpr int LM_RED_W = 64;
+
 __host__ inline size_t lm_smem_bytes(int p, int H, int n_model, int NT) {
     size_t fl = (size_t)2 * ((p + 3) & ~3) + 4 * (size_t)((n_model + 3) & ~3) + 3 * 96 + (1 + DPS) * KROWS +
-                (size_t)(NT / 32) * 48 + 256;
+                (size_t)(NT / 32) * LM_RED_W + 256;
     size_t sortb = (size_t)3 * ((p + 3) & ~3);
     return 4 * (fl > sortb ? fl : sortb);
 }
@@ -63,23 +67,48 @@ __device__ void lm_eval(const ModelDev& M, const float* th, const float* y, cons
     const int h = *s_h;
     int k0, k1;
     active_rows(M, th[0], k0, k1);
-    for (int mm = tid; mm < nm; mm += NT) {
-        float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+    // F' (and at a full evaluation its three basis derivatives): 16 consecutive
+    // model pixels per thread, the table rows (padded to 16 floats) from L2 with
+    // 256-bit loads, each load feeding every contraction; per model pixel the
+    // same sequence of fmas over k as one scalar load per value
+    for (int m0 = tid * 16; m0 < nm; m0 += NT * 16) {
+        constexpr int NQ = FULL ? 4 : 1;
+        float a[NQ][16];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+#pragma unroll
+            for (int r = 0; r < 16; ++r) a[q][r] = 0.0f;
+        const float* crow = M.Cp + m0;
+#pragma unroll 2
         for (int k = k0; k < k1; ++k) {
-            const float c = __ldg(M.C + (size_t)k * nm + mm);
-            a0 = fmaf(phi[k], c, a0);
+            const float* ck = crow + (size_t)k * M.ldc;
+            const float pk = phi[k];
+            float d0 = 0.0f, d1 = 0.0f, d2 = 0.0f;
             if (FULL) {
-                a1 = fmaf(dphi[DPS * k + 0], c, a1);
-                a2 = fmaf(dphi[DPS * k + 1], c, a2);
-                a3 = fmaf(dphi[DPS * k + 2], c, a3);
+                d0 = dphi[DPS * k + 0];
+                d1 = dphi[DPS * k + 1];
+                d2 = dphi[DPS * k + 2];
+            }
+#pragma unroll
+            for (int h8 = 0; h8 < 2; ++h8) {
+                float c[8];
+                ldg8(ck + 8 * h8, c);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    a[0][8 * h8 + e] = fmaf(pk, c[e], a[0][8 * h8 + e]);
+                    if (FULL) {
+                        a[NQ > 1 ? 1 : 0][8 * h8 + e] = fmaf(d0, c[e], a[NQ > 1 ? 1 : 0][8 * h8 + e]);
+                        a[NQ > 2 ? 2 : 0][8 * h8 + e] = fmaf(d1, c[e], a[NQ > 2 ? 2 : 0][8 * h8 + e]);
+                        a[NQ > 3 ? 3 : 0][8 * h8 + e] = fmaf(d2, c[e], a[NQ > 3 ? 3 : 0][8 * h8 + e]);
+                    }
+                }
             }
         }
-        Fp[mm] = a0;
-        if (FULL) {
-            Fp[na + mm] = a1;
-            Fp[2 * na + mm] = a2;
-            Fp[3 * na + mm] = a3;
-        }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+#pragma unroll
+            for (int r = 0; r < 16; ++r)
+                if (m0 + r < nm) Fp[q * na + m0 + r] = a[q][r];
     }
     __syncthreads();
     float f[PPT], df[FULL ? 5 : 1][PPT];
@@ -418,7 +447,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) lm_kernel(const LmParam
     float* phi = g + 288;
     float* dphi = phi + KROWS;
     float* red = phi + (1 + DPS) * KROWS;
-    float* outf = red + (NT / 32) * 48;
+    float* outf = red + (NT / 32) * LM_RED_W;
     float2* outff = reinterpret_cast<float2*>(outf + ((((size_t)(outf - sm)) & 1) ? 1 : 0));
     __shared__ float2 s_G[Gram<D>::NV], s_sum[21];
     __shared__ float s_b[D + 1], s_db[5 * (D + 1)];

@@ -401,6 +401,21 @@ class NativeServer:
             return int(n.value) + len(self._overflow)
 
     def tick(self) -> list[Result]:
+        """One scheduling round; the finished fits as Result objects."""
+        a = self.tick_arrays()
+        tags, lanes = a["tag"].tolist(), a["lane"].tolist()
+        loss, steps, st = a["loss"].tolist(), a["steps"].tolist(), a["status"].tolist()
+        ts, td = (a["t_submit_ns"] * 1e-9).tolist(), (a["t_done_ns"] * 1e-9).tolist()
+        th = a["theta"]
+        out = [Result(tags[i], self.names[lanes[i]], th[i], loss[i], steps[i], st[i], ts[i], td[i])
+               for i in range(len(a))]
+        self.done.extend(out)
+        return out
+
+    def tick_arrays(self) -> np.ndarray:
+        """One scheduling round; the finished fits as one structured array
+        (fields tag, lane, theta[5], loss, steps, status, t_submit_ns,
+        t_done_ns), without a Python object per fit."""
         with self._lock:
             while self._overflow:
                 rid, li, a = self._overflow[0]
@@ -414,23 +429,24 @@ class NativeServer:
         rc = self.lib.lasp_server_tick(self._h, ct.byref(nf))
         if rc:
             raise self._lasp.LaspError(rc, "lasp_server_tick")
-        out = []
+        parts = []
         while True:
             got = ct.c_int()
             self.lib.lasp_server_poll(self._h, self._buf, len(self._buf), ct.byref(got))
             n = got.value
             if n:
-                a = np.frombuffer(self._buf, dtype=_SERVED_DT, count=n).copy()
-                tags, lanes = a["tag"].tolist(), a["lane"].tolist()
-                loss, steps, st = a["loss"].tolist(), a["steps"].tolist(), a["status"].tolist()
-                ts, td = (a["t_submit_ns"] * 1e-9).tolist(), (a["t_done_ns"] * 1e-9).tolist()
-                th = a["theta"]
-                out += [Result(tags[i], self.names[lanes[i]], th[i], loss[i], steps[i], st[i], ts[i], td[i])
-                        for i in range(n)]
+                parts.append(np.frombuffer(self._buf, dtype=_SERVED_DT, count=n).copy())
             if n < len(self._buf):
                 break
-        self.done.extend(out)
-        return out
+        return np.concatenate(parts) if len(parts) > 1 else (parts[0] if parts else np.zeros(0, _SERVED_DT))
+
+    def run_until_idle_arrays(self, max_ticks: int = 100000) -> np.ndarray:
+        parts = []
+        for _ in range(max_ticks):
+            if not self.pending():
+                break
+            parts.append(self.tick_arrays())
+        return np.concatenate(parts) if parts else np.zeros(0, _SERVED_DT)
 
     def run_until_idle(self, max_ticks: int = 100000) -> list[Result]:
         res = []

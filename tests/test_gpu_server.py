@@ -127,3 +127,30 @@ def test_step_running_hint_only_sizes_the_launch(hint):
         assert np.array_equal(theta[s], one["theta"][k].cpu().numpy()), k
         assert steps[s] == int(one["steps"][k])
     pool.close()
+
+
+def test_native_ticks_as_arrays_equal_the_result_objects():
+    """NativeServer.tick_arrays hands back a tick's finished fits as one
+    structured array (what the bench's native scheduler uses); its fields are
+    those of the Result objects of tick()."""
+    from paper_2512_24840_gb300 import lasp
+    from paper_2512_24840_gb300.server import NativeServer
+    lasp.load(build=True)
+    g = S.LAMOST
+    ip = lasp.Interp.from_grid(g, table(g.name), S.EXPS, S.BASIS_LO, S.BASIS_HI, S.BOX_LO, S.BOX_HI)
+    f, iv, gd, th = _observed(g, 20, 65)
+    got = {}
+    for how in ("objects", "arrays"):
+        srv = NativeServer({"l": ip}, {"l": 8}, chunk=9, max_steps=400)
+        rids = [srv.submit("l", f[i], iv[i], gd[i], th[i]) for i in range(20)]
+        if how == "objects":
+            res = {r.rid: (r.theta, r.steps, r.status, r.latency) for r in srv.run_until_idle()}
+        else:
+            a = srv.run_until_idle_arrays()
+            res = {int(r["tag"]): (r["theta"], int(r["steps"]), int(r["status"]),
+                                   (int(r["t_done_ns"]) - int(r["t_submit_ns"])) * 1e-9) for r in a}
+        srv.close()
+        got[how] = [res[rid] for rid in rids]
+    for a, b in zip(got["objects"], got["arrays"]):
+        assert np.array_equal(a[0], b[0]) and a[1] == b[1] and a[2] == b[2]
+        assert a[3] > 0 and b[3] > 0
