@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
 #pragma unroll
                 for (int r = 0; r < PPT / 2; ++r) acc[s][r] = make_float2(0.0f, 0.0f);
             const float* crow = M.Cp + j0;
-#pragma unroll 2
+#pragma unroll 4
             for (int k = kb; k < ke; ++k) {
                 float2 pk[S];
 #pragma unroll
@@ -539,7 +539,7 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
                 for (int r = 0; r < PPT; ++r)
                     dpair[u][r] = make_float2(dfp[2 * u][r], 2 * u + 1 < S ? dfp[2 * u + 1][r] : 0.0f);
             const float* crow = M.Cp + j0;
-#pragma unroll 2
+#pragma unroll 4
             for (int k = kb; k < ke; ++k) {
                 const float* ck = crow + (size_t)k * M.ldc;
                 float c[PPT];
