@@ -23,7 +23,7 @@
 
 namespace lasp {
 
-constexpr int TB = 8;       // taps per block
+constexpr int TB = 12;       // taps per block
 constexpr int TAPBUF = 128; // tap buffer (>= 2 HMAX + 2 TB + 1)
 constexpr int NADJ = 7;     // end-of-step sums: S, nonpos, d/dmu, d/dsigma, d/d(Teff, logg, FeH)
 
