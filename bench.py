@@ -264,10 +264,14 @@ def served_stream(torch, lasp, grids, tables, seconds=2.0, loads=(0.5, 0.8, 0.95
     """Continuous batching of a request mix over the given grids (equal
     shares; random masks 0-20%, SNR 5-100).  The saturated rate is the drain
     rate of a burst; then Poisson arrivals at fractions of it, `repeats`
-    windows of `seconds` each per load.  Latency: submit -> result on host.
-    With one grid, the one-shot batch fit of the same burst is timed too."""
+    windows of `seconds` each per load.  Arrival times are drawn before the
+    window; a producer thread submits every arrival that is due, per lane in
+    one submit_many call of consecutive pool rows.  Latency: scheduled
+    arrival -> result on host (the producer's lag behind the schedule plus
+    the scheduler's submit -> result time).  With one grid, the one-shot batch
+    fit of the same burst is timed too."""
     import threading
-    from paper_2512_24840_gb300.server import Server, latency_percentiles
+    from paper_2512_24840_gb300.server import Server
     from paper_2512_24840_gb300.server import DevicePool, NativeServer
     ips = {g.name: lasp.Interp.from_grid(g, tables[g.name], S.EXPS, S.BASIS_LO, S.BASIS_HI,
                                          S.BOX_LO, S.BOX_HI) for g in grids}
@@ -278,7 +282,8 @@ def served_stream(torch, lasp, grids, tables, seconds=2.0, loads=(0.5, 0.8, 0.95
         model = ips[g.name].forward(torch.tensor(d["truth"], dtype=torch.float32, device=dev),
                                     torch.tensor(d["b_true"], dtype=torch.float32, device=dev))
         flux, ivar = S.finish_obs(model.double().cpu().numpy(), d)
-        pool[g.name] = (flux, ivar, d["good"], np.asarray(d["theta0"], np.float32))
+        pool[g.name] = (np.ascontiguousarray(flux, np.float32), np.ascontiguousarray(ivar, np.float32),
+                        np.ascontiguousarray(d["good"], np.uint8), np.asarray(d["theta0"], np.float32))
     prec = fit_opts.get("precision", "fp32")
     budget = 2 * burst * max(DevicePool.bytes_per_slot(g.n_pix, DEG, prec) for g in grids)
     cls = NativeServer if native else Server
@@ -323,43 +328,69 @@ def served_stream(torch, lasp, grids, tables, seconds=2.0, loads=(0.5, 0.8, 0.95
         rate = load * sat
         wins = []
         for rep in range(repeats):
+            n_arr = int(rate * seconds * 1.2) + 64
+            t_arr = np.cumsum(rng.exponential(1.0 / rate, size=n_arr))
+            lane_arr = rng.integers(len(names), size=n_arr)
             stop = threading.Event()
-            done = []
+            done, rid_parts, lag_parts = [], [], []
+            cur = {nm: int(rng.integers(len(pool[nm][0]))) for nm in names}
 
             def producer():
-                t_next = time.perf_counter()
-                while not stop.is_set():
-                    t_next += rng.exponential(1.0 / rate)
-                    dt = t_next - time.perf_counter()
-                    if dt > 0:
-                        time.sleep(dt)
-                    submit(1)
+                i = 0
+                while not stop.is_set() and i < n_arr:
+                    now = time.perf_counter() - t0
+                    j = int(np.searchsorted(t_arr, now, side="right"))
+                    if j <= i:
+                        time.sleep(min(t_arr[i] - now, 0.001))
+                        continue
+                    for k, nm in enumerate(names):
+                        due = np.nonzero(lane_arr[i:j] == k)[0] + i
+                        f, iv, gd, th = pool[nm]
+                        while len(due):
+                            c = cur[nm]
+                            m = min(len(due), len(f) - c)       # consecutive rows, split at the wrap
+                            t_call = time.perf_counter() - t0
+                            rid_parts.append(srv.submit_many(nm, f[c:c + m], iv[c:c + m], gd[c:c + m],
+                                                             th[c:c + m]))
+                            lag_parts.append(t_call - t_arr[due[:m]])
+                            cur[nm] = (c + m) % len(f)
+                            due = due[m:]
+                    i = j
 
-            th = threading.Thread(target=producer, daemon=True)
+            prod = threading.Thread(target=producer, daemon=True)
             t0 = time.perf_counter()
-            th.start()
+            prod.start()
             while time.perf_counter() - t0 < seconds:
                 done.append(tick()) if arrays else done.extend(tick())
                 if not srv.pending():
                     time.sleep(0.0005)
             stop.set()
-            th.join()
+            prod.join()
+            t_prod = time.perf_counter() - t0
             done.append(drain()) if arrays else done.extend(drain())
             elapsed = time.perf_counter() - t0
+            rids = np.concatenate(rid_parts) if rid_parts else np.zeros(0, np.int64)
+            lags = np.concatenate(lag_parts) if lag_parts else np.zeros(0)
             if arrays:
                 a = np.concatenate(done)
+                tags = a["tag"].astype(np.int64)
                 conv = int(((a["status"] & 3) != 0).sum())
-                lat = (a["t_done_ns"] - a["t_submit_ns"]) * 1e-6
-                pct = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))} if len(a) else {}
-                n_done = len(a)
+                in_sched = (a["t_done_ns"] - a["t_submit_ns"]) * 1e-9
             else:
+                tags = np.array([r.rid for r in done], dtype=np.int64)
                 conv = sum(1 for r in done if r.status & 3)
-                pct = latency_percentiles(done)
-                n_done = len(done)
+                in_sched = np.array([r.t_done - r.t_submit for r in done])
+            n_done = len(tags)
+            pos = np.searchsorted(rids, tags)
+            assert n_done == len(rids) and np.array_equal(rids[np.minimum(pos, len(rids) - 1)], tags)
+            lat = (lags[pos] + in_sched) * 1e3
+            pct = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                   "submit_lag_p99_ms": float(np.percentile(lags, 99) * 1e3)} if n_done else {}
             wins.append({"served_per_s": n_done / elapsed, "converged_per_s": conv / elapsed,
-                         "n": n_done, **pct})
+                         "arrivals_per_s": len(rids) / t_prod, "n": n_done, **pct})
         lv = {"load": load, "offered_per_s": rate}
-        for key in ("served_per_s", "converged_per_s", "p50_ms", "p99_ms"):
+        for key in ("arrivals_per_s", "served_per_s", "converged_per_s", "p50_ms", "p99_ms",
+                    "submit_lag_p99_ms"):
             vals = sorted(w[key] for w in wins if w.get(key) is not None)
             if vals:
                 lv[key] = statistics.median(vals)

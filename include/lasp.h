@@ -343,6 +343,17 @@ void lasp_server_destroy(lasp_server s);
 int lasp_server_submit(lasp_server s, int lane, const float* flux, const float* ivar,
                        const uint8_t* good, const float* theta0, int64_t tag);
 
+/* Copy n requests (rows of n x n_pix flux, ivar float32, n x n_pix good uint8,
+ * n x 5 theta0 float32, all host memory that may be reused on return; tags[n])
+ * into lane `lane`'s ring in row order, under one lock and with one submit
+ * time.  Takes as many rows as the ring has room for, from the first:
+ * *n_taken receives that count.  Returns LASP_OK when all n were taken,
+ * LASP_EBUSY when fewer were (the rest were not copied), LASP_EINVAL for a
+ * bad handle, lane, n < 0 or a NULL pointer (n_taken always; the arrays when
+ * n > 0).  Equivalent to n lasp_server_submit calls. */
+int lasp_server_submit_n(lasp_server s, int lane, int n, const float* flux, const float* ivar,
+                         const uint8_t* good, const float* theta0, const int64_t* tags, int* n_taken);
+
 /* One scheduling round (see above); *n_finished (may be NULL) receives the
  * number of fits retired in it.  Blocks until the round's GPU work is done.
  * Returns LASP_ETIMEOUT when a fit retired in this round carries

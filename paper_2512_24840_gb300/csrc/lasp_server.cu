@@ -221,6 +221,37 @@ int lasp_server_submit(lasp_server S, int lane, const float* flux, const float* 
     return LASP_OK;
 }
 
+int lasp_server_submit_n(lasp_server S, int lane, int n, const float* flux, const float* ivar,
+                         const uint8_t* good, const float* theta0, const int64_t* tags, int* n_taken) {
+    if (n_taken) *n_taken = 0;
+    if (!S || lane < 0 || lane >= (int)S->lanes.size() || n < 0 || !n_taken) return LASP_EINVAL;
+    if (n == 0) return LASP_OK;
+    if (!flux || !ivar || !good || !theta0 || !tags) return LASP_EINVAL;
+    Lane* L = S->lanes[lane];
+    const size_t p = (size_t)L->n_pix;
+    std::lock_guard<std::mutex> g(L->mu);
+    const int64_t room = L->ring - (L->staged - L->released);
+    const int k = (int)std::min<int64_t>(n, room > 0 ? room : 0);
+    const int64_t t = now_ns();
+    // at most two contiguous ranges of ring entries (the second after the wrap)
+    for (int i = 0; i < k;) {
+        const int64_t e = (L->staged + i) % L->ring;
+        const int run = (int)std::min<int64_t>(k - i, L->ring - e);
+        std::memcpy(L->r_flux + e * p, flux + (size_t)i * p, (size_t)run * p * 4);
+        std::memcpy(L->r_ivar + e * p, ivar + (size_t)i * p, (size_t)run * p * 4);
+        std::memcpy(L->r_good + e * p, good + (size_t)i * p, (size_t)run * p);
+        std::memcpy(L->r_th0 + e * 5, theta0 + (size_t)i * 5, (size_t)run * 5 * 4);
+        for (int j = 0; j < run; ++j) {
+            L->r_id[e + j] = tags[i + j];
+            L->r_tsub[e + j] = t;
+        }
+        i += run;
+    }
+    L->staged += k;
+    *n_taken = k;
+    return k == n ? LASP_OK : LASP_EBUSY;
+}
+
 int lasp_server_tick(lasp_server S, int* n_finished) {
     if (n_finished) *n_finished = 0;
     if (!S) return LASP_EINVAL;

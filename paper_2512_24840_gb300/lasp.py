@@ -76,7 +76,8 @@ EXPORTS = ["lasp_init_interp", "lasp_free_interp", "lasp_default_opts", "lasp_fi
            "lasp_slots_step_running",
            "lasp_slots_fetch", "lasp_interp_eval_static", "lasp_clean_mask",
            "lasp_init_interp_piecewise", "lasp_server_create", "lasp_server_destroy",
-           "lasp_server_submit", "lasp_server_tick", "lasp_server_poll", "lasp_server_pending",
+           "lasp_server_submit", "lasp_server_submit_n", "lasp_server_tick", "lasp_server_poll",
+           "lasp_server_pending",
            "lasp_test_wait_limit", "lasp_profile", "lasp_profile_read"]
 
 
@@ -104,6 +105,8 @@ def load(build: bool = False):
         lib.lasp_server_destroy.argtypes = [P]
         lib.lasp_server_submit.argtypes = [P, I, P, P, P, P, ct.c_int64]
         lib.lasp_server_submit.restype = I
+        lib.lasp_server_submit_n.argtypes = [P, I, I, P, P, P, P, P, P]
+        lib.lasp_server_submit_n.restype = I
         lib.lasp_server_tick.argtypes = [P, P]
         lib.lasp_server_tick.restype = I
         lib.lasp_server_poll.argtypes = [P, P, I, P]

@@ -253,9 +253,18 @@ class Server:
             ln = self.lanes[lane]
             stage = getattr(ln.pool, "stage", None)
             k = stage(flux, ivar, good, theta0) if stage is not None else -1
-            keep = (None, None, None, None) if k >= 0 else (flux, ivar, good, theta0)
+            # an unstaged request keeps copies: the caller may reuse its arrays
+            keep = (None, None, None, None) if k >= 0 else (
+                np.array(flux, np.float32), np.array(ivar, np.float32), np.array(good, np.uint8),
+                np.array(theta0, np.float32))
             ln.waiting.append(Request(rid, lane, *keep, t_submit=self.clock(), staged=k))
         return rid
+
+    def submit_many(self, lane: str, flux, ivar, good, theta0) -> np.ndarray:
+        """Submit the rows of (n, n_pix) flux, ivar, good and (n, 5) theta0 as
+        n requests in row order; returns their ids."""
+        return np.array([self.submit(lane, flux[i], ivar[i], good[i], theta0[i])
+                         for i in range(len(flux))], dtype=np.int64)
 
     def pending(self) -> int:
         with self._lock:
@@ -378,17 +387,49 @@ class NativeServer:
             self._next += 1
             queued = bool(self._overflow)
             if queued:
-                self._overflow.append((rid, li, a))
+                # copied: the caller may reuse its arrays once submit returns
+                self._overflow.append((rid, li, tuple(x.copy() for x in a)))
         if queued:
             return rid
         # the library copy runs without the Python lock (ctypes drops the GIL)
         rc = self._submit_now(li, rid, a)
         if rc == self._lasp.EBUSY:
             with self._lock:
-                self._overflow.append((rid, li, a))     # handed to the ring at a later tick
+                # handed to the ring at a later tick
+                self._overflow.append((rid, li, tuple(x.copy() for x in a)))
         elif rc:
             raise self._lasp.LaspError(rc, "lasp_server_submit")
         return rid
+
+    def submit_many(self, lane: str, flux, ivar, good, theta0) -> np.ndarray:
+        """Submit the rows of (n, n_pix) flux, ivar, good and (n, 5) theta0 as
+        n requests in row order with one library call; returns their ids.
+        Rows the ring has no room for wait, copied, for a later tick."""
+        li = self.names.index(lane)
+        a = (np.ascontiguousarray(flux, np.float32), np.ascontiguousarray(ivar, np.float32),
+             np.ascontiguousarray(good, np.uint8), np.ascontiguousarray(theta0, np.float32))
+        n = a[0].shape[0]
+        p = self.n_pix[lane]
+        if a[0].shape != (n, p) or a[1].shape != (n, p) or a[2].shape != (n, p) or a[3].shape != (n, 5):
+            raise ValueError("submit_many: rows of n_pix flux, ivar, good and 5 theta0 expected")
+        with self._lock:
+            rids = np.arange(self._next, self._next + n, dtype=np.int64)
+            self._next += n
+            queued = bool(self._overflow)
+        taken = 0
+        if not queued and n:
+            got = ct.c_int()
+            rc = self.lib.lasp_server_submit_n(self._h, li, n, a[0].ctypes.data, a[1].ctypes.data,
+                                               a[2].ctypes.data, a[3].ctypes.data, rids.ctypes.data,
+                                               ct.byref(got))
+            if rc not in (0, self._lasp.EBUSY):
+                raise self._lasp.LaspError(rc, "lasp_server_submit_n")
+            taken = got.value
+        if taken < n:
+            with self._lock:
+                for i in range(taken, n):
+                    self._overflow.append((int(rids[i]), li, tuple(x[i].copy() for x in a)))
+        return rids
 
     @property
     def slots(self) -> dict:

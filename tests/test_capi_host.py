@@ -110,6 +110,10 @@ def test_null_handle_calls_fail_cleanly(lasp):
     assert lib.lasp_server_tick(None, ct.byref(n)) == lasp.EINVAL and n.value == 0
     lib.lasp_server_pending.argtypes = [P, ct.POINTER(ct.c_int64)]
     assert lib.lasp_server_pending(None, ct.byref(ct.c_int64())) == lasp.EINVAL
+    taken = ct.c_int(-1)
+    assert lib.lasp_server_submit_n(None, 0, 1, None, None, None, None, None,
+                                    ct.byref(taken)) == lasp.EINVAL and taken.value == 0
+    assert lib.lasp_server_submit_n(None, 0, 1, None, None, None, None, None, None) == lasp.EINVAL
 
 
 def test_header_is_plain_c(tmp_path):

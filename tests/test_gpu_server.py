@@ -154,3 +154,35 @@ def test_native_ticks_as_arrays_equal_the_result_objects():
     for a, b in zip(got["objects"], got["arrays"]):
         assert np.array_equal(a[0], b[0]) and a[1] == b[1] and a[2] == b[2]
         assert a[3] > 0 and b[3] > 0
+
+
+@pytest.mark.parametrize("ring", [32, 5])
+def test_native_submit_many_equals_single_submits(ring):
+    """submit_many hands rows to lasp_server_submit_n in one call; with a ring
+    smaller than the batch the rows it has no room for wait on the host and
+    enter at later ticks.  Either way each request's result is bitwise the one
+    of a request submitted on its own, and ids follow the row order."""
+    from paper_2512_24840_gb300 import lasp
+    from paper_2512_24840_gb300.server import NativeServer
+    lasp.load(build=True)
+    g = S.LAMOST
+    ip = lasp.Interp.from_grid(g, table(g.name), S.EXPS, S.BASIS_LO, S.BASIS_HI, S.BOX_LO, S.BOX_HI)
+    f, iv, gd, th = _observed(g, 20, 66)
+    srv = NativeServer({"l": ip}, {"l": 8}, chunk=9, max_steps=400)
+    rids = [srv.submit("l", f[i], iv[i], gd[i], th[i]) for i in range(20)]
+    one = {int(r["tag"]): r for r in srv.run_until_idle_arrays()}
+    srv.close()
+    srv = NativeServer({"l": ip}, {"l": 8}, chunk=9, ring={"l": ring}, max_steps=400)
+    head = srv.submit("l", f[0], iv[0], gd[0], th[0])
+    fb, ivb, gdb, thb = f[1:].copy(), iv[1:].copy(), gd[1:].copy(), th[1:].copy()
+    ids = srv.submit_many("l", fb, ivb, gdb, thb)
+    assert ids.tolist() == list(range(head + 1, head + 20))
+    fb[:] = np.nan                                  # the caller's rows may be reused on return
+    many = {int(r["tag"]): r for r in srv.run_until_idle_arrays()}
+    srv.close()
+    assert len(many) == 20
+    for k in range(20):
+        a, b = one[rids[k]], many[head + k]
+        assert np.array_equal(a["theta"], b["theta"]) and a["steps"] == b["steps"], k
+        assert a["status"] == b["status"] and a["loss"] == b["loss"], k
+    ip.close()
