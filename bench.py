@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the mixed-precision, curvature-aware and piecewise entries")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--served-only", action="store_true",
+                    help="only the LAMOST-only served drain (burst, one-shot comparison and a "
+                         "lasp_profile breakdown of its ticks), printed as one JSON line")
     ap.add_argument("--kernels-only", action="store_true",
                     help="only the per-kernel pass (lasp_profile) on the 4096-spectrum batch: one FP32 "
                          "fit, the stage-9 errors at both normal-equation levels, one curvature-aware "
@@ -309,7 +312,7 @@ def served_stream(torch, lasp, grids, tables, seconds=2.0, loads=(0.5, 0.8, 0.95
     t0 = time.perf_counter()
     res = drain()
     sat = len(res) / (time.perf_counter() - t0)
-    one_shot = None
+    one_shot = tick_profile = None
     if len(grids) == 1:
         # the same kind of burst fitted in one batch call, inputs resident on the device
         g = grids[0]
@@ -323,6 +326,24 @@ def served_stream(torch, lasp, grids, tables, seconds=2.0, loads=(0.5, 0.8, 0.95
         o = ips[g.name].fit(*args, out=o, max_steps=MAX_STEPS, **fit_opts)
         torch.cuda.synchronize()
         one_shot = burst / (time.perf_counter() - t1)
+        # where a tick's time goes: the same burst drained again with lasp_profile on
+        # (each timed kernel and copy waits for its closing event, so this drain is slower)
+        submit(burst)
+        lasp.profile(True)
+        lasp.profile_read()
+        n_ticks, tp0 = 0, time.perf_counter()
+        try:
+            while srv.pending():
+                tick()
+                n_ticks += 1
+        finally:
+            prof = lasp.profile_read()
+            lasp.profile(False)
+        wall_p = (time.perf_counter() - tp0) * 1e3
+        dev_ms = sum(v[1] for v in prof.values())
+        tick_profile = {"ticks": n_ticks, "wall_ms": wall_p, "device_ms_total": dev_ms,
+                        "device_frac_of_wall": dev_ms / wall_p,
+                        "device_ms": {k: [v[0], round(v[1], 3)] for k, v in sorted(prof.items())}}
     levels = []
     for load in loads:
         rate = load * sat
@@ -407,6 +428,7 @@ def served_stream(torch, lasp, grids, tables, seconds=2.0, loads=(0.5, 0.8, 0.95
     if one_shot:
         out["one_shot_same_spectra_per_s"] = one_shot
         out["saturated_vs_one_shot"] = sat / one_shot
+        out["tick_profile"] = tick_profile
     return out
 
 
@@ -445,6 +467,11 @@ def run_ours(args):
     g_th0 = torch.tensor(d["theta0"], dtype=torch.float32, device=dev)
     opts = dict(max_steps=MAX_STEPS, legendre_deg=DEG)
     stream = torch.cuda.current_stream()
+    if args.served_only:
+        if rank == 0:
+            r = served_stream(torch, lasp, [S.LAMOST], {S.LAMOST.name: C}, native=True, loads=())
+            print(json.dumps({"workload": "served_lamost_only", **r}))
+        return
     if args.kernels_only:
         pk, _ = peaks()
         mhz0 = pk.get("sm_max_mhz", 2070.0)

@@ -466,7 +466,10 @@ int lasp_last_launches(void);
  * lasp_errors and the curvature-aware fit bracket each kernel they launch
  * with CUDA events on their stream and wait for it, so every kernel is timed
  * on its own (the tensor-core fit then launches its steps one by one instead
- * of replaying the step graph); calls become synchronous.  lasp_profile_read
+ * of replaying the step graph); calls become synchronous.  The slot calls
+ * time their kernels too, and their host-device copies as the entries
+ * "slots_admit_h2d" (one per lasp_slots_admit) and "slots_fetch_d2h" (one
+ * per lasp_slots_fetch).  lasp_profile_read
  * copies up to `max` entries (one per kernel name: launches and total device
  * milliseconds since the last read) into out, *n the count, and clears the
  * table. */

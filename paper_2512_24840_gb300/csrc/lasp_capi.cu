@@ -660,17 +660,22 @@ int lasp_slots_admit(lasp_slots s, int count, const int32_t* slot_idx, const flo
         if (slot_idx[r] < 0 || slot_idx[r] >= s->n) return LASP_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t p = (size_t)s->h->M.n_pix, c = (size_t)count;
-    int rc = cuda_err(cudaMemcpyAsync(s->f_st, flux, c * p * 4, cudaMemcpyHostToDevice, st));
-    if (!rc) rc = cuda_err(cudaMemcpyAsync(s->iv_st, ivar, c * p * 4, cudaMemcpyHostToDevice, st));
-    if (!rc) rc = cuda_err(cudaMemcpyAsync(s->g_st, good, c * p, cudaMemcpyHostToDevice, st));
-    if (!rc) rc = cuda_err(cudaMemcpyAsync(s->th_st, theta0, c * 5 * 4, cudaMemcpyHostToDevice, st));
-    if (!rc) rc = cuda_err(cudaMemcpyAsync(s->idx_st, slot_idx, c * 4, cudaMemcpyHostToDevice, st));
+    int rc = prof_time("slots_admit_h2d", st, [&] {
+        int r = cuda_err(cudaMemcpyAsync(s->f_st, flux, c * p * 4, cudaMemcpyHostToDevice, st));
+        if (!r) r = cuda_err(cudaMemcpyAsync(s->iv_st, ivar, c * p * 4, cudaMemcpyHostToDevice, st));
+        if (!r) r = cuda_err(cudaMemcpyAsync(s->g_st, good, c * p, cudaMemcpyHostToDevice, st));
+        if (!r) r = cuda_err(cudaMemcpyAsync(s->th_st, theta0, c * 5 * 4, cudaMemcpyHostToDevice, st));
+        if (!r) r = cuda_err(cudaMemcpyAsync(s->idx_st, slot_idx, c * 4, cudaMemcpyHostToDevice, st));
+        return r;
+    });
     if (rc) return rc;
-    slots_scatter_kernel<<<count, 256, 0, st>>>(count, (int)p, s->idx_st, s->f_st, s->iv_st, s->g_st,
-                                                 s->th_st, s->flux, s->ivar, s->good, s->theta0, s->S.t,
-                                                 s->status);
+    rc = prof_time("slots_scatter_kernel", st, [&] {
+        slots_scatter_kernel<<<count, 256, 0, st>>>(count, (int)p, s->idx_st, s->f_st, s->iv_st, s->g_st,
+                                                     s->th_st, s->flux, s->ivar, s->good, s->theta0, s->S.t,
+                                                     s->status);
+        return cuda_err(cudaGetLastError());
+    });
     g_last_launches = 1;
-    rc = cuda_err(cudaGetLastError());
     if (!rc && s->grp) {
         rc = grp_pool_admit(s->grp, count, s->idx_st, st);     // prep + join the active list
         g_last_launches = 2;
@@ -712,13 +717,15 @@ int lasp_slots_fetch(lasp_slots s, float* theta, float* loss, int32_t* steps, ui
     if (!s) return LASP_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t n = (size_t)s->n;
-    int rc = LASP_OK;
-    if (!rc && theta) rc = cuda_err(cudaMemcpyAsync(theta, s->theta, n * 5 * 4, cudaMemcpyDeviceToHost, st));
-    if (!rc && loss) rc = cuda_err(cudaMemcpyAsync(loss, s->loss, n * 4, cudaMemcpyDeviceToHost, st));
-    if (!rc && steps) rc = cuda_err(cudaMemcpyAsync(steps, s->steps, n * 4, cudaMemcpyDeviceToHost, st));
-    if (!rc && status) rc = cuda_err(cudaMemcpyAsync(status, s->status, n * 4, cudaMemcpyDeviceToHost, st));
-    if (!rc && weight) rc = cuda_err(cudaMemcpyAsync(weight, s->weight, n * 4, cudaMemcpyDeviceToHost, st));
-    return rc;
+    return prof_time("slots_fetch_d2h", st, [&] {
+        int rc = LASP_OK;
+        if (!rc && theta) rc = cuda_err(cudaMemcpyAsync(theta, s->theta, n * 5 * 4, cudaMemcpyDeviceToHost, st));
+        if (!rc && loss) rc = cuda_err(cudaMemcpyAsync(loss, s->loss, n * 4, cudaMemcpyDeviceToHost, st));
+        if (!rc && steps) rc = cuda_err(cudaMemcpyAsync(steps, s->steps, n * 4, cudaMemcpyDeviceToHost, st));
+        if (!rc && status) rc = cuda_err(cudaMemcpyAsync(status, s->status, n * 4, cudaMemcpyDeviceToHost, st));
+        if (!rc && weight) rc = cuda_err(cudaMemcpyAsync(weight, s->weight, n * 4, cudaMemcpyDeviceToHost, st));
+        return rc;
+    });
 }
 
 }  // extern "C"

@@ -54,3 +54,36 @@ def test_profile_times_each_kernel_and_changes_nothing(lasp):
     assert times["k1_interp"][0] >= steps + 1            # one K1 per step of the longest fit
     assert lasp.profile_read() == {}                      # read clears
     ip.close()
+
+
+def test_profile_times_a_served_tick(lasp):
+    """The slot calls behind a served tick are profiled too: the admission
+    copies, the scatter and prep kernels, the running-slot list, the step
+    kernel and the result fetch, one entry each."""
+    from paper_2512_24840_gb300.server import NativeServer
+    g = S.LAMOST
+    ip = lasp.Interp.from_grid(g, table(g.name), S.EXPS, S.BASIS_LO, S.BASIS_HI, S.BOX_LO, S.BOX_HI)
+    M, d = observed(g, 12, 402, snr=(30, 100), mask_frac=0.02)
+    th0 = np.asarray(d["theta0"], np.float32)
+    srv = NativeServer({"l": ip}, {"l": 8}, chunk=20, max_steps=300)
+    for i in range(12):
+        srv.submit("l", d["flux"][i], d["ivar"][i], d["good"][i], th0[i])
+    lasp.profile(True)
+    try:
+        lasp.profile_read()
+        n_ticks = 0
+        while srv.pending():
+            srv.tick_arrays()
+            n_ticks += 1
+        times = lasp.profile_read()
+    finally:
+        lasp.profile(False)
+    srv.close()
+    for name in ("slots_admit_h2d", "slots_scatter_kernel", "fit_prep_slots_kernel", "slots_running_list",
+                 "fit_multi_kernel<slots>", "slots_fetch_d2h"):
+        assert name in times, (name, sorted(times))
+        assert times[name][1] > 0.0
+    assert times["slots_fetch_d2h"][0] == n_ticks           # one result fetch a tick
+    assert times["fit_multi_kernel<slots>"][0] == n_ticks   # one step launch a tick
+    assert times["slots_admit_h2d"][0] >= 2                 # 8 slots for 12 requests: two admissions
+    ip.close()
