@@ -23,11 +23,12 @@
 // lanes at three CTAs per SM 24.6 ms (before the later refinements, which
 // brought four lanes to 21.0 ms).
 //
-// The FULL variant adds the Clean update (stage 6; a lane's mask lives in its
-// W row), resumable slots (a lane resumes a running slot from its saved
-// state, suspends it after the step budget, and takes the next one from a
-// list of running slots) and the FP64 normal equations; the plain batch fit
-// runs the lighter variant.
+// Three variants (MODE): the plain batch fit (MULTI_PLAIN); resumable slots
+// (MULTI_SLOTS: a lane resumes a running slot from its saved state, suspends
+// it after the step budget, and takes the next one from a list of running
+// slots); and MULTI_FULL, resumable slots plus the Clean update (stage 6; a
+// lane's mask lives in its W row) and the FP64 normal equations.  Each
+// variant compiles only what it runs, so the lighter ones spill less.
 #pragma once
 
 #include "lasp_clean.cuh"
@@ -185,9 +186,9 @@ __host__ __device__ constexpr int multi_min_blocks() {
     return NT == 256 ? (S <= 2 ? 3 : 2) : 1;
 }
 
-// FULL: with the Clean update and resumable slots; the plain batch fit
-// instantiates FULL = false, whose lighter register use spills less.
-template <int NT, int D, int S, bool FULL>
+constexpr int MULTI_PLAIN = 0, MULTI_FULL = 1, MULTI_SLOTS = 2;
+
+template <int NT, int D, int S, int MODE>
 __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kernel(const FitParams P,
                                                                                   const MultiWs Wk) {
     using Gm = Gram<D>;
@@ -198,6 +199,7 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
     const ModelDev& M = P.M;
     const int p = M.n_pix, H = M.pad, nm = M.n_model;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr bool FULL = MODE == MULTI_FULL;
     const MultiSmem L(p, H, nm, NT, D, M.K, S, FULL);
     float* red = sm + L.red;
     float* out = sm + L.out;
@@ -212,7 +214,7 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
     double b1t = 1.0, b2t = 1.0;
     // resumable slots (P.S.x set): a lane takes running slots, resumes each from
     // its saved state and suspends it after P.S.budget steps
-    const bool slots = FULL && P.S.x != nullptr;
+    const bool slots = MODE != MULTI_PLAIN && P.S.x != nullptr;
 
     if (tid < S) {
         s_i[tid] = -1;

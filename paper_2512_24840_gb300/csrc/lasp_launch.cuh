@@ -77,8 +77,8 @@ int launch_fit_multi(const FitParams& P, cudaStream_t st) {
     // resumable slots, and Clean with too few lanes for its scratch, stay on fit_kernel
     if (P.S.x || (P.O.clean && S < 3) || smem > 227 * 1024 || smem_prep > 227 * 1024) return launch_fit<D>(P, st);
     void (*kern)(const FitParams, const MultiWs) =
-        full ? (NT == 256 ? fit_multi_kernel<256, D, S, true> : fit_multi_kernel<512, D, S, true>)
-             : (NT == 256 ? fit_multi_kernel<256, D, S, false> : fit_multi_kernel<512, D, S, false>);
+        full ? (NT == 256 ? fit_multi_kernel<256, D, S, MULTI_FULL> : fit_multi_kernel<512, D, S, MULTI_FULL>)
+             : (NT == 256 ? fit_multi_kernel<256, D, S, MULTI_PLAIN> : fit_multi_kernel<512, D, S, MULTI_PLAIN>);
     void (*prep)(const FitParams, const MultiWs) =
         NT == 256 ? fit_prep_kernel<256, D> : fit_prep_kernel<512, D>;
     int e = set_smem_attr(kern, smem);
@@ -125,9 +125,12 @@ int launch_fit_multi_slots(const FitParams& P, const MultiWs& W, int n_running, 
     constexpr int S = FIT_LANES;
     const int p = P.M.n_pix, H = P.M.pad, nm = P.M.n_model;
     const int NT = p <= 16 * 256 ? 256 : 512;
-    const size_t smem = fit_multi_smem_bytes(p, H, nm, NT, D, P.M.K, S, true);
+    // the Clean update and the FP64 normal equations only where the options ask for them
+    const bool full = P.O.clean || P.O.fp64_ne == LASP_NE_FP64;
+    const size_t smem = fit_multi_smem_bytes(p, H, nm, NT, D, P.M.K, S, full);
     void (*kern)(const FitParams, const MultiWs) =
-        NT == 256 ? fit_multi_kernel<256, D, S, true> : fit_multi_kernel<512, D, S, true>;
+        full ? (NT == 256 ? fit_multi_kernel<256, D, S, MULTI_FULL> : fit_multi_kernel<512, D, S, MULTI_FULL>)
+             : (NT == 256 ? fit_multi_kernel<256, D, S, MULTI_SLOTS> : fit_multi_kernel<512, D, S, MULTI_SLOTS>);
     int e = set_smem_attr(kern, smem);
     if (e) return e;
     int nb = 0, dev = 0, nsm = 0;
