@@ -264,6 +264,93 @@ struct Gram {
     __device__ static constexpr int idx(int a, int b) { return a * NB - a * (a - 1) / 2 + (b - a); }
 };
 
+// Normal-equation sums of Eq. 6 with the products of one diagonal of G paired
+// into packed FMAs: entries (a, a + d) and (a + 1, a + 1 + d) share one
+// __ffma2_rn, whose operands are then (v P_a, v P_a+1) and (P_a+d, P_a+d+1),
+// both adjacent pairs of the basis.  Every sum receives the same fmas, in the
+// same order, as the scalar triangle loop; unpack() returns them in Gram<D>'s
+// packed order.  Even degrees only.
+template <int D>
+struct GramPairs {
+    static_assert(D % 2 == 0 && D >= 2, "even Legendre degree");
+    static constexpr int NB = D + 1, H2 = D / 2;
+    __host__ __device__ static constexpr int pbase(int d) {
+        int s = 0;
+        for (int q = 0; q < d; ++q) s += (NB - q) / 2;
+        return s;
+    }
+    __host__ __device__ static constexpr int sbase(int d) {
+        int s = 0;
+        for (int q = 0; q < d; ++q) s += (NB - q) & 1;
+        return s;
+    }
+    static constexpr int NPAIR = pbase(NB), NSING = sbase(NB);
+    float2 gp[NPAIR], rp[H2];
+    float gs[NSING], rs;
+
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int i = 0; i < NPAIR; ++i) gp[i] = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int i = 0; i < NSING; ++i) gs[i] = 0.0f;
+#pragma unroll
+        for (int k = 0; k < H2; ++k) rp[k] = make_float2(0.0f, 0.0f);
+        rs = 0.0f;
+    }
+
+    // one pixel: G += vv P P^T, r += uu P
+    __device__ __forceinline__ void add(float vv, float uu, const float (&Pl)[NB]) {
+        float2 pe[H2], po[H2], va[H2];
+#pragma unroll
+        for (int k = 0; k < H2; ++k) {
+            pe[k] = make_float2(Pl[2 * k], Pl[2 * k + 1]);
+            po[k] = make_float2(Pl[2 * k + 1], Pl[2 * k + 2]);
+        }
+        const float2 v2 = make_float2(vv, vv);
+#pragma unroll
+        for (int k = 0; k < H2; ++k) va[k] = __fmul2_rn(v2, pe[k]);
+        const float va_d = vv * Pl[D];
+#pragma unroll
+        for (int d = 0; d <= D; ++d) {
+            const int n = NB - d;
+#pragma unroll
+            for (int a = 0; a + 1 < n; a += 2) {
+                const float2 b2 = (d & 1) ? po[(a + d - 1) / 2] : pe[(a + d) / 2];
+                gp[pbase(d) + a / 2] = __ffma2_rn(va[a / 2], b2, gp[pbase(d) + a / 2]);
+            }
+            if (n & 1) {
+                const int a = n - 1;
+                const float v = a == D ? va_d : va[a / 2].x;
+                gs[sbase(d)] = fmaf(v, Pl[a + d], gs[sbase(d)]);
+            }
+        }
+        const float2 u2 = make_float2(uu, uu);
+#pragma unroll
+        for (int k = 0; k < H2; ++k) rp[k] = __ffma2_rn(u2, pe[k], rp[k]);
+        rs = fmaf(uu, Pl[D], rs);
+    }
+
+    __device__ __forceinline__ void unpack(float (&g)[Gram<D>::NV]) const {
+        using Gm = Gram<D>;
+#pragma unroll
+        for (int d = 0; d <= D; ++d) {
+            const int n = NB - d;
+#pragma unroll
+            for (int a = 0; a + 1 < n; a += 2) {
+                g[Gm::idx(a, a + d)] = gp[pbase(d) + a / 2].x;
+                g[Gm::idx(a + 1, a + 1 + d)] = gp[pbase(d) + a / 2].y;
+            }
+            if (n & 1) g[Gm::idx(n - 1, n - 1 + d)] = gs[sbase(d)];
+        }
+#pragma unroll
+        for (int k = 0; k < H2; ++k) {
+            g[Gm::NG + 2 * k] = rp[k].x;
+            g[Gm::NG + 2 * k + 1] = rp[k].y;
+        }
+        g[Gm::NG + D] = rs;
+    }
+};
+
 // Block-wide sum of NV floats per thread.  Partial sums per warp go to
 // red[warp * NV + i]; thread i < NV adds the warps in a fixed order, so the
 // result depends only on the data of this CTA.  out may alias nothing in red.
