@@ -42,8 +42,8 @@ FP32_LANES_PER_SM, N_SM = 128, 152
 # the current kernel source (reset to None whenever the kernel changes until it
 # is captured again): it reads the prepared y, W rows (8 B a pixel) and the
 # table, and writes the results.
-FIT_KERNEL = "fit_multi_kernel<256,6,4,false>"
-FIT_TRAFFIC_BYTES = 130_102_528 + 3_329_024
+FIT_KERNEL = "fit_multi_kernel<256,6,4,0>"
+FIT_TRAFFIC_BYTES = 130_388_736 + 6_808_576
 
 
 def parse():
