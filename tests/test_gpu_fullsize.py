@@ -56,6 +56,7 @@ def test_fp32_batch_fit_4096_sampled():
     status, err, st_gpu, st_ref = _fit_sampled("lamost4096", 32)
     assert np.all((status & 3) != 0)
     ok = np.all(err <= TOL, axis=1)
+    print(f"FP32 4096 sample: {ok.mean():.3f} within tolerance, same steps {(st_gpu == st_ref).mean():.3f}")
     assert ok.mean() >= 0.9, (ok.mean(), err.max(axis=0))
     assert (st_gpu == st_ref).mean() >= 0.8
 
@@ -67,4 +68,5 @@ def test_mixed_grouped_fit_65536_sampled():
     status, err, _, _ = _fit_sampled("mixed65536", 32, precision="tf32x3", fp64_normal_eq=1)
     assert np.mean((status & 3) != 0) >= 0.99
     ok = np.all(err <= TOL, axis=1)
+    print(f"split-TF32 65536 sample: {ok.mean():.3f} within tolerance")
     assert ok.mean() >= 0.9, (ok.mean(), err.max(axis=0))

@@ -201,6 +201,7 @@ def test_fit_early_stop_parity_lamost(lasp):
     err = np.abs(H(out["theta"]) - ref["theta"])[:, :4]
     ok = np.all(err <= TOL, axis=1)
     same_steps = H(out["steps"]) == ref["steps"]
+    print(f"LAMOST early-stop parity {ok.mean():.3f}, same steps {same_steps.mean():.3f}")
     assert ok.mean() >= 0.95, (ok.mean(), err.max(axis=0))
     assert same_steps.mean() >= 0.9
     assert np.all((H(out["status"]).astype(np.int64) & 7) != 0)
@@ -210,7 +211,9 @@ def test_fit_mixed_grid_desi_parity(lasp):
     M, d = observed(S.DESI, 24, 42, snr=(10, 100), mask_frac=0.0, mask_frac_max=0.2)
     out, ref = _fit_both(lasp, S.DESI, M, d, max_steps=300)
     err = np.abs(H(out["theta"]) - ref["theta"])[:, :4]
-    assert np.mean(np.all(err <= TOL, axis=1)) >= 0.9, err.max(axis=0)
+    ok = np.all(err <= TOL, axis=1)
+    print(f"DESI mixed-grid parity {ok.mean():.3f}")
+    assert ok.mean() >= 0.9, err.max(axis=0)
 
 
 def test_fit_edge_cases(lasp):
