@@ -318,3 +318,24 @@ def test_errors_match_oracle(lasp, grid, ne):
     assert np.allclose(cov, np.transpose(cov, (0, 2, 1)), rtol=1e-12, atol=0)
     assert np.all(np.linalg.eigvalsh(cov) > 0)
     np.testing.assert_allclose(np.sqrt(np.diagonal(cov, axis1=1, axis2=2)), sig, rtol=1e-6)
+
+
+def test_empty_batches_on_every_entry_point(lasp):
+    """N = 0 is a valid call everywhere: every compute entry point returns
+    LASP_OK with empty outputs and enqueues nothing."""
+    grid = S.SMALL
+    ip = interp(lasp, grid)
+    z = lambda *shape, dt=torch.float32: torch.zeros(shape, dtype=dt, device=DEV)
+    args = [z(0, grid.n_pix), z(0, grid.n_pix), z(0, grid.n_pix, dt=torch.uint8), z(0, 5)]
+    for opts in (dict(precision="tf32x3", fp64_normal_eq=1), dict(optimizer="lm"), dict(clean=1)):
+        out = ip.fit(*args, **opts)
+        assert out["theta"].shape == (0, 5) and lasp.load().lasp_last_launches() == 0, opts
+    e = ip.errors(*args[:3], z(0, 5))
+    assert e["sigma"].shape == (0, 5) and e["cov"].shape == (0, 5, 5)
+    assert ip.forward(z(0, 5), z(0, 7)).shape == (0, grid.n_pix)
+    gt, gb = ip.backward(z(0, 5), z(0, 7), z(0, grid.n_pix))
+    assert gt.shape == (0, 5) and gb.shape == (0, 7)
+    for prec in ("fp32", "tf32", "bf16", "tf32x3"):
+        assert ip.interp_eval(z(0, 5), prec).shape == (0, grid.n_model)
+        assert lasp.load().lasp_last_launches() == 0
+    ip.close()
