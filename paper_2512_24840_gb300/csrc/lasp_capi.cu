@@ -356,6 +356,7 @@ int lasp_fit_batch(lasp_interp h, const lasp_batch* b, const lasp_fit_opts* o, l
         L.steps = r->steps;
         L.status = r->status;
         L.weight = r->weight;
+        L.cont = r->cont_coeff;
         cudaStream_t st = (cudaStream_t)stream;
         int e = dispatch_deg(o->legendre_deg, [&](auto dd) {
             constexpr int D = decltype(dd)::value;

@@ -149,6 +149,8 @@ __global__ void __launch_bounds__(NT) k0_prep(const Grp G, const int32_t* __rest
             G.steps[i] = 0;
             G.status[i] = LASP_ST_NODATA;
             if (G.weight) G.weight[i] = w;
+            if (G.cont)
+                for (int a = 0; a < G.NB; ++a) G.cont[(size_t)i * G.NB + a] = NAN;
             G.flags[i] = -1;
         } else {
             G.flags[i] = n_obj;

@@ -35,6 +35,7 @@ struct LmParams {
     int32_t* steps;
     uint32_t* status;
     float* weight;
+    float* cont;          // N x (D+1) continuum coefficients at the result, or nullptr
 };
 
 // Shared reduction space, floats a warp: every block sum of an evaluation has
@@ -454,7 +455,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) lm_kernel(const LmParam
     float* outf = red + (NT / 32) * LM_RED_W;
     float2* outff = reinterpret_cast<float2*>(outf + ((((size_t)(outf - sm)) & 1) ? 1 : 0));
     __shared__ float2 s_G[Gram<D>::NV], s_sum[21];
-    __shared__ float s_b[D + 1], s_db[5 * (D + 1)];
+    __shared__ float s_b[D + 1], s_db[5 * (D + 1)], s_bx[D + 1];
     __shared__ float s_x[5], s_xt[5];
     __shared__ int s_h, s_ok;
     __shared__ LmCtl c;
@@ -484,6 +485,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) lm_kernel(const LmParam
             P.steps[i] = 0;
             P.status[i] = LASP_ST_NODATA;
         }
+        if (P.cont && tid <= D) P.cont[(size_t)i * (D + 1) + tid] = NAN;
         return;
     }
     for (;;) {
@@ -500,13 +502,22 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) lm_kernel(const LmParam
         else
             lm_eval<NT, D, true>(M, th, y, W, Fp, na, g, gmu, gsg, phi, dphi, red, outff, s_G, s_b, s_db,
                                  s_sum, &s_h, &s_ok);
-        if (tid == 0) lm_control(c, ph, s_ok, s_sum, s_x, s_xt, P.max_iter, (float)P.rtol);
+        if (tid == 0) {
+            const int it0 = c.it;
+            lm_control(c, ph, s_ok, s_sum, s_x, s_xt, P.max_iter, (float)P.rtol);
+            // the continuum of the current parameters: that of an evaluation at
+            // them, or of a trial the control step has just accepted
+            if (ph == LM_FULL_CUR || c.it != it0)
+                for (int a = 0; a <= D; ++a) s_bx[a] = s_b[a];
+        }
     }
     if (tid == 0) {
         for (int k = 0; k < 5; ++k) P.theta[5 * i + k] = phys_of(M, k, s_x[k]);
         P.loss[i] = sqrtf((c.S.x + c.S.y) / (float)p);
         P.steps[i] = c.it;
         P.status[i] = c.status;
+        if (P.cont)
+            for (int a = 0; a <= D; ++a) P.cont[(size_t)i * (D + 1) + a] = s_bx[a];
     }
 }
 

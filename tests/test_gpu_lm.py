@@ -45,3 +45,9 @@ def test_lm_matches_oracle_lm(grid, n):
           f"oracle {np.median(ref['steps'])}")
     assert ok.mean() >= 0.95
     np.testing.assert_allclose(out["loss"], ref["loss"], rtol=1e-4)
+    # the continuum coefficients returned are those of the result: the
+    # oracle's weighted least squares (Eq. 6) at the GPU's own parameters
+    for i in range(0, n, max(1, n // 8)):
+        y, W, _, _ = O.prep(d["flux"][i], d["ivar"][i], d["good"][i])
+        b = O.evaluate(M, y, W, O.x_from_phys(M, out["theta"][i]))["b"]
+        np.testing.assert_allclose(out["cont"][i], b, rtol=2e-3, atol=2e-4)

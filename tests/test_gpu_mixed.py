@@ -120,3 +120,24 @@ def test_mixed_desi_grid_and_max_steps(lasp):
     assert np.all(out["steps"] == 60)
     err = np.abs(out["theta"] - ref["theta"])[:, :4]
     assert np.mean(np.all(err <= TOL, axis=1)) >= 0.9
+
+
+def test_tensor_core_fit_reports_nodata_continuum_as_nan():
+    """A spectrum the preprocessing decides (too few usable pixels) ends with
+    LASP_ST_NODATA and NaN continuum coefficients on the tensor-core pipeline,
+    as on the FP32 path."""
+    from paper_2512_24840_gb300 import lasp
+    lasp.load(build=True)
+    g = S.LAMOST
+    ip = lasp.Interp.from_grid(g, table(g.name), S.EXPS, S.BASIS_LO, S.BASIS_HI, S.BOX_LO, S.BOX_HI)
+    M, d = observed(g, 6, 77, snr=(20, 100), mask_frac=0.0)
+    d["good"][2] = 0
+    T = lambda a, dt=torch.float32: torch.as_tensor(np.ascontiguousarray(a)).to(DEV, dt)
+    args = [T(d["flux"]), T(d["ivar"]), T(d["good"], torch.uint8), T(np.asarray(d["theta0"], np.float32))]
+    for prec in ("fp32", "tf32x3"):
+        out = ip.fit(*args, max_steps=200, precision=prec, fp64_normal_eq=1)
+        st = out["status"].cpu().numpy()
+        cont = out["cont"].cpu().numpy()
+        assert st[2] == lasp.ST_NODATA and np.all(np.isnan(cont[2])), prec
+        assert np.all(np.isfinite(np.delete(cont, 2, axis=0))), prec
+    ip.close()
