@@ -381,11 +381,12 @@ int lasp_fit_batch(lasp_interp h, const lasp_batch* b, const lasp_fit_opts* o, l
     P.weight = r->weight;
     cudaStream_t st = (cudaStream_t)stream;
     // several spectra per CTA (the same result as fit_kernel, bit for bit)
+    int nl = 0;
     int e = dispatch_deg(o->legendre_deg, [&](auto dd) {
         constexpr int D = decltype(dd)::value;
-        return launch_fit_multi<D>(P, st);
+        return launch_fit_multi<D>(P, st, &nl);
     });
-    g_last_launches = e ? 0 : 1;
+    g_last_launches = e ? 0 : nl;
     return e;
 }
 

@@ -13,7 +13,7 @@ namespace lasp {
 int cuda_rc(cudaError_t e);
 
 template <int D> int launch_fit(const FitParams& P, cudaStream_t st);
-template <int D> int launch_fit_multi(const FitParams& P, cudaStream_t st);
+template <int D> int launch_fit_multi(const FitParams& P, cudaStream_t st, int* n_launch = nullptr);
 template <int D> int launch_fit_multi_slots(const FitParams& P, const MultiWs& W, int n_running, cudaStream_t st);
 template <int D> int launch_fit_prep_slots(const FitParams& P, const MultiWs& W, const int32_t* idx, int count,
                                            cudaStream_t st);
@@ -67,8 +67,9 @@ int launch_fit(const FitParams& P, cudaStream_t st) {
 // for the launch.
 // Falls back to fit_kernel where the lanes' buffers or the workspace do not fit.
 template <int D>
-int launch_fit_multi(const FitParams& P, cudaStream_t st) {
+int launch_fit_multi(const FitParams& P, cudaStream_t st, int* n_launch) {
     constexpr int S = FIT_LANES;
+    if (n_launch) *n_launch = 1;             // fit_kernel alone where it falls back
     const int p = P.M.n_pix, H = P.M.pad, nm = P.M.n_model;
     const int NT = p <= 16 * 256 ? 256 : 512;
     const bool full = P.O.clean || P.O.fp64_ne == LASP_NE_FP64;
@@ -114,6 +115,7 @@ int launch_fit_multi(const FitParams& P, cudaStream_t st) {
             return cuda_rc(cudaGetLastError());
         });
     const int ef = cuda_rc(cudaFreeAsync(ws, st));
+    if (n_launch) *n_launch = 2;             // fit_prep_kernel and fit_multi_kernel
     return e ? e : ef;
 }
 
@@ -244,7 +246,7 @@ int launch_lm(const LmParams& P, cudaStream_t st) {
 
 #define LASP_INSTANTIATE(D)                                                  \
     template int launch_fit<D>(const FitParams&, cudaStream_t);             \
-    template int launch_fit_multi<D>(const FitParams&, cudaStream_t);       \
+    template int launch_fit_multi<D>(const FitParams&, cudaStream_t, int*); \
     template int launch_fit_multi_slots<D>(const FitParams&, const MultiWs&, int, cudaStream_t); \
     template int launch_fit_prep_slots<D>(const FitParams&, const MultiWs&, const int32_t*, int, cudaStream_t); \
     template int launch_errors<D>(const ErrParams&, cudaStream_t);          \

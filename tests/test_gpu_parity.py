@@ -339,3 +339,17 @@ def test_empty_batches_on_every_entry_point(lasp):
         assert ip.interp_eval(z(0, 5), prec).shape == (0, grid.n_model)
         assert lasp.load().lasp_last_launches() == 0
     ip.close()
+
+
+def test_launch_counts(lasp):
+    """lasp_last_launches counts the kernels a call enqueued: the FP32 batch
+    fit is its preprocessing kernel and the fused fit, the errors one kernel."""
+    grid = S.SMALL
+    ip = interp(lasp, grid)
+    M, d = observed(grid, 8, 45, snr=(20, 50), mask_frac=0.05)
+    args = [T(d["flux"]), T(d["ivar"]), T(d["good"], torch.uint8), T(np.asarray(d["theta0"], np.float32))]
+    out = ip.fit(*args, max_steps=50)
+    assert lasp.last_launches() == 2
+    ip.errors(*args[:3], out["theta"], with_cov=False)
+    assert lasp.last_launches() == 1
+    ip.close()
