@@ -307,8 +307,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) fit_kernel(const FitPar
     float* phi = sm + L.phi;
     float* dphi = sm + L.dphi;
     float* red = sm + L.red;
-    float* out = sm + L.out;
-    double* outd = reinterpret_cast<double*>(sm + ((L.out + 1) & ~1));
+    float* out = sm + L.out;           // even offset: 8-byte aligned for the FP64 solve
     float* ring = sm + L.ring;
     __shared__ float s_x[5], s_b[NB];
     __shared__ int s_h, s_stop, s_k[2];

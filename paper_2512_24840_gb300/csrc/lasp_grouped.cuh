@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) k2_rest(const Grp G, in
     extern __shared__ __align__(16) float sm[];
     const ModelDev& M = G.M;
     const int p = M.n_pix, H = M.pad, nm = M.n_model;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     const RestSmem L(p, H, nm, NT, D);
     float* y = sm + L.y;
     float* W = sm + L.W;
