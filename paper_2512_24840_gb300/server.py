@@ -142,6 +142,22 @@ class DevicePool:
         self.staged += 1
         return self.staged - 1
 
+    def stage_many(self, flux, ivar, good, theta0) -> int:
+        """Copy the rows of a batch of requests into the ring in order, as far
+        as it has room (caller serialises calls): one copy per array and
+        contiguous ring range.  Returns how many rows were staged; row r got
+        ring index (staged before the call) + r."""
+        n = min(len(flux), self.ring - (self.staged - self.released))
+        done = 0
+        while done < n:
+            k = (self.staged + done) % self.ring
+            m = min(n - done, self.ring - k)
+            for dst, src in zip(self.rn, (flux, ivar, good, theta0)):
+                dst[k:k + m] = src[done:done + m]
+            done += m
+        self.staged += n
+        return n
+
     def _admit_rows(self, c, idx_off, flux, ivar, good, th0):
         st = ct.c_void_p(self.stream.cuda_stream)
         rc = self.lib.lasp_slots_admit(self._h, c, self.h_idx.data_ptr() + 4 * idx_off, flux, ivar, good,
@@ -262,9 +278,29 @@ class Server:
 
     def submit_many(self, lane: str, flux, ivar, good, theta0) -> np.ndarray:
         """Submit the rows of (n, n_pix) flux, ivar, good and (n, 5) theta0 as
-        n requests in row order; returns their ids."""
-        return np.array([self.submit(lane, flux[i], ivar[i], good[i], theta0[i])
-                         for i in range(len(flux))], dtype=np.int64)
+        n requests in row order; returns their ids.  A pool with stage_many
+        copies the rows into its ring with one copy per array."""
+        ln = self.lanes[lane]
+        stage_many = getattr(ln.pool, "stage_many", None)
+        if stage_many is None:
+            return np.array([self.submit(lane, flux[i], ivar[i], good[i], theta0[i])
+                             for i in range(len(flux))], dtype=np.int64)
+        n = len(flux)
+        with self._lock:
+            rids = np.arange(self._next, self._next + n, dtype=np.int64)
+            self._next += n
+            k0 = ln.pool.staged
+            taken = stage_many(flux, ivar, good, theta0)
+            t = self.clock()
+            for r in range(n):
+                if r < taken:
+                    ln.waiting.append(Request(int(rids[r]), lane, None, None, None, None, t_submit=t,
+                                              staged=k0 + r))
+                else:      # no ring room: the request keeps copies of its rows
+                    ln.waiting.append(Request(int(rids[r]), lane, np.array(flux[r], np.float32),
+                                              np.array(ivar[r], np.float32), np.array(good[r], np.uint8),
+                                              np.array(theta0[r], np.float32), t_submit=t))
+        return rids
 
     def pending(self) -> int:
         with self._lock:

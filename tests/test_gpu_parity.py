@@ -338,7 +338,6 @@ def test_empty_batches_on_every_entry_point(lasp):
     for prec in ("fp32", "tf32", "bf16", "tf32x3"):
         assert ip.interp_eval(z(0, 5), prec).shape == (0, grid.n_model)
         assert lasp.load().lasp_last_launches() == 0
-    ip.close()
 
 
 def test_launch_counts(lasp):
@@ -352,4 +351,3 @@ def test_launch_counts(lasp):
     assert lasp.last_launches() == 2
     ip.errors(*args[:3], out["theta"], with_cov=False)
     assert lasp.last_launches() == 1
-    ip.close()

@@ -186,3 +186,32 @@ def test_native_submit_many_equals_single_submits(ring):
         assert np.array_equal(a["theta"], b["theta"]) and a["steps"] == b["steps"], k
         assert a["status"] == b["status"] and a["loss"] == b["loss"], k
     ip.close()
+
+
+@pytest.mark.parametrize("ring", [32, 5])
+def test_python_submit_many_equals_single_submits(ring):
+    """The Python scheduler's submit_many stages a batch of rows into the
+    pool's ring with one copy per array (rows without ring room keep copies
+    and are staged at admission); each result is bitwise the one of a
+    request submitted on its own."""
+    from paper_2512_24840_gb300 import lasp
+    from paper_2512_24840_gb300.server import DevicePool, Server
+    lasp.load(build=True)
+    g = S.LAMOST
+    ip = lasp.Interp.from_grid(g, table(g.name), S.EXPS, S.BASIS_LO, S.BASIS_HI, S.BOX_LO, S.BOX_HI)
+    f, iv, gd, th = _observed(g, 20, 67)
+    srv = Server({"l": DevicePool(ip, 8, max_steps=400)}, chunk=9)
+    rids = [srv.submit("l", f[i], iv[i], gd[i], th[i]) for i in range(20)]
+    one = {r.rid: r for r in srv.run_until_idle()}
+    srv.close()
+    srv = Server({"l": DevicePool(ip, 8, ring=ring, max_steps=400)}, chunk=9)
+    fb, ivb, gdb, thb = f.copy(), iv.copy(), gd.copy(), th.copy()
+    ids = srv.submit_many("l", fb, ivb, gdb, thb)
+    fb[:] = np.nan                                  # the caller's rows may be reused on return
+    many = {r.rid: r for r in srv.run_until_idle()}
+    srv.close()
+    assert len(many) == 20
+    for k in range(20):
+        a, b = one[rids[k]], many[int(ids[k])]
+        assert np.array_equal(a.theta, b.theta) and a.steps == b.steps and a.status == b.status, k
+    ip.close()
