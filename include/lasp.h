@@ -306,7 +306,7 @@ int lasp_slots_fetch(lasp_slots s, float* theta, float* loss, int32_t* steps, ui
  * and a pinned submission ring of `ring` requests.  lasp_server_submit copies
  * one request (host arrays) into its lane's ring and may be called from any
  * thread, also while another thread is inside lasp_server_tick.
- * lasp_server_tick runs one scheduling round: on every lane it admits waiting
+ * lasp_server_tick runs one scheduling tick: on every lane it admits waiting
  * requests (FIFO) into free slots, runs at most `chunk` Adam steps on the
  * running slots (the lanes' streams overlap on the GPU), fetches status and
  * results, waits for its lanes, and moves the finished fits to the result
@@ -354,9 +354,9 @@ int lasp_server_submit(lasp_server s, int lane, const float* flux, const float* 
 int lasp_server_submit_n(lasp_server s, int lane, int n, const float* flux, const float* ivar,
                          const uint8_t* good, const float* theta0, const int64_t* tags, int* n_taken);
 
-/* One scheduling round (see above); *n_finished (may be NULL) receives the
- * number of fits retired in it.  Blocks until the round's GPU work is done.
- * Returns LASP_ETIMEOUT when a fit retired in this round carries
+/* One scheduling tick (see above); *n_finished (may be NULL) receives the
+ * number of fits retired in it.  Blocks until the tick's GPU work is done.
+ * Returns LASP_ETIMEOUT when a fit retired in this tick carries
  * LASP_ST_TIMEOUT (its result is still queued, with that status). */
 int lasp_server_tick(lasp_server s, int* n_finished);
 

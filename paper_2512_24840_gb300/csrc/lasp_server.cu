@@ -298,8 +298,8 @@ int lasp_server_tick(lasp_server S, int* n_finished) {
         for (const lasp_served& r : done) S->out.push_back(r);
     }
     if (n_finished) *n_finished = fin;
-    // a bounded device wait gave up in this round: its fits are retired with
-    // LASP_ST_TIMEOUT, and the round reports it
+    // a bounded device wait gave up in this tick: its fits are retired with
+    // LASP_ST_TIMEOUT, and the tick reports it
     if (!rc && timed_out) rc = LASP_ETIMEOUT;
     return rc;
 }
