@@ -21,7 +21,7 @@
 // a quarter of fit_kernel's.  Measured on the 4096 x 3909 batch (fit_kernel:
 // 30.8 ms): four lanes at two CTAs per SM 23.6 ms, three lanes 24.1 ms, two
 // lanes at three CTAs per SM 24.6 ms (before the later refinements, which
-// brought four lanes to 21.0 ms).
+// brought four lanes to 19.3 ms).
 //
 // Three variants (MODE): the plain batch fit (MULTI_PLAIN); resumable slots
 // (MULTI_SLOTS: a lane resumes a running slot from its saved state, suspends
