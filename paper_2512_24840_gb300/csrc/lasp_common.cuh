@@ -613,21 +613,59 @@ __device__ __forceinline__ void block_sum_ff(float (&v)[NV], float* red, float2*
 // thread's value is widened to double, the warp adds by xor shuffles, thread
 // i < NV adds the warps in a fixed order.  redd: (NT/32) NV doubles; outd[i]
 // is visible to every thread after the closing barrier.
+// Warp sums in double of values 32 g .. 32 g + 31 of v (zero past NV), each
+// widened from float: lane l returns the sum of value 32 g + l.  More than
+// eight values go through a reduce-scatter (a lane sends, at each level, the
+// half of its sums that its partner keeps: 31 double additions a lane for the
+// group, where an xor butterfly per value takes five a value); fewer go
+// through one butterfly each.
+template <int NV>
+__device__ __forceinline__ double warp_sums_group_f64(const float (&v)[NV], int g) {
+    const int lane = threadIdx.x & 31;
+    if (NV - 32 * g > 8) {
+        double t[16];
+        const bool up16 = (lane & 16) != 0;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const double a = 32 * g + i < NV ? (double)v[32 * g + i] : 0.0;
+            const double b = 32 * g + i + 16 < NV ? (double)v[32 * g + i + 16] : 0.0;
+            t[i] = (up16 ? b : a) + __shfl_xor_sync(0xffffffffu, up16 ? a : b, 16);
+        }
+#pragma unroll
+        for (int w = 8; w >= 1; w >>= 1) {
+            const bool up = (lane & w) != 0;
+#pragma unroll
+            for (int i = 0; i < w; ++i) {
+                const double send = up ? t[i] : t[i + w];
+                const double keep = up ? t[i + w] : t[i];
+                t[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+            }
+        }
+        return t[0];
+    }
+    double mine = 0.0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        if (32 * g + i < NV) {
+            double x = (double)v[32 * g + i];
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == i) mine = x;
+        }
+    return mine;
+}
+
 template <int NV, int NT>
 __device__ __forceinline__ void block_sum_f64(const float (&v)[NV], double* redd, double* outd) {
+    constexpr int NP = (NV + 31) / 32 * 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int i = 0; i < NV; ++i) {
-        double s = (double)v[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) redd[warp * NV + i] = s;
-    }
+    for (int g = 0; g < NP / 32; ++g) redd[warp * NP + 32 * g + lane] = warp_sums_group_f64<NV>(v, g);
     __syncthreads();
     if (threadIdx.x < NV) {
         double s = 0.0;
 #pragma unroll
-        for (int w = 0; w < NT / 32; ++w) s += redd[w * NV + threadIdx.x];
+        for (int w = 0; w < NT / 32; ++w) s += redd[w * NP + threadIdx.x];
         outd[threadIdx.x] = s;
     }
     __syncthreads();

@@ -186,25 +186,21 @@ __device__ __forceinline__ void reduce_to_warp0_ff(float (&v)[NV], float* red, f
 }
 
 // As reduce_to_warp0 with every partial sum in FP64: each thread's FP32 sum
-// over its own pixels is widened to double, the warp adds by xor shuffles in
-// double and warp 0 adds the warps in double.  redd: (NT/32) NV doubles;
+// over its own pixels is widened to double, the warp reduce-scatters in double
+// and warp 0 adds the warps in double.  redd: (NT/32) round32(NV) doubles;
 // outd[i] is visible to warp 0 on return.
 template <int NV, int NT>
 __device__ __forceinline__ void reduce_to_warp0_f64(const float (&v)[NV], double* redd, double* outd) {
+    constexpr int NP = round32(NV);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int i = 0; i < NV; ++i) {
-        double s = (double)v[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) redd[warp * NV + i] = s;
-    }
+    for (int g = 0; g < NP / 32; ++g) redd[warp * NP + 32 * g + lane] = warp_sums_group_f64<NV>(v, g);
     __syncthreads();
     if (warp == 0) {
         for (int i = lane; i < NV; i += 32) {
             double s = 0.0;
 #pragma unroll
-            for (int w = 0; w < NT / 32; ++w) s += redd[w * NV + i];
+            for (int w = 0; w < NT / 32; ++w) s += redd[w * NP + i];
             outd[i] = s;
         }
         __syncwarp();
