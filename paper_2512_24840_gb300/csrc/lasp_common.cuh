@@ -586,33 +586,68 @@ __device__ __forceinline__ bool warp_chol_solve_ff(const float2* packed, const f
     return true;
 }
 
-// Block-wide sum of NV floats per thread: FP32 within each warp, the warps
-// added in float-float (exact two-sums) by thread i < NV; out[i] = (hi, lo),
+// Warp reduce-scatter of 32 values (butterfly transpose): afterwards v[0] of
+// lane l holds the warp sum of value l.  31 shuffles instead of 5 x 32.
+__device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const bool up = (lane & w) != 0;
+#pragma unroll
+        for (int i = 0; i < w; ++i) {
+            const float send = up ? v[i] : v[i + w];
+            const float keep = up ? v[i + w] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+        }
+    }
+    return v[0];
+}
+
+// Warp sums of values 32 g .. 32 g + 31 of v (zero past NV): lane l returns the
+// warp sum of value 32 g + l.  Eight values or fewer go through xor butterflies
+// with the levels in the scatter's order (16, 8, 4, 2, 1), which pair the same
+// lanes at every level, so the sums are bitwise those of the scatter.
+template <int NV>
+__device__ __forceinline__ float warp_sums_group(const float (&v)[NV], int g) {
+    const int lane = threadIdx.x & 31;
+    if (NV - 32 * g > 8) {
+        float t[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) t[i] = (32 * g + i < NV) ? v[32 * g + i] : 0.0f;
+        return warp_reduce_scatter32(t);
+    }
+    float mine = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        if (32 * g + i < NV) {
+            float s = v[32 * g + i];
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == i) mine = s;
+        }
+    return mine;
+}
+
+// Block-wide sum of NV floats per thread: FP32 within each warp (a
+// reduce-scatter), the warps added in float-float (exact two-sums) by thread
+// i < NV; red: (NT/32) round32(NV) floats; out[i] = (hi, lo),
 // visible to every thread after the closing barrier.
 template <int NV, int NT>
 __device__ __forceinline__ void block_sum_ff(float (&v)[NV], float* red, float2* out) {
+    constexpr int NP = (NV + 31) / 32 * 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int i = 0; i < NV; ++i) {
-        float s = v[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) red[warp * NV + i] = s;
-    }
+    for (int g = 0; g < NP / 32; ++g) red[warp * NP + 32 * g + lane] = warp_sums_group<NV>(v, g);
     __syncthreads();
     if (threadIdx.x < NV) {
         float2 s = make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int w = 0; w < NT / 32; ++w) s = ff_add(s, red[w * NV + threadIdx.x]);
+        for (int w = 0; w < NT / 32; ++w) s = ff_add(s, red[w * NP + threadIdx.x]);
         out[threadIdx.x] = s;
     }
     __syncthreads();
 }
 
-// Block-wide sum of NV floats per thread with every addition in FP64: each
-// thread's value is widened to double, the warp adds by xor shuffles, thread
-// i < NV adds the warps in a fixed order.  redd: (NT/32) NV doubles; outd[i]
-// is visible to every thread after the closing barrier.
 // Warp sums in double of values 32 g .. 32 g + 31 of v (zero past NV), each
 // widened from float: lane l returns the sum of value 32 g + l.  More than
 // eight values go through a reduce-scatter (a lane sends, at each level, the
@@ -655,6 +690,10 @@ __device__ __forceinline__ double warp_sums_group_f64(const float (&v)[NV], int 
     return mine;
 }
 
+// Block-wide sum of NV floats per thread with every addition in FP64: each
+// thread's value is widened to double, the warp reduce-scatters in double,
+// thread i < NV adds the warps in a fixed order.  redd: (NT/32) round32(NV)
+// doubles; outd[i] is visible to every thread after the closing barrier.
 template <int NV, int NT>
 __device__ __forceinline__ void block_sum_f64(const float (&v)[NV], double* redd, double* outd) {
     constexpr int NP = (NV + 31) / 32 * 32;

@@ -96,48 +96,6 @@ __host__ inline size_t fit_smem_bytes(int p, int H, int n_model, int NT, int D, 
     return 4 * ((size_t)s.total > sort_end ? (size_t)s.total : sort_end);
 }
 
-// Warp reduce-scatter of 32 values (butterfly transpose): afterwards v[0] of
-// lane l holds the warp sum of value l.  31 shuffles instead of 5 x 32.
-__device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32]) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int w = 16; w >= 1; w >>= 1) {
-        const bool up = (lane & w) != 0;
-#pragma unroll
-        for (int i = 0; i < w; ++i) {
-            const float send = up ? v[i] : v[i + w];
-            const float keep = up ? v[i + w] : v[i];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
-        }
-    }
-    return v[0];
-}
-
-// Warp sums of values 32 g .. 32 g + 31 of v (zero past NV): lane l returns the
-// warp sum of value 32 g + l.  Eight values or fewer go through xor butterflies
-// with the levels in the scatter's order (16, 8, 4, 2, 1), which pair the same
-// lanes at every level, so the sums are bitwise those of the scatter.
-template <int NV>
-__device__ __forceinline__ float warp_sums_group(const float (&v)[NV], int g) {
-    const int lane = threadIdx.x & 31;
-    if (NV - 32 * g > 8) {
-        float t[32];
-#pragma unroll
-        for (int i = 0; i < 32; ++i) t[i] = (32 * g + i < NV) ? v[32 * g + i] : 0.0f;
-        return warp_reduce_scatter32(t);
-    }
-    float mine = 0.0f;
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-        if (32 * g + i < NV) {
-            float s = v[32 * g + i];
-#pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == i) mine = s;
-        }
-    return mine;
-}
-
 // Reduce NV per-thread values over the CTA; the sums end in out[0..NV) and
 // are visible to warp 0 only (after __syncwarp), with one CTA barrier.  Each
 // warp reduce-scatters groups of 32 values, then warp 0 adds the warps in a
