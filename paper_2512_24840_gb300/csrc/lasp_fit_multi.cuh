@@ -181,6 +181,36 @@ __global__ void __launch_bounds__(NT) fit_prep_slots_kernel(const FitParams P, c
     if (nodata && P.cont && tid < NB) P.cont[(size_t)i * NB + tid] = NAN;
 }
 
+// Order in which the batch fit takes the spectra of a piecewise interpolator:
+// grouped by the Teff segment (a regime alone, or the blend of two) of their
+// starting parameters, so that a CTA's four lanes tend to need the same table
+// rows and its table passes run over fewer of them.  A counting sort: segment
+// and count per spectrum, offsets (one thread; it also sets the list length
+// next[1] = N), scatter.  Each spectrum's fit does not depend on the order.
+static __global__ void regime_count_kernel(const ModelDev M, int N, const float* __restrict__ theta0,
+                                           int* __restrict__ seg, int* __restrict__ count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float x = fminf(1.0f, fmaxf(-1.0f, (theta0[5 * i] - M.plo[0]) / M.phalf[0] - 1.0f));
+    const int s = teff_segment(M, phys_of(M, 0, x));
+    seg[i] = s;
+    atomicAdd(&count[s], 1);
+}
+static __global__ void regime_offsets_kernel(int N, int n_seg, int* count, int* next) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int o = 0;
+    for (int s = 0; s < n_seg; ++s) {
+        const int c = count[s];
+        count[s] = o;
+        o += c;
+    }
+    next[1] = N;
+}
+static __global__ void regime_scatter_kernel(int N, const int* __restrict__ seg, int* count, int* order) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) order[atomicAdd(&count[seg[i]], 1)] = i;
+}
+
 template <int NT, int S>
 __host__ __device__ constexpr int multi_min_blocks() {
     return NT == 256 ? (S <= 2 ? 3 : 2) : 1;

@@ -96,16 +96,31 @@ int launch_fit_multi(const FitParams& P, cudaStream_t st, int* n_launch) {
     W.ldw = (p + 15) & ~15;
     const size_t rows = (size_t)P.N * 2 * W.ldw * sizeof(float);
     const size_t wq = ((size_t)P.N * sizeof(float) + 255) & ~(size_t)255;   // w, then the mean ivar
+    const bool order = P.M.n_reg > 1;                  // piecewise: spectra taken grouped by regime
+    const size_t ob = order ? 2 * wq : 0;              // segment and order, N ints each
     void* ws = nullptr;
-    if (cudaMallocAsync(&ws, 256 + 2 * wq + rows, st) != cudaSuccess) {
+    if (cudaMallocAsync(&ws, 256 + 2 * wq + ob + rows, st) != cudaSuccess) {
         cudaGetLastError();
         return launch_fit<D>(P, st);          // no room for the workspace: one spectrum per CTA
     }
     W.next = static_cast<int*>(ws);
     W.wq = reinterpret_cast<float*>(static_cast<char*>(ws) + 256);
     W.im = reinterpret_cast<float*>(static_cast<char*>(ws) + 256 + wq);
-    W.yw = reinterpret_cast<float*>(static_cast<char*>(ws) + 256 + 2 * wq);
+    W.yw = reinterpret_cast<float*>(static_cast<char*>(ws) + 256 + 2 * wq + ob);
     e = cuda_rc(cudaMemsetAsync(ws, 0, 256, st));
+    if (!e && order) {
+        int* seg = reinterpret_cast<int*>(static_cast<char*>(ws) + 256 + 2 * wq);
+        int* ord = reinterpret_cast<int*>(static_cast<char*>(ws) + 256 + 3 * wq);
+        int* count = W.next + 16;                      // 2 NREG - 1 counters in the zeroed header
+        const int nb256 = (P.N + 255) / 256;
+        e = prof_time("regime_order_kernels", st, [&]() {
+            regime_count_kernel<<<nb256, 256, 0, st>>>(P.M, P.N, P.theta0, seg, count);
+            regime_offsets_kernel<<<1, 32, 0, st>>>(P.N, 2 * P.M.n_reg - 1, count, W.next);
+            regime_scatter_kernel<<<nb256, 256, 0, st>>>(P.N, seg, count, ord);
+            return cuda_rc(cudaGetLastError());
+        });
+        W.list = ord;
+    }
     if (!e) e = prof_time("fit_prep_kernel", st, [&]() {
             prep<<<P.N, NT, smem_prep, st>>>(P, W);
             return cuda_rc(cudaGetLastError());
@@ -115,7 +130,7 @@ int launch_fit_multi(const FitParams& P, cudaStream_t st, int* n_launch) {
             return cuda_rc(cudaGetLastError());
         });
     const int ef = cuda_rc(cudaFreeAsync(ws, st));
-    if (n_launch) *n_launch = 2;             // fit_prep_kernel and fit_multi_kernel
+    if (n_launch) *n_launch = order ? 5 : 2;  // (the regime order,) fit_prep_kernel, fit_multi_kernel
     return e ? e : ef;
 }
 

@@ -190,3 +190,17 @@ def test_one_regime_piecewise_handle_equals_plain_handle(lasp):
     a = plain.fit(*args, max_steps=300)
     b = one.fit(*args, max_steps=300)
     assert torch.equal(a["theta"], b["theta"]) and torch.equal(a["steps"], b["steps"])
+
+
+def test_fit_results_do_not_depend_on_batch_order(lasp):
+    """The batch fit takes a piecewise batch's spectra grouped by the Teff
+    range of their starting parameters; each spectrum's result is bitwise the
+    same whatever the order of the batch (here reversed and shuffled)."""
+    M, d = _inputs(S.LAMOST, 200, 64, snr=(5, 100), mask_frac=0.05)
+    base = _gpu(lasp, S.LAMOST, d, max_steps=300)
+    for perm in (np.arange(200)[::-1], np.random.default_rng(5).permutation(200)):
+        dp = {k: (v[perm] if isinstance(v, np.ndarray) and v.shape[:1] == (200,) else v) for k, v in d.items()}
+        out = _gpu(lasp, S.LAMOST, dp, max_steps=300)
+        for k in ("theta", "loss", "steps", "status", "cont"):
+            assert np.array_equal(out[k], base[k][perm], equal_nan=True), k
+    assert lasp.last_launches() == 5        # the regime order, the preprocessing and the fit
