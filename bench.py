@@ -218,10 +218,10 @@ def kernel_rooflines(torch, lasp, ip, g_in, grid, theta_np, steps_np, pk, alu_pe
         row("errors_kernel", prof, "alu", err_flops(th, grid), "stage-9 FLOPs per spectrum, summed")
         row("errors_kernel<fp64>", prof, "alu", err_flops(th, grid),
             "as errors_kernel; sums across the CTA and the 7x7 solves in FP64")
-        # the FULL variant (Clean masking, slots, FP64 normal equations compiled in) with Clean on
+        # the Clean variant of the fused fit (the Clean update compiled in), Clean on
         oc = ip.fit(*g_in, clean=1, **opts)
         prof = lasp.profile_read()
-        row("fit_multi_kernel<full>", prof, "alu",
+        row("fit_multi_kernel<clean>", prof, "alu",
             algorithmic_flops(oc["theta"].double().cpu().numpy(), oc["steps"].cpu().numpy(), grid),
             "the fused step's FLOPs (Clean updates not counted), Clean on")
         lo = dict(max_steps=100, tol=1e-10, legendre_deg=DEG, optimizer="lm")

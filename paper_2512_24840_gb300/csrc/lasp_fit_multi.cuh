@@ -23,12 +23,13 @@
 // lanes at three CTAs per SM 24.6 ms (before the later refinements, which
 // brought four lanes to 19.3 ms).
 //
-// Three variants (MODE): the plain batch fit (MULTI_PLAIN); resumable slots
-// (MULTI_SLOTS: a lane resumes a running slot from its saved state, suspends
-// it after the step budget, and takes the next one from a list of running
-// slots); and MULTI_FULL, resumable slots plus the Clean update (stage 6; a
-// lane's mask lives in its W row) and the FP64 normal equations.  Each
-// variant compiles only what it runs, so the lighter ones spill less.
+// Four variants (MODE): the plain batch fit (MULTI_PLAIN); the batch fit with
+// the Clean update (MULTI_CLEAN; stage 6, a lane's mask lives in its W row);
+// resumable slots (MULTI_SLOTS: a lane resumes a running slot from its saved
+// state, suspends it after the step budget, and takes the next one from a
+// list of running slots); and MULTI_FULL, resumable slots plus the Clean
+// update and the FP64 normal equations.  Each variant compiles only what it
+// runs, so the lighter ones spill less.
 #pragma once
 
 #include "lasp_clean.cuh"
@@ -216,7 +217,7 @@ __host__ __device__ constexpr int multi_min_blocks() {
     return NT == 256 ? (S <= 2 ? 3 : 2) : 1;
 }
 
-constexpr int MULTI_PLAIN = 0, MULTI_FULL = 1, MULTI_SLOTS = 2;
+constexpr int MULTI_PLAIN = 0, MULTI_FULL = 1, MULTI_SLOTS = 2, MULTI_CLEAN = 3;
 
 template <int NT, int D, int S, int MODE>
 __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kernel(const FitParams P,
@@ -230,6 +231,7 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
     const int p = M.n_pix, H = M.pad, nm = M.n_model;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr bool FULL = MODE == MULTI_FULL;
+    constexpr bool CLEAN = FULL || MODE == MULTI_CLEAN;      // the Clean update compiled in
     const MultiSmem L(p, H, nm, NT, D, M.K, S, FULL);
     float* red = sm + L.red;
     float* out = sm + L.out;
@@ -244,7 +246,7 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
     double b1t = 1.0, b2t = 1.0;
     // resumable slots (P.S.x set): a lane takes running slots, resumes each from
     // its saved state and suspends it after P.S.budget steps
-    const bool slots = MODE != MULTI_PLAIN && P.S.x != nullptr;
+    const bool slots = (MODE == MULTI_FULL || MODE == MULTI_SLOTS) && P.S.x != nullptr;
 
     if (tid < S) {
         s_i[tid] = -1;
@@ -684,7 +686,7 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
                     }
                     for (int q = lane; q < WINMAX; q += 32) P.S.ring[(size_t)i * WINMAX + q] = ring[q];
                 }
-                if (FULL && clean_step(P.O, t)) {
+                if (CLEAN && clean_step(P.O, t)) {
                     // the Clean update below needs the basis and taps of x_t
                     if (lane == 0) s_cln[s] = t;
                 } else {
@@ -701,7 +703,7 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
         // from the residual at x_t (the code of fit_kernel's update).  The lane's
         // F' of x_t was overwritten by its delta, so one table pass recomputes
         // it; two other lanes' buffers, free between steps, hold r and m.
-        if constexpr (FULL && S >= 3) {
+        if constexpr (CLEAN && S >= 3) {
             if (P.O.clean) {
 #pragma unroll 1
                 for (int s = 0; s < S; ++s) {

@@ -77,9 +77,12 @@ int launch_fit_multi(const FitParams& P, cudaStream_t st, int* n_launch) {
     const size_t smem_prep = 4 * (size_t)fit_prep_smem_floats(p);
     // resumable slots, and Clean with too few lanes for its scratch, stay on fit_kernel
     if (P.S.x || (P.O.clean && S < 3) || smem > 227 * 1024 || smem_prep > 227 * 1024) return launch_fit<D>(P, st);
+    // the Clean batch fit on its own variant unless the FP64 normal equations need the full one
+    const int mode = P.O.fp64_ne == LASP_NE_FP64 ? MULTI_FULL : P.O.clean ? MULTI_CLEAN : MULTI_PLAIN;
     void (*kern)(const FitParams, const MultiWs) =
-        full ? (NT == 256 ? fit_multi_kernel<256, D, S, MULTI_FULL> : fit_multi_kernel<512, D, S, MULTI_FULL>)
-             : (NT == 256 ? fit_multi_kernel<256, D, S, MULTI_PLAIN> : fit_multi_kernel<512, D, S, MULTI_PLAIN>);
+        mode == MULTI_FULL  ? (NT == 256 ? fit_multi_kernel<256, D, S, MULTI_FULL> : fit_multi_kernel<512, D, S, MULTI_FULL>)
+        : mode == MULTI_CLEAN ? (NT == 256 ? fit_multi_kernel<256, D, S, MULTI_CLEAN> : fit_multi_kernel<512, D, S, MULTI_CLEAN>)
+                              : (NT == 256 ? fit_multi_kernel<256, D, S, MULTI_PLAIN> : fit_multi_kernel<512, D, S, MULTI_PLAIN>);
     void (*prep)(const FitParams, const MultiWs) =
         NT == 256 ? fit_prep_kernel<256, D> : fit_prep_kernel<512, D>;
     int e = set_smem_attr(kern, smem);
@@ -125,7 +128,9 @@ int launch_fit_multi(const FitParams& P, cudaStream_t st, int* n_launch) {
             prep<<<P.N, NT, smem_prep, st>>>(P, W);
             return cuda_rc(cudaGetLastError());
         });
-    if (!e) e = prof_time(full ? "fit_multi_kernel<full>" : "fit_multi_kernel", st, [&]() {
+    const char* name = mode == MULTI_FULL ? "fit_multi_kernel<full>"
+                       : mode == MULTI_CLEAN ? "fit_multi_kernel<clean>" : "fit_multi_kernel";
+    if (!e) e = prof_time(name, st, [&]() {
             kern<<<grid, NT, smem, st>>>(P, W);
             return cuda_rc(cudaGetLastError());
         });

@@ -30,7 +30,7 @@ def test_profile_times_each_kernel_and_changes_nothing(lasp):
     T = lambda a, dt=torch.float32: torch.as_tensor(np.ascontiguousarray(a)).to(DEV, dt)
     args = [T(d["flux"]), T(d["ivar"]), T(d["good"], torch.uint8), T(np.asarray(d["theta0"], np.float32))]
     forms = [dict(max_steps=300), dict(max_steps=300, precision="tf32x3", fp64_normal_eq=1),
-             dict(max_steps=300, fp64_normal_eq=2)]
+             dict(max_steps=300, fp64_normal_eq=2), dict(max_steps=300, clean=1)]
     plain = [ip.fit(*args, **o) for o in forms]
     e_plain = ip.errors(*args[:3], plain[0]["theta"], with_cov=False)
     lasp.profile(True)
@@ -45,7 +45,8 @@ def test_profile_times_each_kernel_and_changes_nothing(lasp):
         assert torch.equal(a["theta"], b["theta"]) and torch.equal(a["status"], b["status"])
         assert torch.equal(a["steps"], b["steps"])
     assert torch.equal(e_plain["sigma"], e_prof["sigma"])
-    for name in ("fit_prep_kernel", "fit_multi_kernel", "fit_multi_kernel<full>", "errors_kernel",
+    for name in ("fit_prep_kernel", "fit_multi_kernel", "fit_multi_kernel<full>", "fit_multi_kernel<clean>",
+                 "errors_kernel",
                  "k0_prep", "k1_interp", "k2_rest", "k3_back", "k4_adam"):
         assert name in times, (name, sorted(times))
         launches, ms = times[name]
