@@ -23,8 +23,9 @@
 // lanes at three CTAs per SM 24.6 ms (before the later refinements, which
 // brought four lanes to 19.3 ms).
 //
-// Four variants (MODE): the plain batch fit (MULTI_PLAIN); the batch fit with
-// the Clean update (MULTI_CLEAN; stage 6, a lane's mask lives in its W row);
+// Five variants (MODE): the plain batch fit (MULTI_PLAIN); the batch fit with
+// the Clean update (MULTI_CLEAN; stage 6, a lane's mask lives in its W row) or
+// with the FP64 normal equations (MULTI_NE64);
 // resumable slots (MULTI_SLOTS: a lane resumes a running slot from its saved
 // state, suspends it after the step budget, and takes the next one from a
 // list of running slots); and MULTI_FULL, resumable slots plus the Clean
@@ -217,7 +218,7 @@ __host__ __device__ constexpr int multi_min_blocks() {
     return NT == 256 ? (S <= 2 ? 3 : 2) : 1;
 }
 
-constexpr int MULTI_PLAIN = 0, MULTI_FULL = 1, MULTI_SLOTS = 2, MULTI_CLEAN = 3;
+constexpr int MULTI_PLAIN = 0, MULTI_FULL = 1, MULTI_SLOTS = 2, MULTI_CLEAN = 3, MULTI_NE64 = 4;
 
 template <int NT, int D, int S, int MODE>
 __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kernel(const FitParams P,
@@ -232,7 +233,8 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr bool FULL = MODE == MULTI_FULL;
     constexpr bool CLEAN = FULL || MODE == MULTI_CLEAN;      // the Clean update compiled in
-    const MultiSmem L(p, H, nm, NT, D, M.K, S, FULL);
+    constexpr bool NE64 = FULL || MODE == MULTI_NE64;        // the FP64 normal equations compiled in
+    const MultiSmem L(p, H, nm, NT, D, M.K, S, NE64);
     float* red = sm + L.red;
     float* out = sm + L.out;
     __shared__ float s_x[S][5], s_b[S][NB], s_w[S];
@@ -453,7 +455,7 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
                     }
                 }
             }
-            solve_continuum<D, NT, FULL>(gacc, P.O.fp64_ne, red, out, s_b[s]);
+            solve_continuum<D, NT, NE64>(gacc, P.O.fp64_ne, red, out, s_b[s]);
 
             // a6: residual (Eq. 7), loss (Eq. 9); delta = W eps c (unscaled)
             float racc[2] = {0.0f, 0.0f};

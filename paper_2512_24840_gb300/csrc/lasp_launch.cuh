@@ -77,10 +77,12 @@ int launch_fit_multi(const FitParams& P, cudaStream_t st, int* n_launch) {
     const size_t smem_prep = 4 * (size_t)fit_prep_smem_floats(p);
     // resumable slots, and Clean with too few lanes for its scratch, stay on fit_kernel
     if (P.S.x || (P.O.clean && S < 3) || smem > 227 * 1024 || smem_prep > 227 * 1024) return launch_fit<D>(P, st);
-    // the Clean batch fit on its own variant unless the FP64 normal equations need the full one
-    const int mode = P.O.fp64_ne == LASP_NE_FP64 ? MULTI_FULL : P.O.clean ? MULTI_CLEAN : MULTI_PLAIN;
+    // Clean and the FP64 normal equations each on their own variant, both on the full one
+    const bool ne64 = P.O.fp64_ne == LASP_NE_FP64;
+    const int mode = ne64 ? (P.O.clean ? MULTI_FULL : MULTI_NE64) : P.O.clean ? MULTI_CLEAN : MULTI_PLAIN;
     void (*kern)(const FitParams, const MultiWs) =
-        mode == MULTI_FULL  ? (NT == 256 ? fit_multi_kernel<256, D, S, MULTI_FULL> : fit_multi_kernel<512, D, S, MULTI_FULL>)
+        mode == MULTI_FULL    ? (NT == 256 ? fit_multi_kernel<256, D, S, MULTI_FULL> : fit_multi_kernel<512, D, S, MULTI_FULL>)
+        : mode == MULTI_NE64  ? (NT == 256 ? fit_multi_kernel<256, D, S, MULTI_NE64> : fit_multi_kernel<512, D, S, MULTI_NE64>)
         : mode == MULTI_CLEAN ? (NT == 256 ? fit_multi_kernel<256, D, S, MULTI_CLEAN> : fit_multi_kernel<512, D, S, MULTI_CLEAN>)
                               : (NT == 256 ? fit_multi_kernel<256, D, S, MULTI_PLAIN> : fit_multi_kernel<512, D, S, MULTI_PLAIN>);
     void (*prep)(const FitParams, const MultiWs) =
@@ -128,7 +130,8 @@ int launch_fit_multi(const FitParams& P, cudaStream_t st, int* n_launch) {
             prep<<<P.N, NT, smem_prep, st>>>(P, W);
             return cuda_rc(cudaGetLastError());
         });
-    const char* name = mode == MULTI_FULL ? "fit_multi_kernel<full>"
+    const char* name = mode == MULTI_FULL    ? "fit_multi_kernel<full>"
+                       : mode == MULTI_NE64  ? "fit_multi_kernel<ne64>"
                        : mode == MULTI_CLEAN ? "fit_multi_kernel<clean>" : "fit_multi_kernel";
     if (!e) e = prof_time(name, st, [&]() {
             kern<<<grid, NT, smem, st>>>(P, W);

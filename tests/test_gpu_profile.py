@@ -45,7 +45,7 @@ def test_profile_times_each_kernel_and_changes_nothing(lasp):
         assert torch.equal(a["theta"], b["theta"]) and torch.equal(a["status"], b["status"])
         assert torch.equal(a["steps"], b["steps"])
     assert torch.equal(e_plain["sigma"], e_prof["sigma"])
-    for name in ("fit_prep_kernel", "fit_multi_kernel", "fit_multi_kernel<full>", "fit_multi_kernel<clean>",
+    for name in ("fit_prep_kernel", "fit_multi_kernel", "fit_multi_kernel<ne64>", "fit_multi_kernel<clean>",
                  "errors_kernel",
                  "k0_prep", "k1_interp", "k2_rest", "k3_back", "k4_adam"):
         assert name in times, (name, sorted(times))
