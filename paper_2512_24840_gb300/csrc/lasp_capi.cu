@@ -576,7 +576,7 @@ void lasp_slots_free(lasp_slots s) {
     if (!s) return;
     if (s->grp) grp_pool_free(s->grp);
     void* ptrs[] = {s->flux, s->ivar, s->theta0, s->good, s->f_st, s->iv_st, s->th_st, s->g_st,
-                    s->idx_st, s->S.x, s->S.m, s->S.v, s->S.ring, s->S.prev, s->S.rise, s->S.t,
+                    s->idx_st, s->S.x, s->S.m, s->S.v, s->S.ring, s->S.prev, s->S.rise, s->S.t, s->S.b12,
                     s->S.w, s->S.imean, s->S.cmask, s->theta, s->loss, s->cont, s->weight, s->steps,
                     s->status, s->yw, s->ctr, s->list};
     for (void* p : ptrs)
@@ -619,6 +619,7 @@ int lasp_slots_create(lasp_interp h, int n_slots, const lasp_fit_opts* o, lasp_s
     alloc(&s->S.prev, n * 4);
     alloc(&s->S.rise, n * 4);
     alloc(&s->S.t, n * 4);
+    alloc(&s->S.b12, n * 2 * 8);
     alloc(&s->S.w, n * 4);
     alloc(&s->S.imean, n * 4);
     const lasp::ModelDev& M = h->M;

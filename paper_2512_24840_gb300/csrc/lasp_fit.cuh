@@ -39,6 +39,7 @@ struct SlotState {
     float* prev;       // S
     int* rise;         // S
     int* t;            // S
+    double* b12;       // S x 2: beta1^t, beta2^t (the running products of the bias corrections)
     float* w;          // S  (weight, set at the first launch)
     float* imean;      // S  (mean inverse variance)
     uint16_t* cmask;   // S x ceil(p / 16) zero-weight bits of each thread's 16 pixels (Clean), or nullptr
@@ -334,9 +335,9 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) fit_kernel(const FitPar
     int rise = 0, ri = t0 % P.O.window;   // ring slot of step t
     double b1t = 1.0, b2t = 1.0;
     if (warp == 0) {
-        if (t0 > 0) {
-            b1t = pow((double)P.O.beta1, (double)t0);
-            b2t = pow((double)P.O.beta2, (double)t0);
+        if (t0 > 0) {                       // the products saved with the slot, exactly
+            b1t = P.S.b12[2 * i];
+            b2t = P.S.b12[2 * i + 1];
         }
         if (lane < 5) {
             if (fresh) {
@@ -624,6 +625,8 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) fit_kernel(const FitPar
                         P.S.prev[i] = prev;
                         P.S.rise[i] = rise;
                         P.S.t[i] = t + 1;
+                        P.S.b12[2 * i] = b1t;
+                        P.S.b12[2 * i + 1] = b2t;
                     }
                     stop = 2;
                 }

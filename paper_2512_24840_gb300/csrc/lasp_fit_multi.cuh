@@ -297,8 +297,8 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
                         ri = t0 % P.O.window;
                         prev = P.S.prev[i];
                         rise = P.S.rise[i];
-                        b1t = t0 > 0 ? pow((double)P.O.beta1, (double)t0) : 1.0;
-                        b2t = t0 > 0 ? pow((double)P.O.beta2, (double)t0) : 1.0;
+                        b1t = t0 > 0 ? P.S.b12[2 * i] : 1.0;        // saved with the slot, exactly
+                        b2t = t0 > 0 ? P.S.b12[2 * i + 1] : 1.0;
                         if (lane < 5) {
                             xk = P.S.x[5 * i + lane];
                             mk = P.S.m[5 * i + lane];
@@ -684,6 +684,8 @@ __global__ void __launch_bounds__(NT, multi_min_blocks<NT, S>()) fit_multi_kerne
                         P.S.prev[i] = prev;
                         P.S.rise[i] = rise;
                         P.S.t[i] = t + 1;
+                        P.S.b12[2 * i] = b1t;
+                        P.S.b12[2 * i + 1] = b2t;
                         s_need[s] = 1;
                     }
                     for (int q = lane; q < WINMAX; q += 32) P.S.ring[(size_t)i * WINMAX + q] = ring[q];
