@@ -62,7 +62,7 @@ def test_fp32_batch_fit_4096_sampled():
 
 
 def test_mixed_grouped_fit_65536_sampled():
-    """configs[3]'s size on the grouped tensor-core pipeline as the bench runs
+    """The 65536 x 3909 mixed-precision batch on the grouped tensor-core pipeline as the bench runs
     it: a 32-spectrum sample agrees with the oracle within the parameter
     tolerances (the bench's 512-spectrum sample: 99.6%)."""
     status, err, _, _ = _fit_sampled("mixed65536", 32, precision="tf32x3", fp64_normal_eq=1)
