@@ -15,6 +15,17 @@ from oracle import oracle as O
 DEG = 6
 TOL = np.array([1.0, 0.005, 0.005, 0.1])          # Teff K, logg, [Fe/H], RV km/s
 
+# Gradient parity of the FP32 adjoint against the FP64 oracle.  A gradient
+# component is a sum over the pixels (through dF' and the table contraction)
+# added in FP32 in blocks: 16 pixels a thread, then a tree over the threads,
+# about 30 roundings on any path, so its error is at most about 30 u sum|terms|
+# (u = 2^-24).  With random-sign cotangents, as in the tests, sum|terms| / |sum|
+# is about sqrt(p), 63 at 3909 pixels: 30 x 6e-8 x 63 = 1.1e-4.  Bounds: theta
+# 2e-4 of |g| + 1e-3 max|g| (the floor for components that cancel to near
+# zero); Legendre coefficients 1e-4 of max|g|.
+GRAD_RTOL_THETA = 2e-4
+GRAD_TOL_LEG = 1e-4
+
 
 def oracle_model(grid, C=None, deg=DEG) -> O.Model:
     if C is None:

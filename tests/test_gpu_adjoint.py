@@ -7,7 +7,7 @@ import pytest
 
 import lasp_synth as S
 from oracle import oracle as O
-from tests.helpers import DEG, oracle_model, table
+from tests.helpers import DEG, GRAD_RTOL_THETA, GRAD_TOL_LEG, oracle_model, table
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -37,16 +37,22 @@ def test_autograd_matches_oracle_vjp_full_size(setup):
     (model * torch.tensor(gm, dtype=torch.float32, device=dev)).sum().backward()
     gth, gb = theta.grad.double().cpu().numpy(), bb.grad.double().cpu().numpy()
     M = oracle_model(g)
+    worst_th = worst_b = 0.0
     for i in np.random.default_rng(8).choice(1024, 24, replace=False):
         rth, rb = O.model_vjp(M, th[i], b[i], gm[i])
         scale = np.abs(rth) + 1e-3 * np.abs(rth).max()
-        assert np.all(np.abs(gth[i] - rth) <= 1e-3 * scale), (i, gth[i], rth)
-        np.testing.assert_allclose(gb[i], rb, rtol=1e-4, atol=1e-4 * np.abs(rb).max())
+        worst_th = max(worst_th, float(np.max(np.abs(gth[i] - rth) / scale)))
+        worst_b = max(worst_b, float(np.max(np.abs(gb[i] - rb)) / np.abs(rb).max()))
+        assert np.all(np.abs(gth[i] - rth) <= GRAD_RTOL_THETA * scale), (i, gth[i], rth)
+        np.testing.assert_allclose(gb[i], rb, rtol=GRAD_TOL_LEG, atol=GRAD_TOL_LEG * np.abs(rb).max())
+    print(f"adjoint vs oracle VJP (24 of 1024): theta {worst_th:.2e} (bound {GRAD_RTOL_THETA:g}), "
+          f"Legendre {worst_b:.2e} of max (bound {GRAD_TOL_LEG:g})")
 
 
 def test_autograd_matches_central_differences(setup):
     """Central differences with h = 1e-4 relative, taken in FP64 on the
-    oracle's forward model, against the GPU adjoint (1e-3); and central
+    oracle's forward model, against the GPU adjoint (GRAD_RTOL_THETA, GRAD_TOL_LEG;
+    the differences' own truncation and rounding errors are below 1e-7); and central
     differences of the GPU's own FP32 forward with a step large enough for
     FP32 (3e-3 relative; median agreement 5e-2), so forward and adjoint of
     the CUDA path are consistent with each other."""
@@ -59,6 +65,7 @@ def test_autograd_matches_central_differences(setup):
     gmt = torch.tensor(gm[idx], dtype=torch.float32, device=dev)
     gth, gb = ip.backward(theta, bb, gmt)
     gth, gb = gth.double().cpu().numpy(), gb.double().cpu().numpy()
+    worst_th = worst_b = 0.0
     for n, i in enumerate(idx):
         f = lambda t, c: float(gm[i] @ O.model_flux(M, t, c)["model"])
         for k in range(5):
@@ -67,13 +74,17 @@ def test_autograd_matches_central_differences(setup):
             tp[k] += h
             tm[k] -= h
             fd = (f(tp, b[i]) - f(tm, b[i])) / (2 * h)
-            assert abs(fd - gth[n, k]) <= 1e-3 * abs(fd) + 1e-6 * np.abs(gth[n]).max(), (i, k, fd, gth[n, k])
+            worst_th = max(worst_th, abs(fd - gth[n, k]) / (abs(fd) + 1e-3 * np.abs(gth[n]).max()))
+            assert abs(fd - gth[n, k]) <= GRAD_RTOL_THETA * (abs(fd) + 1e-3 * np.abs(gth[n]).max()), (i, k, fd, gth[n, k])
         for k in range(DEG + 1):
             bp, bm = b[i].copy(), b[i].copy()
             bp[k] += 1e-4
             bm[k] -= 1e-4
             fd = (f(th[i], bp) - f(th[i], bm)) / 2e-4
-            assert abs(fd - gb[n, k]) <= 1e-3 * np.abs(gb[n]).max()
+            worst_b = max(worst_b, abs(fd - gb[n, k]) / np.abs(gb[n]).max())
+            assert abs(fd - gb[n, k]) <= GRAD_TOL_LEG * np.abs(gb[n]).max()
+    print(f"adjoint vs FP64 central differences: theta {worst_th:.2e} (bound {GRAD_RTOL_THETA:g}), "
+          f"Legendre {worst_b:.2e} of max (bound {GRAD_TOL_LEG:g})")
     # FD of the FP32 forward itself
     fg = lambda t, c: (ip.forward(t, c).double() * gmt.double()).sum(dim=1)
     for k in range(5):
@@ -83,4 +94,5 @@ def test_autograd_matches_central_differences(setup):
         tm[:, k] -= h
         fd = ((fg(tp, bb) - fg(tm, bb)) / (tp[:, k] - tm[:, k]).double()).cpu().numpy()
         rel = np.abs(fd - gth[:, k]) / (np.abs(gth[:, k]) + 1e-30)
+        print(f"FP32 forward differences, parameter {k}: median rel {np.median(rel):.2e} (bound 5e-2)")
         assert np.median(rel) < 5e-2, (k, rel)

@@ -10,7 +10,7 @@ import pytest
 
 import lasp_synth as S
 from oracle import oracle as O
-from tests.helpers import DEG, TOL, observed, oracle_model, table
+from tests.helpers import DEG, GRAD_RTOL_THETA, GRAD_TOL_LEG, TOL, observed, oracle_model, table
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -118,11 +118,14 @@ def test_backward_matches_oracle_vjp(lasp, grid):
     ip = interp(lasp, grid)
     gth, gb = ip.backward(T(d["theta0"]), T(b), T(gm))
     gth, gb = H(gth), H(gb)
+    worst = 0.0
     for i in range(6):
         rth, rb = O.model_vjp(M, d["theta0"][i], b[i], gm[i])
         scale_th = np.abs(rth) + 1e-3 * np.abs(rth).max()
-        assert np.all(np.abs(gth[i] - rth) <= 1e-3 * scale_th), (gth[i], rth)
-        np.testing.assert_allclose(gb[i], rb, rtol=1e-4, atol=1e-4 * np.abs(rb).max())
+        worst = max(worst, float(np.max(np.abs(gth[i] - rth) / scale_th)))
+        assert np.all(np.abs(gth[i] - rth) <= GRAD_RTOL_THETA * scale_th), (gth[i], rth)
+        np.testing.assert_allclose(gb[i], rb, rtol=GRAD_TOL_LEG, atol=GRAD_TOL_LEG * np.abs(rb).max())
+    print(f"{grid.name} adjoint vs oracle VJP: theta {worst:.2e} (bound {GRAD_RTOL_THETA:g})")
 
 
 # ------------------------------------------------ fits (stage 8)

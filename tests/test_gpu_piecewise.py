@@ -8,7 +8,7 @@ import pytest
 
 import lasp_synth as S
 from oracle import oracle as O
-from tests.helpers import DEG, TOL, observed, piecewise_model, pw_tables, table
+from tests.helpers import DEG, GRAD_RTOL_THETA, GRAD_TOL_LEG, TOL, observed, piecewise_model, pw_tables, table
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -85,11 +85,14 @@ def test_forward_and_backward_all_ranges(lasp):
     gm = q32(rng.normal(0, 1, (n, grid.n_pix)))
     gth, gb = ip.backward(T(th), T(b), T(gm))
     gth, gb = H(gth), H(gb)
+    worst = 0.0
     for i in range(n):
         rth, rb = O.model_vjp(M, th[i], b[i], gm[i])
         scale = np.abs(rth) + 1e-3 * np.abs(rth).max()
-        assert np.all(np.abs(gth[i] - rth) <= 1e-3 * scale), (i, th[i, 0], gth[i], rth)
-        np.testing.assert_allclose(gb[i], rb, rtol=1e-4, atol=1e-4 * np.abs(rb).max())
+        worst = max(worst, float(np.max(np.abs(gth[i] - rth) / scale)))
+        assert np.all(np.abs(gth[i] - rth) <= GRAD_RTOL_THETA * scale), (i, th[i, 0], gth[i], rth)
+        np.testing.assert_allclose(gb[i], rb, rtol=GRAD_TOL_LEG, atol=GRAD_TOL_LEG * np.abs(rb).max())
+    print(f"piecewise adjoint vs oracle VJP, all Teff ranges: theta {worst:.2e} (bound {GRAD_RTOL_THETA:g})")
 
 
 def _inputs(grid, n, seed, **kw):
