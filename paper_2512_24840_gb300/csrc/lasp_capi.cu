@@ -57,6 +57,12 @@ void prof_add(const char* name, float ms) {
 namespace lasp {
 int cuda_rc(cudaError_t e) {
     if (e == cudaSuccess) return LASP_OK;
+    // The runtime also keeps a failed call as this thread's last error, which
+    // the launch checks read with cudaGetLastError: reset it here, so that an
+    // error already returned (a failed allocation, say) is not reported again
+    // by a later, unrelated launch.  An error that corrupts the context is
+    // returned by every later call regardless.
+    (void)cudaGetLastError();
     if (e == cudaErrorMemoryAllocation) return LASP_ENOMEM;
     return LASP_ECUDA;
 }

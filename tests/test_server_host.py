@@ -94,3 +94,55 @@ def test_latency_percentiles_and_threaded_submit():
     assert len(res) == 100 and len({r.rid for r in res}) == 100
     pct = latency_percentiles(res)
     assert 0 < pct["p50_ms"] <= pct["p99_ms"]
+
+
+def test_stalled_producer_does_not_block_ticks():
+    """A producer thread that stops in mid-stream (here: waits on an event
+    that the test sets later) leaves the scheduler usable: ticks return the
+    fits already submitted, idle ticks return nothing at once, and the rest
+    complete once the producer resumes.  A producer that dies with an
+    exception leaves no half-submitted request behind."""
+    pools = {"a": FakePool(2)}
+    t = [0.0]
+    srv = Server(pools, chunk=4, clock=lambda: t[0])
+    go_on = threading.Event()
+    first = threading.Event()
+
+    def producer():
+        for s in (3, 6, 2):
+            srv.submit("a", *_req(s))
+        first.set()
+        go_on.wait(timeout=30)
+        for s in (5, 1):
+            srv.submit("a", *_req(s))
+        raise RuntimeError("producer dies after its last request")
+
+    errors = []
+    th = threading.Thread(target=lambda: _catch(producer, errors))
+    th.start()
+    assert first.wait(timeout=30)
+    done = []
+    for _ in range(10):                      # the producer is stalled meanwhile
+        t[0] += 1.0
+        done += srv.tick()
+    assert sorted(r.rid for r in done) == [0, 1, 2]
+    assert srv.pending() == 0
+    t[0] += 1.0
+    assert srv.tick() == []                  # idle tick: nothing admitted, nothing retired
+    go_on.set()
+    th.join(timeout=30)
+    assert not th.is_alive() and len(errors) == 1
+    assert srv.pending() == 2
+    while srv.pending():
+        t[0] += 1.0
+        done += srv.tick()
+    assert sorted(r.rid for r in done) == [0, 1, 2, 3, 4]
+    assert all(r.status == 1 for r in done)
+    assert len(srv.lanes["a"].free) == 2 and not srv.lanes["a"].busy
+
+
+def _catch(fn, errors):
+    try:
+        fn()
+    except RuntimeError as e:
+        errors.append(e)
