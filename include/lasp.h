@@ -91,8 +91,11 @@ extern "C" {
  * mapped linearly onto the box (stage 8 rescaling). */
 typedef struct {
     int K;                  /* basis terms, 1..32                                 */
-    int n_pix;              /* observed pixels p (>= 16)                          */
-    int pad;                /* H >= ceil(max|mu| + 5 max sigma) over the box      */
+    int n_pix;              /* observed pixels p >= 16, with the model grid
+                               n_pix + 2 pad <= 8192 (16 model pixels a thread
+                               of a 512-thread CTA); larger is LASP_EINVAL       */
+    int pad;                /* H >= ceil(max|mu| + 5 max sigma) over the box,
+                               at most 47 (2H+1 <= 95 taps)                      */
     double dln;             /* ln-lambda step of the grid (> 0)                   */
     const int8_t* exps;     /* host, K x 3 non-negative exponents (<= 8)          */
     double basis_lo[3], basis_hi[3];
@@ -133,7 +136,7 @@ void lasp_free_interp(lasp_interp h);
 typedef struct {
     int n_reg;              /* 1..3                                            */
     int K[3];               /* terms per regime, each >= 1, sum <= 96          */
-    int n_pix;              /* observed pixels p (>= 16)                       */
+    int n_pix;              /* p >= 16 with p + 2 pad <= 8192                  */
     int pad;                /* H, as lasp_interp_desc                          */
     double dln;             /* ln-lambda step of the grid (> 0)                */
     const int8_t* exps;     /* host, (sum K) x 3 non-negative exponents (<= 8) */

@@ -221,8 +221,8 @@ void lasp_default_opts(lasp_fit_opts* o) {
 int lasp_init_interp_piecewise(const lasp_piecewise_desc* d, const float* coeff, lasp_interp* out) {
     if (!d || !coeff || !out) return LASP_EINVAL;
     *out = nullptr;
-    if (d->n_reg < 1 || d->n_reg > NREG || d->n_pix < 16 || d->n_pix > 16 * 512 || d->pad < 0 ||
-        d->pad > HMAX || !(d->dln > 0.0) || !d->exps)
+    if (d->n_reg < 1 || d->n_reg > NREG || d->n_pix < 16 || d->pad < 0 || d->pad > HMAX ||
+        d->n_pix + 2 * d->pad > MODEL_PIX_MAX || !(d->dln > 0.0) || !d->exps)
         return LASP_EINVAL;
     int K = 0;
     for (int r = 0; r < d->n_reg; ++r) {

@@ -23,6 +23,12 @@ constexpr int PPT = 16;           // pixels per thread of the per-spectrum kerne
 constexpr int WINMAX = 64;        // stop-rule window supported
 constexpr int HMAX = 47;          // kernel half width supported (2H+1 <= 96 taps)
 constexpr int TAPS_MAX = 2 * HMAX + 1;
+constexpr int MODEL_PIX_MAX = PPT * 512;   // model pixels n_pix + 2 pad of one spectrum
+
+// Threads per CTA of the fit kernels (one-spectrum, multi-lane and the grouped
+// step body): each thread owns one run of PPT model pixels and the observed
+// pixels of the same indices, so the block covers the whole model grid.
+inline int fit_threads(int n_model) { return n_model <= PPT * 256 ? 256 : 512; }
 
 // Interpolator constants passed by value to every kernel.  A piecewise
 // interpolator (Eq. 1 with Teff regimes) stacks the rows of its regimes,

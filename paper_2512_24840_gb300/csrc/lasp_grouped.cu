@@ -267,7 +267,7 @@ int grp_pool_create(const ModelDev& M, const TcImages& tc, int n, const lasp_fit
     }
     G.bct = P->bct;
     if (!e) {
-        const int NT = M.n_pix <= 16 * 256 ? 256 : 512;
+        const int NT = fit_threads(M.n_model);
         if (NT == 256) {
             e = o->precision == LASP_PREC_TF32   ? pool_setup<6, 1, 256>(P)
                 : o->precision == LASP_PREC_BF16 ? pool_setup<6, 2, 256>(P)

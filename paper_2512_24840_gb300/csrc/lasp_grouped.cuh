@@ -1183,7 +1183,7 @@ int run_grouped(Grp& G, const TcImages& tc, cudaStream_t st, int* launches) {
 // unit (lasp_grouped.cu for D = 6, lasp_grp_d<D>.cu for the others).
 template <int D>
 int grp_run_deg(Grp& G, const TcImages& tc, const lasp_fit_opts* o, cudaStream_t st, int* launches) {
-    const int NT = G.M.n_pix <= 16 * 256 ? 256 : 512;
+    const int NT = fit_threads(G.M.n_model);
     if (NT == 256) {
         if (o->precision == LASP_PREC_TF32) return run_grouped<D, 1, 256>(G, tc, st, launches);
         if (o->precision == LASP_PREC_BF16) return run_grouped<D, 2, 256>(G, tc, st, launches);

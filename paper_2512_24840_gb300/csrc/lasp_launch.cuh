@@ -28,7 +28,7 @@ constexpr int FIT_LANES = 4;
 // Whether resumable slots of this table and degree run on fit_multi_kernel
 // (its shared memory fits), with y, W rows of 2 ldw floats per slot.
 inline bool fit_multi_slots_ok(int p, int H, int nm, int K, int D) {
-    const int NT = p <= 16 * 256 ? 256 : 512;
+    const int NT = fit_threads(nm);
     return fit_multi_smem_bytes(p, H, nm, NT, D, K, FIT_LANES, true) <= 227 * 1024 &&
            4 * (size_t)fit_prep_smem_floats(p) <= 227 * 1024;
 }
@@ -44,7 +44,7 @@ template <int D>
 int launch_fit(const FitParams& P, cudaStream_t st) {
     const int p = P.M.n_pix, H = P.M.pad, nm = P.M.n_model;
     return prof_time("fit_kernel", st, [&]() {
-        if (p <= 16 * 256) {
+        if (fit_threads(nm) == 256) {
             size_t smem = fit_smem_bytes(p, H, nm, 256, D, P.M.K);
             int e = set_smem_attr(fit_kernel<256, D>, smem);
             if (e) return e;
@@ -71,7 +71,7 @@ int launch_fit_multi(const FitParams& P, cudaStream_t st, int* n_launch) {
     constexpr int S = FIT_LANES;
     if (n_launch) *n_launch = 1;             // fit_kernel alone where it falls back
     const int p = P.M.n_pix, H = P.M.pad, nm = P.M.n_model;
-    const int NT = p <= 16 * 256 ? 256 : 512;
+    const int NT = fit_threads(nm);
     const bool full = P.O.clean || P.O.fp64_ne == LASP_NE_FP64;
     const size_t smem = fit_multi_smem_bytes(p, H, nm, NT, D, P.M.K, S, full);
     const size_t smem_prep = 4 * (size_t)fit_prep_smem_floats(p);
@@ -149,7 +149,7 @@ template <int D>
 int launch_fit_multi_slots(const FitParams& P, const MultiWs& W, int n_running, cudaStream_t st) {
     constexpr int S = FIT_LANES;
     const int p = P.M.n_pix, H = P.M.pad, nm = P.M.n_model;
-    const int NT = p <= 16 * 256 ? 256 : 512;
+    const int NT = fit_threads(nm);
     // the Clean update and the FP64 normal equations only where the options ask for them
     const bool full = P.O.clean || P.O.fp64_ne == LASP_NE_FP64;
     const size_t smem = fit_multi_smem_bytes(p, H, nm, NT, D, P.M.K, S, full);
@@ -186,7 +186,7 @@ template <int D>
 int launch_fit_prep_slots(const FitParams& P, const MultiWs& W, const int32_t* idx, int count,
                           cudaStream_t st) {
     const int p = P.M.n_pix;
-    const int NT = p <= 16 * 256 ? 256 : 512;
+    const int NT = fit_threads(P.M.n_model);      // as the batch fit's preprocessing: the same sums
     const size_t smem = 4 * (size_t)fit_prep_smem_floats(p);
     void (*prep)(const FitParams, const MultiWs, const int32_t*) =
         NT == 256 ? fit_prep_slots_kernel<256, D> : fit_prep_slots_kernel<512, D>;
@@ -210,7 +210,7 @@ int launch_errors(const ErrParams& P, cudaStream_t st) {
     };
     return prof_time(f64 ? "errors_kernel<fp64>" : "errors_kernel", st, [&]() {
         int e;
-        if (p <= 16 * 256) e = f64 ? go(errors_kernel<256, D, true>, 256) : go(errors_kernel<256, D, false>, 256);
+        if (fit_threads(nm) == 256) e = f64 ? go(errors_kernel<256, D, true>, 256) : go(errors_kernel<256, D, false>, 256);
         else e = f64 ? go(errors_kernel<512, D, true>, 512) : go(errors_kernel<512, D, false>, 512);
         return e ? e : cuda_rc(cudaGetLastError());
     });
@@ -220,7 +220,7 @@ template <int D>
 int launch_forward(const ModelParams& P, cudaStream_t st) {
     const int p = P.M.n_pix, H = P.M.pad, nm = P.M.n_model;
     size_t smem = model_smem_bytes(p, H, nm);
-    if (p <= 16 * 256) {
+    if (fit_threads(nm) == 256) {
         int e = set_smem_attr(forward_kernel<256, D>, smem);
         if (e) return e;
         forward_kernel<256, D><<<P.N, 256, smem, st>>>(P);
@@ -236,7 +236,7 @@ template <int D>
 int launch_backward(const ModelParams& P, cudaStream_t st) {
     const int p = P.M.n_pix, H = P.M.pad, nm = P.M.n_model;
     size_t smem = model_smem_bytes(p, H, nm);
-    if (p <= 16 * 256) {
+    if (fit_threads(nm) == 256) {
         int e = set_smem_attr(backward_kernel<256, D>, smem);
         if (e) return e;
         backward_kernel<256, D><<<P.N, 256, smem, st>>>(P);
@@ -252,7 +252,7 @@ template <int D>
 int launch_lm(const LmParams& P, cudaStream_t st) {
     const int p = P.M.n_pix, H = P.M.pad, nm = P.M.n_model;
     return prof_time("lm_kernel", st, [&]() {
-        if (p <= 16 * 256) {
+        if (fit_threads(nm) == 256) {
             size_t smem = lm_smem_bytes(p, H, nm, 256);
             int e = set_smem_attr(lm_kernel<256, D>, smem);
             if (e) return e;

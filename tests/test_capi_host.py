@@ -69,6 +69,16 @@ def test_init_validation(lasp):
     d = _desc(lasp, g, exps=bad)
     assert lib.lasp_init_interp(ct.byref(d), C.ctypes.data, ct.byref(h)) == lasp.EINVAL
     assert lib.lasp_init_interp(None, C.ctypes.data, ct.byref(h)) == lasp.EINVAL
+    # the largest accepted sizes: 8192 model pixels (n_pix + 2 pad), a margin of 47 pixels
+    big = S.Grid("over", 8192 - 2 * S.DESI.pad + 1, 3600.0, S.DESI.dln)
+    assert big.n_model == 8193
+    Cb = np.zeros((26, big.n_model), dtype=np.float32)
+    d = _desc(lasp, big, exps=exps)
+    assert lib.lasp_init_interp(ct.byref(d), Cb.ctypes.data, ct.byref(h)) == lasp.EINVAL
+    d = _desc(lasp, g, pad=48, exps=exps)
+    Cp = np.zeros((26, g.n_pix + 96), dtype=np.float32)
+    assert lib.lasp_init_interp(ct.byref(d), Cp.ctypes.data, ct.byref(h)) == lasp.EINVAL
+    assert not h.value
 
 
 def test_no_device_is_reported(lasp):
