@@ -170,6 +170,7 @@ class DevicePool:
         ring = [(s, q.staged) for s, q in zip(slots, reqs) if q.staged >= 0]
         rest = [(s, q) for s, q in zip(slots, reqs) if q.staged < 0]
         off = 0
+        admitted_to = self._admitted_to    # taken over only once every copy is enqueued
         if ring:
             # staged requests are admitted in staging order: one run of ring
             # indices, at most two contiguous ranges
@@ -184,7 +185,7 @@ class DevicePool:
                 self._admit_rows(m, done, self.r_flux[k].data_ptr(), self.r_ivar[k].data_ptr(),
                                  self.r_good[k].data_ptr(), self.r_th0[k].data_ptr())
                 done += m
-            self._admitted_to = first + n
+            admitted_to = first + n
             off = n
         if rest:
             # unstaged requests: one stacked copy per array into the staging rows
@@ -197,6 +198,7 @@ class DevicePool:
             self._admit_rows(n, off, self.h_flux.data_ptr(), self.h_ivar.data_ptr(),
                              self.h_good.data_ptr(), self.h_th0.data_ptr())
         assert off + len(rest) == c
+        self._admitted_to = admitted_to
 
     def step(self, budget: int, n_running: int | None = None):
         """lasp_slots_step; with n_running (the caller's count of running
@@ -319,7 +321,16 @@ class Server:
                 reqs = [lane.waiting.popleft() for _ in range(n)]
             slots = [lane.free.pop() for _ in range(n)]
             if n:
-                lane.pool.admit(slots, reqs)
+                try:
+                    lane.pool.admit(slots, reqs)
+                except BaseException:
+                    # nothing is committed: the slots stay free and the requests
+                    # wait again, in order, for the next tick (a pool keeps the
+                    # ring entries of requests it did not admit)
+                    lane.free.extend(reversed(slots))
+                    with self._lock:
+                        lane.waiting.extendleft(reversed(reqs))
+                    raise
                 for s, q in zip(slots, reqs):
                     lane.busy[s] = q
             if lane.busy:

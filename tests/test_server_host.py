@@ -146,3 +146,47 @@ def _catch(fn, errors):
         fn()
     except RuntimeError as e:
         errors.append(e)
+
+
+class FlakyPool(FakePool):
+    """Admission fails once (as a device copy might), before anything is admitted."""
+
+    def __init__(self, n_slots, fail_at):
+        super().__init__(n_slots)
+        self.calls = 0
+        self.fail_at = fail_at
+
+    def admit(self, slots, reqs):
+        self.calls += 1
+        if self.calls == self.fail_at:
+            raise RuntimeError("admission failed")
+        super().admit(slots, reqs)
+
+
+def test_failed_admission_is_rolled_back():
+    """An admission that raises leaves its slots free and its requests
+    waiting in submission order; the next tick admits them and every request
+    completes once."""
+    pool = FlakyPool(3, fail_at=2)
+    t = [0.0]
+    srv = Server({"a": pool}, chunk=5, clock=lambda: t[0])
+    ids = [srv.submit("a", *_req(s)) for s in (4, 12, 3, 7, 9)]
+    done = []
+    t[0] += 1.0
+    done += srv.tick()                      # admits 0, 1, 2; 0 and 2 finish
+    assert sorted(r.rid for r in done) == [0, 2]
+    t[0] += 1.0
+    try:
+        srv.tick()                          # the admission of 3 and 4 fails
+        raise AssertionError("the failing admission did not raise")
+    except RuntimeError:
+        pass
+    lane = srv.lanes["a"]
+    assert [q.rid for q in lane.waiting] == [3, 4]
+    assert sorted(lane.free) == [0, 2] and list(lane.busy) == [1]
+    assert srv.pending() == 3
+    while srv.pending():
+        t[0] += 1.0
+        done += srv.tick()
+    assert sorted(r.rid for r in done) == ids
+    assert pool.admitted == [0, 1, 2, 3, 4]
