@@ -171,6 +171,29 @@ def _dev(t, dtype):
     return t
 
 
+def _arg(t, dtype, shape, name):
+    """Dtype and shape (None matches any extent) of a tensor argument, checked
+    before its pointer reaches the library, which sizes every buffer from N
+    and the grid."""
+    if not isinstance(t, torch.Tensor) or t.dtype != dtype:
+        raise TypeError(f"{name}: expected a {dtype} tensor")
+    if t.dim() != len(shape) or any(n is not None and t.shape[k] != n for k, n in enumerate(shape)):
+        want = "x".join("*" if n is None else str(n) for n in shape)
+        raise ValueError(f"{name}: shape {tuple(t.shape)}, expected {want}")
+    return t
+
+
+def _on_device(**ts):
+    """The tensors of one call: contiguous, on CUDA and on one device (the
+    kernels run on the current device)."""
+    for name, t in ts.items():
+        if t is not None and not (t.is_cuda and t.is_contiguous()):
+            raise TypeError(f"{name}: expected a contiguous CUDA tensor")
+    devs = {t.device for t in ts.values() if t is not None}
+    if len(devs) > 1:
+        raise ValueError(f"tensor arguments on several devices: {sorted(str(d) for d in devs)}")
+
+
 def default_opts(**kw) -> FitOpts:
     o = FitOpts()
     load().lasp_default_opts(ct.byref(o))
@@ -331,6 +354,7 @@ class Interp:
         if flux.shape != (N, self.n_pix) or ivar.shape != flux.shape or good.shape != flux.shape \
                 or theta0.shape != (N, 5):
             raise ValueError("batch shapes must be N x n_pix (and N x 5 for theta0)")
+        _on_device(flux=flux, ivar=ivar, good=good, theta0=theta0)
         return Batch(N, self.n_pix, flux.data_ptr(), ivar.data_ptr(), good.data_ptr(),
                      theta0.data_ptr())
 
@@ -347,6 +371,16 @@ class Interp:
                        status=torch.empty(N, device=dev, dtype=torch.int32),
                        cont=torch.empty((N, o.legendre_deg + 1), device=dev),
                        weight=torch.empty(N, device=dev))
+        else:      # the caller's buffers: the library writes N rows into each
+            f32, i32 = torch.float32, torch.int32
+            _arg(out["theta"], f32, (N, 5), "out['theta']"), _arg(out["loss"], f32, (N,), "out['loss']")
+            _arg(out["steps"], i32, (N,), "out['steps']"), _arg(out["status"], i32, (N,), "out['status']")
+            if out.get("cont") is not None:
+                _arg(out["cont"], f32, (N, o.legendre_deg + 1), "out['cont']")
+            if out.get("weight") is not None:
+                _arg(out["weight"], f32, (N,), "out['weight']")
+            _on_device(flux=flux, **{f"out['{k}']": out.get(k)
+                                     for k in ("theta", "loss", "steps", "status", "cont", "weight")})
         r = Result(out["theta"].data_ptr(), out["loss"].data_ptr(), out["steps"].data_ptr(),
                    out["status"].data_ptr(),
                    out["cont"].data_ptr() if out.get("cont") is not None else None,
@@ -368,16 +402,23 @@ class Interp:
         return dict(sigma=sigma, cov=cov, status=status)
 
     def forward(self, theta, b, stream=None):
-        _dev(theta, torch.float32), _dev(b, torch.float32)
-        N, deg = theta.shape[0], b.shape[1] - 1
+        _arg(theta, torch.float32, (None, 5), "theta")
+        N = theta.shape[0]
+        _arg(b, torch.float32, (N, None), "b")
+        _on_device(theta=theta, b=b)
+        deg = b.shape[1] - 1
         model = torch.empty((N, self.n_pix), device=theta.device)
         _check(load().lasp_forward(self._h, N, _ptr(theta), _ptr(b), deg, _ptr(model),
                                    _stream(stream)), "lasp_forward")
         return model
 
     def backward(self, theta, b, gmodel, stream=None):
-        _dev(theta, torch.float32), _dev(b, torch.float32), _dev(gmodel, torch.float32)
-        N, deg = theta.shape[0], b.shape[1] - 1
+        _arg(theta, torch.float32, (None, 5), "theta")
+        N = theta.shape[0]
+        _arg(b, torch.float32, (N, None), "b")
+        _arg(gmodel, torch.float32, (N, self.n_pix), "gmodel")
+        _on_device(theta=theta, b=b, gmodel=gmodel)
+        deg = b.shape[1] - 1
         gtheta = torch.empty((N, 5), device=theta.device)
         gb = torch.empty((N, deg + 1), device=theta.device)
         _check(load().lasp_backward(self._h, N, _ptr(theta), _ptr(b), deg, _ptr(gmodel),
@@ -385,7 +426,8 @@ class Interp:
         return gtheta, gb
 
     def interp_eval(self, theta, precision="fp32", stream=None):
-        _dev(theta, torch.float32)
+        _arg(theta, torch.float32, (None, 5), "theta")
+        _on_device(theta=theta)
         N = theta.shape[0]
         Fp = torch.empty((N, self.n_model), device=theta.device)
         _check(load().lasp_interp_eval(self._h, N, _ptr(theta), _ptr(Fp), PREC[precision],

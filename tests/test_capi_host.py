@@ -145,3 +145,28 @@ def test_header_is_plain_c(tmp_path):
                         f"-I{inc}", str(src), "-o", str(tmp_path / "use_lasp.o")],
                        capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_binding_checks_tensor_shapes_before_any_call(lasp):
+    """The binding checks each tensor's dtype and shape before its pointer
+    reaches the library (which sizes every buffer from N and the grid), then
+    that it is a contiguous CUDA tensor: host tensors never reach a kernel."""
+    torch = pytest.importorskip("torch")
+    ip = object.__new__(lasp.Interp)
+    ip._h, ip.n_pix, ip.n_model = None, 16, 56
+    f = lambda *shape: torch.zeros(shape, dtype=torch.float32)
+    with pytest.raises(ValueError, match="theta"):
+        ip.forward(f(3, 4), f(3, 7))
+    with pytest.raises(ValueError, match="b"):
+        ip.forward(f(3, 5), f(2, 7))
+    with pytest.raises(ValueError, match="gmodel"):
+        ip.backward(f(3, 5), f(3, 7), f(3, 15))
+    with pytest.raises(ValueError, match="theta"):
+        ip.interp_eval(f(3, 5, 1))
+    with pytest.raises(TypeError, match="b"):
+        ip.forward(f(3, 5), torch.zeros((3, 7), dtype=torch.float64))
+    # right dtypes and shapes, but host tensors
+    with pytest.raises(TypeError, match="CUDA"):
+        ip.backward(f(3, 5), f(3, 7), f(3, 16))
+    with pytest.raises(TypeError, match="CUDA"):
+        ip.forward(f(0, 5), f(0, 7))
