@@ -170,3 +170,24 @@ def test_binding_checks_tensor_shapes_before_any_call(lasp):
         ip.backward(f(3, 5), f(3, 7), f(3, 16))
     with pytest.raises(TypeError, match="CUDA"):
         ip.forward(f(0, 5), f(0, 7))
+
+
+def test_every_accepted_grid_can_launch(tmp_path):
+    """tests/limits_host.cu, built as host code and run here: over every grid
+    lasp_init_interp accepts, the fit kernels' blocks cover the model grid and
+    every kernel's shared memory fits a CTA (no device needed)."""
+    import shutil
+    import subprocess
+    nvcc = next((c for c in ("/usr/local/cuda/bin/nvcc", shutil.which("nvcc")) if c and os.path.exists(c)), None)
+    if nvcc is None:
+        pytest.skip("no nvcc")
+    exe = tmp_path / "limits_host"
+    r = subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=compute_103a", "-O1", "-std=c++17",
+                        f"-I{os.path.join(ROOT, 'include')}",
+                        f"-I{os.path.join(ROOT, 'paper_2512_24840_gb300', 'csrc')}",
+                        os.path.join(ROOT, "tests", "limits_host.cu"), "-o", str(exe)],
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=600)
+    print(r.stdout)
+    assert r.returncode == 0, r.stdout
