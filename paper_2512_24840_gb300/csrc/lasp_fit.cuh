@@ -25,6 +25,9 @@ namespace lasp {
 
 constexpr int TB = 12;       // taps per block
 constexpr int TAPBUF = 128; // tap buffer (>= 2 HMAX + 2 TB + 1)
+// the correlations read taps in whole blocks of TB past the widest kernel (2 HMAX + 1 taps)
+static_assert(TAPBUF >= 2 * HMAX + 2 * TB + 1, "tap buffer shorter than the widest kernel in blocks");
+static_assert(MODEL_PIX_MAX == PPT * 512, "the largest model grid is one run of PPT pixels per thread of 512");
 constexpr int NADJ = 7;     // end-of-step sums: S, nonpos, d/dmu, d/dsigma, d/d(Teff, logg, FeH)
 
 // Device-resident fit state of resumable slots (struct of arrays, S slots).
