@@ -2,6 +2,7 @@
 every symbol include/lasp.h declares, and rejects bad arguments before any
 device work."""
 import ctypes as ct
+import math
 import os
 import re
 
@@ -191,3 +192,60 @@ def test_every_accepted_grid_can_launch(tmp_path):
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=600)
     print(r.stdout)
     assert r.returncode == 0, r.stdout
+
+
+def _pw_desc(lasp, g, Ks, pad=None, n_pix=None, tb=(4000.0, 4550.0, 7000.0, 9000.0)):
+    exps = np.ascontiguousarray(np.concatenate([S.EXPS[:k] for k in Ks]), dtype=np.int8) \
+        if sum(Ks) <= 3 * len(S.EXPS) else np.zeros((sum(Ks), 3), np.int8)
+    d = lasp.PiecewiseDesc()
+    d.n_reg = len(Ks)
+    for r, k in enumerate(Ks[:3]):
+        d.K[r] = k
+    d.n_pix = g.n_pix if n_pix is None else n_pix
+    d.pad = g.pad if pad is None else pad
+    d.dln = g.dln
+    d.exps = exps.ctypes.data
+    lo = [math.log10(3000.0), 0.5, -2.5]
+    for r in range(3):
+        for k in range(3):
+            d.basis_lo[r][k] = lo[k] + 0.1 * r
+            d.basis_hi[r][k] = lo[k] + 1.0 + 0.1 * r
+    d.teff_blend = (ct.c_double * 4)(*tb)
+    d.box_lo = (ct.c_double * 5)(*S.BOX_LO)
+    d.box_hi = (ct.c_double * 5)(*S.BOX_HI)
+    return d, exps
+
+
+def test_piecewise_init_validation(lasp):
+    """lasp_init_interp_piecewise rejects bad descriptors before any device
+    work: regime count outside 1..3, a regime without terms, more than 96 rows,
+    blend bounds not increasing, a margin above 47 or a model grid above 8192
+    pixels (LASP_EINVAL), and a margin too small for the box (LASP_EGRID)."""
+    lib = lasp.load()
+    lib.lasp_init_interp_piecewise.argtypes = [ct.c_void_p, ct.c_void_p, ct.c_void_p]
+    g = S.SMALL
+    h = ct.c_void_p()
+    C = np.zeros((200, g.n_pix + 2 * 47 + 200), dtype=np.float32)
+
+    def rc(*a, **k):
+        d, exps = _pw_desc(lasp, g, *a, **k)
+        return lib.lasp_init_interp_piecewise(ct.byref(d), C.ctypes.data, ct.byref(h))
+
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        # the descriptor the cases below spoil one field of is itself valid:
+        # without a device it gets as far as the device check
+        assert rc([25, 26, 19]) == lasp.ENODEV
+    d, _ = _pw_desc(lasp, g, [25, 26, 19])
+    d.n_reg = 0
+    assert lib.lasp_init_interp_piecewise(ct.byref(d), C.ctypes.data, ct.byref(h)) == lasp.EINVAL
+    d.n_reg = 4
+    assert lib.lasp_init_interp_piecewise(ct.byref(d), C.ctypes.data, ct.byref(h)) == lasp.EINVAL
+    assert rc([25, 0, 19]) == lasp.EINVAL
+    assert rc([40, 40, 20]) == lasp.EINVAL                       # 100 rows > 96
+    assert rc([25, 26, 19], tb=(4000.0, 3900.0, 7000.0, 9000.0)) == lasp.EINVAL
+    assert rc([25, 26, 19], pad=48) == lasp.EINVAL
+    assert rc([25, 26, 19], n_pix=8192 - 2 * g.pad + 1) == lasp.EINVAL
+    assert rc([25, 26, 19], pad=g.pad - 1) == lasp.EGRID
+    assert lib.lasp_init_interp_piecewise(None, C.ctypes.data, ct.byref(h)) == lasp.EINVAL
+    assert not h.value
