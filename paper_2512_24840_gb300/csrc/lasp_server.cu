@@ -34,6 +34,7 @@ int64_t now_ns() {
 
 int cuda_e(cudaError_t e) {
     if (e == cudaSuccess) return LASP_OK;
+    (void)cudaGetLastError();    // returned here: not to be reported again by a later launch check
     return e == cudaErrorMemoryAllocation ? LASP_ENOMEM : LASP_ECUDA;
 }
 
