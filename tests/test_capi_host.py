@@ -249,3 +249,43 @@ def test_piecewise_init_validation(lasp):
     assert rc([25, 26, 19], pad=g.pad - 1) == lasp.EGRID
     assert lib.lasp_init_interp_piecewise(None, C.ctypes.data, ct.byref(h)) == lasp.EINVAL
     assert not h.value
+
+
+def test_binding_structs_match_the_header(lasp, tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets
+    of the C struct in include/lasp.h (compiled by the host C compiler), and
+    the numpy view of lasp_served matches too."""
+    import shutil
+    import subprocess
+    from paper_2512_24840_gb300 import server
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    structs = {"lasp_interp_desc": lasp.InterpDesc, "lasp_piecewise_desc": lasp.PiecewiseDesc,
+               "lasp_batch": lasp.Batch, "lasp_fit_opts": lasp.FitOpts, "lasp_result": lasp.Result,
+               "lasp_kernel_time": lasp.KernelTime, "lasp_served": server._Served}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "lasp.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in cls._fields_:
+            lines.append(f'    printf("{cname} {f[0]} %zu\\n", offsetof({cname}, {f[0]}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run(["gcc", "-std=c99", f"-I{os.path.join(ROOT, 'include')}", str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    c = {}
+    for line in out:
+        if line:
+            cname, field, v = line.split()
+            c[(cname, field)] = int(v)
+    for cname, cls in structs.items():
+        assert ct.sizeof(cls) == c[(cname, "size")], cname
+        for f in cls._fields_:
+            assert getattr(cls, f[0]).offset == c[(cname, f[0])], (cname, f[0])
+    dt = server._SERVED_DT
+    assert dt.itemsize == c[("lasp_served", "size")]
+    for name in dt.names:
+        assert dt.fields[name][1] == c[("lasp_served", name)], name
