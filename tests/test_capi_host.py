@@ -289,3 +289,55 @@ def test_binding_structs_match_the_header(lasp, tmp_path):
     assert dt.itemsize == c[("lasp_served", "size")]
     for name in dt.names:
         assert dt.fields[name][1] == c[("lasp_served", name)], name
+
+
+def _prototypes():
+    """name -> (return type, [parameter types]) of every lasp_* prototype in
+    include/lasp.h, each parameter reduced to pointer / int / int64 / float /
+    double (the opaque handle typedefs are pointers)."""
+    txt = open(os.path.join(ROOT, "include", "lasp.h")).read()
+    txt = re.sub(r"/\*.*?\*/", " ", txt, flags=re.S)
+    txt = re.sub(r"^\s*#.*$", " ", txt, flags=re.M)           # preprocessor lines
+    txt = re.sub(r"\s+", " ", txt)
+    handles = {"lasp_interp", "lasp_slots", "lasp_server"}
+    kinds = {"int": "int", "int32_t": "int", "uint32_t": "int", "int64_t": "int64", "float": "float",
+             "double": "double"}
+    protos = {}
+    for chunk in re.split(r"[;{}]", txt):
+        m = re.fullmatch(r"\s*([A-Za-z_][\w ]*?\**)\s*\b(lasp_\w+)\s*\(([^)]*)\)\s*", chunk)
+        if not m or m.group(1).strip() in ("typedef", "struct"):
+            continue
+        ret, name, params = m.groups()
+        ps = []
+        for prm in [p.strip() for p in params.split(",")]:
+            if prm in ("", "void"):
+                continue
+            words = prm.replace("*", " * ").split()
+            if "*" in words:
+                ps.append("pointer")
+            else:
+                base = [w for w in words[:-1] if w not in ("const", "unsigned")]
+                ps.append("pointer" if base[-1] in handles else kinds[base[-1]])
+        protos[name] = (ret.strip(), ps)
+    return protos
+
+
+def test_binding_signatures_match_the_header(lasp):
+    """The argument lists the binding declares to ctypes have the header's
+    arity and, parameter by parameter, its kind (pointer, int, int64, float,
+    double)."""
+    lib = lasp.load()
+    protos = _prototypes()
+    kind = {ct.c_void_p: "pointer", ct.c_char_p: "pointer", ct.c_int: "int", ct.c_int64: "int64",
+            ct.c_float: "float", ct.c_double: "double"}
+    checked = 0
+    for name, (ret, params) in protos.items():
+        fn = getattr(lib, name)
+        if fn.argtypes is None:
+            continue              # declared where it is used (slot pools, tests)
+        got = [kind.get(a, "pointer" if hasattr(a, "contents") or a.__name__.startswith("LP_") else "?")
+               for a in fn.argtypes]
+        assert got == params, (name, got, params)
+        checked += 1
+    assert checked >= 20, checked
+    assert protos["lasp_strerror"][0].endswith("*") and lib.lasp_strerror.restype is ct.c_char_p
